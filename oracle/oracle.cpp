@@ -1,0 +1,1157 @@
+// CPU oracle for the TPC track-finding and refit hot path.
+//
+// TEST INFRASTRUCTURE ONLY: this file is compiled into oracle/liborc.so, which
+// only the tests, the smoke check and the CPU-baseline leg of the benchmark
+// load. It shares no source with the CUDA library.
+//
+// It is deliberately plain: brute-force loops over the clusters of a pad row,
+// full 5x5 matrices, one track at a time, in the order the method states.
+// Section references are to arXiv:1811.11481. Three arithmetic types
+// instantiate the same templates:
+//   double - the FP64 reference for continuous outputs;
+//   float  - the FP32 mirror: every decision (windows, argmins, chi2 cuts) is
+//            taken in single precision, one IEEE rounding per written
+//            operation, so the discrete outputs of an FP32 implementation of
+//            the same formulas can be compared exactly;
+//   Var    - a reverse-mode tape over double that differentiates the FP64
+//            refit for the gradient reference (no hand-derived adjoint here).
+// In FP32 the only inverse sine (arc length of a helix chord) is evaluated
+// with the half-angle identity asin(h) = 2 asin(h / sqrt(2 (1 + sqrt(1-h^2))))
+// and the Maclaurin series of asin(h)/h: a fixed sequence of IEEE operations.
+//
+// Parity unpinned: the cellular-automaton cut values (neighbour windows, the
+// pick-up cut, the miss limit) are readings of Sec. 2 and Sec. 4, which give no
+// numbers; the tests pin the arithmetic and the invariants, not those values.
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <map>
+#include <vector>
+
+namespace {
+
+// ------------------------------------------------------------------ tape AD
+struct Tape {
+  std::vector<int> pa, pb;
+  std::vector<double> da, db;
+  std::vector<double> adj;
+  void clear() { pa.clear(); pb.clear(); da.clear(); db.clear(); adj.clear(); }
+  int push(int a, double ga, int b, double gb) {
+    pa.push_back(a); da.push_back(ga); pb.push_back(b); db.push_back(gb);
+    return (int)pa.size() - 1;
+  }
+  void backward(int root, double seed) {
+    adj.assign(pa.size(), 0.0);
+    if (root < 0) return;
+    adj[root] = seed;
+    for (int i = root; i >= 0; --i) {
+      double g = adj[i];
+      if (g == 0.0) continue;
+      if (pa[i] >= 0) adj[pa[i]] += g * da[i];
+      if (pb[i] >= 0) adj[pb[i]] += g * db[i];
+    }
+  }
+};
+Tape g_tape;
+
+struct Var {
+  double v;
+  int id;
+  Var() : v(0.0), id(-1) {}
+  Var(double x) : v(x), id(-1) {}
+  static Var leaf(double x) { Var r(x); r.id = g_tape.push(-1, 0.0, -1, 0.0); return r; }
+};
+inline Var mk(double v, int a, double ga, int b, double gb) {
+  Var r(v);
+  if (a >= 0 || b >= 0) r.id = g_tape.push(a, ga, b, gb);
+  return r;
+}
+inline Var operator+(Var a, Var b) { return mk(a.v + b.v, a.id, 1.0, b.id, 1.0); }
+inline Var operator-(Var a, Var b) { return mk(a.v - b.v, a.id, 1.0, b.id, -1.0); }
+inline Var operator-(Var a) { return mk(-a.v, a.id, -1.0, -1, 0.0); }
+inline Var operator*(Var a, Var b) { return mk(a.v * b.v, a.id, b.v, b.id, a.v); }
+inline Var operator/(Var a, Var b) {
+  double q = a.v / b.v;
+  return mk(q, a.id, 1.0 / b.v, b.id, -q / b.v);
+}
+inline bool operator<(Var a, Var b) { return a.v < b.v; }
+inline bool operator>(Var a, Var b) { return a.v > b.v; }
+inline bool operator<=(Var a, Var b) { return a.v <= b.v; }
+inline bool operator>=(Var a, Var b) { return a.v >= b.v; }
+inline bool operator==(Var a, Var b) { return a.v == b.v; }
+
+inline double val(double x) { return x; }
+inline double val(float x) { return x; }
+inline double val(Var x) { return x.v; }
+
+inline float sqrt_(float x) { return std::sqrt(x); }
+inline double sqrt_(double x) { return std::sqrt(x); }
+inline Var sqrt_(Var a) {
+  double s = std::sqrt(a.v);
+  return mk(s, a.id, 0.5 / s, -1, 0.0);
+}
+inline float abs_(float x) { return std::fabs(x); }
+inline double abs_(double x) { return std::fabs(x); }
+inline Var abs_(Var a) { return a.v < 0 ? -a : a; }
+inline Var asin_(Var a) {
+  return mk(std::asin(a.v), a.id, 1.0 / std::sqrt(1.0 - a.v * a.v), -1, 0.0);
+}
+
+// Wide type: float64 timestamps stay float64 in the FP32 mirror (Sec. 4).
+template <class R> struct WideT { using T = double; };
+template <> struct WideT<Var> { using T = Var; };
+template <class R> using W = typename WideT<R>::T;
+template <class R> R narrow(W<R> x);
+template <> float narrow<float>(double x) { return (float)x; }
+template <> double narrow<double>(double x) { return x; }
+template <> Var narrow<Var>(Var x) { return x; }
+
+// A(h) = asin(h)/h and B(h) = A'(h) = (1/sqrt(1-h^2) - A(h))/h.
+inline float seriesA_f(float h2) {
+  float p = 35.0f / 1152.0f;
+  p = 5.0f / 112.0f + h2 * p;
+  p = 3.0f / 40.0f + h2 * p;
+  p = 1.0f / 6.0f + h2 * p;
+  p = 1.0f + h2 * p;
+  return p;
+}
+inline float A_of(float h) {
+  if (std::fabs(h) < 0.125f) return seriesA_f(h * h);
+  if (!(std::fabs(h) <= 1.0f)) return NAN;
+  float hh = h, m = 1.0f;
+  while (std::fabs(hh) >= 0.125f) {
+    float c = std::sqrt(1.0f - hh * hh);
+    hh = hh / std::sqrt(2.0f * (1.0f + c));
+    m = m * 2.0f;
+  }
+  return ((m * hh) * seriesA_f(hh * hh)) / h;
+}
+inline float B_of(float h) {
+  if (std::fabs(h) < 0.125f) {
+    float h2 = h * h;
+    float c = 315.0f / 1408.0f;
+    c = 35.0f / 144.0f + h2 * c;
+    c = 15.0f / 56.0f + h2 * c;
+    c = 3.0f / 10.0f + h2 * c;
+    c = 1.0f / 3.0f + h2 * c;
+    return h * c;
+  }
+  float e = 1.0f / std::sqrt(1.0f - h * h);
+  return (e - A_of(h)) / h;
+}
+// FP64: Maclaurin coefficients e_n of (1-h^2)^(-1/2) from their recurrence
+// e_{n+1} = e_n (2n+1)/(2n+2); A has e_n/(2n+1), B has e_{n+1}(2n+2)/(2n+3).
+template <class T> T seriesA64(T h) {
+  T h2 = h * h, s = T(0.0), hp = T(1.0);
+  double e = 1.0;
+  for (int n = 0; n < 8; ++n) {
+    s = s + (e / (2.0 * n + 1.0)) * hp;
+    e = e * (2.0 * n + 1.0) / (2.0 * n + 2.0);
+    hp = hp * h2;
+  }
+  return s;
+}
+template <class T> T seriesB64(T h) {
+  T h2 = h * h, s = T(0.0), hp = h;
+  double e = 0.5;
+  for (int n = 0; n < 12; ++n) {
+    s = s + (e * (2.0 * n + 2.0) / (2.0 * n + 3.0)) * hp;
+    e = e * (2.0 * n + 3.0) / (2.0 * n + 4.0);
+    hp = hp * h2;
+  }
+  return s;
+}
+inline double A_of(double h) {
+  if (std::fabs(h) < 1e-2) return seriesA64(h);
+  return std::asin(h) / h;
+}
+inline double B_of(double h) {
+  if (std::fabs(h) < 0.05) return seriesB64(h);
+  double E = 1.0 / std::sqrt(1.0 - h * h);
+  return (E - std::asin(h) / h) / h;
+}
+inline Var A_of(Var h) {
+  if (std::fabs(h.v) < 1e-2) return seriesA64(h);
+  return asin_(h) / h;
+}
+inline Var B_of(Var h) {
+  if (std::fabs(h.v) < 0.05) return seriesB64(h);
+  Var E = Var(1.0) / sqrt_(Var(1.0) - h * h);
+  return (E - asin_(h) / h) / h;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------ C interface
+extern "C" {
+
+struct OrcGeom {
+  const float* row_x;
+  int32_t n_rows;
+  float tan_half;
+  float drift_length;
+  float bz;
+};
+
+struct OrcParams {
+  float sigma;            // cluster position error (cm)
+  float shared_scale;     // error scale for clusters flagged shared
+  float nb_wy, nb_wz;     // neighbour windows (cm)
+  float nb_teta;          // sinh(eta_max): z slope of the window
+  float nb_ty;            // tan(phi_max): y slope of the window
+  float nb_dmax;          // max squared straight-line deviation (cm^2)
+  float chi2_pick;        // pick-up cut on the normalised distance
+  int32_t max_miss;       // consecutive missed rows that end following
+  int32_t max_gap;        // largest row gap inside an emitted track
+  int32_t min_track_hits; // minimum hits of an emitted track
+  float s_max;            // |sin(phi)| limit of the propagation
+  float inward_cov_scale; // covariance scale at the start of the inward pass
+  float c0t[5];           // tracklet seed covariance diagonal
+  float c0r[5];           // refit covariance diagonal (start of each pass)
+  float chi2_out;         // refit outlier cut
+  int32_t min_acc_reject; // accepted clusters before rejection starts
+  float refit_inflate;    // passes 2 and 3 start from the previous pass's
+                          // final covariance times this factor
+};
+
+struct OrcCalib {
+  double vdrift;          // cm/us
+  double t0;              // us
+  double tf_start;        // us
+  const float* spline;    // [36][2][8][8][8] or NULL
+  float spl_x0, spl_dx;   // u = (x - spl_x0) / spl_dx
+};
+
+struct OrcClusters {
+  int64_t n;
+  int32_t mode;           // 0: z given (single events), 1: t given (time frame)
+  int32_t n_events;
+  const float* y;
+  const float* z;
+  const double* t;
+  const uint8_t* row;
+  const uint8_t* sector;
+  const uint8_t* flags;
+  const uint32_t* event;
+};
+
+}  // extern "C"
+
+namespace {
+
+constexpr double kCLight = 2.99792458e-3;
+constexpr int kNS = 36;
+constexpr int kSpl = 8;
+constexpr uint8_t kFlagShared = 0x10;
+
+struct Ctx {
+  OrcGeom g;
+  OrcParams p;
+  OrcCalib c;
+  OrcClusters cl;
+  std::vector<float> rowx;
+  std::vector<float> spline;
+  bool spline_active = false;
+  std::vector<float> zs32;
+  std::vector<double> zs64;
+  std::vector<std::vector<int64_t>> rows;  // (event, sector, row) -> clusters
+  const std::vector<int64_t>& rowlist(int64_t ev, int sec, int r) const {
+    return rows[((size_t)ev * kNS + sec) * g.n_rows + r];
+  }
+};
+
+template <class R> R kB_of(const Ctx& c) { return R(kCLight) * R(c.g.bz); }
+template <> float kB_of<float>(const Ctx& c) { return (float)kCLight * c.g.bz; }
+
+// Seeding coordinate (Sec. 4): the cluster time scaled linearly to z with the
+// time-frame start as reference; tracking then assumes an arbitrarily long TPC.
+template <class R> R seed_z(const Ctx& c, int64_t i) {
+  if (c.cl.mode == 0) return R(c.cl.z[i]);
+  double sg = c.cl.sector[i] < 18 ? 1.0 : -1.0;
+  double zeta = c.c.vdrift * ((c.cl.t[i] - c.c.t0) - c.c.tf_start);
+  return (R)(sg * ((double)c.g.drift_length - zeta));
+}
+
+// ------------------------------------------------- distortion spline (Sec. 5.2)
+// Per-sector tensor-product uniform cubic B-spline with 8 control points per
+// axis (5 uniform intervals on [0,1]) for the space-point correction.
+template <class R> void bspline_basis(R f, R b[4]) {
+  R g = R(1) - f;
+  R f2 = f * f;
+  R f3 = f2 * f;
+  b[0] = ((g * g) * g) / R(6);
+  b[1] = ((R(3) * f3 - R(6) * f2) + R(4)) / R(6);
+  b[2] = (((R(-3) * f3 + R(3) * f2) + R(3) * f) + R(1)) / R(6);
+  b[3] = f3 / R(6);
+}
+template <class R> R clamp01(R v) { return v < R(0) ? R(0) : (v > R(1) ? R(1) : v); }
+template <class R> void split_arg(R u, int& i, R& f) {
+  R t = u * R(kSpl - 3);
+  int k = (int)val(t);
+  if (k > kSpl - 4) k = kSpl - 4;
+  if (k < 0) k = 0;
+  i = k;
+  f = t - R((double)k);
+}
+
+// Spline coefficients become tape leaves (created on first use) when the Var
+// instantiation needs their gradient.
+struct CoefLeaves {
+  std::map<int, Var> m;
+  Var get(int idx, float v) {
+    auto it = m.find(idx);
+    if (it != m.end()) return it->second;
+    Var l = Var::leaf(v);
+    m[idx] = l;
+    return l;
+  }
+};
+template <class R> R coef_at(const Ctx& c, int idx, CoefLeaves*) { return R(c.spline[idx]); }
+template <> Var coef_at<Var>(const Ctx& c, int idx, CoefLeaves* lv) {
+  return lv ? lv->get(idx, c.spline[idx]) : Var(c.spline[idx]);
+}
+
+template <class R>
+void spline_eval(const Ctx& c, int sector, R x, R y, R az, R out[2], CoefLeaves* lv) {
+  R u = clamp01<R>((x - R(c.c.spl_x0)) / R(c.c.spl_dx));
+  R v = clamp01<R>((y / x + R(c.g.tan_half)) / (R(2) * R(c.g.tan_half)));
+  R w = clamp01<R>(az / R(c.g.drift_length));
+  int iu, iv, iw;
+  R fu, fv, fw;
+  split_arg(u, iu, fu);
+  split_arg(v, iv, fv);
+  split_arg(w, iw, fw);
+  R bu[4], bv[4], bw[4];
+  bspline_basis(fu, bu);
+  bspline_basis(fv, bv);
+  bspline_basis(fw, bw);
+  for (int comp = 0; comp < 2; ++comp) {
+    R acc = R(0);
+    for (int cc = 0; cc < 4; ++cc)
+      for (int bb = 0; bb < 4; ++bb) {
+        R wb = bw[cc] * bv[bb];
+        for (int aa = 0; aa < 4; ++aa) {
+          int idx = (((sector * 2 + comp) * kSpl + (iw + cc)) * kSpl + (iv + bb)) * kSpl + (iu + aa);
+          acc = acc + (wb * bu[aa]) * coef_at<R>(c, idx, lv);
+        }
+      }
+    out[comp] = acc;
+  }
+}
+
+// Calibrated position of cluster i once a collision time 'that' is assigned
+// (Sec. 4: conversion to absolute z, then the space-point correction).
+template <class R> struct CalIn {
+  W<R> vdrift, t0, t;
+  R y, z;
+};
+template <class R> CalIn<R> cal_in(const Ctx& c, int64_t i) {
+  CalIn<R> a;
+  a.vdrift = W<R>(c.c.vdrift);
+  a.t0 = W<R>(c.c.t0);
+  a.t = W<R>(c.cl.mode == 1 ? c.cl.t[i] : 0.0);
+  a.y = R(c.cl.y[i]);
+  a.z = R(c.cl.mode == 0 ? c.cl.z[i] : 0.0f);
+  return a;
+}
+template <class R>
+void calibrate(const Ctx& c, int64_t i, double that, const CalIn<R>& a, R& yc, R& zc,
+               CoefLeaves* lv) {
+  int sec = c.cl.sector[i];
+  R zabs;
+  if (c.cl.mode == 0) {
+    zabs = a.z;
+  } else {
+    W<R> sg = W<R>(sec < 18 ? 1.0 : -1.0);
+    W<R> zeta = a.vdrift * ((a.t - a.t0) - W<R>(that));
+    zabs = narrow<R>(sg * (W<R>((double)c.g.drift_length) - zeta));
+  }
+  if (c.spline_active) {
+    R d[2];
+    R x = R(c.rowx[c.cl.row[i]]);
+    spline_eval<R>(c, sec, x, a.y, abs_(zabs), d, lv);
+    yc = a.y + d[0];
+    zc = zabs + d[1];
+  } else {
+    yc = a.y;
+    zc = zabs;
+  }
+}
+
+// ---------------------------------------------------- track model (Sec. 2-3)
+// State at local x: (y, z, s = sin(phi), t = tan(lambda), q = q/pT); helix in
+// a uniform field Bz, kappa = kB q, d s / d x = -kappa.
+template <class R> struct Trk {
+  R p[5];
+  R C[5][5];
+  R x;
+};
+template <class R> void set_diag(Trk<R>& st, const float* d) {
+  for (int i = 0; i < 5; ++i)
+    for (int j = 0; j < 5; ++j) st.C[i][j] = R(0);
+  for (int i = 0; i < 5; ++i) st.C[i][i] = R(d[i]);
+}
+
+// Exact helix transport to the plane x2 and its analytic Jacobian.
+template <class R> bool propagate(const Ctx& c, Trk<R>& st, R x2, R* Jout = nullptr) {
+  const R kB = kB_of<R>(c);
+  R dx = x2 - st.x;
+  R y = st.p[0], z = st.p[1], s = st.p[2], t = st.p[3], q = st.p[4];
+  R kap = kB * q;
+  R s2 = s - kap * dx;
+  if (!(abs_(s2) < R(c.p.s_max))) return false;
+  R c1 = sqrt_(R(1) - s * s);
+  R c2 = sqrt_(R(1) - s2 * s2);
+  R N = s + s2;
+  R D = c1 + c2;
+  R T = N / D;
+  R dy = dx * T;
+  R opt = R(1) + T * T;
+  R d = dx * sqrt_(opt);
+  R h = (kap * d) * R(0.5);
+  R A = A_of(h);
+  R l = d * A;
+  // Jacobian entries that differ from the identity
+  R dDds = -(s / c1) - (s2 / c2);
+  R kdx = kB * dx;
+  R dDdq = kdx * (s2 / c2);
+  R dTds = (R(2) - T * dDds) / D;
+  R dTdq = (-kdx - T * dDdq) / D;
+  R Jys = dx * dTds;
+  R Jyq = dx * dTdq;
+  R g = (d * T) / opt;
+  R dds = g * dTds;
+  R ddq = g * dTdq;
+  R E = R(1) / sqrt_(R(1) - h * h);
+  R Bh = B_of(h);
+  R Jzs = t * (E * dds);
+  R Jzq = t * (E * ddq + (kB * ((d * d) * Bh)) * R(0.5));
+  R Jzt = l;
+  R Jsq = -kdx;
+  R J[5][5];
+  for (int i = 0; i < 5; ++i)
+    for (int j = 0; j < 5; ++j) J[i][j] = R(i == j ? 1 : 0);
+  J[0][2] = Jys; J[0][4] = Jyq;
+  J[1][2] = Jzs; J[1][3] = Jzt; J[1][4] = Jzq;
+  J[2][4] = Jsq;
+  if (Jout)
+    for (int i = 0; i < 5; ++i)
+      for (int j = 0; j < 5; ++j) Jout[i * 5 + j] = J[i][j];
+  // C' = J C J^T, lower triangle computed with index-ascending sums, mirrored
+  R Tm[5][5];
+  for (int i = 0; i < 5; ++i)
+    for (int l2 = 0; l2 < 5; ++l2) {
+      R acc = R(0);
+      for (int k = 0; k < 5; ++k) acc = acc + J[i][k] * st.C[k][l2];
+      Tm[i][l2] = acc;
+    }
+  for (int i = 0; i < 5; ++i)
+    for (int j = 0; j <= i; ++j) {
+      R acc = R(0);
+      for (int l2 = 0; l2 < 5; ++l2) acc = acc + Tm[i][l2] * J[j][l2];
+      st.C[i][j] = acc;
+      st.C[j][i] = acc;
+    }
+  st.p[0] = y + dy;
+  st.p[1] = z + t * l;
+  st.p[2] = s2;
+  st.x = x2;
+  return true;
+}
+
+// Kalman innovation for a (y, z) measurement with variances vy, vz.
+template <class R> struct Innov {
+  R r0, r1, W00, W01, W11, chi2;
+};
+template <class R> Innov<R> innovation(const Trk<R>& st, R my, R mz, R vy, R vz) {
+  Innov<R> in;
+  in.r0 = my - st.p[0];
+  in.r1 = mz - st.p[1];
+  R S00 = st.C[0][0] + vy;
+  R S01 = st.C[1][0];
+  R S11 = st.C[1][1] + vz;
+  R det = S00 * S11 - S01 * S01;
+  in.W00 = S11 / det;
+  in.W01 = -(S01 / det);
+  in.W11 = S00 / det;
+  in.chi2 = in.r0 * (in.W00 * in.r0 + in.W01 * in.r1) + in.r1 * (in.W01 * in.r0 + in.W11 * in.r1);
+  return in;
+}
+// p += K r, C -= K H C (short form), K = C H^T S^-1.
+template <class R> void apply_update(Trk<R>& st, const Innov<R>& in) {
+  R K0[5], K1[5];
+  for (int i = 0; i < 5; ++i) {
+    K0[i] = st.C[i][0] * in.W00 + st.C[i][1] * in.W01;
+    K1[i] = st.C[i][0] * in.W01 + st.C[i][1] * in.W11;
+  }
+  R HC0[5], HC1[5];
+  for (int j = 0; j < 5; ++j) { HC0[j] = st.C[0][j]; HC1[j] = st.C[1][j]; }
+  for (int i = 0; i < 5; ++i) st.p[i] = st.p[i] + (K0[i] * in.r0 + K1[i] * in.r1);
+  for (int i = 0; i < 5; ++i)
+    for (int j = 0; j <= i; ++j) {
+      R v = st.C[i][j] - (K0[i] * HC0[j] + K1[i] * HC1[j]);
+      st.C[i][j] = v;
+      st.C[j][i] = v;
+    }
+}
+
+// Seed state through two points: straight line, q/pT = 0 (Sec. 2 seed fit).
+template <class R>
+void seed_two_points(const Ctx& c, Trk<R>& st, R x0, R y0, R z0, R x1, R y1, R z1) {
+  R dx = x1 - x0, dy = y1 - y0, dz = z1 - z0;
+  R dl = sqrt_(dx * dx + dy * dy);
+  st.p[0] = y0;
+  st.p[1] = z0;
+  st.p[2] = dy / dl;
+  st.p[3] = dz / dl;
+  st.p[4] = R(0);
+  st.x = x0;
+  set_diag(st, c.p.c0t);
+}
+
+// z of the closest approach of the fitted helix to the beam line (Sec. 4).
+template <class R> R dca_z(const Ctx& c, const Trk<R>& st) {
+  const R kB = kB_of<R>(c);
+  R x = st.x, y = st.p[0], z = st.p[1], s = st.p[2], t = st.p[3], q = st.p[4];
+  R kap = kB * q;
+  R cs = sqrt_(R(1) - s * s);
+  if (abs_(kap) * (abs_(x) + abs_(y)) < R(1e-4)) {
+    R a = x * cs + y * s;
+    return z - t * a;
+  }
+  R cx = x + s / kap;
+  R cy = y - cs / kap;
+  R rc = sqrt_(cx * cx + cy * cy);
+  R rad = R(1) / abs_(kap);
+  R f = R(1) - rad / rc;
+  R px = cx * f, py = cy * f;
+  R ex = x - px, ey = y - py;
+  R ch = sqrt_(ex * ex + ey * ey);
+  R h = (ch * abs_(kap)) * R(0.5);
+  if (h > R(1)) h = R(1);
+  return z - t * (ch * A_of(h));
+}
+
+Ctx* build_ctx(const OrcGeom* g, const OrcParams* p, const OrcCalib* cal, const OrcClusters* cl) {
+  Ctx* c = new Ctx();
+  c->g = *g;
+  c->p = *p;
+  c->c = *cal;
+  c->cl = *cl;
+  c->rowx.assign(g->row_x, g->row_x + g->n_rows);
+  c->g.row_x = c->rowx.data();
+  c->spline.assign((size_t)kNS * 2 * kSpl * kSpl * kSpl, 0.0f);
+  if (cal->spline) {
+    std::memcpy(c->spline.data(), cal->spline, c->spline.size() * sizeof(float));
+    for (float v : c->spline) if (v != 0.0f) { c->spline_active = true; break; }
+  }
+  c->c.spline = c->spline.data();
+  int ne = std::max(1, cl->n_events);
+  c->rows.assign((size_t)ne * kNS * g->n_rows, {});
+  for (int64_t i = 0; i < cl->n; ++i) {
+    size_t k = ((size_t)cl->event[i] * kNS + cl->sector[i]) * g->n_rows + cl->row[i];
+    c->rows[k].push_back(i);
+  }
+  c->zs32.resize(cl->n);
+  c->zs64.resize(cl->n);
+  for (int64_t i = 0; i < cl->n; ++i) {
+    c->zs32[i] = seed_z<float>(*c, i);
+    c->zs64[i] = seed_z<double>(*c, i);
+  }
+  return c;
+}
+
+template <class R> R zs_of(const Ctx& c, int64_t i);
+template <> float zs_of<float>(const Ctx& c, int64_t i) { return c.zs32[i]; }
+template <> double zs_of<double>(const Ctx& c, int64_t i) { return c.zs64[i]; }
+
+// --------------------------------------------------- neighbour finder (Sec. 2)
+// For hit h in row r: the pair (u in row r+1, d in row r-1), each inside a
+// slope window around h -- in z the eta window of Sec. 4 (no vertex
+// constraint), in y a direction window, so that legs of loopers that do not
+// point to the vertex are linked too -- whose d lies closest to the straight
+// line through h and u. Ties go to the lowest (u, d) index pair.
+template <class R> void neighbours_of(const Ctx& c, int64_t h, int32_t& up, int32_t& dn) {
+  up = -1;
+  dn = -1;
+  int r = c.cl.row[h];
+  if (r < 1 || r + 1 >= c.g.n_rows) return;
+  int ev = c.cl.event[h], sec = c.cl.sector[h];
+  const auto& U = c.rowlist(ev, sec, r + 1);
+  const auto& Dn = c.rowlist(ev, sec, r - 1);
+  R xh = R(c.rowx[r]), xu = R(c.rowx[r + 1]), xd = R(c.rowx[r - 1]);
+  R yh = R(c.cl.y[h]), zh = zs_of<R>(c, h);
+  R dxu = xu - xh, dxd = xh - xd;
+  R wy_u = dxu * R(c.p.nb_ty) + R(c.p.nb_wy);
+  R wy_d = dxd * R(c.p.nb_ty) + R(c.p.nb_wy);
+  R wz_u = dxu * R(c.p.nb_teta) + R(c.p.nb_wz);
+  R wz_d = dxd * R(c.p.nb_teta) + R(c.p.nb_wz);
+  R f = dxd / dxu;
+  R dmax = R(c.p.nb_dmax);
+  bool found = false;
+  R best = R(0);
+  for (int64_t u : U) {
+    R yu = R(c.cl.y[u]), zu = zs_of<R>(c, u);
+    if (!(abs_(yu - yh) <= wy_u)) continue;
+    if (!(abs_(zu - zh) <= wz_u)) continue;
+    R py = yh - (yu - yh) * f;
+    R pz = zh - (zu - zh) * f;
+    for (int64_t d : Dn) {
+      R yd = R(c.cl.y[d]), zd = zs_of<R>(c, d);
+      if (!(abs_(yd - yh) <= wy_d)) continue;
+      if (!(abs_(zd - zh) <= wz_d)) continue;
+      R ey = yd - py, ez = zd - pz;
+      R D = ey * ey + ez * ez;
+      if (!(D <= dmax)) continue;
+      // lists are in increasing index order, so strict '<' keeps the lowest pair
+      if (!found || D < best) {
+        found = true;
+        best = D;
+        up = (int32_t)u;
+        dn = (int32_t)d;
+      }
+    }
+  }
+}
+
+// -------------------------------------------------- tracklet constructor
+struct TrackletOut {
+  int32_t nh;
+  double that;
+  double state[5];
+  double x;
+};
+
+template <class R>
+int64_t pick(const Ctx& c, int ev, int sec, int r, const Trk<R>& st, double that) {
+  const auto& L = c.rowlist(ev, sec, r);
+  R sig2 = R(c.p.sigma) * R(c.p.sigma);
+  R cut = R(c.p.chi2_pick);
+  int64_t bj = -1;
+  R bd = R(0);
+  for (int64_t j : L) {
+    R yc, zc;
+    calibrate<R>(c, j, that, cal_in<R>(c, j), yc, zc, nullptr);
+    R ry = yc - st.p[0];
+    R rz = zc - st.p[1];
+    R d2 = (ry * ry) / (st.C[0][0] + sig2) + (rz * rz) / (st.C[1][1] + sig2);
+    if (!(d2 <= cut)) continue;
+    if (bj < 0 || d2 < bd) { bj = j; bd = d2; }
+  }
+  return bj;
+}
+
+// Sec. 2: follow the chain of links, fit it with the simplified Kalman filter,
+// Sec. 4: closest approach -> collision time, calibrated coordinates, refit the
+// seed, then follow outward and inward (Sec. 3: the inward pass also runs
+// through the seed) picking up at most one cluster per row.
+template <class R>
+TrackletOut tracklet(const Ctx& c, const int32_t* upc, int64_t start, int32_t* hits) {
+  TrackletOut o;
+  o.nh = -1;
+  o.that = 0.0;
+  for (int i = 0; i < 5; ++i) o.state[i] = 0.0;
+  o.x = 0.0;
+  for (int r = 0; r < c.g.n_rows; ++r) hits[r] = -1;
+  std::vector<int64_t> H;
+  int64_t cur = start;
+  H.push_back(cur);
+  while (upc[cur] >= 0) {
+    cur = upc[cur];
+    H.push_back(cur);
+  }
+  int ev = c.cl.event[start], sec = c.cl.sector[start];
+  size_t n = H.size();
+  const R sig2 = R(c.p.sigma) * R(c.p.sigma);
+  auto X = [&](int64_t i) { return R(c.rowx[c.cl.row[i]]); };
+  // seed fit in seeding coordinates
+  Trk<R> st;
+  seed_two_points<R>(c, st, X(H[0]), R(c.cl.y[H[0]]), zs_of<R>(c, H[0]), X(H[n - 1]),
+                     R(c.cl.y[H[n - 1]]), zs_of<R>(c, H[n - 1]));
+  for (size_t k = 0; k < n; ++k) {
+    if (!propagate<R>(c, st, X(H[k]))) return o;
+    Innov<R> in = innovation<R>(st, R(c.cl.y[H[k]]), zs_of<R>(c, H[k]), sig2, sig2);
+    apply_update<R>(st, in);
+  }
+  double that = 0.0;
+  if (c.cl.mode == 1) {
+    R zd = dca_z<R>(c, st);
+    double sg = sec < 18 ? 1.0 : -1.0;
+    that = c.c.tf_start - (sg * (double)zd) / c.c.vdrift;
+  }
+  // seed fit in calibrated coordinates
+  std::vector<R> yc(n), zc(n);
+  for (size_t k = 0; k < n; ++k)
+    calibrate<R>(c, H[k], that, cal_in<R>(c, H[k]), yc[k], zc[k], nullptr);
+  seed_two_points<R>(c, st, X(H[0]), yc[0], zc[0], X(H[n - 1]), yc[n - 1], zc[n - 1]);
+  for (size_t k = 0; k < n; ++k) {
+    if (!propagate<R>(c, st, X(H[k]))) return o;
+    Innov<R> in = innovation<R>(st, yc[k], zc[k], sig2, sig2);
+    apply_update<R>(st, in);
+  }
+  // outward
+  Trk<R> best = st;
+  int rlast = c.cl.row[H[n - 1]];
+  int miss = 0;
+  for (int r = rlast + 1; r < c.g.n_rows; ++r) {
+    if (!propagate<R>(c, st, R(c.rowx[r]))) break;
+    int64_t j = pick<R>(c, ev, sec, r, st, that);
+    if (j >= 0) {
+      R y, z;
+      calibrate<R>(c, j, that, cal_in<R>(c, j), y, z, nullptr);
+      apply_update<R>(st, innovation<R>(st, y, z, sig2, sig2));
+      best = st;
+      rlast = r;
+      miss = 0;
+    } else if (++miss >= c.p.max_miss) {
+      break;
+    }
+  }
+  // inward, through the seed
+  st = best;
+  for (int i = 0; i < 5; ++i)
+    for (int j = 0; j < 5; ++j) st.C[i][j] = st.C[i][j] * R(c.p.inward_cov_scale);
+  Trk<R> inner = st;
+  int nh = 0;
+  miss = 0;
+  for (int r = rlast; r >= 0; --r) {
+    if (!propagate<R>(c, st, R(c.rowx[r]))) break;
+    int64_t j = pick<R>(c, ev, sec, r, st, that);
+    if (j >= 0) {
+      R y, z;
+      calibrate<R>(c, j, that, cal_in<R>(c, j), y, z, nullptr);
+      apply_update<R>(st, innovation<R>(st, y, z, sig2, sig2));
+      hits[r] = (int32_t)j;
+      ++nh;
+      miss = 0;
+      inner = st;
+    } else if (++miss >= c.p.max_miss) {
+      break;
+    }
+  }
+  o.nh = nh;
+  o.that = that;
+  for (int i = 0; i < 5; ++i) o.state[i] = val(inner.p[i]);
+  o.x = val(inner.x);
+  return o;
+}
+
+// ------------------------------------------------------------- final refit
+// Sec. 3: three iterations (inward, outward, inward) with outlier rejection
+// on the predicted chi2; the seed of the first pass is a three-point circle.
+struct RefitOut {
+  double p[5];
+  double C[15];
+  double x;
+  double chi2;
+  int32_t ndf;
+  int32_t status;  // 0 ok, 1 propagation failed, 2 no seed
+};
+
+template <class R>
+bool seed_three_points(const Ctx& c, const std::vector<R>& x, const std::vector<R>& yc,
+                       const std::vector<R>& zc, double out[5]) {
+  size_t n = x.size();
+  if (n < 3) return false;
+  size_t i0 = 0, im = n / 2, i2 = n - 1;
+  R ax = x[im] - x[i0], ay = yc[im] - yc[i0];
+  R bx = x[i2] - x[i0], by = yc[i2] - yc[i0];
+  R ex = x[i2] - x[im], ey = yc[i2] - yc[im];
+  R cross = ax * by - ay * bx;
+  R la = sqrt_(ax * ax + ay * ay), lb = sqrt_(bx * bx + by * by), le = sqrt_(ex * ex + ey * ey);
+  R kap = (R(-2) * cross) / ((la * lb) * le);
+  R q = kap / kB_of<R>(c);
+  R hs = (kap * lb) * R(0.5);
+  if (!(abs_(hs) < R(1))) return false;
+  R s2 = (by / lb) * sqrt_(R(1) - hs * hs) - (bx / lb) * hs;
+  R arc = lb * A_of(hs);
+  R t = (zc[i2] - zc[i0]) / arc;
+  out[0] = val(yc[i2]);
+  out[1] = val(zc[i2]);
+  out[2] = val(s2);
+  out[3] = val(t);
+  out[4] = val(q);
+  return true;
+}
+
+template <class R>
+RefitOut refit_core(const Ctx& c, const std::vector<R>& x, const std::vector<R>& yc,
+                    const std::vector<R>& zc, const std::vector<R>& var, const double seed[5],
+                    uint8_t* rej, bool frozen, R* chi2_out) {
+  RefitOut o;
+  std::memset(&o, 0, sizeof(o));
+  size_t n = x.size();
+  Trk<R> st;
+  for (int i = 0; i < 5; ++i) st.p[i] = R(seed[i]);
+  st.x = x[n - 1];
+  R chi2 = R(0);
+  int ndf = 0;
+  set_diag(st, c.p.c0r);
+  for (int pass = 1; pass <= 3; ++pass) {
+    if (pass > 1)
+      for (int i = 0; i < 5; ++i)
+        for (int j = 0; j < 5; ++j) st.C[i][j] = st.C[i][j] * R(c.p.refit_inflate);
+    chi2 = R(0);
+    ndf = 0;
+    int nacc = 0;
+    for (size_t k = 0; k < n; ++k) {
+      size_t i = (pass == 2) ? k : n - 1 - k;
+      if (rej[i] != 0 && rej[i] < pass) continue;
+      if (!propagate<R>(c, st, x[i])) {
+        o.status = 1;
+        *chi2_out = R(0);
+        return o;
+      }
+      Innov<R> in = innovation<R>(st, yc[i], zc[i], var[i], var[i]);
+      bool reject;
+      if (frozen) {
+        reject = rej[i] == pass;
+      } else {
+        reject = nacc >= c.p.min_acc_reject && in.chi2 > R(c.p.chi2_out);
+        if (reject) rej[i] = (uint8_t)pass;
+      }
+      if (reject) continue;
+      apply_update<R>(st, in);
+      chi2 = chi2 + in.chi2;
+      ndf += 2;
+      ++nacc;
+    }
+  }
+  for (int i = 0; i < 5; ++i) o.p[i] = val(st.p[i]);
+  int k = 0;
+  for (int i = 0; i < 5; ++i)
+    for (int j = 0; j <= i; ++j) o.C[k++] = val(st.C[i][j]);
+  o.x = val(st.x);
+  o.chi2 = val(chi2);
+  o.ndf = ndf;
+  *chi2_out = chi2;
+  return o;
+}
+
+template <class R>
+void track_inputs(const Ctx& c, const uint32_t* idx, size_t n, double that, std::vector<R>& x,
+                  std::vector<R>& yc, std::vector<R>& zc, std::vector<R>& var) {
+  x.resize(n); yc.resize(n); zc.resize(n); var.resize(n);
+  for (size_t k = 0; k < n; ++k) {
+    int64_t i = idx[k];
+    x[k] = R(c.rowx[c.cl.row[i]]);
+    calibrate<R>(c, i, that, cal_in<R>(c, i), yc[k], zc[k], nullptr);
+    R sc = (c.cl.flags[i] & kFlagShared) ? R(c.p.shared_scale) : R(1);
+    R e = R(c.p.sigma) * sc;
+    var[k] = e * e;
+  }
+}
+
+}  // namespace
+
+// ======================================================================
+// exported entry points (ctypes)
+// ======================================================================
+extern "C" {
+
+void* orc_create(const OrcGeom* g, const OrcParams* p, const OrcCalib* cal,
+                 const OrcClusters* cl) {
+  return build_ctx(g, p, cal, cl);
+}
+void orc_destroy(void* ctx) { delete (Ctx*)ctx; }
+
+void orc_seed_z(void* ctx, int prec, void* out) {
+  Ctx& c = *(Ctx*)ctx;
+  if (prec == 32) std::memcpy(out, c.zs32.data(), c.zs32.size() * sizeof(float));
+  else std::memcpy(out, c.zs64.data(), c.zs64.size() * sizeof(double));
+}
+
+// Calibrated (yc, zc) of clusters idx[k] with collision time that[k].
+void orc_calibrate(void* ctx, int prec, int64_t m, const uint32_t* idx, const double* that,
+                   double* yc, double* zc) {
+  Ctx& c = *(Ctx*)ctx;
+  for (int64_t k = 0; k < m; ++k) {
+    if (prec == 32) {
+      float a, b;
+      calibrate<float>(c, idx[k], that[k], cal_in<float>(c, idx[k]), a, b, nullptr);
+      yc[k] = a; zc[k] = b;
+    } else {
+      double a, b;
+      calibrate<double>(c, idx[k], that[k], cal_in<double>(c, idx[k]), a, b, nullptr);
+      yc[k] = a; zc[k] = b;
+    }
+  }
+}
+
+// Spline value at explicit points (for closed-form checks of the spline).
+void orc_spline(void* ctx, int64_t m, const int32_t* sector, const double* x, const double* y,
+                const double* az, double* dy, double* dz) {
+  Ctx& c = *(Ctx*)ctx;
+  for (int64_t k = 0; k < m; ++k) {
+    double d[2];
+    spline_eval<double>(c, sector[k], x[k], y[k], az[k], d, nullptr);
+    dy[k] = d[0];
+    dz[k] = d[1];
+  }
+}
+
+// Neighbour links (original cluster indices, -1 = none) of hits[k]
+// (all clusters when hits == NULL).
+void orc_neighbours(void* ctx, int prec, const int64_t* hits, int64_t nh, int32_t* up,
+                    int32_t* dn) {
+  Ctx& c = *(Ctx*)ctx;
+  int64_t m = hits ? nh : c.cl.n;
+  for (int64_t k = 0; k < m; ++k) {
+    int64_t h = hits ? hits[k] : k;
+    if (prec == 32) neighbours_of<float>(c, h, up[k], dn[k]);
+    else neighbours_of<double>(c, h, up[k], dn[k]);
+  }
+}
+
+// Link cleaner (Sec. 2 "evolution"): keep only mutual links.
+void orc_clean(void* ctx, const int32_t* up, const int32_t* dn, int32_t* upc, int32_t* dnc) {
+  Ctx& c = *(Ctx*)ctx;
+  for (int64_t h = 0; h < c.cl.n; ++h) {
+    upc[h] = (up[h] >= 0 && dn[up[h]] == h) ? up[h] : -1;
+    dnc[h] = (dn[h] >= 0 && up[dn[h]] == h) ? dn[h] : -1;
+  }
+}
+
+// Chain heads with at least three linked hits, increasing index order.
+int64_t orc_start_hits(void* ctx, const int32_t* upc, const int32_t* dnc, int64_t* out) {
+  Ctx& c = *(Ctx*)ctx;
+  int64_t m = 0;
+  for (int64_t h = 0; h < c.cl.n; ++h)
+    if (dnc[h] < 0 && upc[h] >= 0 && upc[upc[h]] >= 0) out[m++] = h;
+  return m;
+}
+
+// One tracklet per start hit; hits is [m][n_rows], state [m][5].
+void orc_tracklets(void* ctx, int prec, const int32_t* upc, int64_t m, const int64_t* starts,
+                   int32_t* nh, int32_t* hits, double* that, double* state, double* xout) {
+  Ctx& c = *(Ctx*)ctx;
+  for (int64_t k = 0; k < m; ++k) {
+    TrackletOut o = prec == 32 ? tracklet<float>(c, upc, starts[k], hits + k * c.g.n_rows)
+                               : tracklet<double>(c, upc, starts[k], hits + k * c.g.n_rows);
+    nh[k] = o.nh;
+    that[k] = o.that;
+    for (int i = 0; i < 5; ++i) state[k * 5 + i] = o.state[i];
+    xout[k] = o.x;
+  }
+}
+
+// Tracklet selector: each cluster goes to the tracklet with the most hits
+// (ties: lower start index); a tracklet becomes a track when it keeps at
+// least min_track_hits clusters with no row gap above max_gap.
+int64_t orc_select(void* ctx, int64_t m, const int64_t* starts, const int32_t* nh,
+                   const int32_t* hits, const double* that, uint32_t* track_start,
+                   uint32_t* cluster_idx, double* track_that, int64_t* track_id,
+                   int64_t cap_tracks, int64_t cap_clusters) {
+  Ctx& c = *(Ctx*)ctx;
+  int R = c.g.n_rows;
+  std::vector<uint64_t> w(c.cl.n, 0);
+  auto wt = [&](int64_t k) {
+    return ((uint64_t)(uint32_t)nh[k] << 32) | (uint64_t)(0xFFFFFFFFu - (uint32_t)starts[k]);
+  };
+  for (int64_t k = 0; k < m; ++k) {
+    if (nh[k] < c.p.min_track_hits) continue;
+    uint64_t wk = wt(k);
+    for (int r = 0; r < R; ++r) {
+      int32_t j = hits[k * R + r];
+      if (j >= 0 && w[j] < wk) w[j] = wk;
+    }
+  }
+  int64_t nt = 0, nc = 0;
+  track_start[0] = 0;
+  for (int64_t k = 0; k < m; ++k) {
+    if (nh[k] < c.p.min_track_hits) continue;
+    uint64_t wk = wt(k);
+    int kept = 0, lastr = -1, maxgap = 0;
+    for (int r = 0; r < R; ++r) {
+      int32_t j = hits[k * R + r];
+      if (j < 0 || w[j] != wk) continue;
+      if (lastr >= 0) maxgap = std::max(maxgap, r - lastr - 1);
+      lastr = r;
+      ++kept;
+    }
+    if (kept < c.p.min_track_hits || maxgap > c.p.max_gap) continue;
+    if (nt >= cap_tracks || nc + kept > cap_clusters) return -1;
+    for (int r = 0; r < R; ++r) {
+      int32_t j = hits[k * R + r];
+      if (j >= 0 && w[j] == wk) cluster_idx[nc++] = (uint32_t)j;
+    }
+    track_that[nt] = that[k];
+    track_id[nt] = starts[k];
+    ++nt;
+    track_start[nt] = (uint32_t)nc;
+  }
+  return nt;
+}
+
+// Refit of tracks (CSR, clusters in increasing row order). seeds: optional
+// [nt][5] seed states at the outermost cluster; seeds_out receives the seeds
+// used. rej: [n_assigned] rejection pass per cluster (0 kept); with
+// frozen != 0 it is an input and no new decision is taken.
+void orc_refit(void* ctx, int prec, int64_t nt, const uint32_t* track_start,
+               const uint32_t* cluster_idx, const double* that, const double* seeds,
+               double* seeds_out, int frozen, uint8_t* rej, double* params, double* cov,
+               double* xout, double* chi2, int32_t* ndf, int32_t* status) {
+  Ctx& c = *(Ctx*)ctx;
+  for (int64_t k = 0; k < nt; ++k) {
+    size_t a = track_start[k], b = track_start[k + 1], n = b - a;
+    uint8_t* rj = rej + a;
+    if (!frozen) std::memset(rj, 0, n);
+    RefitOut o;
+    std::memset(&o, 0, sizeof(o));
+    double seed[5];
+    bool ok;
+    if (prec == 32) {
+      std::vector<float> x, yc, zc, var;
+      track_inputs<float>(c, cluster_idx + a, n, that[k], x, yc, zc, var);
+      ok = seeds ? true : seed_three_points<float>(c, x, yc, zc, seed);
+      if (seeds) for (int i = 0; i < 5; ++i) seed[i] = seeds[k * 5 + i];
+      if (ok) { float ch; o = refit_core<float>(c, x, yc, zc, var, seed, rj, frozen, &ch); }
+    } else {
+      std::vector<double> x, yc, zc, var;
+      track_inputs<double>(c, cluster_idx + a, n, that[k], x, yc, zc, var);
+      ok = seeds ? true : seed_three_points<double>(c, x, yc, zc, seed);
+      if (seeds) for (int i = 0; i < 5; ++i) seed[i] = seeds[k * 5 + i];
+      if (ok) { double ch; o = refit_core<double>(c, x, yc, zc, var, seed, rj, frozen, &ch); }
+    }
+    if (!ok) o.status = 2;
+    if (seeds_out) for (int i = 0; i < 5; ++i) seeds_out[k * 5 + i] = ok ? seed[i] : 0.0;
+    for (int i = 0; i < 5; ++i) params[k * 5 + i] = o.p[i];
+    for (int i = 0; i < 15; ++i) cov[k * 15 + i] = o.C[i];
+    xout[k] = o.x;
+    chi2[k] = o.chi2;
+    ndf[k] = o.ndf;
+    status[k] = o.status;
+  }
+}
+
+// Gradient of L = sum_k g[k] chi2_k (pass 3) by reverse-mode differentiation
+// of the FP64 refit with frozen rejections and seeds. Outputs per assigned
+// cluster d/dy and d/d(t or z) of the raw measurement, and
+// grad_calib = [dL/dvdrift, dL/dt0, dL/dspline[36*2*512]] (accumulated).
+void orc_refit_grad(void* ctx, int64_t nt, const uint32_t* track_start,
+                    const uint32_t* cluster_idx, const double* that, const double* seeds,
+                    const uint8_t* rej, const double* g, double* grad_y, double* grad_zt,
+                    double* grad_calib) {
+  Ctx& c = *(Ctx*)ctx;
+  for (int64_t k = 0; k < nt; ++k) {
+    size_t a = track_start[k], b = track_start[k + 1], n = b - a;
+    g_tape.clear();
+    CoefLeaves lv;
+    Var vd = Var::leaf(c.c.vdrift);
+    Var t0 = Var::leaf(c.c.t0);
+    std::vector<Var> ly(n), lz(n), x(n), yc(n), zc(n), var(n);
+    for (size_t q = 0; q < n; ++q) {
+      int64_t i = cluster_idx[a + q];
+      CalIn<Var> in;
+      in.vdrift = vd;
+      in.t0 = t0;
+      ly[q] = Var::leaf(c.cl.y[i]);
+      if (c.cl.mode == 1) {
+        lz[q] = Var::leaf(c.cl.t[i]);
+        in.t = lz[q];
+        in.z = Var(0.0);
+      } else {
+        lz[q] = Var::leaf(c.cl.z[i]);
+        in.z = lz[q];
+        in.t = Var(0.0);
+      }
+      in.y = ly[q];
+      x[q] = Var(c.rowx[c.cl.row[i]]);
+      calibrate<Var>(c, i, that[k], in, yc[q], zc[q], &lv);
+      double sc = (c.cl.flags[i] & kFlagShared) ? c.p.shared_scale : 1.0;
+      double e = (double)c.p.sigma * sc;
+      var[q] = Var(e * e);
+    }
+    std::vector<uint8_t> rj(rej + a, rej + b);
+    Var chi2;
+    RefitOut o = refit_core<Var>(c, x, yc, zc, var, seeds + k * 5, rj.data(), true, &chi2);
+    if (o.status != 0) continue;
+    g_tape.backward(chi2.id, g[k]);
+    auto adj = [&](const Var& v) { return v.id >= 0 ? g_tape.adj[v.id] : 0.0; };
+    for (size_t q = 0; q < n; ++q) {
+      grad_y[a + q] += adj(ly[q]);
+      grad_zt[a + q] += adj(lz[q]);
+    }
+    grad_calib[0] += adj(vd);
+    grad_calib[1] += adj(t0);
+    for (auto& kv : lv.m) grad_calib[2 + kv.first] += adj(kv.second);
+  }
+  g_tape.clear();
+}
+
+// Refit of one track given float64 points directly (for closed-form checks).
+int orc_refit_points(void* ctx, int64_t n, const double* x, const double* y, const double* z,
+                     double var, double* params_out, double* chi2, int32_t* ndf) {
+  Ctx& c = *(Ctx*)ctx;
+  std::vector<double> X(x, x + n), Y(y, y + n), Z(z, z + n), V(n, var);
+  double seed[5];
+  if (!seed_three_points<double>(c, X, Y, Z, seed)) return 2;
+  std::vector<uint8_t> rj(n, 0);
+  double ch;
+  RefitOut o = refit_core<double>(c, X, Y, Z, V, seed, rj.data(), false, &ch);
+  for (int i = 0; i < 5; ++i) params_out[i] = o.p[i];
+  *chi2 = o.chi2;
+  *ndf = o.ndf;
+  return o.status;
+}
+
+// Single-step helpers exposed for closed-form checks of the track model.
+int orc_propagate(void* ctx, const double* state_in, double x1, double x2, const double* cov_in,
+                  double* state_out, double* cov_out) {
+  Ctx& c = *(Ctx*)ctx;
+  Trk<double> st;
+  for (int i = 0; i < 5; ++i) st.p[i] = state_in[i];
+  st.x = x1;
+  for (int i = 0; i < 5; ++i)
+    for (int j = 0; j < 5; ++j) st.C[i][j] = cov_in[i * 5 + j];
+  if (!propagate<double>(c, st, x2)) return 0;
+  for (int i = 0; i < 5; ++i) state_out[i] = st.p[i];
+  for (int i = 0; i < 5; ++i)
+    for (int j = 0; j < 5; ++j) cov_out[i * 5 + j] = st.C[i][j];
+  return 1;
+}
+
+int orc_jacobian(void* ctx, const double* state_in, double x1, double x2, double* state_out,
+                 double* J) {
+  Ctx& c = *(Ctx*)ctx;
+  Trk<double> st;
+  for (int i = 0; i < 5; ++i) st.p[i] = state_in[i];
+  st.x = x1;
+  set_diag(st, c.p.c0r);
+  if (!propagate<double>(c, st, x2, J)) return 0;
+  for (int i = 0; i < 5; ++i) state_out[i] = st.p[i];
+  return 1;
+}
+
+void orc_update(const double* state_in, const double* cov_in, double my, double mz, double vy,
+                double vz, double* state_out, double* cov_out, double* chi2) {
+  Trk<double> st;
+  for (int i = 0; i < 5; ++i) st.p[i] = state_in[i];
+  for (int i = 0; i < 5; ++i)
+    for (int j = 0; j < 5; ++j) st.C[i][j] = cov_in[i * 5 + j];
+  st.x = 0;
+  Innov<double> in = innovation<double>(st, my, mz, vy, vz);
+  apply_update<double>(st, in);
+  *chi2 = in.chi2;
+  for (int i = 0; i < 5; ++i) state_out[i] = st.p[i];
+  for (int i = 0; i < 5; ++i)
+    for (int j = 0; j < 5; ++j) cov_out[i * 5 + j] = st.C[i][j];
+}
+
+double orc_dca_z(void* ctx, const double* state, double x) {
+  Ctx& c = *(Ctx*)ctx;
+  Trk<double> st;
+  for (int i = 0; i < 5; ++i) st.p[i] = state[i];
+  st.x = x;
+  return dca_z<double>(c, st);
+}
+
+double orc_arc_factor(int prec, double h) {
+  return prec == 32 ? (double)A_of((float)h) : A_of(h);
+}
+double orc_arc_deriv(int prec, double h) {
+  return prec == 32 ? (double)B_of((float)h) : B_of(h);
+}
+
+}  // extern "C"

@@ -1,0 +1,500 @@
+"""Pins of the CPU oracle against references that are not the oracle itself.
+
+Each test checks one piece of the oracle against something independent: the
+generator's global-frame helix (closed-form circle/plane intersection),
+central finite differences, the information form of the Kalman update
+(numpy.linalg), scipy's B-spline and least-squares routines, closed forms
+and brute-force constructions whose answer is known.
+"""
+import math
+
+import numpy as np
+import pytest
+import scipy.optimize as so
+import scipy.stats as st
+
+import oracle
+import synth
+from synth.events import eval_distortion
+
+KB = 2.99792458e-3 * 0.5
+
+
+def _oracle(ev, geo, params, calib=None, **kw):
+    return oracle.Oracle(ev, geo, params, calib or synth.nominal_calib(), **kw)
+
+
+# ---------------------------------------------------------------- arc length
+@pytest.mark.parametrize("prec,rtol", [(64, 2e-15), (32, 6e-7)])
+def test_arc_factor_matches_asin(prec, rtol):
+    for h in np.concatenate([np.linspace(-0.999, 0.999, 401), [1e-9, -1e-6, 0.124999, 0.125, 0.5]]):
+        ref = math.asin(h) / h
+        assert abs(oracle.arc_factor(h, prec) - ref) <= rtol * ref, h
+
+
+@pytest.mark.parametrize("prec,rtol", [(64, 1e-8), (32, 2e-4)])
+def test_arc_derivative_is_derivative(prec, rtol):
+    # B(h) = d/dh [asin(h)/h]; compare with a central difference of asin(h)/h
+    for h in np.linspace(-0.95, 0.95, 77):
+        e = 1e-5
+        fd = (math.asin(h + e) / (h + e) - math.asin(h - e) / (h - e)) / (2 * e) if abs(h) > 2e-5 else 0.0
+        b = oracle.arc_deriv(h, prec)
+        assert abs(b - fd) <= rtol * max(abs(fd), 1e-3), (h, b, fd)
+
+
+# ------------------------------------------------------ helix propagation
+def test_propagation_matches_generator_helix(geo, params):
+    ev = synth.make_tiny(seed=11, n_tracks=60, sectors=(0, 7, 20), sigma=0.0)
+    o = _oracle(ev, geo, params)
+    seg = ev.segment
+    checked = 0
+    worst = np.zeros(5)
+    for s in np.unique(seg[seg >= 0]):
+        idx = np.nonzero(seg == s)[0]
+        idx = idx[np.argsort(ev.row[idx])]
+        if idx.size < 20 or np.max(np.abs(ev.s_true[idx])) >= params["s_max"]:
+            continue
+        a, b = idx[0], idx[-1]
+        for (i, j) in [(a, b), (b, a), (idx[3], idx[4])]:
+            s0 = [ev.y_true[i], ev.z_true[i], ev.s_true[i], ev.tl_true[i], ev.q_true[i]]
+            out, _ = o.propagate(s0, geo.row_x[ev.row[i]], geo.row_x[ev.row[j]])
+            assert out is not None
+            ref = [ev.y_true[j], ev.z_true[j], ev.s_true[j], ev.tl_true[j], ev.q_true[j]]
+            worst = np.maximum(worst, np.abs(out - ref))
+            checked += 1
+    assert checked > 50
+    assert worst[0] < 1e-9 and worst[1] < 1e-9, worst
+    assert worst[2] < 1e-12 and worst[3] == 0 and worst[4] == 0, worst
+
+
+def test_jacobian_matches_finite_differences(geo, params):
+    ev = synth.make_tiny(seed=12, n_tracks=4)
+    o = _oracle(ev, geo, params)
+    rng = np.random.default_rng(0)
+    for _ in range(40):
+        s0 = np.array([rng.uniform(-5, 5), rng.uniform(-50, 50), rng.uniform(-0.6, 0.6),
+                       rng.uniform(-1, 1), rng.uniform(-8, 8)])
+        x1 = rng.uniform(85, 245)
+        x2 = x1 + rng.choice([-1, 1]) * rng.uniform(0.5, 8)
+        out, J = o.jacobian(s0, x1, x2)
+        if out is None:
+            continue
+        for k in range(5):
+            e = 1e-6 * max(1.0, abs(s0[k]))
+            sp = s0.copy(); sp[k] += e
+            sm = s0.copy(); sm[k] -= e
+            op, _ = o.jacobian(sp, x1, x2)
+            om, _ = o.jacobian(sm, x1, x2)
+            fd = (op - om) / (2 * e)
+            np.testing.assert_allclose(J[:, k], fd, rtol=1e-6, atol=1e-8)
+
+
+def test_covariance_transport_is_JCJt(geo, params):
+    ev = synth.make_tiny(seed=12, n_tracks=4)
+    o = _oracle(ev, geo, params)
+    rng = np.random.default_rng(1)
+    A = rng.normal(size=(5, 5))
+    C = A @ A.T + np.eye(5)
+    s0 = np.array([1.0, 20.0, 0.2, 0.3, 2.0])
+    out, J = o.jacobian(s0, 100.0, 103.0)
+    out2, C2 = o.propagate(s0, 100.0, 103.0, C)
+    np.testing.assert_allclose(out2, out, rtol=0, atol=0)
+    np.testing.assert_allclose(C2, J @ C @ J.T, rtol=1e-13, atol=1e-13)
+
+
+# ----------------------------------------------------------- Kalman update
+def test_update_equals_information_form():
+    rng = np.random.default_rng(2)
+    H = np.zeros((2, 5)); H[0, 0] = 1; H[1, 1] = 1
+    for _ in range(20):
+        A = rng.normal(size=(5, 5))
+        C = A @ A.T + 0.1 * np.eye(5)
+        p = rng.normal(size=5)
+        m = rng.normal(size=2)
+        V = np.diag(rng.uniform(0.005, 0.05, 2))
+        p2, C2, chi2 = oracle.Oracle.update(p, C, m[0], m[1], V[0, 0], V[1, 1])
+        Ci = np.linalg.inv(C)
+        Cn = np.linalg.inv(Ci + H.T @ np.linalg.inv(V) @ H)
+        pn = Cn @ (Ci @ p + H.T @ np.linalg.inv(V) @ m)
+        r = m - H @ p
+        S = H @ C @ H.T + V
+        np.testing.assert_allclose(p2, pn, rtol=1e-9, atol=1e-10)
+        np.testing.assert_allclose(C2, Cn, rtol=1e-8, atol=1e-10)
+        assert abs(chi2 - r @ np.linalg.solve(S, r)) < 1e-10 * max(1, chi2)
+
+
+# --------------------------------------------------------------- the refit
+def _truth_refit(ev, geo, params, min_hits=40, prec=64):
+    ts, ci, tc, sids = synth.truth_tracks(ev, min_hits)
+    o = _oracle(ev, geo, params)
+    r = o.refit(ts, ci, np.zeros(ts.size - 1), prec=prec)
+    inner = ci[ts[:-1]]
+    return o, ts, ci, r, inner
+
+
+def test_noise_free_refit_returns_generating_helix(geo, params):
+    ev = synth.make_tiny(seed=13, n_tracks=80, sectors=(0, 9), sigma=0.0)
+    o, ts, ci, r, inner = _truth_refit(ev, geo, params)
+    ok = r["status"] == 0
+    assert ok.sum() >= 50
+    truth = np.stack([ev.y_true, ev.z_true, ev.s_true, ev.tl_true, ev.q_true], 1)[inner]
+    np.testing.assert_allclose(r["x"][ok], geo.row_x[ev.row[inner]][ok].astype(np.float64))
+    d = np.abs(r["params"][ok] - truth[ok])
+    # clusters are float32: compare with the helix through the rounded points
+    assert np.max(d[:, 0]) < 2e-5 and np.max(d[:, 1]) < 2e-5, np.max(d, 0)
+    assert np.max(d[:, 2]) < 1e-6 and np.max(d[:, 3]) < 1e-6
+    assert np.max(d[:, 4] / np.abs(truth[ok, 4])) < 2e-4
+    assert np.all(r["rej"] == 0)
+
+
+def test_refit_of_exact_points_is_exact(geo, params):
+    """Float64 points exactly on a generated helix refit to it within 1e-9."""
+    ev = synth.make_tiny(seed=14, n_tracks=40, sectors=(0,), sigma=0.0)
+    o = _oracle(ev, geo, params)
+    ts, ci, tc, sids = synth.truth_tracks(ev, 60)
+    n = 0
+    for k in range(ts.size - 1):
+        idx = ci[ts[k]:ts[k + 1]]
+        if np.max(np.abs(ev.s_true[idx])) > 0.9:
+            continue
+        x = geo.row_x[ev.row[idx]].astype(np.float64)
+        stt, p, chi2, ndf = o.refit_points(x, ev.y_true[idx], ev.z_true[idx], 0.01)
+        assert stt == 0
+        i = idx[0]
+        truth = np.array([ev.y_true[i], ev.z_true[i], ev.s_true[i], ev.tl_true[i], ev.q_true[i]])
+        assert np.all(np.abs(p - truth) < 1e-9 * np.array([1, 1, 1, 1, max(1, abs(truth[4]))])), (
+            p - truth)
+        assert chi2 < 1e-12 and ndf == 2 * idx.size
+        n += 1
+    assert n >= 10
+
+
+def _helix_at_planes(p, x0, xs, kB=KB):
+    """Independent helix model: circle through (x0, y0) with direction phi,
+    curvature kB*q, intersected with planes x = xs; z advances with arc length."""
+    y0, z0, s, t, q = p
+    kap = kB * q
+    c = math.sqrt(1 - s * s)
+    if abs(kap) < 1e-12:
+        ys = y0 + (xs - x0) * s / c
+        ls = (xs - x0) / c
+        return ys, z0 + t * ls
+    # centre of curvature: clockwise for kap > 0
+    xc, yc = x0 + s / kap, y0 - c / kap
+    R = 1 / abs(kap)
+    dx = xs - xc
+    dy = np.sqrt(R * R - dx * dx)
+    # branch continuous with the start point
+    sgn = np.sign(y0 - yc)
+    ys = yc + sgn * dy
+    ang0 = math.atan2(y0 - yc, x0 - xc)
+    ang = np.arctan2(ys - yc, xs - xc)
+    dang = np.angle(np.exp(1j * (ang0 - ang)))  # clockwise positive for kap>0
+    ls = dang / kap
+    return ys, z0 + t * ls
+
+
+def _ls_fit(geo, e, idx, p_start, sigma=0.1):
+    x = geo.row_x[e.row[idx]].astype(np.float64)
+    y = e.y[idx].astype(np.float64)
+    z = e.z[idx].astype(np.float64)
+    x0 = x[0]
+
+    def res(p):
+        yy, zz = _helix_at_planes(p, x0, x)
+        return np.concatenate([(yy - y) / sigma, (zz - z) / sigma])
+    sol = so.least_squares(res, p_start, xtol=1e-15, ftol=1e-15, gtol=1e-15,
+                           x_scale=np.array([0.1, 0.1, 1e-3, 1e-3, 1e-2]))
+    return sol.x
+
+
+def test_refit_agrees_with_least_squares(geo, params):
+    ev = synth.make_tiny(seed=15, n_tracks=40, sectors=(0,))
+    ts, ci, tc, sids = synth.truth_tracks(ev, 50)
+    o = _oracle(ev, geo, params)
+    r = o.refit(ts, ci, np.zeros(ts.size - 1), prec=64)
+    n = 0
+    for k in range(ts.size - 1):
+        if r["status"][k] != 0 or np.any(r["rej"][ts[k]:ts[k + 1]]):
+            continue
+        idx = ci[ts[k]:ts[k + 1]]
+        p_ls = _ls_fit(geo, ev, idx, r["params"][k])
+        C = np.zeros((5, 5))
+        C[np.tril_indices(5)] = r["cov"][k]
+        sig = np.sqrt(np.diag(C))
+        # the extended Kalman filter agrees with Gauss-Newton to a small
+        # fraction of the parameter uncertainty
+        assert np.all(np.abs(r["params"][k] - p_ls) < 0.03 * sig), (k, (r["params"][k] - p_ls) / sig)
+        n += 1
+    assert n >= 15
+
+
+def test_refit_pulls_and_chi2(geo, params):
+    ev = synth.make_tiny(seed=16, n_tracks=600, sectors=(0, 5, 11, 19, 30))
+    o, ts, ci, r, inner = _truth_refit(ev, geo, params, min_hits=40)
+    ok = (r["status"] == 0)
+    for k in np.nonzero(ok)[0]:
+        if np.any(r["rej"][ts[k]:ts[k + 1]]):
+            ok[k] = False
+    truth = np.stack([ev.y_true, ev.z_true, ev.s_true, ev.tl_true, ev.q_true], 1)[inner]
+    C = r["cov"]
+    diag = C[:, [0, 2, 5, 9, 14]]
+    pulls = (r["params"][ok] - truth[ok]) / np.sqrt(diag[ok])
+    N = pulls.shape[0]
+    assert N > 300
+    m = pulls.mean(0)
+    s = pulls.std(0)
+    assert np.all(np.abs(m) < 4 / math.sqrt(N)), m
+    assert np.all(np.abs(s - 1) < 4 / math.sqrt(2 * N)), s
+    u = st.chi2.cdf(r["chi2"][ok], r["ndf"][ok] - 5)
+    assert st.kstest(u, "uniform").pvalue > 1e-3
+
+
+# ------------------------------------------------------------ time -> z
+def test_time_to_z_round_trip(geo, params):
+    ev = synth.make_tiny(seed=17, n_tracks=30, sectors=(0, 20), mode="time", tf_start=1.0e6,
+                         n_coll=3)
+    o = _oracle(ev, geo, params)
+    sig = np.nonzero(ev.label >= 0)[0]
+    tcoll = ev.t_coll[ev.label[sig]]
+    yc, zc = o.calibrate(sig, tcoll, prec=64)
+    assert np.max(np.abs(zc - ev.info["z_meas"][sig])) < 1e-9
+    assert np.max(np.abs(yc - ev.y[sig])) == 0
+    z32 = o.seed_z(32)
+    z64 = o.seed_z(64)
+    # the float32 seeding coordinate is the correctly rounded float64 one
+    np.testing.assert_array_equal(z32, z64.astype(np.float32))
+    # and equals the linear time scaling with the time-frame start as reference
+    sg = np.where(ev.sector < 18, 1.0, -1.0)
+    ref = sg * (250.0 - 2.58 * (ev.t - ev.tf_start))
+    assert np.max(np.abs(z64 - ref)) < 1e-7
+
+
+# --------------------------------------------------------------- spline
+def test_spline_matches_scipy_bspline(geo, params):
+    rng = np.random.default_rng(3)
+    cal = synth.nominal_calib()
+    cal.spline = synth.random_distortion(rng, 1.0)
+    ev = synth.make_tiny(seed=18, n_tracks=2)
+    o = _oracle(ev, geo, params, cal)
+    m = 4000
+    sec = rng.integers(0, 36, m)
+    x = rng.uniform(85, 245, m)
+    y = rng.uniform(-1, 1, m) * x * math.tan(math.pi / 18)
+    az = rng.uniform(0, 250, m)
+    dy, dz = o.spline(sec, x, y, az)
+    ry, rz = eval_distortion(geo, cal.spline, sec, x, y, az)
+    np.testing.assert_allclose(dy, ry, atol=1e-12)
+    np.testing.assert_allclose(dz, rz, atol=1e-12)
+
+
+def test_spline_partition_of_unity_and_linear_precision(geo, params):
+    ev = synth.make_tiny(seed=18, n_tracks=2)
+    cal = synth.nominal_calib()
+    spl = np.zeros_like(cal.spline)
+    spl[:, 0] = 1.0                                    # constant 1 in dy
+    g = (np.arange(8) - 1.0) / 5.0                     # Greville abscissae
+    spl[:, 1] = g[None, None, None, :]                 # dz = u (linear in x)
+    cal.spline = spl.astype(np.float32)
+    o = _oracle(ev, geo, params, cal)
+    rng = np.random.default_rng(4)
+    x = rng.uniform(85, 245, 500)
+    y = rng.uniform(-0.15, 0.15, 500) * x
+    az = rng.uniform(0, 250, 500)
+    dy, dz = o.spline(np.zeros(500, np.int32), x, y, az)
+    np.testing.assert_allclose(dy, 1.0, atol=1e-6)
+    np.testing.assert_allclose(dz, (x - 85.0) / 160.0, atol=2e-7)
+
+
+# ------------------------------------------------------------------ DCA
+def test_dca_of_primary_helix_is_vertex(geo, params):
+    ev = synth.make_tiny(seed=19, n_tracks=40, sectors=(0, 3), sigma=0.0, central=False)
+    ev.part["zv"][:] = 0.0
+    o = _oracle(ev, geo, params)
+    rng = np.random.default_rng(5)
+    first_leg = np.nonzero((ev.segment >= 0) & (ev.segment % 4 == 0))[0]
+    for i in rng.choice(first_leg, 60, replace=False):
+        s0 = [ev.y_true[i], ev.z_true[i], ev.s_true[i], ev.tl_true[i], ev.q_true[i]]
+        zd = o.dca_z(s0, geo.row_x[ev.row[i]])
+        zv = ev.part["zv"][ev.label[i]]
+        assert abs(zd - zv) < 1e-6, (zd, zv)
+
+
+# ------------------------------------------------------ neighbour finder
+class _Mini:
+    """Hand-built clusters in one sector."""
+
+    def __init__(self, rows, ys, zs):
+        self.mode = "event"
+        self.row = np.asarray(rows, np.uint8)
+        self.y = np.asarray(ys, np.float32)
+        self.z = np.asarray(zs, np.float32)
+        n = self.y.size
+        self.sector = np.zeros(n, np.uint8)
+        self.flags = np.zeros(n, np.uint8)
+        self.event = np.zeros(n, np.uint32)
+        self.n_events = 1
+        self.tf_start = 0.0
+        self.t = None
+
+
+def test_neighbours_on_constructed_lines(geo, params):
+    x = geo.row_x.astype(np.float64)
+    # a straight line through rows 10, 11, 12 plus distractors in the outer rows
+    ys = [2.0, 2.0 + 0.3 * (x[11] - x[10]), 2.0 + 0.3 * (x[12] - x[10]),
+          2.0 + 0.3 * (x[12] - x[10]) + 0.4,  # displaced by 0.4 cm in y (D = 0.16)
+          2.0 - 0.3 * (x[10] - x[9]) * 0 - 0.3 * (x[10] - x[9]),  # true continuation in row 9
+          30.0]                                # far away
+    zs = [10.0, 10.0 + 0.5 * (x[11] - x[10]), 10.0 + 0.5 * (x[12] - x[10]),
+          10.0 + 0.5 * (x[12] - x[10]), 10.0 - 0.5 * (x[10] - x[9]), 10.0]
+    rows = [10, 11, 12, 12, 9, 11]
+    ev = _Mini(rows, ys, zs)
+    o = _oracle(ev, geo, params)
+    up, dn = o.neighbours(32)
+    upd, dnd = o.neighbours(64)
+    # hit 1 (row 11): down = 0, up = 2 (the exact line, not the displaced 3)
+    assert (up[1], dn[1]) == (2, 0)
+    # hit 0 (row 10): down = 4 (row 9), up = 1
+    assert (up[0], dn[0]) == (1, 4)
+    # row 12 and row 9 hits have no row on one side within reach -> no links
+    assert up[2] == -1 and up[4] == -1
+    # the far cluster has no neighbours
+    assert up[5] == -1 and dn[5] == -1
+    np.testing.assert_array_equal(up, upd)
+    np.testing.assert_array_equal(dn, dnd)
+
+
+def test_neighbours_prefer_smaller_deviation_and_respect_windows(geo, params):
+    x = geo.row_x.astype(np.float64)
+    h_y, h_z = 0.0, 0.0
+    dxu, dxd = x[51] - x[50], x[50] - x[49]
+    # two up candidates and two down candidates; pairs (u0,d0) exact, others off
+    ys = [h_y, 0.0, 0.2, 0.0, 0.25, 0.0]
+    zs = [h_z, 0.0, 0.0, 0.0, 0.0, dxu * params["nb_teta"] + params["nb_wz"] + 0.01]
+    rows = [50, 51, 51, 49, 49, 51]
+    ev = _Mini(rows, ys, zs)
+    o = _oracle(ev, geo, params)
+    up, dn = o.neighbours(32)
+    assert (up[0], dn[0]) == (1, 3)
+    # cluster 5 is outside the eta window of hit 0: never its up link
+    assert up[0] != 5
+
+
+def test_neighbour_tie_goes_to_lowest_pair(geo, params):
+    # mirror-symmetric candidates give identical deviations
+    ys = [0.0, 0.1, -0.1, 0.1, -0.1]
+    zs = [0.0, 0.0, 0.0, 0.0, 0.0]
+    rows = [60, 61, 61, 59, 59]
+    ev = _Mini(rows, ys, zs)
+    o = _oracle(ev, geo, params)
+    up, dn = o.neighbours(32)
+    # D(u=1, d=4) = D(u=2, d=3) exactly (symmetric); lowest pair (1, 4) wins
+    assert (up[0], dn[0]) == (1, 4)
+
+
+# ------------------------------------------------ CA invariants, end to end
+def test_ca_invariants_and_efficiency_single_sector(geo, params):
+    ev = synth.make_single_sector()
+    o = _oracle(ev, geo, params)
+    f = o.find(32)
+    up, dn, upc, dnc = f["up"], f["dn"], f["upc"], f["dnc"]
+    # every kept link is mutual and connects adjacent rows of one sector
+    k = np.nonzero(upc >= 0)[0]
+    assert np.all(dnc[upc[k]] == k)
+    assert np.all(ev.row[upc[k]] == ev.row[k] + 1)
+    # start hits are chain heads of chains with >= 3 hits
+    s = f["starts"]
+    assert np.all(dnc[s] < 0) and np.all(upc[s] >= 0) and np.all(upc[upc[s]] >= 0)
+    tr = f["tracks"]
+    ci = tr["cluster_idx"]
+    assert np.unique(ci).size == ci.size, "a cluster is in two tracks"
+    lens = np.diff(tr["track_start"].astype(np.int64))
+    assert np.all(lens >= params["min_track_hits"])
+    # tracks: clusters in increasing row order, one sector
+    for a, b in zip(tr["track_start"][:-1], tr["track_start"][1:]):
+        r = ev.row[ci[a:b]]
+        assert np.all(np.diff(r.astype(int)) > 0)
+    # the tracklet with the globally largest weight keeps all its hits
+    tl = f["tracklets"]
+    w = tl["nh"].astype(np.int64) * 2**32 + (2**32 - 1 - s)
+    top = np.argmax(w)
+    top_hits = tl["hits"][top][tl["hits"][top] >= 0]
+    assert np.isin(top_hits, ci).all()
+    # sanity bound on an isolated, noise-free sector
+    seg = ev.segment
+    from collections import Counter
+    matched, fake = set(), 0
+    for a, b in zip(tr["track_start"][:-1], tr["track_start"][1:]):
+        c = Counter(seg[ci[a:b]])
+        m, cnt = c.most_common(1)[0]
+        if m < 0 or cnt < 0.9 * (b - a):
+            fake += 1
+        else:
+            matched.add(m)
+    cnt = Counter(seg[seg >= 0])
+    findable = [q for q, c in cnt.items() if c >= 70]
+    eff = np.mean([q in matched for q in findable])
+    assert eff >= 0.99 and fake == 0, (eff, fake)
+
+
+# ------------------------------------------------------------- adjoint
+def test_gradient_matches_finite_differences(geo, params):
+    rng = np.random.default_rng(6)
+    cal = synth.nominal_calib()
+    cal.spline = synth.random_distortion(rng, 0.5)
+    ev = synth.make_tiny(seed=20, n_tracks=6, sectors=(2,), mode="time", tf_start=1.0e6,
+                         calib=cal)
+    ts, ci, tc, sids = synth.truth_tracks(ev, 40)
+    nt = min(3, ts.size - 1)
+    ts = ts[:nt + 1]
+    ci = ci[:ts[-1]]
+    tc = tc[:nt]
+    o = _oracle(ev, geo, params, cal)
+    r = o.refit(ts, ci, tc, prec=64)
+    seeds, rej = r["seeds"], r["rej"]
+    g = np.array([1.0, 0.7, 1.3])[:nt]
+    gy, gz, gc = o.refit_grad(ts, ci, tc, seeds, rej, g)
+
+    def loss(ev_mod=None, cal_mod=None):
+        oo = _oracle(ev_mod or ev, geo, params, cal_mod or cal)
+        rr = oo.refit(ts, ci, tc, prec=64, seeds=seeds, rej=rej)
+        oo.close()
+        return float(np.sum(g * rr["chi2"]))
+
+    class Ev:
+        pass
+
+    def perturbed(field, i, e):
+        E = Ev()
+        for k in ("mode", "row", "sector", "flags", "event", "n_events", "tf_start", "z"):
+            setattr(E, k, getattr(ev, k))
+        E.y = ev.y.copy()
+        E.t = ev.t.copy()
+        getattr(E, field)[i] += e
+        return E
+
+    # cluster coordinates (y is float32 in storage: use a large step)
+    for q in [0, 7, ts[1] + 3]:
+        i = ci[q]
+        ey = 1e-2
+        fd = (loss(perturbed("y", i, ey)) - loss(perturbed("y", i, -ey))) / (2 * ey)
+        assert abs(fd - gy[q]) < 2e-3 * max(1, abs(fd)), (q, fd, gy[q])
+        et = 1e-5
+        fd = (loss(perturbed("t", i, et)) - loss(perturbed("t", i, -et))) / (2 * et)
+        assert abs(fd - gz[q]) < 1e-4 * max(1, abs(fd)), (q, fd, gz[q])
+    # vdrift and t0
+    for k, name, e in [(0, "vdrift", 1e-7), (1, "t0", 1e-6)]:
+        cp, cm = cal.copy(), cal.copy()
+        setattr(cp, name, getattr(cal, name) + e)
+        setattr(cm, name, getattr(cal, name) - e)
+        fd = (loss(cal_mod=cp) - loss(cal_mod=cm)) / (2 * e)
+        assert abs(fd - gc[k]) < 1e-5 * max(1, abs(fd)), (name, fd, gc[k])
+    # spline coefficients with the largest gradients
+    flat = cal.spline.reshape(-1)
+    for j in np.argsort(-np.abs(gc[2:]))[:4]:
+        e = 1e-3
+        cp, cm = cal.copy(), cal.copy()
+        cp.spline.reshape(-1)[j] = flat[j] + e
+        cm.spline.reshape(-1)[j] = flat[j] - e
+        fd = (loss(cal_mod=cp) - loss(cal_mod=cm)) / (2 * e)
+        assert abs(fd - gc[2 + j]) < 1e-3 * max(1, abs(fd)), (j, fd, gc[2 + j])
