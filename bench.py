@@ -1,0 +1,417 @@
+#!/usr/bin/env python
+"""Throughput of the TPC hot path on B300: clusters/s tracked.
+
+One step = load a batch (bucketing, seeding transform, search grid), find
+tracks (neighbours, link cleaning, start hits, tracklets, selection,
+calibration transform), refit them (3 passes, saved for the adjoint) and run
+the adjoint refit (gradient of the summed chi2 w.r.t. cluster coordinates and
+calibration). Default workload: one central Pb-Pb-like event (36 sectors,
+10,000 primaries, 10 % noise, seed 1), synthetic.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank processes its own independent event (seed 1 + rank):
+weak scaling with no collective on the data path; the barrier and the
+max-over-ranks timing use torch.distributed.
+"""
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+L2_BYTES = 126 * 1024 * 1024
+METRIC = "TPC clusters/s tracked (CA+Kalman) on 1 B300; adjoint refit time vs fwd"
+UNIT = "clusters/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="central",
+                    choices=["central", "timeframe", "batched", "single_sector"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--profile-steps", type=int, default=0,
+                    help="only run W+K steps with kernel timing (for ncu launch lists)")
+    return ap.parse_args()
+
+
+def make_workload(name, rank):
+    import synth
+    if name == "central":
+        ev = synth.make_central(seed=1 + rank)
+        cfg = dict(workload="central Pb-Pb-like event: 36 sectors x 152 rows, 10000 primaries "
+                            "(pT power law, mean 0.5 GeV), 10% noise, event mode", seed=1 + rank)
+    elif name == "timeframe":
+        ev = synth.make_timeframe(seed=2 + rank)
+        cfg = dict(workload="50 kHz continuous-readout time frame: 50 collisions, "
+                            "multiplicity Exp(2000), 15% noise, float64 times", seed=2 + rank)
+    elif name == "batched":
+        ev = synth.make_batched(seed=3 + rank)
+        cfg = dict(workload="64 events, log-uniform 20..10000 tracks, one batch", seed=3 + rank)
+    else:
+        ev = synth.make_single_sector(seed=rank)
+        cfg = dict(workload="single sector, 200 helices", seed=rank)
+    cfg.update(n_clusters=int(ev.n), n_events=int(ev.n_events), mode=ev.mode)
+    return ev, cfg
+
+
+# ---------------------------------------------------------------- clocks
+class Clocks:
+    Q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+    NAMES = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if not self.proc:
+            return dict(sm_mhz=None, sm_max_mhz=None, reasons=[], samples=0)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 6:
+                continue
+            try:
+                sm.append(float(f[0]))
+                smax.append(float(f[1]))
+            except ValueError:
+                continue
+            for name, v in zip(self.NAMES, f[2:6]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return dict(sm_mhz=float(np.median(sm)) if sm else None,
+                    sm_max_mhz=float(max(smax)) if smax else None,
+                    reasons=sorted(reasons), samples=len(sm))
+
+
+# -------------------------------------------------------- byte model
+def algorithmic_bytes(kernel, c):
+    """Compulsory DRAM bytes of one launch (reads + writes of its inputs and
+    outputs once; re-reads served on chip are not counted)."""
+    n, mode, nt, na, ntl, nh = c["n"], c["mode"], c["n_tracks"], c["n_assigned"], \
+        c["n_tracklets"], c["sum_nh"]
+    zt = 8 if mode == 1 else 4
+    ev = 4 if c["n_events"] > 1 else 0
+    model = {
+        "k_hist": n * (2 + zt + ev + 4),
+        "k_scatter": n * (2 + ev + 4),
+        "k_row_sort": n * (4 + 4 + 4 + zt * (mode == 1) + 16 + 8 * (mode == 1)),
+        "k_neighbours": n * (12 + 8),
+        "k_clean": n * (8 + 8),
+        "k_write_starts": n * 8 + ntl * 4,
+        "k_tracklets": n * 12 + ntl * (4 + 152 * 4 + 16) + nh * (8 + 8 * (mode == 1)),
+        "k_select_count": ntl * (152 * 4 + 8) + nh * 8,
+        "k_select_write": ntl * (152 * 4 + 16) + na * 8 + nt * 16,
+        "k_calib": na * (4 + 4 + 8 + 4 + zt + 3 + 12),
+        "k_refit": na * (12 + 1) + nt * (5 + 15 + 4) * 4,
+        "k_refit_bwd": na * (12 + 1 + 8) + nt * 4,
+        "k_calib_grad": na * (8 + 8 + 8 + 4 + zt + 2 + 8 + 8),
+    }
+    return model.get(kernel)
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return dict(hbm_gbs=float(d["hbm_gbs"]), source="measured",
+                    sm_max_mhz=float(d.get("sm_max_mhz", 2032.0)))
+    return dict(hbm_gbs=6400.0, source="fallback", sm_max_mhz=2032.0)
+
+
+# ------------------------------------------------------------- our arm
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    import synth
+    from paper_1811_11481_b300.binding import Tracker, TPC_GRAD_CALIB_SIZE
+
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    geo = synth.geometry()
+    ev, cfg = make_workload(args.workload, rank)
+    tr = Tracker(geo)
+    tr.set_calib()
+    cl = tr.upload(ev)
+    L, h = tr.L, tr.h
+    n = ev.n
+    cap_tr = n // 10 + 1
+    dev = tr.dev
+    out = dict(params=torch.empty(cap_tr, 5, device=dev), cov=torch.empty(cap_tr, 15, device=dev),
+               x=torch.empty(cap_tr, device=dev), chi2=torch.empty(cap_tr, device=dev),
+               ndf=torch.empty(cap_tr, dtype=torch.int32, device=dev),
+               status=torch.empty(cap_tr, dtype=torch.int32, device=dev),
+               rej=torch.empty(n + 1, dtype=torch.uint8, device=dev))
+    ones = torch.ones(cap_tr, device=dev)
+    gy = torch.empty(n + 1, device=dev)
+    gz = torch.empty(n + 1, device=dev)
+    gc = torch.empty(TPC_GRAD_CALIB_SIZE, dtype=torch.float64, device=dev)
+    import ctypes as C
+    P = lambda t: C.c_void_p(t.data_ptr())
+    stream = torch.cuda.current_stream()
+
+    def ck(st, what):
+        if st != 0:
+            raise RuntimeError(f"{what}: status {st}: {L.tpc_last_error(h).decode()}")
+
+    def step(refit=True, backward=True):
+        tr.load(cl)
+        ck(L.tpc_find_tracks_async(h), "find")
+        if refit:
+            ck(L.tpc_refit(h, 1, P(out["params"]), P(out["cov"]), P(out["x"]), P(out["chi2"]),
+                           P(out["ndf"]), P(out["status"]), P(out["rej"])), "refit")
+        if backward:
+            ck(L.tpc_refit_backward(h, P(ones), P(gy), P(gz), P(gc)), "backward")
+
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+
+    # warm-up (allocations happen here), then a count check
+    for _ in range(max(3, args.warmup)):
+        step()
+    nt, na, ntl = tr.counts()
+    tl = tr.tracklets()
+    sum_nh = int(tl["nh"].clamp(min=0).sum().item())
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ---- timed region: device-resident inputs, L2 flushed before each step
+    tr.profile(True)
+    clocks = Clocks(local)
+    clocks.start()
+    barrier()
+    times = []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        times.append((e0, e1))
+    barrier()
+    clk = clocks.stop()
+    ms = [a.elapsed_time(b) for a, b in times]
+    kstats, launches = tr.profile_read()
+    tr.profile(False)
+    total_ms = float(np.sum(ms))
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * n * args.steps / (total_ms / 1000.0)
+
+    # ---- forward-only vs adjoint timing (phases of the same step)
+    def phase_time(fn, reps=5):
+        torch.cuda.synchronize()
+        acc = 0.0
+        for _ in range(reps):
+            flush.fill_(1.0)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            acc += a.elapsed_time(b)
+        return acc / reps
+    step()
+    torch.cuda.synchronize()
+    t_fwd = phase_time(lambda: ck(L.tpc_refit(h, 1, P(out["params"]), P(out["cov"]), P(out["x"]),
+                                              P(out["chi2"]), P(out["ndf"]), P(out["status"]),
+                                              P(out["rej"])), "refit"))
+    t_fwd_nosave = phase_time(lambda: ck(L.tpc_refit(h, 0, P(out["params"]), P(out["cov"]),
+                                                     P(out["x"]), P(out["chi2"]), P(out["ndf"]),
+                                                     P(out["status"]), P(out["rej"])), "refit"))
+    step()
+    t_bwd = phase_time(lambda: ck(L.tpc_refit_backward(h, P(ones), P(gy), P(gz), P(gc)), "bwd"))
+
+    # ---- end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        host = {k: (v.cpu().pin_memory() if v is not None else None) for k, v in cl.items()
+                if hasattr(v, "cpu")}
+        res_h = torch.empty(cap_tr * 6 + 8, dtype=torch.float32).pin_memory()
+        cnt_h = torch.empty(3, dtype=torch.int64)
+        h2d = sum(v.numel() * v.element_size() for v in host.values() if v is not None)
+        d2h = res_h.numel() * 4
+        barrier()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(args.steps):
+            for k, v in host.items():
+                if v is not None:
+                    cl[k].copy_(v, non_blocking=True)
+            step()
+            res_h[:cap_tr * 5].view(cap_tr, 5).copy_(out["params"], non_blocking=True)
+            res_h[cap_tr * 5:cap_tr * 6].copy_(out["chi2"], non_blocking=True)
+        b.record(stream)
+        barrier()
+        e2e_ms = a.elapsed_time(b)
+        if world > 1:
+            t = torch.tensor([e2e_ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_ms = float(t.item())
+        e2e = dict(value=world * n * args.steps / (e2e_ms / 1000.0), unit=UNIT,
+                   h2d_bytes_per_step=int(h2d), d2h_bytes_per_step=int(d2h))
+
+    # ---- roofline of the dominant kernel
+    counts = dict(n=n, mode=1 if ev.mode == "time" else 0, n_tracks=nt, n_assigned=na,
+                  n_tracklets=ntl, sum_nh=sum_nh, n_events=ev.n_events)
+    peaks = load_peaks()
+    tot = sum(v[1] for v in kstats.values()) or 1.0
+    dom = max(kstats, key=lambda k: kstats[k][1]) if kstats else None
+    roof = None
+    if dom:
+        nl, kms = kstats[dom]
+        per_launch_ms = kms / nl
+        ab = algorithmic_bytes(dom, counts)
+        ach = ab / (per_launch_ms / 1000.0) / 1e9 if ab else None
+        roof = dict(kernel=dom, bound="hbm", achieved=ach, peak=peaks["hbm_gbs"], unit="GB/s",
+                    frac=(ach / peaks["hbm_gbs"]) if ach else None, traffic=None,
+                    algorithmic_bytes=ab, ms_per_launch=per_launch_ms,
+                    share=kms / tot, peak_source=peaks["source"] + " (burst copy)")
+    kernels = {k: dict(launches=v[0], ms_per_step=v[1] / args.steps, share=v[1] / tot)
+               for k, v in sorted(kstats.items(), key=lambda kv: -kv[1][1])}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(ev, geo, secs=list(range(36)))
+
+    line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps,
+                warmup=args.warmup, ms_per_step=total_ms / args.steps, higher_is_better=True,
+                scaling="weak", vs_baseline=None, dtype="f32 (f64 timestamps and gradient sums)",
+                data="synthetic",
+                config=dict(cfg, l2="flushed before every timed step (256 MB write)",
+                            parallelism=f"replicas x{world}, one independent event per GPU"),
+                tracks_per_s=world * nt * args.steps / (total_ms / 1000.0),
+                n_tracks=nt, n_assigned=na, n_tracklets=ntl,
+                refit_fwd_ms=t_fwd, refit_fwd_nosave_ms=t_fwd_nosave, adjoint_ms=t_bwd,
+                adjoint_vs_fwd=t_bwd / t_fwd_nosave if t_fwd_nosave > 0 else None,
+                roofline=roof, kernels=kernels, gpu_launches=launches,
+                clocks=clk, e2e=e2e, cpu_baseline=cpu)
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------- CPU baseline
+def _subset(ev, secs):
+    class S:
+        pass
+    m = np.isin(ev.sector, secs)
+    s = S()
+    for k in ("mode", "n_events", "tf_start"):
+        setattr(s, k, getattr(ev, k))
+    for k in ("y", "z", "t", "row", "sector", "flags", "event"):
+        v = getattr(ev, k)
+        setattr(s, k, None if v is None else v[m])
+    return s, int(m.sum())
+
+
+def cpu_baseline(ev, geo, secs):
+    """The oracle as it stands, single thread, on the sectors 'secs' of the
+    same event: find (FP32 mirror), refit (FP64) and tape gradient."""
+    import oracle
+    import synth
+    from paper_1811_11481_b300.config import default_params
+    sub, n = _subset(ev, secs)
+    t0 = time.time()
+    o = oracle.Oracle(sub, geo, default_params(), synth.nominal_calib())
+    f = o.find(32)
+    tr = f["tracks"]
+    r = o.refit(tr["track_start"], tr["cluster_idx"], tr["that"], prec=64)
+    o.refit_grad(tr["track_start"], tr["cluster_idx"], tr["that"], r["seeds"], r["rej"])
+    dt = time.time() - t0
+    o.close()
+    return dict(value=n / dt, unit=UNIT, cores=1, kind="oracle",
+                sample=f"sectors {secs[0]}..{secs[-1]} of the same event ({n} clusters): "
+                       f"find (FP32 mirror) + refit (FP64) + tape-AD gradient, {dt:.1f} s")
+
+
+# ------------------------------------------------------- reference arm
+def run_reference(args):
+    rank = int(os.environ.get("RANK", 0))
+    if rank != 0:
+        return
+    import synth
+    geo = synth.geometry()
+    ev, cfg = make_workload(args.workload, 0)
+    per_step = 2  # sectors per step
+    for w in range(args.warmup):
+        cpu_baseline(ev, geo, secs=[(2 * w) % 36, (2 * w + 1) % 36])
+    tot_n, tot_t = 0, 0.0
+    for k in range(args.steps):
+        secs = [(per_step * k + j) % 36 for j in range(per_step)]
+        sub, n = _subset(ev, secs)
+        t0 = time.time()
+        cpu_baseline(ev, geo, secs)
+        tot_t += time.time() - t0
+        tot_n += n
+    v = tot_n / tot_t
+    cb = dict(value=v, unit=UNIT, cores=1, kind="oracle",
+              sample=f"{per_step} sectors of the event per step, single thread")
+    line = dict(impl="reference", metric=METRIC, value=v, unit=UNIT,
+                n_gpus=int(os.environ.get("WORLD_SIZE", args.gpus)), steps=args.steps,
+                warmup=args.warmup, ms_per_step=1000.0 * tot_t / args.steps,
+                higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f64 (oracle)",
+                data="synthetic", config=cfg, cpu_baseline=cb,
+                e2e=dict(value=v, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,259 @@
+/*
+ * tpc.h - C ABI of the B300 TPC track-finding and refit library.
+ *
+ * The library implements the data-parallel hot path of the ALICE Run 3 TPC
+ * tracking described in arXiv:1811.11481 ("Track Reconstruction in the ALICE
+ * TPC using GPUs for LHC Run 3"):
+ *   - Sec. 2: sector-local cellular-automaton seeding (neighbour finder, link
+ *     cleaning "evolution", start hits), tracklet construction with a
+ *     simplified Kalman filter and cluster pick-up, tracklet selection;
+ *   - Sec. 4: cluster time scaled linearly to z for seeding, closest approach
+ *     to the beam line as the collision-time estimate, calibration applied
+ *     between seeding and fitting;
+ *   - Sec. 3: final Kalman refit iterated three times (inward, outward,
+ *     inward) with outlier rejection on the predicted chi2;
+ *   - an adjoint of the fixed-assignment refit (not in the paper).
+ *
+ * Conventions shared by every entry point:
+ *   - Pointers documented as "device" must point to memory of the device that
+ *     was current when the context was created; "host" pointers to host memory.
+ *   - Every call returns tpc_status; nothing throws across the ABI. Errors
+ *     detected on the device (capacity overflow, invalid cluster fields,
+ *     non-finite fits) are latched in a device error word and reported by the
+ *     next call that synchronises (tpc_find_tracks, tpc_sync, tpc_get_counts).
+ *     tpc_last_error() gives a text for the last non-OK status.
+ *   - All work is issued on the stream given to tpc_create, in call order.
+ *     A context is not thread-safe; separate contexts are independent.
+ *   - Units: cm, microseconds, Tesla, GeV. Local sector frame: x along the
+ *     sector's centre line (pad-row planes x = row_x[r]), y along the pad row,
+ *     z along the drift direction (global z).
+ *   - A track state is (y, z, sin(phi), tan(lambda), q/pT) at a local x.
+ *     Covariances are packed lower triangles in the order (0,0) (1,0) (1,1)
+ *     (2,0) (2,1) (2,2) ... (4,4), 15 floats.
+ */
+#ifndef TPC_H_
+#define TPC_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  TPC_OK = 0,
+  TPC_ERR_ARG = 1,       /* invalid argument or invalid cluster field     */
+  TPC_ERR_CAPACITY = 2,  /* an internal buffer was too small (see text)   */
+  TPC_ERR_CUDA = 3,      /* a CUDA runtime call failed                    */
+  TPC_ERR_TIMEOUT = 4,   /* a bounded device wait gave up                 */
+  TPC_ERR_STATE = 5,     /* call sequence violated (e.g. backward first)  */
+  TPC_ERR_NUMERIC = 6    /* non-finite value in a fit                     */
+} tpc_status;
+
+/* Cluster flag bits (Sec. 3 lists these special cluster types). Only
+ * TPC_FLAG_SHARED changes the arithmetic: it scales the cluster error. */
+#define TPC_FLAG_SPLIT 0x01u
+#define TPC_FLAG_SINGLE_ROW 0x02u
+#define TPC_FLAG_SINGLE_TIME 0x04u
+#define TPC_FLAG_EDGE 0x08u
+#define TPC_FLAG_SHARED 0x10u
+
+#define TPC_N_SECTORS 36      /* 18 in azimuth x 2 sides (Sec. 2)            */
+#define TPC_MAX_ROWS 160      /* row tables are sized for up to 160 rows     */
+#define TPC_SPLINE_N 8        /* control points per spline axis              */
+#define TPC_SPLINE_SIZE (TPC_N_SECTORS * 2 * 8 * 8 * 8) /* floats           */
+#define TPC_GRAD_CALIB_SIZE (2 + TPC_SPLINE_SIZE)        /* doubles          */
+
+typedef struct tpc_ctx tpc_ctx;
+
+/* Detector geometry (Sec. 2: 36 trapezoidal sectors, 152 pad rows). Sector k
+ * is rotated by ((k mod 18) + 1/2) * 20 degrees; k < 18 is the A side (z > 0),
+ * k >= 18 the C side. Copied at tpc_create. */
+typedef struct {
+  int32_t n_rows;       /* number of pad rows, 3 .. TPC_MAX_ROWS            */
+  const float* row_x;   /* host [n_rows], plane positions (cm), increasing  */
+  float tan_half;       /* tan of the sector half-opening angle             */
+  float drift_length;   /* L (cm): |z| of the readout plane                  */
+  float bz;             /* uniform field (T)                                 */
+} tpc_geometry;
+
+/* Cut values of the method (the paper gives none; defaults by
+ * tpc_default_params). Copied at tpc_create. */
+typedef struct {
+  float sigma;            /* cluster position error (cm), y and z          */
+  float shared_scale;     /* error scale for TPC_FLAG_SHARED clusters      */
+  float nb_wy, nb_wz;     /* neighbour window offsets (cm)                 */
+  float nb_teta;          /* neighbour z-slope window, sinh(eta_max)       */
+  float nb_ty;            /* neighbour y-slope window, tan(phi_max)        */
+  float nb_dmax;          /* max squared deviation from straight line      */
+  float chi2_pick;        /* pick-up cut on the normalised distance        */
+  int32_t max_miss;       /* consecutive empty rows that end following     */
+  int32_t max_gap;        /* largest row gap inside an emitted track       */
+  int32_t min_track_hits; /* minimum clusters of a track                   */
+  float s_max;            /* |sin(phi)| limit of the propagation           */
+  float inward_cov_scale; /* covariance scale before the inward pass       */
+  float c0t[5];           /* tracklet seed covariance diagonal             */
+  float c0r[5];           /* refit pass-1 covariance diagonal              */
+  float chi2_out;         /* refit outlier cut on the predicted chi2       */
+  int32_t min_acc_reject; /* accepted clusters before rejection starts     */
+  float refit_inflate;    /* covariance inflation between refit passes     */
+} tpc_params;
+
+/* Calibration (Sec. 4 and Sec. 5.2): drift velocity, time offset and a
+ * per-sector distortion given as a tensor-product uniform cubic B-spline with
+ * 8 control points per axis over u = (x - spl_x0)/spl_dx,
+ * v = (y/x + tan_half)/(2 tan_half), w = |z|/drift_length (each clamped to
+ * [0,1]). corrected = measured + spline. */
+typedef struct {
+  double vdrift;        /* cm/us                                            */
+  double t0;            /* us                                               */
+  const float* spline;  /* device [36][2][8][8][8]: [sector][dy,dz][w][v][u],
+                           or NULL for no distortion. Copied by the call.   */
+  float spl_x0, spl_dx; /* spline x domain (cm)                             */
+} tpc_calib;
+
+/* One batch of clusters (structure of arrays, device pointers, caller-owned;
+ * they must stay valid and unchanged until the last call that reads them:
+ * tpc_find_tracks / tpc_refit / tpc_refit_backward of this batch). */
+typedef struct {
+  int64_t n;              /* number of clusters (< 2^31)                    */
+  int32_t mode;           /* 0: z given (triggered events), 1: t given
+                             (continuous readout, Sec. 4)                   */
+  int32_t n_events;       /* independent events in the batch (>= 1)         */
+  double tf_start;        /* time-frame start (us), mode 1                  */
+  const float* y;         /* device [n] local y (cm)                         */
+  const float* z;         /* device [n] z (cm), mode 0; else NULL           */
+  const double* t;        /* device [n] absolute drift time (us), mode 1    */
+  const uint8_t* row;     /* device [n] pad row, < n_rows                   */
+  const uint8_t* sector;  /* device [n] sector, < 36                        */
+  const uint8_t* flags;   /* device [n] TPC_FLAG_* bits, or NULL            */
+  const uint32_t* event;  /* device [n] event index < n_events, or NULL     */
+} tpc_clusters;
+
+/* A set of tracks as CSR over cluster indices of the loaded batch.
+ * Returned by tpc_find_tracks (library-owned device memory, valid until the
+ * next tpc_load_clusters / tpc_find_tracks / tpc_set_tracks / tpc_destroy), or
+ * given by the caller to tpc_set_tracks (caller-owned device memory). */
+typedef struct {
+  int64_t n_tracks;
+  int64_t n_assigned;            /* = track_start[n_tracks]                  */
+  const uint32_t* track_start;   /* device [n_tracks + 1]                    */
+  const uint32_t* cluster_idx;   /* device [n_assigned], input cluster index,
+                                    strictly increasing pad row per track,
+                                    one sector per track                    */
+  const double* t_coll;          /* device [n_tracks] collision time (us) used
+                                    for the absolute z (mode 1)             */
+  const uint32_t* start_hit;     /* device [n_tracks] input index of the
+                                    chain head (found tracks), may be NULL  */
+} tpc_tracks;
+
+/* Fill *p with the default cut values. */
+void tpc_default_params(tpc_params* p);
+
+/* Create a context on the current device. stream: a cudaStream_t (NULL =
+ * legacy default stream). Copies geometry and params. Allocates scratch
+ * lazily as batches are loaded. Returns TPC_ERR_ARG for invalid geometry. */
+tpc_status tpc_create(const tpc_geometry* geo, const tpc_params* params, void* stream,
+                      tpc_ctx** out);
+
+/* Destroy the context and free all library-owned device memory. NULL is a
+ * no-op. Synchronises the context's stream. */
+void tpc_destroy(tpc_ctx* ctx);
+
+/* Set the calibration (Sec. 4: applied between seeding and fitting). The
+ * spline is copied (device to device, asynchronous on the stream); its
+ * bounds are reduced on the device. Must precede tpc_load_clusters for the
+ * seeding transform (vdrift, t0). */
+tpc_status tpc_set_calib(tpc_ctx* ctx, const tpc_calib* calib);
+
+/* Load a batch: validates fields, converts t to the seeding z (Sec. 4: linear
+ * time scaling with tf_start as reference), buckets clusters by (event,
+ * sector, row) and builds the per-row search grid. Asynchronous. May
+ * allocate device memory when the batch is larger than any before (not
+ * while a stream capture is active). */
+tpc_status tpc_load_clusters(tpc_ctx* ctx, const tpc_clusters* cl);
+
+/* Run the track finder on the loaded batch (neighbours, link cleaning, start
+ * hits, tracklets, selection) and the calibration transform of the assigned
+ * clusters. Synchronises once to read the track count, then fills *out.
+ * Returns TPC_ERR_CAPACITY if the tracklet buffer overflowed (the next call
+ * retries with twice the capacity). */
+tpc_status tpc_find_tracks(tpc_ctx* ctx, tpc_tracks* out);
+
+/* Same as tpc_find_tracks without the synchronisation: counts stay on the
+ * device (readable with tpc_get_counts) and *out is not filled. Makes the
+ * whole load-find-refit sequence capturable in a CUDA graph once buffers
+ * are allocated. */
+tpc_status tpc_find_tracks_async(tpc_ctx* ctx);
+
+/* Replace the context's track set by caller-given tracks (truth assignment,
+ * merged tracks ...). Copies the CSR asynchronously and applies the
+ * calibration transform to the assigned clusters. */
+tpc_status tpc_set_tracks(tpc_ctx* ctx, const tpc_tracks* tracks);
+
+/* Refit the context's track set (Sec. 3). Outputs are caller-owned device
+ * buffers with room for the number of tracks (params [n][5], cov [n][15],
+ * x [n], chi2 [n], ndf [n]; rej [n_assigned] receives for each cluster the
+ * refit pass that rejected it, 0 = kept; any output may be NULL). status[n]
+ * per track: 0 ok, 1 propagation failed, 2 no seed (fewer than 3 clusters or
+ * no circle), 3 invalid track range (also raises TPC_ERR_ARG). With save_for_backward != 0 the per-step filter states are
+ * kept for tpc_refit_backward. */
+tpc_status tpc_refit(tpc_ctx* ctx, int save_for_backward, float* params, float* cov, float* x,
+                     float* chi2, int32_t* ndf, int32_t* status, uint8_t* rej);
+
+/* Adjoint of the last saved refit (not in the paper): for
+ * L = sum_k dL_dchi2[k] * chi2_k with chi2_k the pass-3 chi2, writes
+ * grad_y[j], grad_zt[j] = dL/d(y, t or z) of the input cluster cluster_idx[j]
+ * (device [n_assigned] each, overwritten) and grad_calib = dL/d(vdrift, t0,
+ * spline[36*2*512]) (device double [TPC_GRAD_CALIB_SIZE], overwritten).
+ * Rejections and seed states are held fixed. dL_dchi2: device [n_tracks].
+ * Returns TPC_ERR_STATE without a preceding tpc_refit(save_for_backward=1). */
+tpc_status tpc_refit_backward(tpc_ctx* ctx, const float* dL_dchi2, float* grad_y,
+                              float* grad_zt, double* grad_calib);
+
+/* Synchronise the stream and report the latched device error word. */
+tpc_status tpc_sync(tpc_ctx* ctx);
+
+/* Synchronise and read the counts of the current track set. */
+tpc_status tpc_get_counts(tpc_ctx* ctx, int64_t* n_tracks, int64_t* n_assigned,
+                          int64_t* n_tracklets);
+
+/* Introspection of intermediate results, for tests (device outputs, cluster
+ * indices in input numbering, -1 = none; asynchronous):
+ *   links: up/dn neighbour links before cleaning and upc/dnc after, [n];
+ *   tracklets (capacity n_cap): start hit, hit count, collision-time
+ *     estimate and the per-row hit table [n_cap][n_rows];
+ *   calibrated: corrected (y, z) of each assigned cluster [n_assigned];
+ *   grid: cluster index in bucket order [n] and the start of each
+ *     (event, sector, row) bucket [n_events*36*n_rows + 1]. */
+tpc_status tpc_get_links(tpc_ctx* ctx, int32_t* up, int32_t* dn, int32_t* upc, int32_t* dnc);
+tpc_status tpc_get_tracklets(tpc_ctx* ctx, int64_t n_cap, uint32_t* start_hit, int32_t* n_hits,
+                             double* t_coll, int32_t* hits);
+tpc_status tpc_get_calibrated(tpc_ctx* ctx, float* yc, float* zc);
+tpc_status tpc_get_grid(tpc_ctx* ctx, uint32_t* order, uint32_t* row_start);
+
+/* Kernel accounting (tracing). Every kernel launch of a context is counted.
+ * tpc_profile(ctx, 1) also brackets each launch with CUDA events on the
+ * context's stream (adds a few microseconds per launch); tpc_profile(ctx, 0)
+ * stops timing. Both synchronise and reset the statistics.
+ * tpc_profile_read synchronises and returns per-kernel launch counts and
+ * summed device time (out: host [cap], n_out: number of distinct kernels,
+ * launches: all launches since the last reset). */
+typedef struct {
+  char name[32];
+  int64_t launches;
+  double total_ms;
+} tpc_kernel_stat;
+tpc_status tpc_profile(tpc_ctx* ctx, int enable);
+tpc_status tpc_profile_read(tpc_ctx* ctx, tpc_kernel_stat* out, int32_t cap, int32_t* n_out,
+                            int64_t* launches);
+
+/* Text of the last error of this context ("" if none). Valid until the next
+ * call on the context. */
+const char* tpc_last_error(const tpc_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TPC_H_ */

@@ -1,0 +1,612 @@
+// C ABI of the library (declared in include/tpc.h).
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "tpc_impl.h"
+
+using namespace tpc;
+
+struct tpc_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  Geo geo{};
+  Params prm{};
+  tpc_params prm_c{};
+  Cal cal{};
+  float* d_spline = nullptr;
+  float* d_spl_bound = nullptr;
+  uint32_t* d_err = nullptr;
+  uint32_t* d_cnt = nullptr;
+  uint32_t* h_pinned = nullptr;  // [kCntSize + 1]: counters and error word
+  // batch
+  ClIn cl{};
+  bool loaded = false;
+  int K = 0;
+  GridDims gd{};
+  FindBuf fb{};
+  TrackBuf tb{};
+  RefitBuf rb{};
+  Prof prof;
+  // capacities
+  int64_t cap_n = 0, cap_K = 0, cap_bins = 0, cap_blk = 0, cap_ev = 0;
+  int64_t tl_factor = 8;  // cap_tl = n / tl_factor (halved on overflow)
+  int64_t cap_tr_alloc = 0, cap_asg_alloc = 0, cap_ckpt_alloc = 0;
+  bool tracks_valid = false;
+  bool saved = false;
+  bool part_alloc = false;
+  std::string err;
+};
+
+namespace {
+
+tpc_status fail(tpc_ctx* c, tpc_status s, const std::string& msg) {
+  if (c) c->err = msg;
+  return s;
+}
+
+#define CK(call)                                                                     \
+  do {                                                                               \
+    cudaError_t e_ = (call);                                                         \
+    if (e_ != cudaSuccess)                                                           \
+      return fail(ctx, TPC_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+template <class T>
+cudaError_t grow(T*& p, int64_t& cap, int64_t need) {
+  if (need <= cap && p) return cudaSuccess;
+  if (p) cudaFree(p);
+  p = nullptr;
+  int64_t c = need > 0 ? need : 1;
+  cudaError_t e = cudaMalloc((void**)&p, sizeof(T) * (size_t)c);
+  cap = e == cudaSuccess ? c : 0;
+  return e;
+}
+
+template <class T>
+cudaError_t alloc(T*& p, int64_t n) {
+  if (p) cudaFree(p);
+  p = nullptr;
+  return cudaMalloc((void**)&p, sizeof(T) * (size_t)(n > 0 ? n : 1));
+}
+
+void copy_params(const tpc_params& s, Params& d) {
+  d.sigma = s.sigma;
+  d.shared_scale = s.shared_scale;
+  d.nb_wy = s.nb_wy;
+  d.nb_wz = s.nb_wz;
+  d.nb_teta = s.nb_teta;
+  d.nb_ty = s.nb_ty;
+  d.nb_dmax = s.nb_dmax;
+  d.chi2_pick = s.chi2_pick;
+  d.max_miss = s.max_miss;
+  d.max_gap = s.max_gap;
+  d.min_track_hits = s.min_track_hits;
+  d.s_max = s.s_max;
+  d.inward_cov_scale = s.inward_cov_scale;
+  for (int i = 0; i < 5; ++i) {
+    d.c0t[i] = s.c0t[i];
+    d.c0r[i] = s.c0r[i];
+  }
+  d.chi2_out = s.chi2_out;
+  d.min_acc_reject = s.min_acc_reject;
+  d.refit_inflate = s.refit_inflate;
+}
+
+std::string err_text(uint32_t e) {
+  std::string s;
+  if (e & kErrArg) s += "invalid cluster field (row, sector, event or time); ";
+  if (e & kErrCapStart) s += "start-hit buffer overflow (retry enlarges it); ";
+  if (e & kErrCapRow) s += "a pad-row bucket exceeds 4096 clusters; ";
+  if (e & kErrCapTrack) s += "track buffer overflow; ";
+  if (e & kErrNumeric) s += "non-finite value in a refit; ";
+  if (e & kErrTimeout) s += "a bounded device wait gave up; ";
+  return s;
+}
+
+tpc_status status_of(uint32_t e) {
+  if (e & kErrArg) return TPC_ERR_ARG;
+  if (e & (kErrCapStart | kErrCapRow | kErrCapTrack)) return TPC_ERR_CAPACITY;
+  if (e & kErrTimeout) return TPC_ERR_TIMEOUT;
+  if (e & kErrNumeric) return TPC_ERR_NUMERIC;
+  return TPC_OK;
+}
+
+// Read counters and error word (synchronises the stream).
+tpc_status read_back(tpc_ctx* ctx) {
+  CK(cudaMemcpyAsync(ctx->h_pinned, ctx->d_cnt, sizeof(uint32_t) * kCntSize,
+                     cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->h_pinned + kCntSize, ctx->d_err, sizeof(uint32_t),
+                     cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  uint32_t e = ctx->h_pinned[kCntSize];
+  if (e) {
+    CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(uint32_t), ctx->stream));
+    if (e & kErrCapStart) ctx->tl_factor = ctx->tl_factor > 1 ? ctx->tl_factor / 2 : 1;
+    return fail(ctx, status_of(e), err_text(e));
+  }
+  return TPC_OK;
+}
+
+tpc_status ensure_track_buffers(tpc_ctx* ctx, int64_t cap_tr, int64_t cap_asg) {
+  TrackBuf& t = ctx->tb;
+  if (cap_tr > ctx->cap_tr_alloc) {
+    CK(alloc(t.track_start, cap_tr + 1));
+    CK(alloc(t.t_coll, cap_tr));
+    CK(alloc(t.start_hit, cap_tr));
+    CK(alloc(ctx->rb.seed, cap_tr * 5));
+    CK(alloc(ctx->rb.status, cap_tr));
+    ctx->cap_tr_alloc = cap_tr;
+  }
+  if (cap_asg > ctx->cap_asg_alloc) {
+    CK(alloc(t.cluster_idx, cap_asg));
+    CK(alloc(t.asg_track, cap_asg));
+    CK(alloc(t.yc, cap_asg));
+    CK(alloc(t.zc, cap_asg));
+    CK(alloc(t.meta, cap_asg));
+    CK(alloc(ctx->rb.rej, cap_asg));
+    CK(alloc(ctx->rb.gyc, cap_asg));
+    CK(alloc(ctx->rb.gzc, cap_asg));
+    ctx->cap_asg_alloc = cap_asg;
+  }
+  t.cap_tr = cap_tr;
+  t.cap_asg = cap_asg;
+  return TPC_OK;
+}
+
+tpc_status ensure_tracklets(tpc_ctx* ctx) {
+  int64_t n = ctx->cl.n;
+  int64_t cap = n / ctx->tl_factor + 1024;
+  if (cap > n + 1) cap = n + 1;
+  FindBuf& b = ctx->fb;
+  if (cap > b.cap_tl) {
+    CK(alloc(b.starts, cap));
+    CK(alloc(b.nh, cap));
+    CK(alloc(b.hits, cap * (int64_t)ctx->geo.n_rows));
+    CK(alloc(b.that, cap));
+    CK(alloc(b.nkeep, cap));
+    b.cap_tl = cap;
+    int64_t nblk = (cap + 255) / 256 + 1;
+    if (nblk > ctx->cap_blk) {
+      int64_t tmp = 0;
+      CK(grow(b.blk_a, tmp, nblk));
+      tmp = 0;
+      CK(grow(b.blk_b, tmp, nblk));
+      tmp = 0;
+      CK(grow(b.off_a, tmp, nblk + 1));
+      tmp = 0;
+      CK(grow(b.off_b, tmp, nblk + 1));
+      ctx->cap_blk = nblk;
+    }
+  }
+  return TPC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void tpc_default_params(tpc_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->sigma = 0.1f;
+  p->shared_scale = 2.0f;
+  p->nb_wy = 0.5f;
+  p->nb_wz = 0.5f;
+  p->nb_teta = (float)std::sinh(1.0);
+  p->nb_ty = 1.0f;
+  p->nb_dmax = 0.5f;
+  p->chi2_pick = 16.0f;
+  p->max_miss = 4;
+  p->max_gap = 4;
+  p->min_track_hits = 10;
+  p->s_max = 0.95f;
+  p->inward_cov_scale = 4.0f;
+  const float c0t[5] = {0.01f, 0.01f, 1.0f, 1.0f, 100.0f};
+  const float c0r[5] = {1.0f, 1.0f, 0.1f, 0.1f, 10.0f};
+  for (int i = 0; i < 5; ++i) {
+    p->c0t[i] = c0t[i];
+    p->c0r[i] = c0r[i];
+  }
+  p->chi2_out = 25.0f;
+  p->min_acc_reject = 5;
+  p->refit_inflate = 100.0f;
+}
+
+tpc_status tpc_create(const tpc_geometry* geo, const tpc_params* params, void* stream,
+                      tpc_ctx** out) {
+  if (!out) return TPC_ERR_ARG;
+  *out = nullptr;
+  if (!geo || !geo->row_x || geo->n_rows < 3 || geo->n_rows > TPC_MAX_ROWS) return TPC_ERR_ARG;
+  for (int r = 1; r < geo->n_rows; ++r)
+    if (!(geo->row_x[r] > geo->row_x[r - 1])) return TPC_ERR_ARG;
+  if (!(geo->tan_half > 0.0f) || !(geo->drift_length > 0.0f)) return TPC_ERR_ARG;
+  tpc_ctx* ctx = new tpc_ctx();
+  if (cudaGetDevice(&ctx->device) != cudaSuccess) {
+    delete ctx;
+    return TPC_ERR_CUDA;
+  }
+  ctx->stream = (cudaStream_t)stream;
+  Geo& g = ctx->geo;
+  std::memset(&g, 0, sizeof(g));
+  for (int r = 0; r < geo->n_rows; ++r) g.row_x[r] = geo->row_x[r];
+  g.n_rows = geo->n_rows;
+  g.tan_half = geo->tan_half;
+  g.L = geo->drift_length;
+  g.bz = geo->bz;
+  g.kB = (float)2.99792458e-3 * geo->bz;
+  if (params) ctx->prm_c = *params;
+  else tpc_default_params(&ctx->prm_c);
+  copy_params(ctx->prm_c, ctx->prm);
+  tpc_status st = TPC_OK;
+  auto chk = [&](cudaError_t e) {
+    if (e != cudaSuccess && st == TPC_OK) {
+      st = TPC_ERR_CUDA;
+      ctx->err = cudaGetErrorString(e);
+    }
+  };
+  chk(cudaMalloc(&ctx->d_spline, sizeof(float) * TPC_SPLINE_SIZE));
+  chk(cudaMalloc(&ctx->d_spl_bound, sizeof(float) * 4));
+  chk(cudaMalloc(&ctx->d_err, sizeof(uint32_t)));
+  chk(cudaMalloc(&ctx->d_cnt, sizeof(uint32_t) * kCntSize));
+  chk(cudaMallocHost(&ctx->h_pinned, sizeof(uint32_t) * (kCntSize + 1)));
+  if (st != TPC_OK) {
+    tpc_destroy(ctx);
+    return st;
+  }
+  chk(cudaMemsetAsync(ctx->d_spline, 0, sizeof(float) * TPC_SPLINE_SIZE, ctx->stream));
+  chk(cudaMemsetAsync(ctx->d_spl_bound, 0, sizeof(float) * 4, ctx->stream));
+  chk(cudaMemsetAsync(ctx->d_err, 0, sizeof(uint32_t), ctx->stream));
+  chk(cudaMemsetAsync(ctx->d_cnt, 0, sizeof(uint32_t) * kCntSize, ctx->stream));
+  ctx->cal.vdrift = 2.58;
+  ctx->cal.t0 = 0.0;
+  ctx->cal.tf_start = 0.0;
+  ctx->cal.spline = ctx->d_spline;
+  ctx->cal.spl_bound = ctx->d_spl_bound;
+  ctx->cal.spl_x0 = 85.0f;
+  ctx->cal.spl_dx = 160.0f;
+  if (st != TPC_OK) {
+    tpc_destroy(ctx);
+    return st;
+  }
+  *out = ctx;
+  return TPC_OK;
+}
+
+void tpc_destroy(tpc_ctx* ctx) {
+  if (!ctx) return;
+  cudaStreamSynchronize(ctx->stream);
+  void* ptrs[] = {ctx->d_spline, ctx->d_spl_bound, ctx->d_err, ctx->d_cnt,
+                  ctx->fb.cnt, ctx->fb.row_start, ctx->fb.fill, ctx->fb.zmm, ctx->fb.zr,
+                  ctx->fb.zs_in, ctx->fb.perm, ctx->fb.gy, ctx->fb.gz, ctx->fb.gt,
+                  ctx->fb.gorig, ctx->fb.gseg, ctx->fb.bin_start, ctx->fb.up, ctx->fb.dn,
+                  ctx->fb.upc, ctx->fb.dnc, ctx->fb.blk_a, ctx->fb.blk_b, ctx->fb.off_a,
+                  ctx->fb.off_b, ctx->fb.starts, ctx->fb.nh, ctx->fb.hits, ctx->fb.that,
+                  ctx->fb.weight, ctx->fb.nkeep, ctx->tb.track_start, ctx->tb.cluster_idx,
+                  ctx->tb.asg_track, ctx->tb.t_coll, ctx->tb.start_hit, ctx->tb.yc, ctx->tb.zc,
+                  ctx->tb.meta, ctx->rb.seed, ctx->rb.rej, ctx->rb.status, ctx->rb.ckpt,
+                  ctx->rb.gyc, ctx->rb.gzc, ctx->rb.part_spline, ctx->rb.part_cal};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
+  delete ctx;
+}
+
+tpc_status tpc_set_calib(tpc_ctx* ctx, const tpc_calib* calib) {
+  if (!ctx || !calib) return fail(ctx, TPC_ERR_ARG, "null argument");
+  if (!(calib->vdrift > 0.0) || !(calib->spl_dx != 0.0f))
+    return fail(ctx, TPC_ERR_ARG, "vdrift must be > 0 and spl_dx != 0");
+  ctx->cal.vdrift = calib->vdrift;
+  ctx->cal.t0 = calib->t0;
+  ctx->cal.spl_x0 = calib->spl_x0;
+  ctx->cal.spl_dx = calib->spl_dx;
+  if (calib->spline) {
+    CK(cudaMemcpyAsync(ctx->d_spline, calib->spline, sizeof(float) * TPC_SPLINE_SIZE,
+                       cudaMemcpyDeviceToDevice, ctx->stream));
+  } else {
+    CK(cudaMemsetAsync(ctx->d_spline, 0, sizeof(float) * TPC_SPLINE_SIZE, ctx->stream));
+  }
+  launch_spline_bound(ctx->d_spline, ctx->d_spl_bound, ctx->stream);
+  CK(cudaGetLastError());
+  return TPC_OK;
+}
+
+tpc_status tpc_load_clusters(tpc_ctx* ctx, const tpc_clusters* in) {
+  if (!ctx || !in) return fail(ctx, TPC_ERR_ARG, "null argument");
+  if (in->n < 0 || in->n >= (int64_t)1 << 31) return fail(ctx, TPC_ERR_ARG, "n out of range");
+  if (in->mode != 0 && in->mode != 1) return fail(ctx, TPC_ERR_ARG, "mode must be 0 or 1");
+  if (in->n_events < 1 || in->n_events > 4096) return fail(ctx, TPC_ERR_ARG, "n_events");
+  if (in->n > 0 && (!in->y || !in->row || !in->sector || (in->mode == 0 && !in->z) ||
+                    (in->mode == 1 && !in->t)))
+    return fail(ctx, TPC_ERR_ARG, "missing cluster array");
+  if (in->n_events > 1 && in->n > 0 && !in->event)
+    return fail(ctx, TPC_ERR_ARG, "event array required for n_events > 1");
+  ctx->cl.n = (int32_t)in->n;
+  ctx->cl.mode = in->mode;
+  ctx->cl.n_events = in->n_events;
+  ctx->cl.y = in->y;
+  ctx->cl.z = in->z;
+  ctx->cl.t = in->t;
+  ctx->cl.row = in->row;
+  ctx->cl.sector = in->sector;
+  ctx->cl.flags = in->flags;
+  ctx->cl.event = in->event;
+  ctx->cal.tf_start = in->mode == 1 ? in->tf_start : 0.0;
+  int64_t n = in->n;
+  int K = in->n_events * TPC_N_SECTORS * ctx->geo.n_rows;
+  ctx->K = K;
+  // grid: ~2 clusters per bin
+  double avg = (double)n / (double)K;
+  int nbt = (int)(avg / 2.0);
+  if (nbt < 1) nbt = 1;
+  if (nbt > 4096) nbt = 4096;
+  int ny = (int)std::sqrt(nbt / 4.0);
+  if (ny < 1) ny = 1;
+  if (ny > 16) ny = 16;
+  int nz = nbt / ny;
+  if (nz < 1) nz = 1;
+  ctx->gd.ny = ny;
+  ctx->gd.nz = nz;
+  ctx->gd.nb = ny * nz;
+  ctx->gd.y_margin = 2.0f;
+  ctx->gd.z_margin = 1.0f;
+  FindBuf& b = ctx->fb;
+  if (n > ctx->cap_n || ctx->cap_n == 0) {
+    int64_t c = n > 0 ? n : 1;
+    CK(alloc(b.zs_in, c));
+    CK(alloc(b.perm, c));
+    CK(alloc(b.gy, c));
+    CK(alloc(b.gz, c));
+    CK(alloc(b.gt, c));
+    CK(alloc(b.gorig, c));
+    CK(alloc(b.gseg, c));
+    CK(alloc(b.up, c));
+    CK(alloc(b.dn, c));
+    CK(alloc(b.upc, c));
+    CK(alloc(b.dnc, c));
+    CK(alloc(b.weight, c));
+    ctx->cap_n = c;
+    int64_t nblk = (c + 255) / 256 + 1;
+    if (nblk > ctx->cap_blk) {
+      int64_t tmp = 0;
+      CK(grow(b.blk_a, tmp, nblk));
+      tmp = 0;
+      CK(grow(b.blk_b, tmp, nblk));
+      tmp = 0;
+      CK(grow(b.off_a, tmp, nblk + 1));
+      tmp = 0;
+      CK(grow(b.off_b, tmp, nblk + 1));
+      ctx->cap_blk = nblk;
+    }
+  }
+  if (K > ctx->cap_K) {
+    CK(alloc(b.cnt, K));
+    CK(alloc(b.row_start, (int64_t)K + 1));
+    CK(alloc(b.fill, K));
+    ctx->cap_K = K;
+  }
+  if (in->n_events > ctx->cap_ev) {
+    CK(alloc(b.zmm, (int64_t)in->n_events * 4));
+    CK(alloc(b.zr, (int64_t)in->n_events * 4));
+    ctx->cap_ev = in->n_events;
+  }
+  int64_t nbins = (int64_t)K * (ctx->gd.nb + 1);
+  if (nbins > ctx->cap_bins) {
+    CK(alloc(b.bin_start, nbins));
+    ctx->cap_bins = nbins;
+  }
+  tpc_status st = ensure_tracklets(ctx);
+  if (st != TPC_OK) return st;
+  st = ensure_track_buffers(ctx, n / (ctx->prm.min_track_hits > 0 ? ctx->prm.min_track_hits : 1) + 1,
+                            n + 1);
+  if (st != TPC_OK) return st;
+  launch_load(&ctx->prof, ctx->geo, ctx->cal, ctx->cl, ctx->gd, K, b, ctx->d_err, ctx->stream);
+  CK(cudaGetLastError());
+  ctx->loaded = true;
+  ctx->tracks_valid = false;
+  ctx->saved = false;
+  return TPC_OK;
+}
+
+tpc_status tpc_find_tracks_async(tpc_ctx* ctx) {
+  if (!ctx) return TPC_ERR_ARG;
+  if (!ctx->loaded) return fail(ctx, TPC_ERR_STATE, "no batch loaded");
+  tpc_status st = ensure_tracklets(ctx);
+  if (st != TPC_OK) return st;
+  launch_find(&ctx->prof, ctx->geo, ctx->cal, ctx->prm, ctx->cl, ctx->gd, ctx->K, ctx->fb, ctx->tb,
+              ctx->d_cnt, ctx->d_err, ctx->stream);
+  CK(cudaGetLastError());
+  ctx->tracks_valid = true;
+  ctx->saved = false;
+  return TPC_OK;
+}
+
+tpc_status tpc_find_tracks(tpc_ctx* ctx, tpc_tracks* out) {
+  tpc_status st = tpc_find_tracks_async(ctx);
+  if (st != TPC_OK) return st;
+  st = read_back(ctx);
+  if (st == TPC_ERR_CAPACITY && (ctx->h_pinned[kCntSize] & kErrCapStart)) {
+    // retry once with a larger tracklet buffer
+    st = tpc_find_tracks_async(ctx);
+    if (st != TPC_OK) return st;
+    st = read_back(ctx);
+  }
+  if (st != TPC_OK) return st;
+  if (out) {
+    out->n_tracks = ctx->h_pinned[kCntTracks];
+    out->n_assigned = ctx->h_pinned[kCntAssigned];
+    out->track_start = ctx->tb.track_start;
+    out->cluster_idx = ctx->tb.cluster_idx;
+    out->t_coll = ctx->tb.t_coll;
+    out->start_hit = ctx->tb.start_hit;
+  }
+  return TPC_OK;
+}
+
+tpc_status tpc_set_tracks(tpc_ctx* ctx, const tpc_tracks* t) {
+  if (!ctx || !t) return fail(ctx, TPC_ERR_ARG, "null argument");
+  if (!ctx->loaded) return fail(ctx, TPC_ERR_STATE, "no batch loaded");
+  if (t->n_tracks < 0 || t->n_assigned < 0 || t->n_assigned > ctx->cl.n ||
+      (t->n_tracks > 0 && (!t->track_start || !t->cluster_idx || !t->t_coll)))
+    return fail(ctx, TPC_ERR_ARG, "invalid track set");
+  tpc_status st = ensure_track_buffers(ctx, t->n_tracks > ctx->tb.cap_tr ? t->n_tracks : ctx->tb.cap_tr,
+                                       t->n_assigned > ctx->tb.cap_asg ? t->n_assigned : ctx->tb.cap_asg);
+  if (st != TPC_OK) return st;
+  if (t->n_tracks > 0) {
+    CK(cudaMemcpyAsync(ctx->tb.track_start, t->track_start, sizeof(uint32_t) * (t->n_tracks + 1),
+                       cudaMemcpyDeviceToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->tb.cluster_idx, t->cluster_idx, sizeof(uint32_t) * t->n_assigned,
+                       cudaMemcpyDeviceToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->tb.t_coll, t->t_coll, sizeof(double) * t->n_tracks,
+                       cudaMemcpyDeviceToDevice, ctx->stream));
+    if (t->start_hit)
+      CK(cudaMemcpyAsync(ctx->tb.start_hit, t->start_hit, sizeof(uint32_t) * t->n_tracks,
+                         cudaMemcpyDeviceToDevice, ctx->stream));
+  }
+  ctx->h_pinned[kCntTracks] = (uint32_t)t->n_tracks;
+  ctx->h_pinned[kCntAssigned] = (uint32_t)t->n_assigned;
+  CK(cudaMemcpyAsync(ctx->d_cnt + kCntTracks, ctx->h_pinned + kCntTracks, sizeof(uint32_t) * 2,
+                     cudaMemcpyHostToDevice, ctx->stream));
+  launch_set_tracks(&ctx->prof, ctx->geo, ctx->cal, ctx->cl, t->n_tracks, t->n_assigned, ctx->tb,
+                    ctx->d_cnt, ctx->d_err, ctx->stream);
+  CK(cudaGetLastError());
+  // the pinned words are read by the copy above: keep them stable
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->tracks_valid = true;
+  ctx->saved = false;
+  return TPC_OK;
+}
+
+tpc_status tpc_refit(tpc_ctx* ctx, int save_for_backward, float* params, float* cov, float* x,
+                     float* chi2, int32_t* ndf, int32_t* status, uint8_t* rej) {
+  if (!ctx) return TPC_ERR_ARG;
+  if (!ctx->tracks_valid) return fail(ctx, TPC_ERR_STATE, "no track set");
+  if (save_for_backward) {
+    int64_t need = 3 * ctx->tb.cap_asg * 20;
+    if (need > ctx->cap_ckpt_alloc) {
+      CK(alloc(ctx->rb.ckpt, need));
+      ctx->cap_ckpt_alloc = need;
+    }
+  }
+  launch_refit(&ctx->prof, ctx->geo, ctx->prm, ctx->tb.cap_tr, ctx->d_cnt, ctx->tb, ctx->rb,
+               save_for_backward != 0, params, cov, x, chi2, ndf, status, rej, ctx->d_err,
+               ctx->stream);
+  CK(cudaGetLastError());
+  ctx->saved = save_for_backward != 0;
+  return TPC_OK;
+}
+
+tpc_status tpc_refit_backward(tpc_ctx* ctx, const float* dl_dchi2, float* grad_y, float* grad_zt,
+                              double* grad_calib) {
+  if (!ctx) return TPC_ERR_ARG;
+  if (!ctx->saved) return fail(ctx, TPC_ERR_STATE, "refit_backward needs a saved refit");
+  if (!dl_dchi2 || !grad_y || !grad_zt || !grad_calib)
+    return fail(ctx, TPC_ERR_ARG, "null output");
+  if (!ctx->part_alloc) {
+    CK(alloc(ctx->rb.part_spline, (int64_t)kCalibGradBlocks * TPC_SPLINE_SIZE));
+    CK(alloc(ctx->rb.part_cal, (int64_t)kCalibGradBlocks * 2));
+    ctx->part_alloc = true;
+  }
+  launch_refit_backward(&ctx->prof, ctx->geo, ctx->cal, ctx->prm, ctx->cl, ctx->tb.cap_tr, ctx->tb.cap_asg,
+                        ctx->d_cnt, ctx->tb, ctx->rb, dl_dchi2, grad_y, grad_zt, grad_calib,
+                        ctx->stream);
+  CK(cudaGetLastError());
+  return TPC_OK;
+}
+
+tpc_status tpc_sync(tpc_ctx* ctx) {
+  if (!ctx) return TPC_ERR_ARG;
+  return read_back(ctx);
+}
+
+tpc_status tpc_get_counts(tpc_ctx* ctx, int64_t* n_tracks, int64_t* n_assigned,
+                          int64_t* n_tracklets) {
+  if (!ctx) return TPC_ERR_ARG;
+  tpc_status st = read_back(ctx);
+  if (n_tracks) *n_tracks = ctx->h_pinned[kCntTracks];
+  if (n_assigned) *n_assigned = ctx->h_pinned[kCntAssigned];
+  if (n_tracklets) *n_tracklets = ctx->h_pinned[kCntStart];
+  return st;
+}
+
+tpc_status tpc_get_links(tpc_ctx* ctx, int32_t* up, int32_t* dn, int32_t* upc, int32_t* dnc) {
+  if (!ctx) return TPC_ERR_ARG;
+  if (!ctx->tracks_valid) return fail(ctx, TPC_ERR_STATE, "run tpc_find_tracks first");
+  int n = ctx->cl.n;
+  int32_t* outs[4] = {up, dn, upc, dnc};
+  for (int32_t* o : outs)
+    if (o && n > 0) CK(cudaMemsetAsync(o, 0xff, sizeof(int32_t) * n, ctx->stream));
+  launch_export_links(ctx->fb, n, ctx->K, up, dn, upc, dnc, ctx->stream);
+  CK(cudaGetLastError());
+  return TPC_OK;
+}
+
+tpc_status tpc_get_tracklets(tpc_ctx* ctx, int64_t n_cap, uint32_t* start_hit, int32_t* n_hits,
+                             double* t_coll, int32_t* hits) {
+  if (!ctx) return TPC_ERR_ARG;
+  if (!ctx->tracks_valid) return fail(ctx, TPC_ERR_STATE, "run tpc_find_tracks first");
+  launch_export_tracklets(ctx->fb, ctx->geo.n_rows, n_cap, ctx->d_cnt, start_hit, n_hits, t_coll,
+                          hits, ctx->stream);
+  CK(cudaGetLastError());
+  return TPC_OK;
+}
+
+tpc_status tpc_get_calibrated(tpc_ctx* ctx, float* yc, float* zc) {
+  if (!ctx) return TPC_ERR_ARG;
+  if (!ctx->tracks_valid) return fail(ctx, TPC_ERR_STATE, "no track set");
+  tpc_status st = read_back(ctx);
+  if (st != TPC_OK) return st;
+  size_t m = ctx->h_pinned[kCntAssigned];
+  if (m) {
+    if (yc) CK(cudaMemcpyAsync(yc, ctx->tb.yc, sizeof(float) * m, cudaMemcpyDeviceToDevice, ctx->stream));
+    if (zc) CK(cudaMemcpyAsync(zc, ctx->tb.zc, sizeof(float) * m, cudaMemcpyDeviceToDevice, ctx->stream));
+  }
+  return TPC_OK;
+}
+
+tpc_status tpc_get_grid(tpc_ctx* ctx, uint32_t* order, uint32_t* row_start) {
+  if (!ctx) return TPC_ERR_ARG;
+  if (!ctx->loaded) return fail(ctx, TPC_ERR_STATE, "no batch loaded");
+  if (order && ctx->cl.n > 0)
+    CK(cudaMemcpyAsync(order, ctx->fb.gorig, sizeof(uint32_t) * ctx->cl.n, cudaMemcpyDeviceToDevice,
+                       ctx->stream));
+  if (row_start)
+    CK(cudaMemcpyAsync(row_start, ctx->fb.row_start, sizeof(uint32_t) * (ctx->K + 1),
+                       cudaMemcpyDeviceToDevice, ctx->stream));
+  return TPC_OK;
+}
+
+tpc_status tpc_profile(tpc_ctx* ctx, int enable) {
+  if (!ctx) return TPC_ERR_ARG;
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->prof.collect();
+  ctx->prof.stats.clear();
+  ctx->prof.launches = 0;
+  ctx->prof.on = enable != 0;
+  return TPC_OK;
+}
+
+tpc_status tpc_profile_read(tpc_ctx* ctx, tpc_kernel_stat* out, int32_t cap, int32_t* n_out,
+                            int64_t* launches) {
+  if (!ctx) return TPC_ERR_ARG;
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->prof.collect();
+  int32_t k = 0;
+  for (auto& kv : ctx->prof.stats) {
+    if (out && k < cap) {
+      std::memset(out[k].name, 0, sizeof(out[k].name));
+      std::strncpy(out[k].name, kv.first.c_str(), sizeof(out[k].name) - 1);
+      out[k].launches = kv.second.first;
+      out[k].total_ms = kv.second.second;
+    }
+    ++k;
+  }
+  if (n_out) *n_out = k;
+  if (launches) *launches = ctx->prof.launches;
+  return TPC_OK;
+}
+
+const char* tpc_last_error(const tpc_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+}  // extern "C"

@@ -1,0 +1,218 @@
+// Internal declarations shared by the CUDA translation units and the C ABI.
+#pragma once
+
+#include <cstdint>
+#include <map>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "tpc.h"
+#include "tpc_math.cuh"
+
+namespace tpc {
+
+// device error word bits
+enum : uint32_t {
+  kErrArg = 1u,           // invalid cluster field
+  kErrCapStart = 2u,      // start-hit / tracklet buffer overflow
+  kErrCapRow = 4u,        // a pad-row bucket exceeds the sort tile
+  kErrCapTrack = 8u,      // track buffer overflow
+  kErrNumeric = 16u,      // non-finite fit output
+  kErrTimeout = 32u,      // a bounded wait gave up
+};
+
+// device counters (uint32 each)
+enum : int {
+  kCntStart = 0,     // start hits (= tracklets)
+  kCntTracks = 1,    // emitted tracks
+  kCntAssigned = 2,  // clusters assigned to tracks
+  kCntSize = 8,
+};
+
+struct Params {
+  float sigma, shared_scale, nb_wy, nb_wz, nb_teta, nb_ty, nb_dmax, chi2_pick;
+  int32_t max_miss, max_gap, min_track_hits;
+  float s_max, inward_cov_scale;
+  float c0t[5], c0r[5];
+  float chi2_out;
+  int32_t min_acc_reject;
+  float refit_inflate;
+};
+
+// Search-grid geometry of a batch: ny x nz bins per (event, sector, row).
+struct GridDims {
+  int32_t ny, nz, nb;     // nb = ny * nz
+  float y_margin;         // cm beyond the sector edge
+  float z_margin;         // cm beyond the (event, side) z range
+};
+
+// Cluster input as the kernels see it (device pointers).
+struct ClIn {
+  int32_t n;
+  int32_t mode;
+  int32_t n_events;
+  const float* y;
+  const float* z;
+  const double* t;
+  const uint8_t* row;
+  const uint8_t* sector;
+  const uint8_t* flags;
+  const uint32_t* event;
+};
+
+// Buffers of the finder (device).
+struct FindBuf {
+  // bucketing
+  uint32_t* cnt;        // [K] cluster count per (event, sector, row)
+  uint32_t* row_start;  // [K + 1]
+  uint32_t* fill;       // [K]
+  int32_t* zmm;         // [n_events * 2 * 2] ordered-int min/max of seed z per side
+  float* zr;            // [n_events * 2 * 2] z0, 1/dz per (event, side)
+  float* zs_in;         // [n] seed z in input order
+  uint32_t* perm;       // [n] input index in bucket order
+  // grid order (bucket, bin, input index)
+  float* gy;            // [n]
+  float* gz;            // [n] seed z
+  double* gt;           // [n] drift time (mode 1)
+  uint32_t* gorig;      // [n] input index
+  uint32_t* gseg;       // [n] bucket (event*36 + sector)*n_rows + row
+  uint32_t* bin_start;  // [K * (nb + 1)]
+  // links (grid positions)
+  int32_t* up;
+  int32_t* dn;
+  int32_t* upc;
+  int32_t* dnc;
+  // compaction scratch
+  uint32_t* blk_a;      // [n_blocks]
+  uint32_t* blk_b;
+  uint32_t* off_a;      // [n_blocks + 1]
+  uint32_t* off_b;
+  // tracklets
+  uint32_t* starts;     // [cap_tl] grid position of the start hit
+  int32_t* nh;          // [cap_tl]
+  int32_t* hits;        // [cap_tl * n_rows] grid positions
+  double* that;         // [cap_tl]
+  unsigned long long* weight;  // [n]
+  uint32_t* nkeep;      // [cap_tl]
+  int64_t cap_tl;
+};
+
+// The current track set (device).
+struct TrackBuf {
+  uint32_t* track_start;  // [cap_tr + 1]
+  uint32_t* cluster_idx;  // [cap_asg]
+  uint32_t* asg_track;    // [cap_asg]
+  double* t_coll;         // [cap_tr]
+  uint32_t* start_hit;    // [cap_tr]
+  float* yc;              // [cap_asg] calibrated
+  float* zc;              // [cap_asg]
+  uint32_t* meta;         // [cap_asg] row | flags << 8 | sector << 16
+  int64_t cap_tr, cap_asg;
+};
+
+struct RefitBuf {
+  float* seed;            // [cap_tr * 5]
+  uint8_t* rej;           // [cap_asg]
+  int32_t* status;        // [cap_tr]
+  float* ckpt;            // [3 * cap_asg * 20]
+  float* gyc;             // [cap_asg] dL/d(calibrated y)
+  float* gzc;             // [cap_asg]
+  float* part_spline;     // [n_part_blocks * TPC_SPLINE_SIZE]
+  double* part_cal;       // [n_part_blocks * 2]
+  int64_t cap_ckpt;
+};
+
+// Per-context kernel accounting: every launch is counted; with timing on, a
+// pair of CUDA events on the launch stream brackets each kernel.
+struct Prof {
+  bool on = false;
+  int64_t launches = 0;
+  struct Rec {
+    const char* name;
+    cudaEvent_t a, b;
+  };
+  std::vector<Rec> pending;
+  std::vector<cudaEvent_t> pool;
+  std::map<std::string, std::pair<int64_t, double>> stats;  // name -> (launches, ms)
+  const char* cur = nullptr;
+  cudaEvent_t ev() {
+    cudaEvent_t e;
+    if (!pool.empty()) {
+      e = pool.back();
+      pool.pop_back();
+    } else {
+      cudaEventCreate(&e);
+    }
+    return e;
+  }
+  void begin(const char* name, cudaStream_t s) {
+    ++launches;
+    if (!on) return;
+    Rec r{name, ev(), ev()};
+    cudaEventRecord(r.a, s);
+    pending.push_back(r);
+  }
+  void end(cudaStream_t s) {
+    if (!on || pending.empty()) return;
+    cudaEventRecord(pending.back().b, s);
+  }
+  // Requires the stream to be synchronised.
+  void collect() {
+    for (auto& r : pending) {
+      float ms = 0.0f;
+      cudaEventElapsedTime(&ms, r.a, r.b);
+      auto& st = stats[r.name];
+      st.first += 1;
+      st.second += ms;
+      pool.push_back(r.a);
+      pool.push_back(r.b);
+    }
+    pending.clear();
+  }
+  ~Prof() {
+    for (auto& r : pending) {
+      cudaEventDestroy(r.a);
+      cudaEventDestroy(r.b);
+    }
+    for (auto e : pool) cudaEventDestroy(e);
+  }
+};
+
+#define TPC_LAUNCH(P, NAME, S, ...) \
+  do {                              \
+    if (P) (P)->begin(NAME, S);     \
+    __VA_ARGS__;                    \
+    if (P) (P)->end(S);             \
+  } while (0)
+
+constexpr int kSortTile = 4096;   // max clusters per pad-row bucket
+constexpr int kCalibGradBlocks = 148;
+
+// launchers (tpc_find.cu)
+void launch_load(Prof* P, const Geo& g, const Cal& c, const ClIn& cl, const GridDims& gd, int K,
+                 FindBuf& b, uint32_t* err, cudaStream_t s);
+void launch_find(Prof* P, const Geo& g, const Cal& c, const Params& p, const ClIn& cl,
+                 const GridDims& gd, int K, FindBuf& b, TrackBuf& tb, uint32_t* cnt,
+                 uint32_t* err, cudaStream_t s);
+void launch_set_tracks(Prof* P, const Geo& g, const Cal& c, const ClIn& cl, int64_t n_tracks,
+                       int64_t n_asg, TrackBuf& tb, uint32_t* cnt, uint32_t* err, cudaStream_t s);
+void launch_spline_bound(const float* spline, float* bound, cudaStream_t s);
+void launch_export_links(const FindBuf& b, int n, int K, int32_t* up, int32_t* dn, int32_t* upc,
+                         int32_t* dnc, cudaStream_t s);
+void launch_export_tracklets(const FindBuf& b, int n_rows, int64_t n_cap, const uint32_t* cnt,
+                             uint32_t* start_hit, int32_t* nh, double* that, int32_t* hits,
+                             cudaStream_t s);
+
+// launchers (tpc_refit.cu)
+void launch_refit(Prof* P, const Geo& g, const Params& p, int64_t cap_tr, const uint32_t* cnt,
+                  const TrackBuf& tb, RefitBuf& rb, bool save, float* params, float* cov,
+                  float* x, float* chi2, int32_t* ndf, int32_t* status, uint8_t* rej,
+                  uint32_t* err, cudaStream_t s);
+void launch_refit_backward(Prof* P, const Geo& g, const Cal& c, const Params& p, const ClIn& cl,
+                           int64_t cap_tr, int64_t cap_asg, const uint32_t* cnt,
+                           const TrackBuf& tb, RefitBuf& rb, const float* dl_dchi2,
+                           float* grad_y, float* grad_zt, double* grad_calib, cudaStream_t s);
+
+}  // namespace tpc

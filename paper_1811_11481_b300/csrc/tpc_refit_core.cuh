@@ -1,0 +1,412 @@
+// Per-track refit (arXiv:1811.11481 Sec. 3) and its adjoint, as plain
+// __host__ __device__ functions; the kernels in tpc_refit.cu run one track per
+// thread through them.
+#pragma once
+
+#include "tpc_math.cuh"
+
+namespace tpc {
+
+constexpr int kCk = 20;  // floats per checkpoint: state (5) + covariance (15)
+
+struct TrackIn {
+  const uint32_t* track_start;
+  const float* yc;
+  const float* zc;
+  const uint32_t* meta;  // row | flags << 8 | sector << 16
+};
+
+struct RefitCfg {
+  float kB, s_max, sigma, shared_scale, chi2_out, refit_inflate;
+  int32_t min_acc_reject;
+  float c0r[5];
+};
+
+TPC_HD float cl_var(const RefitCfg& p, uint32_t meta) {
+  float e = ((meta >> 8) & TPC_FLAG_SHARED) ? p.sigma * p.shared_scale : p.sigma;
+  return e * e;
+}
+
+// Seed at the outermost cluster from the circle through the innermost,
+// middle and outermost clusters.
+TPC_HD bool seed3(const Geo& g, const TrackIn& in, uint32_t a, int n, float st[5]) {
+  if (n < 3) return false;
+  int i0 = 0, im = n / 2, i2 = n - 1;
+  float x0 = g.row_x[in.meta[a + i0] & 0xffu], xm = g.row_x[in.meta[a + im] & 0xffu],
+        x2 = g.row_x[in.meta[a + i2] & 0xffu];
+  float y0 = in.yc[a + i0], ym = in.yc[a + im], y2 = in.yc[a + i2];
+  float ax = xm - x0, ay = ym - y0, bx = x2 - x0, by = y2 - y0, ex = x2 - xm, ey = y2 - ym;
+  float cross = ax * by - ay * bx;
+  float la = sqrtf(ax * ax + ay * ay), lb = sqrtf(bx * bx + by * by),
+        le = sqrtf(ex * ex + ey * ey);
+  float kap = (-2.0f * cross) / ((la * lb) * le);
+  float hs = (kap * lb) * 0.5f;
+  if (!(fabsf(hs) < 1.0f)) return false;
+  float s2 = (by / lb) * sqrtf(1.0f - hs * hs) - (bx / lb) * hs;
+  float arc = lb * arc_factor(hs);
+  st[0] = y2;
+  st[1] = in.zc[a + i2];
+  st[2] = s2;
+  st[3] = (in.zc[a + i2] - in.zc[a + i0]) / arc;
+  st[4] = kap / g.kB;
+  return true;
+}
+
+struct RefitOut {
+  float st[5];
+  float C[15];
+  float x;
+  float chi2;
+  int32_t ndf;
+  int32_t status;  // 0 ok, 1 propagation failed, 2 no seed
+};
+
+// Three passes (inward, outward, inward); rej[k] receives the pass that
+// rejected cluster k (0 = kept). ckpt (may be null): state before each step
+// at [(3 a + (pass - 1) n + k) * kCk].
+TPC_HD RefitOut refit_track(const Geo& g, const RefitCfg& p, const TrackIn& in, uint32_t a, int n,
+                            uint8_t* rej, float* seed_out, float* ckpt) {
+  RefitOut o;
+  for (int k = 0; k < n; ++k) rej[a + k] = 0;
+  o.status = 0;
+  o.chi2 = 0.0f;
+  o.ndf = 0;
+  float* st = o.st;
+  float* C = o.C;
+  if (!seed3(g, in, a, n, st)) {
+    o.status = 2;
+    for (int i = 0; i < 5; ++i) st[i] = 0.0f;
+    for (int i = 0; i < 15; ++i) C[i] = 0.0f;
+    o.x = 0.0f;
+    return o;
+  }
+  if (seed_out)
+    for (int i = 0; i < 5; ++i) seed_out[i] = st[i];
+  float x = g.row_x[in.meta[a + n - 1] & 0xffu];
+  set_diag(C, p.c0r);
+  float chi2 = 0.0f;
+  int ndf = 0;
+  for (int pass = 1; pass <= 3; ++pass) {
+    if (pass > 1)
+      for (int i = 0; i < 15; ++i) C[i] = C[i] * p.refit_inflate;
+    chi2 = 0.0f;
+    ndf = 0;
+    int nacc = 0;
+    for (int k = 0; k < n; ++k) {
+      int i = pass == 2 ? k : n - 1 - k;
+      int rj = rej[a + i];
+      if (rj != 0 && rj < pass) continue;
+      if (ckpt) {
+        float* ck = ckpt + ((size_t)3 * a + (size_t)(pass - 1) * n + k) * kCk;
+        for (int j = 0; j < 5; ++j) ck[j] = st[j];
+        for (int j = 0; j < 15; ++j) ck[5 + j] = C[j];
+      }
+      uint32_t m = in.meta[a + i];
+      if (!propagate(p.kB, p.s_max, st, C, x, g.row_x[m & 0xffu])) {
+        o.status = 1;
+        o.x = x;
+        return o;
+      }
+      float v = cl_var(p, m);
+      Innov iv = innovation(st, C, in.yc[a + i], in.zc[a + i], v, v);
+      if (nacc >= p.min_acc_reject && iv.chi2 > p.chi2_out) {
+        rej[a + i] = (uint8_t)pass;
+        continue;
+      }
+      apply_update(st, C, iv);
+      chi2 = chi2 + iv.chi2;
+      ndf += 2;
+      ++nacc;
+    }
+  }
+  o.x = x;
+  o.chi2 = chi2;
+  o.ndf = ndf;
+  return o;
+}
+
+// ------------------------------------------------------------ dual numbers
+// Forward-mode derivative in (sin phi, tan lambda, q/pT).
+struct D3 {
+  float v, d0, d1, d2;
+};
+TPC_HD D3 dc(float v) { return D3{v, 0.f, 0.f, 0.f}; }
+TPC_HD D3 operator+(D3 a, D3 b) { return D3{a.v + b.v, a.d0 + b.d0, a.d1 + b.d1, a.d2 + b.d2}; }
+TPC_HD D3 operator-(D3 a, D3 b) { return D3{a.v - b.v, a.d0 - b.d0, a.d1 - b.d1, a.d2 - b.d2}; }
+TPC_HD D3 operator-(D3 a) { return D3{-a.v, -a.d0, -a.d1, -a.d2}; }
+TPC_HD D3 operator*(D3 a, D3 b) {
+  return D3{a.v * b.v, a.d0 * b.v + a.v * b.d0, a.d1 * b.v + a.v * b.d1, a.d2 * b.v + a.v * b.d2};
+}
+TPC_HD D3 operator*(float s, D3 b) { return D3{s * b.v, s * b.d0, s * b.d1, s * b.d2}; }
+TPC_HD D3 operator/(D3 a, D3 b) {
+  float q = a.v / b.v, ib = 1.0f / b.v;
+  return D3{q, (a.d0 - q * b.d0) * ib, (a.d1 - q * b.d1) * ib, (a.d2 - q * b.d2) * ib};
+}
+TPC_HD D3 dsqrt(D3 a) {
+  float s = sqrtf(a.v), h = 0.5f / s;
+  return D3{s, a.d0 * h, a.d1 * h, a.d2 * h};
+}
+TPC_HD D3 chain(D3 a, float f, float df) { return D3{f, a.d0 * df, a.d1 * df, a.d2 * df}; }
+
+// d/dh of B(h) = A'(h): from the series for small h, else E^3 - 2 B / h.
+TPC_HD float arc_factor_deriv2(float h) {
+  if (fabsf(h) < 0.125f) {
+    float h2 = h * h;
+    float c = 315.0f / 1408.0f;
+    c = 35.0f / 144.0f + h2 * c;
+    c = 15.0f / 56.0f + h2 * c;
+    c = 3.0f / 10.0f + h2 * c;
+    c = 1.0f / 3.0f + h2 * c;
+    float dc2 = 4.0f * (315.0f / 1408.0f);
+    dc2 = 3.0f * (35.0f / 144.0f) + h2 * dc2;
+    dc2 = 2.0f * (15.0f / 56.0f) + h2 * dc2;
+    dc2 = 3.0f / 10.0f + h2 * dc2;
+    return c + 2.0f * h2 * dc2;
+  }
+  float e = 1.0f / sqrtf(1.0f - h * h);
+  return e * e * e - 2.0f * arc_factor_deriv(h) / h;
+}
+
+// Gradient in (s, t, q) of <Jbar, J> over the state-dependent Jacobian entries.
+TPC_HD void jac_vjp(float kB, float dx, float sv, float tv, float qv, float b_ys, float b_yq,
+                    float b_zs, float b_zt, float b_zq, float g[3]) {
+  D3 s{sv, 1.f, 0.f, 0.f}, t{tv, 0.f, 1.f, 0.f}, q{qv, 0.f, 0.f, 1.f};
+  D3 kap = kB * q;
+  D3 s2 = s - dx * kap;
+  D3 one = dc(1.0f);
+  D3 c1 = dsqrt(one - s * s);
+  D3 c2 = dsqrt(one - s2 * s2);
+  D3 N = s + s2;
+  D3 D = c1 + c2;
+  D3 T = N / D;
+  D3 opt = one + T * T;
+  D3 d = dx * dsqrt(opt);
+  D3 h = 0.5f * (kap * d);
+  D3 A = chain(h, arc_factor(h.v), arc_factor_deriv(h.v));
+  D3 l = d * A;
+  D3 dDds = -(s / c1) - (s2 / c2);
+  float kdx = kB * dx;
+  D3 dDdq = kdx * (s2 / c2);
+  D3 dTds = (dc(2.0f) - T * dDds) / D;
+  D3 dTdq = (dc(-kdx) - T * dDdq) / D;
+  D3 Jys = dx * dTds;
+  D3 Jyq = dx * dTdq;
+  D3 gg = (d * T) / opt;
+  D3 dds = gg * dTds;
+  D3 ddq = gg * dTdq;
+  D3 E = one / dsqrt(one - h * h);
+  D3 Bh = chain(h, arc_factor_deriv(h.v), arc_factor_deriv2(h.v));
+  D3 Jzs = t * (E * dds);
+  D3 Jzq = t * (E * ddq + 0.5f * (kB * ((d * d) * Bh)));
+  D3 Jzt = l;
+  g[0] = b_ys * Jys.d0 + b_yq * Jyq.d0 + b_zs * Jzs.d0 + b_zt * Jzt.d0 + b_zq * Jzq.d0;
+  g[1] = b_ys * Jys.d1 + b_yq * Jyq.d1 + b_zs * Jzs.d1 + b_zt * Jzt.d1 + b_zq * Jzq.d1;
+  g[2] = b_ys * Jys.d2 + b_yq * Jyq.d2 + b_zs * Jzs.d2 + b_zt * Jzt.d2 + b_zq * Jzq.d2;
+}
+
+TPC_HD void unpack(const float P[15], float F[5][5]) {
+  for (int i = 0; i < 5; ++i)
+    for (int j = 0; j < 5; ++j) F[i][j] = P[sidx(i, j)];
+}
+
+// Adjoint of the Kalman update at the predicted state (Pp = predicted
+// covariance): on entry pb, G are the adjoints of the updated state and of
+// the updated covariance (full symmetric matrix, packed); on exit those of
+// the predicted ones. cbar is the adjoint of the chi2 increment; mbar
+// receives the adjoint of the measurement.
+TPC_HD void update_adjoint(const float Pp[15], const Innov& in, float cbar, float pb[5],
+                           float G[15], float mbar[2]) {
+  float P[5][5], Gf[5][5];
+  unpack(Pp, P);
+  unpack(G, Gf);
+  float r0 = in.r0, r1 = in.r1;
+  float W00 = in.W00, W01 = in.W01, W11 = in.W11;
+  float u0 = W00 * r0 + W01 * r1, u1 = W01 * r0 + W11 * r1;
+  float ub0 = 0.f, ub1 = 0.f;
+  for (int i = 0; i < 5; ++i) {
+    ub0 += P[i][0] * pb[i];
+    ub1 += P[i][1] * pb[i];
+  }
+  float BW0[5], BW1[5];
+  for (int i = 0; i < 5; ++i) {
+    BW0[i] = P[i][0] * W00 + P[i][1] * W01;
+    BW1[i] = P[i][0] * W01 + P[i][1] * W11;
+  }
+  float Bb0[5], Bb1[5], GB0[5], GB1[5];
+  for (int i = 0; i < 5; ++i) {
+    float a0 = 0.f, a1 = 0.f, c0 = 0.f, c1 = 0.f;
+    for (int k = 0; k < 5; ++k) {
+      a0 += Gf[i][k] * BW0[k];
+      a1 += Gf[i][k] * BW1[k];
+      c0 += Gf[i][k] * P[k][0];
+      c1 += Gf[i][k] * P[k][1];
+    }
+    Bb0[i] = pb[i] * u0 - 2.0f * a0;
+    Bb1[i] = pb[i] * u1 - 2.0f * a1;
+    GB0[i] = c0;
+    GB1[i] = c1;
+  }
+  float M00 = 0.f, M01 = 0.f, M10 = 0.f, M11 = 0.f;  // B^T G B
+  for (int i = 0; i < 5; ++i) {
+    M00 += P[i][0] * GB0[i];
+    M01 += P[i][0] * GB1[i];
+    M10 += P[i][1] * GB0[i];
+    M11 += P[i][1] * GB1[i];
+  }
+  float Wb00 = -M00 + cbar * r0 * r0 + ub0 * r0;
+  float Wb01 = -M01 + cbar * r0 * r1 + ub0 * r1;
+  float Wb10 = -M10 + cbar * r1 * r0 + ub1 * r0;
+  float Wb11 = -M11 + cbar * r1 * r1 + ub1 * r1;
+  float rb0 = 2.0f * cbar * u0 + W00 * ub0 + W01 * ub1;
+  float rb1 = 2.0f * cbar * u1 + W01 * ub0 + W11 * ub1;
+  // S_bar = -W Wbar W
+  float X00 = W00 * Wb00 + W01 * Wb10, X01 = W00 * Wb01 + W01 * Wb11;
+  float X10 = W01 * Wb00 + W11 * Wb10, X11 = W01 * Wb01 + W11 * Wb11;
+  float Sb00 = -(X00 * W00 + X01 * W01), Sb01 = -(X00 * W01 + X01 * W11);
+  float Sb10 = -(X10 * W00 + X11 * W01), Sb11 = -(X10 * W01 + X11 * W11);
+  float Pb[5][5];
+  for (int i = 0; i < 5; ++i)
+    for (int j = 0; j < 5; ++j) Pb[i][j] = Gf[i][j];
+  for (int i = 0; i < 5; ++i) {
+    Pb[i][0] += Bb0[i];
+    Pb[i][1] += Bb1[i];
+  }
+  Pb[0][0] += Sb00;
+  Pb[0][1] += Sb01;
+  Pb[1][0] += Sb10;
+  Pb[1][1] += Sb11;
+  for (int i = 0; i < 5; ++i)
+    for (int j = 0; j <= i; ++j) G[sidx(i, j)] = 0.5f * (Pb[i][j] + Pb[j][i]);
+  mbar[0] = rb0;
+  mbar[1] = rb1;
+  pb[0] -= rb0;
+  pb[1] -= rb1;
+}
+
+// Adjoint of the helix transport of state and covariance. p, Cp: state and
+// covariance before the step; on entry pb, G are the adjoints after it.
+TPC_HD void transport_adjoint(float kB, float dx, const float p[5], const float Cp[15],
+                              const Jac& J, float pb[5], float G[15]) {
+  float Jf[5][5];
+  for (int i = 0; i < 5; ++i)
+    for (int j = 0; j < 5; ++j) Jf[i][j] = i == j ? 1.0f : 0.0f;
+  Jf[0][2] = J.ys;
+  Jf[0][4] = J.yq;
+  Jf[1][2] = J.zs;
+  Jf[1][3] = J.zt;
+  Jf[1][4] = J.zq;
+  Jf[2][4] = J.sq;
+  float Cf[5][5], Gf[5][5];
+  unpack(Cp, Cf);
+  unpack(G, Gf);
+  float M[5][5];  // J C
+  for (int i = 0; i < 5; ++i)
+    for (int l = 0; l < 5; ++l) {
+      float acc = 0.f;
+      for (int k = 0; k < 5; ++k) acc += Jf[i][k] * Cf[k][l];
+      M[i][l] = acc;
+    }
+  float Jb[2][5];  // rows 0 and 1 of Jbar = 2 G J C
+  for (int a = 0; a < 2; ++a)
+    for (int b = 0; b < 5; ++b) {
+      float acc = 0.f;
+      for (int c = 0; c < 5; ++c) acc += Gf[a][c] * M[c][b];
+      Jb[a][b] = 2.0f * acc;
+    }
+  float gq[3];
+  jac_vjp(kB, dx, p[2], p[3], p[4], Jb[0][2], Jb[0][4], Jb[1][2], Jb[1][3], Jb[1][4], gq);
+  float n0 = pb[0], n1 = pb[1];
+  float n2 = J.ys * pb[0] + J.zs * pb[1] + pb[2] + gq[0];
+  float n3 = J.zt * pb[1] + pb[3] + gq[1];
+  float n4 = J.yq * pb[0] + J.zq * pb[1] + J.sq * pb[2] + pb[4] + gq[2];
+  pb[0] = n0;
+  pb[1] = n1;
+  pb[2] = n2;
+  pb[3] = n3;
+  pb[4] = n4;
+  float GJ[5][5];
+  for (int i = 0; i < 5; ++i)
+    for (int j = 0; j < 5; ++j) {
+      float acc = 0.f;
+      for (int k = 0; k < 5; ++k) acc += Gf[i][k] * Jf[k][j];
+      GJ[i][j] = acc;
+    }
+  for (int i = 0; i < 5; ++i)
+    for (int j = 0; j <= i; ++j) {
+      float acc = 0.f;
+      for (int k = 0; k < 5; ++k) acc += Jf[k][i] * GJ[k][j];
+      G[sidx(i, j)] = acc;
+    }
+}
+
+TPC_HD bool step_active(int rj, int pass) { return !(rj != 0 && rj < pass); }
+
+// Reverse sweep of one saved refit: writes the adjoints of the calibrated
+// coordinates gyc[a + k], gzc[a + k] of L = gT * chi2(pass 3).
+TPC_HD void refit_backward_track(const Geo& g, const RefitCfg& p, const TrackIn& in, uint32_t a,
+                                 int n, const uint8_t* rej, const float* ckpt, float gT,
+                                 float* gyc, float* gzc) {
+  for (int k = 0; k < n; ++k) {
+    gyc[a + k] = 0.0f;
+    gzc[a + k] = 0.0f;
+  }
+  auto xof = [&](int i) { return g.row_x[in.meta[a + i] & 0xffu]; };
+  auto idx_of = [&](int pass, int k) { return pass == 2 ? k : n - 1 - k; };
+  float xend[4];
+  xend[0] = xof(n - 1);
+  for (int pass = 1; pass <= 3; ++pass) {
+    xend[pass] = xend[pass - 1];
+    for (int k = n - 1; k >= 0; --k) {
+      int i = idx_of(pass, k);
+      if (step_active(rej[a + i], pass)) {
+        xend[pass] = xof(i);
+        break;
+      }
+    }
+  }
+  float pb[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+  float G[15];
+  for (int i = 0; i < 15; ++i) G[i] = 0.0f;
+  for (int pass = 3; pass >= 1; --pass) {
+    float cbar = pass == 3 ? gT : 0.0f;
+    for (int k = n - 1; k >= 0; --k) {
+      int i = idx_of(pass, k);
+      int rj = rej[a + i];
+      if (!step_active(rj, pass)) continue;
+      float xprev = xend[pass - 1];
+      for (int kk = k - 1; kk >= 0; --kk) {
+        int ii = idx_of(pass, kk);
+        if (step_active(rej[a + ii], pass)) {
+          xprev = xof(ii);
+          break;
+        }
+      }
+      const float* ck = ckpt + ((size_t)3 * a + (size_t)(pass - 1) * n + k) * kCk;
+      float p0[5], C0[15];
+      for (int j = 0; j < 5; ++j) p0[j] = ck[j];
+      for (int j = 0; j < 15; ++j) C0[j] = ck[5 + j];
+      float pp[5];
+      for (int j = 0; j < 5; ++j) pp[j] = p0[j];
+      float xx = xprev;
+      float xi = xof(i);
+      Jac J;
+      transport(p.kB, 2.0f, pp, xx, xi, J);
+      float Cp[15];
+      for (int j = 0; j < 15; ++j) Cp[j] = C0[j];
+      transport_cov(J, Cp);
+      if (rj != pass) {
+        float v = cl_var(p, in.meta[a + i]);
+        Innov iv = innovation(pp, Cp, in.yc[a + i], in.zc[a + i], v, v);
+        float mb[2];
+        update_adjoint(Cp, iv, cbar, pb, G, mb);
+        gyc[a + i] += mb[0];
+        gzc[a + i] += mb[1];
+      }
+      transport_adjoint(p.kB, xi - xprev, p0, C0, J, pb, G);
+    }
+    if (pass > 1)
+      for (int j = 0; j < 15; ++j) G[j] = G[j] * p.refit_inflate;
+  }
+}
+
+}  // namespace tpc
