@@ -36,7 +36,7 @@ UNIT = "clusters/s"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="central",
@@ -84,7 +84,7 @@ class Clocks:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                 "--format=csv,noheader,nounits", "-lms", "100"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.th = threading.Thread(target=self._read, daemon=True)
             self.th.start()
@@ -209,6 +209,15 @@ def run_ours(args):
     # warm-up (allocations happen here), then a count check
     for _ in range(max(3, args.warmup)):
         step()
+    if args.profile_steps:
+        # steady-state steps only: for ncu launch lists and captures
+        tr.profile(True)
+        for _ in range(args.profile_steps):
+            step()
+        kstats, launches = tr.profile_read()
+        print(json.dumps(dict(profile_steps=args.profile_steps, launches=launches,
+                              kernels={k: v for k, v in kstats.items()})))
+        return
     nt, na, ntl = tr.counts()
     tl = tr.tracklets()
     sum_nh = int(tl["nh"].clamp(min=0).sum().item())
@@ -219,9 +228,12 @@ def run_ours(args):
         torch.cuda.synchronize()
 
     # ---- timed region: device-resident inputs, L2 flushed before each step
-    tr.profile(True)
     clocks = Clocks(local)
     clocks.start()
+    t_end = time.time() + 1.5  # keep the GPU busy while the sampler starts
+    while time.time() < t_end:
+        step()
+    tr.profile(True)
     barrier()
     times = []
     for _ in range(args.steps):

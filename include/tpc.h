@@ -97,6 +97,7 @@ typedef struct {
   float chi2_out;         /* refit outlier cut on the predicted chi2       */
   int32_t min_acc_reject; /* accepted clusters before rejection starts     */
   float refit_inflate;    /* covariance inflation between refit passes     */
+  int32_t seed_max_hits;  /* chain hits used by the tracklet seed fit      */
 } tpc_params;
 
 /* Calibration (Sec. 4 and Sec. 5.2): drift velocity, time offset and a

@@ -53,7 +53,8 @@ class _Params(C.Structure):
                 ("min_track_hits", C.c_int32), ("s_max", C.c_float),
                 ("inward_cov_scale", C.c_float), ("c0t", C.c_float * 5),
                 ("c0r", C.c_float * 5), ("chi2_out", C.c_float),
-                ("min_acc_reject", C.c_int32), ("refit_inflate", C.c_float)]
+                ("min_acc_reject", C.c_int32), ("refit_inflate", C.c_float),
+                ("seed_max_hits", C.c_int32)]
 
 
 class _Calib(C.Structure):

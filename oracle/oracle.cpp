@@ -213,6 +213,7 @@ struct OrcParams {
   int32_t min_acc_reject; // accepted clusters before rejection starts
   float refit_inflate;    // passes 2 and 3 start from the previous pass's
                           // final covariance times this factor
+  int32_t seed_max_hits;  // chain hits used by the seed fit (Sec. 2: 4 to 10)
 };
 
 struct OrcCalib {
@@ -657,7 +658,8 @@ TrackletOut tracklet(const Ctx& c, const int32_t* upc, int64_t start, int32_t* h
   std::vector<int64_t> H;
   int64_t cur = start;
   H.push_back(cur);
-  while (upc[cur] >= 0) {
+  // the seed is the first segment of at most seed_max_hits linked hits
+  while (upc[cur] >= 0 && (int)H.size() < c.p.seed_max_hits) {
     cur = upc[cur];
     H.push_back(cur);
   }

@@ -42,7 +42,8 @@ class tpc_params(C.Structure):
                 ("max_gap", C.c_int32), ("min_track_hits", C.c_int32), ("s_max", C.c_float),
                 ("inward_cov_scale", C.c_float), ("c0t", C.c_float * 5),
                 ("c0r", C.c_float * 5), ("chi2_out", C.c_float),
-                ("min_acc_reject", C.c_int32), ("refit_inflate", C.c_float)]
+                ("min_acc_reject", C.c_int32), ("refit_inflate", C.c_float),
+                ("seed_max_hits", C.c_int32)]
 
 
 class tpc_calib(C.Structure):

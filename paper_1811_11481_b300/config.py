@@ -27,6 +27,7 @@ DEFAULT_PARAMS = dict(
     chi2_out=25.0,           # outlier cut on the predicted chi2 (Sec. 3)
     min_acc_reject=5,        # accepted clusters before rejection starts
     refit_inflate=100.0,     # covariance inflation between refit passes
+    seed_max_hits=10,        # chain hits in the seed fit (Sec. 2: segments of 4-10 hits)
 )
 
 # flag bits of a cluster (Sec. 3 lists the special cluster types)

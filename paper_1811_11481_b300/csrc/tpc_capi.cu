@@ -92,6 +92,7 @@ void copy_params(const tpc_params& s, Params& d) {
   d.chi2_out = s.chi2_out;
   d.min_acc_reject = s.min_acc_reject;
   d.refit_inflate = s.refit_inflate;
+  d.seed_max_hits = s.seed_max_hits;
 }
 
 std::string err_text(uint32_t e) {
@@ -212,6 +213,7 @@ void tpc_default_params(tpc_params* p) {
   p->chi2_out = 25.0f;
   p->min_acc_reject = 5;
   p->refit_inflate = 100.0f;
+  p->seed_max_hits = 10;
 }
 
 tpc_status tpc_create(const tpc_geometry* geo, const tpc_params* params, void* stream,
@@ -279,7 +281,7 @@ void tpc_destroy(tpc_ctx* ctx) {
   cudaStreamSynchronize(ctx->stream);
   void* ptrs[] = {ctx->d_spline, ctx->d_spl_bound, ctx->d_err, ctx->d_cnt,
                   ctx->fb.cnt, ctx->fb.row_start, ctx->fb.fill, ctx->fb.zmm, ctx->fb.zr,
-                  ctx->fb.zs_in, ctx->fb.perm, ctx->fb.gy, ctx->fb.gz, ctx->fb.gt,
+                  ctx->fb.zs_in, ctx->fb.perm, ctx->fb.gyz, ctx->fb.gt,
                   ctx->fb.gorig, ctx->fb.gseg, ctx->fb.bin_start, ctx->fb.up, ctx->fb.dn,
                   ctx->fb.upc, ctx->fb.dnc, ctx->fb.blk_a, ctx->fb.blk_b, ctx->fb.off_a,
                   ctx->fb.off_b, ctx->fb.starts, ctx->fb.nh, ctx->fb.hits, ctx->fb.that,
@@ -356,8 +358,7 @@ tpc_status tpc_load_clusters(tpc_ctx* ctx, const tpc_clusters* in) {
     int64_t c = n > 0 ? n : 1;
     CK(alloc(b.zs_in, c));
     CK(alloc(b.perm, c));
-    CK(alloc(b.gy, c));
-    CK(alloc(b.gz, c));
+    CK(alloc(b.gyz, c));
     CK(alloc(b.gt, c));
     CK(alloc(b.gorig, c));
     CK(alloc(b.gseg, c));

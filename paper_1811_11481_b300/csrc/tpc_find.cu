@@ -162,8 +162,8 @@ __device__ __forceinline__ int bin_z(const GridDims& gd, const float* zr, int si
 // One block per (event, sector, row) bucket: bitonic sort of (bin, input index)
 // keys in shared memory, then the grid-ordered SoA and the bin offsets.
 __global__ void k_row_sort(Geo g, ClIn cl, GridDims gd, const uint32_t* row_start,
-                           const uint32_t* perm, const float* zs_in, const float* zr, float* gy,
-                           float* gz, double* gt, uint32_t* gorig, uint32_t* gseg,
+                           const uint32_t* perm, const float* zs_in, const float* zr, float2* gyz,
+                           double* gt, uint32_t* gorig, uint32_t* gseg,
                            uint32_t* bin_start, uint32_t* err) {
   extern __shared__ unsigned long long keys[];
   int seg = blockIdx.x;
@@ -179,8 +179,7 @@ __global__ void k_row_sort(Geo g, ClIn cl, GridDims gd, const uint32_t* row_star
     for (int b = threadIdx.x; b <= gd.nb; b += blockDim.x) bs[b] = start;
     for (int j = threadIdx.x; j < n; j += blockDim.x) {
       uint32_t i = perm[start + j];
-      gy[start + j] = cl.y[i];
-      gz[start + j] = zs_in[i];
+      gyz[start + j] = make_float2(cl.y[i], zs_in[i]);
       if (cl.mode == 1) gt[start + j] = cl.t[i];
       gorig[start + j] = i;
       gseg[start + j] = (uint32_t)seg;
@@ -227,8 +226,7 @@ __global__ void k_row_sort(Geo g, ClIn cl, GridDims gd, const uint32_t* row_star
     for (int q = bprev + 1; q <= b; ++q) bs[q] = start + j;
     if (j == n - 1)
       for (int q = b + 1; q <= gd.nb; ++q) bs[q] = start + n;
-    gy[start + j] = cl.y[i];
-    gz[start + j] = zs_in[i];
+    gyz[start + j] = make_float2(cl.y[i], zs_in[i]);
     if (cl.mode == 1) gt[start + j] = cl.t[i];
     gorig[start + j] = i;
     gseg[start + j] = (uint32_t)seg;
@@ -255,7 +253,7 @@ __device__ __forceinline__ Box make_box(const Geo& g, const GridDims& gd, const 
 // windows whose d lies closest to the straight line through h and u; ties go
 // to the lowest pair of input indices.
 __global__ void k_neighbours(Geo g, Params p, GridDims gd, const uint32_t* nvalid,
-                             const float* gy, const float* gz, const uint32_t* gorig,
+                             const float2* __restrict__ gyz, const uint32_t* __restrict__ gorig,
                              const uint32_t* gseg, const uint32_t* bin_start, const float* zr,
                              int32_t* up, int32_t* dn) {
   int h = blockIdx.x * blockDim.x + threadIdx.x;
@@ -268,7 +266,8 @@ __global__ void k_neighbours(Geo g, Params p, GridDims gd, const uint32_t* nvali
     int e = es / kNS, s = es % kNS;
     int side = e * 2 + (s >= 18 ? 1 : 0);
     float xh = g.row_x[r], xu = g.row_x[r + 1], xd = g.row_x[r - 1];
-    float yh = gy[h], zh = gz[h];
+    float2 hh = gyz[h];
+    float yh = hh.x, zh = hh.y;
     float dxu = xu - xh, dxd = xh - xd;
     float wy_u = dxu * p.nb_ty + p.nb_wy;
     float wy_d = dxd * p.nb_ty + p.nb_wy;
@@ -288,7 +287,8 @@ __global__ void k_neighbours(Geo g, Params p, GridDims gd, const uint32_t* nvali
     for (int iz = BU.iz0; iz <= BU.iz1; ++iz) {
       uint32_t u0 = bsu[iz * gd.ny + BU.iy0], u1 = bsu[iz * gd.ny + BU.iy1 + 1];
       for (uint32_t u = u0; u < u1; ++u) {
-        float yu = gy[u], zu = gz[u];
+        float2 uu = gyz[u];
+        float yu = uu.x, zu = uu.y;
         if (!(fabsf(yu - yh) <= wy_u)) continue;
         if (!(fabsf(zu - zh) <= wz_u)) continue;
         float py = yh - (yu - yh) * f;
@@ -297,7 +297,8 @@ __global__ void k_neighbours(Geo g, Params p, GridDims gd, const uint32_t* nvali
         for (int jz = BD.iz0; jz <= BD.iz1; ++jz) {
           uint32_t d0 = bsd[jz * gd.ny + BD.iy0], d1 = bsd[jz * gd.ny + BD.iy1 + 1];
           for (uint32_t d = d0; d < d1; ++d) {
-            float yd = gy[d], zd = gz[d];
+            float2 dd = gyz[d];
+            float yd = dd.x, zd = dd.y;
             if (!(fabsf(yd - yh) <= wy_d)) continue;
             if (!(fabsf(zd - zh) <= wz_d)) continue;
             float ey = yd - py, ez = zd - pz;
@@ -412,8 +413,7 @@ __global__ void k_write_starts(const uint32_t* nvalid, const int32_t* upc, const
 
 // ------------------------------------------------------ a7: tracklets
 struct Grid {
-  const float* gy;
-  const float* gz;
+  const float2* gyz;
   const double* gt;
   const uint32_t* gorig;
   const uint32_t* bin_start;
@@ -436,27 +436,38 @@ __device__ int pick(const Geo& g, const Cal& c, const Params& p, const GridDims&
   float yp = st[0], zp = st[1] - shift;
   Box B = make_box(g, gd, G.zr, r, side, yp - wy - dymax - eps, yp + wy + dymax + eps,
                    zp - wz - dzmax - eps, zp + wz + dzmax + eps);
-  const uint32_t* bs = G.bin_start + (size_t)seg * (gd.nb + 1);
+  const uint32_t* __restrict__ bs = G.bin_start + (size_t)seg * (gd.nb + 1);
   int best = -1;
   float bd = 0.0f;
-  uint32_t bo = 0;
-  for (int iz = B.iz0; iz <= B.iz1; ++iz) {
-    uint32_t j0 = bs[iz * gd.ny + B.iy0], j1 = bs[iz * gd.ny + B.iy1 + 1];
-    for (uint32_t j = j0; j < j1; ++j) {
-      float yc, zc;
-      calibrate(g, c, spl_on, mode, sec, r, G.gy[j], G.gz[j], mode == 1 ? G.gt[j] : 0.0, that,
-                yc, zc);
-      float ry = yc - st[0];
-      float rz = zc - st[1];
-      float d2 = (ry * ry) / vy + (rz * rz) / vz;
-      if (!(d2 <= p.chi2_pick)) continue;
-      uint32_t o = G.gorig[j];
-      if (best < 0 || d2 < bd || (d2 == bd && o < bo)) {
-        best = (int)j;
-        bd = d2;
-        bo = o;
-        ycb = yc;
-        zcb = zc;
+  for (int izb = B.iz0; izb <= B.iz1; izb += 4) {
+    // bin offsets of up to four z rows of the box, loaded together
+    uint32_t lo[4], hi[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      int iz = izb + q;
+      bool in = iz <= B.iz1;
+      lo[q] = in ? __ldg(bs + iz * gd.ny + B.iy0) : 0u;
+      hi[q] = in ? __ldg(bs + iz * gd.ny + B.iy1 + 1) : 0u;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      for (uint32_t j = lo[q]; j < hi[q]; ++j) {
+        float2 yz = __ldg(G.gyz + j);
+        double tj = mode == 1 ? __ldg(G.gt + j) : 0.0;
+        float yc, zc;
+        calibrate(g, c, spl_on, mode, sec, r, yz.x, yz.y, tj, that, yc, zc);
+        float ry = yc - st[0];
+        float rz = zc - st[1];
+        float d2 = (ry * ry) / vy + (rz * rz) / vz;
+        if (!(d2 <= p.chi2_pick)) continue;
+        bool take = best < 0 || d2 < bd;
+        if (!take && d2 == bd) take = __ldg(G.gorig + j) < __ldg(G.gorig + best);
+        if (take) {
+          best = (int)j;
+          bd = d2;
+          ycb = yc;
+          zcb = zc;
+        }
       }
     }
   }
@@ -484,21 +495,23 @@ __global__ void __launch_bounds__(128) k_tracklets(Geo g, Cal c, Params p, GridD
   bool spl_on = c.spl_bound[2] > 0.0f;
   float dymax = spl_on ? c.spl_bound[0] : 0.0f;
   float dzmax = spl_on ? c.spl_bound[1] : 0.0f;
-  // chain end
-  int hl = h0, rl = r0;
-  while (upc[hl] >= 0) {
+  // the seed: the first segment of at most seed_max_hits linked hits
+  int hl = h0, rl = r0, nseed = 1;
+  while (upc[hl] >= 0 && nseed < p.seed_max_hits) {
     hl = upc[hl];
     ++rl;
+    ++nseed;
   }
   float st[5], C[15], x;
   // seed fit in seeding coordinates
-  seed_two_points(st, C, x, p.c0t, g.row_x[r0], G.gy[h0], G.gz[h0], g.row_x[rl], G.gy[hl],
-                  G.gz[hl]);
+  float2 yz0 = G.gyz[h0], yzl = G.gyz[hl];
+  seed_two_points(st, C, x, p.c0t, g.row_x[r0], yz0.x, yz0.y, g.row_x[rl], yzl.x, yzl.y);
   {
     int h = h0, r = r0;
     while (true) {
       if (!propagate(g.kB, p.s_max, st, C, x, g.row_x[r])) return;
-      apply_update(st, C, innovation(st, C, G.gy[h], G.gz[h], sig2, sig2));
+      float2 yz = G.gyz[h];
+      apply_update(st, C, innovation(st, C, yz.x, yz.y, sig2, sig2));
       if (h == hl) break;
       h = upc[h];
       ++r;
@@ -515,17 +528,17 @@ __global__ void __launch_bounds__(128) k_tracklets(Geo g, Cal c, Params p, GridD
   // seed fit in calibrated coordinates
   {
     float y0, z0, y1, z1;
-    calibrate(g, c, spl_on, mode, sec, r0, G.gy[h0], G.gz[h0], mode == 1 ? G.gt[h0] : 0.0, that,
-              y0, z0);
-    calibrate(g, c, spl_on, mode, sec, rl, G.gy[hl], G.gz[hl], mode == 1 ? G.gt[hl] : 0.0, that,
-              y1, z1);
+    calibrate(g, c, spl_on, mode, sec, r0, yz0.x, yz0.y, mode == 1 ? G.gt[h0] : 0.0, that, y0,
+              z0);
+    calibrate(g, c, spl_on, mode, sec, rl, yzl.x, yzl.y, mode == 1 ? G.gt[hl] : 0.0, that, y1,
+              z1);
     seed_two_points(st, C, x, p.c0t, g.row_x[r0], y0, z0, g.row_x[rl], y1, z1);
     int h = h0, r = r0;
     while (true) {
       if (!propagate(g.kB, p.s_max, st, C, x, g.row_x[r])) return;
       float yc, zc;
-      calibrate(g, c, spl_on, mode, sec, r, G.gy[h], G.gz[h], mode == 1 ? G.gt[h] : 0.0, that,
-                yc, zc);
+      float2 yz = G.gyz[h];
+      calibrate(g, c, spl_on, mode, sec, r, yz.x, yz.y, mode == 1 ? G.gt[h] : 0.0, that, yc, zc);
       apply_update(st, C, innovation(st, C, yc, zc, sig2, sig2));
       if (h == hl) break;
       h = upc[h];
@@ -775,7 +788,7 @@ void launch_load(Prof* P, const Geo& g, const Cal& c, const ClIn& cl, const Grid
     TPC_LAUNCH(P, "k_scatter", s,
                k_scatter<<<nblk(cl.n, kB256), kB256, 0, s>>>(g, cl, b.row_start, b.fill, b.perm));
   size_t smem = kSortTile * sizeof(unsigned long long);
-  TPC_LAUNCH(P, "k_row_sort", s, k_row_sort<<<K, 512, smem, s>>>(g, cl, gd, b.row_start, b.perm, b.zs_in, b.zr, b.gy, b.gz,
+  TPC_LAUNCH(P, "k_row_sort", s, k_row_sort<<<K, 512, smem, s>>>(g, cl, gd, b.row_start, b.perm, b.zs_in, b.zr, b.gyz,
                                    b.gt, b.gorig, b.gseg, b.bin_start, err));
 }
 
@@ -786,7 +799,7 @@ void launch_find(Prof* P, const Geo& g, const Cal& c, const Params& p, const ClI
   int nb = nblk(n, kB256);
   if (n > 0) {
     const uint32_t* nv = b.row_start + K;
-    TPC_LAUNCH(P, "k_neighbours", s, k_neighbours<<<nb, kB256, 0, s>>>(g, p, gd, nv, b.gy, b.gz, b.gorig, b.gseg, b.bin_start,
+    TPC_LAUNCH(P, "k_neighbours", s, k_neighbours<<<nb, kB256, 0, s>>>(g, p, gd, nv, b.gyz, b.gorig, b.gseg, b.bin_start,
                                       b.zr, b.up, b.dn));
     TPC_LAUNCH(P, "k_clean", s, k_clean<<<nb, kB256, 0, s>>>(nv, b.up, b.dn, b.upc, b.dnc, b.blk_a));
   }
@@ -796,7 +809,7 @@ void launch_find(Prof* P, const Geo& g, const Cal& c, const Params& p, const ClI
     TPC_LAUNCH(P, "k_write_starts", s, k_write_starts<<<nb, kB256, 0, s>>>(b.row_start + K, b.upc, b.dnc, b.off_a,
                                         (uint32_t)b.cap_tl, b.starts));
   cudaMemsetAsync(b.weight, 0, sizeof(unsigned long long) * (size_t)(n > 0 ? n : 1), s);
-  Grid G{b.gy, b.gz, b.gt, b.gorig, b.bin_start, b.zr};
+  Grid G{b.gyz, b.gt, b.gorig, b.bin_start, b.zr};
   int ntl_blk = nblk(b.cap_tl, 128);
   TPC_LAUNCH(P, "k_tracklets", s, k_tracklets<<<ntl_blk, 128, 0, s>>>(g, c, p, gd, G, cl.mode, b.upc, b.gseg, b.starts, cnt, b.nh,
                                       b.hits, b.that, b.weight));

@@ -39,6 +39,7 @@ struct Params {
   float chi2_out;
   int32_t min_acc_reject;
   float refit_inflate;
+  int32_t seed_max_hits;
 };
 
 // Search-grid geometry of a batch: ny x nz bins per (event, sector, row).
@@ -73,8 +74,7 @@ struct FindBuf {
   float* zs_in;         // [n] seed z in input order
   uint32_t* perm;       // [n] input index in bucket order
   // grid order (bucket, bin, input index)
-  float* gy;            // [n]
-  float* gz;            // [n] seed z
+  float2* gyz;          // [n] (y, seed z)
   double* gt;           // [n] drift time (mode 1)
   uint32_t* gorig;      // [n] input index
   uint32_t* gseg;       // [n] bucket (event*36 + sector)*n_rows + row

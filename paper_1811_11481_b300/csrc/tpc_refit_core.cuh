@@ -285,58 +285,54 @@ TPC_HD void update_adjoint(const float Pp[15], const Innov& in, float cbar, floa
 
 // Adjoint of the helix transport of state and covariance. p, Cp: state and
 // covariance before the step; on entry pb, G are the adjoints after it.
+// J differs from the identity only in (0,2) (0,4) (1,2) (1,3) (1,4) (2,4).
 TPC_HD void transport_adjoint(float kB, float dx, const float p[5], const float Cp[15],
                               const Jac& J, float pb[5], float G[15]) {
-  float Jf[5][5];
-  for (int i = 0; i < 5; ++i)
-    for (int j = 0; j < 5; ++j) Jf[i][j] = i == j ? 1.0f : 0.0f;
-  Jf[0][2] = J.ys;
-  Jf[0][4] = J.yq;
-  Jf[1][2] = J.zs;
-  Jf[1][3] = J.zt;
-  Jf[1][4] = J.zq;
-  Jf[2][4] = J.sq;
   float Cf[5][5], Gf[5][5];
   unpack(Cp, Cf);
   unpack(G, Gf);
-  float M[5][5];  // J C
-  for (int i = 0; i < 5; ++i)
-    for (int l = 0; l < 5; ++l) {
-      float acc = 0.f;
-      for (int k = 0; k < 5; ++k) acc += Jf[i][k] * Cf[k][l];
-      M[i][l] = acc;
-    }
-  float Jb[2][5];  // rows 0 and 1 of Jbar = 2 G J C
+  // M = J C (rows 3 and 4 are those of C)
+  float M[5][5];
+  for (int l = 0; l < 5; ++l) {
+    M[0][l] = Cf[0][l] + J.ys * Cf[2][l] + J.yq * Cf[4][l];
+    M[1][l] = Cf[1][l] + J.zs * Cf[2][l] + J.zt * Cf[3][l] + J.zq * Cf[4][l];
+    M[2][l] = Cf[2][l] + J.sq * Cf[4][l];
+    M[3][l] = Cf[3][l];
+    M[4][l] = Cf[4][l];
+  }
+  // Jbar = 2 G J C at the state-dependent entries (rows 0 and 1)
+  float Jb[2][5];
   for (int a = 0; a < 2; ++a)
-    for (int b = 0; b < 5; ++b) {
+    for (int b = 2; b < 5; ++b) {
       float acc = 0.f;
       for (int c = 0; c < 5; ++c) acc += Gf[a][c] * M[c][b];
       Jb[a][b] = 2.0f * acc;
     }
   float gq[3];
   jac_vjp(kB, dx, p[2], p[3], p[4], Jb[0][2], Jb[0][4], Jb[1][2], Jb[1][3], Jb[1][4], gq);
-  float n0 = pb[0], n1 = pb[1];
   float n2 = J.ys * pb[0] + J.zs * pb[1] + pb[2] + gq[0];
   float n3 = J.zt * pb[1] + pb[3] + gq[1];
   float n4 = J.yq * pb[0] + J.zq * pb[1] + J.sq * pb[2] + pb[4] + gq[2];
-  pb[0] = n0;
-  pb[1] = n1;
   pb[2] = n2;
   pb[3] = n3;
   pb[4] = n4;
-  float GJ[5][5];
-  for (int i = 0; i < 5; ++i)
-    for (int j = 0; j < 5; ++j) {
-      float acc = 0.f;
-      for (int k = 0; k < 5; ++k) acc += Gf[i][k] * Jf[k][j];
-      GJ[i][j] = acc;
-    }
-  for (int i = 0; i < 5; ++i)
-    for (int j = 0; j <= i; ++j) {
-      float acc = 0.f;
-      for (int k = 0; k < 5; ++k) acc += Jf[k][i] * GJ[k][j];
-      G[sidx(i, j)] = acc;
-    }
+  // X = G J (column operations), then J^T X (row operations)
+  float X[5][5];
+  for (int i = 0; i < 5; ++i) {
+    X[i][0] = Gf[i][0];
+    X[i][1] = Gf[i][1];
+    X[i][2] = J.ys * Gf[i][0] + J.zs * Gf[i][1] + Gf[i][2];
+    X[i][3] = J.zt * Gf[i][1] + Gf[i][3];
+    X[i][4] = J.yq * Gf[i][0] + J.zq * Gf[i][1] + J.sq * Gf[i][2] + Gf[i][4];
+  }
+  for (int j = 0; j < 5; ++j) {
+    float r0 = X[0][j], r1 = X[1][j], r2 = X[2][j], r3 = X[3][j], r4 = X[4][j];
+    float c2 = J.ys * r0 + J.zs * r1 + r2;
+    float c3 = J.zt * r1 + r3;
+    float c4 = J.yq * r0 + J.zq * r1 + J.sq * r2 + r4;
+    float col[5] = {r0, r1, c2, c3, c4};
+    for (int i = j; i < 5; ++i) G[sidx(i, j)] = col[i];
+  }
 }
 
 TPC_HD bool step_active(int rj, int pass) { return !(rj != 0 && rj < pass); }
