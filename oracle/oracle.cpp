@@ -181,6 +181,21 @@ inline Var B_of(Var h) {
   return (E - asin_(h) / h) / h;
 }
 
+// E(h) = 1/sqrt(1 - h^2): Maclaurin series (coefficients e_n) for small h.
+inline float E_of(float h) {
+  if (std::fabs(h) < 0.125f) {
+    float h2 = h * h;
+    float p = 35.0f / 128.0f;
+    p = 5.0f / 16.0f + h2 * p;
+    p = 3.0f / 8.0f + h2 * p;
+    p = 0.5f + h2 * p;
+    return 1.0f + h2 * p;
+  }
+  return 1.0f / std::sqrt(1.0f - h * h);
+}
+inline double E_of(double h) { return 1.0 / std::sqrt(1.0 - h * h); }
+inline Var E_of(Var h) { return Var(1.0) / sqrt_(Var(1.0) - h * h); }
+
 }  // namespace
 
 // ------------------------------------------------------------ C interface
@@ -404,9 +419,12 @@ template <class R> bool propagate(const Ctx& c, Trk<R>& st, R x2, R* Jout = null
   if (!(abs_(s2) < R(c.p.s_max))) return false;
   R c1 = sqrt_(R(1) - s * s);
   R c2 = sqrt_(R(1) - s2 * s2);
+  R ic1 = R(1) / c1;
+  R ic2 = R(1) / c2;
   R N = s + s2;
   R D = c1 + c2;
-  R T = N / D;
+  R iD = R(1) / D;
+  R T = N * iD;
   R dy = dx * T;
   R opt = R(1) + T * T;
   R d = dx * sqrt_(opt);
@@ -414,17 +432,17 @@ template <class R> bool propagate(const Ctx& c, Trk<R>& st, R x2, R* Jout = null
   R A = A_of(h);
   R l = d * A;
   // Jacobian entries that differ from the identity
-  R dDds = -(s / c1) - (s2 / c2);
+  R dDds = -(s * ic1) - (s2 * ic2);
   R kdx = kB * dx;
-  R dDdq = kdx * (s2 / c2);
-  R dTds = (R(2) - T * dDds) / D;
-  R dTdq = (-kdx - T * dDdq) / D;
+  R dDdq = kdx * (s2 * ic2);
+  R dTds = (R(2) - T * dDds) * iD;
+  R dTdq = (-kdx - T * dDdq) * iD;
   R Jys = dx * dTds;
   R Jyq = dx * dTdq;
   R g = (d * T) / opt;
   R dds = g * dTds;
   R ddq = g * dTdq;
-  R E = R(1) / sqrt_(R(1) - h * h);
+  R E = E_of(h);
   R Bh = B_of(h);
   R Jzs = t * (E * dds);
   R Jzq = t * (E * ddq + (kB * ((d * d) * Bh)) * R(0.5));
@@ -473,9 +491,10 @@ template <class R> Innov<R> innovation(const Trk<R>& st, R my, R mz, R vy, R vz)
   R S01 = st.C[1][0];
   R S11 = st.C[1][1] + vz;
   R det = S00 * S11 - S01 * S01;
-  in.W00 = S11 / det;
-  in.W01 = -(S01 / det);
-  in.W11 = S00 / det;
+  R idet = R(1) / det;
+  in.W00 = S11 * idet;
+  in.W01 = -(S01 * idet);
+  in.W11 = S00 * idet;
   in.chi2 = in.r0 * (in.W00 * in.r0 + in.W01 * in.r1) + in.r1 * (in.W01 * in.r0 + in.W11 * in.r1);
   return in;
 }
@@ -617,6 +636,29 @@ template <class R> void neighbours_of(const Ctx& c, int64_t h, int32_t& up, int3
 }
 
 // -------------------------------------------------- tracklet constructor
+// During following (Sec. 4) the seeding coordinate of a cluster is shifted in
+// z by the offset that the estimated collision time implies,
+// shift = side * vdrift * (that - tf_start) (computed once in float64), and
+// the space-point correction is applied at the shifted position.
+template <class R> R follow_shift(const Ctx& c, int sec, double that) {
+  if (c.cl.mode == 0) return R(0);
+  double sg = sec < 18 ? 1.0 : -1.0;
+  return (R)(sg * c.c.vdrift * (that - c.c.tf_start));
+}
+template <class R> void calibrate_follow(const Ctx& c, int64_t i, R shift, R& yc, R& zc) {
+  R y = R(c.cl.y[i]);
+  R za = zs_of<R>(c, i) + shift;
+  if (c.spline_active) {
+    R d[2];
+    spline_eval<R>(c, c.cl.sector[i], R(c.rowx[c.cl.row[i]]), y, abs_(za), d, nullptr);
+    yc = y + d[0];
+    zc = za + d[1];
+  } else {
+    yc = y;
+    zc = za;
+  }
+}
+
 struct TrackletOut {
   int32_t nh;
   double that;
@@ -625,18 +667,20 @@ struct TrackletOut {
 };
 
 template <class R>
-int64_t pick(const Ctx& c, int ev, int sec, int r, const Trk<R>& st, double that) {
+int64_t pick(const Ctx& c, int ev, int sec, int r, const Trk<R>& st, R shift) {
   const auto& L = c.rowlist(ev, sec, r);
   R sig2 = R(c.p.sigma) * R(c.p.sigma);
   R cut = R(c.p.chi2_pick);
+  R ivy = R(1) / (st.C[0][0] + sig2);
+  R ivz = R(1) / (st.C[1][1] + sig2);
   int64_t bj = -1;
   R bd = R(0);
   for (int64_t j : L) {
     R yc, zc;
-    calibrate<R>(c, j, that, cal_in<R>(c, j), yc, zc, nullptr);
+    calibrate_follow<R>(c, j, shift, yc, zc);
     R ry = yc - st.p[0];
     R rz = zc - st.p[1];
-    R d2 = (ry * ry) / (st.C[0][0] + sig2) + (rz * rz) / (st.C[1][1] + sig2);
+    R d2 = (ry * ry) * ivy + (rz * rz) * ivz;
     if (!(d2 <= cut)) continue;
     if (bj < 0 || d2 < bd) { bj = j; bd = d2; }
   }
@@ -682,10 +726,11 @@ TrackletOut tracklet(const Ctx& c, const int32_t* upc, int64_t start, int32_t* h
     double sg = sec < 18 ? 1.0 : -1.0;
     that = c.c.tf_start - (sg * (double)zd) / c.c.vdrift;
   }
+  const R shift = follow_shift<R>(c, sec, that);
   // seed fit in calibrated coordinates
   std::vector<R> yc(n), zc(n);
   for (size_t k = 0; k < n; ++k)
-    calibrate<R>(c, H[k], that, cal_in<R>(c, H[k]), yc[k], zc[k], nullptr);
+    calibrate_follow<R>(c, H[k], shift, yc[k], zc[k]);
   seed_two_points<R>(c, st, X(H[0]), yc[0], zc[0], X(H[n - 1]), yc[n - 1], zc[n - 1]);
   for (size_t k = 0; k < n; ++k) {
     if (!propagate<R>(c, st, X(H[k]))) return o;
@@ -698,10 +743,10 @@ TrackletOut tracklet(const Ctx& c, const int32_t* upc, int64_t start, int32_t* h
   int miss = 0;
   for (int r = rlast + 1; r < c.g.n_rows; ++r) {
     if (!propagate<R>(c, st, R(c.rowx[r]))) break;
-    int64_t j = pick<R>(c, ev, sec, r, st, that);
+    int64_t j = pick<R>(c, ev, sec, r, st, shift);
     if (j >= 0) {
       R y, z;
-      calibrate<R>(c, j, that, cal_in<R>(c, j), y, z, nullptr);
+      calibrate_follow<R>(c, j, shift, y, z);
       apply_update<R>(st, innovation<R>(st, y, z, sig2, sig2));
       best = st;
       rlast = r;
@@ -719,10 +764,10 @@ TrackletOut tracklet(const Ctx& c, const int32_t* upc, int64_t start, int32_t* h
   miss = 0;
   for (int r = rlast; r >= 0; --r) {
     if (!propagate<R>(c, st, R(c.rowx[r]))) break;
-    int64_t j = pick<R>(c, ev, sec, r, st, that);
+    int64_t j = pick<R>(c, ev, sec, r, st, shift);
     if (j >= 0) {
       R y, z;
-      calibrate<R>(c, j, that, cal_in<R>(c, j), y, z, nullptr);
+      calibrate_follow<R>(c, j, shift, y, z);
       apply_update<R>(st, innovation<R>(st, y, z, sig2, sig2));
       hits[r] = (int32_t)j;
       ++nh;

@@ -99,7 +99,7 @@ std::string err_text(uint32_t e) {
   std::string s;
   if (e & kErrArg) s += "invalid cluster field (row, sector, event or time); ";
   if (e & kErrCapStart) s += "start-hit buffer overflow (retry enlarges it); ";
-  if (e & kErrCapRow) s += "a pad-row bucket exceeds 4096 clusters; ";
+  if (e & kErrCapRow) s += "a pad-row bucket exceeds 16384 clusters; ";
   if (e & kErrCapTrack) s += "track buffer overflow; ";
   if (e & kErrNumeric) s += "non-finite value in a refit; ";
   if (e & kErrTimeout) s += "a bounded device wait gave up; ";
@@ -132,23 +132,33 @@ tpc_status read_back(tpc_ctx* ctx) {
 
 tpc_status ensure_track_buffers(tpc_ctx* ctx, int64_t cap_tr, int64_t cap_asg) {
   TrackBuf& t = ctx->tb;
+  RefitBuf& rb = ctx->rb;
   if (cap_tr > ctx->cap_tr_alloc) {
     CK(alloc(t.track_start, cap_tr + 1));
     CK(alloc(t.t_coll, cap_tr));
     CK(alloc(t.start_hit, cap_tr));
-    CK(alloc(ctx->rb.seed, cap_tr * 5));
-    CK(alloc(ctx->rb.status, cap_tr));
+    CK(alloc(rb.seed, cap_tr * 5));
+    CK(alloc(rb.order, cap_tr));
+    CK(alloc(rb.slot, cap_tr));
+    CK(alloc(rb.wlen, cap_tr / 32 + 2));
+    CK(alloc(rb.wbase, cap_tr / 32 + 3));
+    CK(alloc(rb.status, cap_tr));
     ctx->cap_tr_alloc = cap_tr;
   }
   if (cap_asg > ctx->cap_asg_alloc) {
+    int64_t cap_w = cap_asg + 32 * 257;
     CK(alloc(t.cluster_idx, cap_asg));
     CK(alloc(t.asg_track, cap_asg));
     CK(alloc(t.yc, cap_asg));
     CK(alloc(t.zc, cap_asg));
     CK(alloc(t.meta, cap_asg));
-    CK(alloc(ctx->rb.rej, cap_asg));
-    CK(alloc(ctx->rb.gyc, cap_asg));
-    CK(alloc(ctx->rb.gzc, cap_asg));
+    CK(alloc(rb.w_yc, cap_w));
+    CK(alloc(rb.w_zc, cap_w));
+    CK(alloc(rb.w_meta, cap_w));
+    CK(alloc(rb.rej, cap_w));
+    CK(alloc(rb.gyc, cap_w));
+    CK(alloc(rb.gzc, cap_w));
+    rb.cap_w = cap_w;
     ctx->cap_asg_alloc = cap_asg;
   }
   t.cap_tr = cap_tr;
@@ -252,6 +262,9 @@ tpc_status tpc_create(const tpc_geometry* geo, const tpc_params* params, void* s
   chk(cudaMalloc(&ctx->d_spl_bound, sizeof(float) * 4));
   chk(cudaMalloc(&ctx->d_err, sizeof(uint32_t)));
   chk(cudaMalloc(&ctx->d_cnt, sizeof(uint32_t) * kCntSize));
+  chk(cudaMalloc(&ctx->rb.len_hist, sizeof(uint32_t) * 1024));
+  chk(cudaMalloc(&ctx->fb.list_counts, sizeof(uint32_t) * 2));
+  chk(cudaMalloc(&ctx->fb.n_bins, sizeof(uint32_t)));
   chk(cudaMallocHost(&ctx->h_pinned, sizeof(uint32_t) * (kCntSize + 1)));
   if (st != TPC_OK) {
     tpc_destroy(ctx);
@@ -281,13 +294,15 @@ void tpc_destroy(tpc_ctx* ctx) {
   cudaStreamSynchronize(ctx->stream);
   void* ptrs[] = {ctx->d_spline, ctx->d_spl_bound, ctx->d_err, ctx->d_cnt,
                   ctx->fb.cnt, ctx->fb.row_start, ctx->fb.fill, ctx->fb.zmm, ctx->fb.zr,
-                  ctx->fb.zs_in, ctx->fb.perm, ctx->fb.gyz, ctx->fb.gt,
-                  ctx->fb.gorig, ctx->fb.gseg, ctx->fb.bin_start, ctx->fb.up, ctx->fb.dn,
+                  ctx->fb.zs_in, ctx->fb.perm, ctx->fb.gyz,
+                  ctx->fb.gorig, ctx->fb.gseg, ctx->fb.bin_start, ctx->fb.big_list, ctx->fb.mid_list, ctx->fb.list_counts,
+                  ctx->fb.n_bins, ctx->fb.es_dims, ctx->fb.up, ctx->fb.dn,
                   ctx->fb.upc, ctx->fb.dnc, ctx->fb.blk_a, ctx->fb.blk_b, ctx->fb.off_a,
                   ctx->fb.off_b, ctx->fb.starts, ctx->fb.nh, ctx->fb.hits, ctx->fb.that,
                   ctx->fb.weight, ctx->fb.nkeep, ctx->tb.track_start, ctx->tb.cluster_idx,
                   ctx->tb.asg_track, ctx->tb.t_coll, ctx->tb.start_hit, ctx->tb.yc, ctx->tb.zc,
-                  ctx->tb.meta, ctx->rb.seed, ctx->rb.rej, ctx->rb.status, ctx->rb.ckpt,
+                  ctx->tb.meta, ctx->rb.seed, ctx->rb.order, ctx->rb.slot, ctx->rb.wlen, ctx->rb.wbase, ctx->rb.len_hist,
+                  ctx->rb.w_yc, ctx->rb.w_zc, ctx->rb.w_meta, ctx->rb.rej, ctx->rb.status, ctx->rb.ckpt,
                   ctx->rb.gyc, ctx->rb.gzc, ctx->rb.part_spline, ctx->rb.part_cal};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -338,19 +353,10 @@ tpc_status tpc_load_clusters(tpc_ctx* ctx, const tpc_clusters* in) {
   int64_t n = in->n;
   int K = in->n_events * TPC_N_SECTORS * ctx->geo.n_rows;
   ctx->K = K;
-  // grid: ~2 clusters per bin
-  double avg = (double)n / (double)K;
-  int nbt = (int)(avg / 2.0);
-  if (nbt < 1) nbt = 1;
-  if (nbt > 4096) nbt = 4096;
-  int ny = (int)std::sqrt(nbt / 4.0);
-  if (ny < 1) ny = 1;
-  if (ny > 16) ny = 16;
-  int nz = nbt / ny;
-  if (nz < 1) nz = 1;
-  ctx->gd.ny = ny;
-  ctx->gd.nz = nz;
-  ctx->gd.nb = ny * nz;
+  // search grid: about one cluster per bin, geometry chosen on the device
+  ctx->gd.tau = 1.0f;
+  ctx->gd.nb_max = 8192;
+  ctx->gd.ny_max = 16;
   ctx->gd.y_margin = 2.0f;
   ctx->gd.z_margin = 1.0f;
   FindBuf& b = ctx->fb;
@@ -359,7 +365,6 @@ tpc_status tpc_load_clusters(tpc_ctx* ctx, const tpc_clusters* in) {
     CK(alloc(b.zs_in, c));
     CK(alloc(b.perm, c));
     CK(alloc(b.gyz, c));
-    CK(alloc(b.gt, c));
     CK(alloc(b.gorig, c));
     CK(alloc(b.gseg, c));
     CK(alloc(b.up, c));
@@ -382,6 +387,8 @@ tpc_status tpc_load_clusters(tpc_ctx* ctx, const tpc_clusters* in) {
     }
   }
   if (K > ctx->cap_K) {
+    CK(alloc(b.big_list, K));
+    CK(alloc(b.mid_list, K));
     CK(alloc(b.cnt, K));
     CK(alloc(b.row_start, (int64_t)K + 1));
     CK(alloc(b.fill, K));
@@ -390,9 +397,11 @@ tpc_status tpc_load_clusters(tpc_ctx* ctx, const tpc_clusters* in) {
   if (in->n_events > ctx->cap_ev) {
     CK(alloc(b.zmm, (int64_t)in->n_events * 4));
     CK(alloc(b.zr, (int64_t)in->n_events * 4));
+    CK(alloc(b.es_dims, (int64_t)in->n_events * TPC_N_SECTORS));
     ctx->cap_ev = in->n_events;
   }
-  int64_t nbins = (int64_t)K * (ctx->gd.nb + 1);
+  // per row: nb + 1 <= total / (rows * tau) + ny_max + 1 entries
+  int64_t nbins = (int64_t)((double)n / ctx->gd.tau) + (int64_t)K * (ctx->gd.ny_max + 2) + 64;
   if (nbins > ctx->cap_bins) {
     CK(alloc(b.bin_start, nbins));
     ctx->cap_bins = nbins;
@@ -484,7 +493,7 @@ tpc_status tpc_refit(tpc_ctx* ctx, int save_for_backward, float* params, float* 
   if (!ctx) return TPC_ERR_ARG;
   if (!ctx->tracks_valid) return fail(ctx, TPC_ERR_STATE, "no track set");
   if (save_for_backward) {
-    int64_t need = 3 * ctx->tb.cap_asg * 20;
+    int64_t need = 3 * ctx->rb.cap_w * 20;
     if (need > ctx->cap_ckpt_alloc) {
       CK(alloc(ctx->rb.ckpt, need));
       ctx->cap_ckpt_alloc = need;

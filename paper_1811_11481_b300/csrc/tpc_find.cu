@@ -103,9 +103,12 @@ __global__ void k_hist(Geo g, Cal c, ClIn cl, uint32_t* cnt, float* zs_in, int32
   if (o > zmm[2 * side + 1]) atomicMax(&zmm[2 * side + 1], o);
 }
 
-// Single block: bucket offsets and z-bin geometry per (event, side).
-__global__ void k_scan_rows(int K, int n_events, GridDims gd, const uint32_t* cnt,
-                            uint32_t* row_start, const int32_t* zmm, float* zr) {
+// Single block: bucket offsets, the z range of each (event, side) and the bin
+// geometry of each (event, sector): ny x nz bins of about tau clusters each,
+// square in (y, z) on average, shared by the rows of the sector.
+__global__ void k_scan_rows(Geo g, int K, int n_events, GridDims gd, const uint32_t* cnt,
+                            uint32_t* row_start, const int32_t* zmm, float* zr, uint2* es_dims,
+                            uint32_t* n_bins) {
   __shared__ uint32_t carry;
   if (threadIdx.x == 0) carry = 0u;
   __syncthreads();
@@ -129,9 +132,45 @@ __global__ void k_scan_rows(int K, int n_events, GridDims gd, const uint32_t* cn
       float z0 = lo - gd.z_margin;
       float span = (hi + gd.z_margin) - z0;
       zr[2 * i] = z0;
-      zr[2 * i + 1] = (float)gd.nz / span;
+      zr[2 * i + 1] = 1.0f / span;
     }
   }
+  __syncthreads();
+  if (threadIdx.x == 0) carry = 0u;
+  __syncthreads();
+  int nes = n_events * kNS;
+  int R = g.n_rows;
+  float xm = g.row_x[R / 2];
+  float W = 2.0f * (xm * g.tan_half + gd.y_margin);
+  for (int base = 0; base < nes; base += blockDim.x) {
+    int es = base + threadIdx.x;
+    uint32_t sz = 0u;
+    uint32_t dims = 1u | (1u << 16);
+    if (es < nes) {
+      uint32_t tot = row_start[(es + 1) * R] - row_start[es * R];
+      int nbt = (int)((float)tot / ((float)R * gd.tau));
+      if (nbt < 1) nbt = 1;
+      if (nbt > gd.nb_max) nbt = gd.nb_max;
+      int side = (es / kNS) * 2 + ((es % kNS) >= 18 ? 1 : 0);
+      float invspan = zr[2 * side + 1];
+      float H = invspan > 0.0f ? 1.0f / invspan : 1.0f;
+      int ny = (int)(sqrtf((float)nbt * W / H) + 0.5f);
+      if (ny < 1) ny = 1;
+      if (ny > gd.ny_max) ny = gd.ny_max;
+      if (ny > nbt) ny = nbt;
+      int nz = nbt / ny;
+      if (nz < 1) nz = 1;
+      dims = (uint32_t)ny | ((uint32_t)nz << 16);
+      sz = (uint32_t)R * (uint32_t)(ny * nz + 1);
+    }
+    uint32_t tot;
+    uint32_t ex = block_excl_scan(sz, &tot);
+    if (es < nes) es_dims[es] = make_uint2(carry + ex, dims);
+    __syncthreads();
+    if (threadIdx.x == 0) carry += tot;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *n_bins = carry;
 }
 
 __global__ void k_scatter(Geo g, ClIn cl, const uint32_t* row_start, uint32_t* fill,
@@ -146,46 +185,42 @@ __global__ void k_scatter(Geo g, ClIn cl, const uint32_t* row_start, uint32_t* f
   perm[pos] = (uint32_t)i;
 }
 
-__device__ __forceinline__ int bin_y(const Geo& g, const GridDims& gd, int r, float y) {
-  float hw = g.row_x[r] * g.tan_half + gd.y_margin;
-  float v = (y + hw) * ((float)gd.ny / (2.0f * hw));
-  int iy = (int)floorf(v);
-  return iy < 0 ? 0 : (iy >= gd.ny ? gd.ny - 1 : iy);
+// Search-grid geometry of one (event, sector): tables of nb + 1 bin offsets
+// per row starting at base + row * (nb + 1).
+struct Bins {
+  uint32_t base;
+  int ny, nz, nb;
+};
+__device__ __forceinline__ Bins es_bins(const uint2* es_dims, int es) {
+  uint2 d = es_dims[es];
+  Bins b;
+  b.base = d.x;
+  b.ny = (int)(d.y & 0xffffu);
+  b.nz = (int)(d.y >> 16);
+  b.nb = b.ny * b.nz;
+  return b;
 }
-__device__ __forceinline__ int bin_z(const GridDims& gd, const float* zr, int side, float z) {
-  float v = (z - zr[2 * side]) * zr[2 * side + 1];
+__device__ __forceinline__ int bin_y(const Geo& g, const GridDims& gd, int r, int ny, float y) {
+  float hw = g.row_x[r] * g.tan_half + gd.y_margin;
+  float v = (y + hw) * ((float)ny / (2.0f * hw));
+  int iy = (int)floorf(v);
+  if (!(v == v)) iy = 0;
+  return iy < 0 ? 0 : (iy >= ny ? ny - 1 : iy);
+}
+__device__ __forceinline__ int bin_z(const float* zr, int side, int nz, float z) {
+  float v = (z - zr[2 * side]) * ((float)nz * zr[2 * side + 1]);
   int iz = (int)floorf(v);
   if (!(v == v)) iz = 0;
-  return iz < 0 ? 0 : (iz >= gd.nz ? gd.nz - 1 : iz);
+  return iz < 0 ? 0 : (iz >= nz ? nz - 1 : iz);
 }
 
-// One block per (event, sector, row) bucket: bitonic sort of (bin, input index)
-// keys in shared memory, then the grid-ordered SoA and the bin offsets.
-__global__ void k_row_sort(Geo g, ClIn cl, GridDims gd, const uint32_t* row_start,
-                           const uint32_t* perm, const float* zs_in, const float* zr, float2* gyz,
-                           double* gt, uint32_t* gorig, uint32_t* gseg,
-                           uint32_t* bin_start, uint32_t* err) {
-  extern __shared__ unsigned long long keys[];
-  int seg = blockIdx.x;
-  uint32_t start = row_start[seg];
-  int n = (int)(row_start[seg + 1] - start);
-  uint32_t* bs = bin_start + (size_t)seg * (gd.nb + 1);
-  if (n == 0) {
-    for (int b = threadIdx.x; b <= gd.nb; b += blockDim.x) bs[b] = start;
-    return;
-  }
-  if (n > kSortTile) {
-    if (threadIdx.x == 0) atomicOr(err, kErrCapRow);
-    for (int b = threadIdx.x; b <= gd.nb; b += blockDim.x) bs[b] = start;
-    for (int j = threadIdx.x; j < n; j += blockDim.x) {
-      uint32_t i = perm[start + j];
-      gyz[start + j] = make_float2(cl.y[i], zs_in[i]);
-      if (cl.mode == 1) gt[start + j] = cl.t[i];
-      gorig[start + j] = i;
-      gseg[start + j] = (uint32_t)seg;
-    }
-    return;
-  }
+// Bitonic sort of one (event, sector, row) bucket by (bin, input index) in
+// shared memory (keys[] holds 'tile' entries), then the grid-ordered SoA and
+// the bin offsets of the bucket.
+__device__ void sort_bucket(const Geo& g, const ClIn& cl, const GridDims& gd, const Bins& B,
+                            int seg, uint32_t start, int n, const uint32_t* perm,
+                            const float* zs_in, const float* zr, float2* gyz, uint32_t* gorig,
+                            uint32_t* gseg, uint32_t* bs, unsigned long long* keys) {
   int r = seg % g.n_rows;
   int es = seg / g.n_rows;
   int e = es / kNS, s = es % kNS;
@@ -196,7 +231,7 @@ __global__ void k_row_sort(Geo g, ClIn cl, GridDims gd, const uint32_t* row_star
     unsigned long long k = ~0ull;
     if (j < n) {
       uint32_t i = perm[start + j];
-      int b = bin_z(gd, zr, side, zs_in[i]) * gd.ny + bin_y(g, gd, r, cl.y[i]);
+      int b = bin_z(zr, side, B.nz, zs_in[i]) * B.ny + bin_y(g, gd, r, B.ny, cl.y[i]);
       k = ((unsigned long long)(uint32_t)b << 32) | i;
     }
     keys[j] = k;
@@ -225,11 +260,125 @@ __global__ void k_row_sort(Geo g, ClIn cl, GridDims gd, const uint32_t* row_star
     int bprev = j > 0 ? (int)(keys[j - 1] >> 32) : -1;
     for (int q = bprev + 1; q <= b; ++q) bs[q] = start + j;
     if (j == n - 1)
-      for (int q = b + 1; q <= gd.nb; ++q) bs[q] = start + n;
+      for (int q = b + 1; q <= B.nb; ++q) bs[q] = start + n;
     gyz[start + j] = make_float2(cl.y[i], zs_in[i]);
-    if (cl.mode == 1) gt[start + j] = cl.t[i];
     gorig[start + j] = i;
     gseg[start + j] = (uint32_t)seg;
+  }
+}
+
+// Bucket too large for any tile: copied unsorted, its bins left empty (the
+// capacity error is raised).
+__device__ void copy_bucket_unsorted(const ClIn& cl, int nb, int seg, uint32_t start, int n,
+                                     const uint32_t* perm, const float* zs_in, float2* gyz,
+                                     uint32_t* gorig, uint32_t* gseg, uint32_t* bs) {
+  for (int b = threadIdx.x; b <= nb; b += blockDim.x) bs[b] = start;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    uint32_t i = perm[start + j];
+    gyz[start + j] = make_float2(cl.y[i], zs_in[i]);
+    gorig[start + j] = i;
+    gseg[start + j] = (uint32_t)seg;
+  }
+}
+
+// Small buckets (<= 256 clusters): one warp each, 8 per block, bitonic sort
+// in a 256-entry shared tile per warp. Larger buckets are listed for the
+// block sorts below.
+constexpr int kWarpTile = 256;
+__global__ void k_row_sort_warp(Geo g, ClIn cl, GridDims gd, int K, const uint32_t* row_start,
+                                const uint2* es_dims, const uint32_t* perm, const float* zs_in,
+                                const float* zr, float2* gyz, uint32_t* gorig, uint32_t* gseg,
+                                uint32_t* bin_start, uint32_t* mid_list, uint32_t* mid_count,
+                                uint32_t* big_list, uint32_t* big_count) {
+  __shared__ unsigned long long tiles[8][kWarpTile];
+  int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int seg = blockIdx.x * 8 + w;
+  if (seg >= K) return;
+  uint32_t start = row_start[seg];
+  int n = (int)(row_start[seg + 1] - start);
+  int r = seg % g.n_rows;
+  int es = seg / g.n_rows;
+  Bins B = es_bins(es_dims, es);
+  uint32_t* bs = bin_start + B.base + (size_t)r * (B.nb + 1);
+  if (n == 0) {
+    for (int q = lane; q <= B.nb; q += 32) bs[q] = start;
+    return;
+  }
+  if (n > kSortTileBig) {
+    if (lane == 0) big_list[atomicAdd(big_count, 1u)] = (uint32_t)seg;
+    return;
+  }
+  if (n > kWarpTile) {
+    if (lane == 0) mid_list[atomicAdd(mid_count, 1u)] = (uint32_t)seg;
+    return;
+  }
+  unsigned long long* keys = tiles[w];
+  int e = es / kNS, sc = es % kNS;
+  int side = e * 2 + (sc >= 18 ? 1 : 0);
+  int P = 1;
+  while (P < n) P <<= 1;
+  for (int j = lane; j < P; j += 32) {
+    unsigned long long k = ~0ull;
+    if (j < n) {
+      uint32_t i = perm[start + j];
+      int b = bin_z(zr, side, B.nz, zs_in[i]) * B.ny + bin_y(g, gd, r, B.ny, cl.y[i]);
+      k = ((unsigned long long)(uint32_t)b << 32) | i;
+    }
+    keys[j] = k;
+  }
+  __syncwarp();
+  for (int k = 2; k <= P; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = lane; i < P; i += 32) {
+        int ixj = i ^ j;
+        if (ixj > i) {
+          unsigned long long a = keys[i], b = keys[ixj];
+          bool up = (i & k) == 0;
+          if ((a > b) == up) {
+            keys[i] = b;
+            keys[ixj] = a;
+          }
+        }
+      }
+      __syncwarp();
+    }
+  }
+  for (int j = lane; j < n; j += 32) {
+    unsigned long long k = keys[j];
+    uint32_t i = (uint32_t)(k & 0xffffffffu);
+    int b = (int)(k >> 32);
+    int bprev = j > 0 ? (int)(keys[j - 1] >> 32) : -1;
+    for (int q = bprev + 1; q <= b; ++q) bs[q] = start + j;
+    if (j == n - 1)
+      for (int q = b + 1; q <= B.nb; ++q) bs[q] = start + n;
+    gyz[start + j] = make_float2(cl.y[i], zs_in[i]);
+    gorig[start + j] = i;
+    gseg[start + j] = (uint32_t)seg;
+  }
+}
+
+// Listed buckets, persistent blocks; 'tile' entries of shared memory.
+__global__ void k_row_sort_list(Geo g, ClIn cl, GridDims gd, int tile, const uint32_t* row_start,
+                                const uint2* es_dims, const uint32_t* perm, const float* zs_in,
+                                const float* zr, float2* gyz, uint32_t* gorig, uint32_t* gseg,
+                                uint32_t* bin_start, const uint32_t* list, const uint32_t* count,
+                                uint32_t* err) {
+  extern __shared__ unsigned long long keys[];
+  int nl = (int)*count;
+  for (int q = blockIdx.x; q < nl; q += gridDim.x) {
+    int seg = (int)list[q];
+    uint32_t start = row_start[seg];
+    int n = (int)(row_start[seg + 1] - start);
+    int r = seg % g.n_rows;
+    Bins B = es_bins(es_dims, seg / g.n_rows);
+    uint32_t* bs = bin_start + B.base + (size_t)r * (B.nb + 1);
+    if (n > tile) {
+      if (threadIdx.x == 0) atomicOr(err, kErrCapRow);
+      copy_bucket_unsorted(cl, B.nb, seg, start, n, perm, zs_in, gyz, gorig, gseg, bs);
+    } else {
+      sort_bucket(g, cl, gd, B, seg, start, n, perm, zs_in, zr, gyz, gorig, gseg, bs, keys);
+    }
+    __syncthreads();
   }
 }
 
@@ -238,13 +387,13 @@ struct Box {
   int iy0, iy1, iz0, iz1;
 };
 __device__ __forceinline__ Box make_box(const Geo& g, const GridDims& gd, const float* zr,
-                                        int r, int side, float ylo, float yhi, float zlo,
-                                        float zhi) {
+                                        const Bins& B, int r, int side, float ylo, float yhi,
+                                        float zlo, float zhi) {
   Box b;
-  b.iy0 = bin_y(g, gd, r, ylo);
-  b.iy1 = bin_y(g, gd, r, yhi);
-  b.iz0 = bin_z(gd, zr, side, zlo);
-  b.iz1 = bin_z(gd, zr, side, zhi);
+  b.iy0 = bin_y(g, gd, r, B.ny, ylo);
+  b.iy1 = bin_y(g, gd, r, B.ny, yhi);
+  b.iz0 = bin_z(zr, side, B.nz, zlo);
+  b.iz1 = bin_z(zr, side, B.nz, zhi);
   return b;
 }
 
@@ -252,7 +401,8 @@ __device__ __forceinline__ Box make_box(const Geo& g, const GridDims& gd, const 
 // For hit h in row r: the pair (u in row r+1, d in row r-1) inside the slope
 // windows whose d lies closest to the straight line through h and u; ties go
 // to the lowest pair of input indices.
-__global__ void k_neighbours(Geo g, Params p, GridDims gd, const uint32_t* nvalid,
+__global__ void k_neighbours(Geo g, Params p, GridDims gd, const uint2* es_dims,
+                             const uint32_t* nvalid,
                              const float2* __restrict__ gyz, const uint32_t* __restrict__ gorig,
                              const uint32_t* gseg, const uint32_t* bin_start, const float* zr,
                              int32_t* up, int32_t* dn) {
@@ -275,17 +425,18 @@ __global__ void k_neighbours(Geo g, Params p, GridDims gd, const uint32_t* nvali
     float wz_d = dxd * p.nb_teta + p.nb_wz;
     float f = dxd / dxu;
     const float eps = 1.0e-3f;
-    Box BU = make_box(g, gd, zr, r + 1, side, yh - wy_u - eps, yh + wy_u + eps, zh - wz_u - eps,
-                      zh + wz_u + eps);
-    Box BD = make_box(g, gd, zr, r - 1, side, yh - wy_d - eps, yh + wy_d + eps, zh - wz_d - eps,
-                      zh + wz_d + eps);
-    const uint32_t* bsu = bin_start + (size_t)(seg + 1) * (gd.nb + 1);
-    const uint32_t* bsd = bin_start + (size_t)(seg - 1) * (gd.nb + 1);
+    Bins BB = es_bins(es_dims, es);
+    Box BU = make_box(g, gd, zr, BB, r + 1, side, yh - wy_u - eps, yh + wy_u + eps,
+                      zh - wz_u - eps, zh + wz_u + eps);
+    Box BD = make_box(g, gd, zr, BB, r - 1, side, yh - wy_d - eps, yh + wy_d + eps,
+                      zh - wz_d - eps, zh + wz_d + eps);
+    const uint32_t* bsu = bin_start + BB.base + (size_t)(r + 1) * (BB.nb + 1);
+    const uint32_t* bsd = bin_start + BB.base + (size_t)(r - 1) * (BB.nb + 1);
     bool found = false;
     float best = 0.0f;
     uint32_t bou = 0, bod = 0;
     for (int iz = BU.iz0; iz <= BU.iz1; ++iz) {
-      uint32_t u0 = bsu[iz * gd.ny + BU.iy0], u1 = bsu[iz * gd.ny + BU.iy1 + 1];
+      uint32_t u0 = bsu[iz * BB.ny + BU.iy0], u1 = bsu[iz * BB.ny + BU.iy1 + 1];
       for (uint32_t u = u0; u < u1; ++u) {
         float2 uu = gyz[u];
         float yu = uu.x, zu = uu.y;
@@ -295,7 +446,7 @@ __global__ void k_neighbours(Geo g, Params p, GridDims gd, const uint32_t* nvali
         float pz = zh - (zu - zh) * f;
         uint32_t ou = gorig[u];
         for (int jz = BD.iz0; jz <= BD.iz1; ++jz) {
-          uint32_t d0 = bsd[jz * gd.ny + BD.iy0], d1 = bsd[jz * gd.ny + BD.iy1 + 1];
+          uint32_t d0 = bsd[jz * BB.ny + BD.iy0], d1 = bsd[jz * BB.ny + BD.iy1 + 1];
           for (uint32_t d = d0; d < d1; ++d) {
             float2 dd = gyz[d];
             float yd = dd.x, zd = dd.y;
@@ -414,29 +565,46 @@ __global__ void k_write_starts(const uint32_t* nvalid, const int32_t* upc, const
 // ------------------------------------------------------ a7: tracklets
 struct Grid {
   const float2* gyz;
-  const double* gt;
   const uint32_t* gorig;
   const uint32_t* bin_start;
   const float* zr;
 };
 
+// Calibrated position of a candidate during following (Sec. 4): the seeding z
+// shifted by the offset of the estimated collision time, then the space-point
+// correction at the shifted position.
+__device__ __forceinline__ void calibrate_follow(const Geo& g, const Cal& c, bool spl_on, int sec,
+                                                 int r, float y, float zs, float shift,
+                                                 float& yc, float& zc) {
+  float za = zs + shift;
+  if (spl_on) {
+    float d[2];
+    spline_eval(g, c, sec, g.row_x[r], y, fabsf(za), d);
+    yc = y + d[0];
+    zc = za + d[1];
+  } else {
+    yc = y;
+    zc = za;
+  }
+}
+
 // Nearest cluster of row r (calibrated frame) by the normalised distance,
 // inside the pick-up cut; ties to the lowest input index. Returns grid
 // position or -1, and the calibrated coordinates of the pick.
 __device__ int pick(const Geo& g, const Cal& c, const Params& p, const GridDims& gd,
-                    const Grid& G, int mode, int ev, int sec, int r, const float st[5],
+                    const Bins& BB, const Grid& G, int ev, int sec, int r, const float st[5],
                     const float C[15], double that, float shift, bool spl_on, float dymax,
                     float dzmax, float& ycb, float& zcb) {
-  int seg = (ev * kNS + sec) * g.n_rows + r;
   int side = ev * 2 + (sec >= 18 ? 1 : 0);
   float sig2 = p.sigma * p.sigma;
   float vy = C[0] + sig2, vz = C[2] + sig2;
+  float ivy = 1.0f / vy, ivz = 1.0f / vz;
   float wy = sqrtf(p.chi2_pick * vy), wz = sqrtf(p.chi2_pick * vz);
   float eps = 0.01f + 1.0e-6f * fabsf(shift);
   float yp = st[0], zp = st[1] - shift;
-  Box B = make_box(g, gd, G.zr, r, side, yp - wy - dymax - eps, yp + wy + dymax + eps,
+  Box B = make_box(g, gd, G.zr, BB, r, side, yp - wy - dymax - eps, yp + wy + dymax + eps,
                    zp - wz - dzmax - eps, zp + wz + dzmax + eps);
-  const uint32_t* __restrict__ bs = G.bin_start + (size_t)seg * (gd.nb + 1);
+  const uint32_t* __restrict__ bs = G.bin_start + BB.base + (size_t)r * (BB.nb + 1);
   int best = -1;
   float bd = 0.0f;
   for (int izb = B.iz0; izb <= B.iz1; izb += 4) {
@@ -446,19 +614,18 @@ __device__ int pick(const Geo& g, const Cal& c, const Params& p, const GridDims&
     for (int q = 0; q < 4; ++q) {
       int iz = izb + q;
       bool in = iz <= B.iz1;
-      lo[q] = in ? __ldg(bs + iz * gd.ny + B.iy0) : 0u;
-      hi[q] = in ? __ldg(bs + iz * gd.ny + B.iy1 + 1) : 0u;
+      lo[q] = in ? __ldg(bs + iz * BB.ny + B.iy0) : 0u;
+      hi[q] = in ? __ldg(bs + iz * BB.ny + B.iy1 + 1) : 0u;
     }
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       for (uint32_t j = lo[q]; j < hi[q]; ++j) {
         float2 yz = __ldg(G.gyz + j);
-        double tj = mode == 1 ? __ldg(G.gt + j) : 0.0;
         float yc, zc;
-        calibrate(g, c, spl_on, mode, sec, r, yz.x, yz.y, tj, that, yc, zc);
+        calibrate_follow(g, c, spl_on, sec, r, yz.x, yz.y, shift, yc, zc);
         float ry = yc - st[0];
         float rz = zc - st[1];
-        float d2 = (ry * ry) / vy + (rz * rz) / vz;
+        float d2 = (ry * ry) * ivy + (rz * rz) * ivz;
         if (!(d2 <= p.chi2_pick)) continue;
         bool take = best < 0 || d2 < bd;
         if (!take && d2 == bd) take = __ldg(G.gorig + j) < __ldg(G.gorig + best);
@@ -474,8 +641,19 @@ __device__ int pick(const Geo& g, const Cal& c, const Params& p, const GridDims&
   return best;
 }
 
+// One thread per start hit, written as a step machine: every iteration of the
+// loop transports the state to the next row and updates it with either the
+// next seed hit or the picked cluster, so that the threads of a warp execute
+// the same instructions whatever phase their tracklet is in.
+//   phase 0: seed fit in seeding coordinates (chain hits h0 .. hl)
+//   phase 1: seed fit in calibrated coordinates (after the collision time)
+//   phase 2: outward following from the seed end
+//   phase 3: inward following from the outermost pick down to row 0
+enum : int { kSeed1 = 0, kSeed2 = 1, kOut = 2, kIn = 3, kDone = 4 };
+
 __global__ void __launch_bounds__(128) k_tracklets(Geo g, Cal c, Params p, GridDims gd, Grid G,
-                                                  int mode, const int32_t* upc,
+                                                  const uint2* es_dims, int mode,
+                                                  const int32_t* upc,
                                                   const uint32_t* gseg, const uint32_t* starts,
                                                   const uint32_t* cnt, int32_t* nh_out,
                                                   int32_t* hits, double* that_out,
@@ -484,13 +662,12 @@ __global__ void __launch_bounds__(128) k_tracklets(Geo g, Cal c, Params p, GridD
   if (t >= (int)cnt[kCntStart]) return;
   int32_t* H = hits + (size_t)t * g.n_rows;
   for (int r = 0; r < g.n_rows; ++r) H[r] = -1;
-  nh_out[t] = -1;
-  that_out[t] = 0.0;
   int h0 = (int)starts[t];
   int seg0 = (int)gseg[h0];
   int r0 = seg0 % g.n_rows;
   int es = seg0 / g.n_rows;
   int ev = es / kNS, sec = es % kNS;
+  Bins BB = es_bins(es_dims, es);
   const float sig2 = p.sigma * p.sigma;
   bool spl_on = c.spl_bound[2] > 0.0f;
   float dymax = spl_on ? c.spl_bound[0] : 0.0f;
@@ -503,103 +680,122 @@ __global__ void __launch_bounds__(128) k_tracklets(Geo g, Cal c, Params p, GridD
     ++nseed;
   }
   float st[5], C[15], x;
-  // seed fit in seeding coordinates
   float2 yz0 = G.gyz[h0], yzl = G.gyz[hl];
   seed_two_points(st, C, x, p.c0t, g.row_x[r0], yz0.x, yz0.y, g.row_x[rl], yzl.x, yzl.y);
-  {
-    int h = h0, r = r0;
-    while (true) {
-      if (!propagate(g.kB, p.s_max, st, C, x, g.row_x[r])) return;
-      float2 yz = G.gyz[h];
-      apply_update(st, C, innovation(st, C, yz.x, yz.y, sig2, sig2));
-      if (h == hl) break;
-      h = upc[h];
-      ++r;
-    }
-  }
   double that = 0.0;
   float shift = 0.0f;
-  if (mode == 1) {
-    float zd = dca_z(g.kB, st, x);
-    double sg = sec < 18 ? 1.0 : -1.0;
-    that = c.tf_start - (sg * (double)zd) / c.vdrift;
-    shift = (float)(sg * c.vdrift * (that - c.tf_start));
-  }
-  // seed fit in calibrated coordinates
-  {
-    float y0, z0, y1, z1;
-    calibrate(g, c, spl_on, mode, sec, r0, yz0.x, yz0.y, mode == 1 ? G.gt[h0] : 0.0, that, y0,
-              z0);
-    calibrate(g, c, spl_on, mode, sec, rl, yzl.x, yzl.y, mode == 1 ? G.gt[hl] : 0.0, that, y1,
-              z1);
-    seed_two_points(st, C, x, p.c0t, g.row_x[r0], y0, z0, g.row_x[rl], y1, z1);
-    int h = h0, r = r0;
-    while (true) {
-      if (!propagate(g.kB, p.s_max, st, C, x, g.row_x[r])) return;
-      float yc, zc;
-      float2 yz = G.gyz[h];
-      calibrate(g, c, spl_on, mode, sec, r, yz.x, yz.y, mode == 1 ? G.gt[h] : 0.0, that, yc, zc);
-      apply_update(st, C, innovation(st, C, yc, zc, sig2, sig2));
-      if (h == hl) break;
-      h = upc[h];
-      ++r;
-    }
-  }
-  // outward following
   float bst[5], bC[15], bx = x;
+  int phase = kSeed1, h = h0, r = r0, rlast = rl, miss = 0, nh = 0;
+  bool failed = false;
+  while (phase != kDone) {
+    bool ok = propagate(g.kB, p.s_max, st, C, x, g.row_x[r]);
+    bool have = false;
+    float my = 0.0f, mz = 0.0f;
+    int j = -1;
+    if (ok) {
+      if (phase == kSeed1) {
+        float2 yz = G.gyz[h];
+        my = yz.x;
+        mz = yz.y;
+        have = true;
+      } else if (phase == kSeed2) {
+        float2 yz = G.gyz[h];
+        calibrate_follow(g, c, spl_on, sec, r, yz.x, yz.y, shift, my, mz);
+        have = true;
+      } else {
+        j = pick(g, c, p, gd, BB, G, ev, sec, r, st, C, that, shift, spl_on, dymax, dzmax, my, mz);
+        have = j >= 0;
+      }
+      if (have) apply_update(st, C, innovation(st, C, my, mz, sig2, sig2));
+    }
+    bool start_in = false;
+    if (phase == kSeed1 || phase == kSeed2) {
+      if (!ok) {
+        failed = true;
+        phase = kDone;
+      } else if (h != hl) {
+        h = upc[h];
+        ++r;
+      } else if (phase == kSeed1) {
+        if (mode == 1) {
+          float zd = dca_z(g.kB, st, x);
+          double sg = sec < 18 ? 1.0 : -1.0;
+          that = c.tf_start - (sg * (double)zd) / c.vdrift;
+          shift = (float)(sg * c.vdrift * (that - c.tf_start));
+        }
+        float y0, z0, y1, z1;
+        calibrate_follow(g, c, spl_on, sec, r0, yz0.x, yz0.y, shift, y0, z0);
+        calibrate_follow(g, c, spl_on, sec, rl, yzl.x, yzl.y, shift, y1, z1);
+        seed_two_points(st, C, x, p.c0t, g.row_x[r0], y0, z0, g.row_x[rl], y1, z1);
+        phase = kSeed2;
+        h = h0;
+        r = r0;
+      } else {
 #pragma unroll
-  for (int i = 0; i < 5; ++i) bst[i] = st[i];
+        for (int i = 0; i < 5; ++i) bst[i] = st[i];
 #pragma unroll
-  for (int i = 0; i < 15; ++i) bC[i] = C[i];
-  int rlast = rl;
-  int miss = 0;
-  for (int r = rl + 1; r < g.n_rows; ++r) {
-    if (!propagate(g.kB, p.s_max, st, C, x, g.row_x[r])) break;
-    float yc, zc;
-    int j = pick(g, c, p, gd, G, mode, ev, sec, r, st, C, that, shift, spl_on, dymax, dzmax, yc,
-                 zc);
-    if (j >= 0) {
-      apply_update(st, C, innovation(st, C, yc, zc, sig2, sig2));
+        for (int i = 0; i < 15; ++i) bC[i] = C[i];
+        bx = x;
+        rlast = rl;
+        miss = 0;
+        phase = kOut;
+        r = rl + 1;
+        if (r >= g.n_rows) start_in = true;
+      }
+    } else if (phase == kOut) {
+      if (!ok) {
+        start_in = true;
+      } else {
+        if (have) {
 #pragma unroll
-      for (int i = 0; i < 5; ++i) bst[i] = st[i];
+          for (int i = 0; i < 5; ++i) bst[i] = st[i];
 #pragma unroll
-      for (int i = 0; i < 15; ++i) bC[i] = C[i];
-      bx = x;
-      rlast = r;
+          for (int i = 0; i < 15; ++i) bC[i] = C[i];
+          bx = x;
+          rlast = r;
+          miss = 0;
+        } else if (++miss >= p.max_miss) {
+          start_in = true;
+        }
+        if (!start_in && ++r >= g.n_rows) start_in = true;
+      }
+    } else {  // kIn
+      if (!ok) {
+        phase = kDone;
+      } else {
+        if (have) {
+          H[r] = j;
+          ++nh;
+          miss = 0;
+        } else if (++miss >= p.max_miss) {
+          phase = kDone;
+        }
+        if (phase != kDone && --r < 0) phase = kDone;
+      }
+    }
+    if (start_in) {
+#pragma unroll
+      for (int i = 0; i < 5; ++i) st[i] = bst[i];
+#pragma unroll
+      for (int i = 0; i < 15; ++i) C[i] = bC[i] * p.inward_cov_scale;
+      x = bx;
+      r = rlast;
       miss = 0;
-    } else if (++miss >= p.max_miss) {
-      break;
+      phase = kIn;
     }
   }
-  // inward following through the seed
-#pragma unroll
-  for (int i = 0; i < 5; ++i) st[i] = bst[i];
-#pragma unroll
-  for (int i = 0; i < 15; ++i) C[i] = bC[i] * p.inward_cov_scale;
-  x = bx;
-  int nh = 0;
-  miss = 0;
-  for (int r = rlast; r >= 0; --r) {
-    if (!propagate(g.kB, p.s_max, st, C, x, g.row_x[r])) break;
-    float yc, zc;
-    int j = pick(g, c, p, gd, G, mode, ev, sec, r, st, C, that, shift, spl_on, dymax, dzmax, yc,
-                 zc);
-    if (j >= 0) {
-      apply_update(st, C, innovation(st, C, yc, zc, sig2, sig2));
-      H[r] = j;
-      ++nh;
-      miss = 0;
-    } else if (++miss >= p.max_miss) {
-      break;
-    }
+  if (failed) {
+    nh_out[t] = -1;
+    that_out[t] = 0.0;
+    return;
   }
   nh_out[t] = nh;
   that_out[t] = that;
   if (nh >= p.min_track_hits) {
     unsigned long long w = ((unsigned long long)(uint32_t)nh << 32) |
                            (unsigned long long)(0xffffffffu - G.gorig[h0]);
-    for (int r = 0; r < g.n_rows; ++r)
-      if (H[r] >= 0) atomicMax(&weight[H[r]], w);
+    for (int rr = 0; rr < g.n_rows; ++rr)
+      if (H[rr] >= 0) atomicMax(&weight[H[rr]], w);
   }
 }
 
@@ -779,17 +975,43 @@ inline int nblk(int64_t n, int b) { return (int)((n + b - 1) / b); }
 void launch_load(Prof* P, const Geo& g, const Cal& c, const ClIn& cl, const GridDims& gd, int K,
                  FindBuf& b, uint32_t* err, cudaStream_t s) {
   int init_n = K > cl.n_events * 2 ? K : cl.n_events * 2;
-  TPC_LAUNCH(P, "k_init_load", s, k_init_load<<<nblk(init_n, kB256), kB256, 0, s>>>(K, cl.n_events, b.cnt, b.fill, b.zmm));
+  TPC_LAUNCH(P, "k_init_load", s,
+             k_init_load<<<nblk(init_n, kB256), kB256, 0, s>>>(K, cl.n_events, b.cnt, b.fill,
+                                                               b.zmm));
   if (cl.n > 0)
     TPC_LAUNCH(P, "k_hist", s,
                k_hist<<<nblk(cl.n, kB256), kB256, 0, s>>>(g, c, cl, b.cnt, b.zs_in, b.zmm, err));
-  TPC_LAUNCH(P, "k_scan_rows", s, k_scan_rows<<<1, 1024, 0, s>>>(K, cl.n_events, gd, b.cnt, b.row_start, b.zmm, b.zr));
+  TPC_LAUNCH(P, "k_scan_rows", s,
+             k_scan_rows<<<1, 1024, 0, s>>>(g, K, cl.n_events, gd, b.cnt, b.row_start, b.zmm, b.zr,
+                                            b.es_dims, b.n_bins));
   if (cl.n > 0)
     TPC_LAUNCH(P, "k_scatter", s,
                k_scatter<<<nblk(cl.n, kB256), kB256, 0, s>>>(g, cl, b.row_start, b.fill, b.perm));
+  cudaMemsetAsync(b.list_counts, 0, 2 * sizeof(uint32_t), s);
+  TPC_LAUNCH(P, "k_row_sort_warp", s,
+             k_row_sort_warp<<<nblk(K, 8), 256, 0, s>>>(g, cl, gd, K, b.row_start, b.es_dims,
+                                                        b.perm, b.zs_in, b.zr, b.gyz, b.gorig,
+                                                        b.gseg, b.bin_start, b.mid_list,
+                                                        b.list_counts, b.big_list,
+                                                        b.list_counts + 1));
   size_t smem = kSortTile * sizeof(unsigned long long);
-  TPC_LAUNCH(P, "k_row_sort", s, k_row_sort<<<K, 512, smem, s>>>(g, cl, gd, b.row_start, b.perm, b.zs_in, b.zr, b.gyz,
-                                   b.gt, b.gorig, b.gseg, b.bin_start, err));
+  TPC_LAUNCH(P, "k_row_sort_mid", s,
+             k_row_sort_list<<<4 * 148, 512, smem, s>>>(g, cl, gd, kSortTile, b.row_start,
+                                                        b.es_dims, b.perm, b.zs_in, b.zr, b.gyz,
+                                                        b.gorig, b.gseg, b.bin_start, b.mid_list,
+                                                        b.list_counts, err));
+  size_t smem_big = kSortTileBig * sizeof(unsigned long long);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_row_sort_list, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem_big);
+    attr = true;
+  }
+  TPC_LAUNCH(P, "k_row_sort_big", s,
+             k_row_sort_list<<<148, 1024, smem_big, s>>>(g, cl, gd, kSortTileBig, b.row_start,
+                                                         b.es_dims, b.perm, b.zs_in, b.zr, b.gyz,
+                                                         b.gorig, b.gseg, b.bin_start,
+                                                         b.big_list, b.list_counts + 1, err));
 }
 
 void launch_find(Prof* P, const Geo& g, const Cal& c, const Params& p, const ClIn& cl,
@@ -799,7 +1021,7 @@ void launch_find(Prof* P, const Geo& g, const Cal& c, const Params& p, const ClI
   int nb = nblk(n, kB256);
   if (n > 0) {
     const uint32_t* nv = b.row_start + K;
-    TPC_LAUNCH(P, "k_neighbours", s, k_neighbours<<<nb, kB256, 0, s>>>(g, p, gd, nv, b.gyz, b.gorig, b.gseg, b.bin_start,
+    TPC_LAUNCH(P, "k_neighbours", s, k_neighbours<<<nb, kB256, 0, s>>>(g, p, gd, b.es_dims, nv, b.gyz, b.gorig, b.gseg, b.bin_start,
                                       b.zr, b.up, b.dn));
     TPC_LAUNCH(P, "k_clean", s, k_clean<<<nb, kB256, 0, s>>>(nv, b.up, b.dn, b.upc, b.dnc, b.blk_a));
   }
@@ -809,9 +1031,9 @@ void launch_find(Prof* P, const Geo& g, const Cal& c, const Params& p, const ClI
     TPC_LAUNCH(P, "k_write_starts", s, k_write_starts<<<nb, kB256, 0, s>>>(b.row_start + K, b.upc, b.dnc, b.off_a,
                                         (uint32_t)b.cap_tl, b.starts));
   cudaMemsetAsync(b.weight, 0, sizeof(unsigned long long) * (size_t)(n > 0 ? n : 1), s);
-  Grid G{b.gyz, b.gt, b.gorig, b.bin_start, b.zr};
+  Grid G{b.gyz, b.gorig, b.bin_start, b.zr};
   int ntl_blk = nblk(b.cap_tl, 128);
-  TPC_LAUNCH(P, "k_tracklets", s, k_tracklets<<<ntl_blk, 128, 0, s>>>(g, c, p, gd, G, cl.mode, b.upc, b.gseg, b.starts, cnt, b.nh,
+  TPC_LAUNCH(P, "k_tracklets", s, k_tracklets<<<ntl_blk, 128, 0, s>>>(g, c, p, gd, G, b.es_dims, cl.mode, b.upc, b.gseg, b.starts, cnt, b.nh,
                                       b.hits, b.that, b.weight));
   int nsel = nblk(b.cap_tl, kB256);
   TPC_LAUNCH(P, "k_select_count", s, k_select_count<<<nsel, kB256, 0, s>>>(g.n_rows, p, cnt, b.nh, b.hits, b.starts, b.gorig,

@@ -42,9 +42,13 @@ struct Params {
   int32_t seed_max_hits;
 };
 
-// Search-grid geometry of a batch: ny x nz bins per (event, sector, row).
+// Search-grid parameters of a batch. The bin geometry itself (ny x nz bins
+// per row, the same for all rows of an (event, sector)) is chosen on the
+// device from the sector's occupancy.
 struct GridDims {
-  int32_t ny, nz, nb;     // nb = ny * nz
+  float tau;              // target clusters per bin
+  int32_t nb_max;         // bins per row at most
+  int32_t ny_max;         // bins along y at most
   float y_margin;         // cm beyond the sector edge
   float z_margin;         // cm beyond the (event, side) z range
 };
@@ -75,10 +79,14 @@ struct FindBuf {
   uint32_t* perm;       // [n] input index in bucket order
   // grid order (bucket, bin, input index)
   float2* gyz;          // [n] (y, seed z)
-  double* gt;           // [n] drift time (mode 1)
   uint32_t* gorig;      // [n] input index
   uint32_t* gseg;       // [n] bucket (event*36 + sector)*n_rows + row
-  uint32_t* bin_start;  // [K * (nb + 1)]
+  uint32_t* bin_start;  // [cap_bins] per row: nb + 1 bin offsets
+  uint2* es_dims;       // [n_events * 36]: table base, ny | nz << 16
+  uint32_t* n_bins;     // [1] bin-table entries used
+  uint32_t* mid_list;   // [K] buckets for the 4096-entry block sort
+  uint32_t* big_list;   // [K] buckets for the 16384-entry block sort
+  uint32_t* list_counts;  // [2]
   // links (grid positions)
   int32_t* up;
   int32_t* dn;
@@ -112,13 +120,26 @@ struct TrackBuf {
   int64_t cap_tr, cap_asg;
 };
 
+// The refit runs one track per thread over tracks sorted by decreasing length;
+// per-cluster data and checkpoints are stored warp-interleaved: element k of
+// lane l of warp w at (wbase[w] + k) * 32 + l, so that each step of a warp is
+// one coalesced access.
 struct RefitBuf {
+  uint32_t* order;        // [cap_tr] thread slot -> track, decreasing length
+  uint32_t* slot;         // [cap_tr] track -> thread slot
+  uint32_t* wlen;         // [cap_warp] longest track of each warp
+  uint32_t* wbase;        // [cap_warp + 1] first interleaved row of each warp
+  uint32_t* len_hist;     // [1024] length histogram and fill counters
+  float* w_yc;            // [cap_w] interleaved calibrated y
+  float* w_zc;            // [cap_w]
+  uint32_t* w_meta;       // [cap_w]
   float* seed;            // [cap_tr * 5]
-  uint8_t* rej;           // [cap_asg]
+  uint8_t* rej;           // [cap_w] interleaved rejection pass
   int32_t* status;        // [cap_tr]
-  float* ckpt;            // [3 * cap_asg * 20]
-  float* gyc;             // [cap_asg] dL/d(calibrated y)
-  float* gzc;             // [cap_asg]
+  float* ckpt;            // [3 * cap_w * 20]
+  float* gyc;             // [cap_w] dL/d(calibrated y), interleaved
+  float* gzc;             // [cap_w]
+  int64_t cap_w;          // interleaved capacity: cap_asg + 32 * 257
   float* part_spline;     // [n_part_blocks * TPC_SPLINE_SIZE]
   double* part_cal;       // [n_part_blocks * 2]
   int64_t cap_ckpt;
@@ -187,7 +208,8 @@ struct Prof {
     if (P) (P)->end(S);             \
   } while (0)
 
-constexpr int kSortTile = 4096;   // max clusters per pad-row bucket
+constexpr int kSortTile = 4096;      // pad-row bucket tile of the common sort
+constexpr int kSortTileBig = 16384;  // tile of the large-bucket sort (128 KB)
 constexpr int kCalibGradBlocks = 148;
 
 // launchers (tpc_find.cu)

@@ -164,6 +164,19 @@ struct Jac {
   float ys, yq, zs, zt, zq, sq;  // non-identity entries
 };
 
+// 1/sqrt(1 - h^2): Maclaurin series for |h| < 1/8, else direct.
+TPC_HD float inv_cos_half(float h) {
+  if (fabsf(h) < 0.125f) {
+    float h2 = h * h;
+    float p = 35.0f / 128.0f;
+    p = 5.0f / 16.0f + h2 * p;
+    p = 3.0f / 8.0f + h2 * p;
+    p = 0.5f + h2 * p;
+    return 1.0f + h2 * p;
+  }
+  return 1.0f / sqrtf(1.0f - h * h);
+}
+
 // Exact helix transport to x2 in a uniform field with its analytic Jacobian.
 // Returns false when |sin(phi)| would reach s_max.
 TPC_HD bool transport(float kB, float s_max, float p[5], float& x, float x2, Jac& J) {
@@ -174,26 +187,29 @@ TPC_HD bool transport(float kB, float s_max, float p[5], float& x, float x2, Jac
   if (!(fabsf(s2) < s_max)) return false;
   float c1 = sqrtf(1.0f - s * s);
   float c2 = sqrtf(1.0f - s2 * s2);
+  float ic1 = 1.0f / c1;
+  float ic2 = 1.0f / c2;
   float N = s + s2;
   float D = c1 + c2;
-  float T = N / D;
+  float iD = 1.0f / D;
+  float T = N * iD;
   float dy = dx * T;
   float opt = 1.0f + T * T;
   float d = dx * sqrtf(opt);
   float h = (kap * d) * 0.5f;
   float A = arc_factor(h);
   float l = d * A;
-  float dDds = -(s / c1) - (s2 / c2);
+  float dDds = -(s * ic1) - (s2 * ic2);
   float kdx = kB * dx;
-  float dDdq = kdx * (s2 / c2);
-  float dTds = (2.0f - T * dDds) / D;
-  float dTdq = (-kdx - T * dDdq) / D;
+  float dDdq = kdx * (s2 * ic2);
+  float dTds = (2.0f - T * dDds) * iD;
+  float dTdq = (-kdx - T * dDdq) * iD;
   J.ys = dx * dTds;
   J.yq = dx * dTdq;
   float gg = (d * T) / opt;
   float dds = gg * dTds;
   float ddq = gg * dTdq;
-  float E = 1.0f / sqrtf(1.0f - h * h);
+  float E = inv_cos_half(h);
   float Bh = arc_factor_deriv(h);
   J.zs = t * (E * dds);
   J.zq = t * (E * ddq + (kB * ((d * d) * Bh)) * 0.5f);
@@ -251,9 +267,10 @@ TPC_HD Innov innovation(const float p[5], const float C[15], float my, float mz,
   float S01 = C[1];
   float S11 = C[2] + vz;
   float det = S00 * S11 - S01 * S01;
-  in.W00 = S11 / det;
-  in.W01 = -(S01 / det);
-  in.W11 = S00 / det;
+  float idet = 1.0f / det;
+  in.W00 = S11 * idet;
+  in.W01 = -(S01 * idet);
+  in.W11 = S00 * idet;
   in.chi2 = in.r0 * (in.W00 * in.r0 + in.W01 * in.r1) + in.r1 * (in.W01 * in.r0 + in.W11 * in.r1);
   return in;
 }

@@ -36,16 +36,142 @@ RefitCfg make_cfg(const Geo& g, const Params& p) {
   return c;
 }
 
-__global__ void __launch_bounds__(kB) k_refit(Geo g, RefitCfg p, const uint32_t* cnt, TrackIn in,
-                                               float* seed_out, uint8_t* rej, int32_t* status,
-                                               float* ckpt, int save, float* o_params,
-                                               float* o_cov, float* o_x, float* o_chi2,
-                                               int32_t* o_ndf, int32_t* o_status,
-                                               uint8_t* o_rej, uint32_t* err) {
+// Counting sort of the tracks by decreasing cluster count, so that the
+// threads of a warp run tracks of similar length.
+constexpr int kLenBins = 256;
+__global__ void k_len_init(uint32_t* hist) {
+  int i = threadIdx.x;
+  hist[i] = 0u;
+  hist[kLenBins + i] = 0u;
+}
+__device__ __forceinline__ int len_bin(const uint32_t* ts, int T) {
+  uint32_t n = ts[T + 1] - ts[T];
+  return kLenBins - 1 - (int)(n < (uint32_t)(kLenBins - 1) ? n : (uint32_t)(kLenBins - 1));
+}
+__global__ void k_len_hist(const uint32_t* cnt, const uint32_t* ts, uint32_t* hist) {
   int T = blockIdx.x * blockDim.x + threadIdx.x;
   if (T >= (int)cnt[kCntTracks]) return;
+  atomicAdd(&hist[len_bin(ts, T)], 1u);
+}
+__global__ void k_len_scan(uint32_t* hist) {
+  __shared__ uint32_t s[kLenBins];
+  int i = threadIdx.x;
+  s[i] = hist[i];
+  __syncthreads();
+  if (i == 0) {
+    uint32_t acc = 0;
+    for (int k = 0; k < kLenBins; ++k) {
+      uint32_t v = s[k];
+      s[k] = acc;
+      acc += v;
+    }
+  }
+  __syncthreads();
+  hist[i] = s[i];
+}
+__global__ void k_len_scatter(const uint32_t* cnt, const uint32_t* ts, uint32_t* hist,
+                              uint32_t* order, uint32_t* slot) {
+  int T = blockIdx.x * blockDim.x + threadIdx.x;
+  if (T >= (int)cnt[kCntTracks]) return;
+  int b = len_bin(ts, T);
+  uint32_t pos = hist[b] + atomicAdd(&hist[kLenBins + b], 1u);
+  order[pos] = (uint32_t)T;
+  slot[T] = pos;
+}
+
+// Longest track of each warp of thread slots.
+__global__ void k_warp_len(const uint32_t* cnt, const uint32_t* ts, const uint32_t* order,
+                           uint32_t* wlen) {
+  int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  int nt = (int)cnt[kCntTracks];
+  uint32_t n = 0;
+  if (tid < nt) {
+    int T = (int)order[tid];
+    n = ts[T + 1] - ts[T];
+  }
+  uint32_t m = __reduce_max_sync(0xffffffffu, n);
+  if ((threadIdx.x & 31) == 0 && tid < nt) wlen[tid >> 5] = m;
+}
+
+// Single block: exclusive scan of the warp lengths.
+__global__ void k_warp_scan(const uint32_t* cnt, const uint32_t* wlen, uint32_t* wbase) {
+  __shared__ uint32_t carry;
+  __shared__ uint32_t ws[32];
+  int nw = ((int)cnt[kCntTracks] + 31) / 32;
+  if (threadIdx.x == 0) carry = 0u;
+  __syncthreads();
+  for (int b0 = 0; b0 < nw; b0 += blockDim.x) {
+    int i = b0 + threadIdx.x;
+    uint32_t v = i < nw ? wlen[i] : 0u;
+    uint32_t x = v;
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) ws[w] = x;
+    __syncthreads();
+    if (w == 0) {
+      uint32_t s = lane < (int)(blockDim.x >> 5) ? ws[lane] : 0u;
+      for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, s, o);
+        if (lane >= o) s += y;
+      }
+      ws[lane] = s;
+    }
+    __syncthreads();
+    uint32_t excl = (w > 0 ? ws[w - 1] : 0u) + x - v;
+    if (i < nw) wbase[i] = carry + excl;
+    __syncthreads();
+    if (threadIdx.x == 0) carry += ws[(blockDim.x >> 5) - 1];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) wbase[nw] = carry;
+}
+
+__device__ __forceinline__ Lay warp_layout(const uint32_t* wbase, const uint32_t* wlen, int tid) {
+  int w = tid >> 5, lane = tid & 31;
+  Lay l;
+  l.base = (size_t)wbase[w] * 32 + lane;
+  l.stride = 32;
+  l.L = (int)wlen[w];
+  l.ck_base = (size_t)3 * wbase[w] * 32 * kCk + lane;
+  l.ck_step = 32 * kCk;
+  l.ck_comp = 32;
+  return l;
+}
+
+// Copy each track's calibrated clusters into the warp-interleaved layout.
+__global__ void k_interleave(const uint32_t* cnt, TrackIn in, const uint32_t* order,
+                             const uint32_t* wbase, const uint32_t* wlen, float* w_yc,
+                             float* w_zc, uint32_t* w_meta) {
+  int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid >= (int)cnt[kCntTracks]) return;
+  int T = (int)order[tid];
   uint32_t a = in.track_start[T];
   uint32_t b = in.track_start[T + 1];
+  if (b < a || b > cnt[kCntAssigned]) return;
+  Lay ly = warp_layout(wbase, wlen, tid);
+  for (int k = 0; k < (int)(b - a); ++k) {
+    w_yc[ly.at(k)] = in.yc[a + k];
+    w_zc[ly.at(k)] = in.zc[a + k];
+    w_meta[ly.at(k)] = in.meta[a + k];
+  }
+}
+
+__global__ void __launch_bounds__(kB) k_refit(Geo g, RefitCfg p, const uint32_t* cnt,
+                                               const uint32_t* order, const uint32_t* wbase,
+                                               const uint32_t* wlen, const uint32_t* track_start,
+                                               TrackIn win, float* seed_out, uint8_t* rej,
+                                               int32_t* status, float* ckpt, int save,
+                                               float* o_params, float* o_cov, float* o_x,
+                                               float* o_chi2, int32_t* o_ndf, int32_t* o_status,
+                                               uint8_t* o_rej, uint32_t* err) {
+  int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid >= (int)cnt[kCntTracks]) return;
+  int T = (int)order[tid];
+  uint32_t a = track_start[T];
+  uint32_t b = track_start[T + 1];
   if (b < a || b > cnt[kCntAssigned]) {  // invalid CSR: leave the track alone
     status[T] = 3;
     if (o_status) o_status[T] = 3;
@@ -53,7 +179,8 @@ __global__ void __launch_bounds__(kB) k_refit(Geo g, RefitCfg p, const uint32_t*
     return;
   }
   int n = (int)(b - a);
-  RefitOut o = refit_track(g, p, in, a, n, rej, seed_out + (size_t)T * 5, save ? ckpt : nullptr);
+  Lay ly = warp_layout(wbase, wlen, tid);
+  RefitOut o = refit_track(g, p, win, ly, n, rej, seed_out + (size_t)T * 5, save ? ckpt : nullptr);
   if (o.status == 0 && !(fabsf(o.chi2) < 1.0e30f && fabsf(o.st[4]) < 1.0e30f))
     atomicOr(err, kErrNumeric);
   if (o.status != 0) {
@@ -72,27 +199,30 @@ __global__ void __launch_bounds__(kB) k_refit(Geo g, RefitCfg p, const uint32_t*
   if (o_chi2) o_chi2[T] = o.chi2;
   if (o_ndf) o_ndf[T] = o.ndf;
   if (o_rej)
-    for (int k = 0; k < n; ++k) o_rej[a + k] = rej[a + k];
+    for (int k = 0; k < n; ++k) o_rej[a + k] = rej[ly.at(k)];
 }
 
 __global__ void __launch_bounds__(kB) k_refit_bwd(Geo g, RefitCfg p, const uint32_t* cnt,
-                                                   TrackIn in, const uint8_t* rej,
-                                                   const int32_t* status, const float* ckpt,
-                                                   const float* dl_dchi2, float* gyc,
-                                                   float* gzc) {
-  int T = blockIdx.x * blockDim.x + threadIdx.x;
-  if (T >= (int)cnt[kCntTracks]) return;
-  uint32_t a = in.track_start[T];
-  int n = (int)(in.track_start[T + 1] - a);
+                                                   const uint32_t* order, const uint32_t* wbase,
+                                                   const uint32_t* wlen,
+                                                   const uint32_t* track_start, TrackIn win,
+                                                   const uint8_t* rej, const int32_t* status,
+                                                   const float* ckpt, const float* dl_dchi2,
+                                                   float* gyc, float* gzc) {
+  int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid >= (int)cnt[kCntTracks]) return;
+  int T = (int)order[tid];
+  if (status[T] == 3) return;
+  int n = (int)(track_start[T + 1] - track_start[T]);
+  Lay ly = warp_layout(wbase, wlen, tid);
   if (status[T] != 0) {
-    if (status[T] == 3) return;
     for (int k = 0; k < n; ++k) {
-      gyc[a + k] = 0.0f;
-      gzc[a + k] = 0.0f;
+      gyc[ly.at(k)] = 0.0f;
+      gzc[ly.at(k)] = 0.0f;
     }
     return;
   }
-  refit_backward_track(g, p, in, a, n, rej, ckpt, dl_dchi2[T], gyc, gzc);
+  refit_backward_track(g, p, win, ly, n, rej, ckpt, dl_dchi2[T], gyc, gzc);
 }
 
 // Chain rule through the calibration transform (Sec. 4): calibrated (y, z)
@@ -100,6 +230,8 @@ __global__ void __launch_bounds__(kB) k_refit_bwd(Geo g, RefitCfg p, const uint3
 __global__ void __launch_bounds__(512) k_calib_grad(Geo g, Cal c, ClIn cl, const uint32_t* cnt,
                                                      const uint32_t* cluster_idx,
                                                      const uint32_t* asg_track,
+                                                     const uint32_t* track_start,
+                                                     const uint32_t* slot, const uint32_t* wbase,
                                                      const double* t_coll, const float* gyc,
                                                      const float* gzc, float* grad_y,
                                                      float* grad_zt, float* part_spline,
@@ -126,13 +258,16 @@ __global__ void __launch_bounds__(512) k_calib_grad(Geo g, Cal c, ClIn cl, const
     if (jj >= len) continue;
     int j = j0 + jj;
     uint32_t i = cluster_idx[j];
-    double that = t_coll[asg_track[j]];
+    uint32_t T = asg_track[j];
+    double that = t_coll[T];
+    uint32_t sl = slot[T];
+    size_t wpos = ((size_t)wbase[sl >> 5] + (j - track_start[T])) * 32 + (sl & 31);
     int r = cl.row[i], s = cl.sector[i];
     float x = g.row_x[r];
     float y = cl.y[i];
     float za = abs_z(g, c, cl.mode, cl.mode == 0 ? cl.z[i] : 0.0f, cl.mode == 1 ? cl.t[i] : 0.0,
                      s, that);
-    float by = gyc[j], bz = gzc[j];
+    float by = gyc[wpos], bz = gzc[wpos];
     float gy = by, gza = bz;
     if (spl_on) {
       float ur = (x - c.spl_x0) / c.spl_dx;
@@ -237,30 +372,52 @@ void launch_refit(Prof* P, const Geo& g, const Params& p, int64_t cap_tr, const 
                   uint32_t* err, cudaStream_t s) {
   if (cap_tr <= 0) return;
   TrackIn in{tb.track_start, tb.yc, tb.zc, tb.meta};
-  TPC_LAUNCH(P, "k_refit", s, k_refit<<<nblk(cap_tr, kB), kB, 0, s>>>(g, make_cfg(g, p), cnt, in, rb.seed, rb.rej, rb.status, rb.ckpt,
-                                          save ? 1 : 0, params, cov, x, chi2, ndf, status, rej,
-                                          err));
+  TrackIn win{tb.track_start, rb.w_yc, rb.w_zc, rb.w_meta};
+  int nb = nblk(cap_tr, 256);
+  TPC_LAUNCH(P, "k_len_init", s, k_len_init<<<1, kLenBins, 0, s>>>(rb.len_hist));
+  TPC_LAUNCH(P, "k_len_hist", s, k_len_hist<<<nb, 256, 0, s>>>(cnt, tb.track_start, rb.len_hist));
+  TPC_LAUNCH(P, "k_len_scan", s, k_len_scan<<<1, kLenBins, 0, s>>>(rb.len_hist));
+  TPC_LAUNCH(P, "k_len_scatter", s,
+             k_len_scatter<<<nb, 256, 0, s>>>(cnt, tb.track_start, rb.len_hist, rb.order,
+                                               rb.slot));
+  TPC_LAUNCH(P, "k_warp_len", s,
+             k_warp_len<<<nb, 256, 0, s>>>(cnt, tb.track_start, rb.order, rb.wlen));
+  TPC_LAUNCH(P, "k_warp_scan", s, k_warp_scan<<<1, 1024, 0, s>>>(cnt, rb.wlen, rb.wbase));
+  TPC_LAUNCH(P, "k_interleave", s,
+             k_interleave<<<nb, 256, 0, s>>>(cnt, in, rb.order, rb.wbase, rb.wlen, rb.w_yc,
+                                              rb.w_zc, rb.w_meta));
+  TPC_LAUNCH(P, "k_refit", s,
+             k_refit<<<nblk(cap_tr, kB), kB, 0, s>>>(g, make_cfg(g, p), cnt, rb.order, rb.wbase,
+                                                     rb.wlen, tb.track_start, win, rb.seed,
+                                                     rb.rej, rb.status, rb.ckpt, save ? 1 : 0,
+                                                     params, cov, x, chi2, ndf, status, rej,
+                                                     err));
 }
 
 void launch_refit_backward(Prof* P, const Geo& g, const Cal& c, const Params& p, const ClIn& cl,
                            int64_t cap_tr, int64_t cap_asg, const uint32_t* cnt,
                            const TrackBuf& tb, RefitBuf& rb, const float* dl_dchi2,
                            float* grad_y, float* grad_zt, double* grad_calib, cudaStream_t s) {
-  TrackIn in{tb.track_start, tb.yc, tb.zc, tb.meta};
+  TrackIn win{tb.track_start, rb.w_yc, rb.w_zc, rb.w_meta};
   if (cap_tr > 0)
-    TPC_LAUNCH(P, "k_refit_bwd", s, k_refit_bwd<<<nblk(cap_tr, kB), kB, 0, s>>>(g, make_cfg(g, p), cnt, in, rb.rej, rb.status, rb.ckpt,
-                                                 dl_dchi2, rb.gyc, rb.gzc));
+    TPC_LAUNCH(P, "k_refit_bwd", s,
+               k_refit_bwd<<<nblk(cap_tr, kB), kB, 0, s>>>(g, make_cfg(g, p), cnt, rb.order,
+                                                           rb.wbase, rb.wlen, tb.track_start,
+                                                           win, rb.rej, rb.status, rb.ckpt,
+                                                           dl_dchi2, rb.gyc, rb.gzc));
   size_t smem = TPC_SPLINE_SIZE * sizeof(float);
   static bool attr_set = false;
   if (!attr_set) {
     cudaFuncSetAttribute(k_calib_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     attr_set = true;
   }
-  TPC_LAUNCH(P, "k_calib_grad", s, k_calib_grad<<<kCalibGradBlocks, 512, smem, s>>>(g, c, cl, cnt, tb.cluster_idx, tb.asg_track,
-                                                   tb.t_coll, rb.gyc, rb.gzc, grad_y, grad_zt,
-                                                   rb.part_spline, rb.part_cal));
-  TPC_LAUNCH(P, "k_calib_reduce", s, k_calib_reduce<<<nblk(TPC_GRAD_CALIB_SIZE, 256), 256, 0, s>>>(kCalibGradBlocks, rb.part_spline,
-                                                               rb.part_cal, grad_calib));
+  TPC_LAUNCH(P, "k_calib_grad", s,
+             k_calib_grad<<<kCalibGradBlocks, 512, smem, s>>>(
+                 g, c, cl, cnt, tb.cluster_idx, tb.asg_track, tb.track_start, rb.slot, rb.wbase,
+                 tb.t_coll, rb.gyc, rb.gzc, grad_y, grad_zt, rb.part_spline, rb.part_cal));
+  TPC_LAUNCH(P, "k_calib_reduce", s,
+             k_calib_reduce<<<nblk(TPC_GRAD_CALIB_SIZE, 256), 256, 0, s>>>(
+                 kCalibGradBlocks, rb.part_spline, rb.part_cal, grad_calib));
 }
 
 }  // namespace tpc

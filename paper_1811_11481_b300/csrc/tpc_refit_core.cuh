@@ -16,6 +16,33 @@ struct TrackIn {
   const uint32_t* meta;  // row | flags << 8 | sector << 16
 };
 
+// Where one track's per-cluster data and checkpoints live: element i at
+// base + i * stride; checkpoint (pass, k, component c) at
+// ck_base + ((pass - 1) * L + k) * ck_step + c * ck_comp. The contiguous
+// layout has stride 1; the warp-interleaved layout has stride 32.
+struct Lay {
+  size_t base;
+  int stride;
+  size_t ck_base;
+  int L;
+  int ck_step;
+  int ck_comp;
+  TPC_HD size_t at(int i) const { return base + (size_t)i * stride; }
+  TPC_HD size_t ck(int pass, int k, int c) const {
+    return ck_base + ((size_t)(pass - 1) * L + k) * ck_step + (size_t)c * ck_comp;
+  }
+};
+TPC_HD Lay contiguous_layout(uint32_t a, int n) {
+  Lay l;
+  l.base = a;
+  l.stride = 1;
+  l.ck_base = (size_t)3 * a * kCk;
+  l.L = n;
+  l.ck_step = kCk;
+  l.ck_comp = 1;
+  return l;
+}
+
 struct RefitCfg {
   float kB, s_max, sigma, shared_scale, chi2_out, refit_inflate;
   int32_t min_acc_reject;
@@ -29,12 +56,12 @@ TPC_HD float cl_var(const RefitCfg& p, uint32_t meta) {
 
 // Seed at the outermost cluster from the circle through the innermost,
 // middle and outermost clusters.
-TPC_HD bool seed3(const Geo& g, const TrackIn& in, uint32_t a, int n, float st[5]) {
+TPC_HD bool seed3(const Geo& g, const TrackIn& in, const Lay& ly, int n, float st[5]) {
   if (n < 3) return false;
   int i0 = 0, im = n / 2, i2 = n - 1;
-  float x0 = g.row_x[in.meta[a + i0] & 0xffu], xm = g.row_x[in.meta[a + im] & 0xffu],
-        x2 = g.row_x[in.meta[a + i2] & 0xffu];
-  float y0 = in.yc[a + i0], ym = in.yc[a + im], y2 = in.yc[a + i2];
+  float x0 = g.row_x[in.meta[ly.at(i0)] & 0xffu], xm = g.row_x[in.meta[ly.at(im)] & 0xffu],
+        x2 = g.row_x[in.meta[ly.at(i2)] & 0xffu];
+  float y0 = in.yc[ly.at(i0)], ym = in.yc[ly.at(im)], y2 = in.yc[ly.at(i2)];
   float ax = xm - x0, ay = ym - y0, bx = x2 - x0, by = y2 - y0, ex = x2 - xm, ey = y2 - ym;
   float cross = ax * by - ay * bx;
   float la = sqrtf(ax * ax + ay * ay), lb = sqrtf(bx * bx + by * by),
@@ -45,9 +72,9 @@ TPC_HD bool seed3(const Geo& g, const TrackIn& in, uint32_t a, int n, float st[5
   float s2 = (by / lb) * sqrtf(1.0f - hs * hs) - (bx / lb) * hs;
   float arc = lb * arc_factor(hs);
   st[0] = y2;
-  st[1] = in.zc[a + i2];
+  st[1] = in.zc[ly.at(i2)];
   st[2] = s2;
-  st[3] = (in.zc[a + i2] - in.zc[a + i0]) / arc;
+  st[3] = (in.zc[ly.at(i2)] - in.zc[ly.at(i0)]) / arc;
   st[4] = kap / g.kB;
   return true;
 }
@@ -61,19 +88,18 @@ struct RefitOut {
   int32_t status;  // 0 ok, 1 propagation failed, 2 no seed
 };
 
-// Three passes (inward, outward, inward); rej[k] receives the pass that
-// rejected cluster k (0 = kept). ckpt (may be null): state before each step
-// at [(3 a + (pass - 1) n + k) * kCk].
-TPC_HD RefitOut refit_track(const Geo& g, const RefitCfg& p, const TrackIn& in, uint32_t a, int n,
-                            uint8_t* rej, float* seed_out, float* ckpt) {
+// Three passes (inward, outward, inward); rej[at(k)] receives the pass that
+// rejected cluster k (0 = kept). ckpt (may be null): state before each step.
+TPC_HD RefitOut refit_track(const Geo& g, const RefitCfg& p, const TrackIn& in, const Lay& ly,
+                            int n, uint8_t* rej, float* seed_out, float* ckpt) {
   RefitOut o;
-  for (int k = 0; k < n; ++k) rej[a + k] = 0;
+  for (int k = 0; k < n; ++k) rej[ly.at(k)] = 0;
   o.status = 0;
   o.chi2 = 0.0f;
   o.ndf = 0;
   float* st = o.st;
   float* C = o.C;
-  if (!seed3(g, in, a, n, st)) {
+  if (!seed3(g, in, ly, n, st)) {
     o.status = 2;
     for (int i = 0; i < 5; ++i) st[i] = 0.0f;
     for (int i = 0; i < 15; ++i) C[i] = 0.0f;
@@ -82,7 +108,7 @@ TPC_HD RefitOut refit_track(const Geo& g, const RefitCfg& p, const TrackIn& in, 
   }
   if (seed_out)
     for (int i = 0; i < 5; ++i) seed_out[i] = st[i];
-  float x = g.row_x[in.meta[a + n - 1] & 0xffu];
+  float x = g.row_x[in.meta[ly.at(n - 1)] & 0xffu];
   set_diag(C, p.c0r);
   float chi2 = 0.0f;
   int ndf = 0;
@@ -92,31 +118,44 @@ TPC_HD RefitOut refit_track(const Geo& g, const RefitCfg& p, const TrackIn& in, 
     chi2 = 0.0f;
     ndf = 0;
     int nacc = 0;
+    // data of the current step; the next step's is loaded before the
+    // current step's arithmetic so that the loads overlap it
+    int i = pass == 2 ? 0 : n - 1;
+    int rj = rej[ly.at(i)];
+    uint32_t m = in.meta[ly.at(i)];
+    float my = in.yc[ly.at(i)], mz = in.zc[ly.at(i)];
     for (int k = 0; k < n; ++k) {
-      int i = pass == 2 ? k : n - 1 - k;
-      int rj = rej[a + i];
-      if (rj != 0 && rj < pass) continue;
-      if (ckpt) {
-        float* ck = ckpt + ((size_t)3 * a + (size_t)(pass - 1) * n + k) * kCk;
-        for (int j = 0; j < 5; ++j) ck[j] = st[j];
-        for (int j = 0; j < 15; ++j) ck[5 + j] = C[j];
+      int k1 = k + 1 < n ? k + 1 : k;
+      int i1 = pass == 2 ? k1 : n - 1 - k1;
+      int rj1 = rej[ly.at(i1)];
+      uint32_t m1 = in.meta[ly.at(i1)];
+      float my1 = in.yc[ly.at(i1)], mz1 = in.zc[ly.at(i1)];
+      if (!(rj != 0 && rj < pass)) {
+        if (ckpt) {
+          for (int j = 0; j < 5; ++j) ckpt[ly.ck(pass, k, j)] = st[j];
+          for (int j = 0; j < 15; ++j) ckpt[ly.ck(pass, k, 5 + j)] = C[j];
+        }
+        if (!propagate(p.kB, p.s_max, st, C, x, g.row_x[m & 0xffu])) {
+          o.status = 1;
+          o.x = x;
+          return o;
+        }
+        float v = cl_var(p, m);
+        Innov iv = innovation(st, C, my, mz, v, v);
+        if (nacc >= p.min_acc_reject && iv.chi2 > p.chi2_out) {
+          rej[ly.at(i)] = (uint8_t)pass;
+        } else {
+          apply_update(st, C, iv);
+          chi2 = chi2 + iv.chi2;
+          ndf += 2;
+          ++nacc;
+        }
       }
-      uint32_t m = in.meta[a + i];
-      if (!propagate(p.kB, p.s_max, st, C, x, g.row_x[m & 0xffu])) {
-        o.status = 1;
-        o.x = x;
-        return o;
-      }
-      float v = cl_var(p, m);
-      Innov iv = innovation(st, C, in.yc[a + i], in.zc[a + i], v, v);
-      if (nacc >= p.min_acc_reject && iv.chi2 > p.chi2_out) {
-        rej[a + i] = (uint8_t)pass;
-        continue;
-      }
-      apply_update(st, C, iv);
-      chi2 = chi2 + iv.chi2;
-      ndf += 2;
-      ++nacc;
+      i = i1;
+      rj = rj1;
+      m = m1;
+      my = my1;
+      mz = mz1;
     }
   }
   o.x = x;
@@ -338,15 +377,15 @@ TPC_HD void transport_adjoint(float kB, float dx, const float p[5], const float 
 TPC_HD bool step_active(int rj, int pass) { return !(rj != 0 && rj < pass); }
 
 // Reverse sweep of one saved refit: writes the adjoints of the calibrated
-// coordinates gyc[a + k], gzc[a + k] of L = gT * chi2(pass 3).
-TPC_HD void refit_backward_track(const Geo& g, const RefitCfg& p, const TrackIn& in, uint32_t a,
+// coordinates gyc[at(k)], gzc[at(k)] of L = gT * chi2(pass 3).
+TPC_HD void refit_backward_track(const Geo& g, const RefitCfg& p, const TrackIn& in, const Lay& ly,
                                  int n, const uint8_t* rej, const float* ckpt, float gT,
                                  float* gyc, float* gzc) {
   for (int k = 0; k < n; ++k) {
-    gyc[a + k] = 0.0f;
-    gzc[a + k] = 0.0f;
+    gyc[ly.at(k)] = 0.0f;
+    gzc[ly.at(k)] = 0.0f;
   }
-  auto xof = [&](int i) { return g.row_x[in.meta[a + i] & 0xffu]; };
+  auto xof = [&](int i) { return g.row_x[in.meta[ly.at(i)] & 0xffu]; };
   auto idx_of = [&](int pass, int k) { return pass == 2 ? k : n - 1 - k; };
   float xend[4];
   xend[0] = xof(n - 1);
@@ -354,7 +393,7 @@ TPC_HD void refit_backward_track(const Geo& g, const RefitCfg& p, const TrackIn&
     xend[pass] = xend[pass - 1];
     for (int k = n - 1; k >= 0; --k) {
       int i = idx_of(pass, k);
-      if (step_active(rej[a + i], pass)) {
+      if (step_active(rej[ly.at(i)], pass)) {
         xend[pass] = xof(i);
         break;
       }
@@ -365,40 +404,67 @@ TPC_HD void refit_backward_track(const Geo& g, const RefitCfg& p, const TrackIn&
   for (int i = 0; i < 15; ++i) G[i] = 0.0f;
   for (int pass = 3; pass >= 1; --pass) {
     float cbar = pass == 3 ? gT : 0.0f;
-    for (int k = n - 1; k >= 0; --k) {
-      int i = idx_of(pass, k);
-      int rj = rej[a + i];
-      if (!step_active(rj, pass)) continue;
-      float xprev = xend[pass - 1];
-      for (int kk = k - 1; kk >= 0; --kk) {
-        int ii = idx_of(pass, kk);
-        if (step_active(rej[a + ii], pass)) {
-          xprev = xof(ii);
-          break;
-        }
+    // previous active step (in processing order) at or before k, or -1
+    auto prev_active = [&](int k) {
+      for (; k >= 0; --k)
+        if (step_active(rej[ly.at(idx_of(pass, k))], pass)) return k;
+      return -1;
+    };
+    int kc = prev_active(n - 1);
+    if (kc < 0) continue;
+    // record of the current step: checkpoint, cluster data
+    float p0[5], C0[15];
+    int ic = idx_of(pass, kc);
+    for (int j = 0; j < 5; ++j) p0[j] = ckpt[ly.ck(pass, kc, j)];
+    for (int j = 0; j < 15; ++j) C0[j] = ckpt[ly.ck(pass, kc, 5 + j)];
+    uint32_t mc = in.meta[ly.at(ic)];
+    float myc = in.yc[ly.at(ic)], mzc = in.zc[ly.at(ic)];
+    int rjc = rej[ly.at(ic)];
+    while (kc >= 0) {
+      // prefetch the previous active step
+      int kp = prev_active(kc - 1);
+      float p1[5], C1[15];
+      uint32_t mp = 0;
+      float myp = 0.f, mzp = 0.f;
+      int rjp = 0;
+      if (kp >= 0) {
+        int ip = idx_of(pass, kp);
+        for (int j = 0; j < 5; ++j) p1[j] = ckpt[ly.ck(pass, kp, j)];
+        for (int j = 0; j < 15; ++j) C1[j] = ckpt[ly.ck(pass, kp, 5 + j)];
+        mp = in.meta[ly.at(ip)];
+        myp = in.yc[ly.at(ip)];
+        mzp = in.zc[ly.at(ip)];
+        rjp = rej[ly.at(ip)];
       }
-      const float* ck = ckpt + ((size_t)3 * a + (size_t)(pass - 1) * n + k) * kCk;
-      float p0[5], C0[15];
-      for (int j = 0; j < 5; ++j) p0[j] = ck[j];
-      for (int j = 0; j < 15; ++j) C0[j] = ck[5 + j];
+      float xprev = kp >= 0 ? g.row_x[mp & 0xffu] : xend[pass - 1];
+      float xi = g.row_x[mc & 0xffu];
       float pp[5];
       for (int j = 0; j < 5; ++j) pp[j] = p0[j];
       float xx = xprev;
-      float xi = xof(i);
       Jac J;
       transport(p.kB, 2.0f, pp, xx, xi, J);
       float Cp[15];
       for (int j = 0; j < 15; ++j) Cp[j] = C0[j];
       transport_cov(J, Cp);
-      if (rj != pass) {
-        float v = cl_var(p, in.meta[a + i]);
-        Innov iv = innovation(pp, Cp, in.yc[a + i], in.zc[a + i], v, v);
+      if (rjc != pass) {
+        float v = cl_var(p, mc);
+        Innov iv = innovation(pp, Cp, myc, mzc, v, v);
         float mb[2];
         update_adjoint(Cp, iv, cbar, pb, G, mb);
-        gyc[a + i] += mb[0];
-        gzc[a + i] += mb[1];
+        gyc[ly.at(ic)] += mb[0];
+        gzc[ly.at(ic)] += mb[1];
       }
       transport_adjoint(p.kB, xi - xprev, p0, C0, J, pb, G);
+      kc = kp;
+      if (kp >= 0) {
+        ic = idx_of(pass, kp);
+        for (int j = 0; j < 5; ++j) p0[j] = p1[j];
+        for (int j = 0; j < 15; ++j) C0[j] = C1[j];
+        mc = mp;
+        myc = myp;
+        mzc = mzp;
+        rjc = rjp;
+      }
     }
     if (pass > 1)
       for (int j = 0; j < 15; ++j) G[j] = G[j] * p.refit_inflate;
