@@ -233,6 +233,35 @@ tpc_status tpc_get_tracklets(tpc_ctx* ctx, int64_t n_cap, uint32_t* start_hit, i
 tpc_status tpc_get_calibrated(tpc_ctx* ctx, float* yc, float* zc);
 tpc_status tpc_get_grid(tpc_ctx* ctx, uint32_t* order, uint32_t* row_start);
 
+/* Refit without any device allocation. The paper has no counterpart: this
+ * is for callers that cannot allocate device memory when they need a refit --
+ * code running while a stream is captured into a CUDA graph (an allocation is
+ * not a stream operation), real-time loops that must not take the device-wide
+ * synchronisation an allocation can cause, or plug-ins whose host framework's
+ * caching allocator owns the device memory.
+ * Same three-pass refit as tpc_refit, for tracks given as CSR over assigned
+ * clusters with their calibrated coordinates already computed (device):
+ *   track_start [n_tracks + 1], yc, zc [n_assigned] (cm), row, flags
+ *   [n_assigned] (flags may be NULL); outputs (device, any may be NULL):
+ *   params [n_tracks][5], cov [n_tracks][15], chi2, ndf, status [n_tracks]
+ *   (status 3 marks an invalid track range or row).
+ * Working memory is a fixed device array of TPC_NOALLOC_SCRATCH_BYTES that
+ * every GPU loading the library holds until the process exits; n_assigned
+ * above TPC_NOALLOC_MAX_ASSIGNED returns TPC_ERR_CAPACITY. The first call on
+ * a device looks up the array's device address (cudaGetSymbolAddress); make
+ * that first call before any stream capture on that device. All calls share
+ * the array, so calls that can overlap on the GPU (other streams, other
+ * threads) race; the array is rewritten by every call before it is read.
+ * geo, params: host, as for tpc_create (params NULL = defaults); stream: a
+ * cudaStream_t. Asynchronous: kernel errors surface at the next stream sync. */
+#define TPC_NOALLOC_MAX_ASSIGNED (1 << 20)
+#define TPC_NOALLOC_SCRATCH_BYTES (5 * TPC_NOALLOC_MAX_ASSIGNED)
+tpc_status tpc_refit_noalloc(const tpc_geometry* geo, const tpc_params* params, void* stream,
+                             int64_t n_tracks, int64_t n_assigned, const uint32_t* track_start,
+                             const float* yc, const float* zc, const uint8_t* row,
+                             const uint8_t* flags, float* params_out, float* cov_out,
+                             float* chi2_out, int32_t* ndf_out, int32_t* status_out);
+
 /* Kernel accounting (tracing). Every kernel launch of a context is counted.
  * tpc_profile(ctx, 1) also brackets each launch with CUDA events on the
  * context's stream (adds a few microseconds per launch); tpc_profile(ctx, 0)

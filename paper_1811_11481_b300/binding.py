@@ -89,6 +89,8 @@ _PROTOS = {
     "tpc_get_grid": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "tpc_last_error": (C.c_char_p, [C.c_void_p]),
     "tpc_profile": (C.c_int, [C.c_void_p, C.c_int]),
+    "tpc_refit_noalloc": (C.c_int, [C.POINTER(tpc_geometry), C.POINTER(tpc_params), C.c_void_p,
+                                    C.c_int64, C.c_int64] + [C.c_void_p] * 10),
     "tpc_profile_read": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.POINTER(C.c_int32),
                                    C.POINTER(C.c_int64)]),
 }

@@ -25,6 +25,7 @@ UNITS = {
     "tpc_find.cu": ["-fmad=false"],
     "tpc_refit.cu": ["--use_fast_math"],
     "tpc_capi.cu": [],
+    "tpc_noalloc.cu": ["--use_fast_math"],
 }
 
 
