@@ -282,8 +282,8 @@ __device__ void copy_bucket_unsorted(const ClIn& cl, int nb, int seg, uint32_t s
 }
 
 // Small buckets (<= 256 clusters): one warp each, 8 per block, bitonic sort
-// in a 256-entry shared tile per warp. Larger buckets are listed for the
-// block sorts below.
+// in a 256-entry shared tile per warp. Buckets up to 4096 clusters are listed
+// for the 4096-entry block sort, larger ones for the 16384-entry sort.
 constexpr int kWarpTile = 256;
 __global__ void k_row_sort_warp(Geo g, ClIn cl, GridDims gd, int K, const uint32_t* row_start,
                                 const uint2* es_dims, const uint32_t* perm, const float* zs_in,
@@ -304,7 +304,7 @@ __global__ void k_row_sort_warp(Geo g, ClIn cl, GridDims gd, int K, const uint32
     for (int q = lane; q <= B.nb; q += 32) bs[q] = start;
     return;
   }
-  if (n > kSortTileBig) {
+  if (n > kSortTile) {
     if (lane == 0) big_list[atomicAdd(big_count, 1u)] = (uint32_t)seg;
     return;
   }
