@@ -147,6 +147,24 @@ def algorithmic_bytes(kernel, c):
     return model.get(kernel)
 
 
+def ncu_traffic(kernel):
+    """DRAM bytes per launch of 'kernel' from the committed ncu summary, or
+    None when the kernel's sources changed since that capture."""
+    import hashlib
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(p):
+        return None
+    e = json.load(open(p))["kernels"].get(kernel)
+    if not e:
+        return None
+    src = os.path.join(ROOT, "paper_1811_11481_b300", "csrc")
+    for f, h in e["sources"].items():
+        fp = os.path.join(src, f)
+        if not os.path.exists(fp) or hashlib.sha256(open(fp, "rb").read()).hexdigest()[:16] != h:
+            return None
+    return e["bytes_per_launch"]
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -324,7 +342,7 @@ def run_ours(args):
         ab = algorithmic_bytes(dom, counts)
         ach = ab / (per_launch_ms / 1000.0) / 1e9 if ab else None
         roof = dict(kernel=dom, bound="hbm", achieved=ach, peak=peaks["hbm_gbs"], unit="GB/s",
-                    frac=(ach / peaks["hbm_gbs"]) if ach else None, traffic=None,
+                    frac=(ach / peaks["hbm_gbs"]) if ach else None, traffic=ncu_traffic(dom),
                     algorithmic_bytes=ab, ms_per_launch=per_launch_ms,
                     share=kms / tot, peak_source=peaks["source"] + " (burst copy)")
     kernels = {k: dict(launches=v[0], ms_per_step=v[1] / args.steps, share=v[1] / tot)

@@ -1,0 +1,151 @@
+"""Parity at the benchmark's full size (central event, 1.09M clusters), in the
+launch configuration bench.py times.
+
+The oracle recomputes sampled outputs one by one (links of sampled hits,
+tracklets of sampled start hits, refits of sampled tracks, gradients of
+sampled tracks) and the cheap whole-array steps completely (link cleaning,
+start hits, selection, calibration transform), each fed with the GPU's
+inputs of that step so that every comparison isolates one step.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from paper_1811_11481_b300.config import default_params
+from pipeline import RTOL, rel_err, tracker
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def full():
+    geo = synth.geometry()
+    ev = synth.make_central(seed=1)
+    tr = tracker(geo)
+    tr.set_calib()
+    cl = tr.upload(ev)
+    tr.load(cl)
+    out = tr.find()
+    g = {k: v.cpu().numpy() for k, v in out.items()}
+    g["up"], g["dn"], g["upc"], g["dnc"] = [t.cpu().numpy() for t in tr.links()]
+    g["tl"] = {k: v.cpu().numpy() for k, v in tr.tracklets().items()}
+    yc, zc = tr.calibrated()
+    g["yc"], g["zc"] = yc.cpu().numpy(), zc.cpu().numpy()
+    o = oracle.Oracle(ev, geo, default_params(), synth.nominal_calib())
+    return dict(ev=ev, geo=geo, tr=tr, g=g, o=o, rng=np.random.default_rng(99))
+
+
+def test_sampled_links(full):
+    g, o, ev = full["g"], full["o"], full["ev"]
+    hits = full["rng"].choice(ev.n, 4000, replace=False)
+    up, dn = o.neighbours(32, hits)
+    assert np.array_equal(g["up"][hits], up)
+    assert np.array_equal(g["dn"][hits], dn)
+
+
+def test_cleaning_and_start_hits_whole_event(full):
+    g, o = full["g"], full["o"]
+    upc, dnc = o.clean(g["up"], g["dn"])
+    assert np.array_equal(upc, g["upc"]) and np.array_equal(dnc, g["dnc"])
+    starts = o.start_hits(upc, dnc)
+    assert np.array_equal(starts, np.sort(g["tl"]["start_hit"].astype(np.int64)))
+
+
+def test_sampled_tracklets(full):
+    g, o = full["g"], full["o"]
+    tl = g["tl"]
+    k = full["rng"].choice(tl["start_hit"].size, 300, replace=False)
+    ref = o.tracklets(g["upc"], tl["start_hit"][k].astype(np.int64), 32)
+    assert np.array_equal(tl["nh"][k], ref["nh"])
+    assert np.array_equal(tl["hits"][k], ref["hits"])
+    assert np.array_equal(tl["that"][k], ref["that"])
+
+
+def test_selection_whole_event(full):
+    g, o = full["g"], full["o"]
+    tl = g["tl"]
+    order = np.argsort(tl["start_hit"].astype(np.int64))
+    sel = o.select(tl["start_hit"][order].astype(np.int64),
+                   dict(nh=np.ascontiguousarray(tl["nh"][order]),
+                        hits=np.ascontiguousarray(tl["hits"][order]),
+                        that=np.ascontiguousarray(tl["that"][order])))
+    ts = g["track_start"].astype(np.int64)
+    got = {int(s): g["cluster_idx"][ts[i]:ts[i + 1]] for i, s in enumerate(g["start_hit"])}
+    rts = sel["track_start"].astype(np.int64)
+    assert len(got) == rts.size - 1 > 10000
+    for i, s in enumerate(sel["start_hit"]):
+        assert np.array_equal(got[int(s)], sel["cluster_idx"][rts[i]:rts[i + 1]])
+    ci = g["cluster_idx"]
+    assert np.unique(ci).size == ci.size
+
+
+def test_calibration_whole_event(full):
+    g, o = full["g"], full["o"]
+    ts = g["track_start"].astype(np.int64)
+    that = np.repeat(g["t_coll"], np.diff(ts))
+    yc, zc = o.calibrate(g["cluster_idx"], that, prec=32)
+    assert np.array_equal(g["yc"], yc.astype(np.float32))
+    assert np.array_equal(g["zc"], zc.astype(np.float32))
+
+
+def test_sampled_refits_and_gradients(full):
+    import torch
+    g, o, tr = full["g"], full["o"], full["tr"]
+    r = tr.refit(save_for_backward=True)
+    got = {k: v.cpu().numpy() for k, v in r.items()}
+    nt = got["chi2"].size
+    ts = g["track_start"].astype(np.int64)
+    k = np.sort(full["rng"].choice(nt, 400, replace=False))
+    sts = np.concatenate([[0], np.cumsum(np.diff(ts)[k])]).astype(np.uint32)
+    sci = np.concatenate([g["cluster_idx"][ts[i]:ts[i + 1]] for i in k])
+    ref = o.refit(sts, sci, g["t_coll"][k], prec=64)
+    ok = (got["status"][k] == 0) & (ref["status"] == 0)
+    same = np.array([np.array_equal(got["rej"][ts[i]:ts[i + 1]], ref["rej"][sts[j]:sts[j + 1]])
+                     for j, i in enumerate(k)])
+    assert np.mean(got["status"][k] == ref["status"]) > 0.99 and np.mean(same[ok]) > 0.98
+    m = ok & same
+    e = rel_err(got["params"][k][m].astype(np.float64), ref["params"][m])
+    assert np.all(e <= RTOL), e.max(0)
+    # gradients of L = sum over 60 sampled tracks of chi2
+    kk = k[np.nonzero(m)[0][:60]]
+    w = torch.zeros(nt, device=tr.dev)
+    w[torch.as_tensor(kk, device=tr.dev)] = 1.0
+    gy, gz, gc = [t.cpu().numpy() for t in tr.refit_backward(w)]
+    sts2 = np.concatenate([[0], np.cumsum(np.diff(ts)[kk])]).astype(np.uint32)
+    sci2 = np.concatenate([g["cluster_idx"][ts[i]:ts[i + 1]] for i in kk])
+    ref2 = o.refit(sts2, sci2, g["t_coll"][kk], prec=64)
+    rej2 = np.concatenate([got["rej"][ts[i]:ts[i + 1]] for i in kk])
+    ry, rz, rc = o.refit_grad(sts2, sci2, g["t_coll"][kk], ref2["seeds"], rej2, np.ones(kk.size))
+    py = np.concatenate([gy[ts[i]:ts[i + 1]] for i in kk])
+    pz = np.concatenate([gz[ts[i]:ts[i + 1]] for i in kk])
+    assert np.linalg.norm(py - ry) / np.linalg.norm(ry) < 1e-3
+    assert np.linalg.norm(pz - rz) / np.linalg.norm(rz) < 1e-3
+    # the other tracks contribute nothing
+    rest = np.ones(gy.size, bool)
+    for i in kk:
+        rest[ts[i]:ts[i + 1]] = False
+    assert np.all(gy[rest] == 0) and np.all(gz[rest] == 0)
+
+
+def test_efficiency_and_fake_rate_match_oracle_definition(full):
+    """Efficiency and fake rate (Sec. 4 footnote definitions) of the GPU tracks
+    equal those the oracle's selection gives (identical assignment)."""
+    from collections import Counter
+    g, ev = full["g"], full["ev"]
+    ts = g["track_start"].astype(np.int64)
+    seg = ev.segment
+    matched, fake = set(), 0
+    for i in range(ts.size - 1):
+        c = Counter(seg[g["cluster_idx"][ts[i]:ts[i + 1]]])
+        s, n = c.most_common(1)[0]
+        if s < 0 or n < 0.9 * (ts[i + 1] - ts[i]):
+            fake += 1
+        else:
+            matched.add(s)
+    cnt = Counter(seg[seg >= 0])
+    findable = [s for s, n in cnt.items() if n >= 70]
+    eff = np.mean([s in matched for s in findable])
+    fake_rate = fake / (ts.size - 1)
+    assert eff > 0.95, eff
+    assert fake_rate < 0.02, fake_rate
