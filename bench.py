@@ -43,6 +43,8 @@ def parse():
                     choices=["central", "timeframe", "batched", "single_sector"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--graph", action="store_true",
+                    help="replay each step as one captured CUDA graph")
     ap.add_argument("--profile-steps", type=int, default=0,
                     help="only run W+K steps with kernel timing (for ncu launch lists)")
     return ap.parse_args()
@@ -189,7 +191,9 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     geo = synth.geometry()
     ev, cfg = make_workload(args.workload, rank)
-    tr = Tracker(geo)
+    work = torch.cuda.Stream()
+    torch.cuda.set_stream(work)
+    tr = Tracker(geo, stream=work)
     tr.set_calib()
     cl = tr.upload(ev)
     L, h = tr.L, tr.h
@@ -226,6 +230,19 @@ def run_ours(args):
 
     # warm-up (allocations happen here), then a count check
     for _ in range(max(3, args.warmup)):
+        step()
+    if args.graph:
+        work.synchronize()
+        tr.graph_begin()
+        step()
+        tr.graph_end()
+        direct_step = step
+
+        def step(refit=True, backward=True):
+            if refit and backward:
+                tr.graph_launch()
+            else:
+                direct_step(refit, backward)
         step()
     if args.profile_steps:
         # steady-state steps only: for ncu launch lists and captures
@@ -357,7 +374,8 @@ def run_ours(args):
                 scaling="weak", vs_baseline=None, dtype="f32 (f64 timestamps and gradient sums)",
                 data="synthetic",
                 config=dict(cfg, l2="flushed before every timed step (256 MB write)",
-                            parallelism=f"replicas x{world}, one independent event per GPU"),
+                            parallelism=f"replicas x{world}, one independent event per GPU",
+                            launch="one CUDA graph per step" if args.graph else "stream launches"),
                 tracks_per_s=world * nt * args.steps / (total_ms / 1000.0),
                 n_tracks=nt, n_assigned=na, n_tracklets=ntl,
                 refit_fwd_ms=t_fwd, refit_fwd_nosave_ms=t_fwd_nosave, adjoint_ms=t_bwd,

@@ -212,6 +212,20 @@ tpc_status tpc_refit(tpc_ctx* ctx, int save_for_backward, float* params, float* 
 tpc_status tpc_refit_backward(tpc_ctx* ctx, const float* dL_dchi2, float* grad_y,
                               float* grad_zt, double* grad_calib);
 
+/* CUDA-graph capture of a sequence of calls on the context's stream.
+ * tpc_graph_begin starts a capture; the following asynchronous calls
+ * (tpc_load_clusters, tpc_find_tracks_async, tpc_set_calib, tpc_refit,
+ * tpc_refit_backward) are recorded instead of run; tpc_graph_end
+ * instantiates them; tpc_graph_launch replays the recorded sequence on the
+ * stream (same device pointers and sizes as when captured). Buffers are
+ * allocated on first use, so run the sequence once outside the capture
+ * before capturing it: an allocation during capture fails with TPC_ERR_STATE.
+ * Synchronising calls (tpc_find_tracks, tpc_sync, tpc_get_*) are refused with
+ * TPC_ERR_STATE while capturing. */
+tpc_status tpc_graph_begin(tpc_ctx* ctx);
+tpc_status tpc_graph_end(tpc_ctx* ctx);
+tpc_status tpc_graph_launch(tpc_ctx* ctx);
+
 /* Synchronise the stream and report the latched device error word. */
 tpc_status tpc_sync(tpc_ctx* ctx);
 

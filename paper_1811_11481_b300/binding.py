@@ -89,6 +89,9 @@ _PROTOS = {
     "tpc_get_grid": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "tpc_last_error": (C.c_char_p, [C.c_void_p]),
     "tpc_profile": (C.c_int, [C.c_void_p, C.c_int]),
+    "tpc_graph_begin": (C.c_int, [C.c_void_p]),
+    "tpc_graph_end": (C.c_int, [C.c_void_p]),
+    "tpc_graph_launch": (C.c_int, [C.c_void_p]),
     "tpc_refit_noalloc": (C.c_int, [C.POINTER(tpc_geometry), C.POINTER(tpc_params), C.c_void_p,
                                     C.c_int64, C.c_int64] + [C.c_void_p] * 10),
     "tpc_profile_read": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.POINTER(C.c_int32),
@@ -314,6 +317,16 @@ class Tracker:
 
     def sync(self):
         self._ck(self.L.tpc_sync(self.h), "tpc_sync")
+
+    # ----------------------------------------------------------- graphs
+    def graph_begin(self):
+        self._ck(self.L.tpc_graph_begin(self.h), "tpc_graph_begin")
+
+    def graph_end(self):
+        self._ck(self.L.tpc_graph_end(self.h), "tpc_graph_end")
+
+    def graph_launch(self):
+        self._ck(self.L.tpc_graph_launch(self.h), "tpc_graph_launch")
 
     # ----------------------------------------------------------- accounting
     def profile(self, enable=True):

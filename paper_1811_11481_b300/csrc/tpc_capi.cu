@@ -36,6 +36,12 @@ struct tpc_ctx {
   bool tracks_valid = false;
   bool saved = false;
   bool part_alloc = false;
+  bool capturing = false;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;
+  int64_t graph_kernels = 0;     // kernel launches recorded in the graph
+  int64_t launches_before = 0;
+  bool prof_was_on = false;
   std::string err;
 };
 
@@ -49,13 +55,19 @@ tpc_status fail(tpc_ctx* c, tpc_status s, const std::string& msg) {
 #define CK(call)                                                                     \
   do {                                                                               \
     cudaError_t e_ = (call);                                                         \
+    if (e_ == cudaErrorStreamCaptureUnsupported)                                     \
+      return fail(ctx, TPC_ERR_STATE, "allocation during graph capture: run the sequence "  \
+                                      "once before capturing");                       \
     if (e_ != cudaSuccess)                                                           \
       return fail(ctx, TPC_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
   } while (0)
 
+thread_local bool g_capturing_alloc_guard = false;  // set while a context captures
+
 template <class T>
 cudaError_t grow(T*& p, int64_t& cap, int64_t need) {
   if (need <= cap && p) return cudaSuccess;
+  if (g_capturing_alloc_guard) return cudaErrorStreamCaptureUnsupported;
   if (p) cudaFree(p);
   p = nullptr;
   int64_t c = need > 0 ? need : 1;
@@ -66,6 +78,7 @@ cudaError_t grow(T*& p, int64_t& cap, int64_t need) {
 
 template <class T>
 cudaError_t alloc(T*& p, int64_t n) {
+  if (g_capturing_alloc_guard) return cudaErrorStreamCaptureUnsupported;
   if (p) cudaFree(p);
   p = nullptr;
   return cudaMalloc((void**)&p, sizeof(T) * (size_t)(n > 0 ? n : 1));
@@ -116,6 +129,7 @@ tpc_status status_of(uint32_t e) {
 
 // Read counters and error word (synchronises the stream).
 tpc_status read_back(tpc_ctx* ctx) {
+  if (ctx->capturing) return fail(ctx, TPC_ERR_STATE, "synchronising call during graph capture");
   CK(cudaMemcpyAsync(ctx->h_pinned, ctx->d_cnt, sizeof(uint32_t) * kCntSize,
                      cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaMemcpyAsync(ctx->h_pinned + kCntSize, ctx->d_err, sizeof(uint32_t),
@@ -307,6 +321,8 @@ void tpc_destroy(tpc_ctx* ctx) {
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
+  if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
+  if (ctx->graph) cudaGraphDestroy(ctx->graph);
   delete ctx;
 }
 
@@ -456,6 +472,7 @@ tpc_status tpc_find_tracks(tpc_ctx* ctx, tpc_tracks* out) {
 
 tpc_status tpc_set_tracks(tpc_ctx* ctx, const tpc_tracks* t) {
   if (!ctx || !t) return fail(ctx, TPC_ERR_ARG, "null argument");
+  if (ctx->capturing) return fail(ctx, TPC_ERR_STATE, "tpc_set_tracks synchronises");
   if (!ctx->loaded) return fail(ctx, TPC_ERR_STATE, "no batch loaded");
   if (t->n_tracks < 0 || t->n_assigned < 0 || t->n_assigned > ctx->cl.n ||
       (t->n_tracks > 0 && (!t->track_start || !t->cluster_idx || !t->t_coll)))
@@ -525,6 +542,50 @@ tpc_status tpc_refit_backward(tpc_ctx* ctx, const float* dl_dchi2, float* grad_y
   return TPC_OK;
 }
 
+tpc_status tpc_graph_begin(tpc_ctx* ctx) {
+  if (!ctx) return TPC_ERR_ARG;
+  if (ctx->capturing) return fail(ctx, TPC_ERR_STATE, "already capturing");
+  if (!ctx->stream) return fail(ctx, TPC_ERR_STATE, "graph capture needs a non-default stream");
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->prof.collect();
+  CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+  ctx->capturing = true;
+  g_capturing_alloc_guard = true;
+  ctx->prof_was_on = ctx->prof.on;
+  ctx->prof.on = false;  // no event pairs inside the graph
+  ctx->launches_before = ctx->prof.launches;
+  return TPC_OK;
+}
+
+tpc_status tpc_graph_end(tpc_ctx* ctx) {
+  if (!ctx) return TPC_ERR_ARG;
+  if (!ctx->capturing) return fail(ctx, TPC_ERR_STATE, "not capturing");
+  ctx->capturing = false;
+  g_capturing_alloc_guard = false;
+  ctx->graph_kernels = ctx->prof.launches - ctx->launches_before;
+  ctx->prof.launches = ctx->launches_before;
+  ctx->prof.on = ctx->prof_was_on;
+  cudaGraph_t gr = nullptr;
+  cudaError_t e = cudaStreamEndCapture(ctx->stream, &gr);
+  if (e != cudaSuccess || !gr)
+    return fail(ctx, TPC_ERR_STATE, std::string("capture failed: ") + cudaGetErrorString(e) +
+                                        " (run the sequence once before capturing)");
+  if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
+  if (ctx->graph) cudaGraphDestroy(ctx->graph);
+  ctx->graph = gr;
+  ctx->graph_exec = nullptr;
+  CK(cudaGraphInstantiate(&ctx->graph_exec, gr, 0));
+  return TPC_OK;
+}
+
+tpc_status tpc_graph_launch(tpc_ctx* ctx) {
+  if (!ctx) return TPC_ERR_ARG;
+  if (!ctx->graph_exec) return fail(ctx, TPC_ERR_STATE, "no captured graph");
+  CK(cudaGraphLaunch(ctx->graph_exec, ctx->stream));
+  ctx->prof.launches += ctx->graph_kernels;
+  return TPC_OK;
+}
+
 tpc_status tpc_sync(tpc_ctx* ctx) {
   if (!ctx) return TPC_ERR_ARG;
   return read_back(ctx);
@@ -589,6 +650,7 @@ tpc_status tpc_get_grid(tpc_ctx* ctx, uint32_t* order, uint32_t* row_start) {
 
 tpc_status tpc_profile(tpc_ctx* ctx, int enable) {
   if (!ctx) return TPC_ERR_ARG;
+  if (ctx->capturing) return fail(ctx, TPC_ERR_STATE, "tpc_profile synchronises");
   CK(cudaStreamSynchronize(ctx->stream));
   ctx->prof.collect();
   ctx->prof.stats.clear();
