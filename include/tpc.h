@@ -192,7 +192,9 @@ tpc_status tpc_find_tracks_async(tpc_ctx* ctx);
  * calibration transform to the assigned clusters. */
 tpc_status tpc_set_tracks(tpc_ctx* ctx, const tpc_tracks* tracks);
 
-/* Refit the context's track set (Sec. 3). Outputs are caller-owned device
+/* Refit the context's track set (Sec. 3) with the current calibration: the
+ * calibration transform of the assigned clusters (Sec. 4) is re-applied
+ * first, so tpc_set_calib between refits takes effect. Outputs are caller-owned device
  * buffers with room for the number of tracks (params [n][5], cov [n][15],
  * x [n], chi2 [n], ndf [n]; rej [n_assigned] receives for each cluster the
  * refit pass that rejected it, 0 = kept; any output may be NULL). status[n]
@@ -202,7 +204,8 @@ tpc_status tpc_set_tracks(tpc_ctx* ctx, const tpc_tracks* tracks);
 tpc_status tpc_refit(tpc_ctx* ctx, int save_for_backward, float* params, float* cov, float* x,
                      float* chi2, int32_t* ndf, int32_t* status, uint8_t* rej);
 
-/* Adjoint of the last saved refit (not in the paper): for
+/* Adjoint of the last saved refit (not in the paper; TPC_ERR_STATE if the
+ * calibration was set again after that refit): for
  * L = sum_k dL_dchi2[k] * chi2_k with chi2_k the pass-3 chi2, writes
  * grad_y[j], grad_zt[j] = dL/d(y, t or z) of the input cluster cluster_idx[j]
  * (device [n_assigned] each, overwritten) and grad_calib = dL/d(vdrift, t0,

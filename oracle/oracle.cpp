@@ -27,6 +27,7 @@
 #include <cstdint>
 #include <cstring>
 #include <map>
+#include <type_traits>
 #include <vector>
 
 namespace {
@@ -383,7 +384,9 @@ void calibrate(const Ctx& c, int64_t i, double that, const CalIn<R>& a, R& yc, R
     W<R> zeta = a.vdrift * ((a.t - a.t0) - W<R>(that));
     zabs = narrow<R>(sg * (W<R>((double)c.g.drift_length) - zeta));
   }
-  if (c.spline_active) {
+  // an all-zero spline adds exactly zero, but its coefficients still have a
+  // gradient: the differentiated (Var) evaluation always includes it
+  if (c.spline_active || std::is_same<R, Var>::value) {
     R d[2];
     R x = R(c.rowx[c.cl.row[i]]);
     spline_eval<R>(c, sec, x, a.y, abs_(zabs), d, lv);

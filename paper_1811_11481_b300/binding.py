@@ -242,7 +242,9 @@ class Tracker:
         t = tpc_tracks()
         self._ck(self.L.tpc_find_tracks(self.h, C.byref(t)), "tpc_find_tracks")
         self.n_tracks, self.n_assigned = int(t.n_tracks), int(t.n_assigned)
-        return self._tracks_view(t)
+        view = self._tracks_view(t)
+        self.cluster_idx = view["cluster_idx"]
+        return view
 
     def find_async(self):
         self._ck(self.L.tpc_find_tracks_async(self.h), "tpc_find_tracks_async")
@@ -281,6 +283,7 @@ class Tracker:
                        sh.data_ptr() if sh is not None else None)
         self._ck(self.L.tpc_set_tracks(self.h, C.byref(t)), "tpc_set_tracks")
         self.n_tracks, self.n_assigned = int(t.n_tracks), int(t.n_assigned)
+        self.cluster_idx = ci
 
     # ----------------------------------------------------------- refit
     def refit(self, save_for_backward=False, n_tracks=None, n_assigned=None):

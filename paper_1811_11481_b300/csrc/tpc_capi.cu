@@ -37,6 +37,8 @@ struct tpc_ctx {
   bool saved = false;
   bool part_alloc = false;
   bool capturing = false;
+  int64_t calib_version = 0;        // incremented by tpc_set_calib
+  int64_t refit_calib_version = -1;  // calibration of the saved refit
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
   int64_t graph_kernels = 0;     // kernel launches recorded in the graph
@@ -342,6 +344,7 @@ tpc_status tpc_set_calib(tpc_ctx* ctx, const tpc_calib* calib) {
   }
   launch_spline_bound(ctx->d_spline, ctx->d_spl_bound, ctx->stream);
   CK(cudaGetLastError());
+  ++ctx->calib_version;
   return TPC_OK;
 }
 
@@ -516,11 +519,15 @@ tpc_status tpc_refit(tpc_ctx* ctx, int save_for_backward, float* params, float* 
       ctx->cap_ckpt_alloc = need;
     }
   }
+  // the current calibration applies to the refit inputs (Sec. 4)
+  launch_calib(&ctx->prof, ctx->geo, ctx->cal, ctx->cl, ctx->tb.cap_asg, ctx->tb, ctx->d_cnt,
+               ctx->d_err, ctx->stream);
   launch_refit(&ctx->prof, ctx->geo, ctx->prm, ctx->tb.cap_tr, ctx->d_cnt, ctx->tb, ctx->rb,
                save_for_backward != 0, params, cov, x, chi2, ndf, status, rej, ctx->d_err,
                ctx->stream);
   CK(cudaGetLastError());
   ctx->saved = save_for_backward != 0;
+  ctx->refit_calib_version = ctx->calib_version;
   return TPC_OK;
 }
 
@@ -528,6 +535,8 @@ tpc_status tpc_refit_backward(tpc_ctx* ctx, const float* dl_dchi2, float* grad_y
                               double* grad_calib) {
   if (!ctx) return TPC_ERR_ARG;
   if (!ctx->saved) return fail(ctx, TPC_ERR_STATE, "refit_backward needs a saved refit");
+  if (ctx->refit_calib_version != ctx->calib_version)
+    return fail(ctx, TPC_ERR_STATE, "calibration changed since the saved refit");
   if (!dl_dchi2 || !grad_y || !grad_zt || !grad_calib)
     return fail(ctx, TPC_ERR_ARG, "null output");
   if (!ctx->part_alloc) {

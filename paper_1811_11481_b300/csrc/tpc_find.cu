@@ -1059,6 +1059,15 @@ void launch_set_tracks(Prof* P, const Geo& g, const Cal& c, const ClIn& cl, int6
                                                  tb.t_coll, tb.yc, tb.zc, tb.meta, err));
 }
 
+void launch_calib(Prof* P, const Geo& g, const Cal& c, const ClIn& cl, int64_t cap_asg,
+                  TrackBuf& tb, uint32_t* cnt, uint32_t* err, cudaStream_t s) {
+  if (cap_asg > 0)
+    TPC_LAUNCH(P, "k_calib", s,
+               k_calib<<<nblk(cap_asg, kB256), kB256, 0, s>>>(g, c, cl, cnt, tb.cluster_idx,
+                                                              tb.asg_track, tb.t_coll, tb.yc,
+                                                              tb.zc, tb.meta, err));
+}
+
 void launch_spline_bound(const float* spline, float* bound, cudaStream_t s) {
   k_spline_bound<<<1, 256, 0, s>>>(spline, bound);
 }

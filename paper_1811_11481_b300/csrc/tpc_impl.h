@@ -220,6 +220,8 @@ void launch_find(Prof* P, const Geo& g, const Cal& c, const Params& p, const ClI
                  uint32_t* err, cudaStream_t s);
 void launch_set_tracks(Prof* P, const Geo& g, const Cal& c, const ClIn& cl, int64_t n_tracks,
                        int64_t n_asg, TrackBuf& tb, uint32_t* cnt, uint32_t* err, cudaStream_t s);
+void launch_calib(Prof* P, const Geo& g, const Cal& c, const ClIn& cl, int64_t cap_asg,
+                  TrackBuf& tb, uint32_t* cnt, uint32_t* err, cudaStream_t s);
 void launch_spline_bound(const float* spline, float* bound, cudaStream_t s);
 void launch_export_links(const FindBuf& b, int n, int K, int32_t* up, int32_t* dn, int32_t* upc,
                          int32_t* dnc, cudaStream_t s);

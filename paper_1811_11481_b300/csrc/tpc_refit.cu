@@ -239,9 +239,10 @@ __global__ void __launch_bounds__(512) k_calib_grad(Geo g, Cal c, ClIn cl, const
   extern __shared__ float sacc[];
   __shared__ double red[2][16];
   const int NS = TPC_SPLINE_SIZE;
-  bool spl_on = c.spl_bound[2] > 0.0f;
-  if (spl_on)
-    for (int i = threadIdx.x; i < NS; i += blockDim.x) sacc[i] = 0.0f;
+  // the spline's coefficient gradient is formed even when all coefficients
+  // are zero (the forward then adds exactly zero)
+  bool spl_on = true;
+  for (int i = threadIdx.x; i < NS; i += blockDim.x) sacc[i] = 0.0f;
   __syncthreads();
   int n = (int)cnt[kCntAssigned];
   int per = (n + gridDim.x - 1) / gridDim.x;
@@ -346,7 +347,7 @@ __global__ void __launch_bounds__(512) k_calib_grad(Geo g, Cal c, ClIn cl, const
     part_cal[blockIdx.x * 2 + 1] = s1;
   }
   float* ps = part_spline + (size_t)blockIdx.x * NS;
-  for (int i = threadIdx.x; i < NS; i += blockDim.x) ps[i] = spl_on ? sacc[i] : 0.0f;
+  for (int i = threadIdx.x; i < NS; i += blockDim.x) ps[i] = sacc[i];
 }
 
 __global__ void k_calib_reduce(int nblk, const float* part_spline, const double* part_cal,

@@ -498,3 +498,26 @@ def test_gradient_matches_finite_differences(geo, params):
         cm.spline.reshape(-1)[j] = flat[j] - e
         fd = (loss(cal_mod=cp) - loss(cal_mod=cm)) / (2 * e)
         assert abs(fd - gc[2 + j]) < 1e-3 * max(1, abs(fd)), (j, fd, gc[2 + j])
+
+
+def test_spline_gradient_at_zero_coefficients(geo, params):
+    """An all-zero spline adds nothing, but its coefficients have a gradient."""
+    cal = synth.nominal_calib()
+    ev = synth.make_tiny(seed=21, n_tracks=5, sectors=(3,), mode="time", tf_start=1.0e6)
+    ts, ci, tc, sids = synth.truth_tracks(ev, 40)
+    ts, ci, tc = ts[:3], ci[:ts[2]], tc[:2]
+    o = _oracle(ev, geo, params, cal)
+    r = o.refit(ts, ci, tc, prec=64)
+    gy, gz, gc = o.refit_grad(ts, ci, tc, r["seeds"], r["rej"], np.ones(2))
+    assert np.count_nonzero(gc[2:]) > 0
+    for j in np.argsort(-np.abs(gc[2:]))[:3]:
+        e = 1e-3
+        losses = []
+        for sgn in (1, -1):
+            cm = cal.copy()
+            cm.spline.reshape(-1)[j] = sgn * e
+            oo = _oracle(ev, geo, params, cm)
+            losses.append(float(np.sum(oo.refit(ts, ci, tc, prec=64, seeds=r["seeds"],
+                                                 rej=r["rej"])["chi2"])))
+        fd = (losses[0] - losses[1]) / (2 * e)
+        assert abs(fd - gc[2 + j]) < 1e-3 * max(1, abs(fd)), (j, fd, gc[2 + j])
