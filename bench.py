@@ -149,6 +149,21 @@ def algorithmic_bytes(kernel, c):
     return model.get(kernel)
 
 
+def aggregate(total_ms, units, dist=None, device="cpu"):
+    """Whole-job timing over ranks: the slowest rank's time and the sum of the
+    units (clusters) every rank processed; returns (max_ms, units_sum,
+    units_per_second). Without torch.distributed initialised: this rank's."""
+    if dist is not None and dist.is_available() and dist.is_initialized() and \
+            dist.get_world_size() > 1:
+        import torch
+        t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+        u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+        total_ms, units = float(t.item()), float(u.item())
+    return total_ms, units, units / (total_ms / 1000.0)
+
+
 def ncu_traffic(kernel):
     """DRAM bytes per launch of 'kernel' from the committed ncu summary, or
     None when the kernel's sources changed since that capture."""
@@ -284,12 +299,7 @@ def run_ours(args):
     ms = [a.elapsed_time(b) for a, b in times]
     kstats, launches = tr.profile_read()
     tr.profile(False)
-    total_ms = float(np.sum(ms))
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * n * args.steps / (total_ms / 1000.0)
+    total_ms, units, value = aggregate(float(np.sum(ms)), n * args.steps, dist, dev)
 
     # ---- forward-only vs adjoint timing (phases of the same step)
     def phase_time(fn, reps=5):
@@ -338,12 +348,8 @@ def run_ours(args):
             res_h[cap_tr * 5:cap_tr * 6].copy_(out["chi2"], non_blocking=True)
         b.record(stream)
         barrier()
-        e2e_ms = a.elapsed_time(b)
-        if world > 1:
-            t = torch.tensor([e2e_ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_ms = float(t.item())
-        e2e = dict(value=world * n * args.steps / (e2e_ms / 1000.0), unit=UNIT,
+        _, _, e2e_value = aggregate(a.elapsed_time(b), n * args.steps, dist, dev)
+        e2e = dict(value=e2e_value, unit=UNIT,
                    h2d_bytes_per_step=int(h2d), d2h_bytes_per_step=int(d2h))
 
     # ---- roofline of the dominant kernel
@@ -376,7 +382,7 @@ def run_ours(args):
                 config=dict(cfg, l2="flushed before every timed step (256 MB write)",
                             parallelism=f"replicas x{world}, one independent event per GPU",
                             launch="one CUDA graph per step" if args.graph else "stream launches"),
-                tracks_per_s=world * nt * args.steps / (total_ms / 1000.0),
+                tracks_per_s=aggregate(total_ms, nt * args.steps, dist, dev)[2],
                 n_tracks=nt, n_assigned=na, n_tracklets=ntl,
                 refit_fwd_ms=t_fwd, refit_fwd_nosave_ms=t_fwd_nosave, adjoint_ms=t_bwd,
                 adjoint_vs_fwd=t_bwd / t_fwd_nosave if t_fwd_nosave > 0 else None,
