@@ -189,6 +189,8 @@ tpc_status ensure_tracklets(tpc_ctx* ctx) {
   FindBuf& b = ctx->fb;
   if (cap > b.cap_tl) {
     CK(alloc(b.starts, cap));
+    CK(alloc(b.seed_end, cap));
+    CK(alloc(b.range, cap));
     CK(alloc(b.nh, cap));
     CK(alloc(b.hits, cap * (int64_t)ctx->geo.n_rows));
     CK(alloc(b.that, cap));
@@ -281,7 +283,9 @@ tpc_status tpc_create(const tpc_geometry* geo, const tpc_params* params, void* s
   chk(cudaMalloc(&ctx->rb.len_hist, sizeof(uint32_t) * 1024));
   chk(cudaMalloc(&ctx->fb.list_counts, sizeof(uint32_t) * 2));
   chk(cudaMalloc(&ctx->fb.n_bins, sizeof(uint32_t)));
+  chk(cudaMalloc(&ctx->fb.queue, sizeof(uint32_t)));
   chk(cudaMallocHost(&ctx->h_pinned, sizeof(uint32_t) * (kCntSize + 1)));
+  ctx->fb.tl_blocks = tracklet_resident_blocks();
   if (st != TPC_OK) {
     tpc_destroy(ctx);
     return st;
@@ -312,14 +316,14 @@ void tpc_destroy(tpc_ctx* ctx) {
                   ctx->fb.cnt, ctx->fb.row_start, ctx->fb.fill, ctx->fb.zmm, ctx->fb.zr,
                   ctx->fb.zs_in, ctx->fb.perm, ctx->fb.gyz,
                   ctx->fb.gorig, ctx->fb.gseg, ctx->fb.bin_start, ctx->fb.big_list, ctx->fb.mid_list, ctx->fb.list_counts,
-                  ctx->fb.n_bins, ctx->fb.es_dims, ctx->fb.up, ctx->fb.dn,
+                  ctx->fb.n_bins, ctx->fb.es_dims, ctx->fb.queue, ctx->fb.up, ctx->fb.dn,
                   ctx->fb.upc, ctx->fb.dnc, ctx->fb.blk_a, ctx->fb.blk_b, ctx->fb.off_a,
-                  ctx->fb.off_b, ctx->fb.starts, ctx->fb.nh, ctx->fb.hits, ctx->fb.that,
+                  ctx->fb.off_b, ctx->fb.starts, ctx->fb.seed_end, ctx->fb.range, ctx->fb.nh, ctx->fb.hits, ctx->fb.that,
                   ctx->fb.weight, ctx->fb.nkeep, ctx->tb.track_start, ctx->tb.cluster_idx,
                   ctx->tb.asg_track, ctx->tb.t_coll, ctx->tb.start_hit, ctx->tb.yc, ctx->tb.zc,
                   ctx->tb.meta, ctx->rb.seed, ctx->rb.order, ctx->rb.slot, ctx->rb.wlen, ctx->rb.wbase, ctx->rb.len_hist,
                   ctx->rb.w_yc, ctx->rb.w_zc, ctx->rb.w_meta, ctx->rb.rej, ctx->rb.status, ctx->rb.ckpt,
-                  ctx->rb.gyc, ctx->rb.gzc, ctx->rb.part_spline, ctx->rb.part_cal};
+                  ctx->rb.gyc, ctx->rb.gzc, ctx->rb.acc_spline, ctx->rb.gmax, ctx->rb.part_cal};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
@@ -540,7 +544,8 @@ tpc_status tpc_refit_backward(tpc_ctx* ctx, const float* dl_dchi2, float* grad_y
   if (!dl_dchi2 || !grad_y || !grad_zt || !grad_calib)
     return fail(ctx, TPC_ERR_ARG, "null output");
   if (!ctx->part_alloc) {
-    CK(alloc(ctx->rb.part_spline, (int64_t)kCalibGradBlocks * TPC_SPLINE_SIZE));
+    CK(alloc(ctx->rb.acc_spline, (int64_t)TPC_SPLINE_SIZE));
+    CK(alloc(ctx->rb.gmax, (int64_t)1));
     CK(alloc(ctx->rb.part_cal, (int64_t)kCalibGradBlocks * 2));
     ctx->part_alloc = true;
   }

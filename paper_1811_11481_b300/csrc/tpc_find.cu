@@ -550,15 +550,26 @@ __global__ void k_scan_blocks(int nblk, const uint32_t* a, uint32_t* off_a, cons
   }
 }
 
+// Also the last hit of each start hit's seed: the first seed_max_hits hits
+// of its chain of cleaned links.
 __global__ void k_write_starts(const uint32_t* nvalid, const int32_t* upc, const int32_t* dnc,
-                               const uint32_t* blk_off, uint32_t cap, uint32_t* starts) {
+                               const uint32_t* blk_off, uint32_t cap, int seed_max_hits,
+                               uint32_t* starts, uint32_t* seed_end) {
   int h = blockIdx.x * blockDim.x + threadIdx.x;
   int n = (int)*nvalid;
   uint32_t st = (h < n && is_start(upc, dnc, h)) ? 1u : 0u;
   uint32_t ex = block_excl_scan(st, nullptr);
   if (st) {
     uint32_t pos = blk_off[blockIdx.x] + ex;
-    if (pos < cap) starts[pos] = (uint32_t)h;
+    if (pos < cap) {
+      starts[pos] = (uint32_t)h;
+      int hl = h, nseed = 1;
+      while (upc[hl] >= 0 && nseed < seed_max_hits) {
+        hl = upc[hl];
+        ++nseed;
+      }
+      seed_end[pos] = (uint32_t)hl;
+    }
   }
 }
 
@@ -641,10 +652,12 @@ __device__ int pick(const Geo& g, const Cal& c, const Params& p, const GridDims&
   return best;
 }
 
-// One thread per start hit, written as a step machine: every iteration of the
-// loop transports the state to the next row and updates it with either the
-// next seed hit or the picked cluster, so that the threads of a warp execute
-// the same instructions whatever phase their tracklet is in.
+// Persistent tracklet constructor, written as a step machine: every
+// iteration of the loop transports the state to the next row and updates it
+// with either the next seed hit or the picked cluster, so the threads of a
+// warp execute the same instructions whatever phase their tracklet is in;
+// a thread whose tracklet ends takes the next start hit from a queue, so the
+// lanes of a warp stay busy while work is left.
 //   phase 0: seed fit in seeding coordinates (chain hits h0 .. hl)
 //   phase 1: seed fit in calibrated coordinates (after the collision time)
 //   phase 2: outward following from the seed end
@@ -655,39 +668,63 @@ __global__ void __launch_bounds__(128) k_tracklets(Geo g, Cal c, Params p, GridD
                                                   const uint2* es_dims, int mode,
                                                   const int32_t* upc,
                                                   const uint32_t* gseg, const uint32_t* starts,
-                                                  const uint32_t* cnt, int32_t* nh_out,
-                                                  int32_t* hits, double* that_out,
-                                                  unsigned long long* weight) {
-  int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (int)cnt[kCntStart]) return;
-  int32_t* H = hits + (size_t)t * g.n_rows;
-  for (int r = 0; r < g.n_rows; ++r) H[r] = -1;
-  int h0 = (int)starts[t];
-  int seg0 = (int)gseg[h0];
-  int r0 = seg0 % g.n_rows;
-  int es = seg0 / g.n_rows;
-  int ev = es / kNS, sec = es % kNS;
-  Bins BB = es_bins(es_dims, es);
+                                                  const uint32_t* seed_end, const uint32_t* cnt,
+                                                  int32_t* nh_out, int32_t* hits,
+                                                  uint32_t* range_out, double* that_out,
+                                                  uint32_t* queue) {
+  const int ntl = (int)cnt[kCntStart];
   const float sig2 = p.sigma * p.sigma;
-  bool spl_on = c.spl_bound[2] > 0.0f;
-  float dymax = spl_on ? c.spl_bound[0] : 0.0f;
-  float dzmax = spl_on ? c.spl_bound[1] : 0.0f;
-  // the seed: the first segment of at most seed_max_hits linked hits
-  int hl = h0, rl = r0, nseed = 1;
-  while (upc[hl] >= 0 && nseed < p.seed_max_hits) {
-    hl = upc[hl];
-    ++rl;
-    ++nseed;
-  }
-  float st[5], C[15], x;
-  float2 yz0 = G.gyz[h0], yzl = G.gyz[hl];
-  seed_two_points(st, C, x, p.c0t, g.row_x[r0], yz0.x, yz0.y, g.row_x[rl], yzl.x, yzl.y);
+  const bool spl_on = c.spl_bound[2] > 0.0f;
+  const float dymax = spl_on ? c.spl_bound[0] : 0.0f;
+  const float dzmax = spl_on ? c.spl_bound[1] : 0.0f;
+  int t = -1;
+  int32_t* H = nullptr;
+  int h0 = 0, r0 = 0, ev = 0, sec = 0, hl = 0, rl = 0;
+  Bins BB{0u, 1, 1, 1};
+  float2 yz0 = make_float2(0.f, 0.f), yzl = yz0;
+  float st[5], C[15], x = 0.0f;
   double that = 0.0;
   float shift = 0.0f;
-  float bst[5], bC[15], bx = x;
-  int phase = kSeed1, h = h0, r = r0, rlast = rl, miss = 0, nh = 0;
+  float bst[5], bC[15], bx = 0.0f;
+  int phase = kDone, h = 0, r = 0, rlast = 0, miss = 0, nh = 0;
   bool failed = false;
-  while (phase != kDone) {
+  int rlo = 0;
+  while (true) {
+    if (phase == kDone) {
+      if (t >= 0) {
+        // the current tracklet: hit count, collision time and the rows
+        // [rlo, rlast] its inward pass visited (hits[] holds those rows)
+        nh_out[t] = failed ? -1 : nh;
+        that_out[t] = failed ? 0.0 : that;
+        range_out[t] = failed ? 1u : ((uint32_t)rlo | ((uint32_t)rlast << 16));
+      }
+      t = (int)atomicAdd(queue, 1u);
+      if (t >= ntl) break;
+      H = hits + (size_t)t * g.n_rows;
+      h0 = (int)starts[t];
+      hl = (int)seed_end[t];
+      int seg0 = (int)gseg[h0];
+      rl = (int)gseg[hl] % g.n_rows;
+      yz0 = G.gyz[h0];
+      yzl = G.gyz[hl];
+      r0 = seg0 % g.n_rows;
+      int es = seg0 / g.n_rows;
+      ev = es / kNS;
+      sec = es % kNS;
+      BB = es_bins(es_dims, es);
+      seed_two_points(st, C, x, p.c0t, g.row_x[r0], yz0.x, yz0.y, g.row_x[rl], yzl.x, yzl.y);
+      that = 0.0;
+      shift = 0.0f;
+      bx = x;
+      phase = kSeed1;
+      h = h0;
+      r = r0;
+      rlast = rl;
+      rlo = rl + 1;
+      miss = 0;
+      nh = 0;
+      failed = false;
+    }
     bool ok = propagate(g.kB, p.s_max, st, C, x, g.row_x[r]);
     bool have = false;
     float my = 0.0f, mz = 0.0f;
@@ -763,8 +800,9 @@ __global__ void __launch_bounds__(128) k_tracklets(Geo g, Cal c, Params p, GridD
       if (!ok) {
         phase = kDone;
       } else {
+        H[r] = have ? j : -1;
+        rlo = r;
         if (have) {
-          H[r] = j;
           ++nh;
           miss = 0;
         } else if (++miss >= p.max_miss) {
@@ -780,38 +818,52 @@ __global__ void __launch_bounds__(128) k_tracklets(Geo g, Cal c, Params p, GridD
       for (int i = 0; i < 15; ++i) C[i] = bC[i] * p.inward_cov_scale;
       x = bx;
       r = rlast;
+      rlo = rlast + 1;
       miss = 0;
       phase = kIn;
     }
   }
-  if (failed) {
-    nh_out[t] = -1;
-    that_out[t] = 0.0;
-    return;
-  }
-  nh_out[t] = nh;
-  that_out[t] = that;
-  if (nh >= p.min_track_hits) {
-    unsigned long long w = ((unsigned long long)(uint32_t)nh << 32) |
-                           (unsigned long long)(0xffffffffu - G.gorig[h0]);
-    for (int rr = 0; rr < g.n_rows; ++rr)
-      if (H[rr] >= 0) atomicMax(&weight[H[rr]], w);
-  }
 }
 
 // --------------------------------------------------- a8: tracklet selection
+// Every cluster keeps the largest weight (hit count, then the lowest start
+// hit) of the tracklets of at least min_track_hits hits that picked it
+// (Sec. 3, tracklet selection). One warp per tracklet.
+__global__ void k_tl_weight(int n_rows, int min_track_hits, const uint32_t* cnt,
+                            const int32_t* nh, const int32_t* hits, const uint32_t* range,
+                            const uint32_t* starts, const uint32_t* gorig,
+                            unsigned long long* weight) {
+  int t = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  int lane = threadIdx.x & 31;
+  if (t >= (int)cnt[kCntStart]) return;
+  int n = nh[t];
+  if (n < min_track_hits) return;
+  unsigned long long w = ((unsigned long long)(uint32_t)n << 32) |
+                         (unsigned long long)(0xffffffffu - gorig[starts[t]]);
+  uint32_t rg = range[t];
+  int rlo = (int)(rg & 0xffffu), rhi = (int)(rg >> 16);
+  const int32_t* H = hits + (size_t)t * n_rows;
+  for (int r = rlo + lane; r <= rhi; r += 32) {
+    int j = H[r];
+    if (j >= 0) atomicMax(&weight[j], w);
+  }
+}
+
 __global__ void k_select_count(int n_rows, const Params p, const uint32_t* cnt,
-                               const int32_t* nh, const int32_t* hits, const uint32_t* starts,
-                               const uint32_t* gorig, const unsigned long long* weight,
-                               uint32_t* nkeep, uint32_t* blk_tr, uint32_t* blk_cl) {
+                               const int32_t* nh, const int32_t* hits, const uint32_t* range,
+                               const uint32_t* starts, const uint32_t* gorig,
+                               const unsigned long long* weight, uint32_t* nkeep,
+                               uint32_t* blk_tr, uint32_t* blk_cl) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   uint32_t emit = 0, kept = 0;
   if (t < (int)cnt[kCntStart] && nh[t] >= p.min_track_hits) {
     unsigned long long w = ((unsigned long long)(uint32_t)nh[t] << 32) |
                            (unsigned long long)(0xffffffffu - gorig[starts[t]]);
     const int32_t* H = hits + (size_t)t * n_rows;
+    uint32_t rg = range[t];
+    int rlo = (int)(rg & 0xffffu), rhi = (int)(rg >> 16);
     int lastr = -1, maxgap = 0, k = 0;
-    for (int r = 0; r < n_rows; ++r) {
+    for (int r = rlo; r <= rhi; ++r) {
       int j = H[r];
       if (j < 0 || weight[j] != w) continue;
       if (lastr >= 0) maxgap = max(maxgap, r - lastr - 1);
@@ -834,7 +886,7 @@ __global__ void k_select_count(int n_rows, const Params p, const uint32_t* cnt,
 }
 
 __global__ void k_select_write(int n_rows, const uint32_t* cnt, const int32_t* hits,
-                               const uint32_t* starts, const double* that,
+                               const uint32_t* range, const uint32_t* starts, const double* that,
                                const uint32_t* gorig, const unsigned long long* weight,
                                const int32_t* nh, const uint32_t* nkeep, const uint32_t* off_tr,
                                const uint32_t* off_cl, int64_t cap_tr, int64_t cap_asg,
@@ -855,7 +907,9 @@ __global__ void k_select_write(int n_rows, const uint32_t* cnt, const int32_t* h
   t_coll[id] = that[t];
   start_hit[id] = gorig[starts[t]];
   const int32_t* H = hits + (size_t)t * n_rows;
-  for (int r = 0; r < n_rows; ++r) {
+  uint32_t rg = range[t];
+  int rlo = (int)(rg & 0xffffu), rhi = (int)(rg >> 16);
+  for (int r = rlo; r <= rhi; ++r) {
     int j = H[r];
     if (j < 0 || weight[j] != w) continue;
     cluster_idx[o] = gorig[j];
@@ -951,18 +1005,21 @@ __global__ void k_export_links(const uint32_t* nvalid, const uint32_t* gorig, co
 __global__ void k_export_tracklets(int n_rows, int64_t n_cap, const uint32_t* cnt,
                                    const uint32_t* gorig, const uint32_t* starts,
                                    const int32_t* nh, const double* that, const int32_t* hits,
-                                   uint32_t* o_start, int32_t* o_nh, double* o_that,
-                                   int32_t* o_hits) {
+                                   const uint32_t* range, uint32_t* o_start, int32_t* o_nh,
+                                   double* o_that, int32_t* o_hits) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (int)cnt[kCntStart] || t >= n_cap) return;
   if (o_start) o_start[t] = gorig[starts[t]];
   if (o_nh) o_nh[t] = nh[t];
   if (o_that) o_that[t] = that[t];
-  if (o_hits)
+  if (o_hits) {
+    uint32_t rg = range[t];
+    int rlo = (int)(rg & 0xffffu), rhi = (int)(rg >> 16);
     for (int r = 0; r < n_rows; ++r) {
-      int j = hits[(size_t)t * n_rows + r];
+      int j = (r >= rlo && r <= rhi) ? hits[(size_t)t * n_rows + r] : -1;
       o_hits[(size_t)t * n_rows + r] = j >= 0 ? (int32_t)gorig[j] : -1;
     }
+  }
 }
 
 inline int nblk(int64_t n, int b) { return (int)((n + b - 1) / b); }
@@ -1014,6 +1071,15 @@ void launch_load(Prof* P, const Geo& g, const Cal& c, const ClIn& cl, const Grid
                                                          b.big_list, b.list_counts + 1, err));
 }
 
+int tracklet_resident_blocks() {
+  int dev = 0, sms = 0, per = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_tracklets, 128, 0) != cudaSuccess)
+    return 0;
+  return sms * per;
+}
+
 void launch_find(Prof* P, const Geo& g, const Cal& c, const Params& p, const ClIn& cl,
                  const GridDims& gd, int K, FindBuf& b, TrackBuf& tb, uint32_t* cnt,
                  uint32_t* err, cudaStream_t s) {
@@ -1029,19 +1095,28 @@ void launch_find(Prof* P, const Geo& g, const Cal& c, const Params& p, const ClI
                                    kCntStart, 0, (uint32_t)b.cap_tl, 0u, err, kErrCapStart));
   if (n > 0)
     TPC_LAUNCH(P, "k_write_starts", s, k_write_starts<<<nb, kB256, 0, s>>>(b.row_start + K, b.upc, b.dnc, b.off_a,
-                                        (uint32_t)b.cap_tl, b.starts));
+                                        (uint32_t)b.cap_tl, p.seed_max_hits, b.starts, b.seed_end));
   cudaMemsetAsync(b.weight, 0, sizeof(unsigned long long) * (size_t)(n > 0 ? n : 1), s);
   Grid G{b.gyz, b.gorig, b.bin_start, b.zr};
+  // persistent grid: the resident blocks, or fewer for a small capacity
   int ntl_blk = nblk(b.cap_tl, 128);
-  TPC_LAUNCH(P, "k_tracklets", s, k_tracklets<<<ntl_blk, 128, 0, s>>>(g, c, p, gd, G, b.es_dims, cl.mode, b.upc, b.gseg, b.starts, cnt, b.nh,
-                                      b.hits, b.that, b.weight));
+  if (b.tl_blocks > 0 && ntl_blk > b.tl_blocks) ntl_blk = b.tl_blocks;
+  cudaMemsetAsync(b.queue, 0, sizeof(uint32_t), s);
+  TPC_LAUNCH(P, "k_tracklets", s,
+             k_tracklets<<<ntl_blk, 128, 0, s>>>(g, c, p, gd, G, b.es_dims, cl.mode, b.upc, b.gseg,
+                                                 b.starts, b.seed_end, cnt, b.nh, b.hits,
+                                                 b.range, b.that, b.queue));
+  TPC_LAUNCH(P, "k_tl_weight", s,
+             k_tl_weight<<<nblk(b.cap_tl * 32, kB256), kB256, 0, s>>>(
+                 g.n_rows, p.min_track_hits, cnt, b.nh, b.hits, b.range, b.starts, b.gorig,
+                 b.weight));
   int nsel = nblk(b.cap_tl, kB256);
-  TPC_LAUNCH(P, "k_select_count", s, k_select_count<<<nsel, kB256, 0, s>>>(g.n_rows, p, cnt, b.nh, b.hits, b.starts, b.gorig,
+  TPC_LAUNCH(P, "k_select_count", s, k_select_count<<<nsel, kB256, 0, s>>>(g.n_rows, p, cnt, b.nh, b.hits, b.range, b.starts, b.gorig,
                                         b.weight, b.nkeep, b.blk_a, b.blk_b));
   TPC_LAUNCH(P, "k_scan_blocks", s, k_scan_blocks<<<1, 1024, 0, s>>>(nsel, b.blk_a, b.off_a, b.blk_b, b.off_b, cnt, kCntTracks,
                                    kCntAssigned, (uint32_t)tb.cap_tr, (uint32_t)tb.cap_asg, err,
                                    kErrCapTrack));
-  TPC_LAUNCH(P, "k_select_write", s, k_select_write<<<nsel, kB256, 0, s>>>(g.n_rows, cnt, b.hits, b.starts, b.that, b.gorig,
+  TPC_LAUNCH(P, "k_select_write", s, k_select_write<<<nsel, kB256, 0, s>>>(g.n_rows, cnt, b.hits, b.range, b.starts, b.that, b.gorig,
                                         b.weight, b.nh, b.nkeep, b.off_a, b.off_b, tb.cap_tr,
                                         tb.cap_asg, tb.track_start, tb.cluster_idx, tb.asg_track,
                                         tb.t_coll, tb.start_hit));
@@ -1085,8 +1160,8 @@ void launch_export_tracklets(const FindBuf& b, int n_rows, int64_t n_cap, const 
   int64_t m = n_cap < b.cap_tl ? n_cap : b.cap_tl;
   if (m > 0)
     k_export_tracklets<<<nblk(m, kB256), kB256, 0, s>>>(n_rows, m, cnt, b.gorig, b.starts, b.nh,
-                                                        b.that, b.hits, start_hit, nh, that,
-                                                        hits);
+                                                        b.that, b.hits, b.range, start_hit, nh,
+                                                        that, hits);
 }
 
 }  // namespace tpc

@@ -104,6 +104,10 @@ struct FindBuf {
   double* that;         // [cap_tl]
   unsigned long long* weight;  // [n]
   uint32_t* nkeep;      // [cap_tl]
+  uint32_t* queue;      // [1] next start hit of the persistent tracklet kernel
+  uint32_t* seed_end;   // [cap_tl] last hit of each start hit's seed
+  uint32_t* range;      // [cap_tl] rows lo | hi << 16 of hits[] the tracklet wrote
+  int tl_blocks;        // resident blocks of the persistent tracklet kernel
   int64_t cap_tl;
 };
 
@@ -140,7 +144,8 @@ struct RefitBuf {
   float* gyc;             // [cap_w] dL/d(calibrated y), interleaved
   float* gzc;             // [cap_w]
   int64_t cap_w;          // interleaved capacity: cap_asg + 32 * 257
-  float* part_spline;     // [n_part_blocks * TPC_SPLINE_SIZE]
+  unsigned long long* acc_spline;  // [TPC_SPLINE_SIZE] fixed-point spline-gradient sums
+  uint32_t* gmax;         // [1] largest |coordinate gradient| (float bits)
   double* part_cal;       // [n_part_blocks * 2]
   int64_t cap_ckpt;
 };
@@ -210,11 +215,12 @@ struct Prof {
 
 constexpr int kSortTile = 4096;      // pad-row bucket tile of the common sort
 constexpr int kSortTileBig = 16384;  // tile of the large-bucket sort (128 KB)
-constexpr int kCalibGradBlocks = 148;
+constexpr int kCalibGradBlocks = 4 * 148;
 
 // launchers (tpc_find.cu)
 void launch_load(Prof* P, const Geo& g, const Cal& c, const ClIn& cl, const GridDims& gd, int K,
                  FindBuf& b, uint32_t* err, cudaStream_t s);
+int tracklet_resident_blocks();
 void launch_find(Prof* P, const Geo& g, const Cal& c, const Params& p, const ClIn& cl,
                  const GridDims& gd, int K, FindBuf& b, TrackBuf& tb, uint32_t* cnt,
                  uint32_t* err, cudaStream_t s);

@@ -11,10 +11,13 @@
 //              its checkpoint. The transport Jacobian depends on the state,
 //              so its second-order term is formed with a forward-mode dual
 //              number in (sin phi, tan lambda, q/pT).
-// k_calib_grad persistent blocks: chain rule through the calibration
-//              transform (drift time to z, distortion spline); spline
-//              gradients accumulate in shared memory per block.
-// k_calib_reduce sums the per-block partials in float64.
+// k_calib_grad one warp per range of assigned clusters: chain rule through
+//              the calibration transform (drift time to z, distortion
+//              spline); spline gradients summed in registers per cell and
+//              added to 64-bit fixed-point totals, so that the gradient is
+//              reproducible bit for bit.
+// k_calib_reduce sums the float64 (v_drift, t0) partials in block order and
+//              converts the spline sums back to float64.
 #include "tpc_impl.h"
 #include "tpc_refit_core.cuh"
 
@@ -208,7 +211,7 @@ __global__ void __launch_bounds__(kB) k_refit_bwd(Geo g, RefitCfg p, const uint3
                                                    const uint32_t* track_start, TrackIn win,
                                                    const uint8_t* rej, const int32_t* status,
                                                    const float* ckpt, const float* dl_dchi2,
-                                                   float* gyc, float* gzc) {
+                                                   float* gyc, float* gzc, uint32_t* gmax) {
   int tid = blockIdx.x * blockDim.x + threadIdx.x;
   if (tid >= (int)cnt[kCntTracks]) return;
   int T = (int)order[tid];
@@ -223,69 +226,132 @@ __global__ void __launch_bounds__(kB) k_refit_bwd(Geo g, RefitCfg p, const uint3
     return;
   }
   refit_backward_track(g, p, win, ly, n, rej, ckpt, dl_dchi2[T], gyc, gzc);
+  // largest |gradient| (as float bits, so that NaN ranks above infinity)
+  uint32_t m = 0u;
+  for (int k = 0; k < n; ++k) {
+    m = max(m, __float_as_uint(fabsf(gyc[ly.at(k)])));
+    m = max(m, __float_as_uint(fabsf(gzc[ly.at(k)])));
+  }
+  if (m) atomicMax(gmax, m);
+}
+
+// Fixed-point exponent of the spline-gradient sums: every partial sum of
+// coefficient contributions is bounded by n_assigned * max|gradient| (the
+// B-spline weights of a point sum to one), which is kept below 2^61.
+// Returns false when that maximum is not finite.
+__device__ __forceinline__ bool grad_fixed_exponent(uint32_t gmax_bits, int n_asg, int& k) {
+  float m = __uint_as_float(gmax_bits);
+  if (!isfinite(m)) return false;
+  k = 0;
+  if (m > 0.0f) {
+    int e = 0;
+    frexp((double)m * (double)(n_asg > 0 ? n_asg : 1), &e);
+    k = 61 - e;
+  }
+  return true;
 }
 
 // Chain rule through the calibration transform (Sec. 4): calibrated (y, z)
 // -> raw (y, t or z), v_drift, t0 and the spline coefficients.
-__global__ void __launch_bounds__(512) k_calib_grad(Geo g, Cal c, ClIn cl, const uint32_t* cnt,
-                                                     const uint32_t* cluster_idx,
-                                                     const uint32_t* asg_track,
-                                                     const uint32_t* track_start,
-                                                     const uint32_t* slot, const uint32_t* wbase,
-                                                     const double* t_coll, const float* gyc,
-                                                     const float* gzc, float* grad_y,
-                                                     float* grad_zt, float* part_spline,
-                                                     double* part_cal) {
-  extern __shared__ float sacc[];
-  __shared__ double red[2][16];
-  const int NS = TPC_SPLINE_SIZE;
-  // the spline's coefficient gradient is formed even when all coefficients
-  // are zero (the forward then adds exactly zero)
-  bool spl_on = true;
-  for (int i = threadIdx.x; i < NS; i += blockDim.x) sacc[i] = 0.0f;
-  __syncthreads();
+// v * 2^kx rounded to the nearest integer (ties away from zero), by integer
+// arithmetic on the float's fields. |v| * 2^kx < 2^62 by the choice of kx.
+__device__ __forceinline__ long long to_fixed(float v, int kx) {
+  uint32_t b = __float_as_uint(v);
+  int ex = (int)((b >> 23) & 0xffu);
+  long long m = (long long)(b & 0x7fffffu);
+  if (ex) m |= 0x800000ll;
+  int sh = (ex ? ex : 1) - 150 + kx;
+  long long q;
+  if (sh >= 0) q = m << sh;
+  else if (sh > -26) q = (m + (1ll << (-sh - 1))) >> (-sh);
+  else q = 0;
+  return (b >> 31) ? -q : q;
+}
+
+// One warp per contiguous range of assigned clusters (tracks are contiguous
+// and row-ordered in it). Lanes first take one cluster each: its coordinate
+// gradients through the calibration, its spline cell and B-spline weights.
+// The warp then walks the clusters in order; lane l owns two of the 64
+// coefficients of the current cell (and both components) and sums their
+// contributions in registers while the cell stays the same, which along a
+// track it does for many rows. On a change of cell the sums go to the global
+// 64-bit fixed-point totals. Every sum has a fixed order and integer
+// additions commute, so the gradient is reproducible bit for bit.
+constexpr int kCgThreads = 256;
+__global__ void __launch_bounds__(kCgThreads) k_calib_grad(
+    Geo g, Cal c, ClIn cl, const uint32_t* cnt, const uint32_t* cluster_idx,
+    const uint32_t* asg_track, const uint32_t* track_start, const uint32_t* slot,
+    const uint32_t* wbase, const double* t_coll, const float* gyc, const float* gzc,
+    const uint32_t* gmax, float* grad_y, float* grad_zt, unsigned long long* acc_spline,
+    double* part_cal) {
+  __shared__ double red[2][kCgThreads / 32];
+  constexpr int kComp = kSpl * kSpl * kSpl;
   int n = (int)cnt[kCntAssigned];
-  int per = (n + gridDim.x - 1) / gridDim.x;
-  int j0 = blockIdx.x * per, j1 = min(n, j0 + per);
-  int len = j1 - j0;
-  int nthr = blockDim.x;
+  int kx = 0;
+  // a non-finite gradient leaves the spline sums to k_calib_reduce (NaN)
+  const bool fixed_ok = grad_fixed_exponent(*gmax, n, kx);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int nwarps = gridDim.x * (kCgThreads / 32);
+  const int gw = blockIdx.x * (kCgThreads / 32) + w;
+  int per = (n + nwarps - 1) / nwarps;
+  int jb = gw * per, je = min(n, jb + per);
   double avd = 0.0, at0 = 0.0;
-  // lane-strided order so that the lanes of a warp work on different tracks
-  int lanes = 32, warps = nthr / 32;
-  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  int sub = (len + lanes - 1) / lanes;
-  for (int k = w; k < sub; k += warps) {
-    int jj = lane * sub + k;
-    if (jj >= len) continue;
-    int j = j0 + jj;
-    uint32_t i = cluster_idx[j];
-    uint32_t T = asg_track[j];
-    double that = t_coll[T];
-    uint32_t sl = slot[T];
-    size_t wpos = ((size_t)wbase[sl >> 5] + (j - track_start[T])) * 32 + (sl & 31);
-    int r = cl.row[i], s = cl.sector[i];
-    float x = g.row_x[r];
-    float y = cl.y[i];
-    float za = abs_z(g, c, cl.mode, cl.mode == 0 ? cl.z[i] : 0.0f, cl.mode == 1 ? cl.t[i] : 0.0,
-                     s, that);
-    float by = gyc[wpos], bz = gzc[wpos];
-    float gy = by, gza = bz;
-    if (spl_on) {
+  const float kS = (float)(kSpl - 3);
+  // this lane's two coefficients of a cell: (w, v, u) offsets (cc, bb, aa)
+  // with cc = lane / 16 and cc + 2
+  const int aa = lane & 3, bb = (lane >> 2) & 3, cc1 = lane >> 4;
+  const int off1 = (cc1 * kSpl + bb) * kSpl + aa;
+  const int off2 = off1 + 2 * kSpl * kSpl;
+  float a01 = 0.f, a02 = 0.f, a11 = 0.f, a12 = 0.f;  // [component][coefficient]
+  int cur = -1;                                        // cell base of the sums
+  auto flush = [&]() {
+    long long q;
+    if ((q = to_fixed(a01, kx)) != 0) atomicAdd(&acc_spline[cur + off1], (unsigned long long)q);
+    if ((q = to_fixed(a02, kx)) != 0) atomicAdd(&acc_spline[cur + off2], (unsigned long long)q);
+    if ((q = to_fixed(a11, kx)) != 0)
+      atomicAdd(&acc_spline[cur + kComp + off1], (unsigned long long)q);
+    if ((q = to_fixed(a12, kx)) != 0)
+      atomicAdd(&acc_spline[cur + kComp + off2], (unsigned long long)q);
+    a01 = a02 = a11 = a12 = 0.f;
+  };
+  for (int b0 = jb; b0 < je; b0 += 32) {
+    int j = b0 + lane;
+    bool valid = j < je;
+    float by = 0.0f, bz = 0.0f;
+    int o0 = 0;
+    float bu[4] = {0.f, 0.f, 0.f, 0.f}, bv[4] = {0.f, 0.f, 0.f, 0.f};
+    float bw[4] = {0.f, 0.f, 0.f, 0.f};
+    if (valid) {
+      uint32_t i = cluster_idx[j];
+      uint32_t T = asg_track[j];
+      double that = t_coll[T];
+      uint32_t sl = slot[T];
+      size_t wpos = ((size_t)wbase[sl >> 5] + (j - track_start[T])) * 32 + (sl & 31);
+      int r = cl.row[i], s = cl.sector[i];
+      float x = g.row_x[r];
+      float y = cl.y[i];
+      float za = abs_z(g, c, cl.mode, cl.mode == 0 ? cl.z[i] : 0.0f,
+                       cl.mode == 1 ? cl.t[i] : 0.0, s, that);
+      by = gyc[wpos];
+      bz = gzc[wpos];
       float ur = (x - c.spl_x0) / c.spl_dx;
       float vr = (y / x + g.tan_half) / (2.0f * g.tan_half);
       float wr = fabsf(za) / g.L;
-      float u = clamp01(ur), v = clamp01(vr), w = clamp01(wr);
-      float dvdy = (vr > 0.0f && vr < 1.0f) ? 1.0f / (x * (2.0f * g.tan_half)) : 0.0f;
-      float dwdz = (wr > 0.0f && wr < 1.0f) ? (za >= 0.0f ? 1.0f : -1.0f) / g.L : 0.0f;
+      float u = clamp01(ur), v = clamp01(vr), wv = clamp01(wr);
       int iu, iv, iw;
       float fu, fv, fw;
       spline_split(u, iu, fu);
       spline_split(v, iv, fv);
-      spline_split(w, iw, fw);
-      float bu[4], bv[4], bw[4], dbv[4], dbw[4];
+      spline_split(wv, iw, fw);
       spline_basis(fu, bu);
       spline_basis(fv, bv);
       spline_basis(fw, bw);
+      o0 = s * 2 * kComp + (iw * kSpl + iv) * kSpl + iu;
+      // gradient through the distortion itself: d(spline)/d(y, z) of both
+      // components, and the drift-time chain for v_drift and t0
+      float dvdy = (vr > 0.0f && vr < 1.0f) ? 1.0f / (x * (2.0f * g.tan_half)) : 0.0f;
+      float dwdz = (wr > 0.0f && wr < 1.0f) ? (za >= 0.0f ? 1.0f : -1.0f) / g.L : 0.0f;
+      float dbv[4], dbw[4];
       auto dbasis = [](float f, float d[4]) {
         float gg = 1.0f - f;
         d[0] = -0.5f * gg * gg;
@@ -295,39 +361,63 @@ __global__ void __launch_bounds__(512) k_calib_grad(Geo g, Cal c, ClIn cl, const
       };
       dbasis(fv, dbv);
       dbasis(fw, dbw);
-      const float kS = (float)(kSpl - 3);
       float dval_dv[2] = {0.f, 0.f}, dval_dw[2] = {0.f, 0.f};
-      for (int comp = 0; comp < 2; ++comp) {
-        float cb = comp == 0 ? by : bz;
-        int base = ((s * 2 + comp) * kSpl) * kSpl * kSpl;
-        const float* cf = c.spline + base;
+      for (int cp = 0; cp < 2; ++cp) {
+        const float* cf = c.spline + (s * 2 + cp) * kComp;
         for (int cc = 0; cc < 4; ++cc)
-          for (int bb = 0; bb < 4; ++bb) {
-            int o = ((iw + cc) * kSpl + (iv + bb)) * kSpl + iu;
-            for (int aa = 0; aa < 4; ++aa) {
-              float coef = cf[o + aa];
-              dval_dv[comp] += bw[cc] * dbv[bb] * bu[aa] * coef;
-              dval_dw[comp] += dbw[cc] * bv[bb] * bu[aa] * coef;
-              if (cb != 0.0f) atomicAdd(&sacc[base + o + aa], cb * (bw[cc] * bv[bb] * bu[aa]));
+          for (int b2 = 0; b2 < 4; ++b2) {
+            int o = ((iw + cc) * kSpl + (iv + b2)) * kSpl + iu;
+            for (int a2 = 0; a2 < 4; ++a2) {
+              float coef = cf[o + a2];
+              dval_dv[cp] += bw[cc] * dbv[b2] * bu[a2] * coef;
+              dval_dw[cp] += dbw[cc] * bv[b2] * bu[a2] * coef;
             }
           }
       }
       float dDy_dy = dval_dv[0] * kS * dvdy, dDz_dy = dval_dv[1] * kS * dvdy;
       float dDy_dz = dval_dw[0] * kS * dwdz, dDz_dz = dval_dw[1] * kS * dwdz;
-      gy = by * (1.0f + dDy_dy) + bz * dDz_dy;
-      gza = by * dDy_dz + bz * (1.0f + dDz_dz);
+      float gy = by * (1.0f + dDy_dy) + bz * dDz_dy;
+      float gza = by * dDy_dz + bz * (1.0f + dDz_dz);
+      grad_y[j] = gy;
+      if (cl.mode == 1) {
+        double sg = s < 18 ? 1.0 : -1.0;
+        grad_zt[j] = (float)((double)gza * (-sg * c.vdrift));
+        avd += (double)gza * (-sg * ((cl.t[i] - c.t0) - that));
+        at0 += (double)gza * (sg * c.vdrift);
+      } else {
+        grad_zt[j] = gza;
+      }
     }
-    grad_y[j] = gy;
-    if (cl.mode == 1) {
-      double sg = s < 18 ? 1.0 : -1.0;
-      grad_zt[j] = (float)((double)gza * (-sg * c.vdrift));
-      avd += (double)gza * (-sg * ((cl.t[i] - c.t0) - that));
-      at0 += (double)gza * (sg * c.vdrift);
-    } else {
-      grad_zt[j] = gza;
+    // spline coefficient gradients, one cluster at a time in cluster order
+    unsigned am = __ballot_sync(0xffffffffu, valid && fixed_ok && (by != 0.0f || bz != 0.0f));
+    while (am) {
+      int src = __ffs(am) - 1;
+      am &= am - 1;
+      int o = __shfl_sync(0xffffffffu, o0, src);
+      if (o != cur) {  // uniform over the warp
+        if (cur >= 0) flush();
+        cur = o;
+      }
+      float cy = __shfl_sync(0xffffffffu, by, src);
+      float cz = __shfl_sync(0xffffffffu, bz, src);
+      float u0 = __shfl_sync(0xffffffffu, bu[0], src), u1 = __shfl_sync(0xffffffffu, bu[1], src);
+      float u2 = __shfl_sync(0xffffffffu, bu[2], src), u3 = __shfl_sync(0xffffffffu, bu[3], src);
+      float v0 = __shfl_sync(0xffffffffu, bv[0], src), v1 = __shfl_sync(0xffffffffu, bv[1], src);
+      float v2 = __shfl_sync(0xffffffffu, bv[2], src), v3 = __shfl_sync(0xffffffffu, bv[3], src);
+      float w0 = __shfl_sync(0xffffffffu, bw[0], src), w1 = __shfl_sync(0xffffffffu, bw[1], src);
+      float w2 = __shfl_sync(0xffffffffu, bw[2], src), w3 = __shfl_sync(0xffffffffu, bw[3], src);
+      float ua = aa == 0 ? u0 : aa == 1 ? u1 : aa == 2 ? u2 : u3;
+      float vb = bb == 0 ? v0 : bb == 1 ? v1 : bb == 2 ? v2 : v3;
+      float p1 = (cc1 == 0 ? w0 : w1) * (vb * ua);
+      float p2 = (cc1 == 0 ? w2 : w3) * (vb * ua);
+      a01 += cy * p1;
+      a02 += cy * p2;
+      a11 += cz * p1;
+      a12 += cz * p2;
     }
   }
-  // block reduction of the float64 sums
+  if (cur >= 0) flush();
+  // block reduction of the float64 sums, in a fixed order
   for (int o = 16; o > 0; o >>= 1) {
     avd += __shfl_down_sync(0xffffffffu, avd, o);
     at0 += __shfl_down_sync(0xffffffffu, at0, o);
@@ -339,18 +429,17 @@ __global__ void __launch_bounds__(512) k_calib_grad(Geo g, Cal c, ClIn cl, const
   __syncthreads();
   if (threadIdx.x == 0) {
     double s0 = 0.0, s1 = 0.0;
-    for (int q = 0; q < warps; ++q) {
+    for (int q = 0; q < kCgThreads / 32; ++q) {
       s0 += red[0][q];
       s1 += red[1][q];
     }
     part_cal[blockIdx.x * 2 + 0] = s0;
     part_cal[blockIdx.x * 2 + 1] = s1;
   }
-  float* ps = part_spline + (size_t)blockIdx.x * NS;
-  for (int i = threadIdx.x; i < NS; i += blockDim.x) ps[i] = sacc[i];
 }
 
-__global__ void k_calib_reduce(int nblk, const float* part_spline, const double* part_cal,
+__global__ void k_calib_reduce(int nblk, const uint32_t* cnt, const uint32_t* gmax,
+                               const unsigned long long* acc_spline, const double* part_cal,
                                double* grad_calib) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= TPC_GRAD_CALIB_SIZE) return;
@@ -358,7 +447,11 @@ __global__ void k_calib_reduce(int nblk, const float* part_spline, const double*
   if (i < 2) {
     for (int b = 0; b < nblk; ++b) s += part_cal[b * 2 + i];
   } else {
-    for (int b = 0; b < nblk; ++b) s += (double)part_spline[(size_t)b * TPC_SPLINE_SIZE + (i - 2)];
+    int kx = 0;
+    if (grad_fixed_exponent(*gmax, (int)cnt[kCntAssigned], kx))
+      s = ldexp((double)(long long)acc_spline[i - 2], -kx);
+    else
+      s = __longlong_as_double(0x7ff8000000000000ll);
   }
   grad_calib[i] = s;
 }
@@ -400,25 +493,22 @@ void launch_refit_backward(Prof* P, const Geo& g, const Cal& c, const Params& p,
                            const TrackBuf& tb, RefitBuf& rb, const float* dl_dchi2,
                            float* grad_y, float* grad_zt, double* grad_calib, cudaStream_t s) {
   TrackIn win{tb.track_start, rb.w_yc, rb.w_zc, rb.w_meta};
+  cudaMemsetAsync(rb.gmax, 0, sizeof(uint32_t), s);
+  cudaMemsetAsync(rb.acc_spline, 0, sizeof(unsigned long long) * TPC_SPLINE_SIZE, s);
   if (cap_tr > 0)
     TPC_LAUNCH(P, "k_refit_bwd", s,
                k_refit_bwd<<<nblk(cap_tr, kB), kB, 0, s>>>(g, make_cfg(g, p), cnt, rb.order,
                                                            rb.wbase, rb.wlen, tb.track_start,
                                                            win, rb.rej, rb.status, rb.ckpt,
-                                                           dl_dchi2, rb.gyc, rb.gzc));
-  size_t smem = TPC_SPLINE_SIZE * sizeof(float);
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(k_calib_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    attr_set = true;
-  }
+                                                           dl_dchi2, rb.gyc, rb.gzc, rb.gmax));
   TPC_LAUNCH(P, "k_calib_grad", s,
-             k_calib_grad<<<kCalibGradBlocks, 512, smem, s>>>(
+             k_calib_grad<<<kCalibGradBlocks, kCgThreads, 0, s>>>(
                  g, c, cl, cnt, tb.cluster_idx, tb.asg_track, tb.track_start, rb.slot, rb.wbase,
-                 tb.t_coll, rb.gyc, rb.gzc, grad_y, grad_zt, rb.part_spline, rb.part_cal));
+                 tb.t_coll, rb.gyc, rb.gzc, rb.gmax, grad_y, grad_zt, rb.acc_spline,
+                 rb.part_cal));
   TPC_LAUNCH(P, "k_calib_reduce", s,
              k_calib_reduce<<<nblk(TPC_GRAD_CALIB_SIZE, 256), 256, 0, s>>>(
-                 kCalibGradBlocks, rb.part_spline, rb.part_cal, grad_calib));
+                 kCalibGradBlocks, cnt, rb.gmax, rb.acc_spline, rb.part_cal, grad_calib));
 }
 
 }  // namespace tpc

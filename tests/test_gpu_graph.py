@@ -1,7 +1,6 @@
 """CUDA-graph capture and replay of a whole step through the C ABI."""
 import ctypes as C
 
-import numpy as np
 import pytest
 
 import synth
@@ -66,8 +65,9 @@ def test_graph_replay_equals_direct_run():
         assert torch.equal(b[k][:nt], ref[k][:nt]), k
     assert torch.equal(b["rej"][:na], ref["rej"][:na])
     assert torch.equal(b["gy"][:na], ref["gy"][:na])
-    np.testing.assert_allclose(b["gc"].cpu().numpy(), ref["gc"].cpu().numpy(), rtol=1e-5,
-                               atol=1e-9)
+    # the calibration gradient sums in fixed point: reproducible bit for bit
+    assert torch.equal(b["gc"], ref["gc"])
+    assert torch.equal(b["gz"][:na], ref["gz"][:na])
 
 
 def test_allocation_during_capture_is_refused():
