@@ -43,6 +43,10 @@ def parse():
                     choices=["central", "timeframe", "batched", "single_sector"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default launch shapes instead of tuning them on the workload")
+    ap.add_argument("--tuning", default=None,
+                    help="launch shapes as JSON (tpc_tuning fields), instead of autotuning")
     ap.add_argument("--graph", action="store_true",
                     help="replay each step as one captured CUDA graph")
     ap.add_argument("--profile-steps", type=int, default=0,
@@ -212,6 +216,15 @@ def run_ours(args):
     tr.set_calib()
     cl = tr.upload(ev)
     L, h = tr.L, tr.h
+    if args.tuning:
+        tr.set_tuning(**json.loads(args.tuning))
+        tuning, how = tr.get_tuning(), "given"
+    elif not args.no_autotune:
+        # launch shapes tuned on this workload, before and outside the timed region
+        tr.load(cl)
+        tuning, how = tr.autotune(repeats=3), "autotuned"
+    else:
+        tuning, how = tr.get_tuning(), "default"
     n = ev.n
     cap_tr = n // 10 + 1
     dev = tr.dev
@@ -380,6 +393,7 @@ def run_ours(args):
                 scaling="weak", vs_baseline=None, dtype="f32 (f64 timestamps and gradient sums)",
                 data="synthetic",
                 config=dict(cfg, l2="flushed before every timed step (256 MB write)",
+                            tuning=dict(tuning, chosen=how),
                             parallelism=f"replicas x{world}, one independent event per GPU",
                             launch="one CUDA graph per step" if args.graph else "stream launches"),
                 tracks_per_s=aggregate(total_ms, nt * args.steps, dist, dev)[2],

@@ -177,6 +177,9 @@ tpc_status tpc_load_clusters(tpc_ctx* ctx, const tpc_clusters* cl);
 /* Run the track finder on the loaded batch (neighbours, link cleaning, start
  * hits, tracklets, selection) and the calibration transform of the assigned
  * clusters. Synchronises once to read the track count, then fills *out.
+ * Tracks come ordered by (event, sector, pad row, input index) of their start
+ * hit, whatever the tuning (tpc_set_tuning); tracklets (tpc_get_tracklets)
+ * come in search-grid order, which depends on grid_tau and grid_ny_max.
  * Returns TPC_ERR_CAPACITY if the tracklet buffer overflowed (the next call
  * retries with twice the capacity). */
 tpc_status tpc_find_tracks(tpc_ctx* ctx, tpc_tracks* out);
@@ -294,6 +297,36 @@ typedef struct {
 tpc_status tpc_profile(tpc_ctx* ctx, int enable);
 tpc_status tpc_profile_read(tpc_ctx* ctx, tpc_kernel_stat* out, int32_t cap, int32_t* n_out,
                             int64_t* launches);
+
+/* Launch shapes and tile sizes of the track finder (autotuning). The paper
+ * does not fix them; none of them changes any output bit, only the speed (the
+ * search grid breaks ties by input index, not by bin; tracks are emitted in
+ * an order that does not depend on the grid; the tracklet kernel is built
+ * without contracted multiply-adds, so its block size cannot change rounding).
+ *   grid_tau            target clusters per search-grid bin (0.25 .. 16)
+ *   grid_ny_max         grid bins across a row at most (1 .. 64)
+ *   tracklet_block      threads per block of the tracklet kernel (64, 128, 256)
+ *   tracklet_per_sm     resident tracklet blocks per SM (0 .. 64); 0 = as many
+ *                       as fit
+ * tpc_set_tuning validates (TPC_ERR_ARG) and applies from the next
+ * tpc_load_clusters (grid) or tpc_find_tracks (tracklet kernel);
+ * TPC_ERR_STATE while capturing. tpc_autotune searches one parameter at a
+ * time, in that order, over grid_tau {0.5, 1, 2, 4}, grid_ny_max {8, 16, 32},
+ * tracklet_block {64, 128, 256}, tracklet_per_sm {0, 1, 2, 4}, on the loaded
+ * batch: each candidate runs load + find (grid parameters) or find (tracklet
+ * parameters) `repeats` times (1 .. 50; < 1 means 3) after one untimed run,
+ * timed with CUDA events on the context's stream, and the fastest median is
+ * kept. It synchronises, needs a loaded batch, and leaves the batch loaded
+ * and found with the chosen tuning; out may be NULL. */
+typedef struct {
+  float grid_tau;
+  int32_t grid_ny_max;
+  int32_t tracklet_block;
+  int32_t tracklet_per_sm;
+} tpc_tuning;
+tpc_status tpc_get_tuning(const tpc_ctx* ctx, tpc_tuning* out);
+tpc_status tpc_set_tuning(tpc_ctx* ctx, const tpc_tuning* in);
+tpc_status tpc_autotune(tpc_ctx* ctx, int32_t repeats, tpc_tuning* out);
 
 /* Text of the last error of this context ("" if none). Valid until the next
  * call on the context. */

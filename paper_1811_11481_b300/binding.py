@@ -62,6 +62,14 @@ class tpc_kernel_stat(C.Structure):
     _fields_ = [("name", C.c_char * 32), ("launches", C.c_int64), ("total_ms", C.c_double)]
 
 
+class tpc_tuning(C.Structure):
+    _fields_ = [("grid_tau", C.c_float), ("grid_ny_max", C.c_int32),
+                ("tracklet_block", C.c_int32), ("tracklet_per_sm", C.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class tpc_tracks(C.Structure):
     _fields_ = [("n_tracks", C.c_int64), ("n_assigned", C.c_int64),
                 ("track_start", C.c_void_p), ("cluster_idx", C.c_void_p),
@@ -73,6 +81,9 @@ _PROTOS = {
     "tpc_create": (C.c_int, [C.POINTER(tpc_geometry), C.POINTER(tpc_params), C.c_void_p,
                              C.POINTER(C.c_void_p)]),
     "tpc_destroy": (None, [C.c_void_p]),
+    "tpc_get_tuning": (C.c_int, [C.c_void_p, C.POINTER(tpc_tuning)]),
+    "tpc_set_tuning": (C.c_int, [C.c_void_p, C.POINTER(tpc_tuning)]),
+    "tpc_autotune": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(tpc_tuning)]),
     "tpc_set_calib": (C.c_int, [C.c_void_p, C.POINTER(tpc_calib)]),
     "tpc_load_clusters": (C.c_int, [C.c_void_p, C.POINTER(tpc_clusters)]),
     "tpc_find_tracks": (C.c_int, [C.c_void_p, C.POINTER(tpc_tracks)]),
@@ -345,6 +356,22 @@ class Tracker:
                  "tpc_profile_read")
         return ({buf[i].name.decode(): (int(buf[i].launches), float(buf[i].total_ms))
                  for i in range(min(n.value, 64))}, int(tot.value))
+
+    # ----------------------------------------------------------- tuning
+    def get_tuning(self):
+        t = tpc_tuning()
+        self._ck(self.L.tpc_get_tuning(self.h, C.byref(t)), "tpc_get_tuning")
+        return t.as_dict()
+
+    def set_tuning(self, **kw):
+        t = tpc_tuning(**{**self.get_tuning(), **kw})
+        self._ck(self.L.tpc_set_tuning(self.h, C.byref(t)), "tpc_set_tuning")
+
+    def autotune(self, repeats=3):
+        """Search launch shapes on the loaded batch; returns the chosen tuning."""
+        t = tpc_tuning()
+        self._ck(self.L.tpc_autotune(self.h, int(repeats), C.byref(t)), "tpc_autotune")
+        return t.as_dict()
 
     # ----------------------------------------------------------- introspection
     def links(self):

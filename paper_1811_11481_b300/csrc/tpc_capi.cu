@@ -2,6 +2,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <string>
 
 #include "tpc_impl.h"
@@ -25,6 +26,9 @@ struct tpc_ctx {
   bool loaded = false;
   int K = 0;
   GridDims gd{};
+  tpc_tuning tune{1.0f, 16, 128, 0};
+  Shapes sh{};
+  int sms = 0;
   FindBuf fb{};
   TrackBuf tb{};
   RefitBuf rb{};
@@ -146,6 +150,18 @@ tpc_status read_back(tpc_ctx* ctx) {
   return TPC_OK;
 }
 
+// Launch shapes from the tuning: the persistent tracklet grid is the SM
+// count times the resident blocks per SM (capped by tracklet_per_sm).
+void apply_tuning(tpc_ctx* ctx) {
+  const tpc_tuning& t = ctx->tune;
+  ctx->sh.tl_block = t.tracklet_block;
+  int per = tracklet_blocks_per_sm(t.tracklet_block);
+  if (t.tracklet_per_sm > 0 && t.tracklet_per_sm < per) per = t.tracklet_per_sm;
+  ctx->sh.tl_grid = (ctx->sms > 0 && per > 0) ? ctx->sms * per : 0;
+}
+
+bool valid_block(int b) { return b == 64 || b == 128 || b == 256; }
+
 tpc_status ensure_track_buffers(tpc_ctx* ctx, int64_t cap_tr, int64_t cap_asg) {
   TrackBuf& t = ctx->tb;
   RefitBuf& rb = ctx->rb;
@@ -191,6 +207,12 @@ tpc_status ensure_tracklets(tpc_ctx* ctx) {
     CK(alloc(b.starts, cap));
     CK(alloc(b.seed_end, cap));
     CK(alloc(b.range, cap));
+    CK(alloc(b.tkey, cap));
+    CK(alloc(b.tseg, cap));
+    CK(alloc(b.delta_id, cap));
+    CK(alloc(b.delta_o, cap));
+    b.cap_grp = (uint32_t)(cap / (kSmallGroup + 1) + 1);
+    CK(alloc(b.grp_list, (int64_t)b.cap_grp));
     CK(alloc(b.nh, cap));
     CK(alloc(b.hits, cap * (int64_t)ctx->geo.n_rows));
     CK(alloc(b.that, cap));
@@ -284,8 +306,15 @@ tpc_status tpc_create(const tpc_geometry* geo, const tpc_params* params, void* s
   chk(cudaMalloc(&ctx->fb.list_counts, sizeof(uint32_t) * 2));
   chk(cudaMalloc(&ctx->fb.n_bins, sizeof(uint32_t)));
   chk(cudaMalloc(&ctx->fb.queue, sizeof(uint32_t)));
+  chk(cudaMalloc(&ctx->fb.grp_count, sizeof(uint32_t)));
   chk(cudaMallocHost(&ctx->h_pinned, sizeof(uint32_t) * (kCntSize + 1)));
-  ctx->fb.tl_blocks = tracklet_resident_blocks();
+  {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, dev);
+  }
+  apply_tuning(ctx);
+  setup_find_kernels();
   if (st != TPC_OK) {
     tpc_destroy(ctx);
     return st;
@@ -318,7 +347,7 @@ void tpc_destroy(tpc_ctx* ctx) {
                   ctx->fb.gorig, ctx->fb.gseg, ctx->fb.bin_start, ctx->fb.big_list, ctx->fb.mid_list, ctx->fb.list_counts,
                   ctx->fb.n_bins, ctx->fb.es_dims, ctx->fb.queue, ctx->fb.up, ctx->fb.dn,
                   ctx->fb.upc, ctx->fb.dnc, ctx->fb.blk_a, ctx->fb.blk_b, ctx->fb.off_a,
-                  ctx->fb.off_b, ctx->fb.starts, ctx->fb.seed_end, ctx->fb.range, ctx->fb.nh, ctx->fb.hits, ctx->fb.that,
+                  ctx->fb.off_b, ctx->fb.starts, ctx->fb.seed_end, ctx->fb.range, ctx->fb.tkey, ctx->fb.tseg, ctx->fb.delta_id, ctx->fb.delta_o, ctx->fb.grp_list, ctx->fb.grp_count, ctx->fb.nh, ctx->fb.hits, ctx->fb.that,
                   ctx->fb.weight, ctx->fb.nkeep, ctx->tb.track_start, ctx->tb.cluster_idx,
                   ctx->tb.asg_track, ctx->tb.t_coll, ctx->tb.start_hit, ctx->tb.yc, ctx->tb.zc,
                   ctx->tb.meta, ctx->rb.seed, ctx->rb.order, ctx->rb.slot, ctx->rb.wlen, ctx->rb.wbase, ctx->rb.len_hist,
@@ -352,6 +381,8 @@ tpc_status tpc_set_calib(tpc_ctx* ctx, const tpc_calib* calib) {
   return TPC_OK;
 }
 
+tpc_status prepare_load(tpc_ctx* ctx, int n_events);
+
 tpc_status tpc_load_clusters(tpc_ctx* ctx, const tpc_clusters* in) {
   if (!ctx || !in) return fail(ctx, TPC_ERR_ARG, "null argument");
   if (in->n < 0 || in->n >= (int64_t)1 << 31) return fail(ctx, TPC_ERR_ARG, "n out of range");
@@ -373,13 +404,19 @@ tpc_status tpc_load_clusters(tpc_ctx* ctx, const tpc_clusters* in) {
   ctx->cl.flags = in->flags;
   ctx->cl.event = in->event;
   ctx->cal.tf_start = in->mode == 1 ? in->tf_start : 0.0;
-  int64_t n = in->n;
-  int K = in->n_events * TPC_N_SECTORS * ctx->geo.n_rows;
-  ctx->K = K;
-  // search grid: about one cluster per bin, geometry chosen on the device
-  ctx->gd.tau = 1.0f;
+  ctx->K = in->n_events * TPC_N_SECTORS * ctx->geo.n_rows;
+  return prepare_load(ctx, in->n_events);
+}
+
+// Capacities for the loaded batch and the load kernels (row bucketing, search
+// grid). Also used by the autotuner to rebuild the grid of the same batch.
+tpc_status prepare_load(tpc_ctx* ctx, int n_events) {
+  int64_t n = ctx->cl.n;
+  int K = ctx->K;
+  // search grid: the tuned clusters per bin, geometry chosen on the device
+  ctx->gd.tau = ctx->tune.grid_tau;
   ctx->gd.nb_max = 8192;
-  ctx->gd.ny_max = 16;
+  ctx->gd.ny_max = ctx->tune.grid_ny_max;
   ctx->gd.y_margin = 2.0f;
   ctx->gd.z_margin = 1.0f;
   FindBuf& b = ctx->fb;
@@ -417,11 +454,11 @@ tpc_status tpc_load_clusters(tpc_ctx* ctx, const tpc_clusters* in) {
     CK(alloc(b.fill, K));
     ctx->cap_K = K;
   }
-  if (in->n_events > ctx->cap_ev) {
-    CK(alloc(b.zmm, (int64_t)in->n_events * 4));
-    CK(alloc(b.zr, (int64_t)in->n_events * 4));
-    CK(alloc(b.es_dims, (int64_t)in->n_events * TPC_N_SECTORS));
-    ctx->cap_ev = in->n_events;
+  if (n_events > ctx->cap_ev) {
+    CK(alloc(b.zmm, (int64_t)n_events * 4));
+    CK(alloc(b.zr, (int64_t)n_events * 4));
+    CK(alloc(b.es_dims, (int64_t)n_events * TPC_N_SECTORS));
+    ctx->cap_ev = n_events;
   }
   // per row: nb + 1 <= total / (rows * tau) + ny_max + 1 entries
   int64_t nbins = (int64_t)((double)n / ctx->gd.tau) + (int64_t)K * (ctx->gd.ny_max + 2) + 64;
@@ -447,7 +484,7 @@ tpc_status tpc_find_tracks_async(tpc_ctx* ctx) {
   if (!ctx->loaded) return fail(ctx, TPC_ERR_STATE, "no batch loaded");
   tpc_status st = ensure_tracklets(ctx);
   if (st != TPC_OK) return st;
-  launch_find(&ctx->prof, ctx->geo, ctx->cal, ctx->prm, ctx->cl, ctx->gd, ctx->K, ctx->fb, ctx->tb,
+  launch_find(&ctx->prof, ctx->geo, ctx->cal, ctx->prm, ctx->cl, ctx->gd, ctx->sh, ctx->K, ctx->fb, ctx->tb,
               ctx->d_cnt, ctx->d_err, ctx->stream);
   CK(cudaGetLastError());
   ctx->tracks_valid = true;
@@ -696,3 +733,120 @@ tpc_status tpc_profile_read(tpc_ctx* ctx, tpc_kernel_stat* out, int32_t cap, int
 const char* tpc_last_error(const tpc_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------- tuning
+tpc_status tpc_get_tuning(const tpc_ctx* ctx, tpc_tuning* out) {
+  if (!ctx || !out) return TPC_ERR_ARG;
+  *out = ctx->tune;
+  return TPC_OK;
+}
+
+tpc_status tpc_set_tuning(tpc_ctx* ctx, const tpc_tuning* in) {
+  if (!ctx || !in) return fail(ctx, TPC_ERR_ARG, "null argument");
+  if (ctx->capturing) return fail(ctx, TPC_ERR_STATE, "tuning changes during graph capture");
+  if (!(in->grid_tau >= 0.25f && in->grid_tau <= 16.0f) || in->grid_ny_max < 1 ||
+      in->grid_ny_max > 64 || !valid_block(in->tracklet_block) || in->tracklet_per_sm < 0 ||
+      in->tracklet_per_sm > 64)
+    return fail(ctx, TPC_ERR_ARG, "tuning out of range");
+  ctx->tune = *in;
+  apply_tuning(ctx);
+  return TPC_OK;
+}
+
+namespace {
+
+// Median device time (ms) of `repeats` runs of op after one untimed run.
+template <class Op>
+tpc_status time_median(tpc_ctx* ctx, int repeats, Op op, float* ms_out) {
+  cudaEvent_t a = nullptr, b = nullptr;
+  CK(cudaEventCreate(&a));
+  if (cudaEventCreate(&b) != cudaSuccess) {
+    cudaEventDestroy(a);
+    return fail(ctx, TPC_ERR_CUDA, "event create");
+  }
+  std::vector<float> t;
+  tpc_status st = TPC_OK;
+  for (int i = 0; i <= repeats && st == TPC_OK; ++i) {
+    cudaEventRecord(a, ctx->stream);
+    st = op();
+    cudaEventRecord(b, ctx->stream);
+    if (st == TPC_OK) st = read_back(ctx);
+    float ms = 0.0f;
+    if (st == TPC_OK && cudaEventElapsedTime(&ms, a, b) == cudaSuccess && i > 0) t.push_back(ms);
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if (st != TPC_OK) return st;
+  std::sort(t.begin(), t.end());
+  *ms_out = t.empty() ? 0.0f : t[t.size() / 2];
+  return TPC_OK;
+}
+
+}  // namespace
+
+tpc_status tpc_autotune(tpc_ctx* ctx, int32_t repeats, tpc_tuning* out) {
+  if (!ctx) return TPC_ERR_ARG;
+  if (ctx->capturing) return fail(ctx, TPC_ERR_STATE, "autotune during graph capture");
+  if (!ctx->loaded) return fail(ctx, TPC_ERR_STATE, "no batch loaded");
+  if (repeats < 1) repeats = 3;
+  if (repeats > 50) repeats = 50;
+  // the tuner's own launches are not traced
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->prof.collect();
+  bool prof_on = ctx->prof.on;
+  int64_t launches = ctx->prof.launches;
+  ctx->prof.on = false;
+  // settle the tracklet capacity on this batch (one retry on overflow)
+  tpc_status st = tpc_find_tracks(ctx, nullptr);
+  int n_events = ctx->cl.n_events;
+  auto load_find = [&]() -> tpc_status {
+    tpc_status s = prepare_load(ctx, n_events);
+    return s == TPC_OK ? tpc_find_tracks_async(ctx) : s;
+  };
+  auto find = [&]() -> tpc_status { return tpc_find_tracks_async(ctx); };
+  // one parameter at a time, in pipeline order; each keeps the best so far
+  const float taus[] = {0.5f, 1.0f, 2.0f, 4.0f};
+  const int nys[] = {8, 16, 32};
+  const int blocks[] = {64, 128, 256};
+  const int pers[] = {0, 1, 2, 4};
+  tpc_tuning best = ctx->tune;
+  auto trial = [&](tpc_tuning cand, int which, float* ms) -> tpc_status {
+    ctx->tune = cand;
+    apply_tuning(ctx);
+    return which == 0 ? time_median(ctx, repeats, load_find, ms)
+                      : time_median(ctx, repeats, find, ms);
+  };
+  for (int knob = 0; knob < 4 && st == TPC_OK; ++knob) {
+    float best_ms = 0.0f;
+    tpc_tuning keep = best;
+    int nc = knob == 0 ? 4 : knob == 1 ? 3 : knob == 2 ? 3 : 4;
+    for (int k = 0; k < nc && st == TPC_OK; ++k) {
+      tpc_tuning cand = best;
+      if (knob == 0) cand.grid_tau = taus[k];
+      else if (knob == 1) cand.grid_ny_max = nys[k];
+      else if (knob == 2) cand.tracklet_block = blocks[k];
+      else if (knob == 3) {
+        int mx = tracklet_blocks_per_sm(cand.tracklet_block);
+        if (pers[k] > 0 && pers[k] >= mx) continue;  // same as "as many as fit"
+        cand.tracklet_per_sm = pers[k];
+      }
+      float ms = 0.0f;
+      st = trial(cand, knob <= 1 ? 0 : 1, &ms);
+      if (st == TPC_OK && (best_ms == 0.0f || ms < best_ms)) {
+        best_ms = ms;
+        keep = cand;
+      }
+    }
+    best = keep;
+  }
+  // leave the batch loaded and found with the chosen tuning
+  ctx->tune = best;
+  apply_tuning(ctx);
+  if (st == TPC_OK) st = prepare_load(ctx, n_events);
+  if (st == TPC_OK) st = tpc_find_tracks(ctx, nullptr);
+  if (st == TPC_OK) CK(cudaStreamSynchronize(ctx->stream));
+  ctx->prof.on = prof_on;
+  ctx->prof.launches = launches;
+  if (out) *out = best;
+  return st;
+}

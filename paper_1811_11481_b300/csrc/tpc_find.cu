@@ -664,7 +664,8 @@ __device__ int pick(const Geo& g, const Cal& c, const Params& p, const GridDims&
 //   phase 3: inward following from the outermost pick down to row 0
 enum : int { kSeed1 = 0, kSeed2 = 1, kOut = 2, kIn = 3, kDone = 4 };
 
-__global__ void __launch_bounds__(128) k_tracklets(Geo g, Cal c, Params p, GridDims gd, Grid G,
+template <int BS>
+__global__ void __launch_bounds__(BS) k_tracklets(Geo g, Cal c, Params p, GridDims gd, Grid G,
                                                   const uint2* es_dims, int mode,
                                                   const int32_t* upc,
                                                   const uint32_t* gseg, const uint32_t* starts,
@@ -852,10 +853,27 @@ __global__ void k_tl_weight(int n_rows, int min_track_hits, const uint32_t* cnt,
 __global__ void k_select_count(int n_rows, const Params p, const uint32_t* cnt,
                                const int32_t* nh, const int32_t* hits, const uint32_t* range,
                                const uint32_t* starts, const uint32_t* gorig,
-                               const unsigned long long* weight, uint32_t* nkeep,
+                               const uint32_t* gseg, const unsigned long long* weight,
+                               uint32_t* nkeep, uint32_t* tkey, uint32_t* tseg,
+                               uint32_t* grp_list, uint32_t* grp_count, uint32_t cap_grp,
                                uint32_t* blk_tr, uint32_t* blk_cl) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   uint32_t emit = 0, kept = 0;
+  const int ntl = (int)cnt[kCntStart];
+  if (t < ntl) {
+    // (event, sector, row) and input index of the start hit, for the order
+    // of emission; the first tracklet of a group of more than kSmallGroup
+    // lists the group for k_group_rank
+    uint32_t h0 = starts[t];
+    uint32_t seg = gseg[h0];
+    tkey[t] = gorig[h0];
+    tseg[t] = seg;
+    if ((t == 0 || gseg[starts[t - 1]] != seg) && t + kSmallGroup < ntl &&
+        gseg[starts[t + kSmallGroup]] == seg) {
+      uint32_t q = atomicAdd(grp_count, 1u);
+      if (q < cap_grp) grp_list[q] = (uint32_t)t;
+    }
+  }
   if (t < (int)cnt[kCntStart] && nh[t] >= p.min_track_hits) {
     unsigned long long w = ((unsigned long long)(uint32_t)nh[t] << 32) |
                            (unsigned long long)(0xffffffffu - gorig[starts[t]]);
@@ -885,8 +903,117 @@ __global__ void k_select_count(int n_rows, const Params p, const uint32_t* cnt,
   }
 }
 
+// Emission order inside the groups of more than kSmallGroup tracklets: one
+// block per group sorts the emitted tracklets by start-hit input index
+// (bitonic sort in shared memory) and stores, per tracklet, how far its track
+// moves from the tracklet order: delta_id (tracks) and delta_o (clusters).
+// Groups of more than kRankTile emitted tracklets are marked (kUnranked) and
+// left to the scan in k_select_write.
+constexpr uint32_t kUnranked = 0x80000000u;
+constexpr size_t kRankSmem = (size_t)kRankTile * (sizeof(unsigned long long) + 3 * sizeof(uint32_t));
+__global__ void __launch_bounds__(1024) k_group_rank(const uint32_t* cnt, const uint32_t* tkey,
+                                                     const uint32_t* tseg, const uint32_t* nkeep,
+                                                     const uint32_t* grp_list,
+                                                     const uint32_t* grp_count, uint32_t cap_grp,
+                                                     int32_t* delta_id, int32_t* delta_o) {
+  extern __shared__ unsigned long long skey[];           // [kRankTile]
+  uint32_t* sidx = reinterpret_cast<uint32_t*>(skey + kRankTile);  // local index
+  uint32_t* skept = sidx + kRankTile;                     // kept, index order
+  uint32_t* spre = skept + kRankTile;                     // kept prefix, index order
+  __shared__ uint32_t carry_n, carry_k;
+  const int ntl = (int)cnt[kCntStart];
+  const uint32_t ng = min(*grp_count, cap_grp);
+  for (uint32_t gi = blockIdx.x; gi < ng; gi += gridDim.x) {
+    const int head = (int)grp_list[gi];
+    const uint32_t seg = tseg[head];
+    // end of the group: tseg is non-decreasing
+    int lo = head, hi = ntl;
+    while (hi - lo > 1) {
+      int mid = (lo + hi) >> 1;
+      if (tseg[mid] == seg) lo = mid;
+      else hi = mid;
+    }
+    const int m = hi - head;
+    // emitted tracklets in index order, with their cluster-count prefix
+    if (threadIdx.x == 0) carry_n = carry_k = 0u;
+    __syncthreads();
+    for (int b0 = 0; b0 < m; b0 += blockDim.x) {
+      int u = b0 + threadIdx.x;
+      uint32_t k = u < m ? nkeep[head + u] : 0u;
+      uint32_t tn, tk;
+      uint32_t en = block_excl_scan(k ? 1u : 0u, &tn);
+      uint32_t ek = block_excl_scan(k, &tk);
+      uint32_t pos = carry_n + en;
+      if (k && pos < (uint32_t)kRankTile) {
+        skey[pos] = ((unsigned long long)tkey[head + u] << 32) | pos;
+        sidx[pos] = (uint32_t)u;
+        skept[pos] = k;
+        spre[pos] = carry_k + ek;
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        carry_n += tn;
+        carry_k += tk;
+      }
+      __syncthreads();
+    }
+    const uint32_t M = carry_n;
+    if (M > (uint32_t)kRankTile) {
+      for (int u = threadIdx.x; u < m; u += blockDim.x)
+        if (nkeep[head + u]) delta_id[head + u] = (int32_t)kUnranked;
+      __syncthreads();
+      continue;
+    }
+    int P = 1;
+    while (P < (int)M) P <<= 1;
+    for (int j = (int)M + threadIdx.x; j < P; j += blockDim.x) skey[j] = ~0ull;
+    __syncthreads();
+    for (int k = 2; k <= P; k <<= 1) {
+      for (int j = k >> 1; j > 0; j >>= 1) {
+        for (int i = threadIdx.x; i < P; i += blockDim.x) {
+          int ixj = i ^ j;
+          if (ixj > i) {
+            unsigned long long a = skey[i], b = skey[ixj];
+            bool up = (i & k) == 0;
+            if ((a > b) == up) {
+              skey[i] = b;
+              skey[ixj] = a;
+            }
+          }
+        }
+        __syncthreads();
+      }
+    }
+    // sorted rank r: clusters of the tracks ranked before it
+    if (threadIdx.x == 0) carry_k = 0u;
+    __syncthreads();
+    for (int r0 = 0; r0 < (int)M; r0 += blockDim.x) {
+      int r = r0 + threadIdx.x;
+      uint32_t pos = r < (int)M ? (uint32_t)(skey[r] & 0xffffffffu) : 0u;
+      uint32_t k = r < (int)M ? skept[pos] : 0u;
+      uint32_t tk;
+      uint32_t ek = block_excl_scan(k, &tk);
+      if (r < (int)M) {
+        int u = head + (int)sidx[pos];
+        delta_id[u] = r - (int32_t)pos;
+        delta_o[u] = (int32_t)(carry_k + ek) - (int32_t)spre[pos];
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) carry_k += tk;
+      __syncthreads();
+    }
+  }
+}
+
+// Tracks are emitted in a canonical order: by (event, sector, row) of the
+// start hit, then by its input index -- not by its position in the search
+// grid, which depends on the grid's tuning. Tracklets of one (event, sector,
+// row) are contiguous in the start list (it follows the row buckets), so a
+// track's place is its tracklet's place corrected inside that group.
 __global__ void k_select_write(int n_rows, const uint32_t* cnt, const int32_t* hits,
-                               const uint32_t* range, const uint32_t* starts, const double* that,
+                               const uint32_t* range, const uint32_t* starts,
+                               const uint32_t* tkey, const uint32_t* tseg,
+                               const int32_t* delta_id, const int32_t* delta_o, const double* that,
                                const uint32_t* gorig, const unsigned long long* weight,
                                const int32_t* nh, const uint32_t* nkeep, const uint32_t* off_tr,
                                const uint32_t* off_cl, int64_t cap_tr, int64_t cap_asg,
@@ -900,6 +1027,41 @@ __global__ void k_select_write(int n_rows, const uint32_t* cnt, const int32_t* h
   if (!emit) return;
   uint32_t id = off_tr[blockIdx.x] + ex_tr;
   uint32_t o = off_cl[blockIdx.x] + ex_cl;
+  {
+    const int ntl = (int)cnt[kCntStart];
+    const uint32_t seg = tseg[t];
+    // size of the group, counted up to kSmallGroup + 1
+    int nb = 0, na = 0;
+    while (nb + na < kSmallGroup && t - nb - 1 >= 0 && tseg[t - nb - 1] == seg) ++nb;
+    while (nb + na < kSmallGroup && t + na + 1 < ntl && tseg[t + na + 1] == seg) ++na;
+    bool small = nb + na < kSmallGroup;
+    if (!small && delta_id[t] != (int32_t)kUnranked) {
+      id = (uint32_t)((int32_t)id + delta_id[t]);
+      o = (uint32_t)((int32_t)o + delta_o[t]);
+    } else {
+      const uint32_t me = tkey[t];
+      uint32_t n_before = 0, k_before = 0, n_less = 0, k_less = 0;
+      for (int u = t - 1; u >= 0 && tseg[u] == seg; --u) {
+        uint32_t ku = nkeep[u];
+        if (!ku) continue;
+        ++n_before;
+        k_before += ku;
+        if (tkey[u] < me) {
+          ++n_less;
+          k_less += ku;
+        }
+      }
+      for (int u = t + 1; u < ntl && tseg[u] == seg; ++u) {
+        uint32_t ku = nkeep[u];
+        if (ku && tkey[u] < me) {
+          ++n_less;
+          k_less += ku;
+        }
+      }
+      id = id - n_before + n_less;
+      o = o - k_before + k_less;
+    }
+  }
   if ((int64_t)id >= cap_tr || (int64_t)(o + kept) > cap_asg) return;
   unsigned long long w = ((unsigned long long)(uint32_t)nh[t] << 32) |
                          (unsigned long long)(0xffffffffu - gorig[starts[t]]);
@@ -1071,18 +1233,21 @@ void launch_load(Prof* P, const Geo& g, const Cal& c, const ClIn& cl, const Grid
                                                          b.big_list, b.list_counts + 1, err));
 }
 
-int tracklet_resident_blocks() {
-  int dev = 0, sms = 0, per = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
-  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_tracklets, 128, 0) != cudaSuccess)
-    return 0;
-  return sms * per;
+void setup_find_kernels() {
+  cudaFuncSetAttribute(k_group_rank, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRankSmem);
+}
+
+int tracklet_blocks_per_sm(int block) {
+  int per = 0;
+  cudaError_t e = block == 64    ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_tracklets<64>, 64, 0)
+                  : block == 256 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_tracklets<256>, 256, 0)
+                                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_tracklets<128>, 128, 0);
+  return e == cudaSuccess ? per : 0;
 }
 
 void launch_find(Prof* P, const Geo& g, const Cal& c, const Params& p, const ClIn& cl,
-                 const GridDims& gd, int K, FindBuf& b, TrackBuf& tb, uint32_t* cnt,
-                 uint32_t* err, cudaStream_t s) {
+                 const GridDims& gd, const Shapes& sh, int K, FindBuf& b, TrackBuf& tb,
+                 uint32_t* cnt, uint32_t* err, cudaStream_t s) {
   int n = cl.n;
   int nb = nblk(n, kB256);
   if (n > 0) {
@@ -1098,25 +1263,39 @@ void launch_find(Prof* P, const Geo& g, const Cal& c, const Params& p, const ClI
                                         (uint32_t)b.cap_tl, p.seed_max_hits, b.starts, b.seed_end));
   cudaMemsetAsync(b.weight, 0, sizeof(unsigned long long) * (size_t)(n > 0 ? n : 1), s);
   Grid G{b.gyz, b.gorig, b.bin_start, b.zr};
-  // persistent grid: the resident blocks, or fewer for a small capacity
-  int ntl_blk = nblk(b.cap_tl, 128);
-  if (b.tl_blocks > 0 && ntl_blk > b.tl_blocks) ntl_blk = b.tl_blocks;
+  // persistent grid: the tuned number of resident blocks, or fewer for a
+  // small capacity
   cudaMemsetAsync(b.queue, 0, sizeof(uint32_t), s);
-  TPC_LAUNCH(P, "k_tracklets", s,
-             k_tracklets<<<ntl_blk, 128, 0, s>>>(g, c, p, gd, G, b.es_dims, cl.mode, b.upc, b.gseg,
-                                                 b.starts, b.seed_end, cnt, b.nh, b.hits,
-                                                 b.range, b.that, b.queue));
+#define TPC_TRACKLETS(BS)                                                                   \
+  {                                                                                        \
+    int nbk = nblk(b.cap_tl, BS);                                                          \
+    if (sh.tl_grid > 0 && nbk > sh.tl_grid) nbk = sh.tl_grid;                              \
+    TPC_LAUNCH(P, "k_tracklets", s,                                                        \
+               k_tracklets<BS><<<nbk, BS, 0, s>>>(g, c, p, gd, G, b.es_dims, cl.mode, b.upc, \
+                                                  b.gseg, b.starts, b.seed_end, cnt, b.nh,  \
+                                                  b.hits, b.range, b.that, b.queue));       \
+  }
+  if (sh.tl_block == 64) TPC_TRACKLETS(64)
+  else if (sh.tl_block == 256) TPC_TRACKLETS(256)
+  else TPC_TRACKLETS(128)
+#undef TPC_TRACKLETS
   TPC_LAUNCH(P, "k_tl_weight", s,
              k_tl_weight<<<nblk(b.cap_tl * 32, kB256), kB256, 0, s>>>(
                  g.n_rows, p.min_track_hits, cnt, b.nh, b.hits, b.range, b.starts, b.gorig,
                  b.weight));
   int nsel = nblk(b.cap_tl, kB256);
+  cudaMemsetAsync(b.grp_count, 0, sizeof(uint32_t), s);
   TPC_LAUNCH(P, "k_select_count", s, k_select_count<<<nsel, kB256, 0, s>>>(g.n_rows, p, cnt, b.nh, b.hits, b.range, b.starts, b.gorig,
-                                        b.weight, b.nkeep, b.blk_a, b.blk_b));
+                                        b.gseg, b.weight, b.nkeep, b.tkey, b.tseg, b.grp_list,
+                                        b.grp_count, b.cap_grp, b.blk_a, b.blk_b));
+  TPC_LAUNCH(P, "k_group_rank", s,
+             k_group_rank<<<2 * 148, 1024, kRankSmem, s>>>(cnt, b.tkey, b.tseg, b.nkeep,
+                                                          b.grp_list, b.grp_count, b.cap_grp,
+                                                          b.delta_id, b.delta_o));
   TPC_LAUNCH(P, "k_scan_blocks", s, k_scan_blocks<<<1, 1024, 0, s>>>(nsel, b.blk_a, b.off_a, b.blk_b, b.off_b, cnt, kCntTracks,
                                    kCntAssigned, (uint32_t)tb.cap_tr, (uint32_t)tb.cap_asg, err,
                                    kErrCapTrack));
-  TPC_LAUNCH(P, "k_select_write", s, k_select_write<<<nsel, kB256, 0, s>>>(g.n_rows, cnt, b.hits, b.range, b.starts, b.that, b.gorig,
+  TPC_LAUNCH(P, "k_select_write", s, k_select_write<<<nsel, kB256, 0, s>>>(g.n_rows, cnt, b.hits, b.range, b.starts, b.tkey, b.tseg, b.delta_id, b.delta_o, b.that, b.gorig,
                                         b.weight, b.nh, b.nkeep, b.off_a, b.off_b, tb.cap_tr,
                                         tb.cap_asg, tb.track_start, tb.cluster_idx, tb.asg_track,
                                         tb.t_coll, tb.start_hit));

@@ -107,7 +107,13 @@ struct FindBuf {
   uint32_t* queue;      // [1] next start hit of the persistent tracklet kernel
   uint32_t* seed_end;   // [cap_tl] last hit of each start hit's seed
   uint32_t* range;      // [cap_tl] rows lo | hi << 16 of hits[] the tracklet wrote
-  int tl_blocks;        // resident blocks of the persistent tracklet kernel
+  uint32_t* tkey;       // [cap_tl] input index of the start hit
+  uint32_t* tseg;       // [cap_tl] (event, sector, row) segment of the start hit
+  int32_t* delta_id;    // [cap_tl] track-order shift inside large groups
+  int32_t* delta_o;     // [cap_tl] cluster-offset shift inside large groups
+  uint32_t* grp_list;   // [cap_grp] first tracklet of each large group
+  uint32_t* grp_count;  // [1]
+  uint32_t cap_grp;
   int64_t cap_tl;
 };
 
@@ -213,6 +219,8 @@ struct Prof {
     if (P) (P)->end(S);             \
   } while (0)
 
+constexpr int kSmallGroup = 64;  // start-hit groups up to this size are ranked by a scan
+constexpr int kRankTile = 8192;   // emitted tracklets a block ranks in shared memory
 constexpr int kSortTile = 4096;      // pad-row bucket tile of the common sort
 constexpr int kSortTileBig = 16384;  // tile of the large-bucket sort (128 KB)
 constexpr int kCalibGradBlocks = 4 * 148;
@@ -220,10 +228,18 @@ constexpr int kCalibGradBlocks = 4 * 148;
 // launchers (tpc_find.cu)
 void launch_load(Prof* P, const Geo& g, const Cal& c, const ClIn& cl, const GridDims& gd, int K,
                  FindBuf& b, uint32_t* err, cudaStream_t s);
-int tracklet_resident_blocks();
+// Launch shapes chosen by the autotuner (none of them changes a result).
+struct Shapes {
+  int tl_block = 128;    // tracklet kernel threads per block (64, 128, 256)
+  int tl_grid = 0;       // persistent tracklet grid (0: one block per 128 tracklets)
+};
+// Resident blocks per SM of the tracklet kernel at a block size.
+int tracklet_blocks_per_sm(int block);
+// Kernel attributes (shared-memory limits), once per context.
+void setup_find_kernels();
 void launch_find(Prof* P, const Geo& g, const Cal& c, const Params& p, const ClIn& cl,
-                 const GridDims& gd, int K, FindBuf& b, TrackBuf& tb, uint32_t* cnt,
-                 uint32_t* err, cudaStream_t s);
+                 const GridDims& gd, const Shapes& sh, int K, FindBuf& b, TrackBuf& tb,
+                 uint32_t* cnt, uint32_t* err, cudaStream_t s);
 void launch_set_tracks(Prof* P, const Geo& g, const Cal& c, const ClIn& cl, int64_t n_tracks,
                        int64_t n_asg, TrackBuf& tb, uint32_t* cnt, uint32_t* err, cudaStream_t s);
 void launch_calib(Prof* P, const Geo& g, const Cal& c, const ClIn& cl, int64_t cap_asg,
