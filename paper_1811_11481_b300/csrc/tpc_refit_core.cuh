@@ -412,7 +412,10 @@ TPC_HD void refit_backward_track(const Geo& g, const RefitCfg& p, const TrackIn&
     };
     int kc = prev_active(n - 1);
     if (kc < 0) continue;
-    // record of the current step: checkpoint, cluster data
+    // The loads of a step are issued one step ahead of its use: the
+    // checkpoint of the previous active step kp, and the cluster word of the
+    // step before it (kq, active in all but rare cases: when it is not, the
+    // previous active step is searched for and loaded on the spot).
     float p0[5], C0[15];
     int ic = idx_of(pass, kc);
     for (int j = 0; j < 5; ++j) p0[j] = ckpt[ly.ck(pass, kc, j)];
@@ -420,22 +423,51 @@ TPC_HD void refit_backward_track(const Geo& g, const RefitCfg& p, const TrackIn&
     uint32_t mc = in.meta[ly.at(ic)];
     float myc = in.yc[ly.at(ic)], mzc = in.zc[ly.at(ic)];
     int rjc = rej[ly.at(ic)];
+    int kq = kc - 1;
+    uint32_t mq = 0;
+    float myq = 0.f, mzq = 0.f;
+    int rjq = 0;
+    if (kq >= 0) {
+      int iq = idx_of(pass, kq);
+      mq = in.meta[ly.at(iq)];
+      myq = in.yc[ly.at(iq)];
+      mzq = in.zc[ly.at(iq)];
+      rjq = rej[ly.at(iq)];
+    }
     while (kc >= 0) {
-      // prefetch the previous active step
-      int kp = prev_active(kc - 1);
+      // the previous active step and its cluster word
+      int kp = kq;
+      uint32_t mp = mq;
+      float myp = myq, mzp = mzq;
+      int rjp = rjq;
+      if (kq >= 0 && !step_active(rjq, pass)) {
+        kp = prev_active(kq - 1);
+        if (kp >= 0) {
+          int ip = idx_of(pass, kp);
+          mp = in.meta[ly.at(ip)];
+          myp = in.yc[ly.at(ip)];
+          mzp = in.zc[ly.at(ip)];
+          rjp = rej[ly.at(ip)];
+        }
+      }
+      // issue the loads of the next iteration
       float p1[5], C1[15];
-      uint32_t mp = 0;
-      float myp = 0.f, mzp = 0.f;
-      int rjp = 0;
       if (kp >= 0) {
-        int ip = idx_of(pass, kp);
         for (int j = 0; j < 5; ++j) p1[j] = ckpt[ly.ck(pass, kp, j)];
         for (int j = 0; j < 15; ++j) C1[j] = ckpt[ly.ck(pass, kp, 5 + j)];
-        mp = in.meta[ly.at(ip)];
-        myp = in.yc[ly.at(ip)];
-        mzp = in.zc[ly.at(ip)];
-        rjp = rej[ly.at(ip)];
       }
+      int kq2 = kp - 1;
+      uint32_t mq2 = 0;
+      float myq2 = 0.f, mzq2 = 0.f;
+      int rjq2 = 0;
+      if (kq2 >= 0) {
+        int iq = idx_of(pass, kq2);
+        mq2 = in.meta[ly.at(iq)];
+        myq2 = in.yc[ly.at(iq)];
+        mzq2 = in.zc[ly.at(iq)];
+        rjq2 = rej[ly.at(iq)];
+      }
+      // the current step, from its checkpoint
       float xprev = kp >= 0 ? g.row_x[mp & 0xffu] : xend[pass - 1];
       float xi = g.row_x[mc & 0xffu];
       float pp[5];
@@ -464,6 +496,11 @@ TPC_HD void refit_backward_track(const Geo& g, const RefitCfg& p, const TrackIn&
         myc = myp;
         mzc = mzp;
         rjc = rjp;
+        kq = kq2;
+        mq = mq2;
+        myq = myq2;
+        mzq = mzq2;
+        rjq = rjq2;
       }
     }
     if (pass > 1)
