@@ -423,6 +423,9 @@ TPC_HD void refit_backward_track(const Geo& g, const RefitCfg& p, const TrackIn&
     uint32_t mc = in.meta[ly.at(ic)];
     float myc = in.yc[ly.at(ic)], mzc = in.zc[ly.at(ic)];
     int rjc = rej[ly.at(ic)];
+    // the cluster's gradient so far (read ahead too: an add to global memory
+    // would stall the step on the load); zero before pass 3
+    float gyo = pass < 3 ? gyc[ly.at(ic)] : 0.0f, gzo = pass < 3 ? gzc[ly.at(ic)] : 0.0f;
     int kq = kc - 1;
     uint32_t mq = 0;
     float myq = 0.f, mzq = 0.f;
@@ -452,9 +455,15 @@ TPC_HD void refit_backward_track(const Geo& g, const RefitCfg& p, const TrackIn&
       }
       // issue the loads of the next iteration
       float p1[5], C1[15];
+      float gyo1 = 0.0f, gzo1 = 0.0f;
       if (kp >= 0) {
         for (int j = 0; j < 5; ++j) p1[j] = ckpt[ly.ck(pass, kp, j)];
         for (int j = 0; j < 15; ++j) C1[j] = ckpt[ly.ck(pass, kp, 5 + j)];
+        if (pass < 3) {
+          size_t a1 = ly.at(idx_of(pass, kp));
+          gyo1 = gyc[a1];
+          gzo1 = gzc[a1];
+        }
       }
       int kq2 = kp - 1;
       uint32_t mq2 = 0;
@@ -483,8 +492,8 @@ TPC_HD void refit_backward_track(const Geo& g, const RefitCfg& p, const TrackIn&
         Innov iv = innovation(pp, Cp, myc, mzc, v, v);
         float mb[2];
         update_adjoint(Cp, iv, cbar, pb, G, mb);
-        gyc[ly.at(ic)] += mb[0];
-        gzc[ly.at(ic)] += mb[1];
+        gyc[ly.at(ic)] = gyo + mb[0];
+        gzc[ly.at(ic)] = gzo + mb[1];
       }
       transport_adjoint(p.kB, xi - xprev, p0, C0, J, pb, G);
       kc = kp;
@@ -496,6 +505,8 @@ TPC_HD void refit_backward_track(const Geo& g, const RefitCfg& p, const TrackIn&
         myc = myp;
         mzc = mzp;
         rjc = rjp;
+        gyo = gyo1;
+        gzo = gzo1;
         kq = kq2;
         mq = mq2;
         myq = myq2;
