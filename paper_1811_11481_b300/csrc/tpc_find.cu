@@ -78,29 +78,55 @@ __global__ void k_init_load(int K, int n_events, uint32_t* cnt, uint32_t* fill, 
   }
 }
 
-__global__ void k_hist(Geo g, Cal c, ClIn cl, uint32_t* cnt, float* zs_in, int32_t* zmm,
-                       uint32_t* err) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= cl.n) return;
-  int r = cl.row[i], s = cl.sector[i];
-  int e = cl.event ? (int)cl.event[i] : 0;
-  if (r >= g.n_rows || s >= kNS || e >= cl.n_events) {
-    atomicOr(err, kErrArg);
-    zs_in[i] = 0.0f;
-    return;
+// Row histogram, seeding z and the z range of each (event, side). A fixed
+// grid strides over the clusters; the z range is first reduced per block in
+// shared memory (the global minimum and maximum would otherwise take one
+// contended atomic per cluster), for up to kHistSides (event, side) pairs.
+constexpr int kHistSides = 2048;
+__global__ void __launch_bounds__(256) k_hist(Geo g, Cal c, ClIn cl, uint32_t* cnt,
+                                              float* zs_in, int32_t* zmm, uint32_t* err) {
+  __shared__ int32_t smin[kHistSides], smax[kHistSides];
+  const int nsides = cl.n_events * 2;
+  const bool local = nsides <= kHistSides;
+  if (local)
+    for (int q = threadIdx.x; q < nsides; q += blockDim.x) {
+      smin[q] = f2ord(3.0e38f);
+      smax[q] = f2ord(-3.0e38f);
+    }
+  __syncthreads();
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < cl.n; i += gridDim.x * blockDim.x) {
+    int r = cl.row[i], s = cl.sector[i];
+    int e = cl.event ? (int)cl.event[i] : 0;
+    if (r >= g.n_rows || s >= kNS || e >= cl.n_events) {
+      atomicOr(err, kErrArg);
+      zs_in[i] = 0.0f;
+      continue;
+    }
+    float zs = seed_z(g, c, cl.mode, cl.mode == 0 ? cl.z[i] : 0.0f,
+                      cl.mode == 1 ? cl.t[i] : 0.0, s);
+    zs_in[i] = zs;
+    if (!(fabsf(zs) < 1.0e30f)) {
+      atomicOr(err, kErrArg);
+      continue;
+    }
+    int key = (e * kNS + s) * g.n_rows + r;
+    atomicAdd(&cnt[key], 1u);
+    int side = e * 2 + (s >= 18 ? 1 : 0);
+    int32_t o = f2ord(zs);
+    if (local) {
+      if (o < smin[side]) atomicMin(&smin[side], o);
+      if (o > smax[side]) atomicMax(&smax[side], o);
+    } else {
+      if (o < zmm[2 * side]) atomicMin(&zmm[2 * side], o);
+      if (o > zmm[2 * side + 1]) atomicMax(&zmm[2 * side + 1], o);
+    }
   }
-  float zs = seed_z(g, c, cl.mode, cl.mode == 0 ? cl.z[i] : 0.0f, cl.mode == 1 ? cl.t[i] : 0.0, s);
-  zs_in[i] = zs;
-  if (!(fabsf(zs) < 1.0e30f)) {
-    atomicOr(err, kErrArg);
-    return;
-  }
-  int key = (e * kNS + s) * g.n_rows + r;
-  atomicAdd(&cnt[key], 1u);
-  int side = e * 2 + (s >= 18 ? 1 : 0);
-  int32_t o = f2ord(zs);
-  if (o < zmm[2 * side]) atomicMin(&zmm[2 * side], o);
-  if (o > zmm[2 * side + 1]) atomicMax(&zmm[2 * side + 1], o);
+  __syncthreads();
+  if (local)
+    for (int q = threadIdx.x; q < nsides; q += blockDim.x) {
+      if (smin[q] != f2ord(3.0e38f)) atomicMin(&zmm[2 * q], smin[q]);
+      if (smax[q] != f2ord(-3.0e38f)) atomicMax(&zmm[2 * q + 1], smax[q]);
+    }
 }
 
 // Single block: bucket offsets, the z range of each (event, side) and the bin
@@ -1199,7 +1225,8 @@ void launch_load(Prof* P, const Geo& g, const Cal& c, const ClIn& cl, const Grid
                                                                b.zmm));
   if (cl.n > 0)
     TPC_LAUNCH(P, "k_hist", s,
-               k_hist<<<nblk(cl.n, kB256), kB256, 0, s>>>(g, c, cl, b.cnt, b.zs_in, b.zmm, err));
+               k_hist<<<min(nblk(cl.n, kB256), 8 * 148), kB256, 0, s>>>(g, c, cl, b.cnt, b.zs_in,
+                                                                        b.zmm, err));
   TPC_LAUNCH(P, "k_scan_rows", s,
              k_scan_rows<<<1, 1024, 0, s>>>(g, K, cl.n_events, gd, b.cnt, b.row_start, b.zmm, b.zr,
                                             b.es_dims, b.n_bins));

@@ -145,21 +145,20 @@ __device__ __forceinline__ Lay warp_layout(const uint32_t* wbase, const uint32_t
 }
 
 // Copy each track's calibrated clusters into the warp-interleaved layout.
-__global__ void k_interleave(const uint32_t* cnt, TrackIn in, const uint32_t* order,
-                             const uint32_t* wbase, const uint32_t* wlen, float* w_yc,
+// One thread per assigned cluster: reads are coalesced, each value goes to
+// its place in its warp's interleaved block.
+__global__ void k_interleave(const uint32_t* cnt, TrackIn in, const uint32_t* asg_track,
+                             const uint32_t* slot, const uint32_t* wbase, float* w_yc,
                              float* w_zc, uint32_t* w_meta) {
-  int tid = blockIdx.x * blockDim.x + threadIdx.x;
-  if (tid >= (int)cnt[kCntTracks]) return;
-  int T = (int)order[tid];
-  uint32_t a = in.track_start[T];
-  uint32_t b = in.track_start[T + 1];
-  if (b < a || b > cnt[kCntAssigned]) return;
-  Lay ly = warp_layout(wbase, wlen, tid);
-  for (int k = 0; k < (int)(b - a); ++k) {
-    w_yc[ly.at(k)] = in.yc[a + k];
-    w_zc[ly.at(k)] = in.zc[a + k];
-    w_meta[ly.at(k)] = in.meta[a + k];
-  }
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= (int)cnt[kCntAssigned]) return;
+  uint32_t T = asg_track[j];
+  if (T >= cnt[kCntTracks]) return;
+  uint32_t sl = slot[T];
+  size_t pos = ((size_t)wbase[sl >> 5] + (j - in.track_start[T])) * 32 + (sl & 31);
+  w_yc[pos] = in.yc[j];
+  w_zc[pos] = in.zc[j];
+  w_meta[pos] = in.meta[j];
 }
 
 __global__ void __launch_bounds__(kB) k_refit(Geo g, RefitCfg p, const uint32_t* cnt,
@@ -478,8 +477,9 @@ void launch_refit(Prof* P, const Geo& g, const Params& p, int64_t cap_tr, const 
              k_warp_len<<<nb, 256, 0, s>>>(cnt, tb.track_start, rb.order, rb.wlen));
   TPC_LAUNCH(P, "k_warp_scan", s, k_warp_scan<<<1, 1024, 0, s>>>(cnt, rb.wlen, rb.wbase));
   TPC_LAUNCH(P, "k_interleave", s,
-             k_interleave<<<nb, 256, 0, s>>>(cnt, in, rb.order, rb.wbase, rb.wlen, rb.w_yc,
-                                              rb.w_zc, rb.w_meta));
+             k_interleave<<<nblk(tb.cap_asg, 256), 256, 0, s>>>(cnt, in, tb.asg_track, rb.slot,
+                                                                 rb.wbase, rb.w_yc, rb.w_zc,
+                                                                 rb.w_meta));
   TPC_LAUNCH(P, "k_refit", s,
              k_refit<<<nblk(cap_tr, kB), kB, 0, s>>>(g, make_cfg(g, p), cnt, rb.order, rb.wbase,
                                                      rb.wlen, tb.track_start, win, rb.seed,
