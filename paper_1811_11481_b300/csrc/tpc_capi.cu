@@ -343,7 +343,7 @@ void tpc_destroy(tpc_ctx* ctx) {
   cudaStreamSynchronize(ctx->stream);
   void* ptrs[] = {ctx->d_spline, ctx->d_spl_bound, ctx->d_err, ctx->d_cnt,
                   ctx->fb.cnt, ctx->fb.row_start, ctx->fb.fill, ctx->fb.zmm, ctx->fb.zr,
-                  ctx->fb.zs_in, ctx->fb.perm, ctx->fb.gyz,
+                  ctx->fb.zs_in, ctx->fb.perm, ctx->fb.pyz, ctx->fb.gyz,
                   ctx->fb.gorig, ctx->fb.gseg, ctx->fb.bin_start, ctx->fb.big_list, ctx->fb.mid_list, ctx->fb.list_counts,
                   ctx->fb.n_bins, ctx->fb.es_dims, ctx->fb.queue, ctx->fb.up, ctx->fb.dn,
                   ctx->fb.upc, ctx->fb.dnc, ctx->fb.blk_a, ctx->fb.blk_b, ctx->fb.off_a,
@@ -415,7 +415,7 @@ tpc_status prepare_load(tpc_ctx* ctx, int n_events) {
   int K = ctx->K;
   // search grid: the tuned clusters per bin, geometry chosen on the device
   ctx->gd.tau = ctx->tune.grid_tau;
-  ctx->gd.nb_max = 8192;
+  ctx->gd.nb_max = kGridBinsMax;
   ctx->gd.ny_max = ctx->tune.grid_ny_max;
   ctx->gd.y_margin = 2.0f;
   ctx->gd.z_margin = 1.0f;
@@ -424,6 +424,7 @@ tpc_status prepare_load(tpc_ctx* ctx, int n_events) {
     int64_t c = n > 0 ? n : 1;
     CK(alloc(b.zs_in, c));
     CK(alloc(b.perm, c));
+    CK(alloc(b.pyz, c));
     CK(alloc(b.gyz, c));
     CK(alloc(b.gorig, c));
     CK(alloc(b.gseg, c));

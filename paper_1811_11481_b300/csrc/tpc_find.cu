@@ -199,8 +199,10 @@ __global__ void k_scan_rows(Geo g, int K, int n_events, GridDims gd, const uint3
   if (threadIdx.x == 0) *n_bins = carry;
 }
 
-__global__ void k_scatter(Geo g, ClIn cl, const uint32_t* row_start, uint32_t* fill,
-                          uint32_t* perm) {
+// Bucket order: the input index and, alongside, (y, seeding z), so that the
+// row sorts read their clusters contiguously.
+__global__ void k_scatter(Geo g, ClIn cl, const uint32_t* row_start, const float* zs_in,
+                          uint32_t* fill, uint32_t* perm, float2* pyz) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= cl.n) return;
   int r = cl.row[i], s = cl.sector[i];
@@ -209,6 +211,7 @@ __global__ void k_scatter(Geo g, ClIn cl, const uint32_t* row_start, uint32_t* f
   int key = (e * kNS + s) * g.n_rows + r;
   uint32_t pos = row_start[key] + atomicAdd(&fill[key], 1u);
   perm[pos] = (uint32_t)i;
+  pyz[pos] = make_float2(cl.y[i], zs_in[i]);
 }
 
 // Search-grid geometry of one (event, sector): tables of nb + 1 bin offsets
@@ -240,13 +243,26 @@ __device__ __forceinline__ int bin_z(const float* zr, int side, int nz, float z)
   return iz < 0 ? 0 : (iz >= nz ? nz - 1 : iz);
 }
 
+// Sort key of a cluster in its bucket: bin, then input index, then its slot
+// j in the bucket (unique already; carried to find its (y, z) after sorting).
+__device__ __forceinline__ unsigned long long sort_key(int b, uint32_t i, int j) {
+  return ((unsigned long long)(uint32_t)b << 46) | ((unsigned long long)i << 15) | (uint32_t)j;
+}
+__device__ __forceinline__ int key_bin(unsigned long long k) { return (int)(k >> 46); }
+__device__ __forceinline__ uint32_t key_index(unsigned long long k) {
+  return (uint32_t)((k >> 15) & 0x7fffffffu);
+}
+__device__ __forceinline__ uint32_t key_slot(unsigned long long k) {
+  return (uint32_t)(k & 0x7fffu);
+}
+
 // Bitonic sort of one (event, sector, row) bucket by (bin, input index) in
 // shared memory (keys[] holds 'tile' entries), then the grid-ordered SoA and
 // the bin offsets of the bucket.
-__device__ void sort_bucket(const Geo& g, const ClIn& cl, const GridDims& gd, const Bins& B,
-                            int seg, uint32_t start, int n, const uint32_t* perm,
-                            const float* zs_in, const float* zr, float2* gyz, uint32_t* gorig,
-                            uint32_t* gseg, uint32_t* bs, unsigned long long* keys) {
+__device__ void sort_bucket(const Geo& g, const GridDims& gd, const Bins& B, int seg,
+                            uint32_t start, int n, const uint32_t* perm, const float2* pyz,
+                            const float* zr, float2* gyz, uint32_t* gorig, uint32_t* gseg,
+                            uint32_t* bs, unsigned long long* keys) {
   int r = seg % g.n_rows;
   int es = seg / g.n_rows;
   int e = es / kNS, s = es % kNS;
@@ -257,8 +273,9 @@ __device__ void sort_bucket(const Geo& g, const ClIn& cl, const GridDims& gd, co
     unsigned long long k = ~0ull;
     if (j < n) {
       uint32_t i = perm[start + j];
-      int b = bin_z(zr, side, B.nz, zs_in[i]) * B.ny + bin_y(g, gd, r, B.ny, cl.y[i]);
-      k = ((unsigned long long)(uint32_t)b << 32) | i;
+      float2 v = pyz[start + j];
+      int b = bin_z(zr, side, B.nz, v.y) * B.ny + bin_y(g, gd, r, B.ny, v.x);
+      k = sort_key(b, i, j);
     }
     keys[j] = k;
   }
@@ -281,28 +298,102 @@ __device__ void sort_bucket(const Geo& g, const ClIn& cl, const GridDims& gd, co
   }
   for (int j = threadIdx.x; j < n; j += blockDim.x) {
     unsigned long long k = keys[j];
-    uint32_t i = (uint32_t)(k & 0xffffffffu);
-    int b = (int)(k >> 32);
-    int bprev = j > 0 ? (int)(keys[j - 1] >> 32) : -1;
+    int b = key_bin(k);
+    int bprev = j > 0 ? key_bin(keys[j - 1]) : -1;
     for (int q = bprev + 1; q <= b; ++q) bs[q] = start + j;
     if (j == n - 1)
       for (int q = b + 1; q <= B.nb; ++q) bs[q] = start + n;
-    gyz[start + j] = make_float2(cl.y[i], zs_in[i]);
-    gorig[start + j] = i;
+    gyz[start + j] = pyz[start + key_slot(k)];
+    gorig[start + j] = key_index(k);
     gseg[start + j] = (uint32_t)seg;
   }
 }
 
+// Block counting sort of one row bucket by bin, then by input index inside
+// each bin: the same order as sort_bucket's (bin, input index) keys, in
+// O(n + bins) work. Shared memory: per bin a counter (turned into offsets),
+// per cluster its input index, bin and sorted slot. Returns false, before
+// writing anything, when a bin holds more than kCountBinMax clusters (the
+// per-bin insertion sort would be slow); the caller then uses sort_bucket.
+constexpr int kCountBinMax = 64;
+__device__ bool count_sort_bucket(const Geo& g, const GridDims& gd, const Bins& B, int seg,
+                                  uint32_t start, int n, int tile, const uint32_t* perm,
+                                  const float2* pyz, const float* zr, float2* gyz,
+                                  uint32_t* gorig, uint32_t* gseg, uint32_t* bs,
+                                  uint32_t* smem) {
+  __shared__ uint32_t maxc;
+  uint32_t* arr = smem;                 // [nb] counts, then bin ends
+  uint32_t* si = arr + B.nb;            // [tile] input index, bucket order
+  uint32_t* out = si + tile;            // [tile] bucket slot, sorted
+  uint16_t* kb = reinterpret_cast<uint16_t*>(out + tile);  // [tile] bin
+  int r = seg % g.n_rows;
+  int es = seg / g.n_rows;
+  int e = es / kNS, s = es % kNS;
+  int side = e * 2 + (s >= 18 ? 1 : 0);
+  for (int q = threadIdx.x; q < B.nb; q += blockDim.x) arr[q] = 0u;
+  if (threadIdx.x == 0) maxc = 0u;
+  __syncthreads();
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    uint32_t i = perm[start + j];
+    float2 v = pyz[start + j];
+    int b = bin_z(zr, side, B.nz, v.y) * B.ny + bin_y(g, gd, r, B.ny, v.x);
+    si[j] = i;
+    kb[j] = (uint16_t)b;
+    atomicAdd(&arr[b], 1u);
+  }
+  __syncthreads();
+  // exclusive scan of the counts, in chunks of the block
+  uint32_t carry = 0u;
+  for (int b0 = 0; b0 < B.nb; b0 += blockDim.x) {
+    int q = b0 + threadIdx.x;
+    uint32_t v = q < B.nb ? arr[q] : 0u;
+    if (v > kCountBinMax) atomicMax(&maxc, v);
+    uint32_t tot;
+    uint32_t ex = block_excl_scan(v, &tot);
+    if (q < B.nb) arr[q] = carry + ex;
+    carry += tot;
+  }
+  __syncthreads();
+  if (maxc > (uint32_t)kCountBinMax) return false;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    uint32_t pos = atomicAdd(&arr[kb[j]], 1u);
+    out[pos] = (uint32_t)j;
+  }
+  __syncthreads();
+  // arr[b] is now the end of bin b; input-index order inside each bin
+  for (int b = threadIdx.x; b < B.nb; b += blockDim.x) {
+    int lo = b > 0 ? (int)arr[b - 1] : 0, hi = (int)arr[b];
+    for (int a = lo + 1; a < hi; ++a) {
+      uint32_t v = out[a], iv = si[v];
+      int c = a - 1;
+      while (c >= lo && si[out[c]] > iv) {
+        out[c + 1] = out[c];
+        --c;
+      }
+      out[c + 1] = v;
+    }
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q <= B.nb; q += blockDim.x)
+    bs[q] = start + (q > 0 ? arr[q - 1] : 0u);
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    uint32_t jj = out[j];
+    gyz[start + j] = pyz[start + jj];
+    gorig[start + j] = si[jj];
+    gseg[start + j] = (uint32_t)seg;
+  }
+  return true;
+}
+
 // Bucket too large for any tile: copied unsorted, its bins left empty (the
 // capacity error is raised).
-__device__ void copy_bucket_unsorted(const ClIn& cl, int nb, int seg, uint32_t start, int n,
-                                     const uint32_t* perm, const float* zs_in, float2* gyz,
+__device__ void copy_bucket_unsorted(int nb, int seg, uint32_t start, int n,
+                                     const uint32_t* perm, const float2* pyz, float2* gyz,
                                      uint32_t* gorig, uint32_t* gseg, uint32_t* bs) {
   for (int b = threadIdx.x; b <= nb; b += blockDim.x) bs[b] = start;
   for (int j = threadIdx.x; j < n; j += blockDim.x) {
-    uint32_t i = perm[start + j];
-    gyz[start + j] = make_float2(cl.y[i], zs_in[i]);
-    gorig[start + j] = i;
+    gyz[start + j] = pyz[start + j];
+    gorig[start + j] = perm[start + j];
     gseg[start + j] = (uint32_t)seg;
   }
 }
@@ -311,8 +402,8 @@ __device__ void copy_bucket_unsorted(const ClIn& cl, int nb, int seg, uint32_t s
 // in a 256-entry shared tile per warp. Buckets up to 4096 clusters are listed
 // for the 4096-entry block sort, larger ones for the 16384-entry sort.
 constexpr int kWarpTile = 256;
-__global__ void k_row_sort_warp(Geo g, ClIn cl, GridDims gd, int K, const uint32_t* row_start,
-                                const uint2* es_dims, const uint32_t* perm, const float* zs_in,
+__global__ void k_row_sort_warp(Geo g, GridDims gd, int K, const uint32_t* row_start,
+                                const uint2* es_dims, const uint32_t* perm, const float2* pyz,
                                 const float* zr, float2* gyz, uint32_t* gorig, uint32_t* gseg,
                                 uint32_t* bin_start, uint32_t* mid_list, uint32_t* mid_count,
                                 uint32_t* big_list, uint32_t* big_count) {
@@ -347,8 +438,9 @@ __global__ void k_row_sort_warp(Geo g, ClIn cl, GridDims gd, int K, const uint32
     unsigned long long k = ~0ull;
     if (j < n) {
       uint32_t i = perm[start + j];
-      int b = bin_z(zr, side, B.nz, zs_in[i]) * B.ny + bin_y(g, gd, r, B.ny, cl.y[i]);
-      k = ((unsigned long long)(uint32_t)b << 32) | i;
+      float2 v = pyz[start + j];
+      int b = bin_z(zr, side, B.nz, v.y) * B.ny + bin_y(g, gd, r, B.ny, v.x);
+      k = sort_key(b, i, j);
     }
     keys[j] = k;
   }
@@ -371,25 +463,25 @@ __global__ void k_row_sort_warp(Geo g, ClIn cl, GridDims gd, int K, const uint32
   }
   for (int j = lane; j < n; j += 32) {
     unsigned long long k = keys[j];
-    uint32_t i = (uint32_t)(k & 0xffffffffu);
-    int b = (int)(k >> 32);
-    int bprev = j > 0 ? (int)(keys[j - 1] >> 32) : -1;
+    int b = key_bin(k);
+    int bprev = j > 0 ? key_bin(keys[j - 1]) : -1;
     for (int q = bprev + 1; q <= b; ++q) bs[q] = start + j;
     if (j == n - 1)
       for (int q = b + 1; q <= B.nb; ++q) bs[q] = start + n;
-    gyz[start + j] = make_float2(cl.y[i], zs_in[i]);
-    gorig[start + j] = i;
+    gyz[start + j] = pyz[start + key_slot(k)];
+    gorig[start + j] = key_index(k);
     gseg[start + j] = (uint32_t)seg;
   }
 }
 
 // Listed buckets, persistent blocks; 'tile' entries of shared memory.
-__global__ void k_row_sort_list(Geo g, ClIn cl, GridDims gd, int tile, const uint32_t* row_start,
-                                const uint2* es_dims, const uint32_t* perm, const float* zs_in,
+__global__ void k_row_sort_list(Geo g, GridDims gd, int tile, const uint32_t* row_start,
+                                const uint2* es_dims, const uint32_t* perm, const float2* pyz,
                                 const float* zr, float2* gyz, uint32_t* gorig, uint32_t* gseg,
                                 uint32_t* bin_start, const uint32_t* list, const uint32_t* count,
                                 uint32_t* err) {
   extern __shared__ unsigned long long keys[];
+  uint32_t* words = reinterpret_cast<uint32_t*>(keys);
   int nl = (int)*count;
   for (int q = blockIdx.x; q < nl; q += gridDim.x) {
     int seg = (int)list[q];
@@ -400,9 +492,10 @@ __global__ void k_row_sort_list(Geo g, ClIn cl, GridDims gd, int tile, const uin
     uint32_t* bs = bin_start + B.base + (size_t)r * (B.nb + 1);
     if (n > tile) {
       if (threadIdx.x == 0) atomicOr(err, kErrCapRow);
-      copy_bucket_unsorted(cl, B.nb, seg, start, n, perm, zs_in, gyz, gorig, gseg, bs);
-    } else {
-      sort_bucket(g, cl, gd, B, seg, start, n, perm, zs_in, zr, gyz, gorig, gseg, bs, keys);
+      copy_bucket_unsorted(B.nb, seg, start, n, perm, pyz, gyz, gorig, gseg, bs);
+    } else if (!count_sort_bucket(g, gd, B, seg, start, n, tile, perm, pyz, zr, gyz,
+                                  gorig, gseg, bs, words)) {
+      sort_bucket(g, gd, B, seg, start, n, perm, pyz, zr, gyz, gorig, gseg, bs, keys);
     }
     __syncthreads();
   }
@@ -1212,6 +1305,14 @@ __global__ void k_export_tracklets(int n_rows, int64_t n_cap, const uint32_t* cn
 
 inline int nblk(int64_t n, int b) { return (int)((n + b - 1) / b); }
 
+// Shared memory of a block sort of up to `tile` clusters: the larger of the
+// bitonic keys and the counting sort's arrays.
+inline size_t sort_smem(int tile, int nb_max) {
+  size_t bitonic = (size_t)tile * sizeof(unsigned long long);
+  size_t counting = (size_t)nb_max * 4 + (size_t)tile * (4 + 4 + 2);
+  return bitonic > counting ? bitonic : counting;
+}
+
 }  // namespace
 
 // ======================================================================
@@ -1232,36 +1333,33 @@ void launch_load(Prof* P, const Geo& g, const Cal& c, const ClIn& cl, const Grid
                                             b.es_dims, b.n_bins));
   if (cl.n > 0)
     TPC_LAUNCH(P, "k_scatter", s,
-               k_scatter<<<nblk(cl.n, kB256), kB256, 0, s>>>(g, cl, b.row_start, b.fill, b.perm));
+               k_scatter<<<nblk(cl.n, kB256), kB256, 0, s>>>(g, cl, b.row_start, b.zs_in, b.fill,
+                                                             b.perm, b.pyz));
   cudaMemsetAsync(b.list_counts, 0, 2 * sizeof(uint32_t), s);
   TPC_LAUNCH(P, "k_row_sort_warp", s,
-             k_row_sort_warp<<<nblk(K, 8), 256, 0, s>>>(g, cl, gd, K, b.row_start, b.es_dims,
-                                                        b.perm, b.zs_in, b.zr, b.gyz, b.gorig,
+             k_row_sort_warp<<<nblk(K, 8), 256, 0, s>>>(g, gd, K, b.row_start, b.es_dims,
+                                                        b.perm, b.pyz, b.zr, b.gyz, b.gorig,
                                                         b.gseg, b.bin_start, b.mid_list,
                                                         b.list_counts, b.big_list,
                                                         b.list_counts + 1));
-  size_t smem = kSortTile * sizeof(unsigned long long);
+  size_t smem = sort_smem(kSortTile, gd.nb_max);
   TPC_LAUNCH(P, "k_row_sort_mid", s,
-             k_row_sort_list<<<4 * 148, 512, smem, s>>>(g, cl, gd, kSortTile, b.row_start,
-                                                        b.es_dims, b.perm, b.zs_in, b.zr, b.gyz,
+             k_row_sort_list<<<4 * 148, 512, smem, s>>>(g, gd, kSortTile, b.row_start,
+                                                        b.es_dims, b.perm, b.pyz, b.zr, b.gyz,
                                                         b.gorig, b.gseg, b.bin_start, b.mid_list,
                                                         b.list_counts, err));
-  size_t smem_big = kSortTileBig * sizeof(unsigned long long);
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_row_sort_list, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem_big);
-    attr = true;
-  }
+  size_t smem_big = sort_smem(kSortTileBig, gd.nb_max);
   TPC_LAUNCH(P, "k_row_sort_big", s,
-             k_row_sort_list<<<148, 1024, smem_big, s>>>(g, cl, gd, kSortTileBig, b.row_start,
-                                                         b.es_dims, b.perm, b.zs_in, b.zr, b.gyz,
+             k_row_sort_list<<<148, 1024, smem_big, s>>>(g, gd, kSortTileBig, b.row_start,
+                                                         b.es_dims, b.perm, b.pyz, b.zr, b.gyz,
                                                          b.gorig, b.gseg, b.bin_start,
                                                          b.big_list, b.list_counts + 1, err));
 }
 
 void setup_find_kernels() {
   cudaFuncSetAttribute(k_group_rank, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRankSmem);
+  cudaFuncSetAttribute(k_row_sort_list, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)sort_smem(kSortTileBig, kGridBinsMax));
 }
 
 int tracklet_blocks_per_sm(int block) {

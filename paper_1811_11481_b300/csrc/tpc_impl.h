@@ -77,6 +77,7 @@ struct FindBuf {
   float* zr;            // [n_events * 2 * 2] z0, 1/dz per (event, side)
   float* zs_in;         // [n] seed z in input order
   uint32_t* perm;       // [n] input index in bucket order
+  float2* pyz;          // [n] (y, seeding z) in bucket order
   // grid order (bucket, bin, input index)
   float2* gyz;          // [n] (y, seed z)
   uint32_t* gorig;      // [n] input index
@@ -219,6 +220,7 @@ struct Prof {
     if (P) (P)->end(S);             \
   } while (0)
 
+constexpr int kGridBinsMax = 8192;  // search-grid bins per row at most
 constexpr int kSmallGroup = 64;  // start-hit groups up to this size are ranked by a scan
 constexpr int kRankTile = 8192;   // emitted tracklets a block ranks in shared memory
 constexpr int kSortTile = 4096;      // pad-row bucket tile of the common sort
