@@ -275,7 +275,7 @@ tpc_status tpc_get_grid(tpc_ctx* ctx, uint32_t* order, uint32_t* row_start);
  * geo, params: host, as for tpc_create (params NULL = defaults); stream: a
  * cudaStream_t. Asynchronous: kernel errors surface at the next stream sync. */
 #define TPC_NOALLOC_MAX_ASSIGNED (1 << 20)
-#define TPC_NOALLOC_SCRATCH_BYTES (5 * TPC_NOALLOC_MAX_ASSIGNED)
+#define TPC_NOALLOC_SCRATCH_BYTES (5 * TPC_NOALLOC_MAX_ASSIGNED + 1024)
 tpc_status tpc_refit_noalloc(const tpc_geometry* geo, const tpc_params* params, void* stream,
                              int64_t n_tracks, int64_t n_assigned, const uint32_t* track_start,
                              const float* yc, const float* zc, const uint8_t* row,

@@ -16,6 +16,7 @@ struct tpc_ctx {
   Params prm{};
   tpc_params prm_c{};
   Cal cal{};
+  float* d_rowx = nullptr;       // [TPC_MAX_ROWS] pad-row positions
   float* d_spline = nullptr;
   float* d_spl_bound = nullptr;
   uint32_t* d_err = nullptr;
@@ -282,7 +283,6 @@ tpc_status tpc_create(const tpc_geometry* geo, const tpc_params* params, void* s
   ctx->stream = (cudaStream_t)stream;
   Geo& g = ctx->geo;
   std::memset(&g, 0, sizeof(g));
-  for (int r = 0; r < geo->n_rows; ++r) g.row_x[r] = geo->row_x[r];
   g.n_rows = geo->n_rows;
   g.tan_half = geo->tan_half;
   g.L = geo->drift_length;
@@ -298,6 +298,7 @@ tpc_status tpc_create(const tpc_geometry* geo, const tpc_params* params, void* s
       ctx->err = cudaGetErrorString(e);
     }
   };
+  chk(cudaMalloc(&ctx->d_rowx, sizeof(float) * TPC_MAX_ROWS));
   chk(cudaMalloc(&ctx->d_spline, sizeof(float) * TPC_SPLINE_SIZE));
   chk(cudaMalloc(&ctx->d_spl_bound, sizeof(float) * 4));
   chk(cudaMalloc(&ctx->d_err, sizeof(uint32_t)));
@@ -319,6 +320,8 @@ tpc_status tpc_create(const tpc_geometry* geo, const tpc_params* params, void* s
     tpc_destroy(ctx);
     return st;
   }
+  chk(cudaMemcpy(ctx->d_rowx, geo->row_x, sizeof(float) * geo->n_rows, cudaMemcpyHostToDevice));
+  g.rx = ctx->d_rowx;
   chk(cudaMemsetAsync(ctx->d_spline, 0, sizeof(float) * TPC_SPLINE_SIZE, ctx->stream));
   chk(cudaMemsetAsync(ctx->d_spl_bound, 0, sizeof(float) * 4, ctx->stream));
   chk(cudaMemsetAsync(ctx->d_err, 0, sizeof(uint32_t), ctx->stream));
@@ -341,7 +344,7 @@ tpc_status tpc_create(const tpc_geometry* geo, const tpc_params* params, void* s
 void tpc_destroy(tpc_ctx* ctx) {
   if (!ctx) return;
   cudaStreamSynchronize(ctx->stream);
-  void* ptrs[] = {ctx->d_spline, ctx->d_spl_bound, ctx->d_err, ctx->d_cnt,
+  void* ptrs[] = {ctx->d_rowx, ctx->d_spline, ctx->d_spl_bound, ctx->d_err, ctx->d_cnt,
                   ctx->fb.cnt, ctx->fb.row_start, ctx->fb.fill, ctx->fb.zmm, ctx->fb.zr,
                   ctx->fb.zs_in, ctx->fb.perm, ctx->fb.pyz, ctx->fb.gyz,
                   ctx->fb.gorig, ctx->fb.gseg, ctx->fb.bin_start, ctx->fb.big_list, ctx->fb.mid_list, ctx->fb.list_counts,

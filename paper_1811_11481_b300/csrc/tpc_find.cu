@@ -166,7 +166,7 @@ __global__ void k_scan_rows(Geo g, int K, int n_events, GridDims gd, const uint3
   __syncthreads();
   int nes = n_events * kNS;
   int R = g.n_rows;
-  float xm = g.row_x[R / 2];
+  float xm = g.rx[R / 2];
   float W = 2.0f * (xm * g.tan_half + gd.y_margin);
   for (int base = 0; base < nes; base += blockDim.x) {
     int es = base + threadIdx.x;
@@ -230,7 +230,7 @@ __device__ __forceinline__ Bins es_bins(const uint2* es_dims, int es) {
   return b;
 }
 __device__ __forceinline__ int bin_y(const Geo& g, const GridDims& gd, int r, int ny, float y) {
-  float hw = g.row_x[r] * g.tan_half + gd.y_margin;
+  float hw = g.rx[r] * g.tan_half + gd.y_margin;
   float v = (y + hw) * ((float)ny / (2.0f * hw));
   int iy = (int)floorf(v);
   if (!(v == v)) iy = 0;
@@ -534,7 +534,7 @@ __global__ void k_neighbours(Geo g, Params p, GridDims gd, const uint2* es_dims,
     int es = seg / g.n_rows;
     int e = es / kNS, s = es % kNS;
     int side = e * 2 + (s >= 18 ? 1 : 0);
-    float xh = g.row_x[r], xu = g.row_x[r + 1], xd = g.row_x[r - 1];
+    float xh = g.rx[r], xu = g.rx[r + 1], xd = g.rx[r - 1];
     float2 hh = gyz[h];
     float yh = hh.x, zh = hh.y;
     float dxu = xu - xh, dxd = xh - xd;
@@ -709,7 +709,7 @@ __device__ __forceinline__ void calibrate_follow(const Geo& g, const Cal& c, boo
   float za = zs + shift;
   if (spl_on) {
     float d[2];
-    spline_eval(g, c, sec, g.row_x[r], y, fabsf(za), d);
+    spline_eval(g, c, sec, g.rx[r], y, fabsf(za), d);
     yc = y + d[0];
     zc = za + d[1];
   } else {
@@ -832,7 +832,7 @@ __global__ void __launch_bounds__(BS) k_tracklets(Geo g, Cal c, Params p, GridDi
       ev = es / kNS;
       sec = es % kNS;
       BB = es_bins(es_dims, es);
-      seed_two_points(st, C, x, p.c0t, g.row_x[r0], yz0.x, yz0.y, g.row_x[rl], yzl.x, yzl.y);
+      seed_two_points(st, C, x, p.c0t, g.rx[r0], yz0.x, yz0.y, g.rx[rl], yzl.x, yzl.y);
       that = 0.0;
       shift = 0.0f;
       bx = x;
@@ -845,7 +845,7 @@ __global__ void __launch_bounds__(BS) k_tracklets(Geo g, Cal c, Params p, GridDi
       nh = 0;
       failed = false;
     }
-    bool ok = propagate(g.kB, p.s_max, st, C, x, g.row_x[r]);
+    bool ok = propagate(g.kB, p.s_max, st, C, x, g.rx[r]);
     bool have = false;
     float my = 0.0f, mz = 0.0f;
     int j = -1;
@@ -883,7 +883,7 @@ __global__ void __launch_bounds__(BS) k_tracklets(Geo g, Cal c, Params p, GridDi
         float y0, z0, y1, z1;
         calibrate_follow(g, c, spl_on, sec, r0, yz0.x, yz0.y, shift, y0, z0);
         calibrate_follow(g, c, spl_on, sec, rl, yzl.x, yzl.y, shift, y1, z1);
-        seed_two_points(st, C, x, p.c0t, g.row_x[r0], y0, z0, g.row_x[rl], y1, z1);
+        seed_two_points(st, C, x, p.c0t, g.rx[r0], y0, z0, g.rx[rl], y1, z1);
         phase = kSeed2;
         h = h0;
         r = r0;

@@ -20,8 +20,12 @@ constexpr int kNS = TPC_N_SECTORS;
 constexpr int kMaxRows = TPC_MAX_ROWS;
 constexpr int kSpl = TPC_SPLINE_N;
 
+// Detector geometry as the kernels see it. The row positions are read
+// through a pointer to memory of the executing side (device memory for the
+// kernels): an array held in the kernel parameters would be read with one
+// serialised constant-cache access per distinct row in a warp.
 struct Geo {
-  float row_x[kMaxRows];
+  const float* rx;  // [n_rows] pad-row plane positions (cm)
   int32_t n_rows;
   float tan_half;
   float L;
@@ -149,7 +153,7 @@ TPC_HD void calibrate(const Geo& g, const Cal& c, bool spline_on, int mode, int 
   float za = abs_z(g, c, mode, z, t, sector, that);
   if (spline_on) {
     float d[2];
-    spline_eval(g, c, sector, g.row_x[row], y, fabsf(za), d);
+    spline_eval(g, c, sector, g.rx[row], y, fabsf(za), d);
     yc = y + d[0];
     zc = za + d[1];
   } else {

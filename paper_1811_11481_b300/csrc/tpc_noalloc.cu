@@ -22,7 +22,9 @@ using namespace tpc;
 // pass of the three-pass refit.
 constexpr int64_t kMaxAssigned = TPC_NOALLOC_MAX_ASSIGNED;
 constexpr size_t kMetaBytes = sizeof(uint32_t) * (size_t)kMaxAssigned;
-constexpr size_t kScratchBytes = kMetaBytes + (size_t)kMaxAssigned;
+constexpr size_t kRowXBytes = 1024;  // pad-row positions (TPC_MAX_ROWS floats)
+constexpr size_t kScratchBytes = kRowXBytes + kMetaBytes + (size_t)kMaxAssigned;
+static_assert(sizeof(float) * TPC_MAX_ROWS <= kRowXBytes, "row table");
 static_assert(kScratchBytes == TPC_NOALLOC_SCRATCH_BYTES, "scratch size");
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
@@ -46,6 +48,16 @@ cudaError_t scratch_of_current_device(unsigned char** out) {
   }
   *out = g_scratch_ptr[dev];
   return cudaSuccess;
+}
+
+// The pad-row positions travel by value in the launch (no host memory is
+// read by a copy) into the scratch array.
+struct RowX {
+  float v[TPC_MAX_ROWS];
+};
+__global__ void k_na_rowx(RowX in, int n_rows, float* out) {
+  int r = threadIdx.x;
+  if (r < n_rows) out[r] = in.v[r];
 }
 
 __global__ void k_na_meta(int64_t n_assigned, const uint8_t* row, const uint8_t* flags,
@@ -112,7 +124,9 @@ extern "C" tpc_status tpc_refit_noalloc(const tpc_geometry* geo, const tpc_param
   if (params) pc = *params;
   else tpc_default_params(&pc);
   Geo g;
-  for (int r = 0; r < TPC_MAX_ROWS; ++r) g.row_x[r] = r < geo->n_rows ? geo->row_x[r] : 0.0f;
+  RowX rx;
+  for (int r = 0; r < TPC_MAX_ROWS; ++r) rx.v[r] = r < geo->n_rows ? geo->row_x[r] : 0.0f;
+  g.rx = reinterpret_cast<const float*>(scratch);
   g.n_rows = geo->n_rows;
   g.tan_half = geo->tan_half;
   g.L = geo->drift_length;
@@ -128,8 +142,9 @@ extern "C" tpc_status tpc_refit_noalloc(const tpc_geometry* geo, const tpc_param
   cfg.min_acc_reject = pc.min_acc_reject;
   for (int i = 0; i < 5; ++i) cfg.c0r[i] = pc.c0r[i];
   cudaStream_t s = (cudaStream_t)stream;
-  uint32_t* meta = reinterpret_cast<uint32_t*>(scratch);
-  uint8_t* rej = scratch + kMetaBytes;
+  uint32_t* meta = reinterpret_cast<uint32_t*>(scratch + kRowXBytes);
+  uint8_t* rej = scratch + kRowXBytes + kMetaBytes;
+  k_na_rowx<<<1, TPC_MAX_ROWS, 0, s>>>(rx, g.n_rows, reinterpret_cast<float*>(scratch));
   if (n_assigned > 0)
     k_na_meta<<<(int)((n_assigned + 255) / 256), 256, 0, s>>>(n_assigned, row, flags, g.n_rows,
                                                               meta);

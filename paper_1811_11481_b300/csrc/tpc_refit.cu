@@ -327,7 +327,7 @@ __global__ void __launch_bounds__(kCgThreads) k_calib_grad(
       uint32_t sl = slot[T];
       size_t wpos = ((size_t)wbase[sl >> 5] + (j - track_start[T])) * 32 + (sl & 31);
       int r = cl.row[i], s = cl.sector[i];
-      float x = g.row_x[r];
+      float x = g.rx[r];
       float y = cl.y[i];
       float za = abs_z(g, c, cl.mode, cl.mode == 0 ? cl.z[i] : 0.0f,
                        cl.mode == 1 ? cl.t[i] : 0.0, s, that);

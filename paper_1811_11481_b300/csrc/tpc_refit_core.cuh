@@ -59,8 +59,8 @@ TPC_HD float cl_var(const RefitCfg& p, uint32_t meta) {
 TPC_HD bool seed3(const Geo& g, const TrackIn& in, const Lay& ly, int n, float st[5]) {
   if (n < 3) return false;
   int i0 = 0, im = n / 2, i2 = n - 1;
-  float x0 = g.row_x[in.meta[ly.at(i0)] & 0xffu], xm = g.row_x[in.meta[ly.at(im)] & 0xffu],
-        x2 = g.row_x[in.meta[ly.at(i2)] & 0xffu];
+  float x0 = g.rx[in.meta[ly.at(i0)] & 0xffu], xm = g.rx[in.meta[ly.at(im)] & 0xffu],
+        x2 = g.rx[in.meta[ly.at(i2)] & 0xffu];
   float y0 = in.yc[ly.at(i0)], ym = in.yc[ly.at(im)], y2 = in.yc[ly.at(i2)];
   float ax = xm - x0, ay = ym - y0, bx = x2 - x0, by = y2 - y0, ex = x2 - xm, ey = y2 - ym;
   float cross = ax * by - ay * bx;
@@ -108,7 +108,7 @@ TPC_HD RefitOut refit_track(const Geo& g, const RefitCfg& p, const TrackIn& in, 
   }
   if (seed_out)
     for (int i = 0; i < 5; ++i) seed_out[i] = st[i];
-  float x = g.row_x[in.meta[ly.at(n - 1)] & 0xffu];
+  float x = g.rx[in.meta[ly.at(n - 1)] & 0xffu];
   set_diag(C, p.c0r);
   float chi2 = 0.0f;
   int ndf = 0;
@@ -135,7 +135,7 @@ TPC_HD RefitOut refit_track(const Geo& g, const RefitCfg& p, const TrackIn& in, 
           for (int j = 0; j < 5; ++j) ckpt[ly.ck(pass, k, j)] = st[j];
           for (int j = 0; j < 15; ++j) ckpt[ly.ck(pass, k, 5 + j)] = C[j];
         }
-        if (!propagate(p.kB, p.s_max, st, C, x, g.row_x[m & 0xffu])) {
+        if (!propagate(p.kB, p.s_max, st, C, x, g.rx[m & 0xffu])) {
           o.status = 1;
           o.x = x;
           return o;
@@ -385,7 +385,7 @@ TPC_HD void refit_backward_track(const Geo& g, const RefitCfg& p, const TrackIn&
     gyc[ly.at(k)] = 0.0f;
     gzc[ly.at(k)] = 0.0f;
   }
-  auto xof = [&](int i) { return g.row_x[in.meta[ly.at(i)] & 0xffu]; };
+  auto xof = [&](int i) { return g.rx[in.meta[ly.at(i)] & 0xffu]; };
   auto idx_of = [&](int pass, int k) { return pass == 2 ? k : n - 1 - k; };
   float xend[4];
   xend[0] = xof(n - 1);
@@ -477,8 +477,8 @@ TPC_HD void refit_backward_track(const Geo& g, const RefitCfg& p, const TrackIn&
         rjq2 = rej[ly.at(iq)];
       }
       // the current step, from its checkpoint
-      float xprev = kp >= 0 ? g.row_x[mp & 0xffu] : xend[pass - 1];
-      float xi = g.row_x[mc & 0xffu];
+      float xprev = kp >= 0 ? g.rx[mp & 0xffu] : xend[pass - 1];
+      float xi = g.rx[mc & 0xffu];
       float pp[5];
       for (int j = 0; j < 5; ++j) pp[j] = p0[j];
       float xx = xprev;
