@@ -718,53 +718,82 @@ __device__ __forceinline__ void calibrate_follow(const Geo& g, const Cal& c, boo
   }
 }
 
-// Nearest cluster of row r (calibrated frame) by the normalised distance,
-// inside the pick-up cut; ties to the lowest input index. Returns grid
-// position or -1, and the calibrated coordinates of the pick.
-__device__ int pick(const Geo& g, const Cal& c, const Params& p, const GridDims& gd,
-                    const Bins& BB, const Grid& G, int ev, int sec, int r, const float st[5],
-                    const float C[15], double that, float shift, bool spl_on, float dymax,
-                    float dzmax, float& ycb, float& zcb) {
+enum : int { kSeed1 = 0, kSeed2 = 1, kOut = 2, kIn = 3, kDone = 4 };
+
+// The measurement of one tracklet step. In the seed phases it is the chain
+// hit h, taken without a cut (in seeding coordinates in phase kSeed1,
+// calibrated in kSeed2). When following, it is the nearest cluster of row r
+// (calibrated frame) by the normalised distance inside the pick-up cut, ties
+// to the lowest input index. Returns the grid position or -1, and the
+// calibrated coordinates. Both cases run the same candidate loop, flattened
+// over up to four z rows of bins, so that the lanes of a warp stay together
+// whatever phase their tracklets are in.
+__device__ int step_measurement(const Geo& g, const Cal& c, const Params& p, const GridDims& gd,
+                                const Bins& BB, const Grid& G, int ev, int sec, int r,
+                                const float st[5], const float C[15], float shift, bool spl_on,
+                                float dymax, float dzmax, int phase, int h, float& ycb,
+                                float& zcb) {
+  const bool seed = phase <= kSeed2;
   int side = ev * 2 + (sec >= 18 ? 1 : 0);
   float sig2 = p.sigma * p.sigma;
   float vy = C[0] + sig2, vz = C[2] + sig2;
   float ivy = 1.0f / vy, ivz = 1.0f / vz;
-  float wy = sqrtf(p.chi2_pick * vy), wz = sqrtf(p.chi2_pick * vz);
-  float eps = 0.01f + 1.0e-6f * fabsf(shift);
-  float yp = st[0], zp = st[1] - shift;
-  Box B = make_box(g, gd, G.zr, BB, r, side, yp - wy - dymax - eps, yp + wy + dymax + eps,
-                   zp - wz - dzmax - eps, zp + wz + dzmax + eps);
+  int iz0 = 0, iz1 = 0, iy0 = 0, iy1 = 0;
+  if (!seed) {
+    float wy = sqrtf(p.chi2_pick * vy), wz = sqrtf(p.chi2_pick * vz);
+    float eps = 0.01f + 1.0e-6f * fabsf(shift);
+    float yp = st[0], zp = st[1] - shift;
+    Box B = make_box(g, gd, G.zr, BB, r, side, yp - wy - dymax - eps, yp + wy + dymax + eps,
+                     zp - wz - dzmax - eps, zp + wz + dzmax + eps);
+    iz0 = B.iz0;
+    iz1 = B.iz1;
+    iy0 = B.iy0;
+    iy1 = B.iy1;
+  }
   const uint32_t* __restrict__ bs = G.bin_start + BB.base + (size_t)r * (BB.nb + 1);
   int best = -1;
   float bd = 0.0f;
-  for (int izb = B.iz0; izb <= B.iz1; izb += 4) {
+  for (int izb = iz0; izb <= iz1; izb += 4) {
     // bin offsets of up to four z rows of the box, loaded together
     uint32_t lo[4], hi[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       int iz = izb + q;
-      bool in = iz <= B.iz1;
-      lo[q] = in ? __ldg(bs + iz * BB.ny + B.iy0) : 0u;
-      hi[q] = in ? __ldg(bs + iz * BB.ny + B.iy1 + 1) : 0u;
+      bool in = !seed && iz <= iz1;
+      lo[q] = in ? __ldg(bs + iz * BB.ny + iy0) : 0u;
+      hi[q] = in ? __ldg(bs + iz * BB.ny + iy1 + 1) : 0u;
     }
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      for (uint32_t j = lo[q]; j < hi[q]; ++j) {
-        float2 yz = __ldg(G.gyz + j);
-        float yc, zc;
-        calibrate_follow(g, c, spl_on, sec, r, yz.x, yz.y, shift, yc, zc);
-        float ry = yc - st[0];
-        float rz = zc - st[1];
-        float d2 = (ry * ry) * ivy + (rz * rz) * ivz;
-        if (!(d2 <= p.chi2_pick)) continue;
-        bool take = best < 0 || d2 < bd;
-        if (!take && d2 == bd) take = __ldg(G.gorig + j) < __ldg(G.gorig + best);
-        if (take) {
-          best = (int)j;
-          bd = d2;
-          ycb = yc;
-          zcb = zc;
-        }
+    if (seed) {
+      lo[0] = (uint32_t)h;
+      hi[0] = (uint32_t)h + 1u;
+    }
+    const uint32_t c0 = hi[0] - lo[0], c1 = c0 + (hi[1] - lo[1]), c2 = c1 + (hi[2] - lo[2]);
+    const uint32_t total = c2 + (hi[3] - lo[3]);
+    for (uint32_t k = 0; k < total; ++k) {
+      uint32_t j = k < c0 ? lo[0] + k
+                 : k < c1 ? lo[1] + (k - c0)
+                 : k < c2 ? lo[2] + (k - c1)
+                          : lo[3] + (k - c2);
+      float2 yz = __ldg(G.gyz + j);
+      float yc = yz.x, zc = yz.y;
+      if (phase != kSeed1) calibrate_follow(g, c, spl_on, sec, r, yz.x, yz.y, shift, yc, zc);
+      if (seed) {
+        best = (int)j;
+        ycb = yc;
+        zcb = zc;
+        continue;
+      }
+      float ry = yc - st[0];
+      float rz = zc - st[1];
+      float d2 = (ry * ry) * ivy + (rz * rz) * ivz;
+      if (!(d2 <= p.chi2_pick)) continue;
+      bool take = best < 0 || d2 < bd;
+      if (!take && d2 == bd) take = __ldg(G.gorig + j) < __ldg(G.gorig + best);
+      if (take) {
+        best = (int)j;
+        bd = d2;
+        ycb = yc;
+        zcb = zc;
       }
     }
   }
@@ -781,8 +810,6 @@ __device__ int pick(const Geo& g, const Cal& c, const Params& p, const GridDims&
 //   phase 1: seed fit in calibrated coordinates (after the collision time)
 //   phase 2: outward following from the seed end
 //   phase 3: inward following from the outermost pick down to row 0
-enum : int { kSeed1 = 0, kSeed2 = 1, kOut = 2, kIn = 3, kDone = 4 };
-
 template <int BS>
 __global__ void __launch_bounds__(BS) k_tracklets(Geo g, Cal c, Params p, GridDims gd, Grid G,
                                                   const uint2* es_dims, int mode,
@@ -850,19 +877,9 @@ __global__ void __launch_bounds__(BS) k_tracklets(Geo g, Cal c, Params p, GridDi
     float my = 0.0f, mz = 0.0f;
     int j = -1;
     if (ok) {
-      if (phase == kSeed1) {
-        float2 yz = G.gyz[h];
-        my = yz.x;
-        mz = yz.y;
-        have = true;
-      } else if (phase == kSeed2) {
-        float2 yz = G.gyz[h];
-        calibrate_follow(g, c, spl_on, sec, r, yz.x, yz.y, shift, my, mz);
-        have = true;
-      } else {
-        j = pick(g, c, p, gd, BB, G, ev, sec, r, st, C, that, shift, spl_on, dymax, dzmax, my, mz);
-        have = j >= 0;
-      }
+      j = step_measurement(g, c, p, gd, BB, G, ev, sec, r, st, C, shift, spl_on, dymax, dzmax,
+                           phase, h, my, mz);
+      have = j >= 0;
       if (have) apply_update(st, C, innovation(st, C, my, mz, sig2, sig2));
     }
     bool start_in = false;
