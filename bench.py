@@ -137,15 +137,19 @@ def algorithmic_bytes(kernel, c):
     ev = 4 if c["n_events"] > 1 else 0
     model = {
         "k_hist": n * (2 + zt + ev + 4),
-        "k_scatter": n * (2 + ev + 4),
-        "k_row_sort": n * (4 + 4 + 4 + zt * (mode == 1) + 16 + 8 * (mode == 1)),
+        "k_scatter": n * (2 + ev + 4 + 4 + 4 + 8),
+        "k_row_sort": n * (4 + 8 + 8 + 4 + 4 + 4),
         "k_neighbours": n * (12 + 8),
         "k_clean": n * (8 + 8),
-        "k_write_starts": n * 8 + ntl * 4,
-        "k_tracklets": n * 12 + ntl * (4 + 152 * 4 + 16) + nh * (8 + 8 * (mode == 1)),
-        "k_select_count": ntl * (152 * 4 + 8) + nh * 8,
-        "k_select_write": ntl * (152 * 4 + 16) + na * 8 + nt * 16,
+        "k_write_starts": n * 8 + ntl * 8,
+        # grid coordinates and input index once; per tracklet its start, seed
+        # end, hit count, collision time and row range; per hit its row entry
+        "k_tracklets": n * 12 + ntl * (8 + 16) + nh * 4,
+        "k_tl_weight": ntl * 12 + nh * (4 + 8 + 8),
+        "k_select_count": ntl * (4 + 4 + 8 + 8) + nh * (4 + 8),
+        "k_select_write": ntl * 24 + nh * (4 + 8) + na * 12 + nt * 16,
         "k_calib": na * (4 + 4 + 8 + 4 + zt + 3 + 12),
+        "k_interleave": na * (4 + 12 + 12),
         "k_refit": na * (12 + 1) + nt * (5 + 15 + 4) * 4,
         "k_refit_bwd": na * (12 + 1 + 8) + nt * 4,
         "k_calib_grad": na * (8 + 8 + 8 + 4 + zt + 2 + 8 + 8),
