@@ -200,6 +200,36 @@ def load_peaks():
 
 
 # ------------------------------------------------------------- our arm
+def track_quality(ev, track_start, cluster_idx, min_findable=70, purity=0.9):
+    """Efficiency, fake and clone rates of found tracks against the
+    generator's truth segments (one per particle, sector and leg): a segment
+    with at least min_findable clusters is findable; a track matches the
+    segment of the majority of its clusters if that majority is at least
+    `purity` of them, and is fake otherwise."""
+    ts = np.asarray(track_start, np.int64)
+    nt = ts.size - 1
+    if nt <= 0:
+        return dict(efficiency=0.0, fake_rate=0.0, clone_rate=0.0, findable=0, tracks=0)
+    seg = np.asarray(ev.segment, np.int64)[np.asarray(cluster_idx, np.int64)]
+    lens = np.diff(ts)
+    tid = np.repeat(np.arange(nt), lens)
+    M = int(seg.max()) + 2
+    key, cnt = np.unique(tid * M + (seg + 1), return_counts=True)
+    ktid, kseg = key // M, key % M - 1
+    order = np.lexsort((-cnt, ktid))
+    first = order[np.r_[True, ktid[order][1:] != ktid[order][:-1]]]
+    maj_seg, maj_cnt = kseg[first], cnt[first]
+    good = (maj_seg >= 0) & (maj_cnt >= purity * lens[ktid[first]])
+    matched, per = np.unique(maj_seg[good], return_counts=True)
+    truth = np.bincount(np.asarray(ev.segment, np.int64)[np.asarray(ev.segment) >= 0])
+    findable = np.nonzero(truth >= min_findable)[0]
+    eff = float(np.isin(findable, matched).mean()) if findable.size else 0.0
+    return dict(efficiency=eff, fake_rate=float((~good).sum() / nt),
+                clone_rate=float((per - 1).sum() / nt), findable=int(findable.size), tracks=nt,
+                definition=f"findable: >= {min_findable} clusters of one (particle, sector, leg); "
+                           f"matched: >= {int(purity * 100)}% of a track's clusters from it")
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -288,6 +318,9 @@ def run_ours(args):
     nt, na, ntl = tr.counts()
     tl = tr.tracklets()
     sum_nh = int(tl["nh"].clamp(min=0).sum().item())
+    found = tr.find()
+    quality = track_quality(ev, found["track_start"].cpu().numpy(),
+                            found["cluster_idx"].cpu().numpy())
 
     def barrier():
         if world > 1:
@@ -434,7 +467,7 @@ def run_ours(args):
                 refit_fwd_ms=t_fwd, refit_fwd_nosave_ms=t_fwd_nosave, adjoint_ms=t_bwd,
                 adjoint_vs_fwd=t_bwd / t_fwd_nosave if t_fwd_nosave > 0 else None,
                 roofline=roof, kernels=kernels, gpu_launches=launches,
-                graph_replay=graph_replay,
+                graph_replay=graph_replay, track_quality=quality,
                 clocks=clk, e2e=e2e, cpu_baseline=cpu)
     if rank == 0:
         print(json.dumps(line))
