@@ -970,36 +970,83 @@ __global__ void k_tl_weight(int n_rows, int min_track_hits, const uint32_t* cnt,
                             const int32_t* nh, const int32_t* hits, const uint32_t* range,
                             const uint32_t* starts, const uint32_t* gorig,
                             unsigned long long* weight) {
-  int t = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-  int lane = threadIdx.x & 31;
-  if (t >= (int)cnt[kCntStart]) return;
-  int n = nh[t];
-  if (n < min_track_hits) return;
-  unsigned long long w = ((unsigned long long)(uint32_t)n << 32) |
-                         (unsigned long long)(0xffffffffu - gorig[starts[t]]);
-  uint32_t rg = range[t];
-  int rlo = (int)(rg & 0xffffu), rhi = (int)(rg >> 16);
-  const int32_t* H = hits + (size_t)t * n_rows;
-  for (int r = rlo + lane; r <= rhi; r += 32) {
-    int j = H[r];
-    if (j >= 0) atomicMax(&weight[j], w);
+  const int ntl = (int)cnt[kCntStart];
+  const int lane = threadIdx.x & 31;
+  const int nw = (int)((gridDim.x * blockDim.x) >> 5);
+  for (int t = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); t < ntl; t += nw) {
+    int n = nh[t];
+    if (n < min_track_hits) continue;
+    unsigned long long w = ((unsigned long long)(uint32_t)n << 32) |
+                           (unsigned long long)(0xffffffffu - gorig[starts[t]]);
+    uint32_t rg = range[t];
+    int rlo = (int)(rg & 0xffffu), rhi = (int)(rg >> 16);
+    const int32_t* H = hits + (size_t)t * n_rows;
+    for (int r = rlo + lane; r <= rhi; r += 32) {
+      int j = H[r];
+      if (j >= 0) atomicMax(&weight[j], w);
+    }
   }
 }
 
+// One warp per tracklet of at least min_track_hits hits: the lanes test 32
+// rows at a time for the hits whose cluster weight is the tracklet's own;
+// the track is kept if it keeps min_track_hits of them with no gap above
+// max_gap rows.
 __global__ void k_select_count(int n_rows, const Params p, const uint32_t* cnt,
                                const int32_t* nh, const int32_t* hits, const uint32_t* range,
                                const uint32_t* starts, const uint32_t* gorig,
-                               const uint32_t* gseg, const unsigned long long* weight,
-                               uint32_t* nkeep, uint32_t* tkey, uint32_t* tseg,
-                               uint32_t* grp_list, uint32_t* grp_count, uint32_t cap_grp,
-                               uint32_t* blk_tr, uint32_t* blk_cl) {
-  int t = blockIdx.x * blockDim.x + threadIdx.x;
-  uint32_t emit = 0, kept = 0;
+                               const unsigned long long* weight, uint32_t* nkeep) {
   const int ntl = (int)cnt[kCntStart];
+  const int lane = threadIdx.x & 31;
+  const int nw = (int)((gridDim.x * blockDim.x) >> 5);
+  for (int t = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); t < ntl; t += nw) {
+    uint32_t kept = 0;
+    int n = nh[t];
+    if (n >= p.min_track_hits) {
+      unsigned long long w = ((unsigned long long)(uint32_t)n << 32) |
+                             (unsigned long long)(0xffffffffu - gorig[starts[t]]);
+      const int32_t* H = hits + (size_t)t * n_rows;
+      uint32_t rg = range[t];
+      int rlo = (int)(rg & 0xffffu), rhi = (int)(rg >> 16);
+      int lastr = -1, maxgap = 0, k = 0;
+      for (int r0 = rlo; r0 <= rhi; r0 += 32) {
+        int r = r0 + lane;
+        bool own = false;
+        if (r <= rhi) {
+          int j = H[r];
+          own = j >= 0 && weight[j] == w;
+        }
+        unsigned m = __ballot_sync(0xffffffffu, own);
+        k += __popc(m);
+        // gap before each kept row: to the previous kept lane of this chunk,
+        // else to the last kept row of the chunks before
+        int gap = 0;
+        if (own) {
+          unsigned below = m & ((1u << lane) - 1u);
+          int prev = below ? r0 + 31 - __clz(below) : lastr;
+          if (prev >= 0) gap = r - prev - 1;
+        }
+        maxgap = max(maxgap, __reduce_max_sync(0xffffffffu, gap));
+        if (m) lastr = r0 + 31 - __clz(m);
+      }
+      if (k >= p.min_track_hits && maxgap <= p.max_gap) kept = (uint32_t)k;
+    }
+    if (lane == 0) nkeep[t] = kept;
+  }
+}
+
+// Per block of 256 tracklets: counts of emitted tracks and kept clusters for
+// the ordered compaction; the start hit's (event, sector, row) and input
+// index for the order of emission, and the list of large groups.
+__global__ void k_select_sum(const uint32_t* cnt, const uint32_t* nkeep, const uint32_t* starts,
+                             const uint32_t* gorig, const uint32_t* gseg, uint32_t* tkey,
+                             uint32_t* tseg, uint32_t* grp_list, uint32_t* grp_count,
+                             uint32_t cap_grp, uint32_t* blk_tr, uint32_t* blk_cl) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int ntl = (int)cnt[kCntStart];
+  uint32_t kept = 0;
   if (t < ntl) {
-    // (event, sector, row) and input index of the start hit, for the order
-    // of emission; the first tracklet of a group of more than kSmallGroup
-    // lists the group for k_group_rank
+    kept = nkeep[t];
     uint32_t h0 = starts[t];
     uint32_t seg = gseg[h0];
     tkey[t] = gorig[h0];
@@ -1010,28 +1057,8 @@ __global__ void k_select_count(int n_rows, const Params p, const uint32_t* cnt,
       if (q < cap_grp) grp_list[q] = (uint32_t)t;
     }
   }
-  if (t < (int)cnt[kCntStart] && nh[t] >= p.min_track_hits) {
-    unsigned long long w = ((unsigned long long)(uint32_t)nh[t] << 32) |
-                           (unsigned long long)(0xffffffffu - gorig[starts[t]]);
-    const int32_t* H = hits + (size_t)t * n_rows;
-    uint32_t rg = range[t];
-    int rlo = (int)(rg & 0xffffu), rhi = (int)(rg >> 16);
-    int lastr = -1, maxgap = 0, k = 0;
-    for (int r = rlo; r <= rhi; ++r) {
-      int j = H[r];
-      if (j < 0 || weight[j] != w) continue;
-      if (lastr >= 0) maxgap = max(maxgap, r - lastr - 1);
-      lastr = r;
-      ++k;
-    }
-    if (k >= p.min_track_hits && maxgap <= p.max_gap) {
-      emit = 1;
-      kept = (uint32_t)k;
-    }
-  }
-  if (t < (int)cnt[kCntStart]) nkeep[t] = kept;
   uint32_t tot_tr, tot_cl;
-  block_excl_scan(emit, &tot_tr);
+  block_excl_scan(kept ? 1u : 0u, &tot_tr);
   block_excl_scan(kept, &tot_cl);
   if (threadIdx.x == 0) {
     blk_tr[blockIdx.x] = tot_tr;
@@ -1160,10 +1187,9 @@ __global__ void k_select_write(int n_rows, const uint32_t* cnt, const int32_t* h
   uint32_t emit = kept > 0 ? 1u : 0u;
   uint32_t ex_tr = block_excl_scan(emit, nullptr);
   uint32_t ex_cl = block_excl_scan(kept, nullptr);
-  if (!emit) return;
   uint32_t id = off_tr[blockIdx.x] + ex_tr;
   uint32_t o = off_cl[blockIdx.x] + ex_cl;
-  {
+  if (emit) {
     const int ntl = (int)cnt[kCntStart];
     const uint32_t seg = tseg[t];
     // size of the group, counted up to kSmallGroup + 1
@@ -1198,21 +1224,46 @@ __global__ void k_select_write(int n_rows, const uint32_t* cnt, const int32_t* h
       o = o - k_before + k_less;
     }
   }
-  if ((int64_t)id >= cap_tr || (int64_t)(o + kept) > cap_asg) return;
-  unsigned long long w = ((unsigned long long)(uint32_t)nh[t] << 32) |
-                         (unsigned long long)(0xffffffffu - gorig[starts[t]]);
-  track_start[id] = o;
-  t_coll[id] = that[t];
-  start_hit[id] = gorig[starts[t]];
-  const int32_t* H = hits + (size_t)t * n_rows;
-  uint32_t rg = range[t];
-  int rlo = (int)(rg & 0xffffu), rhi = (int)(rg >> 16);
-  for (int r = rlo; r <= rhi; ++r) {
-    int j = H[r];
-    if (j < 0 || weight[j] != w) continue;
-    cluster_idx[o] = gorig[j];
-    asg_track[o] = id;
-    ++o;
+  bool ok = emit && (int64_t)id < cap_tr && (int64_t)(o + kept) <= cap_asg;
+  unsigned long long w = 0ull;
+  uint32_t rg = 0u;
+  if (ok) {
+    uint32_t h0 = gorig[starts[t]];
+    w = ((unsigned long long)(uint32_t)nh[t] << 32) | (unsigned long long)(0xffffffffu - h0);
+    track_start[id] = o;
+    t_coll[id] = that[t];
+    start_hit[id] = h0;
+    rg = range[t];
+  }
+  // the kept clusters in row order, the warp's tracks one after the other
+  // with the lanes on 32 rows at a time
+  const int lane = threadIdx.x & 31;
+  unsigned todo = __ballot_sync(0xffffffffu, ok);
+  while (todo) {
+    int src = __ffs(todo) - 1;
+    todo &= todo - 1;
+    int ts = __shfl_sync(0xffffffffu, t, src);
+    uint32_t tid = __shfl_sync(0xffffffffu, id, src);
+    uint32_t oo = __shfl_sync(0xffffffffu, o, src);
+    uint32_t rr = __shfl_sync(0xffffffffu, rg, src);
+    unsigned long long ww = __shfl_sync(0xffffffffu, w, src);
+    int rlo = (int)(rr & 0xffffu), rhi = (int)(rr >> 16);
+    const int32_t* H = hits + (size_t)ts * n_rows;
+    for (int r0 = rlo; r0 <= rhi; r0 += 32) {
+      int r = r0 + lane;
+      int j = -1;
+      if (r <= rhi) {
+        j = H[r];
+        if (j >= 0 && weight[j] != ww) j = -1;
+      }
+      unsigned m = __ballot_sync(0xffffffffu, j >= 0);
+      if (j >= 0) {
+        uint32_t pos = oo + __popc(m & ((1u << lane) - 1u));
+        cluster_idx[pos] = gorig[j];
+        asg_track[pos] = tid;
+      }
+      oo += __popc(m);
+    }
   }
 }
 
@@ -1422,14 +1473,18 @@ void launch_find(Prof* P, const Geo& g, const Cal& c, const Params& p, const ClI
   else TPC_TRACKLETS(128)
 #undef TPC_TRACKLETS
   TPC_LAUNCH(P, "k_tl_weight", s,
-             k_tl_weight<<<nblk(b.cap_tl * 32, kB256), kB256, 0, s>>>(
+             k_tl_weight<<<min(nblk(b.cap_tl * 32, kB256), 16 * 148), kB256, 0, s>>>(
                  g.n_rows, p.min_track_hits, cnt, b.nh, b.hits, b.range, b.starts, b.gorig,
                  b.weight));
   int nsel = nblk(b.cap_tl, kB256);
   cudaMemsetAsync(b.grp_count, 0, sizeof(uint32_t), s);
-  TPC_LAUNCH(P, "k_select_count", s, k_select_count<<<nsel, kB256, 0, s>>>(g.n_rows, p, cnt, b.nh, b.hits, b.range, b.starts, b.gorig,
-                                        b.gseg, b.weight, b.nkeep, b.tkey, b.tseg, b.grp_list,
-                                        b.grp_count, b.cap_grp, b.blk_a, b.blk_b));
+  TPC_LAUNCH(P, "k_select_count", s,
+             k_select_count<<<min(nblk(b.cap_tl * 32, kB256), 16 * 148), kB256, 0, s>>>(
+                 g.n_rows, p, cnt, b.nh, b.hits, b.range, b.starts, b.gorig, b.weight, b.nkeep));
+  TPC_LAUNCH(P, "k_select_sum", s,
+             k_select_sum<<<nsel, kB256, 0, s>>>(cnt, b.nkeep, b.starts, b.gorig, b.gseg, b.tkey,
+                                                 b.tseg, b.grp_list, b.grp_count, b.cap_grp,
+                                                 b.blk_a, b.blk_b));
   TPC_LAUNCH(P, "k_group_rank", s,
              k_group_rank<<<2 * 148, 1024, kRankSmem, s>>>(cnt, b.tkey, b.tseg, b.nkeep,
                                                           b.grp_list, b.grp_count, b.cap_grp,

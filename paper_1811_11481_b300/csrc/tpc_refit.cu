@@ -289,6 +289,7 @@ __global__ void __launch_bounds__(kCgThreads) k_calib_grad(
   int kx = 0;
   // a non-finite gradient leaves the spline sums to k_calib_reduce (NaN)
   const bool fixed_ok = grad_fixed_exponent(*gmax, n, kx);
+  const bool spl_on = c.spl_bound[2] > 0.0f;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int nwarps = gridDim.x * (kCgThreads / 32);
   const int gw = blockIdx.x * (kCgThreads / 32) + w;
@@ -347,7 +348,8 @@ __global__ void __launch_bounds__(kCgThreads) k_calib_grad(
       spline_basis(fw, bw);
       o0 = s * 2 * kComp + (iw * kSpl + iv) * kSpl + iu;
       // gradient through the distortion itself: d(spline)/d(y, z) of both
-      // components, and the drift-time chain for v_drift and t0
+      // components (zero when no coefficient is set: the forward then skips
+      // the spline too), and the drift-time chain for v_drift and t0
       float dvdy = (vr > 0.0f && vr < 1.0f) ? 1.0f / (x * (2.0f * g.tan_half)) : 0.0f;
       float dwdz = (wr > 0.0f && wr < 1.0f) ? (za >= 0.0f ? 1.0f : -1.0f) / g.L : 0.0f;
       float dbv[4], dbw[4];
@@ -361,7 +363,7 @@ __global__ void __launch_bounds__(kCgThreads) k_calib_grad(
       dbasis(fv, dbv);
       dbasis(fw, dbw);
       float dval_dv[2] = {0.f, 0.f}, dval_dw[2] = {0.f, 0.f};
-      for (int cp = 0; cp < 2; ++cp) {
+      for (int cp = 0; cp < (spl_on ? 2 : 0); ++cp) {
         const float* cf = c.spline + (s * 2 + cp) * kComp;
         for (int cc = 0; cc < 4; ++cc)
           for (int b2 = 0; b2 < 4; ++b2) {
