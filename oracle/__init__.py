@@ -22,7 +22,9 @@ import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "oracle.cpp")
-LIB = os.path.join(HERE, "liborc.so")
+# TPC_ORACLE_LIB: a prebuilt library to load instead (the mutation tests
+# build variants of oracle.cpp with a planted mistake and run the pins on them)
+LIB = os.environ.get("TPC_ORACLE_LIB") or os.path.join(HERE, "liborc.so")
 N_SPLINE = 36 * 2 * 8 * 8 * 8
 
 CXXFLAGS = ["-O2", "-std=c++17", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
@@ -31,6 +33,8 @@ CXXFLAGS = ["-O2", "-std=c++17", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
 
 def build(force=False):
     """Compile liborc.so (g++, IEEE-strict)."""
+    if os.environ.get("TPC_ORACLE_LIB"):
+        return LIB
     if (not force and os.path.exists(LIB)
             and os.path.getmtime(LIB) >= os.path.getmtime(SRC)):
         return LIB

@@ -1,0 +1,78 @@
+"""Planted mistakes in the oracle: each variant of oracle.cpp below carries one
+plausible error (a flipped sign, a dropped term, a swapped index or operand,
+an off-by-one in a rule) and must make at least one pin of
+tests/test_oracle_pins.py fail. The variants are compiled on the CPU with the
+oracle's own flags; the pins run against them in child processes
+(TPC_ORACLE_LIB points the oracle package at the variant)."""
+import concurrent.futures as cf
+import os
+import subprocess
+import sys
+import tempfile
+
+import pytest
+
+import oracle
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+# name: (text in oracle.cpp, replacement)
+MUTANTS = {
+ 'curvature_sign': ("R s2 = s - kap * dx;", "R s2 = s + kap * dx;"),
+ 'jac_ys_index': ("R Jys = dx * dTds;", "R Jys = dx * dTdq;"),
+ 'cov_transpose': ("acc = acc + Tm[i][l2] * J[j][l2];", "acc = acc + Tm[i][l2] * J[l2][j];"),
+ 'gain_swap': ("K1[i] = st.C[i][0] * in.W01 + st.C[i][1] * in.W11;", "K1[i] = st.C[i][0] * in.W11 + st.C[i][1] * in.W01;"),
+ 'w01_sign': ("in.W01 = -(S01 * idet);", "in.W01 = (S01 * idet);"),
+ 'basis_const': ("b[1] = ((R(3) * f3 - R(6) * f2) + R(4)) / R(6);", "b[1] = ((R(3) * f3 - R(6) * f2) + R(3)) / R(6);"),
+ 'dca_sign': ("R cy = y - cs / kap;", "R cy = y + cs / kap;"),
+ 'tape_div': ("return mk(q, a.id, 1.0 / b.v, b.id, -q / b.v);", "return mk(q, a.id, 1.0 / b.v, b.id, q / b.v);"),
+ 'tape_mul': ("return mk(a.v * b.v, a.id, b.v, b.id, a.v);", "return mk(a.v * b.v, a.id, a.v, b.id, b.v);"),
+ 'chord_not_arc': ("R l = d * A;", "R l = d;"),
+ 'z_uses_chord': ("st.p[1] = z + t * l;", "st.p[1] = z + t * d;"),
+ 't0_sign': ("W<R> zeta = a.vdrift * ((a.t - a.t0) - W<R>(that));", "W<R> zeta = a.vdrift * ((a.t + a.t0) - W<R>(that));"),
+ 'seedz_tf': ("double zeta = c.c.vdrift * ((c.cl.t[i] - c.c.t0) - c.c.tf_start);", "double zeta = c.c.vdrift * ((c.cl.t[i] - c.c.t0) + c.c.tf_start);"),
+ 'reject_count': ("reject = nacc >= c.p.min_acc_reject && in.chi2 > R(c.p.chi2_out);", "reject = nacc > c.p.min_acc_reject && in.chi2 > R(c.p.chi2_out);"),
+ 'no_inflate': ("st.C[i][j] = st.C[i][j] * R(c.p.refit_inflate);", "st.C[i][j] = st.C[i][j];"),
+ 'pass_dir': ("size_t i = (pass == 2) ? k : n - 1 - k;", "size_t i = (pass == 1) ? k : n - 1 - k;"),
+ 'nb_pred_sign': ("R py = yh - (yu - yh) * f;", "R py = yh + (yu - yh) * f;"),
+ 'chi2_drop_term': ("in.chi2 = in.r0 * (in.W00 * in.r0 + in.W01 * in.r1) + in.r1 * (in.W01 * in.r0 + in.W11 * in.r1);", "in.chi2 = in.r0 * (in.W00 * in.r0 + in.W01 * in.r1);"),
+ 'spline_vw_swap': ("R wb = bw[cc] * bv[bb];", "R wb = bw[bb] * bv[cc];"),
+ 'pick_z_weight': ("R d2 = (ry * ry) * ivy + (rz * rz) * ivz;", "R d2 = (ry * ry) * ivy + (rz * rz) * ivy;"),
+ 'no_inward_scale': ("st.C[i][j] = st.C[i][j] * R(c.p.inward_cov_scale);", "st.C[i][j] = st.C[i][j];"),
+ 'clean_one_sided': ("upc[h] = (up[h] >= 0 && dn[up[h]] == h) ? up[h] : -1;", "upc[h] = (up[h] >= 0) ? up[h] : -1;"),
+ 'start_two_hits': ("if (dnc[h] < 0 && upc[h] >= 0 && upc[upc[h]] >= 0) out[m++] = h;", "if (dnc[h] < 0 && upc[h] >= 0) out[m++] = h;"),
+ 'select_tie_high': ("(uint64_t)(0xFFFFFFFFu - (uint32_t)starts[k])", "(uint64_t)((uint32_t)starts[k])"),
+ 'select_gap_ge': ("if (kept < c.p.min_track_hits || maxgap > c.p.max_gap) continue;", "if (kept < c.p.min_track_hits || maxgap >= c.p.max_gap) continue;"),
+ 'seed_max_le': ("while (upc[cur] >= 0 && (int)H.size() < c.p.seed_max_hits) {", "while (upc[cur] >= 0 && (int)H.size() <= c.p.seed_max_hits) {"),
+ 'that_sign': ("that = c.c.tf_start - (sg * (double)zd) / c.c.vdrift;", "that = c.c.tf_start + (sg * (double)zd) / c.c.vdrift;"),
+ 'shared_scale_refit': ("R sc = (c.cl.flags[i] & kFlagShared) ? R(c.p.shared_scale) : R(1);", "R sc = R(1);"),
+ 'nb_dmax_strict': ("if (!(D <= dmax)) continue;", "if (!(D < dmax)) continue;"),
+ 'cov_update_index': ("R v = st.C[i][j] - (K0[i] * HC0[j] + K1[i] * HC1[j]);", "R v = st.C[i][j] - (K0[i] * HC0[j] + K1[i] * HC0[j]);"),
+}
+
+
+def _caught(src, name, tmp):
+    a, b = MUTANTS[name]
+    d = os.path.join(tmp, name)
+    os.makedirs(d)
+    with open(os.path.join(d, "oracle.cpp"), "w") as f:
+        f.write(src.replace(a, b))
+    lib = os.path.join(d, "liborc.so")
+    subprocess.check_call(["g++", *oracle.CXXFLAGS, os.path.join(d, "oracle.cpp"), "-o", lib])
+    env = dict(os.environ, TPC_ORACLE_LIB=lib)
+    r = subprocess.run([sys.executable, "-m", "pytest", "tests/test_oracle_pins.py", "-q", "-x",
+                        "-p", "no:cacheprovider"], cwd=ROOT, env=env, capture_output=True,
+                       text=True)
+    return r.returncode != 0
+
+
+def test_every_planted_mistake_fails_a_pin():
+    with open(oracle.SRC) as f:
+        src = f.read()
+    for name, (a, _) in MUTANTS.items():
+        assert src.count(a) == 1, f"{name}: the text to mutate is no longer unique in oracle.cpp"
+    with tempfile.TemporaryDirectory() as tmp, \
+            cf.ThreadPoolExecutor(max(2, min(16, os.cpu_count() or 2))) as ex:
+        caught = dict(zip(MUTANTS, ex.map(lambda n: _caught(src, n, tmp), MUTANTS)))
+    survivors = [n for n, c in caught.items() if not c]
+    assert not survivors, f"planted mistakes not caught by any pin: {survivors}"

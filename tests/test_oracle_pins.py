@@ -521,3 +521,158 @@ def test_spline_gradient_at_zero_coefficients(geo, params):
                                                  rej=r["rej"])["chi2"])))
         fd = (losses[0] - losses[1]) / (2 * e)
         assert abs(fd - gc[2 + j]) < 1e-3 * max(1, abs(fd)), (j, fd, gc[2 + j])
+
+
+# ------------------------------------------------------ tracklet constructor
+@pytest.mark.parametrize("mode", ["event", "time"])
+def test_tracklets_match_python_reference(geo, params, mode):
+    """The oracle's tracklet constructor against a second implementation of
+    its steps (tests/tracklet_reference.py) on a small noisy event: hit
+    tables, hit counts, collision times and final states."""
+    import tracklet_reference
+    calib = synth.nominal_calib()
+    kw = dict(n_coll=3, tf_start=1.0e6) if mode == "time" else {}
+    ev = synth.make_tiny(seed=41, n_tracks=40, sectors=(2, 25), noise_frac=0.3, mode=mode,
+                         **kw)
+    o = _oracle(ev, geo, params, calib)
+    f = o.find(64)
+    ref = tracklet_reference.tracklets(o, ev, geo, params, calib, f["upc"], f["starts"])
+    tl = f["tracklets"]
+    assert len(f["starts"]) > 40
+    np.testing.assert_array_equal(tl["nh"], ref["nh"])
+    np.testing.assert_array_equal(tl["hits"], ref["hits"])
+    np.testing.assert_allclose(tl["that"], ref["that"], rtol=0, atol=1e-9)
+    ok = ref["nh"] >= 0
+    np.testing.assert_allclose(tl["x"][ok], ref["x"][ok], rtol=0, atol=1e-12)
+    np.testing.assert_allclose(tl["state"][ok], ref["state"][ok], rtol=1e-12, atol=1e-12)
+
+
+# ------------------------------------------- time -> z with calibration offsets
+def test_time_to_z_round_trip_with_offsets(geo, params):
+    """Drift velocity and t0 away from nominal: calibrated z from the true
+    collision time equals the generator's z (Sec. 4 transform)."""
+    cal = synth.nominal_calib()
+    cal.vdrift *= 1.01
+    cal.t0 = 0.07
+    ev = synth.make_tiny(seed=19, n_tracks=30, sectors=(4, 30), mode="time", tf_start=1.0e6,
+                         n_coll=2, calib=cal)
+    o = _oracle(ev, geo, params, cal)
+    sig = np.nonzero(ev.label >= 0)[0]
+    yc, zc = o.calibrate(sig, ev.t_coll[ev.label[sig]], prec=64)
+    assert np.max(np.abs(zc - ev.info["z_meas"][sig])) < 1e-9
+    # a wrong t0 or drift velocity shows up in z
+    o2 = _oracle(ev, geo, params, synth.nominal_calib())
+    _, zc2 = o2.calibrate(sig, ev.t_coll[ev.label[sig]], prec=64)
+    assert np.max(np.abs(zc2 - ev.info["z_meas"][sig])) > 0.1
+
+
+# ----------------------------------------------------- refit outlier rules
+def test_refit_rejection_follows_pass_order(geo, params):
+    """Constructed outliers on a noise-free helix (Sec. 3): pass 1 runs inward
+    from the outermost cluster and may reject only after min_acc_reject
+    accepted clusters; pass 2 runs outward. A 1 cm (10 sigma) outlier third
+    from the outer end is accepted by pass 1 (2 accepted before it) and
+    rejected by pass 2; one at the sixth position of pass 1 (5 accepted
+    before it) is rejected by pass 1; one at the fifth (4 before it) is
+    accepted by pass 1 (it then drags the state, so that later clusters of
+    pass 1 are rejected) and rejected by pass 2."""
+    ev = synth.make_tiny(seed=23, n_tracks=6, sectors=(7,), sigma=0.0)
+    ts, ci, tc, _ = synth.truth_tracks(ev, 60)
+    o_plain = _oracle(ev, geo, params)
+    r0 = o_plain.refit(ts, ci, tc, prec=64)
+    k = int(np.nonzero(r0["status"] == 0)[0][0])      # a track that refits
+    a, b = int(ts[k]), int(ts[k + 1])
+    n = b - a
+    one = (np.array([0, n], np.uint32), ci[a:b].copy(), tc[k:k + 1].copy())
+    y = ev.y.copy()
+    for pos, expect, alone in [(n - 3, 2, True), (n - 6, 1, True), (n - 5, 2, False)]:
+        ev.y[:] = y
+        ev.y[one[1][pos]] += np.float32(1.0)
+        o = _oracle(ev, geo, params)
+        r = o.refit(*one, prec=64)
+        rej = r["rej"][:n]
+        assert r["status"][0] == 0
+        assert rej[pos] == expect, (pos, rej[pos], expect)
+        if alone:
+            assert np.count_nonzero(rej) == 1
+    ev.y[:] = y
+    assert np.count_nonzero(o_plain.refit(*one, prec=64)["rej"][:n]) == 0
+
+
+def test_neighbour_deviation_cut_is_inclusive(geo, params):
+    """A down hit exactly at the deviation cut (D = nb_dmax, exact in
+    floating point) is linked; one just beyond is not."""
+    assert params["nb_dmax"] == 0.5
+    ys = [1.0, 1.0, 1.5, 1.0]
+    zs = [10.0, 10.0, 10.5, 10.0]
+    rows = [70, 71, 69, 72]
+    o = _oracle(_Mini(rows, ys, zs), geo, params)
+    up, dn = o.neighbours(32)
+    # u straight above h: prediction (1.0, 10.0) in row 69, D = 0.25 + 0.25
+    assert (up[0], dn[0]) == (1, 2)
+    zs2 = [10.0, 10.0, 10.5 + 1e-3, 10.0]
+    up2, dn2 = _oracle(_Mini(rows, ys, zs2), geo, params).neighbours(32)
+    assert (up2[0], dn2[0]) == (-1, -1)
+
+
+# ------------------------------------------------------------ selector rules
+def test_selector_weights_and_gaps(geo, params):
+    """Constructed tracklet tables with known answers (Sec. 3 shared
+    clusters): a shared cluster goes to the tracklet with more hits, on equal
+    hit counts to the lower start index; a track keeps at least
+    min_track_hits clusters with no gap above max_gap rows."""
+    R = geo.row_x.size
+    nmin, gmax = params["min_track_hits"], params["max_gap"]
+    ev = _Mini([5] * 200, [0.0] * 200, [0.0] * 200)
+    o = _oracle(ev, geo, params)
+
+    def table(rows_list):
+        hits = -np.ones((len(rows_list), R), np.int32)
+        for k, rs in enumerate(rows_list):
+            for r, j in rs:
+                hits[k, r] = j
+        nh = np.array([len(rs) for rs in rows_list], np.int32)
+        return dict(nh=nh, hits=hits, that=np.zeros(len(rows_list)))
+
+    # A (start 7) and B (start 3), 12 hits each, sharing cluster 50 in row 20
+    A = [(20 + i, 40 + i) for i in range(12)]          # clusters 40..51, 50 at row 30
+    B = [(25 + i, 100 + i) for i in range(12)]
+    B[5] = (30, 50)                                     # the shared cluster, same row
+    tr = o.select(np.array([7, 3]), table([A, B]))
+    lists = [list(tr["cluster_idx"][tr["track_start"][k]:tr["track_start"][k + 1]])
+             for k in range(len(tr["track_start"]) - 1)]
+    # equal hit counts: start 3 (B) wins cluster 50; A keeps 11 >= min hits
+    assert 50 in lists[1] and 50 not in lists[0]
+    # one more hit on A: A wins it
+    A2 = A + [(32, 150)]
+    tr = o.select(np.array([7, 3]), table([A2, B]))
+    lists = [list(tr["cluster_idx"][tr["track_start"][k]:tr["track_start"][k + 1]])
+             for k in range(len(tr["track_start"]) - 1)]
+    assert 50 in lists[0] and all(50 not in l for l in lists[1:])
+    # gaps: max_gap empty rows inside a track are allowed, one more is not
+    ok = [(10 + i, i) for i in range(nmin - 1)] + [(10 + nmin - 1 + gmax, 90)]
+    bad = [(10 + i, 60 + i) for i in range(nmin - 1)] + [(10 + nmin + gmax, 99)]
+    tr = o.select(np.array([1, 2]), table([ok, bad]))
+    assert len(tr["track_start"]) - 1 == 1
+    assert list(tr["cluster_idx"]) == [j for _, j in ok]
+
+
+# -------------------------------------------------- shared-cluster errors
+def test_shared_clusters_have_scaled_errors(geo, params):
+    """TPC_FLAG_SHARED clusters have their error scaled by shared_scale
+    (Sec. 3): flagging every cluster of a track leaves the least-squares
+    estimate unchanged and divides chi2 by shared_scale^2 (up to the weak
+    prior of the first pass)."""
+    ev = synth.make_tiny(seed=29, n_tracks=10, sectors=(11,))
+    ts, ci, tc, _ = synth.truth_tracks(ev, 60)
+    o = _oracle(ev, geo, params)
+    r = o.refit(ts, ci, tc, prec=64)
+    ev.flags[:] = 0x10
+    o2 = _oracle(ev, geo, params)
+    r2 = o2.refit(ts, ci, tc, prec=64)
+    ev.flags[:] = 0
+    ok = (r["status"] == 0) & (r2["status"] == 0)
+    assert ok.sum() >= 3
+    ratio = r2["chi2"][ok] / r["chi2"][ok]
+    s = params["shared_scale"]
+    np.testing.assert_allclose(ratio, 1.0 / (s * s), rtol=2e-2)
