@@ -890,7 +890,7 @@ __global__ void __launch_bounds__(BS) k_tracklets(Geo g, Cal c, Params p, GridDi
       } else if (h != hl) {
         h = upc[h];
         ++r;
-      } else if (phase == kSeed1) {
+      } else if (phase == kSeed1 && (mode == 1 || spl_on)) {
         if (mode == 1) {
           float zd = dca_z(g.kB, st, x);
           double sg = sec < 18 ? 1.0 : -1.0;
@@ -905,6 +905,9 @@ __global__ void __launch_bounds__(BS) k_tracklets(Geo g, Cal c, Params p, GridDi
         h = h0;
         r = r0;
       } else {
+        // seed fitted (in event mode without a distortion map the calibrated
+        // coordinates equal the seeding ones, so the calibrated refit of the
+        // seed would repeat the first fit operation for operation)
 #pragma unroll
         for (int i = 0; i < 5; ++i) bst[i] = st[i];
 #pragma unroll

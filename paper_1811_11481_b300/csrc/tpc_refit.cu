@@ -443,11 +443,18 @@ __global__ void k_calib_reduce(int nblk, const uint32_t* cnt, const uint32_t* gm
                                const unsigned long long* acc_spline, const double* part_cal,
                                double* grad_calib) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= TPC_GRAD_CALIB_SIZE) return;
+  if (blockIdx.x == 0 && threadIdx.x < 64) {
+    // (v_drift, t0): warp w sums component w over the blocks, lane-strided,
+    // then a fixed-order tree; both fixed, so the sum is reproducible
+    int comp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double a = 0.0;
+    for (int b = lane; b < nblk; b += 32) a += part_cal[b * 2 + comp];
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+    if (lane == 0) grad_calib[comp] = a;
+  }
+  if (i < 2 || i >= TPC_GRAD_CALIB_SIZE) return;
   double s = 0.0;
-  if (i < 2) {
-    for (int b = 0; b < nblk; ++b) s += part_cal[b * 2 + i];
-  } else {
+  {
     int kx = 0;
     if (grad_fixed_exponent(*gmax, (int)cnt[kCntAssigned], kx))
       s = ldexp((double)(long long)acc_spline[i - 2], -kx);
