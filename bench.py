@@ -40,7 +40,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="central",
-                    choices=["central", "timeframe", "batched", "single_sector"])
+                    choices=["central", "timeframe", "batched", "single_sector", "adjoint"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true",
@@ -540,10 +540,127 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def run_adjoint(args):
+    """Adjoint-refit workload: ten central events in continuous readout,
+    generated with a distorted calibration (v_drift +0.5 %, t0 +0.05 us, a
+    per-sector spline up to 1 cm); truth-assigned tracks of at least 30
+    clusters (~100k) with fixed assignments. A step is the refit with
+    checkpoints (calibration transform included) and the adjoint back to the
+    cluster coordinates and the calibration, at a calibration halfway between
+    nominal and true (so that the spline is evaluated and differentiated)."""
+    import torch
+    import torch.distributed as dist
+    import synth
+    from paper_1811_11481_b300.binding import TPC_GRAD_CALIB_SIZE, Tracker
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    geo = synth.geometry()
+    ev = synth.make_adjoint(seed=4 + rank)
+    ts, ci, tc, _ = synth.truth_tracks(ev, 30)
+    nom, true = synth.nominal_calib(), ev.calib_true
+    work = torch.cuda.Stream()
+    torch.cuda.set_stream(work)
+    tr = Tracker(geo, stream=work)
+    tr.set_calib(0.5 * (nom.vdrift + true.vdrift), 0.5 * (nom.t0 + true.t0),
+                 0.5 * np.asarray(true.spline, np.float32))
+    cl = tr.upload(ev)
+    tr.load(cl)
+    dev = tr.dev
+    tr.set_tracks(torch.as_tensor(ts.astype(np.int32), device=dev),
+                  torch.as_tensor(ci.astype(np.int32), device=dev),
+                  torch.as_tensor(tc, device=dev))
+    nt, na = ts.size - 1, int(ts[-1])
+    L, h = tr.L, tr.h
+    import ctypes as C
+    P = lambda t: C.c_void_p(t.data_ptr())
+    f32 = lambda *sh: torch.empty(*sh, device=dev)
+    out = dict(params=f32(nt, 5), cov=f32(nt, 15), x=f32(nt), chi2=f32(nt),
+               ndf=torch.empty(nt, dtype=torch.int32, device=dev),
+               status=torch.empty(nt, dtype=torch.int32, device=dev),
+               rej=torch.empty(na, dtype=torch.uint8, device=dev))
+    ones, gy, gz = torch.ones(nt, device=dev), f32(na), f32(na)
+    gc = torch.empty(TPC_GRAD_CALIB_SIZE, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def ck(st, what):
+        if st != 0:
+            raise RuntimeError(f"{what}: status {st}: {L.tpc_last_error(h).decode()}")
+
+    def fwd(save):
+        ck(L.tpc_refit(h, int(save), P(out["params"]), P(out["cov"]), P(out["x"]),
+                       P(out["chi2"]), P(out["ndf"]), P(out["status"]), P(out["rej"])), "refit")
+
+    def bwd():
+        ck(L.tpc_refit_backward(h, P(ones), P(gy), P(gz), P(gc)), "backward")
+
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def timed(fn, k):
+        ev_ = []
+        for _ in range(k):
+            flush.fill_(1.0)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            ev_.append((a, b))
+        torch.cuda.synchronize()
+        return float(np.sum([a.elapsed_time(b) for a, b in ev_]))
+
+    for _ in range(max(3, args.warmup)):
+        fwd(True)
+        bwd()
+    clocks = Clocks(local)
+    clocks.start()
+    t_end = time.time() + 1.5
+    while time.time() < t_end:
+        fwd(True)
+        bwd()
+    tr.profile(True)
+    torch.cuda.synchronize()
+    total = timed(lambda: (fwd(True), bwd()), args.steps)
+    clk = clocks.stop()
+    kstats, launches = tr.profile_read()
+    tr.profile(False)
+    t_fwd = timed(lambda: fwd(False), 20) / 20
+    t_fwd_save = timed(lambda: fwd(True), 20) / 20
+    fwd(True)
+    t_bwd = timed(bwd, 20) / 20
+    total_ms, _, value = aggregate(total, na * args.steps, dist, dev)
+    st = out["status"].cpu().numpy()
+    kernels = {k: dict(launches=v[0], ms_per_step=v[1] / args.steps)
+               for k, v in sorted(kstats.items(), key=lambda kv: -kv[1][1])}
+    line = dict(metric=METRIC, value=value, unit="assigned clusters/s", n_gpus=world,
+                steps=args.steps, warmup=args.warmup, ms_per_step=total_ms / args.steps,
+                higher_is_better=True, scaling="weak", vs_baseline=None,
+                dtype="f32 (f64 timestamps and gradient sums)", data="synthetic",
+                config=dict(workload="adjoint refit: 10 central events, continuous readout, "
+                                     "injected calibration error, truth tracks >= 30 clusters",
+                            seed=4 + rank, n_clusters=int(ev.n), n_tracks=nt, n_assigned=na,
+                            calib="halfway between nominal and true (spline active)",
+                            l2="flushed before every timed step (256 MB write)"),
+                tracks_per_s=aggregate(total, nt * args.steps, dist, dev)[2],
+                refit_fwd_ms=t_fwd, refit_fwd_save_ms=t_fwd_save, adjoint_ms=t_bwd,
+                adjoint_vs_fwd=t_bwd / t_fwd if t_fwd > 0 else None,
+                fit_status_ok=float((st == 0).mean()), kernels=kernels, gpu_launches=launches,
+                clocks=clk)
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "adjoint":
+        run_adjoint(args)
     else:
         run_ours(args)
 

@@ -304,14 +304,13 @@ __global__ void __launch_bounds__(kCgThreads) k_calib_grad(
   const int off2 = off1 + 2 * kSpl * kSpl;
   float a01 = 0.f, a02 = 0.f, a11 = 0.f, a12 = 0.f;  // [component][coefficient]
   int cur = -1;                                        // cell base of the sums
+  unsigned long long* acc = acc_spline;
   auto flush = [&]() {
     long long q;
-    if ((q = to_fixed(a01, kx)) != 0) atomicAdd(&acc_spline[cur + off1], (unsigned long long)q);
-    if ((q = to_fixed(a02, kx)) != 0) atomicAdd(&acc_spline[cur + off2], (unsigned long long)q);
-    if ((q = to_fixed(a11, kx)) != 0)
-      atomicAdd(&acc_spline[cur + kComp + off1], (unsigned long long)q);
-    if ((q = to_fixed(a12, kx)) != 0)
-      atomicAdd(&acc_spline[cur + kComp + off2], (unsigned long long)q);
+    if ((q = to_fixed(a01, kx)) != 0) atomicAdd(&acc[cur + off1], (unsigned long long)q);
+    if ((q = to_fixed(a02, kx)) != 0) atomicAdd(&acc[cur + off2], (unsigned long long)q);
+    if ((q = to_fixed(a11, kx)) != 0) atomicAdd(&acc[cur + kComp + off1], (unsigned long long)q);
+    if ((q = to_fixed(a12, kx)) != 0) atomicAdd(&acc[cur + kComp + off2], (unsigned long long)q);
     a01 = a02 = a11 = a12 = 0.f;
   };
   for (int b0 = jb; b0 < je; b0 += 32) {
@@ -362,18 +361,24 @@ __global__ void __launch_bounds__(kCgThreads) k_calib_grad(
       };
       dbasis(fv, dbv);
       dbasis(fw, dbw);
+      // tensor-product derivatives, summed innermost axis first (u, then v,
+      // then w): 4 x 4 partial sums over u shared by both derivatives
       float dval_dv[2] = {0.f, 0.f}, dval_dw[2] = {0.f, 0.f};
       for (int cp = 0; cp < (spl_on ? 2 : 0); ++cp) {
         const float* cf = c.spline + (s * 2 + cp) * kComp;
-        for (int cc = 0; cc < 4; ++cc)
+#pragma unroll
+        for (int cc = 0; cc < 4; ++cc) {
+          float tv = 0.f, tdv = 0.f;
+#pragma unroll
           for (int b2 = 0; b2 < 4; ++b2) {
-            int o = ((iw + cc) * kSpl + (iv + b2)) * kSpl + iu;
-            for (int a2 = 0; a2 < 4; ++a2) {
-              float coef = cf[o + a2];
-              dval_dv[cp] += bw[cc] * dbv[b2] * bu[a2] * coef;
-              dval_dw[cp] += dbw[cc] * bv[b2] * bu[a2] * coef;
-            }
+            const float* row = cf + ((iw + cc) * kSpl + (iv + b2)) * kSpl + iu;
+            float su = bu[0] * row[0] + bu[1] * row[1] + bu[2] * row[2] + bu[3] * row[3];
+            tv += bv[b2] * su;
+            tdv += dbv[b2] * su;
           }
+          dval_dv[cp] += bw[cc] * tdv;
+          dval_dw[cp] += dbw[cc] * tv;
+        }
       }
       float dDy_dy = dval_dv[0] * kS * dvdy, dDz_dy = dval_dv[1] * kS * dvdy;
       float dDy_dz = dval_dw[0] * kS * dwdz, dDz_dz = dval_dw[1] * kS * dwdz;
@@ -456,10 +461,11 @@ __global__ void k_calib_reduce(int nblk, const uint32_t* cnt, const uint32_t* gm
   double s = 0.0;
   {
     int kx = 0;
-    if (grad_fixed_exponent(*gmax, (int)cnt[kCntAssigned], kx))
+    if (grad_fixed_exponent(*gmax, (int)cnt[kCntAssigned], kx)) {
       s = ldexp((double)(long long)acc_spline[i - 2], -kx);
-    else
+    } else {
       s = __longlong_as_double(0x7ff8000000000000ll);
+    }
   }
   grad_calib[i] = s;
 }
