@@ -41,6 +41,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="central",
                     choices=["central", "timeframe", "batched", "single_sector", "adjoint"])
+    ap.add_argument("--collisions", type=int, default=50,
+                    help="collisions of the time-frame workload (50: the headline frame)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true",
@@ -54,15 +56,15 @@ def parse():
     return ap.parse_args()
 
 
-def make_workload(name, rank):
+def make_workload(name, rank, collisions=50):
     import synth
     if name == "central":
         ev = synth.make_central(seed=1 + rank)
         cfg = dict(workload="central Pb-Pb-like event: 36 sectors x 152 rows, 10000 primaries "
                             "(pT power law, mean 0.5 GeV), 10% noise, event mode", seed=1 + rank)
     elif name == "timeframe":
-        ev = synth.make_timeframe(seed=2 + rank)
-        cfg = dict(workload="50 kHz continuous-readout time frame: 50 collisions, "
+        ev = synth.make_timeframe(seed=2 + rank, n_coll=collisions)
+        cfg = dict(workload=f"50 kHz continuous-readout time frame: {collisions} collisions, "
                             "multiplicity Exp(2000), 15% noise, float64 times", seed=2 + rank)
     elif name == "batched":
         ev = synth.make_batched(seed=3 + rank)
@@ -243,7 +245,7 @@ def run_ours(args):
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     geo = synth.geometry()
-    ev, cfg = make_workload(args.workload, rank)
+    ev, cfg = make_workload(args.workload, rank, args.collisions)
     work = torch.cuda.Stream()
     torch.cuda.set_stream(work)
     tr = Tracker(geo, stream=work)
