@@ -284,6 +284,7 @@ __global__ void __launch_bounds__(kCgThreads) k_calib_grad(
     const uint32_t* gmax, float* grad_y, float* grad_zt, unsigned long long* acc_spline,
     double* part_cal) {
   __shared__ double red[2][kCgThreads / 32];
+  __shared__ float sw[kCgThreads / 32][32][16];  // per lane: weights, gradient, cell
   constexpr int kComp = kSpl * kSpl * kSpl;
   int n = (int)cnt[kCntAssigned];
   int kx = 0;
@@ -394,33 +395,41 @@ __global__ void __launch_bounds__(kCgThreads) k_calib_grad(
         grad_zt[j] = gza;
       }
     }
-    // spline coefficient gradients, one cluster at a time in cluster order
+    // spline coefficient gradients, one cluster at a time in cluster order:
+    // each lane publishes its cluster's cell, gradient and B-spline weights
+    // in shared memory, each lane then reads the four weights of its own
+    // coefficients
+    float* mine = sw[w][lane];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      mine[q] = bu[q];
+      mine[4 + q] = bv[q];
+      mine[8 + q] = bw[q];
+    }
+    mine[12] = by;
+    mine[13] = bz;
+    mine[14] = __int_as_float(o0);
+    __syncwarp();
     unsigned am = __ballot_sync(0xffffffffu, valid && fixed_ok && (by != 0.0f || bz != 0.0f));
     while (am) {
       int src = __ffs(am) - 1;
       am &= am - 1;
-      int o = __shfl_sync(0xffffffffu, o0, src);
+      const float* sc = sw[w][src];
+      int o = __float_as_int(sc[14]);
       if (o != cur) {  // uniform over the warp
         if (cur >= 0) flush();
         cur = o;
       }
-      float cy = __shfl_sync(0xffffffffu, by, src);
-      float cz = __shfl_sync(0xffffffffu, bz, src);
-      float u0 = __shfl_sync(0xffffffffu, bu[0], src), u1 = __shfl_sync(0xffffffffu, bu[1], src);
-      float u2 = __shfl_sync(0xffffffffu, bu[2], src), u3 = __shfl_sync(0xffffffffu, bu[3], src);
-      float v0 = __shfl_sync(0xffffffffu, bv[0], src), v1 = __shfl_sync(0xffffffffu, bv[1], src);
-      float v2 = __shfl_sync(0xffffffffu, bv[2], src), v3 = __shfl_sync(0xffffffffu, bv[3], src);
-      float w0 = __shfl_sync(0xffffffffu, bw[0], src), w1 = __shfl_sync(0xffffffffu, bw[1], src);
-      float w2 = __shfl_sync(0xffffffffu, bw[2], src), w3 = __shfl_sync(0xffffffffu, bw[3], src);
-      float ua = aa == 0 ? u0 : aa == 1 ? u1 : aa == 2 ? u2 : u3;
-      float vb = bb == 0 ? v0 : bb == 1 ? v1 : bb == 2 ? v2 : v3;
-      float p1 = (cc1 == 0 ? w0 : w1) * (vb * ua);
-      float p2 = (cc1 == 0 ? w2 : w3) * (vb * ua);
+      float cy = sc[12], cz = sc[13];
+      float uv = sc[4 + bb] * sc[aa];
+      float p1 = sc[8 + cc1] * uv;
+      float p2 = sc[10 + cc1] * uv;
       a01 += cy * p1;
       a02 += cy * p2;
       a11 += cz * p1;
       a12 += cz * p2;
     }
+    __syncwarp();
   }
   if (cur >= 0) flush();
   // block reduction of the float64 sums, in a fixed order
