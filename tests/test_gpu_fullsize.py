@@ -149,3 +149,18 @@ def test_efficiency_and_fake_rate_match_oracle_definition(full):
     fake_rate = fake / (ts.size - 1)
     assert eff > 0.95, eff
     assert fake_rate < 0.02, fake_rate
+
+
+def test_tracks_come_in_canonical_order(full):
+    """Tracks are emitted by (event, sector, pad row, input index) of their
+    start hit; on the full event the start buckets of the innermost rows hold
+    hundreds of tracklets, so the large-group ordering is exercised too."""
+    g, ev = full["g"], full["ev"]
+    sh = g["start_hit"].astype(np.int64)
+    key = ((ev.event[sh].astype(np.int64) * 36 + ev.sector[sh]) * 152 + ev.row[sh]) * ev.n + sh
+    assert sh.size > 1000
+    assert np.all(np.diff(key) > 0)
+    # and the large groups exist: many tracklets start in one bucket
+    ts = g["tl"]["start_hit"].astype(np.int64)
+    tb = (ev.event[ts].astype(np.int64) * 36 + ev.sector[ts]) * 152 + ev.row[ts]
+    assert np.bincount(np.unique(tb, return_inverse=True)[1]).max() > 64
