@@ -229,9 +229,12 @@ __device__ __forceinline__ Bins es_bins(const uint2* es_dims, int es) {
   b.nb = b.ny * b.nz;
   return b;
 }
+// Bin of a coordinate. The same function places the clusters and bounds
+// the search boxes, so it need not be correctly rounded: the boxes carry a
+// margin (>= 0.01 cm) far above its error, and it is monotone in y.
 __device__ __forceinline__ int bin_y(const Geo& g, const GridDims& gd, int r, int ny, float y) {
   float hw = g.rx[r] * g.tan_half + gd.y_margin;
-  float v = (y + hw) * ((float)ny / (2.0f * hw));
+  float v = (y + hw) * __fdividef((float)ny, 2.0f * hw);
   int iy = (int)floorf(v);
   if (!(v == v)) iy = 0;
   return iy < 0 ? 0 : (iy >= ny ? ny - 1 : iy);
@@ -740,7 +743,10 @@ __device__ int step_measurement(const Geo& g, const Cal& c, const Params& p, con
   float ivy = 1.0f / vy, ivz = 1.0f / vz;
   int iz0 = 0, iz1 = 0, iy0 = 0, iy1 = 0;
   if (!seed) {
-    float wy = sqrtf(p.chi2_pick * vy), wz = sqrtf(p.chi2_pick * vz);
+    // window half-widths bound the search box only (the cut below decides):
+    // a fast square root is enough
+    float qy = p.chi2_pick * vy, qz = p.chi2_pick * vz;
+    float wy = qy * rsqrtf(qy), wz = qz * rsqrtf(qz);
     float eps = 0.01f + 1.0e-6f * fabsf(shift);
     float yp = st[0], zp = st[1] - shift;
     Box B = make_box(g, gd, G.zr, BB, r, side, yp - wy - dymax - eps, yp + wy + dymax + eps,
