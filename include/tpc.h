@@ -295,6 +295,11 @@ typedef struct {
   double total_ms;
 } tpc_kernel_stat;
 tpc_status tpc_profile(tpc_ctx* ctx, int enable);
+/* Restrict the event timing of tpc_profile to the launches of one kernel
+ * (name as reported by tpc_profile_read; NULL or "" = every kernel), so that
+ * a long run can time its dominant kernel with two events per launch. Takes
+ * effect from the next launch; does not synchronise. */
+tpc_status tpc_profile_only(tpc_ctx* ctx, const char* kernel);
 tpc_status tpc_profile_read(tpc_ctx* ctx, tpc_kernel_stat* out, int32_t cap, int32_t* n_out,
                             int64_t* launches);
 

@@ -82,6 +82,7 @@ _PROTOS = {
                              C.POINTER(C.c_void_p)]),
     "tpc_destroy": (None, [C.c_void_p]),
     "tpc_get_tuning": (C.c_int, [C.c_void_p, C.POINTER(tpc_tuning)]),
+    "tpc_profile_only": (C.c_int, [C.c_void_p, C.c_char_p]),
     "tpc_set_tuning": (C.c_int, [C.c_void_p, C.POINTER(tpc_tuning)]),
     "tpc_autotune": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(tpc_tuning)]),
     "tpc_set_calib": (C.c_int, [C.c_void_p, C.POINTER(tpc_calib)]),
@@ -346,6 +347,11 @@ class Tracker:
     def profile(self, enable=True):
         """Reset kernel accounting; with enable, time every kernel with events."""
         self._ck(self.L.tpc_profile(self.h, int(bool(enable))), "tpc_profile")
+
+    def profile_only(self, kernel=None):
+        """Time only the launches of `kernel` (None: every kernel)."""
+        self._ck(self.L.tpc_profile_only(self.h, kernel.encode() if kernel else None),
+                 "tpc_profile_only")
 
     def profile_read(self):
         """{kernel: (launches, total_ms)} and the total launch count."""

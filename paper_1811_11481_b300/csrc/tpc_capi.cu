@@ -714,6 +714,12 @@ tpc_status tpc_profile(tpc_ctx* ctx, int enable) {
   return TPC_OK;
 }
 
+tpc_status tpc_profile_only(tpc_ctx* ctx, const char* kernel) {
+  if (!ctx) return TPC_ERR_ARG;
+  ctx->prof.only = kernel ? kernel : "";
+  return TPC_OK;
+}
+
 tpc_status tpc_profile_read(tpc_ctx* ctx, tpc_kernel_stat* out, int32_t cap, int32_t* n_out,
                             int64_t* launches) {
   if (!ctx) return TPC_ERR_ARG;

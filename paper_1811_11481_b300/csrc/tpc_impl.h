@@ -180,15 +180,18 @@ struct Prof {
     }
     return e;
   }
+  std::string only;          // when set, only launches of this kernel are timed
+  bool timed_last = false;   // the last begin() recorded an event pair
   void begin(const char* name, cudaStream_t s) {
     ++launches;
-    if (!on) return;
+    timed_last = on && (only.empty() || only == name);
+    if (!timed_last) return;
     Rec r{name, ev(), ev()};
     cudaEventRecord(r.a, s);
     pending.push_back(r);
   }
   void end(cudaStream_t s) {
-    if (!on || pending.empty()) return;
+    if (!timed_last || pending.empty()) return;
     cudaEventRecord(pending.back().b, s);
   }
   // Requires the stream to be synchronised.
