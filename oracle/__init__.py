@@ -110,6 +110,8 @@ def lib():
         L.orc_jacobian.argtypes = [vp, vp, C.c_double, C.c_double, vp, vp]
         L.orc_update.argtypes = [vp, vp, C.c_double, C.c_double, C.c_double, C.c_double,
                                  vp, vp, vp]
+        L.orc_rotate.restype = C.c_int
+        L.orc_rotate.argtypes = [vp, vp, C.c_double, C.c_double, vp, vp, vp, vp]
         L.orc_dca_z.restype = C.c_double
         L.orc_dca_z.argtypes = [vp, vp, C.c_double]
         L.orc_arc_factor.restype = C.c_double
@@ -330,6 +332,18 @@ class Oracle:
         stt = lib().orc_refit_points(self.h, x.size, _p(x), _p(y), _p(z), float(var), _p(p),
                                      _p(ch), _p(nd))
         return stt, p, float(ch[0]), int(nd[0])
+
+    def rotate(self, state, x, dalpha, cov=None):
+        """The state re-expressed in a frame rotated by dalpha (and its
+        covariance, 5x5); (None, None, None) when the rotation fails."""
+        s = np.ascontiguousarray(state, np.float64)
+        cv = np.eye(5) if cov is None else np.ascontiguousarray(cov, np.float64)
+        so = np.empty(5)
+        co = np.empty((5, 5))
+        xo = np.empty(1)
+        ok = lib().orc_rotate(self.h, _p(s), float(x), float(dalpha), _p(cv), _p(so), _p(xo),
+                              _p(co))
+        return (so, float(xo[0]), co) if ok else (None, None, None)
 
     def jacobian(self, state, x1, x2):
         so = np.empty(5)

@@ -412,6 +412,24 @@ template <class R> void set_diag(Trk<R>& st, const float* d) {
   for (int i = 0; i < 5; ++i) st.C[i][i] = R(d[i]);
 }
 
+// C' = J C J^T, lower triangle with index-ascending sums, mirrored.
+template <class R> void cov_transform(const R J[5][5], R C[5][5]) {
+  R Tm[5][5];
+  for (int i = 0; i < 5; ++i)
+    for (int l2 = 0; l2 < 5; ++l2) {
+      R acc = R(0);
+      for (int k = 0; k < 5; ++k) acc = acc + J[i][k] * C[k][l2];
+      Tm[i][l2] = acc;
+    }
+  for (int i = 0; i < 5; ++i)
+    for (int j = 0; j <= i; ++j) {
+      R acc = R(0);
+      for (int l2 = 0; l2 < 5; ++l2) acc = acc + Tm[i][l2] * J[j][l2];
+      C[i][j] = acc;
+      C[j][i] = acc;
+    }
+}
+
 // Exact helix transport to the plane x2 and its analytic Jacobian.
 template <class R> bool propagate(const Ctx& c, Trk<R>& st, R x2, R* Jout = nullptr) {
   const R kB = kB_of<R>(c);
@@ -460,21 +478,7 @@ template <class R> bool propagate(const Ctx& c, Trk<R>& st, R x2, R* Jout = null
   if (Jout)
     for (int i = 0; i < 5; ++i)
       for (int j = 0; j < 5; ++j) Jout[i * 5 + j] = J[i][j];
-  // C' = J C J^T, lower triangle computed with index-ascending sums, mirrored
-  R Tm[5][5];
-  for (int i = 0; i < 5; ++i)
-    for (int l2 = 0; l2 < 5; ++l2) {
-      R acc = R(0);
-      for (int k = 0; k < 5; ++k) acc = acc + J[i][k] * st.C[k][l2];
-      Tm[i][l2] = acc;
-    }
-  for (int i = 0; i < 5; ++i)
-    for (int j = 0; j <= i; ++j) {
-      R acc = R(0);
-      for (int l2 = 0; l2 < 5; ++l2) acc = acc + Tm[i][l2] * J[j][l2];
-      st.C[i][j] = acc;
-      st.C[j][i] = acc;
-    }
+  cov_transform<R>(J, st.C);
   st.p[0] = y + dy;
   st.p[1] = z + t * l;
   st.p[2] = s2;
@@ -517,6 +521,43 @@ template <class R> void apply_update(Trk<R>& st, const Innov<R>& in) {
       st.C[i][j] = v;
       st.C[j][i] = v;
     }
+}
+
+// Frame angle of a sector: sector k is rotated by ((k mod 18) + 1/2) * 20
+// degrees about the beam axis (Sec. 2: 36 trapezoidal sectors).
+inline double sector_alpha(int sec) { return ((sec % 18) + 0.5) * (M_PI / 9.0); }
+
+// The same helix at the same point, expressed in a frame rotated by dalpha
+// about the beam axis: the final fit of a track merged from several sectors
+// (Sec. 2, second phase) runs in the frame of the sector of each cluster.
+// Position and direction rotate; the state then refers to the plane
+// x' = x cos + y sin of the new frame, and the covariance follows with the
+// Jacobian of the state at that plane (a shift of y at fixed x moves the
+// point off the plane, and the track is followed back to it along its
+// tangent: dy'/dy = cos(phi)/cos(phi'), dz'/dy = -sin(dalpha) tan(lambda) /
+// cos(phi'), dsin(phi')/dy = kappa sin(dalpha), dsin(phi')/dsin(phi) =
+// cos(phi')/cos(phi)). Fails when the track would leave the new frame's
+// forward half-plane or reach s_max.
+template <class R> bool rotate(const Ctx& c, Trk<R>& st, double dalpha) {
+  const R ca = R(std::cos(dalpha)), sa = R(std::sin(dalpha));
+  R x = st.x, y = st.p[0], s = st.p[2], t = st.p[3], q = st.p[4];
+  R cf = sqrt_(R(1) - s * s);
+  R s2 = s * ca - cf * sa;
+  R c2 = cf * ca + s * sa;
+  if (!(c2 > R(0)) || !(abs_(s2) < R(c.p.s_max))) return false;
+  R kap = kB_of<R>(c) * q;
+  R J[5][5];
+  for (int i = 0; i < 5; ++i)
+    for (int j = 0; j < 5; ++j) J[i][j] = R(i == j ? 1 : 0);
+  J[0][0] = cf / c2;
+  J[1][0] = -(sa * t) / c2;
+  J[2][0] = kap * sa;
+  J[2][2] = c2 / cf;
+  cov_transform<R>(J, st.C);
+  st.x = x * ca + y * sa;
+  st.p[0] = -(x * sa) + y * ca;
+  st.p[2] = s2;
+  return true;
 }
 
 // Seed state through two points: straight line, q/pT = 0 (Sec. 2 seed fit).
@@ -828,13 +869,16 @@ bool seed_three_points(const Ctx& c, const std::vector<R>& x, const std::vector<
 template <class R>
 RefitOut refit_core(const Ctx& c, const std::vector<R>& x, const std::vector<R>& yc,
                     const std::vector<R>& zc, const std::vector<R>& var, const double seed[5],
-                    uint8_t* rej, bool frozen, R* chi2_out) {
+                    uint8_t* rej, bool frozen, R* chi2_out,
+                    const std::vector<double>* alpha = nullptr) {
   RefitOut o;
   std::memset(&o, 0, sizeof(o));
   size_t n = x.size();
   Trk<R> st;
   for (int i = 0; i < 5; ++i) st.p[i] = R(seed[i]);
   st.x = x[n - 1];
+  // frame of the state (clusters of a merged track lie in several sectors)
+  double cur_alpha = alpha ? (*alpha)[n - 1] : 0.0;
   R chi2 = R(0);
   int ndf = 0;
   set_diag(st, c.p.c0r);
@@ -848,6 +892,14 @@ RefitOut refit_core(const Ctx& c, const std::vector<R>& x, const std::vector<R>&
     for (size_t k = 0; k < n; ++k) {
       size_t i = (pass == 2) ? k : n - 1 - k;
       if (rej[i] != 0 && rej[i] < pass) continue;
+      if (alpha && (*alpha)[i] != cur_alpha) {
+        if (!rotate<R>(c, st, (*alpha)[i] - cur_alpha)) {
+          o.status = 1;
+          *chi2_out = R(0);
+          return o;
+        }
+        cur_alpha = (*alpha)[i];
+      }
       if (!propagate<R>(c, st, x[i])) {
         o.status = 1;
         *chi2_out = R(0);
@@ -877,6 +929,35 @@ RefitOut refit_core(const Ctx& c, const std::vector<R>& x, const std::vector<R>&
   o.ndf = ndf;
   *chi2_out = chi2;
   return o;
+}
+
+// Frame angles of a track's clusters, or empty when they share one sector.
+inline std::vector<double> track_alpha(const Ctx& c, const uint32_t* idx, size_t n) {
+  std::vector<double> al;
+  bool multi = false;
+  for (size_t k = 1; k < n; ++k) multi = multi || c.cl.sector[idx[k]] != c.cl.sector[idx[0]];
+  if (!multi) return al;
+  al.resize(n);
+  for (size_t k = 0; k < n; ++k) al[k] = sector_alpha(c.cl.sector[idx[k]]);
+  return al;
+}
+
+// Three-point seed of a track whose clusters may lie in several frames: the
+// points are first expressed in the frame of the outermost cluster.
+template <class R>
+bool seed_track(const Ctx& c, const std::vector<R>& x, const std::vector<R>& yc,
+                const std::vector<R>& zc, const std::vector<double>& al, double out[5]) {
+  if (al.empty()) return seed_three_points<R>(c, x, yc, zc, out);
+  size_t n = x.size();
+  std::vector<R> X(x), Y(yc);
+  for (size_t k = 0; k < n; ++k) {
+    double d = al[n - 1] - al[k];
+    if (d == 0.0) continue;
+    R ca = R(std::cos(d)), sa = R(std::sin(d));
+    X[k] = x[k] * ca + yc[k] * sa;
+    Y[k] = -(x[k] * sa) + yc[k] * ca;
+  }
+  return seed_three_points<R>(c, X, Y, zc, out);
 }
 
 template <class R>
@@ -1051,18 +1132,20 @@ void orc_refit(void* ctx, int prec, int64_t nt, const uint32_t* track_start,
     std::memset(&o, 0, sizeof(o));
     double seed[5];
     bool ok;
+    std::vector<double> al = track_alpha(c, cluster_idx + a, n);
+    const std::vector<double>* alp = al.empty() ? nullptr : &al;
     if (prec == 32) {
       std::vector<float> x, yc, zc, var;
       track_inputs<float>(c, cluster_idx + a, n, that[k], x, yc, zc, var);
-      ok = seeds ? true : seed_three_points<float>(c, x, yc, zc, seed);
+      ok = seeds ? true : seed_track<float>(c, x, yc, zc, al, seed);
       if (seeds) for (int i = 0; i < 5; ++i) seed[i] = seeds[k * 5 + i];
-      if (ok) { float ch; o = refit_core<float>(c, x, yc, zc, var, seed, rj, frozen, &ch); }
+      if (ok) { float ch; o = refit_core<float>(c, x, yc, zc, var, seed, rj, frozen, &ch, alp); }
     } else {
       std::vector<double> x, yc, zc, var;
       track_inputs<double>(c, cluster_idx + a, n, that[k], x, yc, zc, var);
-      ok = seeds ? true : seed_three_points<double>(c, x, yc, zc, seed);
+      ok = seeds ? true : seed_track<double>(c, x, yc, zc, al, seed);
       if (seeds) for (int i = 0; i < 5; ++i) seed[i] = seeds[k * 5 + i];
-      if (ok) { double ch; o = refit_core<double>(c, x, yc, zc, var, seed, rj, frozen, &ch); }
+      if (ok) { double ch; o = refit_core<double>(c, x, yc, zc, var, seed, rj, frozen, &ch, alp); }
     }
     if (!ok) o.status = 2;
     if (seeds_out) for (int i = 0; i < 5; ++i) seeds_out[k * 5 + i] = ok ? seed[i] : 0.0;
@@ -1114,8 +1197,10 @@ void orc_refit_grad(void* ctx, int64_t nt, const uint32_t* track_start,
       var[q] = Var(e * e);
     }
     std::vector<uint8_t> rj(rej + a, rej + b);
+    std::vector<double> al = track_alpha(c, cluster_idx + a, n);
     Var chi2;
-    RefitOut o = refit_core<Var>(c, x, yc, zc, var, seeds + k * 5, rj.data(), true, &chi2);
+    RefitOut o = refit_core<Var>(c, x, yc, zc, var, seeds + k * 5, rj.data(), true, &chi2,
+                                 al.empty() ? nullptr : &al);
     if (o.status != 0) continue;
     g_tape.backward(chi2.id, g[k]);
     auto adj = [&](const Var& v) { return v.id >= 0 ? g_tape.adj[v.id] : 0.0; };
@@ -1128,6 +1213,23 @@ void orc_refit_grad(void* ctx, int64_t nt, const uint32_t* track_start,
     for (auto& kv : lv.m) grad_calib[2 + kv.first] += adj(kv.second);
   }
   g_tape.clear();
+}
+
+// Rotation of a state (and covariance, packed lower triangle) by dalpha.
+int orc_rotate(void* ctx, const double* state, double x, double dalpha, const double* cov,
+               double* state_out, double* x_out, double* cov_out) {
+  Ctx& c = *(Ctx*)ctx;
+  Trk<double> st;
+  for (int i = 0; i < 5; ++i) st.p[i] = state[i];
+  st.x = x;
+  for (int i = 0; i < 5; ++i)
+    for (int j = 0; j < 5; ++j) st.C[i][j] = cov[i * 5 + j];
+  if (!rotate<double>(c, st, dalpha)) return 0;
+  for (int i = 0; i < 5; ++i) state_out[i] = st.p[i];
+  *x_out = st.x;
+  for (int i = 0; i < 5; ++i)
+    for (int j = 0; j < 5; ++j) cov_out[i * 5 + j] = st.C[i][j];
+  return 1;
 }
 
 // Refit of one track given float64 points directly (for closed-form checks).

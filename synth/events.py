@@ -373,17 +373,23 @@ def make_event(rng, geo: Geometry, parts: list, mode="event", t_colls=None,
         q_true=np.concatenate([cr["qpt"], np.full(nn, np.nan)]),
         t_coll=allp["t_coll"], part=allp,
         info=dict(n_signal=n_sig, n_noise=nn, sigma=sigma,
+                  larc=np.concatenate([cr["larc"], np.full(nn, np.nan)]),
                   z_meas=np.concatenate([z_m, np.full(nn, np.nan)]),
                   y_meas=np.concatenate([y_m, np.full(nn, np.nan)])),
     )
 
 
-def truth_tracks(ev: Event, min_hits=40):
-    """Truth-assigned tracks: one per (particle, sector, leg) segment.
+def truth_tracks(ev: Event, min_hits=40, merged=False):
+    """Truth-assigned tracks: one per (particle, sector, leg) segment, or with
+    merged=True one per (particle, leg, side) across sectors.
 
     Returns CSR (track_start uint32[n+1], cluster_idx uint32[...], clusters in
-    increasing row order), the collision time per track and the segment ids.
+    increasing row order -- for merged tracks: along the path, rows
+    increasing), the collision time per track and the segment (or merged
+    track) ids.
     """
+    if merged:
+        return _truth_tracks_merged(ev, min_hits)
     sig = np.nonzero(ev.segment >= 0)[0]
     seg = ev.segment[sig]
     order = np.lexsort((ev.row[sig], seg))
@@ -407,6 +413,38 @@ def truth_tracks(ev: Event, min_hits=40):
     return (np.asarray(ts, np.uint32),
             np.concatenate(ci).astype(np.uint32) if ci else np.zeros(0, np.uint32),
             np.asarray(tc, np.float64), np.asarray(sids, np.int64))
+
+
+def _truth_tracks_merged(ev: Event, min_hits):
+    sig = np.nonzero(ev.segment >= 0)[0]
+    seg = ev.segment[sig]
+    leg = seg % 4
+    side = (ev.sector[sig] >= 18).astype(np.int64)
+    mid = (ev.label[sig].astype(np.int64) * 4 + leg) * 2 + side
+    # along the path: outgoing branches (even leg) cross the rows outward,
+    # incoming ones inward; order so that rows increase
+    larc = ev.info["larc"][sig]
+    key2 = np.where(leg % 2 == 0, larc, -larc)
+    order = np.lexsort((key2, mid))
+    sig, mid = sig[order], mid[order]
+    if sig.size == 0:
+        return (np.zeros(1, np.uint32), np.zeros(0, np.uint32), np.zeros(0),
+                np.zeros(0, np.int64))
+    starts = np.concatenate([[0], np.nonzero(np.diff(mid))[0] + 1, [mid.size]])
+    ts, ci, tc, ids = [0], [], [], []
+    for a, b in zip(starts[:-1], starts[1:]):
+        if b - a < min_hits:
+            continue
+        idx = sig[a:b]
+        if np.any(np.diff(ev.row[idx].astype(np.int64)) < 0):
+            idx = idx[np.argsort(ev.row[idx], kind="stable")]
+        ci.append(idx)
+        ts.append(ts[-1] + idx.size)
+        tc.append(ev.t_coll[ev.label[idx[0]]])
+        ids.append(mid[a])
+    return (np.asarray(ts, np.uint32),
+            np.concatenate(ci).astype(np.uint32) if ci else np.zeros(0, np.uint32),
+            np.asarray(tc, np.float64), np.asarray(ids, np.int64))
 
 
 # ---------------------------------------------------------------------------

@@ -47,6 +47,8 @@ MUTANTS = {
  'that_sign': ("that = c.c.tf_start - (sg * (double)zd) / c.c.vdrift;", "that = c.c.tf_start + (sg * (double)zd) / c.c.vdrift;"),
  'shared_scale_refit': ("R sc = (c.cl.flags[i] & kFlagShared) ? R(c.p.shared_scale) : R(1);", "R sc = R(1);"),
  'nb_dmax_strict': ("if (!(D <= dmax)) continue;", "if (!(D < dmax)) continue;"),
+ 'rotation_curvature_term': ("J[2][0] = kap * sa;", "J[2][0] = -(kap * sa);"),
+ 'rotation_y_factor': ("J[0][0] = cf / c2;", "J[0][0] = c2 / cf;"),
  'cov_update_index': ("R v = st.C[i][j] - (K0[i] * HC0[j] + K1[i] * HC1[j]);", "R v = st.C[i][j] - (K0[i] * HC0[j] + K1[i] * HC0[j]);"),
 }
 

@@ -676,3 +676,122 @@ def test_shared_clusters_have_scaled_errors(geo, params):
     ratio = r2["chi2"][ok] / r["chi2"][ok]
     s = params["shared_scale"]
     np.testing.assert_allclose(ratio, 1.0 / (s * s), rtol=2e-2)
+
+
+# ------------------------------------------- tracks across sectors (rotation)
+def test_rotation_is_the_same_helix_and_its_covariance_transform(geo, params):
+    """A state re-expressed in a rotated frame is the same helix at the same
+    point: the global position and direction agree, rotating back returns the
+    state, and the covariance transform is J C J^T with J taken by finite
+    differences of (rotate, then follow the helix back to the rotated
+    reference plane)."""
+    ev = synth.make_tiny(seed=12, n_tracks=4)
+    o = _oracle(ev, geo, params)
+    rng = np.random.default_rng(3)
+    n_ok = 0
+    for _ in range(60):
+        s0 = np.array([rng.uniform(-20, 20), rng.uniform(-50, 50), rng.uniform(-0.5, 0.5),
+                       rng.uniform(-1, 1), rng.uniform(-5, 5)])
+        x0 = rng.uniform(90, 240)
+        d = rng.choice([-1, 1]) * math.pi / 9
+        s1, x1, _ = o.rotate(s0, x0, d)
+        if s1 is None:
+            continue
+        n_ok += 1
+        # same point and direction in the global frame (frames differ by d)
+        X0, Y0 = x0, s0[0]
+        X1 = x1 * math.cos(d) - s1[0] * math.sin(d)
+        Y1 = x1 * math.sin(d) + s1[0] * math.cos(d)
+        assert abs(X1 - X0) < 1e-10 and abs(Y1 - Y0) < 1e-10
+        assert abs(math.asin(s1[2]) + d - math.asin(s0[2])) < 1e-12
+        assert s1[1] == s0[1] and s1[3] == s0[3] and s1[4] == s0[4]
+        back, xb, _ = o.rotate(s1, x1, -d)
+        np.testing.assert_allclose(back, s0, rtol=0, atol=1e-12)
+        assert abs(xb - x0) < 1e-10
+        # Jacobian at the rotated reference plane x1, by finite differences
+        J = np.zeros((5, 5))
+        for k in range(5):
+            e = 1e-6 * max(1.0, abs(s0[k]))
+            outs = []
+            for sg in (1, -1):
+                sp = s0.copy()
+                sp[k] += sg * e
+                r1, xr, _ = o.rotate(sp, x0, d)
+                r2, _ = o.propagate(r1, xr, x1)
+                outs.append(r2)
+            J[:, k] = (outs[0] - outs[1]) / (2 * e)
+        A = rng.normal(size=(5, 5))
+        C = A @ A.T + np.eye(5)
+        _, _, C1 = o.rotate(s0, x0, d, C)
+        np.testing.assert_allclose(C1, J @ C @ J.T, rtol=1e-6, atol=1e-8)
+    assert n_ok >= 40
+
+
+def _merged_truth(geo, params, **kw):
+    ev = synth.make_central(**kw)
+    ts, ci, tc, ids = synth.truth_tracks(ev, 40, merged=True)
+    multi = np.array([np.unique(ev.sector[ci[a:b]]).size > 1
+                      for a, b in zip(ts[:-1], ts[1:])])
+    return ev, ts, ci, tc, multi
+
+
+def test_noise_free_helix_across_sectors_refits_to_truth(geo, params):
+    """Exact clusters of helices that cross sector boundaries: the refit,
+    rotating its state at every change of sector, returns the generating
+    parameters at the innermost cluster in that cluster's frame."""
+    ev, ts, ci, tc, multi = _merged_truth(geo, params, seed=7, n_tracks=400, noise_frac=0.0)
+    ev.y[:] = ev.y_true.astype(np.float32)
+    ev.z[:] = ev.z_true.astype(np.float32)
+    o = _oracle(ev, geo, params)
+    r = o.refit(ts, ci, tc, prec=64)
+    ok = multi & (r["status"] == 0)
+    assert ok.sum() >= 20
+    inner = ci[ts[:-1].astype(np.int64)]
+    truth = np.stack([ev.y_true, ev.z_true, ev.s_true, ev.tl_true, ev.q_true], 1)[inner]
+    d = np.abs(r["params"][ok] - truth[ok])
+    assert np.max(d[:, 0]) < 2e-5 and np.max(d[:, 1]) < 2e-5, np.max(d, 0)
+    assert np.max(d[:, 2]) < 1e-6 and np.max(d[:, 3]) < 1e-6
+    assert np.max(d[:, 4] / np.abs(truth[ok, 4])) < 2e-4
+    np.testing.assert_allclose(r["x"][ok], geo.row_x[ev.row[inner]][ok].astype(np.float64))
+
+
+def test_gradient_across_sectors_matches_finite_differences(geo, params):
+    """The tape-derived gradient of a multi-sector refit (rotations included)
+    against central finite differences of the cluster coordinates."""
+    ev, ts, ci, tc, multi = _merged_truth(geo, params, seed=8, n_tracks=300, noise_frac=0.0)
+    o = _oracle(ev, geo, params)
+    r = o.refit(ts, ci, tc, prec=64)
+    ks = np.nonzero(multi & (r["status"] == 0))[0][:2]
+    assert ks.size == 2
+    sel_ts = [0]
+    sel_ci = []
+    for k in ks:
+        sel_ci.append(ci[ts[k]:ts[k + 1]])
+        sel_ts.append(sel_ts[-1] + sel_ci[-1].size)
+    ts2, ci2, tc2 = np.array(sel_ts, np.uint32), np.concatenate(sel_ci), tc[ks]
+    r2 = o.refit(ts2, ci2, tc2, prec=64)
+    g = np.array([1.0, 0.6])
+    gy, gz, gc = o.refit_grad(ts2, ci2, tc2, r2["seeds"], r2["rej"], g)
+
+    def loss(y, z):
+        ev.y[:], ev.z[:] = y, z
+        oo = _oracle(ev, geo, params)
+        rr = oo.refit(ts2, ci2, tc2, prec=64, seeds=r2["seeds"], rej=r2["rej"])
+        oo.close()
+        return float(np.sum(g * rr["chi2"]))
+
+    y0, z0 = ev.y.copy(), ev.z.copy()
+    for q in [0, 5, ts2[1] - 1, ts2[1] + 4]:
+        i = ci2[q]
+        e = 1e-2
+        yp, ym = y0.copy(), y0.copy()
+        yp[i] += e
+        ym[i] -= e
+        fd = (loss(yp, z0) - loss(ym, z0)) / (2 * e)
+        assert abs(fd - gy[q]) < 2e-3 * max(1, abs(fd)), (q, fd, gy[q])
+        zp, zm = z0.copy(), z0.copy()
+        zp[i] += e
+        zm[i] -= e
+        fd = (loss(y0, zp) - loss(y0, zm)) / (2 * e)
+        assert abs(fd - gz[q]) < 2e-3 * max(1, abs(fd)), (q, fd, gz[q])
+    ev.y[:], ev.z[:] = y0, z0
