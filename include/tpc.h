@@ -140,8 +140,15 @@ typedef struct {
   int64_t n_assigned;            /* = track_start[n_tracks]                  */
   const uint32_t* track_start;   /* device [n_tracks + 1]                    */
   const uint32_t* cluster_idx;   /* device [n_assigned], input cluster index,
-                                    strictly increasing pad row per track,
-                                    one sector per track                    */
+                                    strictly increasing pad row per track.
+                                    Found tracks lie in one sector; a track
+                                    merged across sectors (Sec. 2, second
+                                    phase) is refitted with the state
+                                    rotated into the frame of each
+                                    cluster's sector (sectors k and k + 18
+                                    share a frame); params, cov and x are
+                                    then given in the frame of the track's
+                                    last fitted cluster                    */
   const double* t_coll;          /* device [n_tracks] collision time (us) used
                                     for the absolute z (mode 1)             */
   const uint32_t* start_hit;     /* device [n_tracks] input index of the
@@ -201,7 +208,7 @@ tpc_status tpc_set_tracks(tpc_ctx* ctx, const tpc_tracks* tracks);
  * buffers with room for the number of tracks (params [n][5], cov [n][15],
  * x [n], chi2 [n], ndf [n]; rej [n_assigned] receives for each cluster the
  * refit pass that rejected it, 0 = kept; any output may be NULL). status[n]
- * per track: 0 ok, 1 propagation failed, 2 no seed (fewer than 3 clusters or
+ * per track: 0 ok, 1 propagation or frame rotation failed, 2 no seed (fewer than 3 clusters or
  * no circle), 3 invalid track range (also raises TPC_ERR_ARG). With save_for_backward != 0 the per-step filter states are
  * kept for tpc_refit_backward. */
 tpc_status tpc_refit(tpc_ctx* ctx, int save_for_backward, float* params, float* cov, float* x,

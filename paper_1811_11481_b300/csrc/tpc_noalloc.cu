@@ -141,6 +141,7 @@ extern "C" tpc_status tpc_refit_noalloc(const tpc_geometry* geo, const tpc_param
   cfg.refit_inflate = pc.refit_inflate;
   cfg.min_acc_reject = pc.min_acc_reject;
   for (int i = 0; i < 5; ++i) cfg.c0r[i] = pc.c0r[i];
+  set_frame_rotations(cfg);
   cudaStream_t s = (cudaStream_t)stream;
   uint32_t* meta = reinterpret_cast<uint32_t*>(scratch + kRowXBytes);
   uint8_t* rej = scratch + kRowXBytes + kMetaBytes;

@@ -36,6 +36,7 @@ RefitCfg make_cfg(const Geo& g, const Params& p) {
   c.refit_inflate = p.refit_inflate;
   c.min_acc_reject = p.min_acc_reject;
   for (int i = 0; i < 5; ++i) c.c0r[i] = p.c0r[i];
+  set_frame_rotations(c);
   return c;
 }
 

@@ -3,6 +3,8 @@
 // thread through them.
 #pragma once
 
+#include <cmath>
+
 #include "tpc_math.cuh"
 
 namespace tpc {
@@ -43,11 +45,79 @@ TPC_HD Lay contiguous_layout(uint32_t a, int n) {
   return l;
 }
 
+// Sector frames (Sec. 2: 18 trapezoidal sectors per side): sectors k and
+// k + 18 share the frame rotated by (k + 1/2) * 20 degrees about the beam
+// axis, so two frames differ by a multiple of 20 degrees.
+constexpr int kFrames = 18;
+
 struct RefitCfg {
   float kB, s_max, sigma, shared_scale, chi2_out, refit_inflate;
   int32_t min_acc_reject;
   float c0r[5];
+  float rot_c[kFrames], rot_s[kFrames];  // cos, sin of m * 20 degrees
 };
+
+inline void set_frame_rotations(RefitCfg& c) {
+  for (int m = 0; m < kFrames; ++m) {
+    double a = m * (3.14159265358979323846 / 9.0);
+    c.rot_c[m] = (float)std::cos(a);
+    c.rot_s[m] = (float)std::sin(a);
+  }
+}
+
+TPC_HD int frame_of(uint32_t meta) { return (int)((meta >> 16) & 0xffu) % kFrames; }
+
+// Rotation index from frame a to frame b (angle alpha_b - alpha_a).
+TPC_HD int frame_step(int a, int b) { return b >= a ? b - a : b - a + kFrames; }
+
+// C' = J C J^T for the rotation Jacobian: J is the identity except
+// J00 = j00, J10 = j10, J20 = j20, J22 = j22.
+TPC_HD void rotate_cov(float j00, float j10, float j20, float j22, float C[15]) {
+  float Cf[5][5];
+#pragma unroll
+  for (int i = 0; i < 5; ++i)
+#pragma unroll
+    for (int j = 0; j < 5; ++j) Cf[i][j] = C[sidx(i, j)];
+  float M[5][5];
+#pragma unroll
+  for (int l = 0; l < 5; ++l) {
+    M[0][l] = j00 * Cf[0][l];
+    M[1][l] = Cf[1][l] + j10 * Cf[0][l];
+    M[2][l] = j20 * Cf[0][l] + j22 * Cf[2][l];
+    M[3][l] = Cf[3][l];
+    M[4][l] = Cf[4][l];
+  }
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    C[sidx(i, 0)] = M[i][0] * j00;
+    if (i >= 1) C[sidx(i, 1)] = M[i][1] + j10 * M[i][0];
+    if (i >= 2) C[sidx(i, 2)] = j20 * M[i][0] + j22 * M[i][2];
+    if (i >= 3) C[sidx(i, 3)] = M[i][3];
+    if (i >= 4) C[sidx(i, 4)] = M[i][4];
+  }
+}
+
+// The same helix at the same point in a frame rotated by alpha (ca, sa =
+// cos, sin): position and direction rotate and the state then refers to the
+// plane x' = x ca + y sa of the new frame. The covariance follows with the
+// Jacobian of the state at that plane: a shift of y at fixed x moves the
+// point off the plane, and the track is followed back to it along its
+// tangent. Returns false when the track would leave the new frame's forward
+// half-plane or reach s_max (merged tracks, Sec. 2 second phase).
+TPC_HD bool rotate_frame(float kB, float s_max, float ca, float sa, float p[5], float C[15],
+                         float& x) {
+  float y = p[0], s = p[2], t = p[3], q = p[4];
+  float cf = sqrtf(1.0f - s * s);
+  float s2 = s * ca - cf * sa;
+  float c2 = cf * ca + s * sa;
+  if (!(c2 > 0.0f) || !(fabsf(s2) < s_max)) return false;
+  rotate_cov(cf / c2, -(sa * t) / c2, (kB * q) * sa, c2 / cf, C);
+  float x2 = x * ca + y * sa;
+  p[0] = -(x * sa) + y * ca;
+  p[2] = s2;
+  x = x2;
+  return true;
+}
 
 TPC_HD float cl_var(const RefitCfg& p, uint32_t meta) {
   float e = ((meta >> 8) & TPC_FLAG_SHARED) ? p.sigma * p.shared_scale : p.sigma;
@@ -56,12 +126,25 @@ TPC_HD float cl_var(const RefitCfg& p, uint32_t meta) {
 
 // Seed at the outermost cluster from the circle through the innermost,
 // middle and outermost clusters.
-TPC_HD bool seed3(const Geo& g, const TrackIn& in, const Lay& ly, int n, float st[5]) {
+// The three points are expressed in the frame of the outermost cluster.
+TPC_HD bool seed3(const Geo& g, const RefitCfg& p, const TrackIn& in, const Lay& ly, int n,
+                  float st[5]) {
   if (n < 3) return false;
   int i0 = 0, im = n / 2, i2 = n - 1;
-  float x0 = g.rx[in.meta[ly.at(i0)] & 0xffu], xm = g.rx[in.meta[ly.at(im)] & 0xffu],
-        x2 = g.rx[in.meta[ly.at(i2)] & 0xffu];
+  uint32_t m0 = in.meta[ly.at(i0)], mm = in.meta[ly.at(im)], m2 = in.meta[ly.at(i2)];
+  float x0 = g.rx[m0 & 0xffu], xm = g.rx[mm & 0xffu], x2 = g.rx[m2 & 0xffu];
   float y0 = in.yc[ly.at(i0)], ym = in.yc[ly.at(im)], y2 = in.yc[ly.at(i2)];
+  int f2 = frame_of(m2);
+  auto to_outer = [&](uint32_t m, float& xx, float& yy) {
+    int d = frame_step(frame_of(m), f2);
+    if (d == 0) return;
+    float ca = p.rot_c[d], sa = p.rot_s[d];
+    float xr = xx * ca + yy * sa;
+    yy = -(xx * sa) + yy * ca;
+    xx = xr;
+  };
+  to_outer(m0, x0, y0);
+  to_outer(mm, xm, ym);
   float ax = xm - x0, ay = ym - y0, bx = x2 - x0, by = y2 - y0, ex = x2 - xm, ey = y2 - ym;
   float cross = ax * by - ay * bx;
   float la = sqrtf(ax * ax + ay * ay), lb = sqrtf(bx * bx + by * by),
@@ -88,10 +171,22 @@ struct RefitOut {
   int32_t status;  // 0 ok, 1 propagation failed, 2 no seed
 };
 
+// True when the track's clusters lie in more than one sector frame.
+TPC_HD bool spans_frames(const TrackIn& in, const Lay& ly, int n) {
+  if (n <= 0) return false;
+  int f0 = frame_of(in.meta[ly.at(0)]);
+  bool multi = false;
+  for (int k = 1; k < n; ++k) multi = multi || frame_of(in.meta[ly.at(k)]) != f0;
+  return multi;
+}
+
 // Three passes (inward, outward, inward); rej[at(k)] receives the pass that
 // rejected cluster k (0 = kept). ckpt (may be null): state before each step.
-TPC_HD RefitOut refit_track(const Geo& g, const RefitCfg& p, const TrackIn& in, const Lay& ly,
-                            int n, uint8_t* rej, float* seed_out, float* ckpt) {
+// kRot: the clusters may lie in several sector frames (the state is rotated
+// into each cluster's frame before the transport to it).
+template <bool kRot>
+TPC_HD RefitOut refit_track_in(const Geo& g, const RefitCfg& p, const TrackIn& in, const Lay& ly,
+                               int n, uint8_t* rej, float* seed_out, float* ckpt) {
   RefitOut o;
   for (int k = 0; k < n; ++k) rej[ly.at(k)] = 0;
   o.status = 0;
@@ -99,7 +194,7 @@ TPC_HD RefitOut refit_track(const Geo& g, const RefitCfg& p, const TrackIn& in, 
   o.ndf = 0;
   float* st = o.st;
   float* C = o.C;
-  if (!seed3(g, in, ly, n, st)) {
+  if (!seed3(g, p, in, ly, n, st)) {
     o.status = 2;
     for (int i = 0; i < 5; ++i) st[i] = 0.0f;
     for (int i = 0; i < 15; ++i) C[i] = 0.0f;
@@ -109,6 +204,7 @@ TPC_HD RefitOut refit_track(const Geo& g, const RefitCfg& p, const TrackIn& in, 
   if (seed_out)
     for (int i = 0; i < 5; ++i) seed_out[i] = st[i];
   float x = g.rx[in.meta[ly.at(n - 1)] & 0xffu];
+  int fr = frame_of(in.meta[ly.at(n - 1)]);  // frame of the state
   set_diag(C, p.c0r);
   float chi2 = 0.0f;
   int ndf = 0;
@@ -134,6 +230,16 @@ TPC_HD RefitOut refit_track(const Geo& g, const RefitCfg& p, const TrackIn& in, 
         if (ckpt) {
           for (int j = 0; j < 5; ++j) ckpt[ly.ck(pass, k, j)] = st[j];
           for (int j = 0; j < 15; ++j) ckpt[ly.ck(pass, k, 5 + j)] = C[j];
+        }
+        int fi = frame_of(m);
+        if (kRot && fi != fr) {
+          int d = frame_step(fr, fi);
+          if (!rotate_frame(p.kB, p.s_max, p.rot_c[d], p.rot_s[d], st, C, x)) {
+            o.status = 1;
+            o.x = x;
+            return o;
+          }
+          fr = fi;
         }
         if (!propagate(p.kB, p.s_max, st, C, x, g.rx[m & 0xffu])) {
           o.status = 1;
@@ -162,6 +268,12 @@ TPC_HD RefitOut refit_track(const Geo& g, const RefitCfg& p, const TrackIn& in, 
   o.chi2 = chi2;
   o.ndf = ndf;
   return o;
+}
+
+TPC_HD RefitOut refit_track(const Geo& g, const RefitCfg& p, const TrackIn& in, const Lay& ly,
+                            int n, uint8_t* rej, float* seed_out, float* ckpt) {
+  return spans_frames(in, ly, n) ? refit_track_in<true>(g, p, in, ly, n, rej, seed_out, ckpt)
+                                 : refit_track_in<false>(g, p, in, ly, n, rej, seed_out, ckpt);
 }
 
 // ------------------------------------------------------------ dual numbers
@@ -374,27 +486,164 @@ TPC_HD void transport_adjoint(float kB, float dx, const float p[5], const float 
   }
 }
 
+// Adjoint of the start x of a transport (the step length dx = x2 - x falls
+// as x grows), for steps that start at a state-dependent x (after a frame
+// rotation). p, Cp: state and covariance before the step, pe: state after
+// it; pb, G: adjoints after the step (before transport_adjoint consumes
+// them). The end point slides along the track (dy/dx = tan phi, dz/dx =
+// tan lambda / cos phi, dsin(phi)/dx = -kappa) and the Jacobian entries
+// change with dx, differentiated with a dual number in dx.
+TPC_HD float transport_x_adjoint(float kB, float dx, const float p[5], const float pe[5],
+                                 const float Cp[15], const Jac& J, const float pb[5],
+                                 const float G[15]) {
+  float kap = kB * p[4];
+  float s2v = pe[2];
+  float ic2 = 1.0f / sqrtf(1.0f - s2v * s2v);
+  float g = pb[0] * (s2v * ic2) + pb[1] * (p[3] * ic2) - pb[2] * kap;
+  D3 X{dx, 1.f, 0.f, 0.f};
+  D3 s = dc(p[2]);
+  float t = p[3];
+  D3 one = dc(1.0f);
+  D3 s2 = s - kap * X;
+  D3 c1 = dsqrt(one - s * s);
+  D3 c2 = dsqrt(one - s2 * s2);
+  D3 N = s + s2;
+  D3 D = c1 + c2;
+  D3 T = N / D;
+  D3 opt = one + T * T;
+  D3 d = X * dsqrt(opt);
+  D3 h = 0.5f * (kap * d);
+  D3 A = chain(h, arc_factor(h.v), arc_factor_deriv(h.v));
+  D3 l = d * A;
+  D3 dDds = -(s / c1) - (s2 / c2);
+  D3 kdx = kB * X;
+  D3 dDdq = kdx * (s2 / c2);
+  D3 dTds = (dc(2.0f) - T * dDds) / D;
+  D3 dTdq = (-kdx - T * dDdq) / D;
+  D3 Jys = X * dTds;
+  D3 Jyq = X * dTdq;
+  D3 gg = (d * T) / opt;
+  D3 E = one / dsqrt(one - h * h);
+  D3 Bh = chain(h, arc_factor_deriv(h.v), arc_factor_deriv2(h.v));
+  D3 Jzs = t * (E * (gg * dTds));
+  D3 Jzq = t * (E * (gg * dTdq) + 0.5f * (kB * ((d * d) * Bh)));
+  D3 Jzt = l;
+  // Jbar = 2 G J C at the entries that depend on dx: rows 0..2, columns 2..4
+  float Cf[5][5], Gf[5][5];
+  unpack(Cp, Cf);
+  unpack(G, Gf);
+  float M[5][3];
+  for (int b = 0; b < 3; ++b) {
+    int l2 = b + 2;
+    M[0][b] = Cf[0][l2] + J.ys * Cf[2][l2] + J.yq * Cf[4][l2];
+    M[1][b] = Cf[1][l2] + J.zs * Cf[2][l2] + J.zt * Cf[3][l2] + J.zq * Cf[4][l2];
+    M[2][b] = Cf[2][l2] + J.sq * Cf[4][l2];
+    M[3][b] = Cf[3][l2];
+    M[4][b] = Cf[4][l2];
+  }
+  float Jb[3][3];
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) {
+      float acc = 0.f;
+      for (int c = 0; c < 5; ++c) acc += Gf[a][c] * M[c][b];
+      Jb[a][b] = 2.0f * acc;
+    }
+  float gj = Jb[0][0] * Jys.d0 + Jb[0][2] * Jyq.d0 + Jb[1][0] * Jzs.d0 + Jb[1][1] * Jzt.d0 +
+             Jb[1][2] * Jzq.d0 - Jb[2][2] * kB;
+  return -(g + gj);
+}
+
+// Adjoint of rotate_frame at the state p (before the rotation, reference x
+// fixed) with covariance Cp: on entry pb, G, xb are the adjoints of the
+// rotated state, covariance and reference x; on exit pb, G are those of p
+// and Cp. The rotation Jacobian depends on (sin phi, tan lambda, q/pT): its
+// second-order term with a dual number in those three.
+TPC_HD void rotate_adjoint(float kB, float ca, float sa, const float p[5], const float Cp[15],
+                           float xb, float pb[5], float G[15]) {
+  D3 s{p[2], 1.f, 0.f, 0.f}, t{p[3], 0.f, 1.f, 0.f}, q{p[4], 0.f, 0.f, 1.f};
+  D3 one = dc(1.0f);
+  D3 cf = dsqrt(one - s * s);
+  D3 c2 = ca * cf + sa * s;
+  D3 j00 = cf / c2;
+  D3 j10 = -(sa * t) / c2;
+  D3 j20 = (kB * sa) * q;
+  D3 j22 = c2 / cf;
+  float Cf[5][5], Gf[5][5];
+  unpack(Cp, Cf);
+  unpack(G, Gf);
+  // columns 0 and 2 of J C
+  float M0[5], M2[5];
+  M0[0] = j00.v * Cf[0][0];
+  M2[0] = j00.v * Cf[0][2];
+  M0[1] = Cf[1][0] + j10.v * Cf[0][0];
+  M2[1] = Cf[1][2] + j10.v * Cf[0][2];
+  M0[2] = j20.v * Cf[0][0] + j22.v * Cf[2][0];
+  M2[2] = j20.v * Cf[0][2] + j22.v * Cf[2][2];
+  M0[3] = Cf[3][0];
+  M2[3] = Cf[3][2];
+  M0[4] = Cf[4][0];
+  M2[4] = Cf[4][2];
+  float b00 = 0.f, b10 = 0.f, b20 = 0.f, b22 = 0.f;
+  for (int c = 0; c < 5; ++c) {
+    b00 += Gf[0][c] * M0[c];
+    b10 += Gf[1][c] * M0[c];
+    b20 += Gf[2][c] * M0[c];
+    b22 += Gf[2][c] * M2[c];
+  }
+  float gs = 2.0f * (b00 * j00.d0 + b10 * j10.d0 + b22 * j22.d0);
+  float gt = 2.0f * (b10 * j10.d1);
+  float gq = 2.0f * (b20 * j20.d2);
+  float dsds = ca + sa * (p[2] / cf.v);
+  float n0 = ca * pb[0] + sa * xb;
+  float n2 = dsds * pb[2] + gs;
+  pb[0] = n0;
+  pb[2] = n2;
+  pb[3] += gt;
+  pb[4] += gq;
+  // G <- J^T G J
+  float X[5][5];
+  for (int i = 0; i < 5; ++i) {
+    X[i][0] = Gf[i][0] * j00.v + Gf[i][1] * j10.v + Gf[i][2] * j20.v;
+    X[i][1] = Gf[i][1];
+    X[i][2] = Gf[i][2] * j22.v;
+    X[i][3] = Gf[i][3];
+    X[i][4] = Gf[i][4];
+  }
+  for (int j = 0; j < 5; ++j) {
+    float col[5] = {j00.v * X[0][j] + j10.v * X[1][j] + j20.v * X[2][j], X[1][j],
+                    j22.v * X[2][j], X[3][j], X[4][j]};
+    for (int i = j; i < 5; ++i) G[sidx(i, j)] = col[i];
+  }
+}
+
 TPC_HD bool step_active(int rj, int pass) { return !(rj != 0 && rj < pass); }
 
 // Reverse sweep of one saved refit: writes the adjoints of the calibrated
-// coordinates gyc[at(k)], gzc[at(k)] of L = gT * chi2(pass 3).
-TPC_HD void refit_backward_track(const Geo& g, const RefitCfg& p, const TrackIn& in, const Lay& ly,
-                                 int n, const uint8_t* rej, const float* ckpt, float gT,
-                                 float* gyc, float* gzc) {
+// coordinates gyc[at(k)], gzc[at(k)] of L = gT * chi2(pass 3). kRot as for
+// refit_track_in.
+template <bool kRot>
+TPC_HD void refit_backward_in(const Geo& g, const RefitCfg& p, const TrackIn& in, const Lay& ly,
+                              int n, const uint8_t* rej, const float* ckpt, float gT, float* gyc,
+                              float* gzc) {
   for (int k = 0; k < n; ++k) {
     gyc[ly.at(k)] = 0.0f;
     gzc[ly.at(k)] = 0.0f;
   }
   auto xof = [&](int i) { return g.rx[in.meta[ly.at(i)] & 0xffu]; };
   auto idx_of = [&](int pass, int k) { return pass == 2 ? k : n - 1 - k; };
+  // x and frame of the state at the end of each pass (0: the seed's)
   float xend[4];
+  int fend[4];
   xend[0] = xof(n - 1);
+  fend[0] = frame_of(in.meta[ly.at(n - 1)]);
   for (int pass = 1; pass <= 3; ++pass) {
     xend[pass] = xend[pass - 1];
+    fend[pass] = fend[pass - 1];
     for (int k = n - 1; k >= 0; --k) {
       int i = idx_of(pass, k);
       if (step_active(rej[ly.at(i)], pass)) {
         xend[pass] = xof(i);
+        fend[pass] = frame_of(in.meta[ly.at(i)]);
         break;
       }
     }
@@ -476,16 +725,24 @@ TPC_HD void refit_backward_track(const Geo& g, const RefitCfg& p, const TrackIn&
         mzq2 = in.zc[ly.at(iq)];
         rjq2 = rej[ly.at(iq)];
       }
-      // the current step, from its checkpoint
+      // the current step, from its checkpoint: a frame rotation when the
+      // cluster lies in another sector frame, then the transport
       float xprev = kp >= 0 ? g.rx[mp & 0xffu] : xend[pass - 1];
+      int fprev = kp >= 0 ? frame_of(mp) : fend[pass - 1];
+      int rot = kRot ? frame_step(fprev, frame_of(mc)) : 0;
       float xi = g.rx[mc & 0xffu];
+      float pr[5], Cr[15];
+      for (int j = 0; j < 5; ++j) pr[j] = p0[j];
+      for (int j = 0; j < 15; ++j) Cr[j] = C0[j];
+      float xs = xprev;
+      if (kRot && rot != 0) rotate_frame(p.kB, 2.0f, p.rot_c[rot], p.rot_s[rot], pr, Cr, xs);
       float pp[5];
-      for (int j = 0; j < 5; ++j) pp[j] = p0[j];
-      float xx = xprev;
+      for (int j = 0; j < 5; ++j) pp[j] = pr[j];
+      float xx = xs;
       Jac J;
       transport(p.kB, 2.0f, pp, xx, xi, J);
       float Cp[15];
-      for (int j = 0; j < 15; ++j) Cp[j] = C0[j];
+      for (int j = 0; j < 15; ++j) Cp[j] = Cr[j];
       transport_cov(J, Cp);
       if (rjc != pass) {
         float v = cl_var(p, mc);
@@ -495,7 +752,10 @@ TPC_HD void refit_backward_track(const Geo& g, const RefitCfg& p, const TrackIn&
         gyc[ly.at(ic)] = gyo + mb[0];
         gzc[ly.at(ic)] = gzo + mb[1];
       }
-      transport_adjoint(p.kB, xi - xprev, p0, C0, J, pb, G);
+      float xb = 0.0f;
+      if (kRot && rot != 0) xb = transport_x_adjoint(p.kB, xi - xs, pr, pp, Cr, J, pb, G);
+      transport_adjoint(p.kB, xi - xs, pr, Cr, J, pb, G);
+      if (kRot && rot != 0) rotate_adjoint(p.kB, p.rot_c[rot], p.rot_s[rot], p0, C0, xb, pb, G);
       kc = kp;
       if (kp >= 0) {
         ic = idx_of(pass, kp);
@@ -517,6 +777,15 @@ TPC_HD void refit_backward_track(const Geo& g, const RefitCfg& p, const TrackIn&
     if (pass > 1)
       for (int j = 0; j < 15; ++j) G[j] = G[j] * p.refit_inflate;
   }
+}
+
+TPC_HD void refit_backward_track(const Geo& g, const RefitCfg& p, const TrackIn& in, const Lay& ly,
+                                 int n, const uint8_t* rej, const float* ckpt, float gT,
+                                 float* gyc, float* gzc) {
+  if (spans_frames(in, ly, n))
+    refit_backward_in<true>(g, p, in, ly, n, rej, ckpt, gT, gyc, gzc);
+  else
+    refit_backward_in<false>(g, p, in, ly, n, rej, ckpt, gT, gyc, gzc);
 }
 
 }  // namespace tpc

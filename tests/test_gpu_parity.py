@@ -162,12 +162,11 @@ def test_gradient_matches_oracle(run, geo):
             assert err < 1e-3, (blk, err)
 
 
-def test_truth_track_refit_time_mode_with_distortion(geo):
-    cal = synth.nominal_calib()
-    cal.spline = synth.random_distortion(np.random.default_rng(8), 1.0)
-    ev = synth.make_tiny(seed=35, n_tracks=300, central=True, mode="time", tf_start=1.0e6,
-                         n_coll=3, calib=cal)
-    ts, ci, tc, _ = synth.truth_tracks(ev, 40)
+def _truth_refit_parity(geo, ev, cal, merged):
+    """Refit of truth tracks given through tpc_set_tracks against the FP64
+    oracle, and the adjoint against the oracle's gradient. Returns the
+    track mask (both sides converged) and the track set."""
+    ts, ci, tc, _ = synth.truth_tracks(ev, 40, merged=merged)
     import torch
     tr = tracker(geo)
     tr.set_calib(cal.vdrift, cal.t0, cal.spline)
@@ -189,13 +188,42 @@ def test_truth_track_refit_time_mode_with_distortion(geo):
     assert sel.sum() > 0.98 * ok.sum()
     e = rel_err(got["params"][sel].astype(np.float64), ref["params"][sel])
     assert np.all(e <= RTOL), e.max(0)
-    gy, gz, gc = [t.cpu().numpy() for t in tr.refit_backward(torch.ones(ts.size - 1, device=tr.dev))]
-    ry, rz, rc = o.refit_grad(ts, ci, tc, ref["seeds"], got["rej"], np.ones(ts.size - 1))
+    np.testing.assert_allclose(got["x"][sel], ref["x"][sel], rtol=0, atol=1e-4)
+    w = np.linspace(0.5, 1.5, ts.size - 1)
+    gy, gz, gc = [t.cpu().numpy() for t in tr.refit_backward(torch.as_tensor(w, device=tr.dev,
+                                                                              dtype=torch.float32))]
+    ry, rz, rc = o.refit_grad(ts, ci, tc, ref["seeds"], got["rej"], w)
     m = np.repeat(ok, np.diff(ts.astype(np.int64)))
     for a, b in ((gy, ry), (gz, rz)):
         assert np.linalg.norm(a[m] - b[m]) / np.linalg.norm(b[m]) < 1e-3
-    for blk in (slice(0, 1), slice(1, 2), slice(2, None)):
-        assert np.linalg.norm(gc[blk] - rc[blk]) / np.linalg.norm(rc[blk]) < 1e-3, blk
+    if ev.mode == "time":
+        for blk in (slice(0, 1), slice(1, 2), slice(2, None)):
+            assert np.linalg.norm(gc[blk] - rc[blk]) / np.linalg.norm(rc[blk]) < 1e-3, blk
+    return ok, ts, ci
+
+
+def test_truth_track_refit_time_mode_with_distortion(geo):
+    cal = synth.nominal_calib()
+    cal.spline = synth.random_distortion(np.random.default_rng(8), 1.0)
+    ev = synth.make_tiny(seed=35, n_tracks=300, central=True, mode="time", tf_start=1.0e6,
+                         n_coll=3, calib=cal)
+    _truth_refit_parity(geo, ev, cal, merged=False)
+
+
+@pytest.mark.parametrize("mode", ["event", "time"])
+def test_tracks_across_sectors(geo, mode):
+    """Truth tracks merged across sectors (Sec. 2, second phase): the refit
+    and its adjoint rotate the state into the frame of each cluster's
+    sector."""
+    cal = synth.nominal_calib()
+    if mode == "time":
+        cal.spline = synth.random_distortion(np.random.default_rng(9), 1.0)
+    ev = synth.make_tiny(seed=36, n_tracks=300, central=True, mode=mode, tf_start=1.0e6,
+                         n_coll=2, calib=cal)
+    ok, ts, ci = _truth_refit_parity(geo, ev, cal, merged=True)
+    multi = np.array([np.unique(ev.sector[ci[ts[k]:ts[k + 1]]] % 18).size > 1
+                      for k in range(ts.size - 1)])
+    assert (ok & multi).sum() >= 50
 
 
 def test_empty_and_degenerate_inputs(geo):
