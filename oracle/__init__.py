@@ -58,7 +58,7 @@ class _Params(C.Structure):
                 ("inward_cov_scale", C.c_float), ("c0t", C.c_float * 5),
                 ("c0r", C.c_float * 5), ("chi2_out", C.c_float),
                 ("min_acc_reject", C.c_int32), ("refit_inflate", C.c_float),
-                ("seed_max_hits", C.c_int32)]
+                ("seed_max_hits", C.c_int32), ("chi2_merge", C.c_float)]
 
 
 class _Calib(C.Structure):
@@ -110,6 +110,9 @@ def lib():
         L.orc_jacobian.argtypes = [vp, vp, C.c_double, C.c_double, vp, vp]
         L.orc_update.argtypes = [vp, vp, C.c_double, C.c_double, C.c_double, C.c_double,
                                  vp, vp, vp]
+        L.orc_merge.restype = C.c_int64
+        L.orc_merge.argtypes = [vp, C.c_int, C.c_int64, vp, vp, vp, vp, vp, vp, vp, vp, vp,
+                                vp, vp, vp, vp]
         L.orc_rotate.restype = C.c_int
         L.orc_rotate.argtypes = [vp, vp, C.c_double, C.c_double, vp, vp, vp, vp]
         L.orc_dca_z.restype = C.c_double
@@ -314,6 +317,27 @@ class Oracle:
                              _p(np.ascontiguousarray(seeds, np.float64)),
                              _p(np.ascontiguousarray(rej, np.uint8)), _p(g), _p(gy), _p(gz), _p(gc))
         return gy, gz, gc
+
+    # --- Sec. 2 second phase: segment merging
+    def merge(self, track_start, cluster_idx, that, params, cov, x, status, prec=32):
+        """Links between segments and the merged track set; params, cov, x,
+        status: the segments' refitted states at their innermost cluster."""
+        ts = np.ascontiguousarray(track_start, np.uint32)
+        ci = np.ascontiguousarray(cluster_idx, np.uint32)
+        nt = ts.size - 1
+        f64 = lambda a, shp: np.ascontiguousarray(np.asarray(a, np.float64).reshape(shp))
+        nxt = np.empty(nt, np.int32)
+        lc = np.empty(nt)
+        ots = np.zeros(nt + 1, np.uint32)
+        oci = np.zeros(max(ci.size, 1), np.uint32)
+        oth = np.zeros(max(nt, 1))
+        ohd = np.zeros(max(nt, 1), np.int64)
+        m = lib().orc_merge(self.h, prec, nt, _p(ts), _p(ci), _p(f64(that, (nt,))),
+                            _p(f64(params, (nt, 5))), _p(f64(cov, (nt, 15))),
+                            _p(f64(x, (nt,))), _p(np.ascontiguousarray(status, np.int32)),
+                            _p(nxt), _p(lc), _p(ots), _p(oci), _p(oth), _p(ohd))
+        return dict(next=nxt, link_chi2=lc, track_start=ots[:m + 1].copy(),
+                    cluster_idx=oci[:ci.size].copy(), that=oth[:m].copy(), head=ohd[:m].copy())
 
     # --- single-step helpers
     def propagate(self, state, x1, x2, cov=None):

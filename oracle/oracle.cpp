@@ -230,6 +230,7 @@ struct OrcParams {
   float refit_inflate;    // passes 2 and 3 start from the previous pass's
                           // final covariance times this factor
   int32_t seed_max_hits;  // chain hits used by the seed fit (Sec. 2: 4 to 10)
+  float chi2_merge;       // segment-merging cut on the 5-parameter chi2
 };
 
 struct OrcCalib {
@@ -974,6 +975,138 @@ void track_inputs(const Ctx& c, const uint32_t* idx, size_t n, double that, std:
   }
 }
 
+// ----------------------------------------------------- segment merging
+// Sec. 2, second phase: the track segments found in the individual sectors
+// are merged before the final fit. The paper gives no procedure; the reading
+// taken here:
+//  - a segment is described by its refitted state at its innermost cluster
+//    (in its sector's frame), its pad-row range and its collision time;
+//  - segment j may continue segment i when both converged, lie in the same
+//    event and on the same side (the central electrode is not crossed), j's
+//    sector frame is i's or one of its two neighbours, and j starts on a pad
+//    row beyond i's last one;
+//  - i's state is rotated into j's frame and transported to j's innermost
+//    x; in the time-frame mode j's z is first expressed with i's collision
+//    time; chi2 = d^T (C_i' + C_j)^-1 d over the five parameters, by a
+//    Cholesky factorisation (the pair is not compared when a pivot is not
+//    positive);
+//  - pairs whose tan(lambda) or q/pT differ by more than sqrt(2 chi2_merge)
+//    standard deviations of the difference are not compared (these two
+//    parameters are unchanged by the rotation and the transport);
+//  - i -> j is a link when chi2 <= chi2_merge and j is i's best continuation
+//    and i is j's best predecessor (smallest chi2, then smallest index);
+//  - a merged track is a chain of links from a segment without predecessor,
+//    its clusters in chain order, its collision time and start hit those of
+//    that first segment; merged tracks are ordered by their first segment.
+struct SegInfo {
+  bool ok;
+  int64_t ev;
+  int side, frame, rlo, rhi;
+};
+
+template <class R>
+bool merge_chi2(const Ctx& c, const R pi[5], const R Ci[15], R xi, double thi, const R pj[5],
+                const R Cj[15], R xj, double thj, int fi, int fj, int side, R& chi2) {
+  R cut = R(c.p.chi2_merge);
+  for (int k = 3; k <= 4; ++k) {
+    int d = k * (k + 1) / 2 + k;
+    R dd = pi[k] - pj[k];
+    if (dd * dd > (R(2) * cut) * (Ci[d] + Cj[d])) return false;
+  }
+  Trk<R> st;
+  for (int k = 0; k < 5; ++k) st.p[k] = pi[k];
+  st.x = xi;
+  for (int a = 0, k = 0; a < 5; ++a)
+    for (int b = 0; b <= a; ++b, ++k) {
+      st.C[a][b] = Ci[k];
+      st.C[b][a] = Ci[k];
+    }
+  if (fj != fi && !rotate<R>(c, st, sector_alpha(fj) - sector_alpha(fi))) return false;
+  if (!propagate<R>(c, st, xj)) return false;
+  R shift = R(0);
+  if (c.cl.mode == 1) {
+    double sg = side == 0 ? 1.0 : -1.0;
+    shift = (R)(sg * c.c.vdrift * (thi - thj));
+  }
+  R d[5];
+  for (int k = 0; k < 5; ++k) d[k] = st.p[k] - pj[k];
+  d[1] = st.p[1] - (pj[1] + shift);
+  // S = C_i' + C_j = L L^T
+  R S[5][5], L[5][5];
+  for (int a = 0, k = 0; a < 5; ++a)
+    for (int b = 0; b <= a; ++b, ++k) S[a][b] = st.C[a][b] + Cj[k];
+  for (int a = 0; a < 5; ++a)
+    for (int b = 0; b <= a; ++b) {
+      R acc = S[a][b];
+      for (int k = 0; k < b; ++k) acc = acc - L[a][k] * L[b][k];
+      if (a == b) {
+        if (!(acc > R(0))) return false;
+        L[a][a] = sqrt_(acc);
+      } else {
+        L[a][b] = acc / L[b][b];
+      }
+    }
+  R w[5];
+  for (int a = 0; a < 5; ++a) {
+    R acc = d[a];
+    for (int k = 0; k < a; ++k) acc = acc - L[a][k] * w[k];
+    w[a] = acc / L[a][a];
+  }
+  R ch = R(0);
+  for (int a = 0; a < 5; ++a) ch = ch + w[a] * w[a];
+  chi2 = ch;
+  return ch <= cut;
+}
+
+template <class R>
+void merge_links(const Ctx& c, int64_t nt, const uint32_t* ts, const uint32_t* ci,
+                 const double* that, const double* params, const double* cov, const double* xs,
+                 const int32_t* status, int32_t* next, double* link_chi2) {
+  std::vector<SegInfo> sg(nt);
+  std::vector<R> P(nt * 5), Cv(nt * 15), X(nt);
+  for (int64_t i = 0; i < nt; ++i) {
+    SegInfo& g = sg[i];
+    uint32_t a = ts[i], b = ts[i + 1];
+    g.ok = status[i] == 0 && b > a;
+    if (b > a) {
+      uint32_t f = ci[a], l = ci[b - 1];
+      g.ev = c.cl.event ? (int64_t)c.cl.event[f] : 0;
+      g.side = c.cl.sector[f] < 18 ? 0 : 1;
+      g.frame = c.cl.sector[f] % 18;
+      g.rlo = c.cl.row[f];
+      g.rhi = c.cl.row[l];
+    }
+    for (int k = 0; k < 5; ++k) P[i * 5 + k] = R(params[i * 5 + k]);
+    for (int k = 0; k < 15; ++k) Cv[i * 15 + k] = R(cov[i * 15 + k]);
+    X[i] = R(xs[i]);
+  }
+  // best continuation of each segment and best predecessor of each segment
+  std::vector<int64_t> out(nt, -1), in(nt, -1);
+  std::vector<R> out_c(nt, R(0)), in_c(nt, R(0));
+  for (int64_t i = 0; i < nt; ++i) {
+    if (!sg[i].ok) continue;
+    for (int64_t j = 0; j < nt; ++j) {
+      if (j == i || !sg[j].ok || sg[j].ev != sg[i].ev || sg[j].side != sg[i].side) continue;
+      int df = (sg[j].frame - sg[i].frame + 18) % 18;
+      if (!(df == 0 || df == 1 || df == 17) || !(sg[j].rlo > sg[i].rhi)) continue;
+      R ch;
+      if (!merge_chi2<R>(c, &P[i * 5], &Cv[i * 15], X[i], that[i], &P[j * 5], &Cv[j * 15], X[j],
+                         that[j], sg[i].frame, sg[j].frame, sg[i].side, ch))
+        continue;
+      if (out[i] < 0 || ch < out_c[i]) { out[i] = j; out_c[i] = ch; }
+      if (in[j] < 0 || ch < in_c[j] || (ch == in_c[j] && i < in[j])) { in[j] = i; in_c[j] = ch; }
+    }
+  }
+  for (int64_t i = 0; i < nt; ++i) {
+    next[i] = -1;
+    link_chi2[i] = 0.0;
+    if (out[i] >= 0 && in[out[i]] == i) {
+      next[i] = (int32_t)out[i];
+      link_chi2[i] = (double)val(out_c[i]);
+    }
+  }
+}
+
 }  // namespace
 
 // ======================================================================
@@ -1213,6 +1346,40 @@ void orc_refit_grad(void* ctx, int64_t nt, const uint32_t* track_start,
     for (auto& kv : lv.m) grad_calib[2 + kv.first] += adj(kv.second);
   }
   g_tape.clear();
+}
+
+// Segment merging (Sec. 2, second phase), decisions in precision prec.
+// Inputs: the segments as a track set (CSR), their collision times and
+// refitted states at the innermost cluster (params [nt][5], cov [nt][15]
+// packed lower triangle, x [nt], status [nt]). Outputs: next [nt] (the
+// following segment or -1) and its chi2; the merged track set (out_ts
+// [nt + 1], out_ci [n_assigned], out_that and out_head [nt]). Returns the
+// number of merged tracks.
+int64_t orc_merge(void* ctx, int prec, int64_t nt, const uint32_t* ts, const uint32_t* ci,
+                  const double* that, const double* params, const double* cov, const double* x,
+                  const int32_t* status, int32_t* next, double* link_chi2, uint32_t* out_ts,
+                  uint32_t* out_ci, double* out_that, int64_t* out_head) {
+  Ctx& c = *(Ctx*)ctx;
+  if (prec == 32)
+    merge_links<float>(c, nt, ts, ci, that, params, cov, x, status, next, link_chi2);
+  else
+    merge_links<double>(c, nt, ts, ci, that, params, cov, x, status, next, link_chi2);
+  std::vector<char> has_in(nt, 0);
+  for (int64_t i = 0; i < nt; ++i)
+    if (next[i] >= 0) has_in[next[i]] = 1;
+  int64_t m = 0;
+  uint32_t nc = 0;
+  out_ts[0] = 0;
+  for (int64_t i = 0; i < nt; ++i) {
+    if (has_in[i]) continue;
+    for (int64_t s = i; s >= 0; s = next[s])
+      for (uint32_t k = ts[s]; k < ts[s + 1]; ++k) out_ci[nc++] = ci[k];
+    out_that[m] = that[i];
+    out_head[m] = i;
+    ++m;
+    out_ts[m] = nc;
+  }
+  return m;
 }
 
 // Rotation of a state (and covariance, packed lower triangle) by dalpha.

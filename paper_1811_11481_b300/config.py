@@ -28,6 +28,7 @@ DEFAULT_PARAMS = dict(
     min_acc_reject=5,        # accepted clusters before rejection starts
     refit_inflate=100.0,     # covariance inflation between refit passes
     seed_max_hits=10,        # chain hits in the seed fit (Sec. 2: segments of 4-10 hits)
+    chi2_merge=30.0,         # segment-merging cut on the 5-parameter chi2 (Sec. 2, phase 2)
 )
 
 # flag bits of a cluster (Sec. 3 lists the special cluster types)

@@ -50,6 +50,15 @@ MUTANTS = {
  'rotation_curvature_term': ("J[2][0] = kap * sa;", "J[2][0] = -(kap * sa);"),
  'rotation_y_factor': ("J[0][0] = cf / c2;", "J[0][0] = c2 / cf;"),
  'cov_update_index': ("R v = st.C[i][j] - (K0[i] * HC0[j] + K1[i] * HC1[j]);", "R v = st.C[i][j] - (K0[i] * HC0[j] + K1[i] * HC0[j]);"),
+ 'merge_shift_sign': ("shift = (R)(sg * c.c.vdrift * (thi - thj));", "shift = (R)(sg * c.c.vdrift * (thj - thi));"),
+ 'merge_drop_cj': ("S[a][b] = st.C[a][b] + Cj[k];", "S[a][b] = st.C[a][b];"),
+ 'merge_rotation_dir': ("rotate<R>(c, st, sector_alpha(fj) - sector_alpha(fi))", "rotate<R>(c, st, sector_alpha(fi) - sector_alpha(fj))"),
+ 'merge_not_mutual': ("if (out[i] >= 0 && in[out[i]] == i) {", "if (out[i] >= 0) {"),
+ 'merge_row_rule': ("!(sg[j].rlo > sg[i].rhi)", "!(sg[j].rlo >= sg[i].rhi)"),
+ 'merge_frames': ("!(df == 0 || df == 1 || df == 17)", "!(df <= 2 || df >= 16)"),
+ 'merge_side': ("sg[j].ev != sg[i].ev || sg[j].side != sg[i].side) continue;", "sg[j].ev != sg[i].ev) continue;"),
+ 'merge_cholesky_sign': ("for (int k = 0; k < b; ++k) acc = acc - L[a][k] * L[b][k];", "for (int k = 0; k < b; ++k) acc = acc + L[a][k] * L[b][k];"),
+ 'merge_solve_operand': ("for (int k = 0; k < a; ++k) acc = acc - L[a][k] * w[k];", "for (int k = 0; k < a; ++k) acc = acc - L[a][k] * d[k];"),
 }
 
 

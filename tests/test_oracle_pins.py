@@ -795,3 +795,175 @@ def test_gradient_across_sectors_matches_finite_differences(geo, params):
         fd = (loss(y0, zp) - loss(y0, zm)) / (2 * e)
         assert abs(fd - gz[q]) < 2e-3 * max(1, abs(fd)), (q, fd, gz[q])
     ev.y[:], ev.z[:] = y0, z0
+
+
+# ------------------------------------------------ segment merging (Sec. 2)
+def _segment_key(ev):
+    """Particle and leg of each cluster (-1 for noise)."""
+    key = ev.label.astype(np.int64) * 4 + np.where(ev.segment >= 0, ev.segment % 4, 0)
+    key[ev.label < 0] = -1
+    return key
+
+
+@pytest.mark.parametrize("mode", ["event", "time"])
+def test_merge_links_segments_of_one_particle(geo, params, mode):
+    """Found and refitted sector segments of a central event (three
+    collisions): every link joins two segments of the same particle leg,
+    nearly every pair of consecutive segments of a leg is linked, and the
+    link chi2 follows a chi2 distribution of 5 degrees of freedom (the
+    covariances are consistent)."""
+    ev = synth.make_tiny(seed=41, n_tracks=300, central=True, mode=mode, noise_frac=0.1,
+                         tf_start=1.0e6, n_coll=3)
+    o = _oracle(ev, geo, params)
+    tr = o.find(prec=32)["tracks"]
+    ts, ci, tt = tr["track_start"], tr["cluster_idx"], tr["that"]
+    r = o.refit(ts, ci, tt, prec=64)
+    m = o.merge(ts, ci, tt, r["params"], r["cov"], r["x"], r["status"])
+    nt = ts.size - 1
+    key = _segment_key(ev)
+    lab = np.array([np.bincount(k[k >= 0]).argmax() if (k >= 0).any() else -1
+                    for k in (key[ci[ts[j]:ts[j + 1]]] for j in range(nt))])
+    nx = m["next"]
+    links = np.nonzero(nx >= 0)[0]
+    assert links.size > 300
+    assert np.all(lab[links] == lab[nx[links]]) and np.all(lab[links] >= 0)
+    assert 4.5 < m["link_chi2"][links].mean() < 6.0
+    assert np.all(m["link_chi2"][links] <= params["chi2_merge"])
+    # consecutive segments of a leg (same side, both refitted)
+    first_row = ev.row[ci[ts[:-1].astype(np.int64)]]
+    side = ev.sector[ci[ts[:-1].astype(np.int64)]] // 18
+    pairs = linked = 0
+    for k in np.unique(lab[lab >= 0]):
+        segs = [j for j in np.nonzero(lab == k)[0] if r["status"][j] == 0]
+        segs.sort(key=lambda j: first_row[j])
+        for a, b in zip(segs[:-1], segs[1:]):
+            if side[a] == side[b]:
+                pairs += 1
+                linked += nx[a] == b
+    assert linked >= 0.99 * pairs and pairs > 300
+    # the merged track set: chains of segments from a segment without
+    # predecessor, in the order of that segment
+    heads = np.setdiff1d(np.arange(nt), nx[links])
+    np.testing.assert_array_equal(m["head"], heads)
+    assert m["track_start"].size - 1 == nt - links.size
+    for t, h in enumerate(heads):
+        chain = [h]
+        while nx[chain[-1]] >= 0:
+            chain.append(nx[chain[-1]])
+        want = np.concatenate([ci[ts[j]:ts[j + 1]] for j in chain])
+        np.testing.assert_array_equal(m["cluster_idx"][m["track_start"][t]:m["track_start"][t + 1]],
+                                      want)
+        assert m["that"][t] == tt[h]
+
+
+def _pick_clusters(ev, sector, rows):
+    """One cluster of the given sector on each of the given rows."""
+    out = []
+    for r in rows:
+        idx = np.nonzero((ev.sector == sector) & (ev.row == r))[0]
+        assert idx.size, (sector, r)
+        out.append(idx[0])
+    return np.array(out, np.uint32)
+
+
+def _spd(rng, scale):
+    A = rng.normal(size=(5, 5))
+    return (A @ A.T + np.eye(5)) * scale
+
+
+def _packed(C):
+    return np.array([C[i, j] for i in range(5) for j in range(i + 1)])
+
+
+def test_merge_chi2_is_the_quadratic_form_and_rules(geo, params):
+    """Constructed segments with known states: the link chi2 equals
+    d^T (C_i' + C_j)^-1 d with C_i' the rotated and transported covariance
+    (numpy solve); only segments on the same side, in the same or a
+    neighbouring sector frame and starting beyond the predecessor's last
+    row are compared; of two predecessors of one segment the one with the
+    smaller chi2 is linked."""
+    ev = synth.make_tiny(seed=43, n_tracks=300, sectors=(3, 4, 5, 22), noise_frac=0.9)
+    o = _oracle(ev, geo, params)
+    rng = np.random.default_rng(5)
+    rx = geo.row_x.astype(np.float64)
+    p0 = np.array([3.0, 20.0, 0.15, 0.3, 0.8])
+    C_a = _spd(rng, 1e-5)
+    C_b = _spd(rng, 1e-5)
+    # B: the exact continuation of p0 in the frame of sector 4 at row 70
+    p1, x1, _ = o.rotate(p0, rx[40], math.pi / 9)
+    p_b, _ = o.propagate(p1, x1, rx[70])
+    p_b40, _ = o.propagate(p1, x1, rx[40])
+    q5, x5, _ = o.rotate(p0, rx[40], 2 * math.pi / 9)
+    p_b5, _ = o.propagate(q5, x5, rx[70])
+
+    def chi2_of(p):
+        q1, y1, C1 = o.rotate(p, rx[40], math.pi / 9, C_a)
+        q2, C2 = o.propagate(q1, y1, rx[70], C1)
+        d = q2 - p_b
+        return d @ np.linalg.solve(C2 + C_b, d)
+
+    u = np.array([0.002, -0.003, 1e-4, 2e-4, 0.001])
+    p_a = p0 + u * math.sqrt(2.0 / chi2_of(p0 + u))     # chi2 about 2
+    p_a2 = p0 + u * math.sqrt(8.0 / chi2_of(p0 + u))    # chi2 about 8
+    want = chi2_of(p_a)
+    segs = [  # sector, rows, state, covariance, x of the state
+        (3, range(10, 41), p_a, C_a, rx[40]),           # 0: A
+        (4, range(70, 100), p_b, C_b, rx[70]),          # 1: B, continuation of A
+        (4, range(40, 75), p_b40, C_b, rx[40]),         # 2: starts on A's last row
+        (5, range(70, 100), p_b5, C_b, rx[70]),         # 3: two frames away
+        (22, range(70, 100), p_b, C_b, rx[70]),         # 4: other side
+        (3, range(11, 41), p_a2, C_a, rx[40]),          # 5: A', a worse predecessor of B
+    ]
+
+    def run(sel):
+        cs = [_pick_clusters(ev, segs[k][0], segs[k][1]) for k in sel]
+        ts = np.concatenate([[0], np.cumsum([c.size for c in cs])]).astype(np.uint32)
+        return o.merge(ts, np.concatenate(cs), np.zeros(len(sel)),
+                       np.array([segs[k][2] for k in sel]),
+                       np.array([_packed(segs[k][3]) for k in sel]),
+                       np.array([segs[k][4] for k in sel]), np.zeros(len(sel), np.int32),
+                       prec=64)
+
+    m = run(range(6))
+    assert list(m["next"]) == [1, -1, -1, -1, -1, -1]
+    assert abs(m["link_chi2"][0] - want) < 1e-9 * want, (m["link_chi2"][0], want)
+    # A' alone is linked to B, with a larger chi2
+    m = run([5, 1])
+    assert m["next"][0] == 1 and want < m["link_chi2"][0] <= params["chi2_merge"]
+    # segments 2, 3, 4 carry exact continuations of A's helix but are never
+    # compared with A
+    for k in (2, 3, 4):
+        assert list(run([0, k])["next"]) == [-1, -1], k
+    # a predecessor farther off is not linked
+    segs[0] = (3, range(10, 41), p0 + u * math.sqrt(40.0 / chi2_of(p0 + u)), C_a, rx[40])
+    assert run([0, 1])["next"][0] == -1
+
+
+def test_merge_expresses_z_with_the_predecessors_time(geo, params):
+    """Time-frame mode: segment j's z was obtained with its own collision
+    time; the clusters' calibration with i's time shifts it by a constant,
+    which the merge takes into account (chi2 about 0 for an exact
+    continuation whose z is given in j's time)."""
+    ev = synth.make_tiny(seed=44, n_tracks=200, sectors=(3, 4), noise_frac=0.9, mode="time",
+                         tf_start=1.0e6, n_coll=2)
+    o = _oracle(ev, geo, params)
+    rng = np.random.default_rng(6)
+    rx = geo.row_x.astype(np.float64)
+    c_a = _pick_clusters(ev, 3, range(10, 41))
+    c_b = _pick_clusters(ev, 4, range(70, 100))
+    th_a, th_b = 1.0e6 + 12.0, 1.0e6 + 31.0
+    # the z offset between the two time bases, from the calibration itself
+    za, _ = o.calibrate(c_b[:1], th_a)[1], None
+    zb = o.calibrate(c_b[:1], th_b)[1]
+    dz = float(za[0] - zb[0])
+    assert abs(dz) > 10.0
+    p_a = np.array([3.0, 20.0, 0.15, 0.3, 0.8])
+    C_a = _spd(rng, 1e-3)
+    p1, x1, C1 = o.rotate(p_a, rx[40], math.pi / 9, C_a)
+    p_b, _ = o.propagate(p1, x1, rx[70], C1)
+    p_b = p_b - np.array([0.0, dz, 0.0, 0.0, 0.0])   # B's z in its own time base
+    ts = np.array([0, c_a.size, c_a.size + c_b.size], np.uint32)
+    m = o.merge(ts, np.concatenate([c_a, c_b]), np.array([th_a, th_b]), np.array([p_a, p_b]),
+                np.array([_packed(C_a), _packed(_spd(rng, 1e-3))]), np.array([rx[40], rx[70]]),
+                np.zeros(2, np.int32), prec=64)
+    assert m["next"][0] == 1 and m["link_chi2"][0] < 1e-8, m["link_chi2"]
