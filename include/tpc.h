@@ -98,6 +98,7 @@ typedef struct {
   int32_t min_acc_reject; /* accepted clusters before rejection starts     */
   float refit_inflate;    /* covariance inflation between refit passes     */
   int32_t seed_max_hits;  /* chain hits used by the tracklet seed fit      */
+  float chi2_merge;       /* segment-merging cut on the 5-parameter chi2   */
 } tpc_params;
 
 /* Calibration (Sec. 4 and Sec. 5.2): drift velocity, time offset and a
@@ -213,6 +214,29 @@ tpc_status tpc_set_tracks(tpc_ctx* ctx, const tpc_tracks* tracks);
  * kept for tpc_refit_backward. */
 tpc_status tpc_refit(tpc_ctx* ctx, int save_for_backward, float* params, float* cov, float* x,
                      float* chi2, int32_t* ndf, int32_t* status, uint8_t* rej);
+
+/* Merge the context's track set, taken as sector segments (from
+ * tpc_find_tracks, or given by tpc_set_tracks), into tracks across sectors
+ * (Sec. 2, second phase: the segments found in the individual sectors are
+ * merged before the final fit). params [n][5], cov [n][15], x [n], status
+ * [n]: the segments' states from tpc_refit of this track set (device,
+ * caller-owned). Segment j continues segment i when both refits converged,
+ * they lie in the same event and on the same side, j's sector is i's or a
+ * neighbour in azimuth, j starts on a pad row beyond i's last one, and the
+ * chi2 of their states (i's rotated into j's frame and transported to j's
+ * x; in mode 1 j's z expressed with i's collision time; covariances added)
+ * is at most params.chi2_merge with each the other's best match (smallest
+ * chi2, then smallest index). Pairs whose tan(lambda) or q/pT differ by
+ * more than sqrt(2 chi2_merge) standard deviations are not compared.
+ * Replaces the track set by the chains of linked segments, ordered by their
+ * first segment, whose collision time and start hit they take; clusters in
+ * chain order. next [n] (device, may be NULL) receives each segment's
+ * continuation or -1, link_chi2 [n] (may be NULL) its chi2 (0 when
+ * unlinked). *out (may be NULL): the merged set (library-owned, as for
+ * tpc_find_tracks). Synchronises. */
+tpc_status tpc_merge_tracks(tpc_ctx* ctx, const float* params, const float* cov, const float* x,
+                            const int32_t* status, int32_t* next, float* link_chi2,
+                            tpc_tracks* out);
 
 /* Adjoint of the last saved refit (not in the paper; TPC_ERR_STATE if the
  * calibration was set again after that refit): for

@@ -43,7 +43,7 @@ class tpc_params(C.Structure):
                 ("inward_cov_scale", C.c_float), ("c0t", C.c_float * 5),
                 ("c0r", C.c_float * 5), ("chi2_out", C.c_float),
                 ("min_acc_reject", C.c_int32), ("refit_inflate", C.c_float),
-                ("seed_max_hits", C.c_int32)]
+                ("seed_max_hits", C.c_int32), ("chi2_merge", C.c_float)]
 
 
 class tpc_calib(C.Structure):
@@ -92,6 +92,7 @@ _PROTOS = {
     "tpc_set_tracks": (C.c_int, [C.c_void_p, C.POINTER(tpc_tracks)]),
     "tpc_refit": (C.c_int, [C.c_void_p, C.c_int] + [C.c_void_p] * 7),
     "tpc_refit_backward": (C.c_int, [C.c_void_p] + [C.c_void_p] * 4),
+    "tpc_merge_tracks": (C.c_int, [C.c_void_p] + [C.c_void_p] * 6 + [C.POINTER(tpc_tracks)]),
     "tpc_sync": (C.c_int, [C.c_void_p]),
     "tpc_get_counts": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
                                  C.POINTER(C.c_int64)]),
@@ -329,6 +330,27 @@ class Tracker:
         self._ck(self.L.tpc_refit_backward(self.h, _ptr(g), _ptr(gy), _ptr(gz), _ptr(gc)),
                  "tpc_refit_backward")
         return gy[:na], gz[:na], gc
+
+    # ----------------------------------------------------------- merging
+    def merge(self, seg):
+        """Merge the current track set (sector segments) using their refit
+        outputs seg (params, cov, x, status as returned by refit); the merged
+        tracks become the track set. Returns next (continuation of each
+        segment or -1) and link_chi2 as tensors."""
+        torch = self.torch
+        nt = int(seg["status"].numel())
+        nx = torch.empty(max(nt, 1), dtype=torch.int32, device=self.dev)
+        lc = torch.empty(max(nt, 1), dtype=torch.float32, device=self.dev)
+        c = lambda k, dt: seg[k].to(self.dev, dt).contiguous()
+        ins = (c("params", torch.float32), c("cov", torch.float32), c("x", torch.float32),
+               c("status", torch.int32))
+        t = tpc_tracks()
+        self._ck(self.L.tpc_merge_tracks(self.h, *[_ptr(a) for a in ins], _ptr(nx), _ptr(lc),
+                                         C.byref(t)), "tpc_merge_tracks")
+        self.n_tracks, self.n_assigned = int(t.n_tracks), int(t.n_assigned)
+        self._merged_view = self._tracks_view(t)
+        self.cluster_idx = self._merged_view["cluster_idx"]
+        return dict(next=nx[:nt], link_chi2=lc[:nt], tracks=self._merged_view)
 
     def sync(self):
         self._ck(self.L.tpc_sync(self.h), "tpc_sync")

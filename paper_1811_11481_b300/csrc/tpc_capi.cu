@@ -33,6 +33,7 @@ struct tpc_ctx {
   FindBuf fb{};
   TrackBuf tb{};
   RefitBuf rb{};
+  MergeBuf mb{};
   Prof prof;
   // capacities
   int64_t cap_n = 0, cap_K = 0, cap_bins = 0, cap_blk = 0, cap_ev = 0;
@@ -113,6 +114,7 @@ void copy_params(const tpc_params& s, Params& d) {
   d.min_acc_reject = s.min_acc_reject;
   d.refit_inflate = s.refit_inflate;
   d.seed_max_hits = s.seed_max_hits;
+  d.chi2_merge = s.chi2_merge;
 }
 
 std::string err_text(uint32_t e) {
@@ -265,6 +267,7 @@ void tpc_default_params(tpc_params* p) {
   p->min_acc_reject = 5;
   p->refit_inflate = 100.0f;
   p->seed_max_hits = 10;
+  p->chi2_merge = 30.0f;
 }
 
 tpc_status tpc_create(const tpc_geometry* geo, const tpc_params* params, void* stream,
@@ -355,7 +358,11 @@ void tpc_destroy(tpc_ctx* ctx) {
                   ctx->tb.asg_track, ctx->tb.t_coll, ctx->tb.start_hit, ctx->tb.yc, ctx->tb.zc,
                   ctx->tb.meta, ctx->rb.seed, ctx->rb.order, ctx->rb.slot, ctx->rb.wlen, ctx->rb.wbase, ctx->rb.len_hist,
                   ctx->rb.w_yc, ctx->rb.w_zc, ctx->rb.w_meta, ctx->rb.rej, ctx->rb.status, ctx->rb.ckpt,
-                  ctx->rb.gyc, ctx->rb.gzc, ctx->rb.acc_spline, ctx->rb.gmax, ctx->rb.part_cal};
+                  ctx->rb.gyc, ctx->rb.gzc, ctx->rb.acc_spline, ctx->rb.gmax, ctx->rb.part_cal,
+                  ctx->mb.seg_ts, ctx->mb.seg_ci, ctx->mb.seg_that, ctx->mb.seg_hit,
+                  ctx->mb.info, ctx->mb.rows, ctx->mb.bk_cnt, ctx->mb.bk_fill, ctx->mb.bk_seg,
+                  ctx->mb.best_in, ctx->mb.best_out, ctx->mb.next, ctx->mb.has_in,
+                  ctx->mb.hpos, ctx->mb.cpos, ctx->mb.blk_h, ctx->mb.blk_c};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
@@ -573,6 +580,92 @@ tpc_status tpc_refit(tpc_ctx* ctx, int save_for_backward, float* params, float* 
   CK(cudaGetLastError());
   ctx->saved = save_for_backward != 0;
   ctx->refit_calib_version = ctx->calib_version;
+  return TPC_OK;
+}
+
+namespace {
+tpc_status ensure_merge_buffers(tpc_ctx* ctx, int64_t n_tr, int64_t n_asg) {
+  MergeBuf& m = ctx->mb;
+  int64_t nb = (int64_t)ctx->cl.n_events * TPC_N_SECTORS;
+  if (n_tr > m.cap_tr) {
+    int64_t c = n_tr + n_tr / 4 + 1024;
+    CK(alloc(m.seg_ts, c + 1));
+    CK(alloc(m.seg_that, c));
+    CK(alloc(m.seg_hit, c));
+    CK(alloc(m.info, c));
+    CK(alloc(m.rows, c));
+    CK(alloc(m.bk_seg, c));
+    CK(alloc(m.best_in, c));
+    CK(alloc(m.best_out, c));
+    CK(alloc(m.next, c));
+    CK(alloc(m.has_in, c));
+    CK(alloc(m.hpos, c));
+    CK(alloc(m.cpos, c));
+    CK(alloc(m.blk_h, c / 1024 + 2));
+    CK(alloc(m.blk_c, c / 1024 + 2));
+    m.cap_tr = c;
+  }
+  if (n_asg > m.cap_asg) {
+    int64_t c = n_asg + n_asg / 4 + 1024;
+    CK(alloc(m.seg_ci, c));
+    m.cap_asg = c;
+  }
+  if (nb > m.cap_bk) {
+    CK(alloc(m.bk_cnt, nb + 1));
+    CK(alloc(m.bk_fill, nb));
+    m.cap_bk = nb;
+  }
+  return TPC_OK;
+}
+}  // namespace
+
+tpc_status tpc_merge_tracks(tpc_ctx* ctx, const float* params, const float* cov, const float* x,
+                            const int32_t* status, int32_t* next, float* link_chi2,
+                            tpc_tracks* out) {
+  if (!ctx) return TPC_ERR_ARG;
+  if (ctx->capturing) return fail(ctx, TPC_ERR_STATE, "tpc_merge_tracks synchronises");
+  if (!ctx->tracks_valid) return fail(ctx, TPC_ERR_STATE, "no track set");
+  tpc_status st = read_back(ctx);  // segment and cluster counts
+  if (st != TPC_OK) return st;
+  int64_t nt = ctx->h_pinned[kCntTracks], na = ctx->h_pinned[kCntAssigned];
+  if (nt > 0 && (!params || !cov || !x || !status))
+    return fail(ctx, TPC_ERR_ARG, "null segment state");
+  st = ensure_merge_buffers(ctx, nt, na);
+  if (st != TPC_OK) return st;
+  MergeBuf& m = ctx->mb;
+  TrackBuf& t = ctx->tb;
+  if (nt > 0) {
+    CK(cudaMemcpyAsync(m.seg_ts, t.track_start, sizeof(uint32_t) * (nt + 1),
+                       cudaMemcpyDeviceToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(m.seg_that, t.t_coll, sizeof(double) * nt, cudaMemcpyDeviceToDevice,
+                       ctx->stream));
+    CK(cudaMemcpyAsync(m.seg_hit, t.start_hit, sizeof(uint32_t) * nt, cudaMemcpyDeviceToDevice,
+                       ctx->stream));
+    if (na > 0)
+      CK(cudaMemcpyAsync(m.seg_ci, t.cluster_idx, sizeof(uint32_t) * na,
+                         cudaMemcpyDeviceToDevice, ctx->stream));
+    launch_merge(&ctx->prof, ctx->geo, ctx->prm, ctx->cal, ctx->cl, nt, t, m, params, cov, x,
+                 status, link_chi2, ctx->d_cnt, ctx->stream);
+    CK(cudaGetLastError());
+    if (next)
+      CK(cudaMemcpyAsync(next, m.next, sizeof(int32_t) * nt, cudaMemcpyDeviceToDevice,
+                         ctx->stream));
+    // the merged set's calibrated coordinates (Sec. 4)
+    launch_calib(&ctx->prof, ctx->geo, ctx->cal, ctx->cl, t.cap_asg, t, ctx->d_cnt, ctx->d_err,
+                 ctx->stream);
+    CK(cudaGetLastError());
+  }
+  st = read_back(ctx);
+  if (st != TPC_OK) return st;
+  ctx->saved = false;
+  if (out) {
+    out->n_tracks = ctx->h_pinned[kCntTracks];
+    out->n_assigned = ctx->h_pinned[kCntAssigned];
+    out->track_start = t.track_start;
+    out->cluster_idx = t.cluster_idx;
+    out->t_coll = t.t_coll;
+    out->start_hit = t.start_hit;
+  }
   return TPC_OK;
 }
 

@@ -40,6 +40,7 @@ struct Params {
   int32_t min_acc_reject;
   float refit_inflate;
   int32_t seed_max_hits;
+  float chi2_merge;
 };
 
 // Search-grid parameters of a batch. The bin geometry itself (ny x nz bins
@@ -157,6 +158,29 @@ struct RefitBuf {
   int64_t cap_ckpt;
 };
 
+// Segment merging (tpc_merge.cu): a copy of the segments being merged and
+// the link search state (device).
+struct MergeBuf {
+  uint32_t* seg_ts;     // [cap_tr + 1] segment CSR
+  uint32_t* seg_ci;     // [cap_asg]
+  double* seg_that;     // [cap_tr]
+  uint32_t* seg_hit;    // [cap_tr]
+  uint32_t* info;       // [cap_tr] bucket (event * 36 + sector) | 1 << 31 when taking part
+  uint32_t* rows;       // [cap_tr] first row | last row << 16
+  uint32_t* bk_cnt;     // [cap_bk + 1] bucket counts, then offsets
+  uint32_t* bk_fill;    // [cap_bk]
+  uint32_t* bk_seg;     // [cap_tr] segments by bucket
+  unsigned long long* best_in;   // [cap_tr] chi2 bits << 32 | best predecessor
+  unsigned long long* best_out;  // [cap_tr] chi2 bits << 32 | best continuation
+  int32_t* next;        // [cap_tr] linked continuation or -1
+  uint8_t* has_in;      // [cap_tr] has a linked predecessor
+  uint32_t* hpos;       // [cap_tr] block-local merged-track index of a first segment
+  uint32_t* cpos;       // [cap_tr] block-local cluster offset
+  uint32_t* blk_h;      // [cap_tr / 1024 + 2] block totals, then offsets
+  uint32_t* blk_c;      // [cap_tr / 1024 + 2]
+  int64_t cap_tr, cap_asg, cap_bk;
+};
+
 // Per-context kernel accounting: every launch is counted; with timing on, a
 // pair of CUDA events on the launch stream brackets each kernel.
 struct Prof {
@@ -265,5 +289,14 @@ void launch_refit_backward(Prof* P, const Geo& g, const Cal& c, const Params& p,
                            int64_t cap_tr, int64_t cap_asg, const uint32_t* cnt,
                            const TrackBuf& tb, RefitBuf& rb, const float* dl_dchi2,
                            float* grad_y, float* grad_zt, double* grad_calib, cudaStream_t s);
+
+// launcher (tpc_merge.cu): merges the n segments copied into mb (refitted
+// states params, cov, x, status) and writes the merged set into tb and its
+// count into cnt[kCntTracks]; link_chi2 (may be null) receives each
+// segment's link chi2.
+void launch_merge(Prof* P, const Geo& g, const Params& p, const Cal& c, const ClIn& cl,
+                  int64_t n, TrackBuf& tb, MergeBuf& mb, const float* params, const float* cov,
+                  const float* x, const int32_t* status, float* link_chi2, uint32_t* cnt,
+                  cudaStream_t s);
 
 }  // namespace tpc

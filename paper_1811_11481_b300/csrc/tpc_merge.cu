@@ -1,0 +1,376 @@
+// Segment merging (arXiv:1811.11481 Sec. 2, second phase: the track segments
+// found in the individual sectors are merged before the final fit).
+//
+// A segment is described by its refitted state at its innermost cluster (in
+// its sector's frame), its pad-row range and its collision time. Segment j
+// may continue segment i when both converged, lie in the same event and on
+// the same side, j's sector frame is i's or a neighbour of it, and j starts
+// on a pad row beyond i's last one. i's state is rotated into j's frame and
+// transported to j's innermost x; in the time-frame mode j's z is expressed
+// with i's collision time; the pair's chi2 is d^T (C_i' + C_j)^-1 d over the
+// five parameters (Cholesky). Pairs whose tan(lambda) or q/pT differ by more
+// than sqrt(2 chi2_merge) standard deviations of the difference are not
+// compared. i -> j is a link when chi2 <= chi2_merge, j is i's best
+// continuation and i is j's best predecessor (smallest chi2, then smallest
+// index). Merged tracks are the chains of links from segments without
+// predecessor, in the order of their first segment, which gives them its
+// collision time and start hit.
+//
+// k_mg_info    one thread per segment: bucket (event, sector), row range,
+//              participation; bucket histogram.
+// k_mg_bucket  one block: bucket offsets.
+// k_mg_scatter one thread per segment: segment lists per bucket.
+// k_mg_best    one thread per segment: chi2 against every segment of the
+//              three candidate buckets; its best continuation, and a 64-bit
+//              atomic minimum (chi2 bits, own index) on each candidate's best
+//              predecessor.
+// k_mg_link    mutual best -> link.
+// k_mg_len     chain length of each first segment, block-local scans.
+// k_mg_top     one block: block offsets, track and cluster totals.
+// k_mg_write   one warp per first segment: the merged track's clusters.
+//
+// Compiled with -fmad=false and IEEE division and square root: the chi2 that
+// decides a link is computed with one rounding per written operation.
+#include "tpc_impl.h"
+#include "tpc_refit_core.cuh"
+
+namespace tpc {
+namespace {
+
+constexpr int kMB = 256;    // threads per block of the per-segment kernels
+constexpr int kScanB = 1024;  // threads per block of the scans
+inline int nblk(int64_t n, int b) { return (int)((n + b - 1) / b); }
+
+struct SegIn {
+  const uint32_t* ts;     // segment CSR (copy of the track set)
+  const uint32_t* ci;
+  const double* that;
+  const float* params;    // [n][5] refitted state at the innermost cluster
+  const float* cov;       // [n][15] packed lower triangle
+  const float* x;         // [n]
+  const int32_t* status;  // [n]
+};
+
+constexpr uint32_t kTakesPart = 0x80000000u;
+
+__global__ void k_mg_info(int n, ClIn cl, SegIn s, uint32_t* info, uint32_t* rows,
+                          uint32_t* bk_cnt, unsigned long long* best_in, uint8_t* has_in) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  best_in[i] = ~0ull;
+  has_in[i] = 0;
+  uint32_t a = s.ts[i], b = s.ts[i + 1];
+  uint32_t w = 0u, r = 0u;
+  if (b > a) {
+    uint32_t f = s.ci[a], l = s.ci[b - 1];
+    uint32_t ev = cl.event ? cl.event[f] : 0u;
+    uint32_t bk = ev * TPC_N_SECTORS + cl.sector[f];
+    // clusters with an invalid event or sector (reported at load) stay out
+    bool ok = s.status[i] == 0 && ev < (uint32_t)cl.n_events && cl.sector[f] < TPC_N_SECTORS;
+    w = ok ? (bk | kTakesPart) : 0u;
+    r = (uint32_t)cl.row[f] | ((uint32_t)cl.row[l] << 16);
+    if (ok) atomicAdd(&bk_cnt[bk], 1u);
+  }
+  info[i] = w;
+  rows[i] = r;
+}
+
+// Exclusive scan of v over a block of kScanB threads; returns the prefix and
+// writes the block total to *total.
+__device__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* total) {
+  __shared__ uint32_t ws[kScanB / 32];
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  uint32_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) ws[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    uint32_t t = lane < kScanB / 32 ? ws[lane] : 0u;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t y = __shfl_up_sync(0xffffffffu, t, o);
+      if (lane >= o) t += y;
+    }
+    if (lane < kScanB / 32) ws[lane] = t;
+  }
+  __syncthreads();
+  uint32_t incl = x + (w > 0 ? ws[w - 1] : 0u);
+  *total = ws[kScanB / 32 - 1];
+  __syncthreads();
+  return incl - v;
+}
+
+// Exclusive scan of a[0..m) in place by one block, a[m] = total.
+__device__ void block_scan_inplace(uint32_t* a, int m) {
+  __shared__ uint32_t carry;
+  if (threadIdx.x == 0) carry = 0u;
+  __syncthreads();
+  for (int base = 0; base < m; base += kScanB) {
+    int i = base + (int)threadIdx.x;
+    uint32_t v = i < m ? a[i] : 0u;
+    uint32_t tot;
+    uint32_t ex = block_exclusive_scan(v, &tot);
+    uint32_t c = carry;
+    if (i < m) a[i] = c + ex;
+    __syncthreads();
+    if (threadIdx.x == 0) carry = c + tot;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) a[m] = carry;
+}
+
+__global__ void __launch_bounds__(kScanB) k_mg_bucket(int nb, uint32_t* bk_cnt, uint32_t* bk_fill) {
+  block_scan_inplace(bk_cnt, nb);  // counts -> offsets
+  for (int i = threadIdx.x; i < nb; i += kScanB) bk_fill[i] = 0u;
+}
+
+__global__ void k_mg_scatter(int n, const uint32_t* info, const uint32_t* bk_start,
+                             uint32_t* bk_fill, uint32_t* bk_seg) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  uint32_t w = info[i];
+  if (!(w & kTakesPart)) return;
+  uint32_t bk = w & ~kTakesPart;
+  bk_seg[bk_start[bk] + atomicAdd(&bk_fill[bk], 1u)] = (uint32_t)i;
+}
+
+struct MergeCfg {
+  RefitCfg rc;   // kB, s_max and the frame rotations
+  float cut;     // chi2_merge
+  int mode;      // 1: time frame
+  double vdrift;
+};
+
+// chi2 of "j continues i"; false when the pair is not compared or fails.
+__device__ bool pair_chi2(const MergeCfg& m, int side, const float pi[5], const float Ci[15],
+                          float xi, double thi, int fi, const float* pj, const float* Cj,
+                          float xj, double thj, int fj, float& chi2) {
+#pragma unroll
+  for (int k = 3; k <= 4; ++k) {
+    int d = sidx(k, k);
+    float dd = pi[k] - pj[k];
+    if (dd * dd > (2.0f * m.cut) * (Ci[d] + Cj[d])) return false;
+  }
+  float p[5], C[15];
+#pragma unroll
+  for (int k = 0; k < 5; ++k) p[k] = pi[k];
+#pragma unroll
+  for (int k = 0; k < 15; ++k) C[k] = Ci[k];
+  float x = xi;
+  if (fj != fi) {
+    int r = frame_step(fi, fj);
+    if (!rotate_frame(m.rc.kB, m.rc.s_max, m.rc.rot_c[r], m.rc.rot_s[r], p, C, x)) return false;
+  }
+  if (!propagate(m.rc.kB, m.rc.s_max, p, C, x, xj)) return false;
+  float shift = 0.0f;
+  if (m.mode == 1) {
+    double sg = side == 0 ? 1.0 : -1.0;
+    shift = (float)(sg * m.vdrift * (thi - thj));
+  }
+  float d[5];
+#pragma unroll
+  for (int k = 0; k < 5; ++k) d[k] = p[k] - pj[k];
+  d[1] = p[1] - (pj[1] + shift);
+  float L[5][5];
+#pragma unroll
+  for (int a = 0; a < 5; ++a)
+#pragma unroll
+    for (int b = 0; b <= a; ++b) {
+      float acc = C[sidx(a, b)] + Cj[sidx(a, b)];
+#pragma unroll
+      for (int k = 0; k < b; ++k) acc = acc - L[a][k] * L[b][k];
+      if (a == b) {
+        if (!(acc > 0.0f)) return false;
+        L[a][a] = sqrtf(acc);
+      } else {
+        L[a][b] = acc / L[b][b];
+      }
+    }
+  float w[5];
+#pragma unroll
+  for (int a = 0; a < 5; ++a) {
+    float acc = d[a];
+#pragma unroll
+    for (int k = 0; k < a; ++k) acc = acc - L[a][k] * w[k];
+    w[a] = acc / L[a][a];
+  }
+  float ch = 0.0f;
+#pragma unroll
+  for (int a = 0; a < 5; ++a) ch = ch + w[a] * w[a];
+  chi2 = ch;
+  return ch <= m.cut;
+}
+
+__global__ void k_mg_best(int n, MergeCfg m, SegIn s, const uint32_t* info, const uint32_t* rows,
+                          const uint32_t* bk_start, const uint32_t* bk_seg,
+                          unsigned long long* best_in, unsigned long long* best_out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  uint32_t wi = info[i];
+  unsigned long long best = ~0ull;
+  if (wi & kTakesPart) {
+    uint32_t bk = wi & ~kTakesPart;
+    int sec = (int)(bk % TPC_N_SECTORS);
+    uint32_t ev0 = bk - (uint32_t)sec;
+    int side = sec / 18, fi = sec % 18;
+    int rhi = (int)(rows[i] >> 16);
+    float pi[5], Ci[15];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) pi[k] = s.params[(size_t)i * 5 + k];
+#pragma unroll
+    for (int k = 0; k < 15; ++k) Ci[k] = s.cov[(size_t)i * 15 + k];
+    float xi = s.x[i];
+    double thi = s.that[i];
+    for (int df = 0; df < 3; ++df) {
+      int fj = df == 0 ? fi : (df == 1 ? (fi + 1) % 18 : (fi + 17) % 18);
+      uint32_t bj = ev0 + (uint32_t)(side * 18 + fj);
+      uint32_t q1 = bk_start[bj + 1];
+      for (uint32_t q = bk_start[bj]; q < q1; ++q) {
+        uint32_t j = bk_seg[q];
+        if ((int)j == i || !((int)(rows[j] & 0xffffu) > rhi)) continue;
+        float chi2;
+        if (!pair_chi2(m, side, pi, Ci, xi, thi, fi, s.params + (size_t)j * 5,
+                       s.cov + (size_t)j * 15, s.x[j], s.that[j], fj, chi2))
+          continue;
+        unsigned long long cb = (unsigned long long)__float_as_uint(chi2) << 32;
+        if ((cb | j) < best) best = cb | j;
+        atomicMin(&best_in[j], cb | (uint32_t)i);
+      }
+    }
+  }
+  best_out[i] = best;
+}
+
+__global__ void k_mg_link(int n, const unsigned long long* best_in,
+                          const unsigned long long* best_out, int32_t* next, float* link_chi2,
+                          uint8_t* has_in) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  unsigned long long b = best_out[i];
+  int32_t nx = -1;
+  float c = 0.0f;
+  if (b != ~0ull) {
+    uint32_t j = (uint32_t)b;
+    if ((uint32_t)best_in[j] == (uint32_t)i) {
+      nx = (int32_t)j;
+      c = __uint_as_float((uint32_t)(b >> 32));
+      has_in[j] = 1;
+    }
+  }
+  next[i] = nx;
+  if (link_chi2) link_chi2[i] = c;
+}
+
+// Chains are acyclic and at most one segment per pad row long: along a link
+// the first row strictly increases.
+__global__ void __launch_bounds__(kScanB) k_mg_len(int n, const uint32_t* ts,
+                                                   const int32_t* next, const uint8_t* has_in,
+                                                   uint32_t* hpos, uint32_t* cpos,
+                                                   uint32_t* blk_h, uint32_t* blk_c) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  uint32_t h = 0u, len = 0u;
+  if (i < n && !has_in[i]) {
+    h = 1u;
+    int s = i;
+    for (int k = 0; s >= 0 && k <= TPC_MAX_ROWS; ++k) {
+      len += ts[s + 1] - ts[s];
+      s = next[s];
+    }
+  }
+  uint32_t th, tc;
+  uint32_t eh = block_exclusive_scan(h, &th);
+  uint32_t ec = block_exclusive_scan(len, &tc);
+  if (i < n) {
+    hpos[i] = eh;
+    cpos[i] = ec;
+  }
+  if (threadIdx.x == 0) {
+    blk_h[blockIdx.x] = th;
+    blk_c[blockIdx.x] = tc;
+  }
+}
+
+__global__ void __launch_bounds__(kScanB) k_mg_top(int nb, uint32_t* blk_h, uint32_t* blk_c,
+                                                   uint32_t* cnt, uint32_t* track_start) {
+  block_scan_inplace(blk_h, nb);
+  block_scan_inplace(blk_c, nb);
+  if (threadIdx.x == 0) {
+    cnt[kCntTracks] = blk_h[nb];
+    track_start[blk_h[nb]] = blk_c[nb];
+  }
+}
+
+__global__ void k_mg_write(int n, SegIn s, const uint32_t* seg_hit, const int32_t* next,
+                           const uint8_t* has_in, const uint32_t* hpos, const uint32_t* cpos,
+                           const uint32_t* blk_h, const uint32_t* blk_c, TrackBuf tb) {
+  int i = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+  int lane = threadIdx.x & 31;
+  if (i >= n || has_in[i]) return;
+  int blk = i / kScanB;
+  uint32_t t = blk_h[blk] + hpos[i];
+  uint32_t o = blk_c[blk] + cpos[i];
+  if (lane == 0) {
+    tb.track_start[t] = o;
+    tb.t_coll[t] = s.that[i];
+    tb.start_hit[t] = seg_hit[i];
+  }
+  int sg = i;
+  for (int k = 0; sg >= 0 && k <= TPC_MAX_ROWS; ++k) {
+    uint32_t a = s.ts[sg], len = s.ts[sg + 1] - a;
+    for (uint32_t q = lane; q < len; q += 32) {
+      tb.cluster_idx[o + q] = s.ci[a + q];
+      tb.asg_track[o + q] = t;
+    }
+    o += len;
+    sg = next[sg];
+  }
+}
+
+}  // namespace
+
+void launch_merge(Prof* P, const Geo& g, const Params& p, const Cal& c, const ClIn& cl,
+                  int64_t n, TrackBuf& tb, MergeBuf& mb, const float* params, const float* cov,
+                  const float* x, const int32_t* status, float* link_chi2, uint32_t* cnt,
+                  cudaStream_t s) {
+  if (n <= 0) return;
+  int nb = cl.n_events * TPC_N_SECTORS;
+  SegIn si{mb.seg_ts, mb.seg_ci, mb.seg_that, params, cov, x, status};
+  MergeCfg m;
+  m.rc = RefitCfg{};
+  m.rc.kB = g.kB;
+  m.rc.s_max = p.s_max;
+  set_frame_rotations(m.rc);
+  m.cut = p.chi2_merge;
+  m.mode = cl.mode;
+  m.vdrift = c.vdrift;
+  cudaMemsetAsync(mb.bk_cnt, 0, sizeof(uint32_t) * (nb + 1), s);
+  TPC_LAUNCH(P, "k_mg_info", s,
+             k_mg_info<<<nblk(n, kMB), kMB, 0, s>>>((int)n, cl, si, mb.info, mb.rows, mb.bk_cnt,
+                                                    mb.best_in, mb.has_in));
+  TPC_LAUNCH(P, "k_mg_bucket", s, k_mg_bucket<<<1, kScanB, 0, s>>>(nb, mb.bk_cnt, mb.bk_fill));
+  TPC_LAUNCH(P, "k_mg_scatter", s,
+             k_mg_scatter<<<nblk(n, kMB), kMB, 0, s>>>((int)n, mb.info, mb.bk_cnt, mb.bk_fill,
+                                                       mb.bk_seg));
+  TPC_LAUNCH(P, "k_mg_best", s,
+             k_mg_best<<<nblk(n, kMB), kMB, 0, s>>>((int)n, m, si, mb.info, mb.rows, mb.bk_cnt,
+                                                    mb.bk_seg, mb.best_in, mb.best_out));
+  TPC_LAUNCH(P, "k_mg_link", s,
+             k_mg_link<<<nblk(n, kMB), kMB, 0, s>>>((int)n, mb.best_in, mb.best_out, mb.next,
+                                                    link_chi2, mb.has_in));
+  int nsb = nblk(n, kScanB);
+  TPC_LAUNCH(P, "k_mg_len", s,
+             k_mg_len<<<nsb, kScanB, 0, s>>>((int)n, mb.seg_ts, mb.next, mb.has_in, mb.hpos,
+                                             mb.cpos, mb.blk_h, mb.blk_c));
+  TPC_LAUNCH(P, "k_mg_top", s,
+             k_mg_top<<<1, kScanB, 0, s>>>(nsb, mb.blk_h, mb.blk_c, cnt, tb.track_start));
+  TPC_LAUNCH(P, "k_mg_write", s,
+             k_mg_write<<<nblk(n * 32, kMB), kMB, 0, s>>>((int)n, si, mb.seg_hit, mb.next,
+                                                          mb.has_in, mb.hpos, mb.cpos, mb.blk_h,
+                                                          mb.blk_c, tb));
+}
+
+}  // namespace tpc

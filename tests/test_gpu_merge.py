@@ -1,0 +1,157 @@
+"""Segment merging (Sec. 2, second phase) on the GPU against the oracle.
+
+On the same segment states (the oracle's FP64 refit rounded to float32) the
+links, their chi2 and the merged track set must equal the oracle's FP32
+merge bit for bit. End to end (GPU finder, GPU refit, GPU merge) the
+decisions are taken on states that agree with the oracle's FP64 refit
+within the refit tolerance: at most 1% of the links may differ; merged
+tracks that both sides form are refitted (across sector frames) within the
+refit tolerance.
+"""
+import numpy as np
+import pytest
+
+import synth
+from pipeline import RTOL, rel_err, tracker
+
+pytestmark = pytest.mark.gpu
+
+
+def _event(mode, seed=41, n_coll=3):
+    return synth.make_tiny(seed=seed, n_tracks=300, central=True, mode=mode, noise_frac=0.1,
+                           tf_start=1.0e6, n_coll=n_coll)
+
+
+def _oracle(ev, geo):
+    import oracle
+    from paper_1811_11481_b300.config import default_params
+    return oracle.Oracle(ev, geo, default_params(), synth.nominal_calib())
+
+
+@pytest.fixture(scope="module")
+def geo():
+    return synth.geometry()
+
+
+@pytest.mark.parametrize("mode", ["event", "time"])
+def test_links_exact_on_the_same_states(geo, mode):
+    import torch
+    ev = _event(mode)
+    o = _oracle(ev, geo)
+    seg = o.find(prec=32)["tracks"]
+    ts, ci, tt = seg["track_start"], seg["cluster_idx"], seg["that"]
+    r = o.refit(ts, ci, tt, prec=64)
+    st = dict(params=r["params"].astype(np.float32), cov=r["cov"].astype(np.float32),
+              x=r["x"].astype(np.float32), status=r["status"].astype(np.int32))
+    want = o.merge(ts, ci, tt, st["params"], st["cov"], st["x"], st["status"], prec=32)
+    tr = tracker(geo)
+    tr.set_calib()
+    tr.load(tr.upload(ev))
+    tr.set_tracks(torch.as_tensor(ts.astype(np.int32)), torch.as_tensor(ci.astype(np.int32)),
+                  torch.as_tensor(tt), torch.as_tensor(seg["start_hit"].astype(np.int32)))
+    got = tr.merge({k: torch.as_tensor(v) for k, v in st.items()})
+    nx = got["next"].cpu().numpy()
+    assert (want["next"] >= 0).sum() > 300
+    np.testing.assert_array_equal(nx, want["next"])
+    np.testing.assert_array_equal(got["link_chi2"].cpu().numpy(),
+                                  want["link_chi2"].astype(np.float32))
+    mt = {k: v.cpu().numpy() for k, v in got["tracks"].items()}
+    np.testing.assert_array_equal(mt["track_start"], want["track_start"].astype(np.int32))
+    np.testing.assert_array_equal(mt["cluster_idx"], want["cluster_idx"].astype(np.int32))
+    np.testing.assert_array_equal(mt["t_coll"], want["that"])
+    np.testing.assert_array_equal(mt["start_hit"], seg["start_hit"][want["head"]])
+    assert tr.n_tracks == want["track_start"].size - 1
+
+
+def test_batched_events_are_not_linked_across_events(geo):
+    """Segments of different events (same sectors, same rows) stay apart."""
+    import torch
+    ev = synth.make_batched(seed=45, n_events=4, lo=150, hi=300)
+    o = _oracle(ev, geo)
+    seg = o.find(prec=32)["tracks"]
+    ts, ci, tt = seg["track_start"], seg["cluster_idx"], seg["that"]
+    r = o.refit(ts, ci, tt, prec=64)
+    st = dict(params=r["params"].astype(np.float32), cov=r["cov"].astype(np.float32),
+              x=r["x"].astype(np.float32), status=r["status"].astype(np.int32))
+    want = o.merge(ts, ci, tt, st["params"], st["cov"], st["x"], st["status"], prec=32)
+    tr = tracker(geo)
+    tr.set_calib()
+    tr.load(tr.upload(ev))
+    tr.set_tracks(torch.as_tensor(ts.astype(np.int32)), torch.as_tensor(ci.astype(np.int32)),
+                  torch.as_tensor(tt))
+    nx = tr.merge({k: torch.as_tensor(v) for k, v in st.items()})["next"].cpu().numpy()
+    np.testing.assert_array_equal(nx, want["next"])
+    ev_of = ev.event[ci[ts[:-1].astype(np.int64)]]
+    lk = np.nonzero(nx >= 0)[0]
+    assert lk.size > 50 and np.all(ev_of[lk] == ev_of[nx[lk]])
+
+
+@pytest.mark.parametrize("mode", ["event", "time"])
+def test_find_refit_merge_refit_end_to_end(geo, mode):
+    """GPU chain against the oracle chain; segments are matched by their
+    start hit (both finders emit the same segments)."""
+    import torch
+    ev = _event(mode, seed=46, n_coll=2)
+    o = _oracle(ev, geo)
+    seg = o.find(prec=32)["tracks"]
+    ts, ci, tt = seg["track_start"], seg["cluster_idx"], seg["that"]
+    r = o.refit(ts, ci, tt, prec=64)
+    want = o.merge(ts, ci, tt, r["params"], r["cov"], r["x"], r["status"], prec=32)
+    tr = tracker(geo)
+    tr.set_calib()
+    tr.load(tr.upload(ev))
+    g = {k: v.cpu().numpy() for k, v in tr.find().items()}
+    rg = tr.refit()
+    got = tr.merge(rg)
+    gnx = got["next"].cpu().numpy()
+    # the same segments, numbered differently
+    o_of = {int(h): k for k, h in enumerate(seg["start_hit"])}
+    perm = np.array([o_of[int(h)] for h in g["start_hit"]])
+    gl = {(perm[i], perm[j]) for i, j in enumerate(gnx) if j >= 0}
+    ol = {(i, int(j)) for i, j in enumerate(want["next"]) if j >= 0}
+    assert len(ol) > 300
+    # link decisions taken on states that differ within the refit tolerance
+    assert len(gl ^ ol) <= 0.01 * len(ol), (len(gl ^ ol), len(ol))
+    # the merged tracks that both sides form: refit within the tolerance
+    rm = tr.refit()
+    mt = {k: v.cpu().numpy() for k, v in got["tracks"].items()}
+    ref = o.refit(want["track_start"], want["cluster_idx"], want["that"], prec=64)
+    key_o = {tuple(want["cluster_idx"][want["track_start"][k]:want["track_start"][k + 1]]): k
+             for k in range(want["track_start"].size - 1)}
+    pg = rm["params"].cpu().numpy()
+    sg = rm["status"].cpu().numpy()
+    n_same = 0
+    errs = []
+    for k in range(mt["track_start"].size - 1):
+        c = tuple(mt["cluster_idx"][mt["track_start"][k]:mt["track_start"][k + 1]].astype(np.uint32))
+        ko = key_o.get(c)
+        if ko is None or sg[k] != 0 or ref["status"][ko] != 0:
+            continue
+        n_same += 1
+        errs.append(rel_err(pg[k].astype(np.float64), ref["params"][ko]))
+    assert n_same > 0.97 * (mt["track_start"].size - 1) * np.mean(ref["status"] == 0)
+    e = np.array(errs)
+    assert np.all(e <= RTOL), e.max(0)
+
+
+def test_merge_of_an_empty_set_and_of_failed_segments(geo):
+    import torch
+    ev = _event("event", seed=47, n_coll=1)
+    tr = tracker(geo)
+    tr.set_calib()
+    tr.load(tr.upload(ev))
+    z = lambda *s: torch.zeros(*s)
+    tr.set_tracks(torch.zeros(1, dtype=torch.int32), torch.zeros(0, dtype=torch.int32),
+                  torch.zeros(0, dtype=torch.float64))
+    out = tr.merge(dict(params=z(0, 5), cov=z(0, 15), x=z(0), status=z(0).int()))
+    assert tr.n_tracks == 0 and out["next"].numel() == 0
+    # every segment failed: nothing is linked, the set is unchanged
+    g = {k: v.cpu().numpy() for k, v in tr.find().items()}
+    n = tr.n_tracks
+    rg = tr.refit()
+    rg["status"][:] = 1
+    out = tr.merge(rg)
+    assert tr.n_tracks == n and np.all(out["next"].cpu().numpy() == -1)
+    mt = {k: v.cpu().numpy() for k, v in out["tracks"].items()}
+    np.testing.assert_array_equal(mt["track_start"], g["track_start"])
+    np.testing.assert_array_equal(mt["cluster_idx"], g["cluster_idx"])
