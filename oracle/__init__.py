@@ -113,6 +113,7 @@ def lib():
         L.orc_merge.restype = C.c_int64
         L.orc_merge.argtypes = [vp, C.c_int, C.c_int64, vp, vp, vp, vp, vp, vp, vp, vp, vp,
                                 vp, vp, vp, vp]
+        L.orc_refine_time.argtypes = [vp, C.c_int, C.c_int64, vp, vp, vp, vp, vp, vp, vp]
         L.orc_rotate.restype = C.c_int
         L.orc_rotate.argtypes = [vp, vp, C.c_double, C.c_double, vp, vp, vp, vp]
         L.orc_dca_z.restype = C.c_double
@@ -338,6 +339,19 @@ class Oracle:
                             _p(nxt), _p(lc), _p(ots), _p(oci), _p(oth), _p(ohd))
         return dict(next=nxt, link_chi2=lc, track_start=ots[:m + 1].copy(),
                     cluster_idx=oci[:ci.size].copy(), that=oth[:m].copy(), head=ohd[:m].copy())
+
+    def refine_time(self, track_start, cluster_idx, that, params, x, status, prec=32):
+        """Collision times refined from the tracks' fits (time-frame mode)."""
+        ts = np.ascontiguousarray(track_start, np.uint32)
+        nt = ts.size - 1
+        out = np.empty(nt)
+        lib().orc_refine_time(self.h, prec, nt, _p(ts),
+                              _p(np.ascontiguousarray(cluster_idx, np.uint32)),
+                              _p(np.ascontiguousarray(that, np.float64)),
+                              _p(np.ascontiguousarray(np.reshape(params, (nt, 5)), np.float64)),
+                              _p(np.ascontiguousarray(x, np.float64)),
+                              _p(np.ascontiguousarray(status, np.int32)), _p(out))
+        return out
 
     # --- single-step helpers
     def propagate(self, state, x1, x2, cov=None):

@@ -1107,6 +1107,38 @@ void merge_links(const Ctx& c, int64_t nt, const uint32_t* ts, const uint32_t* c
   }
 }
 
+// --------------------------------------- collision time after merging
+// Time-frame mode (Sec. 4, the steps after merging): the vertex estimate is
+// refined with the merged track's fit and the track is shifted in z to it;
+// a track with clusters outside the drift volume is shifted back inside.
+// Reading: the collision time moves so that the fitted helix (state p at x,
+// at the innermost cluster) reaches its closest approach to the beam line at
+// z = 0: every cluster's absolute z moves by -z0, i.e. the collision time by
+// -sg z0 / v_drift. Then each cluster's drift time t - t0 - that must lie in
+// [0, L / v_drift]; when the largest exceeds the bound the collision time
+// moves up to meet it, and when the smallest is negative it moves down to it
+// (this last rule wins when both apply).
+template <class R>
+double refine_time(const Ctx& c, const uint32_t* idx, size_t n, double that, const double p[5],
+                   double x) {
+  Trk<R> st;
+  for (int k = 0; k < 5; ++k) st.p[k] = R(p[k]);
+  st.x = R(x);
+  R z0 = dca_z<R>(c, st);
+  double sg = c.cl.sector[idx[0]] < 18 ? 1.0 : -1.0;
+  double th = that - (sg * (double)val(z0)) / c.c.vdrift;
+  double lo = c.cl.t[idx[0]] - c.c.t0, hi = lo;
+  for (size_t k = 1; k < n; ++k) {
+    double d = c.cl.t[idx[k]] - c.c.t0;
+    lo = std::min(lo, d);
+    hi = std::max(hi, d);
+  }
+  double T = (double)c.g.drift_length / c.c.vdrift;
+  if (hi - th > T) th = th + ((hi - th) - T);
+  if (lo - th < 0.0) th = th + (lo - th);
+  return th;
+}
+
 }  // namespace
 
 // ======================================================================
@@ -1380,6 +1412,22 @@ int64_t orc_merge(void* ctx, int prec, int64_t nt, const uint32_t* ts, const uin
     out_ts[m] = nc;
   }
   return m;
+}
+
+// Collision times of tracks refined from their fits (time-frame mode; the
+// event mode and tracks whose refit failed keep theirs).
+void orc_refine_time(void* ctx, int prec, int64_t nt, const uint32_t* ts, const uint32_t* ci,
+                     const double* that, const double* params, const double* x,
+                     const int32_t* status, double* that_out) {
+  Ctx& c = *(Ctx*)ctx;
+  for (int64_t k = 0; k < nt; ++k) {
+    uint32_t a = ts[k], b = ts[k + 1];
+    that_out[k] = that[k];
+    if (c.cl.mode != 1 || status[k] != 0 || b <= a) continue;
+    that_out[k] = prec == 32
+        ? refine_time<float>(c, ci + a, b - a, that[k], params + 5 * k, x[k])
+        : refine_time<double>(c, ci + a, b - a, that[k], params + 5 * k, x[k]);
+  }
 }
 
 // Rotation of a state (and covariance, packed lower triangle) by dalpha.

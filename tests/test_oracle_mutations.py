@@ -58,6 +58,10 @@ MUTANTS = {
  'merge_frames': ("!(df == 0 || df == 1 || df == 17)", "!(df <= 2 || df >= 16)"),
  'merge_side': ("sg[j].ev != sg[i].ev || sg[j].side != sg[i].side) continue;", "sg[j].ev != sg[i].ev) continue;"),
  'merge_cholesky_sign': ("for (int k = 0; k < b; ++k) acc = acc - L[a][k] * L[b][k];", "for (int k = 0; k < b; ++k) acc = acc + L[a][k] * L[b][k];"),
+ 'refine_sign': ("double th = that - (sg * (double)val(z0)) / c.c.vdrift;", "double th = that + (sg * (double)val(z0)) / c.c.vdrift;"),
+ 'refine_side': ("double sg = c.cl.sector[idx[0]] < 18 ? 1.0 : -1.0;", "double sg = 1.0;"),
+ 'refine_upper': ("if (hi - th > T) th = th + ((hi - th) - T);", "if (hi - th > T) th = th - ((hi - th) - T);"),
+ 'refine_lower': ("if (lo - th < 0.0) th = th + (lo - th);", "if (lo - th < 0.0) th = th - (lo - th);"),
  'merge_solve_operand': ("for (int k = 0; k < a; ++k) acc = acc - L[a][k] * w[k];", "for (int k = 0; k < a; ++k) acc = acc - L[a][k] * d[k];"),
 }
 

@@ -967,3 +967,68 @@ def test_merge_expresses_z_with_the_predecessors_time(geo, params):
                 np.array([_packed(C_a), _packed(_spd(rng, 1e-3))]), np.array([rx[40], rx[70]]),
                 np.zeros(2, np.int32), prec=64)
     assert m["next"][0] == 1 and m["link_chi2"][0] < 1e-8, m["link_chi2"]
+
+
+# ------------------------------- collision time after merging (Sec. 4)
+def _timeframe_truth(geo, params, seed):
+    ev = synth.make_tiny(seed=seed, n_tracks=200, central=True, mode="time", tf_start=1.0e6,
+                         n_coll=2, sigma=0.0)
+    ts, ci, tc, ids = synth.truth_tracks(ev, 40, merged=True)
+    first = ci[ts[:-1].astype(np.int64)]
+    leg0 = (ids // 2) % 4 == 0
+    zv = ev.part["zv"][ev.label[first]]
+    return ev, ts, ci, tc, leg0, zv, first
+
+
+def test_refined_time_puts_the_vertex_of_primaries_at_zero(geo, params):
+    """Exact clusters of primaries, refitted with a collision time 0.7 us
+    off: the refined time is the one at which the fitted helix's closest
+    approach lies at z = 0, i.e. the true time shifted by the vertex z
+    (t - sg z_v / v_drift), independently of the starting error."""
+    ev, ts, ci, tc, leg0, zv, first = _timeframe_truth(geo, params, seed=48)
+    cal = synth.nominal_calib()
+    o = _oracle(ev, geo, params)
+    t_start = tc + 0.7
+    r = o.refit(ts, ci, t_start, prec=64)
+    th = o.refine_time(ts, ci, t_start, r["params"], r["x"], r["status"], prec=64)
+    sg = np.where(ev.sector[first] < 18, 1.0, -1.0)
+    want = tc - sg * zv / cal.vdrift
+    # tracks away from both ends of the drift volume (no shift inside needed)
+    L = geo.drift_length
+    inside = np.array([np.all((np.abs(ev.z_true[ci[a:b]]) > 6.0) &
+                              (np.abs(ev.z_true[ci[a:b]]) < L - 6.0))
+                       for a, b in zip(ts[:-1], ts[1:])])
+    ok = leg0 & inside & (r["status"] == 0)
+    assert ok.sum() >= 50
+    assert np.max(np.abs(th[ok] - want[ok])) < 1e-6, np.max(np.abs(th[ok] - want[ok]))
+    # failed refits and the event mode keep their time
+    assert np.all(th[r["status"] != 0] == t_start[r["status"] != 0])
+
+
+def test_refined_time_keeps_every_cluster_inside_the_drift_volume(geo, params):
+    """When the closest-approach estimate would put clusters outside the
+    drift volume (a state with a z offset, as for a secondary), the refined
+    time is that estimate moved into the set of times for which every
+    cluster's drift time lies in [0, L / v_drift]."""
+    ev, ts, ci, tc, leg0, zv, first = _timeframe_truth(geo, params, seed=49)
+    cal = synth.nominal_calib()
+    o = _oracle(ev, geo, params)
+    r = o.refit(ts, ci, tc, prec=64)
+    ok = np.nonzero(r["status"] == 0)[0]
+    T = float(geo.drift_length) / cal.vdrift
+    moved = 0
+    for off in (-120.0, 120.0):
+        p = r["params"].copy()
+        p[:, 1] += off
+        th = o.refine_time(ts, ci, tc, p, r["x"], r["status"], prec=64)
+        for k in ok:
+            d = ev.t[ci[ts[k]:ts[k + 1]]] - cal.t0
+            sg = 1.0 if ev.sector[first[k]] < 18 else -1.0
+            est = tc[k] - sg * o.dca_z(p[k], r["x"][k]) / cal.vdrift
+            lo, hi = d.min(), d.max()
+            assert hi - lo <= T
+            assert abs(th[k] - np.clip(est, hi - T, lo)) < 1e-9, (k, th[k], est, lo, hi - T)
+            tau = d - th[k]
+            assert tau.min() >= -1e-9 and tau.max() <= T + 1e-9
+            moved += est != np.clip(est, hi - T, lo)
+    assert moved >= 50
