@@ -198,6 +198,11 @@ tpc_status tpc_find_tracks(tpc_ctx* ctx, tpc_tracks* out);
  * are allocated. */
 tpc_status tpc_find_tracks_async(tpc_ctx* ctx);
 
+/* Fill *out with the context's current track set (library-owned device
+ * memory, as returned by tpc_find_tracks / tpc_merge_tracks). Synchronises
+ * (reads the counts). */
+tpc_status tpc_get_tracks(tpc_ctx* ctx, tpc_tracks* out);
+
 /* Replace the context's track set by caller-given tracks (truth assignment,
  * merged tracks ...). Copies the CSR asynchronously and applies the
  * calibration transform to the assigned clusters. */
@@ -237,6 +242,22 @@ tpc_status tpc_refit(tpc_ctx* ctx, int save_for_backward, float* params, float* 
 tpc_status tpc_merge_tracks(tpc_ctx* ctx, const float* params, const float* cov, const float* x,
                             const int32_t* status, int32_t* next, float* link_chi2,
                             tpc_tracks* out);
+
+/* Time-frame mode (mode 1; Sec. 4, after merging: the vertex estimate is
+ * refined with the merged track's fit and the track is shifted in z to it;
+ * a track with clusters outside the drift volume is shifted back inside):
+ * each track's collision time moves so that the fitted helix (params [n][5]
+ * at x [n], from tpc_refit of the current track set, device, caller-owned)
+ * reaches its closest approach to the beam line at z = 0, i.e. by
+ * -sg * z0 / vdrift (sg = +1 on the A side); it is then clipped so that
+ * every cluster's drift time t - t0 - t_coll lies in [0, drift_length /
+ * vdrift] (the lower bound wins when both apply). Tracks with status[k] !=
+ * 0, and every track in mode 0, keep their time. The calibration transform
+ * of the assigned clusters is re-applied; t_coll_out [n] (device, may be
+ * NULL) receives the times. Asynchronous; a refit must follow before
+ * tpc_refit_backward. */
+tpc_status tpc_refine_time(tpc_ctx* ctx, const float* params, const float* x,
+                           const int32_t* status, double* t_coll_out);
 
 /* Adjoint of the last saved refit (not in the paper; TPC_ERR_STATE if the
  * calibration was set again after that refit): for

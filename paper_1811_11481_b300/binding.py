@@ -90,9 +90,11 @@ _PROTOS = {
     "tpc_find_tracks": (C.c_int, [C.c_void_p, C.POINTER(tpc_tracks)]),
     "tpc_find_tracks_async": (C.c_int, [C.c_void_p]),
     "tpc_set_tracks": (C.c_int, [C.c_void_p, C.POINTER(tpc_tracks)]),
+    "tpc_get_tracks": (C.c_int, [C.c_void_p, C.POINTER(tpc_tracks)]),
     "tpc_refit": (C.c_int, [C.c_void_p, C.c_int] + [C.c_void_p] * 7),
     "tpc_refit_backward": (C.c_int, [C.c_void_p] + [C.c_void_p] * 4),
     "tpc_merge_tracks": (C.c_int, [C.c_void_p] + [C.c_void_p] * 6 + [C.POINTER(tpc_tracks)]),
+    "tpc_refine_time": (C.c_int, [C.c_void_p] + [C.c_void_p] * 4),
     "tpc_sync": (C.c_int, [C.c_void_p]),
     "tpc_get_counts": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
                                  C.POINTER(C.c_int64)]),
@@ -286,6 +288,13 @@ class Tracker:
                 _memcpy_d2d(out[key].data_ptr(), src, nbytes, self.stream)
         return out
 
+    def tracks(self):
+        """The context's current track set (copies)."""
+        t = tpc_tracks()
+        self._ck(self.L.tpc_get_tracks(self.h, C.byref(t)), "tpc_get_tracks")
+        self.n_tracks, self.n_assigned = int(t.n_tracks), int(t.n_assigned)
+        return self._tracks_view(t)
+
     def set_tracks(self, track_start, cluster_idx, t_coll, start_hit=None):
         ts = track_start.to(self.dev, self.torch.int32).contiguous()
         ci = cluster_idx.to(self.dev, self.torch.int32).contiguous()
@@ -351,6 +360,19 @@ class Tracker:
         self._merged_view = self._tracks_view(t)
         self.cluster_idx = self._merged_view["cluster_idx"]
         return dict(next=nx[:nt], link_chi2=lc[:nt], tracks=self._merged_view)
+
+    def refine_time(self, fit):
+        """Refine the collision times of the current track set from its refit
+        outputs fit (params, x, status); returns the times."""
+        torch = self.torch
+        nt = int(fit["status"].numel())
+        out = torch.empty(max(nt, 1), dtype=torch.float64, device=self.dev)
+        c = lambda k, dt: fit[k].to(self.dev, dt).contiguous()
+        ins = (c("params", torch.float32), c("x", torch.float32), c("status", torch.int32))
+        self._keep["refine"] = ins
+        self._ck(self.L.tpc_refine_time(self.h, *[_ptr(a) for a in ins], _ptr(out)),
+                 "tpc_refine_time")
+        return out[:nt]
 
     def sync(self):
         self._ck(self.L.tpc_sync(self.h), "tpc_sync")

@@ -525,6 +525,20 @@ tpc_status tpc_find_tracks(tpc_ctx* ctx, tpc_tracks* out) {
   return TPC_OK;
 }
 
+tpc_status tpc_get_tracks(tpc_ctx* ctx, tpc_tracks* out) {
+  if (!ctx || !out) return fail(ctx, TPC_ERR_ARG, "null argument");
+  if (!ctx->tracks_valid) return fail(ctx, TPC_ERR_STATE, "no track set");
+  tpc_status st = read_back(ctx);
+  if (st != TPC_OK) return st;
+  out->n_tracks = ctx->h_pinned[kCntTracks];
+  out->n_assigned = ctx->h_pinned[kCntAssigned];
+  out->track_start = ctx->tb.track_start;
+  out->cluster_idx = ctx->tb.cluster_idx;
+  out->t_coll = ctx->tb.t_coll;
+  out->start_hit = ctx->tb.start_hit;
+  return TPC_OK;
+}
+
 tpc_status tpc_set_tracks(tpc_ctx* ctx, const tpc_tracks* t) {
   if (!ctx || !t) return fail(ctx, TPC_ERR_ARG, "null argument");
   if (ctx->capturing) return fail(ctx, TPC_ERR_STATE, "tpc_set_tracks synchronises");
@@ -666,6 +680,22 @@ tpc_status tpc_merge_tracks(tpc_ctx* ctx, const float* params, const float* cov,
     out->t_coll = t.t_coll;
     out->start_hit = t.start_hit;
   }
+  return TPC_OK;
+}
+
+tpc_status tpc_refine_time(tpc_ctx* ctx, const float* params, const float* x,
+                           const int32_t* status, double* t_coll_out) {
+  if (!ctx) return TPC_ERR_ARG;
+  if (!ctx->tracks_valid) return fail(ctx, TPC_ERR_STATE, "no track set");
+  if (!params || !x || !status) return fail(ctx, TPC_ERR_ARG, "null track state");
+  TrackBuf& t = ctx->tb;
+  launch_refine_time(&ctx->prof, ctx->geo, ctx->cal, ctx->cl, t.cap_tr, ctx->d_cnt, t, params, x,
+                     status, t_coll_out, ctx->stream);
+  // the clusters' calibrated coordinates with the new times (Sec. 4)
+  launch_calib(&ctx->prof, ctx->geo, ctx->cal, ctx->cl, t.cap_asg, t, ctx->d_cnt, ctx->d_err,
+               ctx->stream);
+  CK(cudaGetLastError());
+  ctx->saved = false;
   return TPC_OK;
 }
 

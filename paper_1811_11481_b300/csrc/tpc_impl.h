@@ -298,5 +298,10 @@ void launch_merge(Prof* P, const Geo& g, const Params& p, const Cal& c, const Cl
                   int64_t n, TrackBuf& tb, MergeBuf& mb, const float* params, const float* cov,
                   const float* x, const int32_t* status, float* link_chi2, uint32_t* cnt,
                   cudaStream_t s);
+// Collision times of the track set refined from its fit (time-frame mode),
+// written to tb.t_coll and t_out (may be null).
+void launch_refine_time(Prof* P, const Geo& g, const Cal& c, const ClIn& cl, int64_t cap_tr,
+                        const uint32_t* cnt, TrackBuf& tb, const float* params, const float* x,
+                        const int32_t* status, double* t_out, cudaStream_t s);
 
 }  // namespace tpc

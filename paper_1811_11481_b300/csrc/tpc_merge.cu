@@ -330,7 +330,64 @@ __global__ void k_mg_write(int n, SegIn s, const uint32_t* seg_hit, const int32_
   }
 }
 
+// Collision time after merging (time-frame mode, Sec. 4): the closest
+// approach of the fitted helix to the beam line is moved to z = 0, then the
+// time is clipped so that every cluster's drift time t - t0 - that lies in
+// [0, L / v_drift] (the lower bound wins when both apply). One warp per
+// track: lanes reduce the range of t - t0 over the clusters.
+__global__ void k_refine_time(int cap, Geo g, Cal c, ClIn cl, const uint32_t* cnt,
+                              const uint32_t* ts, const uint32_t* ci, const float* params,
+                              const float* x, const int32_t* status, double* t_coll,
+                              double* t_out) {
+  int lane = threadIdx.x & 31;
+  int n = (int)cnt[kCntTracks];
+  if (n > cap) n = cap;
+  int nw = (int)((gridDim.x * (size_t)blockDim.x) >> 5);
+  for (int T = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5); T < n; T += nw) {
+    uint32_t a = ts[T], b = ts[T + 1];
+    double th = t_coll[T];
+    if (cl.mode == 1 && status[T] == 0 && b > a) {
+      double lo = cl.t[ci[a]] - c.t0, hi = lo;
+      for (uint32_t q = a + lane; q < b; q += 32) {
+        double d = cl.t[ci[q]] - c.t0;
+        lo = fmin(lo, d);
+        hi = fmax(hi, d);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+      }
+      float p[5];
+#pragma unroll
+      for (int k = 0; k < 5; ++k) p[k] = params[(size_t)T * 5 + k];
+      float z0 = dca_z(g.kB, p, x[T]);
+      double sg = cl.sector[ci[a]] < 18 ? 1.0 : -1.0;
+      th = th - (sg * (double)z0) / c.vdrift;
+      double tmax = (double)g.L / c.vdrift;
+      if (hi - th > tmax) th = th + ((hi - th) - tmax);
+      if (lo - th < 0.0) th = th + (lo - th);
+    }
+    if (lane == 0) {
+      t_coll[T] = th;
+      if (t_out) t_out[T] = th;
+    }
+  }
+}
+
 }  // namespace
+
+void launch_refine_time(Prof* P, const Geo& g, const Cal& c, const ClIn& cl, int64_t cap_tr,
+                        const uint32_t* cnt, TrackBuf& tb, const float* params, const float* x,
+                        const int32_t* status, double* t_out, cudaStream_t s) {
+  if (cap_tr <= 0) return;
+  int blocks = nblk(cap_tr * 32, kMB);
+  if (blocks > 16 * 148) blocks = 16 * 148;
+  TPC_LAUNCH(P, "k_refine_time", s,
+             k_refine_time<<<blocks, kMB, 0, s>>>((int)cap_tr, g, c, cl, cnt, tb.track_start,
+                                                  tb.cluster_idx, params, x, status, tb.t_coll,
+                                                  t_out));
+}
 
 void launch_merge(Prof* P, const Geo& g, const Params& p, const Cal& c, const ClIn& cl,
                   int64_t n, TrackBuf& tb, MergeBuf& mb, const float* params, const float* cov,

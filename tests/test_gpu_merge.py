@@ -155,3 +155,70 @@ def test_merge_of_an_empty_set_and_of_failed_segments(geo):
     mt = {k: v.cpu().numpy() for k, v in out["tracks"].items()}
     np.testing.assert_array_equal(mt["track_start"], g["track_start"])
     np.testing.assert_array_equal(mt["cluster_idx"], g["cluster_idx"])
+
+
+def test_refined_time_exact_on_the_same_states(geo):
+    """Collision times refined from the same float32 states (some with a z
+    offset, so that the shift back inside the drift volume acts) equal the
+    oracle's FP32 refinement bit for bit."""
+    import torch
+    ev = _event("time", seed=48, n_coll=2)
+    ts, ci, tc, _ = synth.truth_tracks(ev, 40, merged=True)
+    o = _oracle(ev, geo)
+    r = o.refit(ts, ci, tc, prec=64)
+    p = r["params"].copy()
+    rng = np.random.default_rng(3)
+    p[:, 1] += rng.choice([0.0, 0.0, -120.0, 120.0], size=p.shape[0])
+    st = dict(params=p.astype(np.float32), x=r["x"].astype(np.float32),
+              status=r["status"].astype(np.int32))
+    want = o.refine_time(ts, ci, tc, st["params"], st["x"], st["status"], prec=32)
+    assert np.sum(want != tc) > 100
+    tr = tracker(geo)
+    tr.set_calib()
+    tr.load(tr.upload(ev))
+    tr.set_tracks(torch.as_tensor(ts.astype(np.int32)), torch.as_tensor(ci.astype(np.int32)),
+                  torch.as_tensor(tc))
+    got = tr.refine_time({k: torch.as_tensor(v) for k, v in st.items()}).cpu().numpy()
+    np.testing.assert_array_equal(got, want)
+    # and the track set now carries them
+    np.testing.assert_array_equal(tr.tracks()["t_coll"].cpu().numpy(), want)
+
+
+def test_full_chain_with_time_refinement(geo):
+    """Time frame: find, refit, merge, refit, refine the collision times,
+    refit. The GPU chain against the oracle chain on the merged tracks both
+    form: times within 2 ns (the refit tolerance carried to the closest
+    approach: 1e-4 on tan(lambda) over at most 250 cm, plus 1e-4 cm on z,
+    over v_drift), final parameters within the refit tolerance."""
+    ev = _event("time", seed=49, n_coll=3)
+    o = _oracle(ev, geo)
+    seg = o.find(prec=32)["tracks"]
+    ts, ci, tt = seg["track_start"], seg["cluster_idx"], seg["that"]
+    r = o.refit(ts, ci, tt, prec=64)
+    m = o.merge(ts, ci, tt, r["params"], r["cov"], r["x"], r["status"], prec=32)
+    r2 = o.refit(m["track_start"], m["cluster_idx"], m["that"], prec=64)
+    th = o.refine_time(m["track_start"], m["cluster_idx"], m["that"], r2["params"], r2["x"],
+                       r2["status"], prec=64)
+    r3 = o.refit(m["track_start"], m["cluster_idx"], th, prec=64)
+    tr = tracker(geo)
+    tr.set_calib()
+    tr.load(tr.upload(ev))
+    tr.find()
+    tr.merge(tr.refit())
+    gth = tr.refine_time(tr.refit()).cpu().numpy()
+    g3 = tr.refit()
+    mt = {k: v.cpu().numpy() for k, v in tr.tracks().items()}
+    key_o = {tuple(m["cluster_idx"][m["track_start"][k]:m["track_start"][k + 1]]): k
+             for k in range(m["track_start"].size - 1)}
+    pg, sg = g3["params"].cpu().numpy(), g3["status"].cpu().numpy()
+    dt, errs = [], []
+    for k in range(mt["track_start"].size - 1):
+        c = tuple(mt["cluster_idx"][mt["track_start"][k]:mt["track_start"][k + 1]].astype(np.uint32))
+        ko = key_o.get(c)
+        if ko is None or sg[k] != 0 or r3["status"][ko] != 0 or r2["status"][ko] != 0:
+            continue
+        dt.append(abs(gth[k] - th[ko]))
+        errs.append(rel_err(pg[k].astype(np.float64), r3["params"][ko]))
+    assert len(dt) > 300
+    assert max(dt) < 2e-3, max(dt)
+    assert np.all(np.array(errs) <= RTOL), np.array(errs).max(0)
