@@ -45,6 +45,8 @@ def parse():
                     help="collisions of the time-frame workload (50: the headline frame)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-merge", action="store_true",
+                    help="skip the sector-merging stage measured after the timed region")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default launch shapes instead of tuning them on the workload")
     ap.add_argument("--tuning", default=None,
@@ -230,6 +232,98 @@ def track_quality(ev, track_start, cluster_idx, min_findable=70, purity=0.9):
                 clone_rate=float((per - 1).sum() / nt), findable=int(findable.size), tracks=nt,
                 definition=f"findable: >= {min_findable} clusters of one (particle, sector, leg); "
                            f"matched: >= {int(purity * 100)}% of a track's clusters from it")
+
+
+def merged_quality(ev, track_start, cluster_idx, min_findable=70, purity=0.9, cover=0.8):
+    """How many particle legs that cross sector boundaries are found whole:
+    a leg (particle, leg, side) with at least min_findable clusters in two
+    or more sector frames is findable; it is found whole when one track has
+    at least `purity` of its clusters from it and holds at least `cover` of
+    the leg's clusters."""
+    seg = np.asarray(ev.segment, np.int64)
+    lab = np.asarray(ev.label, np.int64)
+    side = (np.asarray(ev.sector) >= 18).astype(np.int64)
+    key = np.where(seg >= 0, (lab * 4 + seg % 4) * 2 + side, -1)
+    sig = key >= 0
+    K = int(key.max()) + 1 if sig.any() else 1
+    size = np.bincount(key[sig], minlength=K)
+    frames = np.zeros(K, np.int64)
+    fk = np.unique(key[sig] * 18 + np.asarray(ev.sector)[sig] % 18)
+    np.add.at(frames, fk // 18, 1)
+    findable = np.nonzero((size >= min_findable) & (frames >= 2))[0]
+    ts = np.asarray(track_start, np.int64)
+    ci = np.asarray(cluster_idx, np.int64)
+    whole = set()
+    for t in range(ts.size - 1):
+        k = key[ci[ts[t]:ts[t + 1]]]
+        if k.size == 0:
+            continue
+        v, c = np.unique(k, return_counts=True)
+        j = np.argmax(c)
+        if v[j] >= 0 and c[j] >= purity * k.size and c[j] >= cover * size[v[j]]:
+            whole.add(int(v[j]))
+    return dict(findable=int(findable.size),
+                found_whole=float(np.isin(findable, list(whole)).mean()) if findable.size else 0.0)
+
+
+def merge_stage(tr, cl, ev, flush, stream, reps=5):
+    """Sector merging and collision-time refinement after the per-sector
+    refit (Sec. 2 second phase, Sec. 4), on the same batch: find, refit,
+    merge, refit, refine the times (time-frame mode), refit."""
+    import torch
+
+    def ev_pair():
+        return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    acc = dict(merge_ms=0.0, merged_refit_ms=0.0, refine_ms=0.0, final_refit_ms=0.0)
+    info = {}
+    for rep in range(reps):
+        tr.load(cl)
+        tr.find()
+        seg = tr.refit()
+        if rep == 0:
+            t0 = tr.tracks()
+            info["segments"] = tr.n_tracks
+            info["before"] = merged_quality(ev, t0["track_start"].cpu().numpy(),
+                                            t0["cluster_idx"].cpu().numpy())
+        flush.fill_(1.0)
+        spans = {}
+        a, b = ev_pair()
+        a.record(stream)
+        m = tr.merge(seg)
+        b.record(stream)
+        spans["merge_ms"] = (a, b)
+        a, b = ev_pair()
+        a.record(stream)
+        r1 = tr.refit()
+        b.record(stream)
+        spans["merged_refit_ms"] = (a, b)
+        a, b = ev_pair()
+        a.record(stream)
+        tr.refine_time(r1)
+        b.record(stream)
+        spans["refine_ms"] = (a, b)
+        a, b = ev_pair()
+        a.record(stream)
+        r2 = tr.refit()
+        b.record(stream)
+        spans["final_refit_ms"] = (a, b)
+        torch.cuda.synchronize()
+        for k, (a, b) in spans.items():
+            acc[k] += a.elapsed_time(b) / reps
+        if rep == 0:
+            nx = m["next"]
+            info["links"] = int((nx >= 0).sum().item())
+            info["merged_tracks"] = tr.n_tracks
+            t1 = tr.tracks()
+            info["after"] = merged_quality(ev, t1["track_start"].cpu().numpy(),
+                                           t1["cluster_idx"].cpu().numpy())
+            info["refit_ok"] = float((r2["status"] == 0).float().mean().item())
+    return dict(acc, **info, reps=reps,
+                note="after the timed region, on the same batch; merge_ms brackets the "
+                     "synchronous tpc_merge_tracks call (segment copies, kernels, count "
+                     "read-back); quality: legs crossing sector boundaries found whole "
+                     "by one track before and after merging")
 
 
 def run_ours(args):
@@ -496,6 +590,8 @@ def run_ours(args):
     kernels = {k: dict(launches=v[0], ms_per_step=v[1] / n_prof, share=v[1] / tot)
                for k, v in sorted(kstats_all.items(), key=lambda kv: -kv[1][1])}
 
+    merge = None if args.no_merge else merge_stage(tr, cl, ev, flush, stream)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(ev, geo, secs=list(range(36)))
@@ -515,7 +611,7 @@ def run_ours(args):
                 roofline=roof, kernels=kernels,
                 kernels_timing=f"separate pass of {n_prof} steps with every launch timed",
                 gpu_launches=launches,
-                graph_replay=graph_replay, track_quality=quality,
+                graph_replay=graph_replay, track_quality=quality, merge_stage=merge,
                 clocks=clk, e2e=e2e, cpu_baseline=cpu)
     if rank == 0:
         print(json.dumps(line))

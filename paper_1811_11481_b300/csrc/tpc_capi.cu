@@ -361,7 +361,9 @@ void tpc_destroy(tpc_ctx* ctx) {
                   ctx->rb.gyc, ctx->rb.gzc, ctx->rb.acc_spline, ctx->rb.gmax, ctx->rb.part_cal,
                   ctx->mb.seg_ts, ctx->mb.seg_ci, ctx->mb.seg_that, ctx->mb.seg_hit,
                   ctx->mb.info, ctx->mb.rows, ctx->mb.bk_cnt, ctx->mb.bk_fill, ctx->mb.bk_seg,
+                  ctx->mb.bk_v, ctx->mb.bk_rlo, ctx->mb.bk_cls,
                   ctx->mb.best_in, ctx->mb.best_out, ctx->mb.next, ctx->mb.has_in,
+                  ctx->mb.pairs, ctx->mb.n_pairs,
                   ctx->mb.hpos, ctx->mb.cpos, ctx->mb.blk_h, ctx->mb.blk_c};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -609,9 +611,14 @@ tpc_status ensure_merge_buffers(tpc_ctx* ctx, int64_t n_tr, int64_t n_asg) {
     CK(alloc(m.info, c));
     CK(alloc(m.rows, c));
     CK(alloc(m.bk_seg, c));
+    CK(alloc(m.bk_v, c));
+    CK(alloc(m.bk_rlo, c));
     CK(alloc(m.best_in, c));
     CK(alloc(m.best_out, c));
     CK(alloc(m.next, c));
+    CK(alloc(m.pairs, 32 * c + 65536));
+    m.cap_pairs = 32 * c + 65536;
+    if (!m.n_pairs) CK(alloc(m.n_pairs, 1));
     CK(alloc(m.has_in, c));
     CK(alloc(m.hpos, c));
     CK(alloc(m.cpos, c));
@@ -627,6 +634,7 @@ tpc_status ensure_merge_buffers(tpc_ctx* ctx, int64_t n_tr, int64_t n_asg) {
   if (nb > m.cap_bk) {
     CK(alloc(m.bk_cnt, nb + 1));
     CK(alloc(m.bk_fill, nb));
+    CK(alloc(m.bk_cls, nb * 5));
     m.cap_bk = nb;
   }
   return TPC_OK;
@@ -658,9 +666,20 @@ tpc_status tpc_merge_tracks(tpc_ctx* ctx, const float* params, const float* cov,
     if (na > 0)
       CK(cudaMemcpyAsync(m.seg_ci, t.cluster_idx, sizeof(uint32_t) * na,
                          cudaMemcpyDeviceToDevice, ctx->stream));
-    launch_merge(&ctx->prof, ctx->geo, ctx->prm, ctx->cal, ctx->cl, nt, t, m, params, cov, x,
-                 status, link_chi2, ctx->d_cnt, ctx->stream);
-    CK(cudaGetLastError());
+    // the candidate-pair list has a capacity: when the pairs that pass the
+    // prefilter exceed it, it grows and the merge runs again (from the copies)
+    for (int attempt = 0;; ++attempt) {
+      launch_merge(&ctx->prof, ctx->geo, ctx->prm, ctx->cal, ctx->cl, nt, t, m, params, cov, x,
+                   status, link_chi2, ctx->d_cnt, ctx->stream);
+      CK(cudaGetLastError());
+      uint32_t np = 0;
+      CK(cudaMemcpyAsync(&np, m.n_pairs, sizeof(uint32_t), cudaMemcpyDeviceToHost, ctx->stream));
+      CK(cudaStreamSynchronize(ctx->stream));
+      if ((int64_t)np <= m.cap_pairs) break;
+      if (attempt > 0) return fail(ctx, TPC_ERR_CAPACITY, "merge candidate pairs overflow");
+      m.cap_pairs = (int64_t)np + np / 4 + 65536;
+      CK(alloc(m.pairs, m.cap_pairs));
+    }
     if (next)
       CK(cudaMemcpyAsync(next, m.next, sizeof(int32_t) * nt, cudaMemcpyDeviceToDevice,
                          ctx->stream));

@@ -169,9 +169,15 @@ struct MergeBuf {
   uint32_t* rows;       // [cap_tr] first row | last row << 16
   uint32_t* bk_cnt;     // [cap_bk + 1] bucket counts, then offsets
   uint32_t* bk_fill;    // [cap_bk]
-  uint32_t* bk_seg;     // [cap_tr] segments by bucket
+  uint32_t* bk_seg;     // [cap_tr] segments by bucket, variance class, tan(lambda)
+  float4* bk_v;         // [cap_tr] their tan(lambda), q/pT and the two variances
+  uint32_t* bk_rlo;     // [cap_tr] their first row
+  uint32_t* bk_cls;     // [cap_bk * 5] class boundaries of each bucket
   unsigned long long* best_in;   // [cap_tr] chi2 bits << 32 | best predecessor
   unsigned long long* best_out;  // [cap_tr] chi2 bits << 32 | best continuation
+  uint2* pairs;         // [cap_pairs] candidate pairs (i, j) that pass the prefilter
+  uint32_t* n_pairs;    // [1] pairs found (may exceed cap_pairs: then merged again)
+  int64_t cap_pairs;
   int32_t* next;        // [cap_tr] linked continuation or -1
   uint8_t* has_in;      // [cap_tr] has a linked predecessor
   uint32_t* hpos;       // [cap_tr] block-local merged-track index of a first segment

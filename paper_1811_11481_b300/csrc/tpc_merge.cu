@@ -20,9 +20,14 @@
 //              participation; bucket histogram.
 // k_mg_bucket  one block: bucket offsets.
 // k_mg_scatter one thread per segment: segment lists per bucket.
-// k_mg_best    one thread per segment: chi2 against every segment of the
-//              three candidate buckets; its best continuation, and a 64-bit
-//              atomic minimum (chi2 bits, own index) on each candidate's best
+// k_mg_sort    one block per bucket: segments in classes of tan(lambda)
+//              variance, sorted by tan(lambda) inside a class.
+// k_mg_cand    one warp per segment: the segments of the three candidate
+//              buckets inside its tan(lambda) window of each variance class
+//              (binary searches, one per lane) that pass the prefilter,
+//              appended to a pair list.
+// k_mg_eval    one thread per pair: chi2; 64-bit atomic minima (chi2 bits,
+//              index) give each segment its best continuation and its best
 //              predecessor.
 // k_mg_link    mutual best -> link.
 // k_mg_len     chain length of each first segment, block-local scans.
@@ -54,10 +59,12 @@ struct SegIn {
 constexpr uint32_t kTakesPart = 0x80000000u;
 
 __global__ void k_mg_info(int n, ClIn cl, SegIn s, uint32_t* info, uint32_t* rows,
-                          uint32_t* bk_cnt, unsigned long long* best_in, uint8_t* has_in) {
+                          uint32_t* bk_cnt, unsigned long long* best_in,
+                          unsigned long long* best_out, uint8_t* has_in) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   best_in[i] = ~0ull;
+  best_out[i] = ~0ull;
   has_in[i] = 0;
   uint32_t a = s.ts[i], b = s.ts[i + 1];
   uint32_t w = 0u, r = 0u;
@@ -138,6 +145,111 @@ __global__ void k_mg_scatter(int n, const uint32_t* info, const uint32_t* bk_sta
   bk_seg[bk_start[bk] + atomicAdd(&bk_fill[bk], 1u)] = (uint32_t)i;
 }
 
+// Each bucket's segments are grouped into classes of tan(lambda) variance and
+// sorted by tan(lambda) inside a class (one block per bucket, bitonic sort in
+// shared memory): a segment then searches, class by class, only the window
+// of tan(lambda) that its prefilter admits against the class's largest
+// variance. The prefilter data of the candidates (tan(lambda), q/pT, their
+// variances, first row) are stored in sorted order next to each other.
+// Buckets above kBucketSortMax stay unsorted and are scanned whole.
+constexpr int kBucketSortMax = 16384;
+constexpr int kSortThreads = 1024;
+constexpr int kVarClasses = 4;
+// upper tan(lambda) variance of the classes but the last (2^-20, 2^-17, 2^-14)
+__constant__ float kClassVar[kVarClasses - 1] = {9.5367431640625e-07f, 7.62939453125e-06f,
+                                                 6.103515625e-05f};
+
+// Sort key of a float: increasing with the value; every NaN after +inf.
+__device__ __forceinline__ uint32_t orderable(float f) {
+  uint32_t u = f == f ? __float_as_uint(f) : 0x7fffffffu;
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+__device__ __forceinline__ int var_class(float v) {
+  int c = 0;
+#pragma unroll
+  for (int k = 0; k < kVarClasses - 1; ++k) c += v > kClassVar[k] ? 1 : 0;
+  return c;
+}
+
+__global__ void __launch_bounds__(kSortThreads) k_mg_sort(const uint32_t* bk_start,
+                                                          uint32_t* bk_seg, float4* bk_v,
+                                                          uint32_t* bk_rlo, uint32_t* bk_cls,
+                                                          const uint32_t* rows,
+                                                          const float* params,
+                                                          const float* cov) {
+  extern __shared__ unsigned long long sk[];
+  int b = blockIdx.x;
+  uint32_t a = bk_start[b], e = bk_start[b + 1];
+  int m = (int)(e - a);
+  if (m > kBucketSortMax) {
+    // unsorted: everything in the last class, which is scanned whole
+    if (threadIdx.x <= kVarClasses)
+      bk_cls[(size_t)b * (kVarClasses + 1) + threadIdx.x] = threadIdx.x == kVarClasses ? e : a;
+    for (int i = threadIdx.x; i < m; i += kSortThreads) {
+      uint32_t j = bk_seg[a + i];
+      bk_v[a + i] = make_float4(params[(size_t)j * 5 + 3], params[(size_t)j * 5 + 4],
+                                cov[(size_t)j * 15 + 9], cov[(size_t)j * 15 + 14]);
+      bk_rlo[a + i] = rows[j] & 0xffffu;
+    }
+    return;
+  }
+  int np = 1;
+  while (np < m) np <<= 1;
+  int cnt[kVarClasses];
+#pragma unroll
+  for (int c = 0; c < kVarClasses; ++c) cnt[c] = 0;
+  for (int i = threadIdx.x; i < np; i += kSortThreads) {
+    if (i < m) {
+      uint32_t j = bk_seg[a + i];
+      int c = var_class(cov[(size_t)j * 15 + 9]);
+      ++cnt[c];
+      sk[i] = ((unsigned long long)c << 62) |
+              ((unsigned long long)orderable(params[(size_t)j * 5 + 3]) << 30) | j;
+    } else {
+      sk[i] = ~0ull;
+    }
+  }
+  // class boundaries
+  __shared__ int ccount[kVarClasses];
+  if (threadIdx.x < kVarClasses) ccount[threadIdx.x] = 0;
+  __syncthreads();
+#pragma unroll
+  for (int c = 0; c < kVarClasses; ++c)
+    if (cnt[c]) atomicAdd(&ccount[c], cnt[c]);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t o = a;
+    for (int c = 0; c < kVarClasses; ++c) {
+      bk_cls[(size_t)b * (kVarClasses + 1) + c] = o;
+      o += (uint32_t)ccount[c];
+    }
+    bk_cls[(size_t)b * (kVarClasses + 1) + kVarClasses] = o;
+  }
+  for (int k = 2; k <= np; k <<= 1)
+    for (int jj = k >> 1; jj > 0; jj >>= 1) {
+      for (int i = threadIdx.x; i < np; i += kSortThreads) {
+        int l = i ^ jj;
+        if (l > i) {
+          unsigned long long x = sk[i], y = sk[l];
+          bool up = (i & k) == 0;
+          if ((x > y) == up) {
+            sk[i] = y;
+            sk[l] = x;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  for (int i = threadIdx.x; i < m; i += kSortThreads) {
+    uint32_t j = (uint32_t)(sk[i] & 0x3fffffffull);
+    bk_seg[a + i] = j;
+    bk_v[a + i] = make_float4(params[(size_t)j * 5 + 3], params[(size_t)j * 5 + 4],
+                              cov[(size_t)j * 15 + 9], cov[(size_t)j * 15 + 14]);
+    bk_rlo[a + i] = rows[j] & 0xffffu;
+  }
+}
+
 struct MergeCfg {
   RefitCfg rc;   // kB, s_max and the frame rotations
   float cut;     // chi2_merge
@@ -205,44 +317,153 @@ __device__ bool pair_chi2(const MergeCfg& m, int side, const float pi[5], const 
   return ch <= m.cut;
 }
 
-__global__ void k_mg_best(int n, MergeCfg m, SegIn s, const uint32_t* info, const uint32_t* rows,
-                          const uint32_t* bk_start, const uint32_t* bk_seg,
-                          unsigned long long* best_in, unsigned long long* best_out) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
+// Candidate pairs. One warp per segment i: lanes 0..11 each find one
+// candidate range (three buckets times four variance classes; in the sorted
+// classes the window of tan(lambda) that the prefilter admits, by binary
+// search), so that the searches run side by side; then the warp scans the
+// concatenated ranges 64 candidates at a time and appends the pairs that
+// pass the prefilter to a list (one atomic per warp and step). The chi2 of
+// the pairs is the long part and runs in k_mg_eval, one thread per pair:
+// here most lanes would idle while one evaluates.
+constexpr int kRanges = 3 * kVarClasses;
+
+__global__ void __launch_bounds__(kMB) k_mg_cand(int n, float cut, const float* params,
+                                                 const float* cov, const uint32_t* info,
+                                                 const uint32_t* rows, const uint32_t* bk_seg,
+                                                 const float4* bk_v, const uint32_t* bk_rlo,
+                                                 const uint32_t* bk_cls, uint2* pairs,
+                                                 uint32_t cap_pairs, uint32_t* n_pairs) {
+  __shared__ uint32_t r_first[kMB / 32][kRanges], r_pre[kMB / 32][kRanges + 1];
+  int i = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+  int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
   if (i >= n) return;
   uint32_t wi = info[i];
-  unsigned long long best = ~0ull;
-  if (wi & kTakesPart) {
-    uint32_t bk = wi & ~kTakesPart;
-    int sec = (int)(bk % TPC_N_SECTORS);
-    uint32_t ev0 = bk - (uint32_t)sec;
-    int side = sec / 18, fi = sec % 18;
-    int rhi = (int)(rows[i] >> 16);
+  if (!(wi & kTakesPart)) return;
+  uint32_t bk = wi & ~kTakesPart;
+  int sec = (int)(bk % TPC_N_SECTORS);
+  uint32_t ev0 = bk - (uint32_t)sec;
+  int side = sec / 18, fi = sec % 18;
+  int rhi = (int)(rows[i] >> 16);
+  const float ti = params[(size_t)i * 5 + 3], qi = params[(size_t)i * 5 + 4];
+  const float vti = cov[(size_t)i * 15 + 9], vqi = cov[(size_t)i * 15 + 14];
+  const float lim = 2.0f * cut;
+  // the candidate ranges, one per lane
+  uint32_t len = 0u;
+  if (lane < kRanges) {
+    int df = lane / kVarClasses, c = lane % kVarClasses;
+    int fj = df == 0 ? fi : (df == 1 ? (fi + 1) % 18 : (fi + 17) % 18);
+    const uint32_t* cls = bk_cls + (size_t)(ev0 + (uint32_t)(side * 18 + fj)) * (kVarClasses + 1);
+    uint32_t q0 = cls[c], q1 = cls[c + 1];
+    if (c < kVarClasses - 1 && q0 < q1) {
+      // the prefilter's tan(lambda) bound with the class's largest variance,
+      // widened against rounding: a superset of the admitted
+      float w = sqrtf(lim * (vti + kClassVar[c])) * 1.001f + 1e-6f;
+      float lo = ti - w, hi = ti + w;
+      uint32_t l = q0, r = q1;
+      while (l < r) {  // first entry not below lo
+        uint32_t mid = (l + r) >> 1;
+        if (bk_v[mid].x < lo)
+          l = mid + 1;
+        else
+          r = mid;
+      }
+      q0 = l;
+      r = q1;
+      while (l < r) {  // first entry beyond hi (NaN counts as beyond)
+        uint32_t mid = (l + r) >> 1;
+        if (!(bk_v[mid].x <= hi))
+          r = mid;
+        else
+          l = mid + 1;
+      }
+      q1 = l;
+    }
+    len = q1 > q0 ? q1 - q0 : 0u;
+    r_first[wl][lane] = q0;
+  }
+  uint32_t incl = len;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane < kRanges) r_pre[wl][lane] = incl - len;
+  uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+  if (lane == 0) r_pre[wl][kRanges] = total;
+  __syncwarp();
+  int k = 0;  // the lane's current range
+  for (uint32_t base = 0; base < total; base += 64) {
+    uint32_t qq[2];
+    bool in[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      uint32_t g = base + (uint32_t)(u * 32 + lane);
+      in[u] = g < total;
+      qq[u] = 0u;
+      if (in[u]) {
+        while (r_pre[wl][k + 1] <= g) ++k;
+        qq[u] = r_first[wl][k] + (g - r_pre[wl][k]);
+      }
+    }
+    uint32_t rl[2], jj[2];
+    float4 v[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      rl[u] = in[u] ? bk_rlo[qq[u]] : 0u;
+      v[u] = in[u] ? bk_v[qq[u]] : make_float4(0.f, 0.f, 0.f, 0.f);
+      jj[u] = in[u] ? bk_seg[qq[u]] : 0u;
+    }
+    bool pass[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      // the prefilter of pair_chi2, on the same values
+      float dt = ti - v[u].x, dq = qi - v[u].y;
+      pass[u] = in[u] && (int)rl[u] > rhi && !(dt * dt > lim * (vti + v[u].z)) &&
+                !(dq * dq > lim * (vqi + v[u].w)) && (int)jj[u] != i;
+    }
+    uint32_t m0 = __ballot_sync(0xffffffffu, pass[0]);
+    uint32_t m1 = __ballot_sync(0xffffffffu, pass[1]);
+    uint32_t cnt = __popc(m0) + __popc(m1);
+    if (cnt == 0) continue;
+    uint32_t at = 0;
+    if (lane == 0) at = atomicAdd(n_pairs, cnt);
+    at = __shfl_sync(0xffffffffu, at, 0);
+    uint32_t below = (1u << lane) - 1u;
+    uint32_t p0 = at + __popc(m0 & below), p1 = at + __popc(m0) + __popc(m1 & below);
+    if (pass[0] && p0 < cap_pairs) pairs[p0] = make_uint2((uint32_t)i, jj[0]);
+    if (pass[1] && p1 < cap_pairs) pairs[p1] = make_uint2((uint32_t)i, jj[1]);
+  }
+}
+
+// chi2 of each candidate pair (one thread per pair), folded into i's best
+// continuation and j's best predecessor (64-bit atomic minimum of chi2 bits
+// and index: the smallest chi2, then the smallest index).
+__global__ void __launch_bounds__(kMB) k_mg_eval(MergeCfg m, SegIn s, const uint32_t* info,
+                                                 const uint2* pairs, uint32_t cap_pairs,
+                                                 const uint32_t* n_pairs,
+                                                 unsigned long long* best_in,
+                                                 unsigned long long* best_out) {
+  uint32_t np = *n_pairs;
+  if (np > cap_pairs) np = cap_pairs;
+  uint32_t stride = gridDim.x * blockDim.x;
+  for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < np; p += stride) {
+    uint2 e = pairs[p];
+    uint32_t i = e.x, j = e.y;
+    uint32_t bki = info[i] & ~kTakesPart, bkj = info[j] & ~kTakesPart;
+    int seci = (int)(bki % TPC_N_SECTORS), secj = (int)(bkj % TPC_N_SECTORS);
     float pi[5], Ci[15];
 #pragma unroll
     for (int k = 0; k < 5; ++k) pi[k] = s.params[(size_t)i * 5 + k];
 #pragma unroll
     for (int k = 0; k < 15; ++k) Ci[k] = s.cov[(size_t)i * 15 + k];
-    float xi = s.x[i];
-    double thi = s.that[i];
-    for (int df = 0; df < 3; ++df) {
-      int fj = df == 0 ? fi : (df == 1 ? (fi + 1) % 18 : (fi + 17) % 18);
-      uint32_t bj = ev0 + (uint32_t)(side * 18 + fj);
-      uint32_t q1 = bk_start[bj + 1];
-      for (uint32_t q = bk_start[bj]; q < q1; ++q) {
-        uint32_t j = bk_seg[q];
-        if ((int)j == i || !((int)(rows[j] & 0xffffu) > rhi)) continue;
-        float chi2;
-        if (!pair_chi2(m, side, pi, Ci, xi, thi, fi, s.params + (size_t)j * 5,
-                       s.cov + (size_t)j * 15, s.x[j], s.that[j], fj, chi2))
-          continue;
-        unsigned long long cb = (unsigned long long)__float_as_uint(chi2) << 32;
-        if ((cb | j) < best) best = cb | j;
-        atomicMin(&best_in[j], cb | (uint32_t)i);
-      }
-    }
+    float chi2;
+    if (!pair_chi2(m, seci / 18, pi, Ci, s.x[i], s.that[i], seci % 18, s.params + (size_t)j * 5,
+                   s.cov + (size_t)j * 15, s.x[j], s.that[j], secj % 18, chi2))
+      continue;
+    unsigned long long cb = (unsigned long long)__float_as_uint(chi2) << 32;
+    atomicMin(&best_out[i], cb | j);
+    atomicMin(&best_in[j], cb | i);
   }
-  best_out[i] = best;
 }
 
 __global__ void k_mg_link(int n, const unsigned long long* best_in,
@@ -407,14 +628,29 @@ void launch_merge(Prof* P, const Geo& g, const Params& p, const Cal& c, const Cl
   cudaMemsetAsync(mb.bk_cnt, 0, sizeof(uint32_t) * (nb + 1), s);
   TPC_LAUNCH(P, "k_mg_info", s,
              k_mg_info<<<nblk(n, kMB), kMB, 0, s>>>((int)n, cl, si, mb.info, mb.rows, mb.bk_cnt,
-                                                    mb.best_in, mb.has_in));
+                                                    mb.best_in, mb.best_out, mb.has_in));
   TPC_LAUNCH(P, "k_mg_bucket", s, k_mg_bucket<<<1, kScanB, 0, s>>>(nb, mb.bk_cnt, mb.bk_fill));
   TPC_LAUNCH(P, "k_mg_scatter", s,
              k_mg_scatter<<<nblk(n, kMB), kMB, 0, s>>>((int)n, mb.info, mb.bk_cnt, mb.bk_fill,
                                                        mb.bk_seg));
-  TPC_LAUNCH(P, "k_mg_best", s,
-             k_mg_best<<<nblk(n, kMB), kMB, 0, s>>>((int)n, m, si, mb.info, mb.rows, mb.bk_cnt,
-                                                    mb.bk_seg, mb.best_in, mb.best_out));
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_mg_sort, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(kBucketSortMax * sizeof(unsigned long long)));
+    attr = true;
+  }
+  TPC_LAUNCH(P, "k_mg_sort", s,
+             k_mg_sort<<<nb, kSortThreads, kBucketSortMax * sizeof(unsigned long long), s>>>(
+                 mb.bk_cnt, mb.bk_seg, mb.bk_v, mb.bk_rlo, mb.bk_cls, mb.rows, params, cov));
+  cudaMemsetAsync(mb.n_pairs, 0, sizeof(uint32_t), s);
+  TPC_LAUNCH(P, "k_mg_cand", s,
+             k_mg_cand<<<nblk(n * 32, kMB), kMB, 0, s>>>((int)n, m.cut, params, cov, mb.info,
+                                                         mb.rows, mb.bk_seg, mb.bk_v, mb.bk_rlo,
+                                                         mb.bk_cls, mb.pairs,
+                                                         (uint32_t)mb.cap_pairs, mb.n_pairs));
+  TPC_LAUNCH(P, "k_mg_eval", s,
+             k_mg_eval<<<4 * 148, kMB, 0, s>>>(m, si, mb.info, mb.pairs, (uint32_t)mb.cap_pairs,
+                                               mb.n_pairs, mb.best_in, mb.best_out));
   TPC_LAUNCH(P, "k_mg_link", s,
              k_mg_link<<<nblk(n, kMB), kMB, 0, s>>>((int)n, mb.best_in, mb.best_out, mb.next,
                                                     link_chi2, mb.has_in));
