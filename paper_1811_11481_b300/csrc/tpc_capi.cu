@@ -178,6 +178,7 @@ tpc_status ensure_track_buffers(tpc_ctx* ctx, int64_t cap_tr, int64_t cap_asg) {
     CK(alloc(rb.wlen, cap_tr / 32 + 2));
     CK(alloc(rb.wbase, cap_tr / 32 + 3));
     CK(alloc(rb.status, cap_tr));
+    CK(alloc(rb.multi, cap_tr));
     ctx->cap_tr_alloc = cap_tr;
   }
   if (cap_asg > ctx->cap_asg_alloc) {
@@ -357,7 +358,7 @@ void tpc_destroy(tpc_ctx* ctx) {
                   ctx->fb.weight, ctx->fb.nkeep, ctx->tb.track_start, ctx->tb.cluster_idx,
                   ctx->tb.asg_track, ctx->tb.t_coll, ctx->tb.start_hit, ctx->tb.yc, ctx->tb.zc,
                   ctx->tb.meta, ctx->rb.seed, ctx->rb.order, ctx->rb.slot, ctx->rb.wlen, ctx->rb.wbase, ctx->rb.len_hist,
-                  ctx->rb.w_yc, ctx->rb.w_zc, ctx->rb.w_meta, ctx->rb.rej, ctx->rb.status, ctx->rb.ckpt,
+                  ctx->rb.w_yc, ctx->rb.w_zc, ctx->rb.w_meta, ctx->rb.rej, ctx->rb.status, ctx->rb.multi, ctx->rb.ckpt,
                   ctx->rb.gyc, ctx->rb.gzc, ctx->rb.acc_spline, ctx->rb.gmax, ctx->rb.part_cal,
                   ctx->mb.seg_ts, ctx->mb.seg_ci, ctx->mb.seg_that, ctx->mb.seg_hit,
                   ctx->mb.info, ctx->mb.rows, ctx->mb.bk_cnt, ctx->mb.bk_fill, ctx->mb.bk_seg,

@@ -148,6 +148,7 @@ struct RefitBuf {
   float* seed;            // [cap_tr * 5]
   uint8_t* rej;           // [cap_w] interleaved rejection pass
   int32_t* status;        // [cap_tr]
+  uint8_t* multi;         // [cap_tr] track across sector frames
   float* ckpt;            // [3 * cap_w * 20]
   float* gyc;             // [cap_w] dL/d(calibrated y), interleaved
   float* gzc;             // [cap_w]

@@ -89,7 +89,8 @@ __global__ void k_na_refit(Geo g, RefitCfg p, int64_t n_tracks, int64_t n_assign
   int n = (int)(b - a);
   TrackIn in{track_start, yc, zc, meta};
   Lay ly = contiguous_layout(a, n);
-  RefitOut o = refit_track(g, p, in, ly, n, rej, nullptr, nullptr);
+  // the packed words carry no sector: one frame per track
+  RefitOut o = refit_track(g, p, in, ly, n, rej, nullptr, nullptr, false);
   if (o.status != 0) {
     o.chi2 = 0.0f;
     o.ndf = 0;

@@ -74,13 +74,14 @@ __global__ void k_len_scan(uint32_t* hist) {
   hist[i] = s[i];
 }
 __global__ void k_len_scatter(const uint32_t* cnt, const uint32_t* ts, uint32_t* hist,
-                              uint32_t* order, uint32_t* slot) {
+                              uint32_t* order, uint32_t* slot, uint8_t* multi) {
   int T = blockIdx.x * blockDim.x + threadIdx.x;
   if (T >= (int)cnt[kCntTracks]) return;
   int b = len_bin(ts, T);
   uint32_t pos = hist[b] + atomicAdd(&hist[kLenBins + b], 1u);
   order[pos] = (uint32_t)T;
   slot[T] = pos;
+  multi[T] = 0;  // set by k_interleave for tracks across sector frames
 }
 
 // Longest track of each warp of thread slots.
@@ -150,16 +151,19 @@ __device__ __forceinline__ Lay warp_layout(const uint32_t* wbase, const uint32_t
 // its place in its warp's interleaved block.
 __global__ void k_interleave(const uint32_t* cnt, TrackIn in, const uint32_t* asg_track,
                              const uint32_t* slot, const uint32_t* wbase, float* w_yc,
-                             float* w_zc, uint32_t* w_meta) {
+                             float* w_zc, uint32_t* w_meta, uint8_t* multi) {
   int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= (int)cnt[kCntAssigned]) return;
   uint32_t T = asg_track[j];
   if (T >= cnt[kCntTracks]) return;
   uint32_t sl = slot[T];
-  size_t pos = ((size_t)wbase[sl >> 5] + (j - in.track_start[T])) * 32 + (sl & 31);
+  uint32_t a = in.track_start[T];
+  size_t pos = ((size_t)wbase[sl >> 5] + (j - a)) * 32 + (sl & 31);
+  uint32_t m = in.meta[j];
   w_yc[pos] = in.yc[j];
   w_zc[pos] = in.zc[j];
-  w_meta[pos] = in.meta[j];
+  w_meta[pos] = m;
+  if (frame_of(m) != frame_of(in.meta[a])) multi[T] = 1;
 }
 
 __global__ void __launch_bounds__(kB) k_refit(Geo g, RefitCfg p, const uint32_t* cnt,
@@ -169,7 +173,8 @@ __global__ void __launch_bounds__(kB) k_refit(Geo g, RefitCfg p, const uint32_t*
                                                int32_t* status, float* ckpt, int save,
                                                float* o_params, float* o_cov, float* o_x,
                                                float* o_chi2, int32_t* o_ndf, int32_t* o_status,
-                                               uint8_t* o_rej, uint32_t* err) {
+                                               uint8_t* o_rej, const uint8_t* multi,
+                                               uint32_t* err) {
   int tid = blockIdx.x * blockDim.x + threadIdx.x;
   if (tid >= (int)cnt[kCntTracks]) return;
   int T = (int)order[tid];
@@ -183,7 +188,8 @@ __global__ void __launch_bounds__(kB) k_refit(Geo g, RefitCfg p, const uint32_t*
   }
   int n = (int)(b - a);
   Lay ly = warp_layout(wbase, wlen, tid);
-  RefitOut o = refit_track(g, p, win, ly, n, rej, seed_out + (size_t)T * 5, save ? ckpt : nullptr);
+  RefitOut o = refit_track(g, p, win, ly, n, rej, seed_out + (size_t)T * 5, save ? ckpt : nullptr,
+                           multi[T] != 0);
   if (o.status == 0 && !(fabsf(o.chi2) < 1.0e30f && fabsf(o.st[4]) < 1.0e30f))
     atomicOr(err, kErrNumeric);
   if (o.status != 0) {
@@ -211,7 +217,8 @@ __global__ void __launch_bounds__(kB) k_refit_bwd(Geo g, RefitCfg p, const uint3
                                                    const uint32_t* track_start, TrackIn win,
                                                    const uint8_t* rej, const int32_t* status,
                                                    const float* ckpt, const float* dl_dchi2,
-                                                   float* gyc, float* gzc, uint32_t* gmax) {
+                                                   float* gyc, float* gzc, const uint8_t* multi,
+                                                   uint32_t* gmax) {
   int tid = blockIdx.x * blockDim.x + threadIdx.x;
   if (tid >= (int)cnt[kCntTracks]) return;
   int T = (int)order[tid];
@@ -225,7 +232,7 @@ __global__ void __launch_bounds__(kB) k_refit_bwd(Geo g, RefitCfg p, const uint3
     }
     return;
   }
-  refit_backward_track(g, p, win, ly, n, rej, ckpt, dl_dchi2[T], gyc, gzc);
+  refit_backward_track(g, p, win, ly, n, rej, ckpt, dl_dchi2[T], gyc, gzc, multi[T] != 0);
   // largest |gradient| (as float bits, so that NaN ranks above infinity)
   uint32_t m = 0u;
   for (int k = 0; k < n; ++k) {
@@ -497,20 +504,20 @@ void launch_refit(Prof* P, const Geo& g, const Params& p, int64_t cap_tr, const 
   TPC_LAUNCH(P, "k_len_scan", s, k_len_scan<<<1, kLenBins, 0, s>>>(rb.len_hist));
   TPC_LAUNCH(P, "k_len_scatter", s,
              k_len_scatter<<<nb, 256, 0, s>>>(cnt, tb.track_start, rb.len_hist, rb.order,
-                                               rb.slot));
+                                               rb.slot, rb.multi));
   TPC_LAUNCH(P, "k_warp_len", s,
              k_warp_len<<<nb, 256, 0, s>>>(cnt, tb.track_start, rb.order, rb.wlen));
   TPC_LAUNCH(P, "k_warp_scan", s, k_warp_scan<<<1, 1024, 0, s>>>(cnt, rb.wlen, rb.wbase));
   TPC_LAUNCH(P, "k_interleave", s,
              k_interleave<<<nblk(tb.cap_asg, 256), 256, 0, s>>>(cnt, in, tb.asg_track, rb.slot,
                                                                  rb.wbase, rb.w_yc, rb.w_zc,
-                                                                 rb.w_meta));
+                                                                 rb.w_meta, rb.multi));
   TPC_LAUNCH(P, "k_refit", s,
              k_refit<<<nblk(cap_tr, kB), kB, 0, s>>>(g, make_cfg(g, p), cnt, rb.order, rb.wbase,
                                                      rb.wlen, tb.track_start, win, rb.seed,
                                                      rb.rej, rb.status, rb.ckpt, save ? 1 : 0,
                                                      params, cov, x, chi2, ndf, status, rej,
-                                                     err));
+                                                     rb.multi, err));
 }
 
 void launch_refit_backward(Prof* P, const Geo& g, const Cal& c, const Params& p, const ClIn& cl,
@@ -525,7 +532,8 @@ void launch_refit_backward(Prof* P, const Geo& g, const Cal& c, const Params& p,
                k_refit_bwd<<<nblk(cap_tr, kB), kB, 0, s>>>(g, make_cfg(g, p), cnt, rb.order,
                                                            rb.wbase, rb.wlen, tb.track_start,
                                                            win, rb.rej, rb.status, rb.ckpt,
-                                                           dl_dchi2, rb.gyc, rb.gzc, rb.gmax));
+                                                           dl_dchi2, rb.gyc, rb.gzc, rb.multi,
+                                                           rb.gmax));
   TPC_LAUNCH(P, "k_calib_grad", s,
              k_calib_grad<<<kCalibGradBlocks, kCgThreads, 0, s>>>(
                  g, c, cl, cnt, tb.cluster_idx, tb.asg_track, tb.track_start, rb.slot, rb.wbase,

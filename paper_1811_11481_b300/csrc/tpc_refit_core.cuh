@@ -270,10 +270,12 @@ TPC_HD RefitOut refit_track_in(const Geo& g, const RefitCfg& p, const TrackIn& i
   return o;
 }
 
+// multi: the track's clusters lie in more than one sector frame
+// (spans_frames).
 TPC_HD RefitOut refit_track(const Geo& g, const RefitCfg& p, const TrackIn& in, const Lay& ly,
-                            int n, uint8_t* rej, float* seed_out, float* ckpt) {
-  return spans_frames(in, ly, n) ? refit_track_in<true>(g, p, in, ly, n, rej, seed_out, ckpt)
-                                 : refit_track_in<false>(g, p, in, ly, n, rej, seed_out, ckpt);
+                            int n, uint8_t* rej, float* seed_out, float* ckpt, bool multi) {
+  return multi ? refit_track_in<true>(g, p, in, ly, n, rej, seed_out, ckpt)
+               : refit_track_in<false>(g, p, in, ly, n, rej, seed_out, ckpt);
 }
 
 // ------------------------------------------------------------ dual numbers
@@ -781,8 +783,8 @@ TPC_HD void refit_backward_in(const Geo& g, const RefitCfg& p, const TrackIn& in
 
 TPC_HD void refit_backward_track(const Geo& g, const RefitCfg& p, const TrackIn& in, const Lay& ly,
                                  int n, const uint8_t* rej, const float* ckpt, float gT,
-                                 float* gyc, float* gzc) {
-  if (spans_frames(in, ly, n))
+                                 float* gyc, float* gzc, bool multi) {
+  if (multi)
     refit_backward_in<true>(g, p, in, ly, n, rej, ckpt, gT, gyc, gzc);
   else
     refit_backward_in<false>(g, p, in, ly, n, rej, ckpt, gT, gyc, gzc);
