@@ -362,7 +362,7 @@ void tpc_destroy(tpc_ctx* ctx) {
                   ctx->rb.gyc, ctx->rb.gzc, ctx->rb.acc_spline, ctx->rb.gmax, ctx->rb.part_cal,
                   ctx->mb.seg_ts, ctx->mb.seg_ci, ctx->mb.seg_that, ctx->mb.seg_hit,
                   ctx->mb.info, ctx->mb.rows, ctx->mb.bk_cnt, ctx->mb.bk_fill, ctx->mb.bk_seg,
-                  ctx->mb.bk_v, ctx->mb.bk_rlo, ctx->mb.bk_cls,
+                  ctx->mb.bk_v, ctx->mb.bk_t, ctx->mb.bk_rlo, ctx->mb.bk_cls,
                   ctx->mb.best_in, ctx->mb.best_out, ctx->mb.next, ctx->mb.has_in,
                   ctx->mb.pairs, ctx->mb.n_pairs,
                   ctx->mb.hpos, ctx->mb.cpos, ctx->mb.blk_h, ctx->mb.blk_c};
@@ -613,6 +613,7 @@ tpc_status ensure_merge_buffers(tpc_ctx* ctx, int64_t n_tr, int64_t n_asg) {
     CK(alloc(m.rows, c));
     CK(alloc(m.bk_seg, c));
     CK(alloc(m.bk_v, c));
+    CK(alloc(m.bk_t, c));
     CK(alloc(m.bk_rlo, c));
     CK(alloc(m.best_in, c));
     CK(alloc(m.best_out, c));

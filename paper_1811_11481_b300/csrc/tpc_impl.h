@@ -172,6 +172,7 @@ struct MergeBuf {
   uint32_t* bk_fill;    // [cap_bk]
   uint32_t* bk_seg;     // [cap_tr] segments by bucket, variance class, tan(lambda)
   float4* bk_v;         // [cap_tr] their tan(lambda), q/pT and the two variances
+  float* bk_t;          // [cap_tr] their tan(lambda) alone (binary searches)
   uint32_t* bk_rlo;     // [cap_tr] their first row
   uint32_t* bk_cls;     // [cap_bk * 5] class boundaries of each bucket
   unsigned long long* best_in;   // [cap_tr] chi2 bits << 32 | best predecessor

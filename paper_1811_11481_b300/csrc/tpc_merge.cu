@@ -62,24 +62,29 @@ __global__ void k_mg_info(int n, ClIn cl, SegIn s, uint32_t* info, uint32_t* row
                           uint32_t* bk_cnt, unsigned long long* best_in,
                           unsigned long long* best_out, uint8_t* has_in) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  best_in[i] = ~0ull;
-  best_out[i] = ~0ull;
-  has_in[i] = 0;
-  uint32_t a = s.ts[i], b = s.ts[i + 1];
-  uint32_t w = 0u, r = 0u;
-  if (b > a) {
-    uint32_t f = s.ci[a], l = s.ci[b - 1];
-    uint32_t ev = cl.event ? cl.event[f] : 0u;
-    uint32_t bk = ev * TPC_N_SECTORS + cl.sector[f];
-    // clusters with an invalid event or sector (reported at load) stay out
-    bool ok = s.status[i] == 0 && ev < (uint32_t)cl.n_events && cl.sector[f] < TPC_N_SECTORS;
-    w = ok ? (bk | kTakesPart) : 0u;
-    r = (uint32_t)cl.row[f] | ((uint32_t)cl.row[l] << 16);
-    if (ok) atomicAdd(&bk_cnt[bk], 1u);
+  uint32_t w = 0u;
+  if (i < n) {
+    best_in[i] = ~0ull;
+    best_out[i] = ~0ull;
+    has_in[i] = 0;
+    uint32_t a = s.ts[i], b = s.ts[i + 1];
+    uint32_t r = 0u;
+    if (b > a) {
+      uint32_t f = s.ci[a], l = s.ci[b - 1];
+      uint32_t ev = cl.event ? cl.event[f] : 0u;
+      uint32_t bk = ev * TPC_N_SECTORS + cl.sector[f];
+      // clusters with an invalid event or sector (reported at load) stay out
+      bool ok = s.status[i] == 0 && ev < (uint32_t)cl.n_events && cl.sector[f] < TPC_N_SECTORS;
+      w = ok ? (bk | kTakesPart) : 0u;
+      r = (uint32_t)cl.row[f] | ((uint32_t)cl.row[l] << 16);
+    }
+    info[i] = w;
+    rows[i] = r;
   }
-  info[i] = w;
-  rows[i] = r;
+  // one atomic per bucket and warp (neighbouring segments share buckets)
+  uint32_t peers = __match_any_sync(0xffffffffu, w);
+  if ((w & kTakesPart) && (threadIdx.x & 31) == __ffs(peers) - 1)
+    atomicAdd(&bk_cnt[w & ~kTakesPart], (uint32_t)__popc(peers));
 }
 
 // Exclusive scan of v over a block of kScanB threads; returns the prefix and
@@ -138,11 +143,17 @@ __global__ void __launch_bounds__(kScanB) k_mg_bucket(int nb, uint32_t* bk_cnt, 
 __global__ void k_mg_scatter(int n, const uint32_t* info, const uint32_t* bk_start,
                              uint32_t* bk_fill, uint32_t* bk_seg) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  uint32_t w = info[i];
+  uint32_t w = i < n ? info[i] : 0u;
+  // one atomic per bucket and warp
+  uint32_t peers = __match_any_sync(0xffffffffu, w);
+  int lane = threadIdx.x & 31, leader = __ffs(peers) - 1;
+  uint32_t base = 0u;
+  if ((w & kTakesPart) && lane == leader)
+    base = atomicAdd(&bk_fill[w & ~kTakesPart], (uint32_t)__popc(peers));
+  base = __shfl_sync(0xffffffffu, base, leader);
   if (!(w & kTakesPart)) return;
   uint32_t bk = w & ~kTakesPart;
-  bk_seg[bk_start[bk] + atomicAdd(&bk_fill[bk], 1u)] = (uint32_t)i;
+  bk_seg[bk_start[bk] + base + __popc(peers & ((1u << lane) - 1u))] = (uint32_t)i;
 }
 
 // Each bucket's segments are grouped into classes of tan(lambda) variance and
@@ -174,7 +185,8 @@ __device__ __forceinline__ int var_class(float v) {
 
 __global__ void __launch_bounds__(kSortThreads) k_mg_sort(const uint32_t* bk_start,
                                                           uint32_t* bk_seg, float4* bk_v,
-                                                          uint32_t* bk_rlo, uint32_t* bk_cls,
+                                                          float* bk_t, uint32_t* bk_rlo,
+                                                          uint32_t* bk_cls,
                                                           const uint32_t* rows,
                                                           const float* params,
                                                           const float* cov) {
@@ -190,6 +202,7 @@ __global__ void __launch_bounds__(kSortThreads) k_mg_sort(const uint32_t* bk_sta
       uint32_t j = bk_seg[a + i];
       bk_v[a + i] = make_float4(params[(size_t)j * 5 + 3], params[(size_t)j * 5 + 4],
                                 cov[(size_t)j * 15 + 9], cov[(size_t)j * 15 + 14]);
+      bk_t[a + i] = params[(size_t)j * 5 + 3];
       bk_rlo[a + i] = rows[j] & 0xffffu;
     }
     return;
@@ -246,6 +259,7 @@ __global__ void __launch_bounds__(kSortThreads) k_mg_sort(const uint32_t* bk_sta
     bk_seg[a + i] = j;
     bk_v[a + i] = make_float4(params[(size_t)j * 5 + 3], params[(size_t)j * 5 + 4],
                               cov[(size_t)j * 15 + 9], cov[(size_t)j * 15 + 14]);
+    bk_t[a + i] = params[(size_t)j * 5 + 3];
     bk_rlo[a + i] = rows[j] & 0xffffu;
   }
 }
@@ -321,16 +335,18 @@ __device__ bool pair_chi2(const MergeCfg& m, int side, const float pi[5], const 
 // candidate range (three buckets times four variance classes; in the sorted
 // classes the window of tan(lambda) that the prefilter admits, by binary
 // search), so that the searches run side by side; then the warp scans the
-// concatenated ranges 64 candidates at a time and appends the pairs that
+// concatenated ranges 128 candidates at a time and appends the pairs that
 // pass the prefilter to a list (one atomic per warp and step). The chi2 of
 // the pairs is the long part and runs in k_mg_eval, one thread per pair:
 // here most lanes would idle while one evaluates.
 constexpr int kRanges = 3 * kVarClasses;
+constexpr int kPerLane = 4;  // candidates per lane and step, their loads issued together
 
 __global__ void __launch_bounds__(kMB) k_mg_cand(int n, float cut, const float* params,
                                                  const float* cov, const uint32_t* info,
                                                  const uint32_t* rows, const uint32_t* bk_seg,
-                                                 const float4* bk_v, const uint32_t* bk_rlo,
+                                                 const float4* bk_v, const float* bk_t,
+                                                 const uint32_t* bk_rlo,
                                                  const uint32_t* bk_cls, uint2* pairs,
                                                  uint32_t cap_pairs, uint32_t* n_pairs) {
   __shared__ uint32_t r_first[kMB / 32][kRanges], r_pre[kMB / 32][kRanges + 1];
@@ -362,7 +378,7 @@ __global__ void __launch_bounds__(kMB) k_mg_cand(int n, float cut, const float* 
       uint32_t l = q0, r = q1;
       while (l < r) {  // first entry not below lo
         uint32_t mid = (l + r) >> 1;
-        if (bk_v[mid].x < lo)
+        if (bk_t[mid] < lo)
           l = mid + 1;
         else
           r = mid;
@@ -371,7 +387,7 @@ __global__ void __launch_bounds__(kMB) k_mg_cand(int n, float cut, const float* 
       r = q1;
       while (l < r) {  // first entry beyond hi (NaN counts as beyond)
         uint32_t mid = (l + r) >> 1;
-        if (!(bk_v[mid].x <= hi))
+        if (!(bk_t[mid] <= hi))
           r = mid;
         else
           l = mid + 1;
@@ -392,11 +408,11 @@ __global__ void __launch_bounds__(kMB) k_mg_cand(int n, float cut, const float* 
   if (lane == 0) r_pre[wl][kRanges] = total;
   __syncwarp();
   int k = 0;  // the lane's current range
-  for (uint32_t base = 0; base < total; base += 64) {
-    uint32_t qq[2];
-    bool in[2];
+  for (uint32_t base = 0; base < total; base += 32 * kPerLane) {
+    uint32_t qq[kPerLane];
+    bool in[kPerLane];
 #pragma unroll
-    for (int u = 0; u < 2; ++u) {
+    for (int u = 0; u < kPerLane; ++u) {
       uint32_t g = base + (uint32_t)(u * 32 + lane);
       in[u] = g < total;
       qq[u] = 0u;
@@ -405,33 +421,35 @@ __global__ void __launch_bounds__(kMB) k_mg_cand(int n, float cut, const float* 
         qq[u] = r_first[wl][k] + (g - r_pre[wl][k]);
       }
     }
-    uint32_t rl[2], jj[2];
-    float4 v[2];
+    uint32_t rl[kPerLane], jj[kPerLane];
+    float4 v[kPerLane];
 #pragma unroll
-    for (int u = 0; u < 2; ++u) {
+    for (int u = 0; u < kPerLane; ++u) {
       rl[u] = in[u] ? bk_rlo[qq[u]] : 0u;
       v[u] = in[u] ? bk_v[qq[u]] : make_float4(0.f, 0.f, 0.f, 0.f);
       jj[u] = in[u] ? bk_seg[qq[u]] : 0u;
     }
-    bool pass[2];
+    uint32_t msk[kPerLane], cnt = 0u;
 #pragma unroll
-    for (int u = 0; u < 2; ++u) {
+    for (int u = 0; u < kPerLane; ++u) {
       // the prefilter of pair_chi2, on the same values
       float dt = ti - v[u].x, dq = qi - v[u].y;
-      pass[u] = in[u] && (int)rl[u] > rhi && !(dt * dt > lim * (vti + v[u].z)) &&
-                !(dq * dq > lim * (vqi + v[u].w)) && (int)jj[u] != i;
+      bool pass = in[u] && (int)rl[u] > rhi && !(dt * dt > lim * (vti + v[u].z)) &&
+                  !(dq * dq > lim * (vqi + v[u].w)) && (int)jj[u] != i;
+      msk[u] = __ballot_sync(0xffffffffu, pass);
+      cnt += __popc(msk[u]);
     }
-    uint32_t m0 = __ballot_sync(0xffffffffu, pass[0]);
-    uint32_t m1 = __ballot_sync(0xffffffffu, pass[1]);
-    uint32_t cnt = __popc(m0) + __popc(m1);
     if (cnt == 0) continue;
     uint32_t at = 0;
     if (lane == 0) at = atomicAdd(n_pairs, cnt);
     at = __shfl_sync(0xffffffffu, at, 0);
     uint32_t below = (1u << lane) - 1u;
-    uint32_t p0 = at + __popc(m0 & below), p1 = at + __popc(m0) + __popc(m1 & below);
-    if (pass[0] && p0 < cap_pairs) pairs[p0] = make_uint2((uint32_t)i, jj[0]);
-    if (pass[1] && p1 < cap_pairs) pairs[p1] = make_uint2((uint32_t)i, jj[1]);
+#pragma unroll
+    for (int u = 0; u < kPerLane; ++u) {
+      uint32_t p = at + __popc(msk[u] & below);
+      if ((msk[u] >> lane) & 1u && p < cap_pairs) pairs[p] = make_uint2((uint32_t)i, jj[u]);
+      at += __popc(msk[u]);
+    }
   }
 }
 
@@ -641,11 +659,13 @@ void launch_merge(Prof* P, const Geo& g, const Params& p, const Cal& c, const Cl
   }
   TPC_LAUNCH(P, "k_mg_sort", s,
              k_mg_sort<<<nb, kSortThreads, kBucketSortMax * sizeof(unsigned long long), s>>>(
-                 mb.bk_cnt, mb.bk_seg, mb.bk_v, mb.bk_rlo, mb.bk_cls, mb.rows, params, cov));
+                 mb.bk_cnt, mb.bk_seg, mb.bk_v, mb.bk_t, mb.bk_rlo, mb.bk_cls, mb.rows, params,
+                 cov));
   cudaMemsetAsync(mb.n_pairs, 0, sizeof(uint32_t), s);
   TPC_LAUNCH(P, "k_mg_cand", s,
              k_mg_cand<<<nblk(n * 32, kMB), kMB, 0, s>>>((int)n, m.cut, params, cov, mb.info,
-                                                         mb.rows, mb.bk_seg, mb.bk_v, mb.bk_rlo,
+                                                         mb.rows, mb.bk_seg, mb.bk_v, mb.bk_t,
+                                                         mb.bk_rlo,
                                                          mb.bk_cls, mb.pairs,
                                                          (uint32_t)mb.cap_pairs, mb.n_pairs));
   TPC_LAUNCH(P, "k_mg_eval", s,
