@@ -621,7 +621,7 @@ void launch_refine_time(Prof* P, const Geo& g, const Cal& c, const ClIn& cl, int
                         const int32_t* status, double* t_out, cudaStream_t s) {
   if (cap_tr <= 0) return;
   int blocks = nblk(cap_tr * 32, kMB);
-  if (blocks > 16 * 148) blocks = 16 * 148;
+  if (blocks > 64 * 148) blocks = 64 * 148;  // grid-stride beyond 64 blocks per SM
   TPC_LAUNCH(P, "k_refine_time", s,
              k_refine_time<<<blocks, kMB, 0, s>>>((int)cap_tr, g, c, cl, cnt, tb.track_start,
                                                   tb.cluster_idx, params, x, status, tb.t_coll,
