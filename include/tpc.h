@@ -243,6 +243,18 @@ tpc_status tpc_merge_tracks(tpc_ctx* ctx, const float* params, const float* cov,
                             const int32_t* status, int32_t* next, float* link_chi2,
                             tpc_tracks* out);
 
+/* The same merge without synchronising (capturable in a CUDA graph): the
+ * counts stay on the device (read them with tpc_get_counts), grids are
+ * sized by the track buffer's capacity, and the candidate-pair list keeps
+ * the capacity it has (32 pairs per segment of capacity unless a
+ * synchronous merge enlarged it). If the pairs that pass the prefilter
+ * exceed it, the next synchronising call reports TPC_ERR_CAPACITY (the
+ * merged set is then incomplete; tpc_merge_tracks on the same segments
+ * enlarges the list). The first call allocates (not during a capture). */
+tpc_status tpc_merge_tracks_async(tpc_ctx* ctx, const float* params, const float* cov,
+                                  const float* x, const int32_t* status, int32_t* next,
+                                  float* link_chi2);
+
 /* Time-frame mode (mode 1; Sec. 4, after merging: the vertex estimate is
  * refined with the merged track's fit and the track is shifted in z to it;
  * a track with clusters outside the drift volume is shifted back inside):

@@ -94,6 +94,7 @@ _PROTOS = {
     "tpc_refit": (C.c_int, [C.c_void_p, C.c_int] + [C.c_void_p] * 7),
     "tpc_refit_backward": (C.c_int, [C.c_void_p] + [C.c_void_p] * 4),
     "tpc_merge_tracks": (C.c_int, [C.c_void_p] + [C.c_void_p] * 6 + [C.POINTER(tpc_tracks)]),
+    "tpc_merge_tracks_async": (C.c_int, [C.c_void_p] + [C.c_void_p] * 6),
     "tpc_refine_time": (C.c_int, [C.c_void_p] + [C.c_void_p] * 4),
     "tpc_sync": (C.c_int, [C.c_void_p]),
     "tpc_get_counts": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
@@ -360,6 +361,18 @@ class Tracker:
         self._merged_view = self._tracks_view(t)
         self.cluster_idx = self._merged_view["cluster_idx"]
         return dict(next=nx[:nt], link_chi2=lc[:nt], tracks=self._merged_view)
+
+    def merge_async(self, seg, next_out=None, link_chi2=None):
+        """tpc_merge_tracks_async: no synchronisation, counts stay on the
+        device (counts() reads them). seg: refit outputs of the segments."""
+        torch = self.torch
+        c = lambda k, dt: seg[k].to(self.dev, dt).contiguous()
+        ins = (c("params", torch.float32), c("cov", torch.float32), c("x", torch.float32),
+               c("status", torch.int32))
+        self._keep["merge"] = ins
+        self._ck(self.L.tpc_merge_tracks_async(self.h, *[_ptr(a) for a in ins], _ptr(next_out),
+                                               _ptr(link_chi2)), "tpc_merge_tracks_async")
+        self.n_tracks = None
 
     def refine_time(self, fit):
         """Refine the collision times of the current track set from its refit

@@ -125,12 +125,14 @@ std::string err_text(uint32_t e) {
   if (e & kErrCapTrack) s += "track buffer overflow; ";
   if (e & kErrNumeric) s += "non-finite value in a refit; ";
   if (e & kErrTimeout) s += "a bounded device wait gave up; ";
+  if (e & kErrCapPairs)
+    s += "merge candidate-pair list overflow (tpc_merge_tracks enlarges it); ";
   return s;
 }
 
 tpc_status status_of(uint32_t e) {
   if (e & kErrArg) return TPC_ERR_ARG;
-  if (e & (kErrCapStart | kErrCapRow | kErrCapTrack)) return TPC_ERR_CAPACITY;
+  if (e & (kErrCapStart | kErrCapRow | kErrCapTrack | kErrCapPairs)) return TPC_ERR_CAPACITY;
   if (e & kErrTimeout) return TPC_ERR_TIMEOUT;
   if (e & kErrNumeric) return TPC_ERR_NUMERIC;
   return TPC_OK;
@@ -364,7 +366,7 @@ void tpc_destroy(tpc_ctx* ctx) {
                   ctx->mb.info, ctx->mb.rows, ctx->mb.bk_cnt, ctx->mb.bk_fill, ctx->mb.bk_seg,
                   ctx->mb.bk_v, ctx->mb.bk_t, ctx->mb.bk_rlo, ctx->mb.bk_cls,
                   ctx->mb.best_in, ctx->mb.best_out, ctx->mb.next, ctx->mb.has_in,
-                  ctx->mb.pairs, ctx->mb.n_pairs,
+                  ctx->mb.pairs, ctx->mb.n_pairs, ctx->mb.n_seg,
                   ctx->mb.hpos, ctx->mb.cpos, ctx->mb.blk_h, ctx->mb.blk_c};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -621,6 +623,7 @@ tpc_status ensure_merge_buffers(tpc_ctx* ctx, int64_t n_tr, int64_t n_asg) {
     CK(alloc(m.pairs, 32 * c + 65536));
     m.cap_pairs = 32 * c + 65536;
     if (!m.n_pairs) CK(alloc(m.n_pairs, 1));
+    if (!m.n_seg) CK(alloc(m.n_seg, 1));
     CK(alloc(m.has_in, c));
     CK(alloc(m.hpos, c));
     CK(alloc(m.cpos, c));
@@ -643,6 +646,25 @@ tpc_status ensure_merge_buffers(tpc_ctx* ctx, int64_t n_tr, int64_t n_asg) {
 }
 }  // namespace
 
+tpc_status tpc_merge_tracks_async(tpc_ctx* ctx, const float* params, const float* cov,
+                                  const float* x, const int32_t* status, int32_t* next,
+                                  float* link_chi2) {
+  if (!ctx) return TPC_ERR_ARG;
+  if (!ctx->tracks_valid) return fail(ctx, TPC_ERR_STATE, "no track set");
+  if (!params || !cov || !x || !status) return fail(ctx, TPC_ERR_ARG, "null segment state");
+  TrackBuf& t = ctx->tb;
+  tpc_status st = ensure_merge_buffers(ctx, t.cap_tr, t.cap_asg);
+  if (st != TPC_OK) return st;
+  launch_merge(&ctx->prof, ctx->geo, ctx->prm, ctx->cal, ctx->cl, t.cap_tr, true, t, ctx->mb,
+               params, cov, x, status, next, link_chi2, ctx->d_cnt, ctx->d_err, ctx->stream);
+  // the merged set's calibrated coordinates (Sec. 4)
+  launch_calib(&ctx->prof, ctx->geo, ctx->cal, ctx->cl, t.cap_asg, t, ctx->d_cnt, ctx->d_err,
+               ctx->stream);
+  CK(cudaGetLastError());
+  ctx->saved = false;
+  return TPC_OK;
+}
+
 tpc_status tpc_merge_tracks(tpc_ctx* ctx, const float* params, const float* cov, const float* x,
                             const int32_t* status, int32_t* next, float* link_chi2,
                             tpc_tracks* out) {
@@ -659,32 +681,22 @@ tpc_status tpc_merge_tracks(tpc_ctx* ctx, const float* params, const float* cov,
   MergeBuf& m = ctx->mb;
   TrackBuf& t = ctx->tb;
   if (nt > 0) {
-    CK(cudaMemcpyAsync(m.seg_ts, t.track_start, sizeof(uint32_t) * (nt + 1),
-                       cudaMemcpyDeviceToDevice, ctx->stream));
-    CK(cudaMemcpyAsync(m.seg_that, t.t_coll, sizeof(double) * nt, cudaMemcpyDeviceToDevice,
-                       ctx->stream));
-    CK(cudaMemcpyAsync(m.seg_hit, t.start_hit, sizeof(uint32_t) * nt, cudaMemcpyDeviceToDevice,
-                       ctx->stream));
-    if (na > 0)
-      CK(cudaMemcpyAsync(m.seg_ci, t.cluster_idx, sizeof(uint32_t) * na,
-                         cudaMemcpyDeviceToDevice, ctx->stream));
     // the candidate-pair list has a capacity: when the pairs that pass the
-    // prefilter exceed it, it grows and the merge runs again (from the copies)
+    // prefilter exceed it, it grows and the merge runs again on the copied
+    // segments
     for (int attempt = 0;; ++attempt) {
-      launch_merge(&ctx->prof, ctx->geo, ctx->prm, ctx->cal, ctx->cl, nt, t, m, params, cov, x,
-                   status, link_chi2, ctx->d_cnt, ctx->stream);
+      launch_merge(&ctx->prof, ctx->geo, ctx->prm, ctx->cal, ctx->cl, nt, attempt == 0, t, m,
+                   params, cov, x, status, next, link_chi2, ctx->d_cnt, ctx->d_err, ctx->stream);
       CK(cudaGetLastError());
       uint32_t np = 0;
       CK(cudaMemcpyAsync(&np, m.n_pairs, sizeof(uint32_t), cudaMemcpyDeviceToHost, ctx->stream));
       CK(cudaStreamSynchronize(ctx->stream));
       if ((int64_t)np <= m.cap_pairs) break;
       if (attempt > 0) return fail(ctx, TPC_ERR_CAPACITY, "merge candidate pairs overflow");
+      CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(uint32_t), ctx->stream));  // the overflow bit
       m.cap_pairs = (int64_t)np + np / 4 + 65536;
       CK(alloc(m.pairs, m.cap_pairs));
     }
-    if (next)
-      CK(cudaMemcpyAsync(next, m.next, sizeof(int32_t) * nt, cudaMemcpyDeviceToDevice,
-                         ctx->stream));
     // the merged set's calibrated coordinates (Sec. 4)
     launch_calib(&ctx->prof, ctx->geo, ctx->cal, ctx->cl, t.cap_asg, t, ctx->d_cnt, ctx->d_err,
                  ctx->stream);

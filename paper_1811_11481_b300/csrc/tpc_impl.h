@@ -21,6 +21,7 @@ enum : uint32_t {
   kErrCapTrack = 8u,      // track buffer overflow
   kErrNumeric = 16u,      // non-finite fit output
   kErrTimeout = 32u,      // a bounded wait gave up
+  kErrCapPairs = 64u,     // merge candidate-pair list overflow
 };
 
 // device counters (uint32 each)
@@ -179,6 +180,7 @@ struct MergeBuf {
   unsigned long long* best_out;  // [cap_tr] chi2 bits << 32 | best continuation
   uint2* pairs;         // [cap_pairs] candidate pairs (i, j) that pass the prefilter
   uint32_t* n_pairs;    // [1] pairs found (may exceed cap_pairs: then merged again)
+  uint32_t* n_seg;      // [1] segments being merged
   int64_t cap_pairs;
   int32_t* next;        // [cap_tr] linked continuation or -1
   uint8_t* has_in;      // [cap_tr] has a linked predecessor
@@ -298,14 +300,17 @@ void launch_refit_backward(Prof* P, const Geo& g, const Cal& c, const Params& p,
                            const TrackBuf& tb, RefitBuf& rb, const float* dl_dchi2,
                            float* grad_y, float* grad_zt, double* grad_calib, cudaStream_t s);
 
-// launcher (tpc_merge.cu): merges the n segments copied into mb (refitted
-// states params, cov, x, status) and writes the merged set into tb and its
-// count into cnt[kCntTracks]; link_chi2 (may be null) receives each
-// segment's link chi2.
+// launcher (tpc_merge.cu): merges the current track set of tb (at most
+// cap_n segments; counts read on the device; refitted states params, cov,
+// x, status), writes the merged set into tb and its count into
+// cnt[kCntTracks]; next_out and link_chi2 (may be null) receive each
+// segment's link and its chi2; a candidate-pair overflow sets kErrCapPairs
+// in err. copy = false merges again the segments copied by the previous
+// call (after a pair-list overflow).
 void launch_merge(Prof* P, const Geo& g, const Params& p, const Cal& c, const ClIn& cl,
-                  int64_t n, TrackBuf& tb, MergeBuf& mb, const float* params, const float* cov,
-                  const float* x, const int32_t* status, float* link_chi2, uint32_t* cnt,
-                  cudaStream_t s);
+                  int64_t cap_n, bool copy, TrackBuf& tb, MergeBuf& mb, const float* params,
+                  const float* cov, const float* x, const int32_t* status, int32_t* next_out,
+                  float* link_chi2, uint32_t* cnt, uint32_t* err, cudaStream_t s);
 // Collision times of the track set refined from its fit (time-frame mode),
 // written to tb.t_coll and t_out (may be null).
 void launch_refine_time(Prof* P, const Geo& g, const Cal& c, const ClIn& cl, int64_t cap_tr,

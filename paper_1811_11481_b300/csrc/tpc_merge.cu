@@ -16,6 +16,7 @@
 // predecessor, in the order of their first segment, which gives them its
 // collision time and start hit.
 //
+// k_mg_copy    the segments copied aside (the merged set replaces them).
 // k_mg_info    one thread per segment: bucket (event, sector), row range,
 //              participation; bucket histogram.
 // k_mg_bucket  one block: bucket offsets.
@@ -58,9 +59,31 @@ struct SegIn {
 
 constexpr uint32_t kTakesPart = 0x80000000u;
 
-__global__ void k_mg_info(int n, ClIn cl, SegIn s, uint32_t* info, uint32_t* rows,
-                          uint32_t* bk_cnt, unsigned long long* best_in,
+// The segments (the current track set) copied aside, so that the merged set
+// can be written in their place; their count kept for the merge kernels
+// (the track count is replaced by the merged count). Counts are read on the
+// device and bounded by the capacities.
+__global__ void k_mg_copy(int64_t cap_tr, int64_t cap_asg, const uint32_t* cnt, TrackBuf tb,
+                          uint32_t* seg_ts, uint32_t* seg_ci, double* seg_that,
+                          uint32_t* seg_hit, uint32_t* nseg) {
+  uint32_t n = cnt[kCntTracks], na = cnt[kCntAssigned];
+  if ((int64_t)n > cap_tr) n = (uint32_t)cap_tr;
+  if ((int64_t)na > cap_asg) na = (uint32_t)cap_asg;
+  size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  size_t stride = (size_t)gridDim.x * blockDim.x;
+  if (t == 0) *nseg = n;
+  for (size_t k = t; k <= n; k += stride) seg_ts[k] = tb.track_start[k];
+  for (size_t k = t; k < n; k += stride) {
+    seg_that[k] = tb.t_coll[k];
+    seg_hit[k] = tb.start_hit[k];
+  }
+  for (size_t k = t; k < na; k += stride) seg_ci[k] = tb.cluster_idx[k];
+}
+
+__global__ void k_mg_info(const uint32_t* nseg, ClIn cl, SegIn s, uint32_t* info,
+                          uint32_t* rows, uint32_t* bk_cnt, unsigned long long* best_in,
                           unsigned long long* best_out, uint8_t* has_in) {
+  int n = (int)*nseg;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   uint32_t w = 0u;
   if (i < n) {
@@ -140,8 +163,9 @@ __global__ void __launch_bounds__(kScanB) k_mg_bucket(int nb, uint32_t* bk_cnt, 
   for (int i = threadIdx.x; i < nb; i += kScanB) bk_fill[i] = 0u;
 }
 
-__global__ void k_mg_scatter(int n, const uint32_t* info, const uint32_t* bk_start,
-                             uint32_t* bk_fill, uint32_t* bk_seg) {
+__global__ void k_mg_scatter(const uint32_t* nseg, const uint32_t* info,
+                             const uint32_t* bk_start, uint32_t* bk_fill, uint32_t* bk_seg) {
+  int n = (int)*nseg;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   uint32_t w = i < n ? info[i] : 0u;
   // one atomic per bucket and warp
@@ -342,7 +366,8 @@ __device__ bool pair_chi2(const MergeCfg& m, int side, const float pi[5], const 
 constexpr int kRanges = 3 * kVarClasses;
 constexpr int kPerLane = 4;  // candidates per lane and step, their loads issued together
 
-__global__ void __launch_bounds__(kMB) k_mg_cand(int n, float cut, const float* params,
+__global__ void __launch_bounds__(kMB) k_mg_cand(const uint32_t* nseg, float cut,
+                                                 const float* params,
                                                  const float* cov, const uint32_t* info,
                                                  const uint32_t* rows, const uint32_t* bk_seg,
                                                  const float4* bk_v, const float* bk_t,
@@ -350,6 +375,7 @@ __global__ void __launch_bounds__(kMB) k_mg_cand(int n, float cut, const float* 
                                                  const uint32_t* bk_cls, uint2* pairs,
                                                  uint32_t cap_pairs, uint32_t* n_pairs) {
   __shared__ uint32_t r_first[kMB / 32][kRanges], r_pre[kMB / 32][kRanges + 1];
+  int n = (int)*nseg;
   int i = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
   int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
   if (i >= n) return;
@@ -484,10 +510,14 @@ __global__ void __launch_bounds__(kMB) k_mg_eval(MergeCfg m, SegIn s, const uint
   }
 }
 
-__global__ void k_mg_link(int n, const unsigned long long* best_in,
-                          const unsigned long long* best_out, int32_t* next, float* link_chi2,
-                          uint8_t* has_in) {
+__global__ void k_mg_link(const uint32_t* nseg, const unsigned long long* best_in,
+                          const unsigned long long* best_out, int32_t* next, int32_t* next_out,
+                          float* link_chi2, uint8_t* has_in, const uint32_t* n_pairs,
+                          uint32_t cap_pairs, uint32_t* err) {
+  int n = (int)*nseg;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
+  // pairs beyond the list's capacity were dropped: the links are incomplete
+  if (i == 0 && *n_pairs > cap_pairs) atomicOr(err, kErrCapPairs);
   if (i >= n) return;
   unsigned long long b = best_out[i];
   int32_t nx = -1;
@@ -501,15 +531,17 @@ __global__ void k_mg_link(int n, const unsigned long long* best_in,
     }
   }
   next[i] = nx;
+  if (next_out) next_out[i] = nx;
   if (link_chi2) link_chi2[i] = c;
 }
 
 // Chains are acyclic and at most one segment per pad row long: along a link
 // the first row strictly increases.
-__global__ void __launch_bounds__(kScanB) k_mg_len(int n, const uint32_t* ts,
+__global__ void __launch_bounds__(kScanB) k_mg_len(const uint32_t* nseg, const uint32_t* ts,
                                                    const int32_t* next, const uint8_t* has_in,
                                                    uint32_t* hpos, uint32_t* cpos,
                                                    uint32_t* blk_h, uint32_t* blk_c) {
+  int n = (int)*nseg;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   uint32_t h = 0u, len = 0u;
   if (i < n && !has_in[i]) {
@@ -543,9 +575,11 @@ __global__ void __launch_bounds__(kScanB) k_mg_top(int nb, uint32_t* blk_h, uint
   }
 }
 
-__global__ void k_mg_write(int n, SegIn s, const uint32_t* seg_hit, const int32_t* next,
+__global__ void k_mg_write(const uint32_t* nseg, SegIn s, const uint32_t* seg_hit,
+                           const int32_t* next,
                            const uint8_t* has_in, const uint32_t* hpos, const uint32_t* cpos,
                            const uint32_t* blk_h, const uint32_t* blk_c, TrackBuf tb) {
+  int n = (int)*nseg;
   int i = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
   int lane = threadIdx.x & 31;
   if (i >= n || has_in[i]) return;
@@ -629,10 +663,10 @@ void launch_refine_time(Prof* P, const Geo& g, const Cal& c, const ClIn& cl, int
 }
 
 void launch_merge(Prof* P, const Geo& g, const Params& p, const Cal& c, const ClIn& cl,
-                  int64_t n, TrackBuf& tb, MergeBuf& mb, const float* params, const float* cov,
-                  const float* x, const int32_t* status, float* link_chi2, uint32_t* cnt,
-                  cudaStream_t s) {
-  if (n <= 0) return;
+                  int64_t cap_n, bool copy, TrackBuf& tb, MergeBuf& mb, const float* params,
+                  const float* cov, const float* x, const int32_t* status, int32_t* next_out,
+                  float* link_chi2, uint32_t* cnt, uint32_t* err, cudaStream_t s) {
+  if (cap_n <= 0) return;
   int nb = cl.n_events * TPC_N_SECTORS;
   SegIn si{mb.seg_ts, mb.seg_ci, mb.seg_that, params, cov, x, status};
   MergeCfg m;
@@ -643,14 +677,21 @@ void launch_merge(Prof* P, const Geo& g, const Params& p, const Cal& c, const Cl
   m.cut = p.chi2_merge;
   m.mode = cl.mode;
   m.vdrift = c.vdrift;
+  int64_t cap_asg = tb.cap_asg < mb.cap_asg ? tb.cap_asg : mb.cap_asg;
+  if (copy)
+    TPC_LAUNCH(P, "k_mg_copy", s,
+               k_mg_copy<<<16 * 148, kMB, 0, s>>>(cap_n, cap_asg, cnt, tb, mb.seg_ts, mb.seg_ci,
+                                                  mb.seg_that, mb.seg_hit, mb.n_seg));
+  cudaMemsetAsync(mb.n_pairs, 0, sizeof(uint32_t), s);
   cudaMemsetAsync(mb.bk_cnt, 0, sizeof(uint32_t) * (nb + 1), s);
   TPC_LAUNCH(P, "k_mg_info", s,
-             k_mg_info<<<nblk(n, kMB), kMB, 0, s>>>((int)n, cl, si, mb.info, mb.rows, mb.bk_cnt,
-                                                    mb.best_in, mb.best_out, mb.has_in));
+             k_mg_info<<<nblk(cap_n, kMB), kMB, 0, s>>>(mb.n_seg, cl, si, mb.info, mb.rows,
+                                                        mb.bk_cnt, mb.best_in, mb.best_out,
+                                                        mb.has_in));
   TPC_LAUNCH(P, "k_mg_bucket", s, k_mg_bucket<<<1, kScanB, 0, s>>>(nb, mb.bk_cnt, mb.bk_fill));
   TPC_LAUNCH(P, "k_mg_scatter", s,
-             k_mg_scatter<<<nblk(n, kMB), kMB, 0, s>>>((int)n, mb.info, mb.bk_cnt, mb.bk_fill,
-                                                       mb.bk_seg));
+             k_mg_scatter<<<nblk(cap_n, kMB), kMB, 0, s>>>(mb.n_seg, mb.info, mb.bk_cnt,
+                                                           mb.bk_fill, mb.bk_seg));
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_mg_sort, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -661,29 +702,28 @@ void launch_merge(Prof* P, const Geo& g, const Params& p, const Cal& c, const Cl
              k_mg_sort<<<nb, kSortThreads, kBucketSortMax * sizeof(unsigned long long), s>>>(
                  mb.bk_cnt, mb.bk_seg, mb.bk_v, mb.bk_t, mb.bk_rlo, mb.bk_cls, mb.rows, params,
                  cov));
-  cudaMemsetAsync(mb.n_pairs, 0, sizeof(uint32_t), s);
   TPC_LAUNCH(P, "k_mg_cand", s,
-             k_mg_cand<<<nblk(n * 32, kMB), kMB, 0, s>>>((int)n, m.cut, params, cov, mb.info,
-                                                         mb.rows, mb.bk_seg, mb.bk_v, mb.bk_t,
-                                                         mb.bk_rlo,
-                                                         mb.bk_cls, mb.pairs,
-                                                         (uint32_t)mb.cap_pairs, mb.n_pairs));
+             k_mg_cand<<<nblk(cap_n * 32, kMB), kMB, 0, s>>>(
+                 mb.n_seg, m.cut, params, cov, mb.info, mb.rows, mb.bk_seg, mb.bk_v, mb.bk_t,
+                 mb.bk_rlo, mb.bk_cls, mb.pairs, (uint32_t)mb.cap_pairs, mb.n_pairs));
   TPC_LAUNCH(P, "k_mg_eval", s,
              k_mg_eval<<<4 * 148, kMB, 0, s>>>(m, si, mb.info, mb.pairs, (uint32_t)mb.cap_pairs,
                                                mb.n_pairs, mb.best_in, mb.best_out));
   TPC_LAUNCH(P, "k_mg_link", s,
-             k_mg_link<<<nblk(n, kMB), kMB, 0, s>>>((int)n, mb.best_in, mb.best_out, mb.next,
-                                                    link_chi2, mb.has_in));
-  int nsb = nblk(n, kScanB);
+             k_mg_link<<<nblk(cap_n, kMB), kMB, 0, s>>>(mb.n_seg, mb.best_in, mb.best_out,
+                                                        mb.next, next_out, link_chi2, mb.has_in,
+                                                        mb.n_pairs, (uint32_t)mb.cap_pairs,
+                                                        err));
+  int nsb = nblk(cap_n, kScanB);
   TPC_LAUNCH(P, "k_mg_len", s,
-             k_mg_len<<<nsb, kScanB, 0, s>>>((int)n, mb.seg_ts, mb.next, mb.has_in, mb.hpos,
+             k_mg_len<<<nsb, kScanB, 0, s>>>(mb.n_seg, mb.seg_ts, mb.next, mb.has_in, mb.hpos,
                                              mb.cpos, mb.blk_h, mb.blk_c));
   TPC_LAUNCH(P, "k_mg_top", s,
              k_mg_top<<<1, kScanB, 0, s>>>(nsb, mb.blk_h, mb.blk_c, cnt, tb.track_start));
   TPC_LAUNCH(P, "k_mg_write", s,
-             k_mg_write<<<nblk(n * 32, kMB), kMB, 0, s>>>((int)n, si, mb.seg_hit, mb.next,
-                                                          mb.has_in, mb.hpos, mb.cpos, mb.blk_h,
-                                                          mb.blk_c, tb));
+             k_mg_write<<<nblk(cap_n * 32, kMB), kMB, 0, s>>>(mb.n_seg, si, mb.seg_hit, mb.next,
+                                                              mb.has_in, mb.hpos, mb.cpos,
+                                                              mb.blk_h, mb.blk_c, tb));
 }
 
 }  // namespace tpc

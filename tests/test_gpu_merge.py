@@ -222,3 +222,87 @@ def test_full_chain_with_time_refinement(geo):
     assert len(dt) > 300
     assert max(dt) < 2e-3, max(dt)
     assert np.all(np.array(errs) <= RTOL), np.array(errs).max(0)
+
+
+def _chain_buffers(torch, dev, n):
+    cap = n // 10 + 1
+    f = lambda *s: torch.zeros(*s, device=dev)
+    i32 = lambda *s: torch.zeros(*s, dtype=torch.int32, device=dev)
+    mk = lambda: dict(params=f(cap, 5), cov=f(cap, 15), x=f(cap), chi2=f(cap), ndf=i32(cap),
+                      status=i32(cap), rej=torch.zeros(n + 1, dtype=torch.uint8, device=dev))
+    return dict(seg=mk(), r1=mk(), r2=mk(), next=i32(cap), lchi=f(cap),
+                t=torch.zeros(cap, dtype=torch.float64, device=dev))
+
+
+def _chain(tr, cl, b):
+    """find, refit the segments, merge (asynchronous), refit, refine the
+    collision times, refit: only asynchronous calls."""
+    import ctypes as C
+    P = lambda t: C.c_void_p(t.data_ptr())
+    L, h = tr.L, tr.h
+    fit = lambda o: L.tpc_refit(h, 0, P(o["params"]), P(o["cov"]), P(o["x"]), P(o["chi2"]),
+                                P(o["ndf"]), P(o["status"]), P(o["rej"]))
+    tr.load(cl)
+    assert L.tpc_find_tracks_async(h) == 0
+    assert fit(b["seg"]) == 0
+    s = b["seg"]
+    assert L.tpc_merge_tracks_async(h, P(s["params"]), P(s["cov"]), P(s["x"]), P(s["status"]),
+                                    P(b["next"]), P(b["lchi"])) == 0
+    assert fit(b["r1"]) == 0
+    r = b["r1"]
+    assert L.tpc_refine_time(h, P(r["params"]), P(r["x"]), P(r["status"]), P(b["t"])) == 0
+    assert fit(b["r2"]) == 0
+
+
+def test_async_merge_and_captured_chain_equal_the_synchronous_merge(geo):
+    """The asynchronous merge gives the synchronous merge's set bit for bit,
+    and the whole chain replays from a CUDA graph with the same outputs."""
+    import torch
+    from paper_1811_11481_b300.binding import Tracker
+    from paper_1811_11481_b300.config import default_params
+    ev = _event("time", seed=50, n_coll=2)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        tr = Tracker(geo, default_params(), stream=stream)
+        tr.set_calib()
+        cl = tr.upload(ev)
+        # synchronous reference
+        tr.load(cl)
+        tr.find()
+        seg = tr.refit()
+        m = tr.merge(seg)
+        ref = {k: v.cpu().numpy() for k, v in tr.tracks().items()}
+        ref_next = m["next"].cpu().numpy()
+        nseg = ref_next.size
+        b = _chain_buffers(torch, tr.dev, ev.n)
+        # the asynchronous merge alone
+        tr.load(cl)
+        tr.find()
+        seg2 = tr.refit()
+        tr.merge_async(seg2, b["next"], b["lchi"])
+        got = {k: v.cpu().numpy() for k, v in tr.tracks().items()}
+        for k in ref:
+            np.testing.assert_array_equal(got[k], ref[k], err_msg=k)
+        np.testing.assert_array_equal(b["next"][:nseg].cpu().numpy(), ref_next)
+        np.testing.assert_array_equal(b["lchi"][:nseg].cpu().numpy(),
+                                      m["link_chi2"].cpu().numpy())
+        # the chain, directly (allocates every buffer), then from a graph
+        _chain(tr, cl, b)
+        nt, na, _ = tr.counts()
+        direct = {k: v.clone() for k, v in b["r2"].items()}
+        t_direct = b["t"][:nt].clone()
+        for o in (b["r1"], b["r2"]):
+            for v in o.values():
+                if v.dtype.is_floating_point:
+                    v.fill_(float("nan"))
+        stream.synchronize()
+        tr.graph_begin()
+        _chain(tr, cl, b)                     # recorded, not run
+        tr.graph_end()
+        tr.graph_launch()
+        stream.synchronize()
+        assert tr.counts()[:2] == (nt, na)
+    for k in ("params", "cov", "chi2", "ndf", "status"):
+        assert torch.equal(b["r2"][k][:nt], direct[k][:nt]), k
+    assert torch.equal(b["t"][:nt], t_direct)
+    assert nt < nseg and nt > 0
