@@ -326,6 +326,68 @@ def merge_stage(tr, cl, ev, flush, stream, reps=5):
                      "by one track before and after merging")
 
 
+def merge_chain(tr, cl, n, flush, stream, steps):
+    """The full chain of the widened path as one CUDA graph per step: load,
+    find, refit of the segments, merge (asynchronous), refit, collision-time
+    refinement, refit; timed over `steps` replays with the L2 flushed
+    before each (after the headline's timed region)."""
+    import ctypes as C
+    import torch
+    P = lambda t: C.c_void_p(t.data_ptr())
+    L, h = tr.L, tr.h
+    cap = n // 10 + 1
+    dev = tr.dev
+    f = lambda *s: torch.zeros(*s, device=dev)
+    i32 = lambda *s: torch.zeros(*s, dtype=torch.int32, device=dev)
+    mk = lambda: dict(params=f(cap, 5), cov=f(cap, 15), x=f(cap), chi2=f(cap), ndf=i32(cap),
+                      status=i32(cap), rej=torch.zeros(n + 1, dtype=torch.uint8, device=dev))
+    seg, r1, r2 = mk(), mk(), mk()
+
+    def ck(st, what):
+        if st != 0:
+            raise RuntimeError(f"{what}: status {st}: {L.tpc_last_error(h).decode()}")
+
+    def fit(o):
+        ck(L.tpc_refit(h, 0, P(o["params"]), P(o["cov"]), P(o["x"]), P(o["chi2"]), P(o["ndf"]),
+                       P(o["status"]), P(o["rej"])), "refit")
+
+    def step():
+        tr.load(cl)
+        ck(L.tpc_find_tracks_async(h), "find")
+        fit(seg)
+        ck(L.tpc_merge_tracks_async(h, P(seg["params"]), P(seg["cov"]), P(seg["x"]),
+                                    P(seg["status"]), None, None), "merge")
+        fit(r1)
+        ck(L.tpc_refine_time(h, P(r1["params"]), P(r1["x"]), P(r1["status"]), None), "refine")
+        fit(r2)
+
+    for _ in range(3):
+        step()
+    tr.counts()                      # reports a capacity error of the asynchronous merge
+    torch.cuda.synchronize()
+    tr.graph_begin()
+    step()
+    tr.graph_end()
+    tr.graph_launch()
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(steps):
+        flush.fill_(1.0)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        tr.graph_launch()
+        b.record(stream)
+        times.append((a, b))
+    torch.cuda.synchronize()
+    nt, na, _ = tr.counts()
+    ms = float(np.mean([a.elapsed_time(b) for a, b in times]))
+    return dict(value=n / (ms / 1000.0), unit=UNIT, ms_per_step=ms, steps=steps,
+                merged_tracks=nt, refit_ok=float((r2["status"][:nt] == 0).float().mean().item()),
+                note="one CUDA graph per step: load, find, refit, merge, refit, collision-time "
+                     "refinement, refit; L2 flushed before each replay")
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -591,6 +653,8 @@ def run_ours(args):
                for k, v in sorted(kstats_all.items(), key=lambda kv: -kv[1][1])}
 
     merge = None if args.no_merge else merge_stage(tr, cl, ev, flush, stream)
+    if merge is not None:
+        merge["chain"] = merge_chain(tr, cl, n, flush, stream, min(args.steps, 50))
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
