@@ -50,8 +50,11 @@ typedef enum {
   TPC_ERR_NUMERIC = 6    /* non-finite value in a fit                     */
 } tpc_status;
 
-/* Cluster flag bits (Sec. 3 lists these special cluster types). Only
- * TPC_FLAG_SHARED changes the arithmetic: it scales the cluster error. */
+/* Cluster flag bits (Sec. 3 lists these special cluster types). In the
+ * final refit each set bit scales the cluster's position error by its
+ * factor (split_scale, single_row_scale, single_time_scale, edge_scale,
+ * shared_scale of tpc_params), in this bit order; track finding uses the
+ * plain error. */
 #define TPC_FLAG_SPLIT 0x01u
 #define TPC_FLAG_SINGLE_ROW 0x02u
 #define TPC_FLAG_SINGLE_TIME 0x04u
@@ -99,6 +102,10 @@ typedef struct {
   float refit_inflate;    /* covariance inflation between refit passes     */
   int32_t seed_max_hits;  /* chain hits used by the tracklet seed fit      */
   float chi2_merge;       /* segment-merging cut on the 5-parameter chi2   */
+  float split_scale;      /* error scale for TPC_FLAG_SPLIT clusters       */
+  float single_row_scale; /* error scale for TPC_FLAG_SINGLE_ROW clusters  */
+  float single_time_scale;/* error scale for TPC_FLAG_SINGLE_TIME clusters */
+  float edge_scale;       /* error scale for TPC_FLAG_EDGE clusters        */
 } tpc_params;
 
 /* Calibration (Sec. 4 and Sec. 5.2): drift velocity, time offset and a

@@ -231,6 +231,10 @@ struct OrcParams {
                           // final covariance times this factor
   int32_t seed_max_hits;  // chain hits used by the seed fit (Sec. 2: 4 to 10)
   float chi2_merge;       // segment-merging cut on the 5-parameter chi2
+  float split_scale;      // error scales of the other special clusters
+  float single_row_scale;
+  float single_time_scale;
+  float edge_scale;
 };
 
 struct OrcCalib {
@@ -261,7 +265,6 @@ namespace {
 constexpr double kCLight = 2.99792458e-3;
 constexpr int kNS = 36;
 constexpr int kSpl = 8;
-constexpr uint8_t kFlagShared = 0x10;
 
 struct Ctx {
   OrcGeom g;
@@ -278,6 +281,18 @@ struct Ctx {
     return rows[((size_t)ev * kNS + sec) * g.n_rows + r];
   }
 };
+
+// Position error of a cluster in the refit (Sec. 3: special clusters get
+// larger errors): sigma times the scale of each flag bit it carries, in bit
+// order (split, single row, single time, edge, shared).
+template <class R> R cluster_error(const Ctx& c, uint8_t flags) {
+  const float sc[5] = {c.p.split_scale, c.p.single_row_scale, c.p.single_time_scale,
+                       c.p.edge_scale, c.p.shared_scale};
+  R e = R(c.p.sigma);
+  for (int b = 0; b < 5; ++b)
+    if (flags & (1u << b)) e = e * R(sc[b]);
+  return e;
+}
 
 template <class R> R kB_of(const Ctx& c) { return R(kCLight) * R(c.g.bz); }
 template <> float kB_of<float>(const Ctx& c) { return (float)kCLight * c.g.bz; }
@@ -969,8 +984,7 @@ void track_inputs(const Ctx& c, const uint32_t* idx, size_t n, double that, std:
     int64_t i = idx[k];
     x[k] = R(c.rowx[c.cl.row[i]]);
     calibrate<R>(c, i, that, cal_in<R>(c, i), yc[k], zc[k], nullptr);
-    R sc = (c.cl.flags[i] & kFlagShared) ? R(c.p.shared_scale) : R(1);
-    R e = R(c.p.sigma) * sc;
+    R e = cluster_error<R>(c, c.cl.flags[i]);
     var[k] = e * e;
   }
 }
@@ -1357,8 +1371,7 @@ void orc_refit_grad(void* ctx, int64_t nt, const uint32_t* track_start,
       in.y = ly[q];
       x[q] = Var(c.rowx[c.cl.row[i]]);
       calibrate<Var>(c, i, that[k], in, yc[q], zc[q], &lv);
-      double sc = (c.cl.flags[i] & kFlagShared) ? c.p.shared_scale : 1.0;
-      double e = (double)c.p.sigma * sc;
+      double e = cluster_error<double>(c, c.cl.flags[i]);
       var[q] = Var(e * e);
     }
     std::vector<uint8_t> rj(rej + a, rej + b);

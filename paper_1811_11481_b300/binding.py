@@ -43,7 +43,9 @@ class tpc_params(C.Structure):
                 ("inward_cov_scale", C.c_float), ("c0t", C.c_float * 5),
                 ("c0r", C.c_float * 5), ("chi2_out", C.c_float),
                 ("min_acc_reject", C.c_int32), ("refit_inflate", C.c_float),
-                ("seed_max_hits", C.c_int32), ("chi2_merge", C.c_float)]
+                ("seed_max_hits", C.c_int32), ("chi2_merge", C.c_float),
+                ("split_scale", C.c_float), ("single_row_scale", C.c_float),
+                ("single_time_scale", C.c_float), ("edge_scale", C.c_float)]
 
 
 class tpc_calib(C.Structure):

@@ -29,6 +29,10 @@ DEFAULT_PARAMS = dict(
     refit_inflate=100.0,     # covariance inflation between refit passes
     seed_max_hits=10,        # chain hits in the seed fit (Sec. 2: segments of 4-10 hits)
     chi2_merge=30.0,         # segment-merging cut on the 5-parameter chi2 (Sec. 2, phase 2)
+    split_scale=1.5,         # error scales of the other special clusters in the refit (Sec. 3)
+    single_row_scale=1.5,
+    single_time_scale=1.5,
+    edge_scale=2.0,
 )
 
 # flag bits of a cluster (Sec. 3 lists the special cluster types)

@@ -115,6 +115,10 @@ void copy_params(const tpc_params& s, Params& d) {
   d.refit_inflate = s.refit_inflate;
   d.seed_max_hits = s.seed_max_hits;
   d.chi2_merge = s.chi2_merge;
+  d.split_scale = s.split_scale;
+  d.single_row_scale = s.single_row_scale;
+  d.single_time_scale = s.single_time_scale;
+  d.edge_scale = s.edge_scale;
 }
 
 std::string err_text(uint32_t e) {
@@ -271,6 +275,10 @@ void tpc_default_params(tpc_params* p) {
   p->refit_inflate = 100.0f;
   p->seed_max_hits = 10;
   p->chi2_merge = 30.0f;
+  p->split_scale = 1.5f;
+  p->single_row_scale = 1.5f;
+  p->single_time_scale = 1.5f;
+  p->edge_scale = 2.0f;
 }
 
 tpc_status tpc_create(const tpc_geometry* geo, const tpc_params* params, void* stream,

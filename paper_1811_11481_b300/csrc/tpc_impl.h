@@ -42,6 +42,7 @@ struct Params {
   float refit_inflate;
   int32_t seed_max_hits;
   float chi2_merge;
+  float split_scale, single_row_scale, single_time_scale, edge_scale;
 };
 
 // Search-grid parameters of a batch. The bin geometry itself (ny x nz bins

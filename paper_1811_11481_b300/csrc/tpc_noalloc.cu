@@ -137,7 +137,11 @@ extern "C" tpc_status tpc_refit_noalloc(const tpc_geometry* geo, const tpc_param
   cfg.kB = g.kB;
   cfg.s_max = pc.s_max;
   cfg.sigma = pc.sigma;
-  cfg.shared_scale = pc.shared_scale;
+  cfg.flag_scale[0] = pc.split_scale;
+  cfg.flag_scale[1] = pc.single_row_scale;
+  cfg.flag_scale[2] = pc.single_time_scale;
+  cfg.flag_scale[3] = pc.edge_scale;
+  cfg.flag_scale[4] = pc.shared_scale;
   cfg.chi2_out = pc.chi2_out;
   cfg.refit_inflate = pc.refit_inflate;
   cfg.min_acc_reject = pc.min_acc_reject;

@@ -31,7 +31,11 @@ RefitCfg make_cfg(const Geo& g, const Params& p) {
   c.kB = g.kB;
   c.s_max = p.s_max;
   c.sigma = p.sigma;
-  c.shared_scale = p.shared_scale;
+  c.flag_scale[0] = p.split_scale;
+  c.flag_scale[1] = p.single_row_scale;
+  c.flag_scale[2] = p.single_time_scale;
+  c.flag_scale[3] = p.edge_scale;
+  c.flag_scale[4] = p.shared_scale;
   c.chi2_out = p.chi2_out;
   c.refit_inflate = p.refit_inflate;
   c.min_acc_reject = p.min_acc_reject;

@@ -51,9 +51,12 @@ TPC_HD Lay contiguous_layout(uint32_t a, int n) {
 constexpr int kFrames = 18;
 
 struct RefitCfg {
-  float kB, s_max, sigma, shared_scale, chi2_out, refit_inflate;
+  float kB, s_max, sigma, chi2_out, refit_inflate;
   int32_t min_acc_reject;
   float c0r[5];
+  // error scale of each cluster flag bit (split, single row, single time,
+  // edge, shared)
+  float flag_scale[5];
   float rot_c[kFrames], rot_s[kFrames];  // cos, sin of m * 20 degrees
 };
 
@@ -119,8 +122,15 @@ TPC_HD bool rotate_frame(float kB, float s_max, float ca, float sa, float p[5], 
   return true;
 }
 
+// Position variance of a cluster: the error scaled by the factor of each
+// flag bit it carries, in bit order (Sec. 3: special clusters get larger
+// errors).
 TPC_HD float cl_var(const RefitCfg& p, uint32_t meta) {
-  float e = ((meta >> 8) & TPC_FLAG_SHARED) ? p.sigma * p.shared_scale : p.sigma;
+  uint32_t f = (meta >> 8) & 0x1fu;
+  float e = p.sigma;
+#pragma unroll
+  for (int b = 0; b < 5; ++b)
+    if (f & (1u << b)) e = e * p.flag_scale[b];
   return e * e;
 }
 

@@ -15,14 +15,23 @@ from pipeline import (RTOL, canonical_tracks, gpu_find, oracle_find, rel_err, tr
 pytestmark = pytest.mark.gpu
 
 
+def _flagged(ev, seed):
+    """Special-cluster flags on a fifth of the clusters (the generator sets
+    none), so that the refit's error scales are exercised."""
+    rng = np.random.default_rng(seed)
+    pick = rng.random(ev.n) < 0.2
+    ev.flags[pick] = rng.integers(1, 32, size=int(pick.sum())).astype(np.uint8)
+    return ev
+
+
 def _cases():
     rng = np.random.default_rng(7)
     spl = synth.nominal_calib()
     spl.spline = synth.random_distortion(rng, 0.8)
     return {
         "single_sector": (lambda: synth.make_single_sector(), None),
-        "central_small": (lambda: synth.make_tiny(seed=31, n_tracks=600, central=True,
-                                                  noise_frac=0.1), None),
+        "central_small": (lambda: _flagged(synth.make_tiny(seed=31, n_tracks=600, central=True,
+                                                           noise_frac=0.1), 71), None),
         "timeframe_small": (lambda: synth.make_tiny(seed=32, n_tracks=250, central=True,
                                                     noise_frac=0.15, mode="time",
                                                     tf_start=1.0e6, n_coll=4), None),

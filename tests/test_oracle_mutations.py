@@ -45,7 +45,7 @@ MUTANTS = {
  'select_gap_ge': ("if (kept < c.p.min_track_hits || maxgap > c.p.max_gap) continue;", "if (kept < c.p.min_track_hits || maxgap >= c.p.max_gap) continue;"),
  'seed_max_le': ("while (upc[cur] >= 0 && (int)H.size() < c.p.seed_max_hits) {", "while (upc[cur] >= 0 && (int)H.size() <= c.p.seed_max_hits) {"),
  'that_sign': ("that = c.c.tf_start - (sg * (double)zd) / c.c.vdrift;", "that = c.c.tf_start + (sg * (double)zd) / c.c.vdrift;"),
- 'shared_scale_refit': ("R sc = (c.cl.flags[i] & kFlagShared) ? R(c.p.shared_scale) : R(1);", "R sc = R(1);"),
+ 'flag_scale_refit': ("if (flags & (1u << b)) e = e * R(sc[b]);", "if (flags & (1u << b)) e = e * R(sc[4 - b]);"),
  'nb_dmax_strict': ("if (!(D <= dmax)) continue;", "if (!(D < dmax)) continue;"),
  'rotation_curvature_term': ("J[2][0] = kap * sa;", "J[2][0] = -(kap * sa);"),
  'rotation_y_factor': ("J[0][0] = cf / c2;", "J[0][0] = c2 / cf;"),

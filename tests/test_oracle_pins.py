@@ -657,25 +657,32 @@ def test_selector_weights_and_gaps(geo, params):
     assert list(tr["cluster_idx"]) == [j for _, j in ok]
 
 
-# -------------------------------------------------- shared-cluster errors
-def test_shared_clusters_have_scaled_errors(geo, params):
-    """TPC_FLAG_SHARED clusters have their error scaled by shared_scale
-    (Sec. 3): flagging every cluster of a track leaves the least-squares
-    estimate unchanged and divides chi2 by shared_scale^2 (up to the weak
-    prior of the first pass)."""
+# -------------------------------------------------- special-cluster errors
+SCALE_OF_BIT = {0x01: "split_scale", 0x02: "single_row_scale", 0x04: "single_time_scale",
+                0x08: "edge_scale", 0x10: "shared_scale"}
+
+
+@pytest.mark.parametrize("flags", [0x01, 0x02, 0x04, 0x08, 0x10, 0x09, 0x1f])
+def test_special_clusters_have_scaled_errors(geo, params, flags):
+    """Flagged clusters have their error scaled by the factor of each flag
+    bit (Sec. 3: special clusters get larger errors): flagging every cluster
+    of a track leaves the least-squares estimate unchanged and divides chi2
+    by the square of the product of the factors (up to the weak prior of the
+    first pass)."""
     ev = synth.make_tiny(seed=29, n_tracks=10, sectors=(11,))
     ts, ci, tc, _ = synth.truth_tracks(ev, 60)
     o = _oracle(ev, geo, params)
     r = o.refit(ts, ci, tc, prec=64)
-    ev.flags[:] = 0x10
+    ev.flags[:] = flags
     o2 = _oracle(ev, geo, params)
     r2 = o2.refit(ts, ci, tc, prec=64)
     ev.flags[:] = 0
     ok = (r["status"] == 0) & (r2["status"] == 0)
     assert ok.sum() >= 3
+    s = np.prod([params[v] for b, v in SCALE_OF_BIT.items() if flags & b])
     ratio = r2["chi2"][ok] / r["chi2"][ok]
-    s = params["shared_scale"]
     np.testing.assert_allclose(ratio, 1.0 / (s * s), rtol=2e-2)
+    np.testing.assert_allclose(r2["params"][ok], r["params"][ok], rtol=0, atol=2e-3 * s)
 
 
 # ------------------------------------------- tracks across sectors (rotation)
