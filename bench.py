@@ -651,6 +651,22 @@ def run_ours(args):
                     timing="CUDA events around each of its launches in the timed region")
     kernels = {k: dict(launches=v[0], ms_per_step=v[1] / n_prof, share=v[1] / tot)
                for k, v in sorted(kstats_all.items(), key=lambda kv: -kv[1][1])}
+    # the whole step against the HBM roofline: the algorithmic bytes of every
+    # modelled kernel of a step over the step's time
+    step_bytes = 0
+    for k, v in kstats_all.items():
+        ab = None if k.startswith("k_row_sort") else algorithmic_bytes(k, counts)
+        if ab:
+            step_bytes += ab * v[0] / n_prof          # launches per step
+    if any(k.startswith("k_row_sort") for k in kstats_all):
+        step_bytes += algorithmic_bytes("k_row_sort", counts)
+    step_ms = total_ms / args.steps
+    step_gbs = step_bytes / (step_ms / 1000.0) / 1e9
+    step_hbm = dict(algorithmic_bytes=step_bytes, achieved=step_gbs, unit="GB/s",
+                    peak=peaks["hbm_gbs"], frac=step_gbs / peaks["hbm_gbs"],
+                    note="algorithmic bytes of all modelled kernels of one step (times "
+                         "their launches per step; the row sorts together once) over the "
+                         "step time, of measured HBM copy bandwidth")
 
     merge = None if args.no_merge else merge_stage(tr, cl, ev, flush, stream)
     if merge is not None:
@@ -672,7 +688,7 @@ def run_ours(args):
                 n_tracks=nt, n_assigned=na, n_tracklets=ntl,
                 refit_fwd_ms=t_fwd, refit_fwd_nosave_ms=t_fwd_nosave, adjoint_ms=t_bwd,
                 adjoint_vs_fwd=t_bwd / t_fwd_nosave if t_fwd_nosave > 0 else None,
-                roofline=roof, kernels=kernels,
+                roofline=roof, step_hbm=step_hbm, kernels=kernels,
                 kernels_timing=f"separate pass of {n_prof} steps with every launch timed",
                 gpu_launches=launches,
                 graph_replay=graph_replay, track_quality=quality, merge_stage=merge,
