@@ -78,6 +78,12 @@ typedef struct {
   float tan_half;       /* tan of the sector half-opening angle             */
   float drift_length;   /* L (cm): |z| of the readout plane                  */
   float bz;             /* uniform field (T)                                 */
+  /* Native pad coordinates (tpc_clusters.pads = 1), or NULL: a cluster at
+   * pad position p (in pads, continuous) of row r lies at
+   * y = (p - pad_center[r]) * pad_width[r], computed in single precision on
+   * the fly by the kernels that read y. */
+  const float* pad_width;   /* host [n_rows] pad pitch (cm)                 */
+  const float* pad_center;  /* host [n_rows] pad position of y = 0 (pads)   */
 } tpc_geometry;
 
 /* Cut values of the method (the paper gives none; defaults by
@@ -137,6 +143,12 @@ typedef struct {
   const uint8_t* sector;  /* device [n] sector, < 36                        */
   const uint8_t* flags;   /* device [n] TPC_FLAG_* bits, or NULL            */
   const uint32_t* event;  /* device [n] event index < n_events, or NULL     */
+  int32_t pads;           /* 1: y holds native pad positions (pads), turned
+                             into cm with the geometry's pad tables on the
+                             fly (the next step the paper names after
+                             Sec. 4: tracking in native pad, row and time
+                             coordinates); the gradient grad_y of
+                             tpc_refit_backward is then per pad. 0: y in cm */
 } tpc_clusters;
 
 /* A set of tracks as CSR over cluster indices of the loaded batch.

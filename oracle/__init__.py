@@ -45,7 +45,8 @@ def build(force=False):
 
 class _Geom(C.Structure):
     _fields_ = [("row_x", C.POINTER(C.c_float)), ("n_rows", C.c_int32),
-                ("tan_half", C.c_float), ("drift_length", C.c_float), ("bz", C.c_float)]
+                ("tan_half", C.c_float), ("drift_length", C.c_float), ("bz", C.c_float),
+                ("pad_width", C.POINTER(C.c_float)), ("pad_center", C.POINTER(C.c_float))]
 
 
 class _Params(C.Structure):
@@ -74,7 +75,7 @@ class _Clusters(C.Structure):
                 ("y", C.POINTER(C.c_float)), ("z", C.POINTER(C.c_float)),
                 ("t", C.POINTER(C.c_double)), ("row", C.POINTER(C.c_uint8)),
                 ("sector", C.POINTER(C.c_uint8)), ("flags", C.POINTER(C.c_uint8)),
-                ("event", C.POINTER(C.c_uint32))]
+                ("event", C.POINTER(C.c_uint32)), ("pads", C.c_int32)]
 
 
 _lib = None
@@ -150,7 +151,8 @@ class Oracle:
     calib: object with vdrift, t0, spline ([36][2][8][8][8] float32)
     """
 
-    def __init__(self, ev, geo, params, calib, tf_start=None, spl_x0=85.0, spl_dx=160.0):
+    def __init__(self, ev, geo, params, calib, tf_start=None, spl_x0=85.0, spl_dx=160.0,
+                 pads=False):
         L = lib()
         self._keep = []
         k = self._keep
@@ -158,8 +160,14 @@ class Oracle:
         self.n_rows = int(len(geo.row_x))
         rowx = np.ascontiguousarray(geo.row_x, np.float32)
         k.append(rowx)
-        self.g = _Geom(rowx.ctypes.data_as(C.POINTER(C.c_float)), self.n_rows,
-                       float(geo.tan_half), float(geo.drift_length), float(geo.bz))
+        fp = lambda a: a.ctypes.data_as(C.POINTER(C.c_float)) if a is not None else None
+        pw = pc = None
+        if pads:
+            pw = np.ascontiguousarray(geo.pad_width, np.float32)
+            pc = np.ascontiguousarray(geo.pad_center, np.float32)
+            k.extend([pw, pc])
+        self.g = _Geom(fp(rowx), self.n_rows, float(geo.tan_half), float(geo.drift_length),
+                       float(geo.bz), fp(pw), fp(pc))
         p = _Params()
         for name, _t in _Params._fields_:
             v = params[name]
@@ -175,7 +183,8 @@ class Oracle:
         self.c = _Calib(float(calib.vdrift), float(calib.t0), tfs,
                         spl.ctypes.data_as(C.POINTER(C.c_float)), spl_x0, spl_dx)
         mode = 0 if ev.mode == "event" else 1
-        y = np.ascontiguousarray(ev.y, np.float32)
+        # with pads, the native pad positions take the place of y
+        y = np.ascontiguousarray(ev.pad if pads else ev.y, np.float32)
         z = np.ascontiguousarray(ev.z, np.float32) if mode == 0 else None
         t = np.ascontiguousarray(ev.t, np.float64) if mode == 1 else None
         row = np.ascontiguousarray(ev.row, np.uint8)
@@ -186,7 +195,8 @@ class Oracle:
         cast = lambda a, T: (a.ctypes.data_as(C.POINTER(T)) if a is not None else None)
         self.cl = _Clusters(self.n, mode, int(ev.n_events), cast(y, C.c_float),
                             cast(z, C.c_float), cast(t, C.c_double), cast(row, C.c_uint8),
-                            cast(sec, C.c_uint8), cast(flg, C.c_uint8), cast(evt, C.c_uint32))
+                            cast(sec, C.c_uint8), cast(flg, C.c_uint8), cast(evt, C.c_uint32),
+                            1 if pads else 0)
         self.mode = mode
         self.h = L.orc_create(C.byref(self.g), C.byref(self.p), C.byref(self.c),
                               C.byref(self.cl))

@@ -208,6 +208,8 @@ struct OrcGeom {
   float tan_half;
   float drift_length;
   float bz;
+  const float* pad_width;   // [n_rows] pad pitch (cm), or NULL
+  const float* pad_center;  // [n_rows] pad position of y = 0, or NULL
 };
 
 struct OrcParams {
@@ -256,6 +258,7 @@ struct OrcClusters {
   const uint8_t* sector;
   const uint8_t* flags;
   const uint32_t* event;
+  int32_t pads;           // 1: y holds native pad positions
 };
 
 }  // extern "C"
@@ -272,6 +275,8 @@ struct Ctx {
   OrcCalib c;
   OrcClusters cl;
   std::vector<float> rowx;
+  std::vector<float> padw, padc;  // pad pitch and centre per row
+  std::vector<float> ynat;        // y (cm) of native pad positions
   std::vector<float> spline;
   bool spline_active = false;
   std::vector<float> zs32;
@@ -621,6 +626,22 @@ Ctx* build_ctx(const OrcGeom* g, const OrcParams* p, const OrcCalib* cal, const 
   c->cl = *cl;
   c->rowx.assign(g->row_x, g->row_x + g->n_rows);
   c->g.row_x = c->rowx.data();
+  // native pad positions (the paper's next step after Sec. 4: tracking in
+  // native pad, row and time coordinates): y = (pad - centre) * pitch of the
+  // cluster's row, in single precision; every step then reads that y
+  if (cl->pads && g->pad_width && g->pad_center) {
+    c->padw.assign(g->pad_width, g->pad_width + g->n_rows);
+    c->padc.assign(g->pad_center, g->pad_center + g->n_rows);
+    c->ynat.resize(cl->n);
+    for (int64_t i = 0; i < cl->n; ++i) {
+      int r = cl->row[i];
+      float d = cl->y[i] - c->padc[r];
+      c->ynat[i] = d * c->padw[r];
+    }
+    c->cl.y = c->ynat.data();
+  } else {
+    c->cl.pads = 0;
+  }
   c->spline.assign((size_t)kNS * 2 * kSpl * kSpl * kSpl, 0.0f);
   if (cal->spline) {
     std::memcpy(c->spline.data(), cal->spline, c->spline.size() * sizeof(float));
@@ -1383,7 +1404,9 @@ void orc_refit_grad(void* ctx, int64_t nt, const uint32_t* track_start,
     g_tape.backward(chi2.id, g[k]);
     auto adj = [&](const Var& v) { return v.id >= 0 ? g_tape.adj[v.id] : 0.0; };
     for (size_t q = 0; q < n; ++q) {
-      grad_y[a + q] += adj(ly[q]);
+      // per pad for native input: dy/dpad is the row's pad pitch
+      double dyp = c.cl.pads ? (double)c.padw[c.cl.row[cluster_idx[a + q]]] : 1.0;
+      grad_y[a + q] += adj(ly[q]) * dyp;
       grad_zt[a + q] += adj(lz[q]);
     }
     grad_calib[0] += adj(vd);

@@ -32,7 +32,8 @@ class TpcError(RuntimeError):
 
 class tpc_geometry(C.Structure):
     _fields_ = [("n_rows", C.c_int32), ("row_x", C.POINTER(C.c_float)),
-                ("tan_half", C.c_float), ("drift_length", C.c_float), ("bz", C.c_float)]
+                ("tan_half", C.c_float), ("drift_length", C.c_float), ("bz", C.c_float),
+                ("pad_width", C.POINTER(C.c_float)), ("pad_center", C.POINTER(C.c_float))]
 
 
 class tpc_params(C.Structure):
@@ -57,7 +58,7 @@ class tpc_clusters(C.Structure):
     _fields_ = [("n", C.c_int64), ("mode", C.c_int32), ("n_events", C.c_int32),
                 ("tf_start", C.c_double), ("y", C.c_void_p), ("z", C.c_void_p),
                 ("t", C.c_void_p), ("row", C.c_void_p), ("sector", C.c_void_p),
-                ("flags", C.c_void_p), ("event", C.c_void_p)]
+                ("flags", C.c_void_p), ("event", C.c_void_p), ("pads", C.c_int32)]
 
 
 class tpc_kernel_stat(C.Structure):
@@ -178,8 +179,13 @@ class Tracker:
         self.stream = stream or torch.cuda.current_stream()
         self.row_x = np.ascontiguousarray(geo.row_x, np.float32)
         self.n_rows = int(self.row_x.size)
-        g = tpc_geometry(self.n_rows, self.row_x.ctypes.data_as(C.POINTER(C.c_float)),
-                         float(geo.tan_half), float(geo.drift_length), float(geo.bz))
+        fp = lambda a: a.ctypes.data_as(C.POINTER(C.c_float)) if a is not None else None
+        self.pad_w = (np.ascontiguousarray(geo.pad_width, np.float32)
+                      if getattr(geo, "pad_width", None) is not None else None)
+        self.pad_c = (np.ascontiguousarray(geo.pad_center, np.float32)
+                      if getattr(geo, "pad_center", None) is not None else None)
+        g = tpc_geometry(self.n_rows, fp(self.row_x), float(geo.tan_half),
+                         float(geo.drift_length), float(geo.bz), fp(self.pad_w), fp(self.pad_c))
         p = params_struct(params) if params is not None else None
         h = C.c_void_p()
         st = self.L.tpc_create(C.byref(g), C.byref(p) if p is not None else None,
@@ -221,12 +227,14 @@ class Tracker:
                       float(spl_x0), float(spl_dx))
         self._ck(self.L.tpc_set_calib(self.h, C.byref(c)), "tpc_set_calib")
 
-    def upload(self, ev):
-        """Copy an event's cluster arrays to device tensors."""
+    def upload(self, ev, pads=False):
+        """Copy an event's cluster arrays to device tensors; with pads, the
+        native pad positions (ev.pad) take the place of y."""
         torch = self.torch
         d = dict(mode=0 if ev.mode == "event" else 1, n_events=int(ev.n_events),
-                 tf_start=float(ev.tf_start))
-        d["y"] = torch.as_tensor(np.ascontiguousarray(ev.y, np.float32), device=self.dev)
+                 tf_start=float(ev.tf_start), pads=1 if pads else 0)
+        d["y"] = torch.as_tensor(np.ascontiguousarray(ev.pad if pads else ev.y, np.float32),
+                                 device=self.dev)
         d["z"] = (torch.as_tensor(np.ascontiguousarray(ev.z, np.float32), device=self.dev)
                   if d["mode"] == 0 else None)
         d["t"] = (torch.as_tensor(np.ascontiguousarray(ev.t, np.float64), device=self.dev)
@@ -248,7 +256,8 @@ class Tracker:
                          cl["t"].data_ptr() if cl.get("t") is not None else None,
                          cl["row"].data_ptr(), cl["sector"].data_ptr(),
                          cl["flags"].data_ptr() if cl.get("flags") is not None else None,
-                         cl["event"].data_ptr() if cl.get("event") is not None else None)
+                         cl["event"].data_ptr() if cl.get("event") is not None else None,
+                         int(cl.get("pads", 0)))
         self.n = n
         self._ck(self.L.tpc_load_clusters(self.h, C.byref(s)), "tpc_load_clusters")
         self.n_tracks = None

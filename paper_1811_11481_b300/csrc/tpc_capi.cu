@@ -17,6 +17,7 @@ struct tpc_ctx {
   tpc_params prm_c{};
   Cal cal{};
   float* d_rowx = nullptr;       // [TPC_MAX_ROWS] pad-row positions
+  float* d_pads = nullptr;       // [2 * TPC_MAX_ROWS] pad pitch and centre per row
   float* d_spline = nullptr;
   float* d_spl_bound = nullptr;
   uint32_t* d_err = nullptr;
@@ -336,6 +337,15 @@ tpc_status tpc_create(const tpc_geometry* geo, const tpc_params* params, void* s
   }
   chk(cudaMemcpy(ctx->d_rowx, geo->row_x, sizeof(float) * geo->n_rows, cudaMemcpyHostToDevice));
   g.rx = ctx->d_rowx;
+  if (geo->pad_width && geo->pad_center) {
+    chk(cudaMalloc(&ctx->d_pads, sizeof(float) * 2 * TPC_MAX_ROWS));
+    chk(cudaMemcpy(ctx->d_pads, geo->pad_width, sizeof(float) * geo->n_rows,
+                   cudaMemcpyHostToDevice));
+    chk(cudaMemcpy(ctx->d_pads + TPC_MAX_ROWS, geo->pad_center, sizeof(float) * geo->n_rows,
+                   cudaMemcpyHostToDevice));
+    g.pw = ctx->d_pads;
+    g.pc = ctx->d_pads + TPC_MAX_ROWS;
+  }
   chk(cudaMemsetAsync(ctx->d_spline, 0, sizeof(float) * TPC_SPLINE_SIZE, ctx->stream));
   chk(cudaMemsetAsync(ctx->d_spl_bound, 0, sizeof(float) * 4, ctx->stream));
   chk(cudaMemsetAsync(ctx->d_err, 0, sizeof(uint32_t), ctx->stream));
@@ -358,7 +368,7 @@ tpc_status tpc_create(const tpc_geometry* geo, const tpc_params* params, void* s
 void tpc_destroy(tpc_ctx* ctx) {
   if (!ctx) return;
   cudaStreamSynchronize(ctx->stream);
-  void* ptrs[] = {ctx->d_rowx, ctx->d_spline, ctx->d_spl_bound, ctx->d_err, ctx->d_cnt,
+  void* ptrs[] = {ctx->d_rowx, ctx->d_pads, ctx->d_spline, ctx->d_spl_bound, ctx->d_err, ctx->d_cnt,
                   ctx->fb.cnt, ctx->fb.row_start, ctx->fb.fill, ctx->fb.zmm, ctx->fb.zr,
                   ctx->fb.zs_in, ctx->fb.perm, ctx->fb.pyz, ctx->fb.gyz,
                   ctx->fb.gorig, ctx->fb.gseg, ctx->fb.bin_start, ctx->fb.big_list, ctx->fb.mid_list, ctx->fb.list_counts,
@@ -416,6 +426,9 @@ tpc_status tpc_load_clusters(tpc_ctx* ctx, const tpc_clusters* in) {
     return fail(ctx, TPC_ERR_ARG, "missing cluster array");
   if (in->n_events > 1 && in->n > 0 && !in->event)
     return fail(ctx, TPC_ERR_ARG, "event array required for n_events > 1");
+  if (in->pads != 0 && in->pads != 1) return fail(ctx, TPC_ERR_ARG, "pads must be 0 or 1");
+  if (in->pads && !ctx->geo.pw)
+    return fail(ctx, TPC_ERR_ARG, "native pad positions need the geometry's pad tables");
   ctx->cl.n = (int32_t)in->n;
   ctx->cl.mode = in->mode;
   ctx->cl.n_events = in->n_events;
@@ -426,6 +439,7 @@ tpc_status tpc_load_clusters(tpc_ctx* ctx, const tpc_clusters* in) {
   ctx->cl.sector = in->sector;
   ctx->cl.flags = in->flags;
   ctx->cl.event = in->event;
+  ctx->cl.pads = in->pads;
   ctx->cal.tf_start = in->mode == 1 ? in->tf_start : 0.0;
   ctx->K = in->n_events * TPC_N_SECTORS * ctx->geo.n_rows;
   return prepare_load(ctx, in->n_events);

@@ -211,7 +211,7 @@ __global__ void k_scatter(Geo g, ClIn cl, const uint32_t* row_start, const float
   int key = (e * kNS + s) * g.n_rows + r;
   uint32_t pos = row_start[key] + atomicAdd(&fill[key], 1u);
   perm[pos] = (uint32_t)i;
-  pyz[pos] = make_float2(cl.y[i], zs_in[i]);
+  pyz[pos] = make_float2(cluster_y(g, cl, i), zs_in[i]);
 }
 
 // Search-grid geometry of one (event, sector): tables of nb + 1 bin offsets
@@ -1298,7 +1298,7 @@ __global__ void k_calib(Geo g, Cal c, ClIn cl, const uint32_t* cnt, const uint32
   int r = cl.row[i], s = cl.sector[i];
   bool spl_on = c.spl_bound[2] > 0.0f;
   float a, b;
-  calibrate(g, c, spl_on, cl.mode, s, r, cl.y[i], cl.mode == 0 ? cl.z[i] : 0.0f,
+  calibrate(g, c, spl_on, cl.mode, s, r, cluster_y(g, cl, i), cl.mode == 0 ? cl.z[i] : 0.0f,
             cl.mode == 1 ? cl.t[i] : 0.0, that, a, b);
   yc[j] = a;
   zc[j] = b;

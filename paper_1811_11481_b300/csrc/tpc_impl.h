@@ -68,7 +68,16 @@ struct ClIn {
   const uint8_t* sector;
   const uint8_t* flags;
   const uint32_t* event;
+  int32_t pads;  // y holds native pad positions
 };
+
+// Local y (cm) of cluster i: the input y, or its native pad position turned
+// into cm with the row's pad pitch (single precision, two roundings).
+TPC_HD float cluster_y(const Geo& g, const ClIn& cl, int64_t i) {
+  if (!cl.pads) return cl.y[i];
+  int r = cl.row[i];
+  return (cl.y[i] - g.pc[r]) * g.pw[r];
+}
 
 // Buffers of the finder (device).
 struct FindBuf {

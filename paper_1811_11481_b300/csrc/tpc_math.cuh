@@ -31,6 +31,8 @@ struct Geo {
   float L;
   float bz;
   float kB;  // curvature per unit q/pT: 2.99792458e-3 * bz, rounded to float
+  const float* pw;  // [n_rows] pad pitch (cm), or null
+  const float* pc;  // [n_rows] pad position of y = 0, or null
 };
 
 struct Cal {

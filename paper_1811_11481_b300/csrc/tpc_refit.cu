@@ -341,7 +341,7 @@ __global__ void __launch_bounds__(kCgThreads) k_calib_grad(
       size_t wpos = ((size_t)wbase[sl >> 5] + (j - track_start[T])) * 32 + (sl & 31);
       int r = cl.row[i], s = cl.sector[i];
       float x = g.rx[r];
-      float y = cl.y[i];
+      float y = cluster_y(g, cl, i);
       float za = abs_z(g, c, cl.mode, cl.mode == 0 ? cl.z[i] : 0.0f,
                        cl.mode == 1 ? cl.t[i] : 0.0, s, that);
       by = gyc[wpos];
@@ -397,7 +397,7 @@ __global__ void __launch_bounds__(kCgThreads) k_calib_grad(
       float dDy_dz = dval_dw[0] * kS * dwdz, dDz_dz = dval_dw[1] * kS * dwdz;
       float gy = by * (1.0f + dDy_dy) + bz * dDz_dy;
       float gza = by * dDy_dz + bz * (1.0f + dDz_dz);
-      grad_y[j] = gy;
+      grad_y[j] = cl.pads ? gy * g.pw[r] : gy;  // per pad for native input
       if (cl.mode == 1) {
         double sg = s < 18 ? 1.0 : -1.0;
         grad_zt[j] = (float)((double)gza * (-sg * c.vdrift));

@@ -40,6 +40,8 @@ class Geometry:
     bz: np.float32               # Tesla
     n_sectors: int = N_SECTORS
     n_rows: int = N_ROWS
+    pad_width: np.ndarray | None = None   # float32[152] pad pitch (cm)
+    pad_center: np.ndarray | None = None  # float32[152] pad position of y = 0
 
     @property
     def tan_half64(self) -> float:
@@ -49,8 +51,21 @@ class Geometry:
 def geometry() -> Geometry:
     r = np.arange(N_ROWS, dtype=np.float64)
     row_x = (85.0 + r * 160.0 / 151.0).astype(np.float32)
-    return Geometry(row_x=row_x, tan_half=np.float32(math.tan(math.pi / 18.0)),
-                    drift_length=np.float32(250.0), bz=np.float32(0.5))
+    tan_half = np.float32(math.tan(math.pi / 18.0))
+    # native pads: 4 mm pitch on the inner 63 rows, 6 mm outside; pad 0 at the
+    # sector's lower edge, so y = 0 lies at ceil(x tan(10 deg) / pitch)
+    pad_width = np.where(r < 63, 0.4, 0.6).astype(np.float32)
+    pad_center = np.ceil(row_x.astype(np.float64) * float(tan_half) /
+                         pad_width).astype(np.float32)
+    return Geometry(row_x=row_x, tan_half=tan_half, drift_length=np.float32(250.0),
+                    bz=np.float32(0.5), pad_width=pad_width, pad_center=pad_center)
+
+
+def pad_positions(geo: Geometry, y, row):
+    """Native pad positions (pads, continuous) of local y (cm) on the rows."""
+    row = np.asarray(row, np.int64)
+    return (np.asarray(y, np.float64) / geo.pad_width[row] + geo.pad_center[row]).astype(
+        np.float32)
 
 
 def sector_alpha(k):
@@ -103,6 +118,7 @@ class Event:
     t_coll: np.ndarray            # float64 per particle collision time
     part: dict                    # per-particle arrays
     info: dict = field(default_factory=dict)
+    pad: np.ndarray | None = None  # float32 native pad positions of y
 
     @property
     def n(self) -> int:
@@ -371,7 +387,7 @@ def make_event(rng, geo: Geometry, parts: list, mode="event", t_colls=None,
         s_true=np.concatenate([cr["s"], np.full(nn, np.nan)]),
         tl_true=np.concatenate([cr["tl"], np.full(nn, np.nan)]),
         q_true=np.concatenate([cr["qpt"], np.full(nn, np.nan)]),
-        t_coll=allp["t_coll"], part=allp,
+        t_coll=allp["t_coll"], part=allp, pad=pad_positions(geo, y, row),
         info=dict(n_signal=n_sig, n_noise=nn, sigma=sigma,
                   larc=np.concatenate([cr["larc"], np.full(nn, np.nan)]),
                   z_meas=np.concatenate([z_m, np.full(nn, np.nan)]),

@@ -62,6 +62,8 @@ MUTANTS = {
  'refine_side': ("double sg = c.cl.sector[idx[0]] < 18 ? 1.0 : -1.0;", "double sg = 1.0;"),
  'refine_upper': ("if (hi - th > T) th = th + ((hi - th) - T);", "if (hi - th > T) th = th - ((hi - th) - T);"),
  'refine_lower': ("if (lo - th < 0.0) th = th + (lo - th);", "if (lo - th < 0.0) th = th - (lo - th);"),
+ 'native_pad_centre_sign': ("float d = cl->y[i] - c->padc[r];", "float d = cl->y[i] + c->padc[r];"),
+ 'native_grad_no_pitch': ("double dyp = c.cl.pads ? (double)c.padw[c.cl.row[cluster_idx[a + q]]] : 1.0;", "double dyp = 1.0;"),
  'merge_solve_operand': ("for (int k = 0; k < a; ++k) acc = acc - L[a][k] * w[k];", "for (int k = 0; k < a; ++k) acc = acc - L[a][k] * d[k];"),
 }
 

@@ -1039,3 +1039,57 @@ def test_refined_time_keeps_every_cluster_inside_the_drift_volume(geo, params):
             assert tau.min() >= -1e-9 and tau.max() <= T + 1e-9
             moved += est != np.clip(est, hi - T, lo)
     assert moved >= 50
+
+
+# ------------------------------------- native pad coordinates (next step)
+def test_native_pads_give_the_same_tracking_as_their_positions(geo, params):
+    """Native pad positions are turned into y = (pad - centre) * pitch of the
+    cluster's row in single precision: the oracle fed with pads finds the
+    same tracks and fits the same parameters as the oracle fed with those y
+    values (numpy float32), the pads reproduce the generator's y within float
+    rounding, and the gradient per pad is the gradient per cm times the
+    pitch, checked by finite differences of a pad."""
+    ev = synth.make_tiny(seed=52, n_tracks=150, central=True, mode="time", tf_start=1.0e6,
+                         n_coll=2, noise_frac=0.05)
+    row = ev.row.astype(np.int64)
+    y_pad = ((ev.pad - geo.pad_center[row]) * geo.pad_width[row]).astype(np.float32)
+    assert np.max(np.abs(y_pad - ev.y)) < 2e-5
+    on = _oracle(ev, geo, params, pads=True)
+    fn = on.find(prec=32)
+    y0 = ev.y.copy()
+    ev.y[:] = y_pad
+    os_ = _oracle(ev, geo, params)
+    fs = os_.find(prec=32)
+    for k in ("up", "dn", "starts"):
+        np.testing.assert_array_equal(fn[k], fs[k])
+    for k in ("track_start", "cluster_idx", "that"):
+        np.testing.assert_array_equal(fn["tracks"][k], fs["tracks"][k])
+    tr = fn["tracks"]
+    ts, ci, tt = tr["track_start"], tr["cluster_idx"], tr["that"]
+    rn = on.refit(ts, ci, tt, prec=64)
+    rs = os_.refit(ts, ci, tt, prec=64)
+    np.testing.assert_array_equal(rn["params"], rs["params"])
+    w = np.linspace(0.5, 1.5, ts.size - 1)
+    gn = on.refit_grad(ts, ci, tt, rn["seeds"], rn["rej"], w)
+    gs = os_.refit_grad(ts, ci, tt, rs["seeds"], rs["rej"], w)
+    np.testing.assert_allclose(gn[0], gs[0] * geo.pad_width[row[ci]], rtol=1e-12, atol=0)
+    np.testing.assert_array_equal(gn[1], gs[1])
+    ev.y[:] = y0
+    # finite differences of one pad position
+    k = int(np.argmax(np.abs(gn[0])))
+    i = ci[k]
+    e = 1e-3
+
+    def loss(p):
+        p0 = ev.pad[i]
+        ev.pad[i] = p
+        oo = _oracle(ev, geo, params, pads=True)
+        rr = oo.refit(ts, ci, tt, prec=64, seeds=rn["seeds"], rej=rn["rej"])
+        oo.close()
+        ev.pad[i] = p0
+        return float(np.sum(w * rr["chi2"]))
+
+    p0 = float(ev.pad[i])
+    fd = (loss(np.float32(p0 + e)) - loss(np.float32(p0 - e))) / (
+        float(np.float32(p0 + e)) - float(np.float32(p0 - e)))
+    assert abs(fd - gn[0][k]) < 2e-2 * abs(gn[0][k]), (fd, gn[0][k])
