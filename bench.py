@@ -45,6 +45,8 @@ def parse():
                     help="collisions of the time-frame workload (50: the headline frame)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--pads", action="store_true",
+                    help="give the clusters as native pad positions instead of y in cm")
     ap.add_argument("--no-merge", action="store_true",
                     help="skip the sector-merging stage measured after the timed region")
     ap.add_argument("--no-autotune", action="store_true",
@@ -406,7 +408,9 @@ def run_ours(args):
     torch.cuda.set_stream(work)
     tr = Tracker(geo, stream=work)
     tr.set_calib()
-    cl = tr.upload(ev)
+    cl = tr.upload(ev, pads=args.pads)
+    if args.pads:
+        cfg = dict(cfg, coordinates="native pad positions, turned into cm on the fly")
     L, h = tr.L, tr.h
     if args.tuning:
         tr.set_tuning(**json.loads(args.tuning))
