@@ -116,6 +116,9 @@ def lib():
         L.orc_merge.restype = C.c_int64
         L.orc_merge.argtypes = [vp, C.c_int, C.c_int64, vp, vp, vp, vp, vp, vp, vp, vp, vp,
                                 vp, vp, vp, vp]
+        L.orc_compress.argtypes = [vp, C.c_int64, vp, vp, vp, C.c_float, C.c_float, vp, vp, vp,
+                                   vp]
+        L.orc_decompress.argtypes = [vp, C.c_int64, vp, vp, C.c_float, C.c_float, vp, vp, vp, vp]
         L.orc_refine_time.argtypes = [vp, C.c_int, C.c_int64, vp, vp, vp, vp, vp, vp, vp]
         L.orc_rotate.restype = C.c_int
         L.orc_rotate.argtypes = [vp, vp, C.c_double, C.c_double, vp, vp, vp, vp]
@@ -364,6 +367,31 @@ class Oracle:
                               _p(np.ascontiguousarray(x, np.float64)),
                               _p(np.ascontiguousarray(status, np.int32)), _p(out))
         return out
+
+    # --- Sec. 5: track-model compression
+    def compress(self, track_start, cluster_idx, that, qy=0.01, qz=0.01):
+        """Residuals (ry, rz) of the track set's clusters and the decoded
+        clusters (dy, dz)."""
+        ts = np.ascontiguousarray(track_start, np.uint32)
+        ci = np.ascontiguousarray(cluster_idx, np.uint32)
+        nt = ts.size - 1
+        ry = np.zeros(ci.size, np.int32)
+        rz = np.zeros(ci.size, np.int32)
+        dy = np.zeros(ci.size, np.float32)
+        dz = np.zeros(ci.size, np.float32)
+        lib().orc_compress(self.h, nt, _p(ts), _p(ci), _p(np.ascontiguousarray(that, np.float64)),
+                           float(qy), float(qz), _p(ry), _p(rz), _p(dy), _p(dz))
+        return dict(ry=ry, rz=rz, dy=dy, dz=dz)
+
+    def decompress(self, track_start, cluster_idx, ry, rz, qy=0.01, qz=0.01):
+        ts = np.ascontiguousarray(track_start, np.uint32)
+        ci = np.ascontiguousarray(cluster_idx, np.uint32)
+        dy = np.zeros(ci.size, np.float32)
+        dz = np.zeros(ci.size, np.float32)
+        lib().orc_decompress(self.h, ts.size - 1, _p(ts), _p(ci), float(qy), float(qz),
+                             _p(np.ascontiguousarray(ry, np.int32)),
+                             _p(np.ascontiguousarray(rz, np.int32)), _p(dy), _p(dz))
+        return dy, dz
 
     # --- single-step helpers
     def propagate(self, state, x1, x2, cov=None):

@@ -1174,6 +1174,110 @@ double refine_time(const Ctx& c, const uint32_t* idx, size_t n, double that, con
   return th;
 }
 
+// ------------------------------------------- track-model compression
+// Sec. 5 (entropy reduction for the TPC data compression): only residuals
+// of the clusters attached to tracks are stored, with respect to the track
+// model, and the track is fitted in the distorted (uncalibrated) coordinate
+// system, so that calibration effects do not enter the residuals. Reading:
+// along each track (clusters in row order; the model restarts where the
+// sector frame changes) the first cluster of a run is stored as quantised
+// absolute (y, z); the second as the quantised difference to the first;
+// from then on a Kalman filter (the tracklet filter: straight-line two-point
+// seed through the first two decoded clusters, helix transport, update with
+// each decoded cluster) predicts (y, z) at the next row and the residual is
+// round((measured - predicted) / q). Every step uses the decoded cluster
+// (prediction + residual * q), so that a decoder running the same single-
+// precision arithmetic on the residuals reproduces the decoded clusters
+// exactly; where the transport fails the prediction is the previous decoded
+// cluster and the filter restarts there. Measured z in the time-frame mode:
+// the drift time turned into z with the track's collision time and v_drift,
+// without the distortion correction. Decisions in FP32.
+struct CompressIO {
+  const float* my;  // measured y, z per cluster of the track (encoder), or null
+  const float* mz;
+  int32_t* ry;      // residuals (out for the encoder, in for the decoder)
+  int32_t* rz;
+  float* dy;        // decoded clusters (out)
+  float* dz;
+};
+
+void code_track(const Ctx& c, const uint32_t* idx, size_t n, float qy, float qz,
+                bool encode, CompressIO& io) {
+  const float iqy = 1.0f / qy, iqz = 1.0f / qz;
+  const float sig2 = c.p.sigma * c.p.sigma;
+  Trk<float> st;
+  int frame = -1;
+  size_t j = 0;        // position inside the current frame run
+  bool model = false;  // the filter holds a state
+  float px = 0.0f, pyd = 0.0f, pzd = 0.0f;  // previous decoded cluster
+  for (size_t k = 0; k < n; ++k) {
+    int64_t i = idx[k];
+    int f = c.cl.sector[i] % 18;
+    float x = c.rowx[c.cl.row[i]];
+    if (f != frame) {
+      frame = f;
+      j = 0;
+      model = false;
+    }
+    float prey = 0.0f, prez = 0.0f;  // prediction
+    bool absolute = j == 0;
+    if (j >= 2 && model && propagate<float>(c, st, x)) {
+      prey = st.p[0];
+      prez = st.p[1];
+    } else if (!absolute) {
+      prey = pyd;
+      prez = pzd;
+      model = false;
+    }
+    int32_t ry, rz;
+    if (encode) {
+      ry = (int32_t)std::nearbyint((io.my[k] - prey) * iqy);
+      rz = (int32_t)std::nearbyint((io.mz[k] - prez) * iqz);
+      io.ry[k] = ry;
+      io.rz[k] = rz;
+    } else {
+      ry = io.ry[k];
+      rz = io.rz[k];
+    }
+    float dy = prey + (float)ry * qy;
+    float dz = prez + (float)rz * qz;
+    io.dy[k] = dy;
+    io.dz[k] = dz;
+    if (j >= 1) {
+      if (!model) {
+        // (re)start: seed through the previous and this decoded cluster,
+        // then the filter takes this cluster
+        seed_two_points<float>(c, st, px, pyd, pzd, x, dy, dz);
+        model = propagate<float>(c, st, x);
+      }
+      if (model) apply_update<float>(st, innovation<float>(st, dy, dz, sig2, sig2));
+    }
+    px = x;
+    pyd = dy;
+    pzd = dz;
+    ++j;
+  }
+}
+
+// Measured (distorted) coordinates of a track's clusters: y as given, z as
+// given (event mode) or from the drift time with the track's collision time.
+void distorted_coords(const Ctx& c, const uint32_t* idx, size_t n, double that,
+                      std::vector<float>& y, std::vector<float>& z) {
+  y.resize(n);
+  z.resize(n);
+  for (size_t k = 0; k < n; ++k) {
+    int64_t i = idx[k];
+    y[k] = c.cl.y[i];
+    if (c.cl.mode == 0) {
+      z[k] = c.cl.z[i];
+    } else {
+      double sg = c.cl.sector[i] < 18 ? 1.0 : -1.0;
+      double zeta = c.c.vdrift * ((c.cl.t[i] - c.c.t0) - that);
+      z[k] = (float)(sg * ((double)c.g.drift_length - zeta));
+    }
+  }
+}
+
 }  // namespace
 
 // ======================================================================
@@ -1448,6 +1552,33 @@ int64_t orc_merge(void* ctx, int prec, int64_t nt, const uint32_t* ts, const uin
     out_ts[m] = nc;
   }
   return m;
+}
+
+// Track-model compression (Sec. 5): residuals (ry, rz) [n_assigned] of the
+// track set's clusters and the decoded clusters (dy, dz).
+void orc_compress(void* ctx, int64_t nt, const uint32_t* ts, const uint32_t* ci,
+                  const double* that, float qy, float qz, int32_t* ry, int32_t* rz, float* dy,
+                  float* dz) {
+  Ctx& c = *(Ctx*)ctx;
+  std::vector<float> my, mz;
+  for (int64_t k = 0; k < nt; ++k) {
+    uint32_t a = ts[k], b = ts[k + 1];
+    distorted_coords(c, ci + a, b - a, that[k], my, mz);
+    CompressIO io{my.data(), mz.data(), ry + a, rz + a, dy + a, dz + a};
+    code_track(c, ci + a, b - a, qy, qz, true, io);
+  }
+}
+
+// The decoder: clusters (dy, dz) from the residuals, the rows and sectors.
+void orc_decompress(void* ctx, int64_t nt, const uint32_t* ts, const uint32_t* ci, float qy,
+                    float qz, const int32_t* ry, const int32_t* rz, float* dy, float* dz) {
+  Ctx& c = *(Ctx*)ctx;
+  for (int64_t k = 0; k < nt; ++k) {
+    uint32_t a = ts[k], b = ts[k + 1];
+    CompressIO io{nullptr, nullptr, const_cast<int32_t*>(ry) + a, const_cast<int32_t*>(rz) + a,
+                  dy + a, dz + a};
+    code_track(c, ci + a, b - a, qy, qz, false, io);
+  }
 }
 
 // Collision times of tracks refined from their fits (time-frame mode; the

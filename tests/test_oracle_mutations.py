@@ -64,6 +64,9 @@ MUTANTS = {
  'refine_lower': ("if (lo - th < 0.0) th = th + (lo - th);", "if (lo - th < 0.0) th = th - (lo - th);"),
  'native_pad_centre_sign': ("float d = cl->y[i] - c->padc[r];", "float d = cl->y[i] + c->padc[r];"),
  'native_grad_no_pitch': ("double dyp = c.cl.pads ? (double)c.padw[c.cl.row[cluster_idx[a + q]]] : 1.0;", "double dyp = 1.0;"),
+ 'compress_update_measured': ("if (model) apply_update<float>(st, innovation<float>(st, dy, dz, sig2, sig2));", "if (model) apply_update<float>(st, innovation<float>(st, encode ? io.my[k] : dy, dz, sig2, sig2));"),
+ 'compress_floor': ("ry = (int32_t)std::nearbyint((io.my[k] - prey) * iqy);", "ry = (int32_t)std::floor((io.my[k] - prey) * iqy);"),
+ 'compress_step_axis': ("float dz = prez + (float)rz * qz;", "float dz = prez + (float)rz * qy;"),
  'merge_solve_operand': ("for (int k = 0; k < a; ++k) acc = acc - L[a][k] * w[k];", "for (int k = 0; k < a; ++k) acc = acc - L[a][k] * d[k];"),
 }
 

@@ -1093,3 +1093,66 @@ def test_native_pads_give_the_same_tracking_as_their_positions(geo, params):
     fd = (loss(np.float32(p0 + e)) - loss(np.float32(p0 - e))) / (
         float(np.float32(p0 + e)) - float(np.float32(p0 - e)))
     assert abs(fd - gn[0][k]) < 2e-2 * abs(gn[0][k]), (fd, gn[0][k])
+
+
+# ------------------------------- track-model compression (Sec. 5)
+def _entropy(a):
+    _, cnt = np.unique(a, return_counts=True)
+    p = cnt / cnt.sum()
+    return float(-(p * np.log2(p)).sum())
+
+
+@pytest.mark.parametrize("mode", ["event", "time"])
+def test_compression_round_trip_is_exact_and_lossless_to_half_a_step(geo, params, mode):
+    """Residuals of the clusters of found tracks and of truth tracks across
+    sectors: a decoder running on the residuals alone (and the rows and
+    sectors) reproduces the encoder's decoded clusters bit for bit, and every
+    decoded cluster lies within half a quantisation step of the measured
+    (distorted) one; the residual entropy is far below that of the absolute
+    positions."""
+    ev = synth.make_tiny(seed=55, n_tracks=300, central=True, mode=mode, tf_start=1.0e6,
+                         n_coll=2, noise_frac=0.1)
+    o = _oracle(ev, geo, params)
+    tr = o.find(prec=32)["tracks"]
+    sets = [(tr["track_start"], tr["cluster_idx"], tr["that"])]
+    ts, ci, tc, _ = synth.truth_tracks(ev, 40, merged=True)
+    sets.append((ts, ci, tc))
+    cal = synth.nominal_calib()
+    for q, qz in ((0.01, 0.013), (0.037, 0.02)):
+        for ts, ci, tt in sets:
+            c = o.compress(ts, ci, tt, qy=q, qz=qz)
+            dy, dz = o.decompress(ts, ci, c["ry"], c["rz"], qy=q, qz=qz)
+            np.testing.assert_array_equal(dy, c["dy"])
+            np.testing.assert_array_equal(dz, c["dz"])
+            my = ev.y[ci]
+            if mode == "event":
+                mz = ev.z[ci]
+            else:
+                that = np.repeat(tt, np.diff(ts.astype(np.int64)))
+                sg = np.where(ev.sector[ci] < 18, 1.0, -1.0)
+                mz = sg * (float(geo.drift_length) - cal.vdrift * ((ev.t[ci] - cal.t0) - that))
+            assert np.max(np.abs(c["dy"] - my)) <= 0.5 * q * (1 + 1e-3) + 1e-5
+            assert np.max(np.abs(c["dz"] - mz)) <= 0.5 * qz * (1 + 1e-3) + 3e-5
+            first = np.zeros(ci.size, bool)
+            first[ts[:-1].astype(np.int64)] = True
+            if q == 0.01:
+                assert _entropy(c["ry"][~first]) < _entropy(np.rint(my / q)) - 4.0
+                assert _entropy(c["rz"][~first]) < _entropy(np.rint(mz / qz)) - 2.0
+
+
+def test_compression_residuals_of_exact_helices_are_small(geo, params):
+    """Clusters exactly on their helices: from the sixth cluster of a run on,
+    the filter's prediction misses by the quantisation noise of the decoded
+    clusters only, so the residuals are a few steps at most."""
+    ev = synth.make_tiny(seed=56, n_tracks=200, central=True, noise_frac=0.0, sigma=0.0)
+    ts, ci, tc, _ = synth.truth_tracks(ev, 40)
+    o = _oracle(ev, geo, params)
+    c = o.compress(ts, ci, tc, qy=0.01, qz=0.01)
+    pos = np.concatenate([np.arange(b - a) for a, b in zip(ts[:-1].astype(np.int64),
+                                                           ts[1:].astype(np.int64))])
+    # away from |sin(phi)| = 0.95, where the transport stops and the previous
+    # cluster becomes the prediction
+    late = (pos >= 5) & (np.abs(ev.s_true[ci]) < 0.9)
+    r = np.abs(np.concatenate([c["ry"][late], c["rz"][late]]))
+    assert late.sum() > 5000
+    assert np.percentile(r, 99) <= 4 and r.max() <= 8, (np.percentile(r, 99), r.max())
