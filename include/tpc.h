@@ -290,6 +290,29 @@ tpc_status tpc_merge_tracks_async(tpc_ctx* ctx, const float* params, const float
 tpc_status tpc_refine_time(tpc_ctx* ctx, const float* params, const float* x,
                            const int32_t* status, double* t_coll_out);
 
+/* Track-model compression of the context's track set (Sec. 5: only the
+ * residuals of the clusters attached to tracks are stored, the track being
+ * fitted in the distorted coordinate system). Along each track (clusters in
+ * order; the model restarts where the sector frame changes, sectors k and
+ * k + 18 sharing a frame) the first cluster of a run is stored as the
+ * quantised absolute (y, z), the second as the quantised difference to the
+ * first, and from then on a Kalman filter (straight-line seed through the
+ * first two decoded clusters, helix transport in the uniform field, update
+ * with each decoded cluster, errors params.sigma, seed covariance
+ * params.c0t) predicts (y, z) at the next row: residual =
+ * round-half-even((measured - predicted) / q). Decoded cluster = prediction
+ * + residual * q, the filter's input, so that a decoder running the same
+ * single-precision operations on the residuals reproduces the decoded
+ * clusters exactly. Measured coordinates: y (cm; from the pad position
+ * with native pads) and z as given (mode 0) or from the drift time with the
+ * track's collision time and v_drift, without distortion correction (mode
+ * 1). Where the transport fails the prediction is the previous decoded
+ * cluster and the filter restarts. Outputs per assigned cluster in track
+ * order (device, caller-owned, [n_assigned]): ry, rz (residuals in steps of
+ * qy, qz cm), dy, dz (decoded clusters, may be NULL). Asynchronous. */
+tpc_status tpc_compress_tracks(tpc_ctx* ctx, float qy, float qz, int32_t* ry, int32_t* rz,
+                               float* dy, float* dz);
+
 /* Adjoint of the last saved refit (not in the paper; TPC_ERR_STATE if the
  * calibration was set again after that refit): for
  * L = sum_k dL_dchi2[k] * chi2_k with chi2_k the pass-3 chi2, writes

@@ -99,6 +99,7 @@ _PROTOS = {
     "tpc_merge_tracks": (C.c_int, [C.c_void_p] + [C.c_void_p] * 6 + [C.POINTER(tpc_tracks)]),
     "tpc_merge_tracks_async": (C.c_int, [C.c_void_p] + [C.c_void_p] * 6),
     "tpc_refine_time": (C.c_int, [C.c_void_p] + [C.c_void_p] * 4),
+    "tpc_compress_tracks": (C.c_int, [C.c_void_p, C.c_float, C.c_float] + [C.c_void_p] * 4),
     "tpc_sync": (C.c_int, [C.c_void_p]),
     "tpc_get_counts": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
                                  C.POINTER(C.c_int64)]),
@@ -384,6 +385,19 @@ class Tracker:
         self._ck(self.L.tpc_merge_tracks_async(self.h, *[_ptr(a) for a in ins], _ptr(next_out),
                                                _ptr(link_chi2)), "tpc_merge_tracks_async")
         self.n_tracks = None
+
+    def compress(self, qy=0.01, qz=0.01):
+        """Track-model residuals (ry, rz) and decoded clusters (dy, dz) of the
+        current track set, per assigned cluster in track order."""
+        torch = self.torch
+        na = self.n_assigned if self.n_assigned is not None else self.counts()[1]
+        i32 = lambda: torch.empty(max(na, 1), dtype=torch.int32, device=self.dev)
+        f32 = lambda: torch.empty(max(na, 1), dtype=torch.float32, device=self.dev)
+        out = dict(ry=i32(), rz=i32(), dy=f32(), dz=f32())
+        self._ck(self.L.tpc_compress_tracks(self.h, float(qy), float(qz), _ptr(out["ry"]),
+                                            _ptr(out["rz"]), _ptr(out["dy"]), _ptr(out["dz"])),
+                 "tpc_compress_tracks")
+        return {k: v[:na] for k, v in out.items()}
 
     def refine_time(self, fit):
         """Refine the collision times of the current track set from its refit

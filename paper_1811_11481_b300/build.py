@@ -1,6 +1,6 @@
 """Build libtpc.so in-tree with nvcc for sm_103a (B300).
 
-The finder and merger translation units are compiled with -fmad=false: their decisions are
+The finder, merger and compression units are compiled with -fmad=false: their decisions are
 taken on single-precision values with one rounding per written operation.
 The refit unit (checked against the FP64 oracle within a tolerance) is
 compiled with --use_fast_math: fused multiply-adds and approximate
@@ -27,6 +27,7 @@ UNITS = {
     "tpc_capi.cu": [],
     "tpc_noalloc.cu": ["--use_fast_math"],
     "tpc_merge.cu": ["-fmad=false"],
+    "tpc_compress.cu": ["-fmad=false"],
 }
 
 

@@ -738,6 +738,19 @@ tpc_status tpc_merge_tracks(tpc_ctx* ctx, const float* params, const float* cov,
   return TPC_OK;
 }
 
+tpc_status tpc_compress_tracks(tpc_ctx* ctx, float qy, float qz, int32_t* ry, int32_t* rz,
+                               float* dy, float* dz) {
+  if (!ctx) return TPC_ERR_ARG;
+  if (!ctx->tracks_valid) return fail(ctx, TPC_ERR_STATE, "no track set");
+  if (!ry || !rz) return fail(ctx, TPC_ERR_ARG, "null residual output");
+  if (!(qy > 0.0f) || !(qz > 0.0f) || !std::isfinite(qy) || !std::isfinite(qz))
+    return fail(ctx, TPC_ERR_ARG, "quantisation steps must be positive");
+  launch_compress(&ctx->prof, ctx->geo, ctx->cal, ctx->cl, ctx->prm, qy, qz, ctx->tb.cap_tr,
+                  ctx->d_cnt, ctx->tb, ry, rz, dy, dz, ctx->stream);
+  CK(cudaGetLastError());
+  return TPC_OK;
+}
+
 tpc_status tpc_refine_time(tpc_ctx* ctx, const float* params, const float* x,
                            const int32_t* status, double* t_coll_out) {
   if (!ctx) return TPC_ERR_ARG;

@@ -321,6 +321,11 @@ void launch_merge(Prof* P, const Geo& g, const Params& p, const Cal& c, const Cl
                   int64_t cap_n, bool copy, TrackBuf& tb, MergeBuf& mb, const float* params,
                   const float* cov, const float* x, const int32_t* status, int32_t* next_out,
                   float* link_chi2, uint32_t* cnt, uint32_t* err, cudaStream_t s);
+// launcher (tpc_compress.cu): residuals of the track set's clusters against
+// the track model (and the decoded clusters; dy, dz may be null).
+void launch_compress(Prof* P, const Geo& g, const Cal& c, const ClIn& cl, const Params& p,
+                     float qy, float qz, int64_t cap_tr, const uint32_t* cnt, const TrackBuf& tb,
+                     int32_t* ry, int32_t* rz, float* dy, float* dz, cudaStream_t s);
 // Collision times of the track set refined from its fit (time-frame mode),
 // written to tb.t_coll and t_out (may be null).
 void launch_refine_time(Prof* P, const Geo& g, const Cal& c, const ClIn& cl, int64_t cap_tr,
