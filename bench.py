@@ -48,7 +48,8 @@ def parse():
     ap.add_argument("--pads", action="store_true",
                     help="give the clusters as native pad positions instead of y in cm")
     ap.add_argument("--no-merge", action="store_true",
-                    help="skip the sector-merging stage measured after the timed region")
+                    help="skip the merging and compression stages measured after the "
+                         "timed region")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default launch shapes instead of tuning them on the workload")
     ap.add_argument("--tuning", default=None,
@@ -390,6 +391,49 @@ def merge_chain(tr, cl, n, flush, stream, steps):
                      "refinement, refit; L2 flushed before each replay")
 
 
+def _entropy_bits(a):
+    _, c = np.unique(a, return_counts=True)
+    p = c / c.sum()
+    return float(-(p * np.log2(p)).sum())
+
+
+def compression_stage(tr, cl, flush, stream, reps=5, qy=0.01, qz=0.01):
+    """Track-model compression of the found tracks (Sec. 5): the encoder
+    kernel timed with CUDA events (after the headline's timed region), and
+    the empirical entropy of the residuals against that of the quantised
+    absolute positions."""
+    import torch
+    tr.load(cl)
+    tr.find()
+    tr.compress(qy, qz)                                  # allocates
+    acc = 0.0
+    for _ in range(reps):
+        flush.fill_(1.0)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        out = tr.compress(qy, qz)
+        b.record(stream)
+        b.synchronize()
+        acc += a.elapsed_time(b)
+    ms = acc / reps
+    ry, rz = out["ry"].cpu().numpy(), out["rz"].cpu().numpy()
+    dy, dz = out["dy"].cpu().numpy(), out["dz"].cpu().numpy()
+    ts = tr.tracks()["track_start"].cpu().numpy().astype(np.int64)
+    first = np.zeros(ry.size, bool)
+    first[ts[:-1]] = True
+    res_bits = _entropy_bits(ry[~first]) + _entropy_bits(rz[~first])
+    abs_bits = _entropy_bits(np.rint(dy / qy).astype(np.int64)) + \
+        _entropy_bits(np.rint(dz / qz).astype(np.int64))
+    na = int(ry.size)
+    return dict(ms=ms, assigned_clusters=na, clusters_per_s=na / (ms / 1000.0),
+                step_cm=[qy, qz], residual_bits_per_cluster=res_bits,
+                absolute_bits_per_cluster=abs_bits, entropy_ratio=abs_bits / res_bits,
+                note="k_compress on the found tracks (one thread per track), CUDA events, "
+                     "L2 flushed; empirical entropies of the (y, z) residuals after the first "
+                     "cluster of each track and of the quantised absolute positions")
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -672,6 +716,7 @@ def run_ours(args):
                          "their launches per step; the row sorts together once) over the "
                          "step time, of measured HBM copy bandwidth")
 
+    compression = None if args.no_merge else compression_stage(tr, cl, flush, stream)
     merge = None if args.no_merge else merge_stage(tr, cl, ev, flush, stream)
     if merge is not None:
         merge["chain"] = merge_chain(tr, cl, n, flush, stream, min(args.steps, 50))
@@ -696,6 +741,7 @@ def run_ours(args):
                 kernels_timing=f"separate pass of {n_prof} steps with every launch timed",
                 gpu_launches=launches,
                 graph_replay=graph_replay, track_quality=quality, merge_stage=merge,
+                compression=compression,
                 clocks=clk, e2e=e2e, cpu_baseline=cpu)
     if rank == 0:
         print(json.dumps(line))
