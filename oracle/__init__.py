@@ -46,7 +46,8 @@ def build(force=False):
 class _Geom(C.Structure):
     _fields_ = [("row_x", C.POINTER(C.c_float)), ("n_rows", C.c_int32),
                 ("tan_half", C.c_float), ("drift_length", C.c_float), ("bz", C.c_float),
-                ("pad_width", C.POINTER(C.c_float)), ("pad_center", C.POINTER(C.c_float))]
+                ("pad_width", C.POINTER(C.c_float)), ("pad_center", C.POINTER(C.c_float)),
+                ("field", C.POINTER(C.c_float))]
 
 
 class _Params(C.Structure):
@@ -120,6 +121,9 @@ def lib():
                                    vp]
         L.orc_decompress.argtypes = [vp, C.c_int64, vp, vp, C.c_float, C.c_float, vp, vp, vp, vp]
         L.orc_refine_time.argtypes = [vp, C.c_int, C.c_int64, vp, vp, vp, vp, vp, vp, vp]
+        L.orc_propagate_field.restype = C.c_int
+        L.orc_propagate_field.argtypes = [vp, vp, C.c_double, C.c_double, C.c_double, vp, vp,
+                                          vp]
         L.orc_rotate.restype = C.c_int
         L.orc_rotate.argtypes = [vp, vp, C.c_double, C.c_double, vp, vp, vp, vp]
         L.orc_dca_z.restype = C.c_double
@@ -155,7 +159,7 @@ class Oracle:
     """
 
     def __init__(self, ev, geo, params, calib, tf_start=None, spl_x0=85.0, spl_dx=160.0,
-                 pads=False):
+                 pads=False, field=None):
         L = lib()
         self._keep = []
         k = self._keep
@@ -169,8 +173,13 @@ class Oracle:
             pw = np.ascontiguousarray(geo.pad_width, np.float32)
             pc = np.ascontiguousarray(geo.pad_center, np.float32)
             k.extend([pw, pc])
+        fld = None
+        if field is not None:
+            fld = np.ascontiguousarray(field, np.float32).reshape(-1)
+            assert fld.size == 30
+            k.append(fld)
         self.g = _Geom(fp(rowx), self.n_rows, float(geo.tan_half), float(geo.drift_length),
-                       float(geo.bz), fp(pw), fp(pc))
+                       float(geo.bz), fp(pw), fp(pc), fp(fld))
         p = _Params()
         for name, _t in _Params._fields_:
             v = params[name]
@@ -422,6 +431,16 @@ class Oracle:
         ok = lib().orc_rotate(self.h, _p(s), float(x), float(dalpha), _p(cv), _p(so), _p(xo),
                               _p(co))
         return (so, float(xo[0]), co) if ok else (None, None, None)
+
+    def propagate_field(self, state, x1, x2, alpha, cov=None):
+        """Transport in the full field in the frame rotated by alpha."""
+        s = np.ascontiguousarray(state, np.float64)
+        cv = np.eye(5) if cov is None else np.ascontiguousarray(cov, np.float64)
+        so = np.empty(5)
+        co = np.empty((5, 5))
+        ok = lib().orc_propagate_field(self.h, _p(s), float(x1), float(x2), float(alpha),
+                                       _p(cv), _p(so), _p(co))
+        return (so, co) if ok else (None, None)
 
     def jacobian(self, state, x1, x2):
         so = np.empty(5)

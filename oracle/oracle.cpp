@@ -210,6 +210,7 @@ struct OrcGeom {
   float bz;
   const float* pad_width;   // [n_rows] pad pitch (cm), or NULL
   const float* pad_center;  // [n_rows] pad position of y = 0, or NULL
+  const float* field;       // [3][10] (Bx, By, Bz) polynomial coefficients, or NULL
 };
 
 struct OrcParams {
@@ -276,6 +277,7 @@ struct Ctx {
   OrcClusters cl;
   std::vector<float> rowx;
   std::vector<float> padw, padc;  // pad pitch and centre per row
+  std::vector<double> field;      // [3][10] field coefficients (empty: uniform bz)
   std::vector<float> ynat;        // y (cm) of native pad positions
   std::vector<float> spline;
   bool spline_active = false;
@@ -452,8 +454,9 @@ template <class R> void cov_transform(const R J[5][5], R C[5][5]) {
 }
 
 // Exact helix transport to the plane x2 and its analytic Jacobian.
-template <class R> bool propagate(const Ctx& c, Trk<R>& st, R x2, R* Jout = nullptr) {
-  const R kB = kB_of<R>(c);
+template <class R>
+bool propagate(const Ctx& c, Trk<R>& st, R x2, R* Jout = nullptr, const R* kB_local = nullptr) {
+  const R kB = kB_local ? *kB_local : kB_of<R>(c);
   R dx = x2 - st.x;
   R y = st.p[0], z = st.p[1], s = st.p[2], t = st.p[3], q = st.p[4];
   R kap = kB * q;
@@ -504,6 +507,91 @@ template <class R> bool propagate(const Ctx& c, Trk<R>& st, R x2, R* Jout = null
   st.p[1] = z + t * l;
   st.p[2] = s2;
   st.x = x2;
+  return true;
+}
+
+// ------------------------------------------------ the full field (Sec. 3)
+// The final fit takes the Bx and By components of the field into account and
+// a three-dimensional polynomial approximation of the field. Here the field
+// is given as quadratic polynomials of (Bx, By, Bz) in the global
+// coordinates in metres (monomials 1, X, Y, Z, X^2, XY, XZ, Y^2, YZ, Z^2).
+template <class R> void field_at(const Ctx& c, R X, R Y, R Z, R B[3]) {
+  R x = X * R(0.01), y = Y * R(0.01), z = Z * R(0.01);
+  const R m[10] = {R(1), x, y, z, x * x, x * y, x * z, y * y, y * z, z * z};
+  for (int k = 0; k < 3; ++k) {
+    R acc = R(0);
+    for (int i = 0; i < 10; ++i) acc = acc + R(c.field[k * 10 + i]) * m[i];
+    B[k] = acc;
+  }
+}
+
+// Transport in the full field from the state's x to x2 in the frame rotated
+// by alpha: the equations of motion of the direction u (unit vector) with x
+// as the variable, dy/dx = u_y / u_x, dz/dx = u_z / u_x,
+// du/dx = k (q/p) (u x B) / u_x, integrated by fourth-order Runge-Kutta in
+// steps of at most 0.5 cm (about 1e-6 cm from the exact helix over 30 cm at
+// pT = 0.14 GeV); q/p is conserved, q/pT = (q/p) / |u_T|. The
+// covariance is transported with the helix Jacobian of the field's Bz at
+// the start point (a reading: the paper does not give the Jacobian used).
+// Fails where u_x would not stay positive or |sin(phi)| reaches s_max.
+template <class R>
+bool propagate_field(const Ctx& c, Trk<R>& st, R x2, double alpha) {
+  const R ca = R(std::cos(alpha)), sa = R(std::sin(alpha));
+  R Bs[3];
+  field_at<R>(c, st.x * ca - st.p[0] * sa, st.x * sa + st.p[0] * ca, st.p[1], Bs);
+  R kBl = R(kCLight) * Bs[2];
+  Trk<R> hx = st;
+  if (!propagate<R>(c, hx, x2, nullptr, &kBl)) return false;
+  R s = st.p[2], t = st.p[3], q = st.p[4];
+  R cl = R(1) / sqrt_(R(1) + t * t);
+  R cf = sqrt_(R(1) - s * s);
+  R v[5] = {st.p[0], st.p[1], cf * cl, s * cl, t * cl};
+  R kq = R(kCLight) * (q * cl);
+  R dx = x2 - st.x;
+  int ns = (int)std::ceil(std::fabs(val(dx)) / 0.5);
+  if (ns < 1) ns = 1;
+  R h = dx / R((double)ns);
+  R x = st.x;
+  auto deriv = [&](R xx, const R w[5], R d[5]) {
+    if (!(w[2] > R(0))) return false;
+    R B[3];
+    field_at<R>(c, xx * ca - w[0] * sa, xx * sa + w[0] * ca, w[1], B);
+    R b0 = B[0] * ca + B[1] * sa, b1 = -(B[0] * sa) + B[1] * ca, b2 = B[2];
+    R iu = R(1) / w[2];
+    R f = kq * iu;
+    d[0] = w[3] * iu;
+    d[1] = w[4] * iu;
+    d[2] = f * (w[3] * b2 - w[4] * b1);
+    d[3] = f * (w[4] * b0 - w[2] * b2);
+    d[4] = f * (w[2] * b1 - w[3] * b0);
+    return true;
+  };
+  for (int i = 0; i < ns; ++i) {
+    R k1[5], k2[5], k3[5], k4[5], w[5];
+    if (!deriv(x, v, k1)) return false;
+    for (int j = 0; j < 5; ++j) w[j] = v[j] + (h * R(0.5)) * k1[j];
+    if (!deriv(x + h * R(0.5), w, k2)) return false;
+    for (int j = 0; j < 5; ++j) w[j] = v[j] + (h * R(0.5)) * k2[j];
+    if (!deriv(x + h * R(0.5), w, k3)) return false;
+    for (int j = 0; j < 5; ++j) w[j] = v[j] + h * k3[j];
+    if (!deriv(x + h, w, k4)) return false;
+    for (int j = 0; j < 5; ++j)
+      v[j] = v[j] + (h / R(6)) * (k1[j] + R(2) * k2[j] + R(2) * k3[j] + k4[j]);
+    x = (i == ns - 1) ? x2 : x + h;
+  }
+  R un = sqrt_(v[2] * v[2] + v[3] * v[3] + v[4] * v[4]);
+  R ux = v[2] / un, uy = v[3] / un, uz = v[4] / un;
+  R rho = sqrt_(ux * ux + uy * uy);
+  R s2 = uy / rho;
+  if (!(ux > R(0)) || !(abs_(s2) < R(c.p.s_max))) return false;
+  st.p[0] = v[0];
+  st.p[1] = v[1];
+  st.p[2] = s2;
+  st.p[3] = uz / rho;
+  st.p[4] = (q * cl) / rho;
+  st.x = x2;
+  for (int i = 0; i < 5; ++i)
+    for (int j = 0; j < 5; ++j) st.C[i][j] = hx.C[i][j];
   return true;
 }
 
@@ -626,6 +714,7 @@ Ctx* build_ctx(const OrcGeom* g, const OrcParams* p, const OrcCalib* cal, const 
   c->cl = *cl;
   c->rowx.assign(g->row_x, g->row_x + g->n_rows);
   c->g.row_x = c->rowx.data();
+  if (g->field) c->field.assign(g->field, g->field + 30);
   // native pad positions (the paper's next step after Sec. 4: tracking in
   // native pad, row and time coordinates): y = (pad - centre) * pitch of the
   // cluster's row, in single precision; every step then reads that y
@@ -937,7 +1026,9 @@ RefitOut refit_core(const Ctx& c, const std::vector<R>& x, const std::vector<R>&
         }
         cur_alpha = (*alpha)[i];
       }
-      if (!propagate<R>(c, st, x[i])) {
+      bool moved = c.field.empty() ? propagate<R>(c, st, x[i])
+                                   : propagate_field<R>(c, st, x[i], cur_alpha);
+      if (!moved) {
         o.status = 1;
         *chi2_out = R(0);
         return o;
@@ -973,7 +1064,8 @@ inline std::vector<double> track_alpha(const Ctx& c, const uint32_t* idx, size_t
   std::vector<double> al;
   bool multi = false;
   for (size_t k = 1; k < n; ++k) multi = multi || c.cl.sector[idx[k]] != c.cl.sector[idx[0]];
-  if (!multi) return al;
+  // the full field needs the frame of every step, one sector or several
+  if (!multi && c.field.empty()) return al;
   al.resize(n);
   for (size_t k = 0; k < n; ++k) al[k] = sector_alpha(c.cl.sector[idx[k]]);
   return al;
@@ -1628,6 +1720,23 @@ int orc_refit_points(void* ctx, int64_t n, const double* x, const double* y, con
   *chi2 = o.chi2;
   *ndf = o.ndf;
   return o.status;
+}
+
+// Transport in the full field (state and covariance, in the frame alpha).
+int orc_propagate_field(void* ctx, const double* state_in, double x1, double x2, double alpha,
+                        const double* cov_in, double* state_out, double* cov_out) {
+  Ctx& c = *(Ctx*)ctx;
+  if (c.field.empty()) return 0;
+  Trk<double> st;
+  for (int i = 0; i < 5; ++i) st.p[i] = state_in[i];
+  st.x = x1;
+  for (int i = 0; i < 5; ++i)
+    for (int j = 0; j < 5; ++j) st.C[i][j] = cov_in[i * 5 + j];
+  if (!propagate_field<double>(c, st, x2, alpha)) return 0;
+  for (int i = 0; i < 5; ++i) state_out[i] = st.p[i];
+  for (int i = 0; i < 5; ++i)
+    for (int j = 0; j < 5; ++j) cov_out[i * 5 + j] = st.C[i][j];
+  return 1;
 }
 
 // Single-step helpers exposed for closed-form checks of the track model.

@@ -14,6 +14,6 @@ from .events import (  # noqa: F401
     Geometry, Calib, Event, geometry, nominal_calib,
     gen_particles_single_sector, gen_particles_central, make_event,
     make_single_sector, make_central, make_timeframe, make_batched,
-    make_adjoint, make_tiny, random_distortion, truth_tracks, pad_positions,
+    make_adjoint, make_tiny, random_distortion, truth_tracks, pad_positions, sector_alpha,
     CONFIGS, make_config,
 )

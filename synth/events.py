@@ -302,12 +302,15 @@ def random_distortion(rng, max_abs=1.0):
 def make_event(rng, geo: Geometry, parts: list, mode="event", t_colls=None,
                noise_frac=0.0, calib: Calib | None = None, sigma=0.1,
                tf_start=0.0, keep_sectors=None, event_ids=None,
-               distortion_iters=8):
+               distortion_iters=8, field=None):
     """Build one batch of clusters.
 
     parts: list of particle dicts, one per collision (event).
     t_colls: collision time per collision (time mode).
     event_ids: batch-event index per collision (default: all 0).
+    field: coefficients [3][10] of a non-uniform field (synth/field.py):
+    particles are traced through it (outgoing legs only) instead of
+    intersecting helices in the uniform geo.bz.
     """
     calib = calib or nominal_calib()
     ncol = len(parts)
@@ -320,7 +323,11 @@ def make_event(rng, geo: Geometry, parts: list, mode="event", t_colls=None,
     col_of = np.repeat(np.arange(ncol), sizes)
     allp["t_coll"] = np.asarray(t_colls, np.float64)[col_of]
     allp["event"] = np.asarray(event_ids)[col_of]
-    cr = _crossings(geo, allp)
+    if field is None:
+        cr = _crossings(geo, allp)
+    else:
+        from .field import crossings_in_field
+        cr = crossings_in_field(geo, allp, field)
     if keep_sectors is not None:
         m = np.isin(cr["sector"], np.asarray(keep_sectors))
         cr = {k: v[m] for k, v in cr.items()}
@@ -534,7 +541,7 @@ def make_adjoint(seed=4, n_events=10, n_tracks=10000, tf_start=1.0e6,
 
 
 def make_tiny(seed=5, n_tracks=20, sectors=(0,), noise_frac=0.0, mode="event",
-              central=False, calib=None, tf_start=0.0, n_coll=1, sigma=0.1):
+              central=False, calib=None, tf_start=0.0, n_coll=1, sigma=0.1, field=None):
     """Small cases for tests: a few tracks in chosen sectors."""
     rng = np.random.default_rng(seed)
     geo = geometry()
@@ -554,7 +561,8 @@ def make_tiny(seed=5, n_tracks=20, sectors=(0,), noise_frac=0.0, mode="event",
     t_colls = tf_start + 10.0 * (1.0 + np.arange(n_coll)) if mode == "time" else None
     ev = make_event(rng, geo, parts, mode=mode, t_colls=t_colls,
                     noise_frac=noise_frac, calib=calib, tf_start=tf_start,
-                    keep_sectors=None if central else list(sectors), sigma=sigma)
+                    keep_sectors=None if central else list(sectors), sigma=sigma,
+                    field=field)
     return ev
 
 

@@ -1156,3 +1156,89 @@ def test_compression_residuals_of_exact_helices_are_small(geo, params):
     r = np.abs(np.concatenate([c["ry"][late], c["rz"][late]]))
     assert late.sum() > 5000
     assert np.percentile(r, 99) <= 4 and r.max() <= 8, (np.percentile(r, 99), r.max())
+
+
+# -------------------------------------------- full field (Sec. 3)
+def _field_event(eps, seed, n=300):
+    from synth.field import solenoid_field
+    f = solenoid_field(eps=eps)
+    ev = synth.make_tiny(seed=seed, n_tracks=n, central=True, sigma=0.0, field=f)
+    ev.y[:] = ev.y_true.astype(np.float32)
+    ev.z[:] = ev.z_true.astype(np.float32)
+    return ev, f
+
+
+def test_field_transport_in_a_uniform_field_is_the_helix(geo, params):
+    """With no inhomogeneity the Runge-Kutta transport in the field gives the
+    exact helix and its covariance transport."""
+    ev, f = _field_event(0.0, 61, n=20)
+    o = _oracle(ev, geo, params, field=f)
+    rng = np.random.default_rng(4)
+    n_ok = 0
+    for _ in range(40):
+        s0 = np.array([rng.uniform(-20, 20), rng.uniform(-100, 100), rng.uniform(-0.6, 0.6),
+                       rng.uniform(-1, 1), rng.uniform(-3, 3)])
+        x0 = rng.uniform(90, 200)
+        x1 = x0 + rng.uniform(-30, 30)
+        A = rng.normal(size=(5, 5))
+        C = A @ A.T + np.eye(5)
+        a, ca = o.propagate_field(s0, x0, x1, rng.uniform(0, 2 * math.pi), C)
+        b, cb = o.propagate(s0, x0, x1, C)
+        if b is None:
+            continue
+        n_ok += 1
+        np.testing.assert_allclose(a, b, rtol=0, atol=1e-8)
+        np.testing.assert_allclose(ca, cb, rtol=1e-12, atol=1e-12)
+    assert n_ok >= 30
+
+
+def test_field_transport_follows_the_traced_particles(geo, params):
+    """In a non-uniform field (4 % solenoid-like inhomogeneity with radial
+    components) the transport from one row crossing of a traced particle to
+    a later one reproduces the tracer's crossing (the generator integrates
+    the Lorentz force in arc length in the global frame, an independent
+    implementation)."""
+    ev, f = _field_event(0.04, 62)
+    o = _oracle(ev, geo, params, field=f)
+    truth = np.stack([ev.y_true, ev.z_true, ev.s_true, ev.tl_true, ev.q_true], 1)
+    checked = 0
+    worst = np.zeros(5)
+    for s in np.unique(ev.segment[ev.segment >= 0])[:400]:
+        idx = np.nonzero(ev.segment == s)[0]
+        idx = idx[np.argsort(ev.row[idx])]
+        if idx.size < 30:
+            continue
+        i, j = idx[2], idx[-3]
+        al = synth.sector_alpha(ev.sector[i])
+        got, _ = o.propagate_field(truth[i], geo.row_x[ev.row[i]], geo.row_x[ev.row[j]], al)
+        if got is None:
+            continue
+        d = np.abs(got - truth[j])
+        d[4] /= abs(truth[j][4])
+        worst = np.maximum(worst, d)
+        checked += 1
+    assert checked >= 50
+    assert worst[0] < 2e-5 and worst[1] < 2e-5, worst
+    assert worst[2] < 1e-6 and worst[3] < 1e-6 and worst[4] < 1e-6, worst
+
+
+def test_field_refit_removes_the_momentum_bias(geo, params):
+    """Exact clusters of particles traced through the non-uniform field: the
+    refit in the full field returns the generating parameters, the refit in
+    the uniform field (Bz only, as before Sec. 3's change) is biased in
+    q/pT."""
+    ev, f = _field_event(0.04, 63)
+    ts, ci, tc, _ = synth.truth_tracks(ev, 40)
+    inner = ci[ts[:-1].astype(np.int64)]
+    truth = np.stack([ev.y_true, ev.z_true, ev.s_true, ev.tl_true, ev.q_true], 1)[inner]
+    rf = _oracle(ev, geo, params, field=f).refit(ts, ci, tc, prec=64)
+    ru = _oracle(ev, geo, params).refit(ts, ci, tc, prec=64)
+    ok = (rf["status"] == 0) & (ru["status"] == 0)
+    assert ok.sum() >= 100
+    df = np.abs(rf["params"][ok] - truth[ok])
+    assert np.max(df[:, 0]) < 1e-4 and np.max(df[:, 1]) < 1e-4, df.max(0)
+    assert np.max(df[:, 2]) < 1e-5 and np.max(df[:, 3]) < 1e-5, df.max(0)
+    qf = df[:, 4] / np.abs(truth[ok, 4])
+    qu = np.abs(ru["params"][ok, 4] - truth[ok, 4]) / np.abs(truth[ok, 4])
+    assert np.max(qf) < 1e-4, np.max(qf)
+    assert np.median(qu) > 20 * np.median(qf) and np.max(qu) > 3e-3, (np.median(qu), np.max(qu))
