@@ -84,6 +84,17 @@ typedef struct {
    * the fly by the kernels that read y. */
   const float* pad_width;   /* host [n_rows] pad pitch (cm)                 */
   const float* pad_center;  /* host [n_rows] pad position of y = 0 (pads)   */
+  /* The full field for the final refit (Sec. 3: Bx and By taken into
+   * account, three-dimensional polynomial field), or NULL for the uniform
+   * bz: host [3][10], the coefficients of Bx, By, Bz (T) as quadratic
+   * polynomials in the global coordinates (X, Y, Z) in metres, monomials
+   * 1, X, Y, Z, X^2, XY, XZ, Y^2, YZ, Z^2 (X, Y: sector k's local frame
+   * rotated by its angle; Z along the beam). tpc_refit then transports the
+   * state by fourth-order Runge-Kutta in the field (steps <= 0.5 cm) and
+   * the covariance with the helix Jacobian of the local Bz; track finding,
+   * merging and compression keep the uniform bz, and tpc_refit_backward
+   * returns TPC_ERR_STATE (its adjoint is that of the uniform-field refit). */
+  const float* field;
 } tpc_geometry;
 
 /* Cut values of the method (the paper gives none; defaults by

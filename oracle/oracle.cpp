@@ -526,26 +526,25 @@ template <class R> void field_at(const Ctx& c, R X, R Y, R Z, R B[3]) {
 }
 
 // Transport in the full field from the state's x to x2 in the frame rotated
-// by alpha: the equations of motion of the direction u (unit vector) with x
+// by alpha. The equations of motion of the direction u (unit vector) with x
 // as the variable, dy/dx = u_y / u_x, dz/dx = u_z / u_x,
-// du/dx = k (q/p) (u x B) / u_x, integrated by fourth-order Runge-Kutta in
-// steps of at most 0.5 cm (about 1e-6 cm from the exact helix over 30 cm at
-// pT = 0.14 GeV); q/p is conserved, q/pT = (q/p) / |u_T|. The
-// covariance is transported with the helix Jacobian of the field's Bz at
-// the start point (a reading: the paper does not give the Jacobian used).
-// Fails where u_x would not stay positive or |sin(phi)| reaches s_max.
+// du/dx = k (q/p) (u x B) / u_x (q/p conserved, q/pT = (q/p) / |u_T|), are
+// integrated by fourth-order Runge-Kutta in steps of at most 0.5 cm twice:
+// in the full field and in the uniform field of the local Bz at the start
+// point. The state is the exact helix of that uniform field plus the
+// difference of the two integrations, so that the steps' truncation and
+// rounding errors largely cancel and a uniform field gives the helix
+// exactly. The covariance is transported with the helix Jacobian (a
+// reading: the paper does not give the Jacobian used). Fails where u_x
+// would not stay positive or |sin(phi)| reaches s_max.
 template <class R>
-bool propagate_field(const Ctx& c, Trk<R>& st, R x2, double alpha) {
+bool rk4_field(const Ctx& c, const Trk<R>& st, R x2, double alpha, bool uniform, R bz,
+               R out[5]) {
   const R ca = R(std::cos(alpha)), sa = R(std::sin(alpha));
-  R Bs[3];
-  field_at<R>(c, st.x * ca - st.p[0] * sa, st.x * sa + st.p[0] * ca, st.p[1], Bs);
-  R kBl = R(kCLight) * Bs[2];
-  Trk<R> hx = st;
-  if (!propagate<R>(c, hx, x2, nullptr, &kBl)) return false;
   R s = st.p[2], t = st.p[3], q = st.p[4];
   R cl = R(1) / sqrt_(R(1) + t * t);
   R cf = sqrt_(R(1) - s * s);
-  R v[5] = {st.p[0], st.p[1], cf * cl, s * cl, t * cl};
+  R v[5] = {R(0), R(0), cf * cl, s * cl, t * cl};  // y, z as offsets from the start
   R kq = R(kCLight) * (q * cl);
   R dx = x2 - st.x;
   int ns = (int)std::ceil(std::fabs(val(dx)) / 0.5);
@@ -554,9 +553,15 @@ bool propagate_field(const Ctx& c, Trk<R>& st, R x2, double alpha) {
   R x = st.x;
   auto deriv = [&](R xx, const R w[5], R d[5]) {
     if (!(w[2] > R(0))) return false;
-    R B[3];
-    field_at<R>(c, xx * ca - w[0] * sa, xx * sa + w[0] * ca, w[1], B);
-    R b0 = B[0] * ca + B[1] * sa, b1 = -(B[0] * sa) + B[1] * ca, b2 = B[2];
+    R b0 = R(0), b1 = R(0), b2 = bz;
+    if (!uniform) {
+      R B[3];
+      R yy = st.p[0] + w[0];
+      field_at<R>(c, xx * ca - yy * sa, xx * sa + yy * ca, st.p[1] + w[1], B);
+      b0 = B[0] * ca + B[1] * sa;
+      b1 = -(B[0] * sa) + B[1] * ca;
+      b2 = B[2];
+    }
     R iu = R(1) / w[2];
     R f = kq * iu;
     d[0] = w[3] * iu;
@@ -582,13 +587,29 @@ bool propagate_field(const Ctx& c, Trk<R>& st, R x2, double alpha) {
   R un = sqrt_(v[2] * v[2] + v[3] * v[3] + v[4] * v[4]);
   R ux = v[2] / un, uy = v[3] / un, uz = v[4] / un;
   R rho = sqrt_(ux * ux + uy * uy);
-  R s2 = uy / rho;
-  if (!(ux > R(0)) || !(abs_(s2) < R(c.p.s_max))) return false;
-  st.p[0] = v[0];
-  st.p[1] = v[1];
-  st.p[2] = s2;
-  st.p[3] = uz / rho;
-  st.p[4] = (q * cl) / rho;
+  if (!(ux > R(0))) return false;
+  out[0] = v[0];
+  out[1] = v[1];
+  out[2] = uy / rho;
+  out[3] = uz / rho;
+  out[4] = (q * cl) / rho;
+  return true;
+}
+
+template <class R>
+bool propagate_field(const Ctx& c, Trk<R>& st, R x2, double alpha) {
+  const R ca = R(std::cos(alpha)), sa = R(std::sin(alpha));
+  R Bs[3];
+  field_at<R>(c, st.x * ca - st.p[0] * sa, st.x * sa + st.p[0] * ca, st.p[1], Bs);
+  R kBl = R(kCLight) * Bs[2];
+  Trk<R> hx = st;
+  if (!propagate<R>(c, hx, x2, nullptr, &kBl)) return false;
+  R full[5], unif[5];
+  if (!rk4_field<R>(c, st, x2, alpha, false, Bs[2], full)) return false;
+  if (!rk4_field<R>(c, st, x2, alpha, true, Bs[2], unif)) return false;
+  R s2 = hx.p[2] + (full[2] - unif[2]);
+  if (!(abs_(s2) < R(c.p.s_max))) return false;
+  for (int k = 0; k < 5; ++k) st.p[k] = hx.p[k] + (full[k] - unif[k]);
   st.x = x2;
   for (int i = 0; i < 5; ++i)
     for (int j = 0; j < 5; ++j) st.C[i][j] = hx.C[i][j];

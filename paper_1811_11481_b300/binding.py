@@ -33,7 +33,8 @@ class TpcError(RuntimeError):
 class tpc_geometry(C.Structure):
     _fields_ = [("n_rows", C.c_int32), ("row_x", C.POINTER(C.c_float)),
                 ("tan_half", C.c_float), ("drift_length", C.c_float), ("bz", C.c_float),
-                ("pad_width", C.POINTER(C.c_float)), ("pad_center", C.POINTER(C.c_float))]
+                ("pad_width", C.POINTER(C.c_float)), ("pad_center", C.POINTER(C.c_float)),
+                ("field", C.POINTER(C.c_float))]
 
 
 class tpc_params(C.Structure):
@@ -170,7 +171,7 @@ def params_struct(d):
 class Tracker:
     """One library context bound to the current CUDA device and torch stream."""
 
-    def __init__(self, geo, params=None, stream=None):
+    def __init__(self, geo, params=None, stream=None, field=None):
         import torch
         self.torch = torch
         if not torch.cuda.is_available():
@@ -185,8 +186,11 @@ class Tracker:
                       if getattr(geo, "pad_width", None) is not None else None)
         self.pad_c = (np.ascontiguousarray(geo.pad_center, np.float32)
                       if getattr(geo, "pad_center", None) is not None else None)
+        self.field = (np.ascontiguousarray(field, np.float32).reshape(-1)
+                      if field is not None else None)
         g = tpc_geometry(self.n_rows, fp(self.row_x), float(geo.tan_half),
-                         float(geo.drift_length), float(geo.bz), fp(self.pad_w), fp(self.pad_c))
+                         float(geo.drift_length), float(geo.bz), fp(self.pad_w), fp(self.pad_c),
+                         fp(self.field))
         p = params_struct(params) if params is not None else None
         h = C.c_void_p()
         st = self.L.tpc_create(C.byref(g), C.byref(p) if p is not None else None,

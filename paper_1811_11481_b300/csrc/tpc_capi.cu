@@ -337,6 +337,10 @@ tpc_status tpc_create(const tpc_geometry* geo, const tpc_params* params, void* s
   }
   chk(cudaMemcpy(ctx->d_rowx, geo->row_x, sizeof(float) * geo->n_rows, cudaMemcpyHostToDevice));
   g.rx = ctx->d_rowx;
+  if (geo->field) {
+    g.field_on = 1;
+    for (int i = 0; i < 30; ++i) g.field[i] = geo->field[i];
+  }
   if (geo->pad_width && geo->pad_center) {
     chk(cudaMalloc(&ctx->d_pads, sizeof(float) * 2 * TPC_MAX_ROWS));
     chk(cudaMemcpy(ctx->d_pads, geo->pad_width, sizeof(float) * geo->n_rows,
@@ -771,6 +775,8 @@ tpc_status tpc_refit_backward(tpc_ctx* ctx, const float* dl_dchi2, float* grad_y
                               double* grad_calib) {
   if (!ctx) return TPC_ERR_ARG;
   if (!ctx->saved) return fail(ctx, TPC_ERR_STATE, "refit_backward needs a saved refit");
+  if (ctx->geo.field_on)
+    return fail(ctx, TPC_ERR_STATE, "the adjoint differentiates the refit in the uniform field");
   if (ctx->refit_calib_version != ctx->calib_version)
     return fail(ctx, TPC_ERR_STATE, "calibration changed since the saved refit");
   if (!dl_dchi2 || !grad_y || !grad_zt || !grad_calib)

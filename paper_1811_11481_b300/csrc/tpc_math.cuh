@@ -33,6 +33,8 @@ struct Geo {
   float kB;  // curvature per unit q/pT: 2.99792458e-3 * bz, rounded to float
   const float* pw;  // [n_rows] pad pitch (cm), or null
   const float* pc;  // [n_rows] pad position of y = 0, or null
+  int32_t field_on;  // the final fit uses the full field below
+  float field[30];   // (Bx, By, Bz) quadratic polynomials in (X, Y, Z) / 100 cm
 };
 
 struct Cal {

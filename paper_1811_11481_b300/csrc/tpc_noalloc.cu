@@ -90,7 +90,7 @@ __global__ void k_na_refit(Geo g, RefitCfg p, int64_t n_tracks, int64_t n_assign
   TrackIn in{track_start, yc, zc, meta};
   Lay ly = contiguous_layout(a, n);
   // the packed words carry no sector: one frame per track
-  RefitOut o = refit_track(g, p, in, ly, n, rej, nullptr, nullptr, false);
+  RefitOut o = refit_track<false>(g, p, in, ly, n, rej, nullptr, nullptr, false);
   if (o.status != 0) {
     o.chi2 = 0.0f;
     o.ndf = 0;

@@ -41,6 +41,8 @@ RefitCfg make_cfg(const Geo& g, const Params& p) {
   c.min_acc_reject = p.min_acc_reject;
   for (int i = 0; i < 5; ++i) c.c0r[i] = p.c0r[i];
   set_frame_rotations(c);
+  c.field_on = g.field_on;
+  for (int i = 0; i < 30; ++i) c.field[i] = g.field[i];
   return c;
 }
 
@@ -170,6 +172,7 @@ __global__ void k_interleave(const uint32_t* cnt, TrackIn in, const uint32_t* as
   if (frame_of(m) != frame_of(in.meta[a])) multi[T] = 1;
 }
 
+template <bool kField>
 __global__ void __launch_bounds__(kB) k_refit(Geo g, RefitCfg p, const uint32_t* cnt,
                                                const uint32_t* order, const uint32_t* wbase,
                                                const uint32_t* wlen, const uint32_t* track_start,
@@ -192,8 +195,8 @@ __global__ void __launch_bounds__(kB) k_refit(Geo g, RefitCfg p, const uint32_t*
   }
   int n = (int)(b - a);
   Lay ly = warp_layout(wbase, wlen, tid);
-  RefitOut o = refit_track(g, p, win, ly, n, rej, seed_out + (size_t)T * 5, save ? ckpt : nullptr,
-                           multi[T] != 0);
+  RefitOut o = refit_track<kField>(g, p, win, ly, n, rej, seed_out + (size_t)T * 5,
+                                   save ? ckpt : nullptr, multi[T] != 0);
   if (o.status == 0 && !(fabsf(o.chi2) < 1.0e30f && fabsf(o.st[4]) < 1.0e30f))
     atomicOr(err, kErrNumeric);
   if (o.status != 0) {
@@ -516,12 +519,18 @@ void launch_refit(Prof* P, const Geo& g, const Params& p, int64_t cap_tr, const 
              k_interleave<<<nblk(tb.cap_asg, 256), 256, 0, s>>>(cnt, in, tb.asg_track, rb.slot,
                                                                  rb.wbase, rb.w_yc, rb.w_zc,
                                                                  rb.w_meta, rb.multi));
-  TPC_LAUNCH(P, "k_refit", s,
-             k_refit<<<nblk(cap_tr, kB), kB, 0, s>>>(g, make_cfg(g, p), cnt, rb.order, rb.wbase,
-                                                     rb.wlen, tb.track_start, win, rb.seed,
-                                                     rb.rej, rb.status, rb.ckpt, save ? 1 : 0,
-                                                     params, cov, x, chi2, ndf, status, rej,
-                                                     rb.multi, err));
+  if (g.field_on)
+    TPC_LAUNCH(P, "k_refit_field", s,
+               k_refit<true><<<nblk(cap_tr, kB), kB, 0, s>>>(
+                   g, make_cfg(g, p), cnt, rb.order, rb.wbase, rb.wlen, tb.track_start, win,
+                   rb.seed, rb.rej, rb.status, rb.ckpt, save ? 1 : 0, params, cov, x, chi2, ndf,
+                   status, rej, rb.multi, err));
+  else
+    TPC_LAUNCH(P, "k_refit", s,
+               k_refit<false><<<nblk(cap_tr, kB), kB, 0, s>>>(
+                   g, make_cfg(g, p), cnt, rb.order, rb.wbase, rb.wlen, tb.track_start, win,
+                   rb.seed, rb.rej, rb.status, rb.ckpt, save ? 1 : 0, params, cov, x, chi2, ndf,
+                   status, rej, rb.multi, err));
 }
 
 void launch_refit_backward(Prof* P, const Geo& g, const Cal& c, const Params& p, const ClIn& cl,

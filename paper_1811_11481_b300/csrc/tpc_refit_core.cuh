@@ -58,6 +58,9 @@ struct RefitCfg {
   // edge, shared)
   float flag_scale[5];
   float rot_c[kFrames], rot_s[kFrames];  // cos, sin of m * 20 degrees
+  float frame_c[kFrames], frame_s[kFrames];  // cos, sin of each frame's angle
+  int32_t field_on;
+  float field[30];  // (Bx, By, Bz) polynomials, as in Geo
 };
 
 inline void set_frame_rotations(RefitCfg& c) {
@@ -65,7 +68,116 @@ inline void set_frame_rotations(RefitCfg& c) {
     double a = m * (3.14159265358979323846 / 9.0);
     c.rot_c[m] = (float)std::cos(a);
     c.rot_s[m] = (float)std::sin(a);
+    double f = (m + 0.5) * (3.14159265358979323846 / 9.0);
+    c.frame_c[m] = (float)std::cos(f);
+    c.frame_s[m] = (float)std::sin(f);
   }
+}
+
+// ---------------------------------------------------- the full field (Sec. 3)
+// (Bx, By, Bz) at global (X, Y, Z) cm: quadratic polynomials in metres.
+TPC_HD void field_at(const RefitCfg& p, float X, float Y, float Z, float B[3]) {
+  float x = X * 0.01f, y = Y * 0.01f, z = Z * 0.01f;
+  const float m[10] = {1.0f, x, y, z, x * x, x * y, x * z, y * y, y * z, z * z};
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    float acc = 0.0f;
+#pragma unroll
+    for (int i = 0; i < 10; ++i) acc += p.field[k * 10 + i] * m[i];
+    B[k] = acc;
+  }
+}
+
+// Transport in the full field from x to x2 in the frame (ca, sa). The
+// equations of motion of the unit direction u with x as the variable
+// (dy/dx = u_y / u_x, dz/dx = u_z / u_x, du/dx = k (q/p) (u x B) / u_x, q/p
+// conserved) are integrated by fourth-order Runge-Kutta in steps of at most
+// 0.5 cm twice: in the full field and in the uniform field of the local Bz at
+// the start. The state is the exact helix of that uniform field plus the
+// difference of the two integrations (their truncation and single-precision
+// rounding errors largely cancel; a uniform field gives the helix exactly);
+// the covariance follows with the helix Jacobian. Fails where u_x would not
+// stay positive or |sin(phi)| reaches s_max.
+TPC_HD bool rk4_field(const RefitCfg& p, const float st[5], float x, float x2, float ca,
+                      float sa, bool uniform, float bz, float out[5]) {
+  float s = st[2], t = st[3], q = st[4];
+  float cl = 1.0f / sqrtf(1.0f + t * t);
+  float cf = sqrtf(1.0f - s * s);
+  float v[5] = {0.0f, 0.0f, cf * cl, s * cl, t * cl};  // y, z as offsets
+  float kq = 2.99792458e-3f * (q * cl);
+  float dx = x2 - x;
+  int ns = (int)ceilf(fabsf(dx) * 2.0f);
+  if (ns < 1) ns = 1;
+  float h = dx / (float)ns;
+  float xx = x;
+  auto deriv = [&](float xa, const float w[5], float d[5]) {
+    if (!(w[2] > 0.0f)) return false;
+    float b0 = 0.0f, b1 = 0.0f, b2 = bz;
+    if (!uniform) {
+      float B[3];
+      float yy = st[0] + w[0];
+      field_at(p, xa * ca - yy * sa, xa * sa + yy * ca, st[1] + w[1], B);
+      b0 = B[0] * ca + B[1] * sa;
+      b1 = -(B[0] * sa) + B[1] * ca;
+      b2 = B[2];
+    }
+    float iu = 1.0f / w[2];
+    float f = kq * iu;
+    d[0] = w[3] * iu;
+    d[1] = w[4] * iu;
+    d[2] = f * (w[3] * b2 - w[4] * b1);
+    d[3] = f * (w[4] * b0 - w[2] * b2);
+    d[4] = f * (w[2] * b1 - w[3] * b0);
+    return true;
+  };
+  for (int i = 0; i < ns; ++i) {
+    float k1[5], k2[5], k3[5], k4[5], w[5];
+    if (!deriv(xx, v, k1)) return false;
+#pragma unroll
+    for (int j = 0; j < 5; ++j) w[j] = v[j] + (h * 0.5f) * k1[j];
+    if (!deriv(xx + h * 0.5f, w, k2)) return false;
+#pragma unroll
+    for (int j = 0; j < 5; ++j) w[j] = v[j] + (h * 0.5f) * k2[j];
+    if (!deriv(xx + h * 0.5f, w, k3)) return false;
+#pragma unroll
+    for (int j = 0; j < 5; ++j) w[j] = v[j] + h * k3[j];
+    if (!deriv(xx + h, w, k4)) return false;
+#pragma unroll
+    for (int j = 0; j < 5; ++j)
+      v[j] = v[j] + (h / 6.0f) * (k1[j] + 2.0f * k2[j] + 2.0f * k3[j] + k4[j]);
+    xx = (i == ns - 1) ? x2 : xx + h;
+  }
+  float un = sqrtf(v[2] * v[2] + v[3] * v[3] + v[4] * v[4]);
+  float ux = v[2] / un, uy = v[3] / un, uz = v[4] / un;
+  float rho = sqrtf(ux * ux + uy * uy);
+  if (!(ux > 0.0f)) return false;
+  out[0] = v[0];
+  out[1] = v[1];
+  out[2] = uy / rho;
+  out[3] = uz / rho;
+  out[4] = (q * cl) / rho;
+  return true;
+}
+
+TPC_HD bool propagate_field(const RefitCfg& p, float st[5], float C[15], float& x, float x2,
+                            float ca, float sa) {
+  float Bs[3];
+  field_at(p, x * ca - st[0] * sa, x * sa + st[0] * ca, st[1], Bs);
+  float kBl = 2.99792458e-3f * Bs[2];
+  float hp[5];
+#pragma unroll
+  for (int i = 0; i < 5; ++i) hp[i] = st[i];
+  float hx = x;
+  if (!propagate(kBl, p.s_max, hp, C, hx, x2)) return false;
+  float full[5], unif[5];
+  if (!rk4_field(p, st, x, x2, ca, sa, false, Bs[2], full)) return false;
+  if (!rk4_field(p, st, x, x2, ca, sa, true, Bs[2], unif)) return false;
+  float s2 = hp[2] + (full[2] - unif[2]);
+  if (!(fabsf(s2) < p.s_max)) return false;
+#pragma unroll
+  for (int k = 0; k < 5; ++k) st[k] = hp[k] + (full[k] - unif[k]);
+  x = x2;
+  return true;
 }
 
 TPC_HD int frame_of(uint32_t meta) { return (int)((meta >> 16) & 0xffu) % kFrames; }
@@ -194,7 +306,8 @@ TPC_HD bool spans_frames(const TrackIn& in, const Lay& ly, int n) {
 // rejected cluster k (0 = kept). ckpt (may be null): state before each step.
 // kRot: the clusters may lie in several sector frames (the state is rotated
 // into each cluster's frame before the transport to it).
-template <bool kRot>
+// kField: transport in the full field (propagate_field) instead of the helix.
+template <bool kRot, bool kField>
 TPC_HD RefitOut refit_track_in(const Geo& g, const RefitCfg& p, const TrackIn& in, const Lay& ly,
                                int n, uint8_t* rej, float* seed_out, float* ckpt) {
   RefitOut o;
@@ -251,7 +364,10 @@ TPC_HD RefitOut refit_track_in(const Geo& g, const RefitCfg& p, const TrackIn& i
           }
           fr = fi;
         }
-        if (!propagate(p.kB, p.s_max, st, C, x, g.rx[m & 0xffu])) {
+        bool moved = kField ? propagate_field(p, st, C, x, g.rx[m & 0xffu], p.frame_c[fr],
+                                              p.frame_s[fr])
+                            : propagate(p.kB, p.s_max, st, C, x, g.rx[m & 0xffu]);
+        if (!moved) {
           o.status = 1;
           o.x = x;
           return o;
@@ -281,11 +397,12 @@ TPC_HD RefitOut refit_track_in(const Geo& g, const RefitCfg& p, const TrackIn& i
 }
 
 // multi: the track's clusters lie in more than one sector frame
-// (spans_frames).
+// (spans_frames). kField: transport in the full field.
+template <bool kField = false>
 TPC_HD RefitOut refit_track(const Geo& g, const RefitCfg& p, const TrackIn& in, const Lay& ly,
                             int n, uint8_t* rej, float* seed_out, float* ckpt, bool multi) {
-  return multi ? refit_track_in<true>(g, p, in, ly, n, rej, seed_out, ckpt)
-               : refit_track_in<false>(g, p, in, ly, n, rej, seed_out, ckpt);
+  return multi ? refit_track_in<true, kField>(g, p, in, ly, n, rej, seed_out, ckpt)
+               : refit_track_in<false, kField>(g, p, in, ly, n, rej, seed_out, ckpt);
 }
 
 // ------------------------------------------------------------ dual numbers

@@ -37,7 +37,7 @@ def test_default_params_agree_with_python_defaults(lib):
 
 def test_struct_layouts_match_header(lib):
     # sizes implied by the header (natural alignment, x86-64)
-    assert C.sizeof(binding.tpc_geometry) == 4 + 4 + 8 + 4 * 3 + 4 + 2 * 8
+    assert C.sizeof(binding.tpc_geometry) == 4 + 4 + 8 + 4 * 3 + 4 + 3 * 8
     assert C.sizeof(binding.tpc_clusters) == 8 + 4 + 4 + 8 + 7 * 8 + 4 + 4
     assert C.sizeof(binding.tpc_tracks) == 8 + 8 + 4 * 8
     assert C.sizeof(binding.tpc_calib) == 8 + 8 + 8 + 4 + 4

@@ -69,8 +69,9 @@ MUTANTS = {
  'compress_step_axis': ("float dz = prez + (float)rz * qz;", "float dz = prez + (float)rz * qy;"),
  'field_cross_sign': ("d[3] = f * (w[4] * b0 - w[2] * b2);", "d[3] = f * (w[4] * b0 + w[2] * b2);"),
  'field_monomials': ("const R m[10] = {R(1), x, y, z, x * x, x * y, x * z, y * y, y * z, z * z};", "const R m[10] = {R(1), x, y, z, x * x, x * y, y * z, y * y, x * z, z * z};"),
- 'field_pt_not_updated': ("st.p[4] = (q * cl) / rho;", "st.p[4] = q;"),
- 'field_not_rotated': ("R b0 = B[0] * ca + B[1] * sa, b1 = -(B[0] * sa) + B[1] * ca, b2 = B[2];", "R b0 = B[0], b1 = B[1], b2 = B[2];"),
+ 'field_pt_not_updated': ("out[4] = (q * cl) / rho;", "out[4] = q;"),
+ 'field_difference_sign': ("for (int k = 0; k < 5; ++k) st.p[k] = hx.p[k] + (full[k] - unif[k]);", "for (int k = 0; k < 5; ++k) st.p[k] = hx.p[k] - (full[k] - unif[k]);"),
+ 'field_not_rotated': ("b0 = B[0] * ca + B[1] * sa;\n      b1 = -(B[0] * sa) + B[1] * ca;", "b0 = B[0];\n      b1 = B[1];"),
  'merge_solve_operand': ("for (int k = 0; k < a; ++k) acc = acc - L[a][k] * w[k];", "for (int k = 0; k < a; ++k) acc = acc - L[a][k] * d[k];"),
 }
 
