@@ -45,6 +45,9 @@ def parse():
                     help="collisions of the time-frame workload (50: the headline frame)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--field", action="store_true",
+                    help="central event traced through a non-uniform field, refit in it "
+                         "(no adjoint in the step)")
     ap.add_argument("--pads", action="store_true",
                     help="give the clusters as native pad positions instead of y in cm")
     ap.add_argument("--no-merge", action="store_true",
@@ -61,12 +64,16 @@ def parse():
     return ap.parse_args()
 
 
-def make_workload(name, rank, collisions=50):
+def make_workload(name, rank, collisions=50, field=None):
     import synth
     if name == "central":
-        ev = synth.make_central(seed=1 + rank)
+        ev = synth.make_central(seed=1 + rank, field=field)
         cfg = dict(workload="central Pb-Pb-like event: 36 sectors x 152 rows, 10000 primaries "
                             "(pT power law, mean 0.5 GeV), 10% noise, event mode", seed=1 + rank)
+        if field is not None:
+            cfg["workload"] += ("; particles traced through a solenoid-like field with 4 % "
+                                "inhomogeneity and radial components (outgoing legs), refit "
+                                "in that full field")
     elif name == "timeframe":
         ev = synth.make_timeframe(seed=2 + rank, n_coll=collisions)
         cfg = dict(workload=f"50 kHz continuous-readout time frame: {collisions} collisions, "
@@ -447,10 +454,16 @@ def run_ours(args):
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     geo = synth.geometry()
-    ev, cfg = make_workload(args.workload, rank, args.collisions)
+    field = None
+    if args.field:
+        if args.workload != "central":
+            raise SystemExit("--field: the central workload only")
+        from synth.field import solenoid_field
+        field = solenoid_field()
+    ev, cfg = make_workload(args.workload, rank, args.collisions, field)
     work = torch.cuda.Stream()
     torch.cuda.set_stream(work)
-    tr = Tracker(geo, stream=work)
+    tr = Tracker(geo, stream=work, field=field)
     tr.set_calib()
     cl = tr.upload(ev, pads=args.pads)
     if args.pads:
@@ -491,7 +504,7 @@ def run_ours(args):
         if refit:
             ck(L.tpc_refit(h, 1, P(out["params"]), P(out["cov"]), P(out["x"]), P(out["chi2"]),
                            P(out["ndf"]), P(out["status"]), P(out["rej"])), "refit")
-        if backward:
+        if backward and field is None:   # the adjoint is that of the uniform-field refit
             ck(L.tpc_refit_backward(h, P(ones), P(gy), P(gz), P(gc)), "backward")
 
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
@@ -623,7 +636,8 @@ def run_ours(args):
     # context's host-side record of what was saved)
     ck(L.tpc_refit(h, 1, P(out["params"]), P(out["cov"]), P(out["x"]), P(out["chi2"]),
                    P(out["ndf"]), P(out["status"]), P(out["rej"])), "refit")
-    t_bwd = phase_time(lambda: ck(L.tpc_refit_backward(h, P(ones), P(gy), P(gz), P(gc)), "bwd"))
+    t_bwd = None if field is not None else phase_time(
+        lambda: ck(L.tpc_refit_backward(h, P(ones), P(gy), P(gz), P(gc)), "bwd"))
 
     # ---- end to end through the C ABI with host buffers
     e2e = None
@@ -655,7 +669,8 @@ def run_ours(args):
             ck(L.tpc_find_tracks_async(h), "find")
             ck(L.tpc_refit(h, 1, P(out["params"]), P(out["cov"]), P(out["x"]), P(out["chi2"]),
                            P(out["ndf"]), P(out["status"]), P(out["rej"])), "refit")
-            ck(L.tpc_refit_backward(h, P(ones), P(gy), P(gz), P(gc)), "backward")
+            if field is None:
+                ck(L.tpc_refit_backward(h, P(ones), P(gy), P(gz), P(gc)), "backward")
 
         barrier()
         a = torch.cuda.Event(enable_timing=True)
@@ -736,7 +751,8 @@ def run_ours(args):
                 tracks_per_s=aggregate(total_ms, nt * args.steps, dist, dev)[2],
                 n_tracks=nt, n_assigned=na, n_tracklets=ntl,
                 refit_fwd_ms=t_fwd, refit_fwd_nosave_ms=t_fwd_nosave, adjoint_ms=t_bwd,
-                adjoint_vs_fwd=t_bwd / t_fwd_nosave if t_fwd_nosave > 0 else None,
+                adjoint_vs_fwd=(t_bwd / t_fwd_nosave if t_bwd is not None and t_fwd_nosave > 0
+                                else None),
                 roofline=roof, step_hbm=step_hbm, kernels=kernels,
                 kernels_timing=f"separate pass of {n_prof} steps with every launch timed",
                 gpu_launches=launches,

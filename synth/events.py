@@ -482,12 +482,13 @@ def make_single_sector(seed=0, n_tracks=200):
     return make_event(rng, geo, [p], mode="event", keep_sectors=[0])
 
 
-def make_central(seed=1, n_tracks=10000, noise_frac=0.10):
-    """One central Pb-Pb-like event: 36 sectors, 10k primaries, 10% noise."""
+def make_central(seed=1, n_tracks=10000, noise_frac=0.10, field=None):
+    """One central Pb-Pb-like event: 36 sectors, 10k primaries, 10% noise
+    (with field: traced through that non-uniform field, outgoing legs)."""
     rng = np.random.default_rng(seed)
     geo = geometry()
     p = gen_particles_central(rng, n_tracks)
-    return make_event(rng, geo, [p], mode="event", noise_frac=noise_frac)
+    return make_event(rng, geo, [p], mode="event", noise_frac=noise_frac, field=field)
 
 
 def make_timeframe(seed=2, n_coll=50, mean_mult=2000, rate_khz=50.0,
