@@ -164,3 +164,26 @@ def test_tracks_come_in_canonical_order(full):
     ts = g["tl"]["start_hit"].astype(np.int64)
     tb = (ev.event[ts].astype(np.int64) * 36 + ev.sector[ts]) * 152 + ev.row[ts]
     assert np.bincount(np.unique(tb, return_inverse=True)[1]).max() > 64
+
+
+def test_merge_whole_event(full):
+    """Segment merging of the whole event's found tracks (20k segments) on
+    the oracle's refitted states: links and merged set bit-exact."""
+    import torch
+    g, o, ev, geo = full["g"], full["o"], full["ev"], full["geo"]
+    ts, ci, tt = g["track_start"], g["cluster_idx"], g["t_coll"]
+    r = o.refit(ts, ci, tt, prec=64)
+    st = dict(params=r["params"].astype(np.float32), cov=r["cov"].astype(np.float32),
+              x=r["x"].astype(np.float32), status=r["status"].astype(np.int32))
+    want = o.merge(ts, ci, tt, st["params"], st["cov"], st["x"], st["status"], prec=32)
+    tr = tracker(geo)
+    tr.set_calib()
+    tr.load(tr.upload(ev))
+    tr.set_tracks(torch.as_tensor(ts.astype(np.int32)), torch.as_tensor(ci.astype(np.int32)),
+                  torch.as_tensor(tt), torch.as_tensor(g["start_hit"].astype(np.int32)))
+    got = tr.merge({k: torch.as_tensor(v) for k, v in st.items()})
+    assert (want["next"] >= 0).sum() > 5000
+    np.testing.assert_array_equal(got["next"].cpu().numpy(), want["next"])
+    mt = {k: v.cpu().numpy() for k, v in got["tracks"].items()}
+    np.testing.assert_array_equal(mt["track_start"], want["track_start"].astype(np.int32))
+    np.testing.assert_array_equal(mt["cluster_idx"], want["cluster_idx"].astype(np.int32))
