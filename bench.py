@@ -46,8 +46,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--field", action="store_true",
-                    help="central event traced through a non-uniform field, refit in it "
-                         "(no adjoint in the step)")
+                    help="central event traced through a non-uniform field, refit (and "
+                         "adjoint) in it")
     ap.add_argument("--pads", action="store_true",
                     help="give the clusters as native pad positions instead of y in cm")
     ap.add_argument("--no-merge", action="store_true",
@@ -504,7 +504,7 @@ def run_ours(args):
         if refit:
             ck(L.tpc_refit(h, 1, P(out["params"]), P(out["cov"]), P(out["x"]), P(out["chi2"]),
                            P(out["ndf"]), P(out["status"]), P(out["rej"])), "refit")
-        if backward and field is None:   # the adjoint is that of the uniform-field refit
+        if backward:
             ck(L.tpc_refit_backward(h, P(ones), P(gy), P(gz), P(gc)), "backward")
 
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
@@ -636,8 +636,7 @@ def run_ours(args):
     # context's host-side record of what was saved)
     ck(L.tpc_refit(h, 1, P(out["params"]), P(out["cov"]), P(out["x"]), P(out["chi2"]),
                    P(out["ndf"]), P(out["status"]), P(out["rej"])), "refit")
-    t_bwd = None if field is not None else phase_time(
-        lambda: ck(L.tpc_refit_backward(h, P(ones), P(gy), P(gz), P(gc)), "bwd"))
+    t_bwd = phase_time(lambda: ck(L.tpc_refit_backward(h, P(ones), P(gy), P(gz), P(gc)), "bwd"))
 
     # ---- end to end through the C ABI with host buffers
     e2e = None
@@ -669,8 +668,7 @@ def run_ours(args):
             ck(L.tpc_find_tracks_async(h), "find")
             ck(L.tpc_refit(h, 1, P(out["params"]), P(out["cov"]), P(out["x"]), P(out["chi2"]),
                            P(out["ndf"]), P(out["status"]), P(out["rej"])), "refit")
-            if field is None:
-                ck(L.tpc_refit_backward(h, P(ones), P(gy), P(gz), P(gc)), "backward")
+            ck(L.tpc_refit_backward(h, P(ones), P(gy), P(gz), P(gc)), "backward")
 
         barrier()
         a = torch.cuda.Event(enable_timing=True)

@@ -91,9 +91,9 @@ typedef struct {
    * 1, X, Y, Z, X^2, XY, XZ, Y^2, YZ, Z^2 (X, Y: sector k's local frame
    * rotated by its angle; Z along the beam). tpc_refit then transports the
    * state by fourth-order Runge-Kutta in the field (steps <= 0.5 cm) and
-   * the covariance with the helix Jacobian of the local Bz; track finding,
-   * merging and compression keep the uniform bz, and tpc_refit_backward
-   * returns TPC_ERR_STATE (its adjoint is that of the uniform-field refit). */
+   * the covariance with the helix Jacobian of the local Bz (tpc_refit_backward
+   * differentiates that transport); track finding, merging and compression
+   * keep the uniform bz. */
   const float* field;
 } tpc_geometry;
 

@@ -775,8 +775,6 @@ tpc_status tpc_refit_backward(tpc_ctx* ctx, const float* dl_dchi2, float* grad_y
                               double* grad_calib) {
   if (!ctx) return TPC_ERR_ARG;
   if (!ctx->saved) return fail(ctx, TPC_ERR_STATE, "refit_backward needs a saved refit");
-  if (ctx->geo.field_on)
-    return fail(ctx, TPC_ERR_STATE, "the adjoint differentiates the refit in the uniform field");
   if (ctx->refit_calib_version != ctx->calib_version)
     return fail(ctx, TPC_ERR_STATE, "calibration changed since the saved refit");
   if (!dl_dchi2 || !grad_y || !grad_zt || !grad_calib)

@@ -218,6 +218,7 @@ __global__ void __launch_bounds__(kB) k_refit(Geo g, RefitCfg p, const uint32_t*
     for (int k = 0; k < n; ++k) o_rej[a + k] = rej[ly.at(k)];
 }
 
+template <bool kField>
 __global__ void __launch_bounds__(kB) k_refit_bwd(Geo g, RefitCfg p, const uint32_t* cnt,
                                                    const uint32_t* order, const uint32_t* wbase,
                                                    const uint32_t* wlen,
@@ -239,7 +240,8 @@ __global__ void __launch_bounds__(kB) k_refit_bwd(Geo g, RefitCfg p, const uint3
     }
     return;
   }
-  refit_backward_track(g, p, win, ly, n, rej, ckpt, dl_dchi2[T], gyc, gzc, multi[T] != 0);
+  refit_backward_track<kField>(g, p, win, ly, n, rej, ckpt, dl_dchi2[T], gyc, gzc,
+                               multi[T] != 0);
   // largest |gradient| (as float bits, so that NaN ranks above infinity)
   uint32_t m = 0u;
   for (int k = 0; k < n; ++k) {
@@ -541,12 +543,11 @@ void launch_refit_backward(Prof* P, const Geo& g, const Cal& c, const Params& p,
   cudaMemsetAsync(rb.gmax, 0, sizeof(uint32_t), s);
   cudaMemsetAsync(rb.acc_spline, 0, sizeof(unsigned long long) * TPC_SPLINE_SIZE, s);
   if (cap_tr > 0)
-    TPC_LAUNCH(P, "k_refit_bwd", s,
-               k_refit_bwd<<<nblk(cap_tr, kB), kB, 0, s>>>(g, make_cfg(g, p), cnt, rb.order,
-                                                           rb.wbase, rb.wlen, tb.track_start,
-                                                           win, rb.rej, rb.status, rb.ckpt,
-                                                           dl_dchi2, rb.gyc, rb.gzc, rb.multi,
-                                                           rb.gmax));
+    TPC_LAUNCH(P, g.field_on ? "k_refit_bwd_field" : "k_refit_bwd", s,
+               (g.field_on ? k_refit_bwd<true> : k_refit_bwd<false>)<<<nblk(cap_tr, kB), kB, 0,
+                                                                       s>>>(
+                   g, make_cfg(g, p), cnt, rb.order, rb.wbase, rb.wlen, tb.track_start, win,
+                   rb.rej, rb.status, rb.ckpt, dl_dchi2, rb.gyc, rb.gzc, rb.multi, rb.gmax));
   TPC_LAUNCH(P, "k_calib_grad", s,
              k_calib_grad<<<kCalibGradBlocks, kCgThreads, 0, s>>>(
                  g, c, cl, cnt, tb.cluster_idx, tb.asg_track, tb.track_start, rb.slot, rb.wbase,

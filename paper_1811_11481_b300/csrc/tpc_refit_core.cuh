@@ -745,12 +745,278 @@ TPC_HD void rotate_adjoint(float kB, float ca, float sa, const float p[5], const
   }
 }
 
+// ------------------------------------------- adjoint of the field transport
+// Gradient of the field (T per cm) at global (X, Y, Z) cm: g[k][c] =
+// dB_k / d(X, Y, Z)_c of the quadratic polynomials.
+TPC_HD void field_grad(const RefitCfg& p, float X, float Y, float Z, float gB[3][3]) {
+  float x = X * 0.01f, y = Y * 0.01f, z = Z * 0.01f;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const float* a = p.field + k * 10;
+    gB[k][0] = 0.01f * (a[1] + 2.0f * a[4] * x + a[5] * y + a[6] * z);
+    gB[k][1] = 0.01f * (a[2] + a[5] * x + 2.0f * a[7] * y + a[8] * z);
+    gB[k][2] = 0.01f * (a[3] + a[6] * x + a[8] * y + 2.0f * a[9] * z);
+  }
+}
+
+// Adjoint of one evaluation of the equations of motion d = f(xa, w) (as in
+// rk4_field) given db: accumulates into wb, and into the adjoints of the
+// start y, z (field position), of kq and of the uniform bz.
+TPC_HD void rk4_deriv_vjp(const RefitCfg& p, const float st[5], float xa, const float w[5],
+                          float ca, float sa, bool uniform, float bz, float kq,
+                          const float db[5], float wb[5], float& y0b, float& z0b, float& kqb,
+                          float& bzb) {
+  float b0 = 0.0f, b1 = 0.0f, b2 = bz;
+  float X = 0.0f, Y = 0.0f, Z = 0.0f;
+  if (!uniform) {
+    float B[3];
+    float yy = st[0] + w[0];
+    X = xa * ca - yy * sa;
+    Y = xa * sa + yy * ca;
+    Z = st[1] + w[1];
+    field_at(p, X, Y, Z, B);
+    b0 = B[0] * ca + B[1] * sa;
+    b1 = -(B[0] * sa) + B[1] * ca;
+    b2 = B[2];
+  }
+  float iu = 1.0f / w[2];
+  float f = kq * iu;
+  float c2 = w[3] * b2 - w[4] * b1, c3 = w[4] * b0 - w[2] * b2, c4 = w[2] * b1 - w[3] * b0;
+  float iub = db[0] * w[3] + db[1] * w[4];
+  wb[3] += db[0] * iu;
+  wb[4] += db[1] * iu;
+  float fb = db[2] * c2 + db[3] * c3 + db[4] * c4;
+  float c2b = db[2] * f, c3b = db[3] * f, c4b = db[4] * f;
+  wb[3] += c2b * b2 - c4b * b0;
+  wb[4] += -(c2b * b1) + c3b * b0;
+  wb[2] += -(c3b * b2) + c4b * b1;
+  float b0b = c3b * w[4] - c4b * w[3];
+  float b1b = -(c2b * w[4]) + c4b * w[2];
+  float b2b = c2b * w[3] - c3b * w[2];
+  kqb += fb * iu;
+  iub += fb * kq;
+  wb[2] += -iub * iu * iu;
+  if (uniform) {
+    bzb += b2b;
+    return;
+  }
+  float gB[3][3];
+  field_grad(p, X, Y, Z, gB);
+  float B0b = b0b * ca - b1b * sa, B1b = b0b * sa + b1b * ca, B2b = b2b;
+  float Xb = B0b * gB[0][0] + B1b * gB[1][0] + B2b * gB[2][0];
+  float Yb = B0b * gB[0][1] + B1b * gB[1][1] + B2b * gB[2][1];
+  float Zb = B0b * gB[0][2] + B1b * gB[1][2] + B2b * gB[2][2];
+  float yyb = -(Xb * sa) + Yb * ca;
+  wb[0] += yyb;
+  y0b += yyb;
+  wb[1] += Zb;
+  z0b += Zb;
+}
+
+constexpr int kMaxSub = 64;  // stored Runge-Kutta sub-step states
+
+// Adjoint of rk4_field: given the adjoint ob of its output, the adjoint sb of
+// the start state (y, z, sin phi, tan lambda, q/pT) and of the uniform bz.
+// Sub-step start states are recomputed by a forward pass (and, beyond
+// kMaxSub sub-steps, again from the start for each sub-step).
+TPC_HD void rk4_field_vjp(const RefitCfg& p, const float st[5], float x, float x2, float ca,
+                          float sa, bool uniform, float bz, const float ob[5], float sb[5],
+                          float& bzb) {
+  float s = st[2], t = st[3], q = st[4];
+  float cl = 1.0f / sqrtf(1.0f + t * t);
+  float cf = sqrtf(1.0f - s * s);
+  float kq = 2.99792458e-3f * (q * cl);
+  float dx = x2 - x;
+  int ns = (int)ceilf(fabsf(dx) * 2.0f);
+  if (ns < 1) ns = 1;
+  float h = dx / (float)ns;
+  auto deriv = [&](float xa, const float w[5], float d[5]) {
+    float b0 = 0.0f, b1 = 0.0f, b2 = bz;
+    if (!uniform) {
+      float B[3];
+      float yy = st[0] + w[0];
+      field_at(p, xa * ca - yy * sa, xa * sa + yy * ca, st[1] + w[1], B);
+      b0 = B[0] * ca + B[1] * sa;
+      b1 = -(B[0] * sa) + B[1] * ca;
+      b2 = B[2];
+    }
+    float iu = 1.0f / w[2];
+    float f = kq * iu;
+    d[0] = w[3] * iu;
+    d[1] = w[4] * iu;
+    d[2] = f * (w[3] * b2 - w[4] * b1);
+    d[3] = f * (w[4] * b0 - w[2] * b2);
+    d[4] = f * (w[2] * b1 - w[3] * b0);
+  };
+  float v0[5] = {0.0f, 0.0f, cf * cl, s * cl, t * cl};
+  auto step = [&](float xa, float v[5]) {
+    float k1[5], k2[5], k3[5], k4[5], w[5];
+    deriv(xa, v, k1);
+    for (int j = 0; j < 5; ++j) w[j] = v[j] + (h * 0.5f) * k1[j];
+    deriv(xa + h * 0.5f, w, k2);
+    for (int j = 0; j < 5; ++j) w[j] = v[j] + (h * 0.5f) * k2[j];
+    deriv(xa + h * 0.5f, w, k3);
+    for (int j = 0; j < 5; ++j) w[j] = v[j] + h * k3[j];
+    deriv(xa + h, w, k4);
+    for (int j = 0; j < 5; ++j)
+      v[j] = v[j] + (h / 6.0f) * (k1[j] + 2.0f * k2[j] + 2.0f * k3[j] + k4[j]);
+  };
+  float vs[kMaxSub][5];
+  float v[5];
+  for (int j = 0; j < 5; ++j) v[j] = v0[j];
+  float xa = x;
+  for (int i = 0; i < ns; ++i) {
+    if (i < kMaxSub)
+      for (int j = 0; j < 5; ++j) vs[i][j] = v[j];
+    step(xa, v);
+    xa = (i == ns - 1) ? x2 : xa + h;
+  }
+  // output: (v0, v1, uy / rho, uz / rho, q cl / rho) with u = v / |v|
+  float un = sqrtf(v[2] * v[2] + v[3] * v[3] + v[4] * v[4]);
+  float ux = v[2] / un, uy = v[3] / un, uz = v[4] / un;
+  float rho = sqrtf(ux * ux + uy * uy);
+  float vb[5] = {ob[0], ob[1], 0.0f, 0.0f, 0.0f};
+  float irho = 1.0f / rho;
+  float uyb = ob[2] * irho, uzb = ob[3] * irho;
+  float rhob = -(ob[2] * uy + ob[3] * uz + ob[4] * (q * cl)) * irho * irho;
+  float qclb = ob[4] * irho;
+  float uxb = rhob * ux * irho;
+  uyb += rhob * uy * irho;
+  float dotb = uxb * v[2] + uyb * v[3] + uzb * v[4];
+  float iun = 1.0f / un;
+  vb[2] = uxb * iun - v[2] * dotb * iun * iun * iun;
+  vb[3] = uyb * iun - v[3] * dotb * iun * iun * iun;
+  vb[4] = uzb * iun - v[4] * dotb * iun * iun * iun;
+  float y0b = 0.0f, z0b = 0.0f, kqb = 0.0f;
+  bzb = 0.0f;
+  for (int i = ns - 1; i >= 0; --i) {
+    float vi[5];
+    if (i < kMaxSub) {
+      for (int j = 0; j < 5; ++j) vi[j] = vs[i][j];
+    } else {
+      for (int j = 0; j < 5; ++j) vi[j] = vs[kMaxSub - 1][j];
+      float xr = x + h * (float)(kMaxSub - 1);
+      for (int r = kMaxSub - 1; r < i; ++r) {
+        step(xr, vi);
+        xr = xr + h;
+      }
+    }
+    float xi0 = x + h * (float)i;
+    float k1[5], k2[5], k3[5], w2[5], w3[5], w4[5];
+    deriv(xi0, vi, k1);
+    for (int j = 0; j < 5; ++j) w2[j] = vi[j] + (h * 0.5f) * k1[j];
+    deriv(xi0 + h * 0.5f, w2, k2);
+    for (int j = 0; j < 5; ++j) w3[j] = vi[j] + (h * 0.5f) * k2[j];
+    deriv(xi0 + h * 0.5f, w3, k3);
+    for (int j = 0; j < 5; ++j) w4[j] = vi[j] + h * k3[j];
+    float k1b[5], k2b[5], k3b[5], k4b[5], wb[5];
+    for (int j = 0; j < 5; ++j) {
+      k1b[j] = (h / 6.0f) * vb[j];
+      k2b[j] = (h / 6.0f) * 2.0f * vb[j];
+      k3b[j] = (h / 6.0f) * 2.0f * vb[j];
+      k4b[j] = (h / 6.0f) * vb[j];
+    }
+    float xe = (i == ns - 1) ? x2 : xi0 + h;
+    for (int j = 0; j < 5; ++j) wb[j] = 0.0f;
+    rk4_deriv_vjp(p, st, xe, w4, ca, sa, uniform, bz, kq, k4b, wb, y0b, z0b, kqb, bzb);
+    for (int j = 0; j < 5; ++j) {
+      vb[j] += wb[j];
+      k3b[j] += h * wb[j];
+      wb[j] = 0.0f;
+    }
+    rk4_deriv_vjp(p, st, xi0 + h * 0.5f, w3, ca, sa, uniform, bz, kq, k3b, wb, y0b, z0b, kqb,
+                  bzb);
+    for (int j = 0; j < 5; ++j) {
+      vb[j] += wb[j];
+      k2b[j] += (h * 0.5f) * wb[j];
+      wb[j] = 0.0f;
+    }
+    rk4_deriv_vjp(p, st, xi0 + h * 0.5f, w2, ca, sa, uniform, bz, kq, k2b, wb, y0b, z0b, kqb,
+                  bzb);
+    for (int j = 0; j < 5; ++j) {
+      vb[j] += wb[j];
+      k1b[j] += (h * 0.5f) * wb[j];
+      wb[j] = 0.0f;
+    }
+    rk4_deriv_vjp(p, st, xi0, vi, ca, sa, uniform, bz, kq, k1b, wb, y0b, z0b, kqb, bzb);
+    for (int j = 0; j < 5; ++j) vb[j] += wb[j];
+  }
+  // the start: v = (0, 0, cf cl, s cl, t cl), kq = K q cl, and q cl of the output
+  float clb = vb[2] * cf + vb[3] * s + vb[4] * t + kqb * 2.99792458e-3f * q + qclb * q;
+  float cfb = vb[2] * cl;
+  sb[0] = y0b;
+  sb[1] = z0b;
+  sb[2] = vb[3] * cl - cfb * s / cf;
+  sb[3] = vb[4] * cl - clb * t * cl * cl * cl;
+  sb[4] = kqb * 2.99792458e-3f * cl + qclb * cl;
+}
+
+// d/dkB of the helix transport: sum of pb . d(state)/dkB and of Jbar .
+// d(Jacobian entries)/dkB (Jbar = 2 G J C), with a dual number in kB.
+TPC_HD float transport_kb_adjoint(float kB, float dx, const float p[5], const float Cp[15],
+                                  const Jac& J, const float pb[5], const float G[15]) {
+  D3 K{kB, 1.f, 0.f, 0.f};
+  D3 s = dc(p[2]);
+  float t = p[3], q = p[4];
+  D3 one = dc(1.0f);
+  D3 kap = q * K;
+  D3 s2 = s - dx * kap;
+  D3 c1 = dsqrt(one - s * s);
+  D3 c2 = dsqrt(one - s2 * s2);
+  D3 N = s + s2;
+  D3 D = c1 + c2;
+  D3 T = N / D;
+  D3 opt = one + T * T;
+  D3 d = dx * dsqrt(opt);
+  D3 h = 0.5f * (kap * d);
+  D3 A = chain(h, arc_factor(h.v), arc_factor_deriv(h.v));
+  D3 l = d * A;
+  D3 dDds = -(s / c1) - (s2 / c2);
+  D3 kdx = dx * K;
+  D3 dDdq = kdx * (s2 / c2);
+  D3 dTds = (dc(2.0f) - T * dDds) / D;
+  D3 dTdq = (-kdx - T * dDdq) / D;
+  D3 Jys = dx * dTds;
+  D3 Jyq = dx * dTdq;
+  D3 gg = (d * T) / opt;
+  D3 E = one / dsqrt(one - h * h);
+  D3 Bh = chain(h, arc_factor_deriv(h.v), arc_factor_deriv2(h.v));
+  D3 Jzs = t * (E * (gg * dTds));
+  D3 Jzq = t * (E * (gg * dTdq) + 0.5f * (K * ((d * d) * Bh)));
+  D3 Jzt = l;
+  // the state: y + dx T, z + t l, s2
+  float g = pb[0] * (dx * T.d0) + pb[1] * (t * l.d0) + pb[2] * s2.d0;
+  // Jbar at the entries: rows 0..2, columns 2..4
+  float Cf[5][5], Gf[5][5];
+  unpack(Cp, Cf);
+  unpack(G, Gf);
+  float M[5][3];
+  for (int b = 0; b < 3; ++b) {
+    int l2 = b + 2;
+    M[0][b] = Cf[0][l2] + J.ys * Cf[2][l2] + J.yq * Cf[4][l2];
+    M[1][b] = Cf[1][l2] + J.zs * Cf[2][l2] + J.zt * Cf[3][l2] + J.zq * Cf[4][l2];
+    M[2][b] = Cf[2][l2] + J.sq * Cf[4][l2];
+    M[3][b] = Cf[3][l2];
+    M[4][b] = Cf[4][l2];
+  }
+  float Jb[3][3];
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) {
+      float acc = 0.f;
+      for (int c = 0; c < 5; ++c) acc += Gf[a][c] * M[c][b];
+      Jb[a][b] = 2.0f * acc;
+    }
+  float gj = Jb[0][0] * Jys.d0 + Jb[0][2] * Jyq.d0 + Jb[1][0] * Jzs.d0 + Jb[1][1] * Jzt.d0 +
+             Jb[1][2] * Jzq.d0 - Jb[2][2] * dx;
+  return g + gj;
+}
+
 TPC_HD bool step_active(int rj, int pass) { return !(rj != 0 && rj < pass); }
 
 // Reverse sweep of one saved refit: writes the adjoints of the calibrated
 // coordinates gyc[at(k)], gzc[at(k)] of L = gT * chi2(pass 3). kRot as for
 // refit_track_in.
-template <bool kRot>
+template <bool kRot, bool kField>
 TPC_HD void refit_backward_in(const Geo& g, const RefitCfg& p, const TrackIn& in, const Lay& ly,
                               int n, const uint8_t* rej, const float* ckpt, float gT, float* gyc,
                               float* gzc) {
@@ -869,7 +1135,24 @@ TPC_HD void refit_backward_in(const Geo& g, const RefitCfg& p, const TrackIn& in
       for (int j = 0; j < 5; ++j) pp[j] = pr[j];
       float xx = xs;
       Jac J;
-      transport(p.kB, 2.0f, pp, xx, xi, J);
+      // the field: the helix of the local Bz plus the difference of the two
+      // Runge-Kutta integrations (propagate_field)
+      float kBs = p.kB, fca = 1.0f, fsa = 0.0f, Bs[3] = {0.f, 0.f, 0.f};
+      int ff = 0;
+      if (kField) {
+        ff = frame_of(mc);
+        fca = p.frame_c[ff];
+        fsa = p.frame_s[ff];
+        field_at(p, xs * fca - pr[0] * fsa, xs * fsa + pr[0] * fca, pr[1], Bs);
+        kBs = 2.99792458e-3f * Bs[2];
+      }
+      transport(kBs, 2.0f, pp, xx, xi, J);
+      if (kField) {
+        float full[5], unif[5];
+        rk4_field(p, pr, xs, xi, fca, fsa, false, Bs[2], full);
+        rk4_field(p, pr, xs, xi, fca, fsa, true, Bs[2], unif);
+        for (int k = 0; k < 5; ++k) pp[k] = pp[k] + (full[k] - unif[k]);
+      }
       float Cp[15];
       for (int j = 0; j < 15; ++j) Cp[j] = Cr[j];
       transport_cov(J, Cp);
@@ -882,8 +1165,28 @@ TPC_HD void refit_backward_in(const Geo& g, const RefitCfg& p, const TrackIn& in
         gzc[ly.at(ic)] = gzo + mb[1];
       }
       float xb = 0.0f;
-      if (kRot && rot != 0) xb = transport_x_adjoint(p.kB, xi - xs, pr, pp, Cr, J, pb, G);
-      transport_adjoint(p.kB, xi - xs, pr, Cr, J, pb, G);
+      if (kRot && rot != 0) xb = transport_x_adjoint(kBs, xi - xs, pr, pp, Cr, J, pb, G);
+      float fb[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+      float kbb = 0.0f, bzb = 0.0f;
+      if (kField) {
+        // the Runge-Kutta difference and the local Bz's dependence on (y, z)
+        float a_full[5], a_unif[5], bz_full = 0.0f;
+        rk4_field_vjp(p, pr, xs, xi, fca, fsa, false, Bs[2], pb, a_full, bz_full);
+        rk4_field_vjp(p, pr, xs, xi, fca, fsa, true, Bs[2], pb, a_unif, bzb);
+        for (int k = 0; k < 5; ++k) fb[k] = a_full[k] - a_unif[k];
+        kbb = transport_kb_adjoint(kBs, xi - xs, pr, Cr, J, pb, G);
+      }
+      transport_adjoint(kBs, xi - xs, pr, Cr, J, pb, G);
+      if (kField) {
+        float gB[3][3];
+        float X = xs * fca - pr[0] * fsa, Y = xs * fsa + pr[0] * fca;
+        field_grad(p, X, Y, pr[1], gB);
+        float dbz_dy = -(gB[2][0] * fsa) + gB[2][1] * fca, dbz_dz = gB[2][2];
+        float w = kbb * 2.99792458e-3f - bzb;  // through kB of the helix, minus the uniform run
+        for (int k = 0; k < 5; ++k) pb[k] += fb[k];
+        pb[0] += w * dbz_dy;
+        pb[1] += w * dbz_dz;
+      }
       if (kRot && rot != 0) rotate_adjoint(p.kB, p.rot_c[rot], p.rot_s[rot], p0, C0, xb, pb, G);
       kc = kp;
       if (kp >= 0) {
@@ -908,13 +1211,14 @@ TPC_HD void refit_backward_in(const Geo& g, const RefitCfg& p, const TrackIn& in
   }
 }
 
+template <bool kField = false>
 TPC_HD void refit_backward_track(const Geo& g, const RefitCfg& p, const TrackIn& in, const Lay& ly,
                                  int n, const uint8_t* rej, const float* ckpt, float gT,
                                  float* gyc, float* gzc, bool multi) {
   if (multi)
-    refit_backward_in<true>(g, p, in, ly, n, rej, ckpt, gT, gyc, gzc);
+    refit_backward_in<true, kField>(g, p, in, ly, n, rej, ckpt, gT, gyc, gzc);
   else
-    refit_backward_in<false>(g, p, in, ly, n, rej, ckpt, gT, gyc, gzc);
+    refit_backward_in<false, kField>(g, p, in, ly, n, rej, ckpt, gT, gyc, gzc);
 }
 
 }  // namespace tpc

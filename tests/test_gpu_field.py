@@ -54,18 +54,33 @@ def test_field_refit_matches_the_oracle(mode):
     assert np.median(eu) > 10 * np.median(e[:, 4])
 
 
-def test_adjoint_in_the_field_is_refused():
+@pytest.mark.parametrize("merged", [False, True])
+def test_field_adjoint_matches_the_oracle_gradient(merged):
+    """The adjoint of the full-field refit (reverse sweep through the
+    Runge-Kutta sub-steps and the local Bz of the helix part) against the
+    oracle's reverse-mode tape through the same transport, on truth tracks
+    per sector and merged across sectors."""
     import torch
-    from paper_1811_11481_b300.binding import TpcError
     from synth.field import solenoid_field
     geo = synth.geometry()
     f = solenoid_field(eps=0.04)
-    ev = synth.make_tiny(seed=65, n_tracks=50, central=True, field=f)
+    ev = synth.make_tiny(seed=65, n_tracks=300, central=True, field=f, noise_frac=0.0)
+    ts, ci, tc, _ = synth.truth_tracks(ev, 30, merged=merged)
     tr = _tracker(geo, f)
     tr.set_calib()
     tr.load(tr.upload(ev))
-    tr.find()
-    tr.refit(save_for_backward=True)
-    with pytest.raises(TpcError) as ei:
-        tr.refit_backward(torch.ones(tr.n_tracks, device=tr.dev))
-    assert ei.value.status == 5
+    tr.set_tracks(torch.as_tensor(ts.astype(np.int32)), torch.as_tensor(ci.astype(np.int32)),
+                  torch.as_tensor(tc))
+    r = {k: v.cpu().numpy() for k, v in tr.refit(save_for_backward=True).items()}
+    nt = ts.size - 1
+    w = torch.linspace(0.5, 1.5, nt, device=tr.dev)
+    gy, gz, _ = [t.cpu().numpy() for t in tr.refit_backward(w)]
+    o = oracle.Oracle(ev, geo, default_params(), synth.nominal_calib(), field=f)
+    ref = o.refit(ts, ci, tc, prec=64)
+    ry, rz, _ = o.refit_grad(ts, ci, tc, ref["seeds"], r["rej"],
+                             w.cpu().numpy().astype(np.float64))
+    ok = (r["status"] == 0) & (ref["status"] == 0)
+    assert ok.sum() > (40 if merged else 150)   # merged loopers reach s_max
+    m = np.repeat(ok, np.diff(ts.astype(np.int64)))
+    for a, b in ((gy, ry), (gz, rz)):
+        assert np.linalg.norm(a[m] - b[m]) / np.linalg.norm(b[m]) < 1e-3
