@@ -331,6 +331,7 @@ tpc_status tpc_create(const tpc_geometry* geo, const tpc_params* params, void* s
   }
   apply_tuning(ctx);
   setup_find_kernels();
+  setup_merge_kernels();
   if (st != TPC_OK) {
     tpc_destroy(ctx);
     return st;

@@ -321,6 +321,8 @@ void launch_merge(Prof* P, const Geo& g, const Params& p, const Cal& c, const Cl
                   int64_t cap_n, bool copy, TrackBuf& tb, MergeBuf& mb, const float* params,
                   const float* cov, const float* x, const int32_t* status, int32_t* next_out,
                   float* link_chi2, uint32_t* cnt, uint32_t* err, cudaStream_t s);
+// Kernel attributes of the merge (shared-memory limit), once per context.
+void setup_merge_kernels();
 // launcher (tpc_compress.cu): residuals of the track set's clusters against
 // the track model (and the decoded clusters; dy, dz may be null).
 void launch_compress(Prof* P, const Geo& g, const Cal& c, const ClIn& cl, const Params& p,

@@ -650,6 +650,11 @@ __global__ void k_refine_time(int cap, Geo g, Cal c, ClIn cl, const uint32_t* cn
 
 }  // namespace
 
+void setup_merge_kernels() {
+  cudaFuncSetAttribute(k_mg_sort, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)(kBucketSortMax * sizeof(unsigned long long)));
+}
+
 void launch_refine_time(Prof* P, const Geo& g, const Cal& c, const ClIn& cl, int64_t cap_tr,
                         const uint32_t* cnt, TrackBuf& tb, const float* params, const float* x,
                         const int32_t* status, double* t_out, cudaStream_t s) {
@@ -692,12 +697,6 @@ void launch_merge(Prof* P, const Geo& g, const Params& p, const Cal& c, const Cl
   TPC_LAUNCH(P, "k_mg_scatter", s,
              k_mg_scatter<<<nblk(cap_n, kMB), kMB, 0, s>>>(mb.n_seg, mb.info, mb.bk_cnt,
                                                            mb.bk_fill, mb.bk_seg));
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_mg_sort, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)(kBucketSortMax * sizeof(unsigned long long)));
-    attr = true;
-  }
   TPC_LAUNCH(P, "k_mg_sort", s,
              k_mg_sort<<<nb, kSortThreads, kBucketSortMax * sizeof(unsigned long long), s>>>(
                  mb.bk_cnt, mb.bk_seg, mb.bk_v, mb.bk_t, mb.bk_rlo, mb.bk_cls, mb.rows, params,
