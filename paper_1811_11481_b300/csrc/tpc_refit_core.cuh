@@ -815,13 +815,52 @@ TPC_HD void rk4_deriv_vjp(const RefitCfg& p, const float st[5], float xa, const 
 
 constexpr int kMaxSub = 64;  // stored Runge-Kutta sub-step states
 
-// Adjoint of rk4_field: given the adjoint ob of its output, the adjoint sb of
-// the start state (y, z, sin phi, tan lambda, q/pT) and of the uniform bz.
-// Sub-step start states are recomputed by a forward pass (and, beyond
-// kMaxSub sub-steps, again from the start for each sub-step).
-TPC_HD void rk4_field_vjp(const RefitCfg& p, const float st[5], float x, float x2, float ca,
-                          float sa, bool uniform, float bz, const float ob[5], float sb[5],
-                          float& bzb) {
+// The forward pass of rk4_field with its sub-step start states kept for the
+// adjoint (the first kMaxSub of them; later ones are recomputed).
+struct Rk4Tape {
+  float vs[kMaxSub][5];
+  float v[5];  // the end state
+  int ns;
+};
+
+TPC_HD void rk4_deriv(const RefitCfg& p, const float st[5], float xa, const float w[5], float ca,
+                      float sa, bool uniform, float bz, float kq, float d[5]) {
+  float b0 = 0.0f, b1 = 0.0f, b2 = bz;
+  if (!uniform) {
+    float B[3];
+    float yy = st[0] + w[0];
+    field_at(p, xa * ca - yy * sa, xa * sa + yy * ca, st[1] + w[1], B);
+    b0 = B[0] * ca + B[1] * sa;
+    b1 = -(B[0] * sa) + B[1] * ca;
+    b2 = B[2];
+  }
+  float iu = 1.0f / w[2];
+  float f = kq * iu;
+  d[0] = w[3] * iu;
+  d[1] = w[4] * iu;
+  d[2] = f * (w[3] * b2 - w[4] * b1);
+  d[3] = f * (w[4] * b0 - w[2] * b2);
+  d[4] = f * (w[2] * b1 - w[3] * b0);
+}
+
+TPC_HD void rk4_substep(const RefitCfg& p, const float st[5], float xa, float h, float ca,
+                        float sa, bool uniform, float bz, float kq, float v[5]) {
+  float k1[5], k2[5], k3[5], k4[5], w[5];
+  rk4_deriv(p, st, xa, v, ca, sa, uniform, bz, kq, k1);
+  for (int j = 0; j < 5; ++j) w[j] = v[j] + (h * 0.5f) * k1[j];
+  rk4_deriv(p, st, xa + h * 0.5f, w, ca, sa, uniform, bz, kq, k2);
+  for (int j = 0; j < 5; ++j) w[j] = v[j] + (h * 0.5f) * k2[j];
+  rk4_deriv(p, st, xa + h * 0.5f, w, ca, sa, uniform, bz, kq, k3);
+  for (int j = 0; j < 5; ++j) w[j] = v[j] + h * k3[j];
+  rk4_deriv(p, st, xa + h, w, ca, sa, uniform, bz, kq, k4);
+  for (int j = 0; j < 5; ++j)
+    v[j] = v[j] + (h / 6.0f) * (k1[j] + 2.0f * k2[j] + 2.0f * k3[j] + k4[j]);
+}
+
+// rk4_field's forward pass (same operations, without the failure checks:
+// the forward refit passed them), keeping the tape; out as rk4_field's.
+TPC_HD void rk4_field_fwd(const RefitCfg& p, const float st[5], float x, float x2, float ca,
+                          float sa, bool uniform, float bz, Rk4Tape& tp, float out[5]) {
   float s = st[2], t = st[3], q = st[4];
   float cl = 1.0f / sqrtf(1.0f + t * t);
   float cf = sqrtf(1.0f - s * s);
@@ -830,47 +869,39 @@ TPC_HD void rk4_field_vjp(const RefitCfg& p, const float st[5], float x, float x
   int ns = (int)ceilf(fabsf(dx) * 2.0f);
   if (ns < 1) ns = 1;
   float h = dx / (float)ns;
-  auto deriv = [&](float xa, const float w[5], float d[5]) {
-    float b0 = 0.0f, b1 = 0.0f, b2 = bz;
-    if (!uniform) {
-      float B[3];
-      float yy = st[0] + w[0];
-      field_at(p, xa * ca - yy * sa, xa * sa + yy * ca, st[1] + w[1], B);
-      b0 = B[0] * ca + B[1] * sa;
-      b1 = -(B[0] * sa) + B[1] * ca;
-      b2 = B[2];
-    }
-    float iu = 1.0f / w[2];
-    float f = kq * iu;
-    d[0] = w[3] * iu;
-    d[1] = w[4] * iu;
-    d[2] = f * (w[3] * b2 - w[4] * b1);
-    d[3] = f * (w[4] * b0 - w[2] * b2);
-    d[4] = f * (w[2] * b1 - w[3] * b0);
-  };
-  float v0[5] = {0.0f, 0.0f, cf * cl, s * cl, t * cl};
-  auto step = [&](float xa, float v[5]) {
-    float k1[5], k2[5], k3[5], k4[5], w[5];
-    deriv(xa, v, k1);
-    for (int j = 0; j < 5; ++j) w[j] = v[j] + (h * 0.5f) * k1[j];
-    deriv(xa + h * 0.5f, w, k2);
-    for (int j = 0; j < 5; ++j) w[j] = v[j] + (h * 0.5f) * k2[j];
-    deriv(xa + h * 0.5f, w, k3);
-    for (int j = 0; j < 5; ++j) w[j] = v[j] + h * k3[j];
-    deriv(xa + h, w, k4);
-    for (int j = 0; j < 5; ++j)
-      v[j] = v[j] + (h / 6.0f) * (k1[j] + 2.0f * k2[j] + 2.0f * k3[j] + k4[j]);
-  };
-  float vs[kMaxSub][5];
-  float v[5];
-  for (int j = 0; j < 5; ++j) v[j] = v0[j];
+  float v[5] = {0.0f, 0.0f, cf * cl, s * cl, t * cl};
   float xa = x;
   for (int i = 0; i < ns; ++i) {
     if (i < kMaxSub)
-      for (int j = 0; j < 5; ++j) vs[i][j] = v[j];
-    step(xa, v);
+      for (int j = 0; j < 5; ++j) tp.vs[i][j] = v[j];
+    rk4_substep(p, st, xa, h, ca, sa, uniform, bz, kq, v);
     xa = (i == ns - 1) ? x2 : xa + h;
   }
+  tp.ns = ns;
+  for (int j = 0; j < 5; ++j) tp.v[j] = v[j];
+  float un = sqrtf(v[2] * v[2] + v[3] * v[3] + v[4] * v[4]);
+  float ux = v[2] / un, uy = v[3] / un, uz = v[4] / un;
+  float rho = sqrtf(ux * ux + uy * uy);
+  out[0] = v[0];
+  out[1] = v[1];
+  out[2] = uy / rho;
+  out[3] = uz / rho;
+  out[4] = (q * cl) / rho;
+}
+
+// Adjoint of rk4_field from its tape: given the adjoint ob of its output, the
+// adjoint sb of the start state (y, z, sin phi, tan lambda, q/pT) and of the
+// uniform bz.
+TPC_HD void rk4_field_rev(const RefitCfg& p, const float st[5], float x, float x2, float ca,
+                          float sa, bool uniform, float bz, const Rk4Tape& tp,
+                          const float ob[5], float sb[5], float& bzb) {
+  float s = st[2], t = st[3], q = st[4];
+  float cl = 1.0f / sqrtf(1.0f + t * t);
+  float cf = sqrtf(1.0f - s * s);
+  float kq = 2.99792458e-3f * (q * cl);
+  int ns = tp.ns;
+  float h = (x2 - x) / (float)ns;
+  const float* v = tp.v;
   // output: (v0, v1, uy / rho, uz / rho, q cl / rho) with u = v / |v|
   float un = sqrtf(v[2] * v[2] + v[3] * v[3] + v[4] * v[4]);
   float ux = v[2] / un, uy = v[3] / un, uz = v[4] / un;
@@ -892,22 +923,22 @@ TPC_HD void rk4_field_vjp(const RefitCfg& p, const float st[5], float x, float x
   for (int i = ns - 1; i >= 0; --i) {
     float vi[5];
     if (i < kMaxSub) {
-      for (int j = 0; j < 5; ++j) vi[j] = vs[i][j];
+      for (int j = 0; j < 5; ++j) vi[j] = tp.vs[i][j];
     } else {
-      for (int j = 0; j < 5; ++j) vi[j] = vs[kMaxSub - 1][j];
+      for (int j = 0; j < 5; ++j) vi[j] = tp.vs[kMaxSub - 1][j];
       float xr = x + h * (float)(kMaxSub - 1);
       for (int r = kMaxSub - 1; r < i; ++r) {
-        step(xr, vi);
+        rk4_substep(p, st, xr, h, ca, sa, uniform, bz, kq, vi);
         xr = xr + h;
       }
     }
     float xi0 = x + h * (float)i;
     float k1[5], k2[5], k3[5], w2[5], w3[5], w4[5];
-    deriv(xi0, vi, k1);
+    rk4_deriv(p, st, xi0, vi, ca, sa, uniform, bz, kq, k1);
     for (int j = 0; j < 5; ++j) w2[j] = vi[j] + (h * 0.5f) * k1[j];
-    deriv(xi0 + h * 0.5f, w2, k2);
+    rk4_deriv(p, st, xi0 + h * 0.5f, w2, ca, sa, uniform, bz, kq, k2);
     for (int j = 0; j < 5; ++j) w3[j] = vi[j] + (h * 0.5f) * k2[j];
-    deriv(xi0 + h * 0.5f, w3, k3);
+    rk4_deriv(p, st, xi0 + h * 0.5f, w3, ca, sa, uniform, bz, kq, k3);
     for (int j = 0; j < 5; ++j) w4[j] = vi[j] + h * k3[j];
     float k1b[5], k2b[5], k3b[5], k4b[5], wb[5];
     for (int j = 0; j < 5; ++j) {
@@ -1147,10 +1178,11 @@ TPC_HD void refit_backward_in(const Geo& g, const RefitCfg& p, const TrackIn& in
         kBs = 2.99792458e-3f * Bs[2];
       }
       transport(kBs, 2.0f, pp, xx, xi, J);
+      Rk4Tape tfull, tunif;  // (used with kField only)
       if (kField) {
         float full[5], unif[5];
-        rk4_field(p, pr, xs, xi, fca, fsa, false, Bs[2], full);
-        rk4_field(p, pr, xs, xi, fca, fsa, true, Bs[2], unif);
+        rk4_field_fwd(p, pr, xs, xi, fca, fsa, false, Bs[2], tfull, full);
+        rk4_field_fwd(p, pr, xs, xi, fca, fsa, true, Bs[2], tunif, unif);
         for (int k = 0; k < 5; ++k) pp[k] = pp[k] + (full[k] - unif[k]);
       }
       float Cp[15];
@@ -1171,8 +1203,8 @@ TPC_HD void refit_backward_in(const Geo& g, const RefitCfg& p, const TrackIn& in
       if (kField) {
         // the Runge-Kutta difference and the local Bz's dependence on (y, z)
         float a_full[5], a_unif[5], bz_full = 0.0f;
-        rk4_field_vjp(p, pr, xs, xi, fca, fsa, false, Bs[2], pb, a_full, bz_full);
-        rk4_field_vjp(p, pr, xs, xi, fca, fsa, true, Bs[2], pb, a_unif, bzb);
+        rk4_field_rev(p, pr, xs, xi, fca, fsa, false, Bs[2], tfull, pb, a_full, bz_full);
+        rk4_field_rev(p, pr, xs, xi, fca, fsa, true, Bs[2], tunif, pb, a_unif, bzb);
         for (int k = 0; k < 5; ++k) fb[k] = a_full[k] - a_unif[k];
         kbb = transport_kb_adjoint(kBs, xi - xs, pr, Cr, J, pb, G);
       }
