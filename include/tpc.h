@@ -430,11 +430,15 @@ tpc_status tpc_profile_read(tpc_ctx* ctx, tpc_kernel_stat* out, int32_t cap, int
  *   tracklet_block      threads per block of the tracklet kernel (64, 128, 256)
  *   tracklet_per_sm     resident tracklet blocks per SM (0 .. 64); 0 = as many
  *                       as fit
+ *   tracklet_regs       register cap of the tracklet kernel: 0 = the compiler's
+ *                       choice (~170 per thread), 128 = at most 128 (twice the
+ *                       resident threads per SM)
  * tpc_set_tuning validates (TPC_ERR_ARG) and applies from the next
  * tpc_load_clusters (grid) or tpc_find_tracks (tracklet kernel);
  * TPC_ERR_STATE while capturing. tpc_autotune searches one parameter at a
  * time, in that order, over grid_tau {0.5, 1, 2, 4}, grid_ny_max {8, 16, 32},
- * tracklet_block {64, 128, 256}, tracklet_per_sm {0, 1, 2, 4}, on the loaded
+ * tracklet_block {64, 128, 256}, tracklet_regs {0, 128}, tracklet_per_sm
+ * {0, 1, 2, 4}, on the loaded
  * batch: each candidate runs load + find (grid parameters) or find (tracklet
  * parameters) `repeats` times (1 .. 50; < 1 means 3) after one untimed run,
  * timed with CUDA events on the context's stream, and the fastest median is
@@ -445,6 +449,7 @@ typedef struct {
   int32_t grid_ny_max;
   int32_t tracklet_block;
   int32_t tracklet_per_sm;
+  int32_t tracklet_regs;
 } tpc_tuning;
 tpc_status tpc_get_tuning(const tpc_ctx* ctx, tpc_tuning* out);
 tpc_status tpc_set_tuning(tpc_ctx* ctx, const tpc_tuning* in);

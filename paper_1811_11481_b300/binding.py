@@ -68,7 +68,8 @@ class tpc_kernel_stat(C.Structure):
 
 class tpc_tuning(C.Structure):
     _fields_ = [("grid_tau", C.c_float), ("grid_ny_max", C.c_int32),
-                ("tracklet_block", C.c_int32), ("tracklet_per_sm", C.c_int32)]
+                ("tracklet_block", C.c_int32), ("tracklet_per_sm", C.c_int32),
+                ("tracklet_regs", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -28,7 +28,7 @@ struct tpc_ctx {
   bool loaded = false;
   int K = 0;
   GridDims gd{};
-  tpc_tuning tune{1.0f, 16, 128, 0};
+  tpc_tuning tune{1.0f, 16, 128, 0, 0};
   Shapes sh{};
   int sms = 0;
   FindBuf fb{};
@@ -165,7 +165,8 @@ tpc_status read_back(tpc_ctx* ctx) {
 void apply_tuning(tpc_ctx* ctx) {
   const tpc_tuning& t = ctx->tune;
   ctx->sh.tl_block = t.tracklet_block;
-  int per = tracklet_blocks_per_sm(t.tracklet_block);
+  ctx->sh.tl_regs = t.tracklet_regs;
+  int per = tracklet_blocks_per_sm(t.tracklet_block, t.tracklet_regs);
   if (t.tracklet_per_sm > 0 && t.tracklet_per_sm < per) per = t.tracklet_per_sm;
   ctx->sh.tl_grid = (ctx->sms > 0 && per > 0) ? ctx->sms * per : 0;
 }
@@ -952,7 +953,7 @@ tpc_status tpc_set_tuning(tpc_ctx* ctx, const tpc_tuning* in) {
   if (ctx->capturing) return fail(ctx, TPC_ERR_STATE, "tuning changes during graph capture");
   if (!(in->grid_tau >= 0.25f && in->grid_tau <= 16.0f) || in->grid_ny_max < 1 ||
       in->grid_ny_max > 64 || !valid_block(in->tracklet_block) || in->tracklet_per_sm < 0 ||
-      in->tracklet_per_sm > 64)
+      in->tracklet_per_sm > 64 || (in->tracklet_regs != 0 && in->tracklet_regs != 128))
     return fail(ctx, TPC_ERR_ARG, "tuning out of range");
   ctx->tune = *in;
   apply_tuning(ctx);
@@ -1014,6 +1015,7 @@ tpc_status tpc_autotune(tpc_ctx* ctx, int32_t repeats, tpc_tuning* out) {
   const float taus[] = {0.5f, 1.0f, 2.0f, 4.0f};
   const int nys[] = {8, 16, 32};
   const int blocks[] = {64, 128, 256};
+  const int regs[] = {0, 128};
   const int pers[] = {0, 1, 2, 4};
   tpc_tuning best = ctx->tune;
   auto trial = [&](tpc_tuning cand, int which, float* ms) -> tpc_status {
@@ -1022,17 +1024,18 @@ tpc_status tpc_autotune(tpc_ctx* ctx, int32_t repeats, tpc_tuning* out) {
     return which == 0 ? time_median(ctx, repeats, load_find, ms)
                       : time_median(ctx, repeats, find, ms);
   };
-  for (int knob = 0; knob < 4 && st == TPC_OK; ++knob) {
+  for (int knob = 0; knob < 5 && st == TPC_OK; ++knob) {
     float best_ms = 0.0f;
     tpc_tuning keep = best;
-    int nc = knob == 0 ? 4 : knob == 1 ? 3 : knob == 2 ? 3 : 4;
+    int nc = knob == 0 ? 4 : knob == 1 ? 3 : knob == 2 ? 3 : knob == 3 ? 2 : 4;
     for (int k = 0; k < nc && st == TPC_OK; ++k) {
       tpc_tuning cand = best;
       if (knob == 0) cand.grid_tau = taus[k];
       else if (knob == 1) cand.grid_ny_max = nys[k];
       else if (knob == 2) cand.tracklet_block = blocks[k];
-      else if (knob == 3) {
-        int mx = tracklet_blocks_per_sm(cand.tracklet_block);
+      else if (knob == 3) cand.tracklet_regs = regs[k];
+      else if (knob == 4) {
+        int mx = tracklet_blocks_per_sm(cand.tracklet_block, cand.tracklet_regs);
         if (pers[k] > 0 && pers[k] >= mx) continue;  // same as "as many as fit"
         cand.tracklet_per_sm = pers[k];
       }

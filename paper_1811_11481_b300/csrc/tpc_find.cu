@@ -816,8 +816,13 @@ __device__ int step_measurement(const Geo& g, const Cal& c, const Params& p, con
 //   phase 1: seed fit in calibrated coordinates (after the collision time)
 //   phase 2: outward following from the seed end
 //   phase 3: inward following from the outermost pick down to row 0
-template <int BS>
-__global__ void __launch_bounds__(BS) k_tracklets(Geo g, Cal c, Params p, GridDims gd, Grid G,
+// kCap: the launch bound asks for 512 resident threads per SM, which holds
+// the kernel to 128 registers per thread (no spills): 16 warps per SM instead
+// of 8-12, for the workloads with more tracklets than resident threads.
+// Without it the compiler takes ~170 registers, which keeps a single long
+// tracklet a little faster.
+template <int BS, bool kCap>
+__global__ void __launch_bounds__(BS, kCap ? 512 / BS : 1) k_tracklets(Geo g, Cal c, Params p, GridDims gd, Grid G,
                                                   const uint2* es_dims, int mode,
                                                   const int32_t* upc,
                                                   const uint32_t* gseg, const uint32_t* starts,
@@ -1439,11 +1444,17 @@ void setup_find_kernels() {
                        (int)sort_smem(kSortTileBig, kGridBinsMax));
 }
 
-int tracklet_blocks_per_sm(int block) {
+template <bool kCap>
+cudaError_t tracklet_occupancy(int* per, int block) {
+  return block == 64    ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(per, k_tracklets<64, kCap>, 64, 0)
+         : block == 256 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(per, k_tracklets<256, kCap>, 256, 0)
+                        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(per, k_tracklets<128, kCap>, 128, 0);
+}
+
+int tracklet_blocks_per_sm(int block, int regs) {
   int per = 0;
-  cudaError_t e = block == 64    ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_tracklets<64>, 64, 0)
-                  : block == 256 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_tracklets<256>, 256, 0)
-                                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_tracklets<128>, 128, 0);
+  cudaError_t e = regs == 128 ? tracklet_occupancy<true>(&per, block)
+                              : tracklet_occupancy<false>(&per, block);
   return e == cudaSuccess ? per : 0;
 }
 
@@ -1468,18 +1479,23 @@ void launch_find(Prof* P, const Geo& g, const Cal& c, const Params& p, const ClI
   // persistent grid: the tuned number of resident blocks, or fewer for a
   // small capacity
   cudaMemsetAsync(b.queue, 0, sizeof(uint32_t), s);
-#define TPC_TRACKLETS(BS)                                                                   \
+#define TPC_TRACKLETS(BS, CAP)                                                              \
   {                                                                                        \
     int nbk = nblk(b.cap_tl, BS);                                                          \
     if (sh.tl_grid > 0 && nbk > sh.tl_grid) nbk = sh.tl_grid;                              \
     TPC_LAUNCH(P, "k_tracklets", s,                                                        \
-               k_tracklets<BS><<<nbk, BS, 0, s>>>(g, c, p, gd, G, b.es_dims, cl.mode, b.upc, \
-                                                  b.gseg, b.starts, b.seed_end, cnt, b.nh,  \
-                                                  b.hits, b.range, b.that, b.queue));       \
+               (k_tracklets<BS, CAP><<<nbk, BS, 0, s>>>(                                   \
+                   g, c, p, gd, G, b.es_dims, cl.mode, b.upc, b.gseg, b.starts,             \
+                   b.seed_end, cnt, b.nh, b.hits, b.range, b.that, b.queue)));             \
   }
-  if (sh.tl_block == 64) TPC_TRACKLETS(64)
-  else if (sh.tl_block == 256) TPC_TRACKLETS(256)
-  else TPC_TRACKLETS(128)
+  const bool cap = sh.tl_regs == 128;
+  if (sh.tl_block == 64) {
+    if (cap) TPC_TRACKLETS(64, true) else TPC_TRACKLETS(64, false)
+  } else if (sh.tl_block == 256) {
+    if (cap) TPC_TRACKLETS(256, true) else TPC_TRACKLETS(256, false)
+  } else {
+    if (cap) TPC_TRACKLETS(128, true) else TPC_TRACKLETS(128, false)
+  }
 #undef TPC_TRACKLETS
   TPC_LAUNCH(P, "k_tl_weight", s,
              k_tl_weight<<<min(nblk(b.cap_tl * 32, kB256), 16 * 148), kB256, 0, s>>>(

@@ -281,9 +281,10 @@ void launch_load(Prof* P, const Geo& g, const Cal& c, const ClIn& cl, const Grid
 struct Shapes {
   int tl_block = 128;    // tracklet kernel threads per block (64, 128, 256)
   int tl_grid = 0;       // persistent tracklet grid (0: one block per 128 tracklets)
+  int tl_regs = 0;       // tracklet kernel register cap (0: compiler's choice, 128)
 };
 // Resident blocks per SM of the tracklet kernel at a block size.
-int tracklet_blocks_per_sm(int block);
+int tracklet_blocks_per_sm(int block, int regs);
 // Kernel attributes (shared-memory limits), once per context.
 void setup_find_kernels();
 void launch_find(Prof* P, const Geo& g, const Cal& c, const Params& p, const ClIn& cl,

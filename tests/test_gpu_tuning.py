@@ -11,9 +11,10 @@ pytestmark = pytest.mark.gpu
 
 # corners of the tuning space (the autotuner's candidates lie inside)
 TUNINGS = [
-    dict(grid_tau=0.25, grid_ny_max=1, tracklet_block=64, tracklet_per_sm=1),
-    dict(grid_tau=4.0, grid_ny_max=64, tracklet_block=256, tracklet_per_sm=0),
-    dict(grid_tau=16.0, grid_ny_max=8, tracklet_block=128, tracklet_per_sm=2),
+    dict(grid_tau=0.25, grid_ny_max=1, tracklet_block=64, tracklet_per_sm=1, tracklet_regs=0),
+    dict(grid_tau=4.0, grid_ny_max=64, tracklet_block=256, tracklet_per_sm=0, tracklet_regs=128),
+    dict(grid_tau=16.0, grid_ny_max=8, tracklet_block=128, tracklet_per_sm=2, tracklet_regs=128),
+    dict(grid_tau=1.0, grid_ny_max=16, tracklet_block=64, tracklet_per_sm=0, tracklet_regs=128),
 ]
 
 
@@ -64,6 +65,7 @@ def test_autotune_chooses_a_candidate_and_keeps_results():
     assert t["grid_ny_max"] in (8, 16, 32)
     assert t["tracklet_block"] in (64, 128, 256)
     assert t["tracklet_per_sm"] in (0, 1, 2, 4)
+    assert t["tracklet_regs"] in (0, 128)
     assert tr.get_tuning() == t
     # the batch stays loaded and found with the chosen tuning
     nt, na, _ = tr.counts()
@@ -75,7 +77,8 @@ def test_invalid_tuning_is_refused():
     tr = tracker(synth.geometry())
     good = tr.get_tuning()
     for bad in (dict(grid_tau=0.0), dict(grid_tau=100.0), dict(grid_ny_max=0),
-                dict(tracklet_block=96), dict(tracklet_block=512), dict(tracklet_per_sm=-1)):
+                dict(tracklet_block=96), dict(tracklet_block=512), dict(tracklet_per_sm=-1),
+                dict(tracklet_regs=64), dict(tracklet_regs=-1)):
         with pytest.raises(TpcError) as ei:
             tr.set_tuning(**bad)
         assert ei.value.status == 1
