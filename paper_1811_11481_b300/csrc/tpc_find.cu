@@ -819,10 +819,10 @@ __device__ int step_measurement(const Geo& g, const Cal& c, const Params& p, con
 // kCap: the launch bound asks for 512 resident threads per SM, which holds
 // the kernel to 128 registers per thread (no spills): 16 warps per SM instead
 // of 8-12, for the workloads with more tracklets than resident threads.
-// Without it the compiler takes ~170 registers, which keeps a single long
-// tracklet a little faster.
+// Without it (a minimum of 0 blocks: no occupancy target) the compiler
+// takes ~170 registers, which keeps a single long tracklet a little faster.
 template <int BS, bool kCap>
-__global__ void __launch_bounds__(BS, kCap ? 512 / BS : 1) k_tracklets(Geo g, Cal c, Params p, GridDims gd, Grid G,
+__global__ void __launch_bounds__(BS, kCap ? 512 / BS : 0) k_tracklets(Geo g, Cal c, Params p, GridDims gd, Grid G,
                                                   const uint2* es_dims, int mode,
                                                   const int32_t* upc,
                                                   const uint32_t* gseg, const uint32_t* starts,
