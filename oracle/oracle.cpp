@@ -999,7 +999,8 @@ bool seed_three_points(const Ctx& c, const std::vector<R>& x, const std::vector<
   R cross = ax * by - ay * bx;
   R la = sqrt_(ax * ax + ay * ay), lb = sqrt_(bx * bx + by * by), le = sqrt_(ex * ex + ey * ey);
   R kap = (R(-2) * cross) / ((la * lb) * le);
-  R q = kap / kB_of<R>(c);
+  // no field: q/pT is not observable and is held at 0 (straight lines)
+  R q = kB_of<R>(c) != R(0) ? kap / kB_of<R>(c) : R(0);
   R hs = (kap * lb) * R(0.5);
   if (!(abs_(hs) < R(1))) return false;
   R s2 = (by / lb) * sqrt_(R(1) - hs * hs) - (bx / lb) * hs;

@@ -280,7 +280,8 @@ TPC_HD bool seed3(const Geo& g, const RefitCfg& p, const TrackIn& in, const Lay&
   st[1] = in.zc[ly.at(i2)];
   st[2] = s2;
   st[3] = (in.zc[ly.at(i2)] - in.zc[ly.at(i0)]) / arc;
-  st[4] = kap / g.kB;
+  // without a field q/pT is not observable: it stays 0 (straight lines)
+  st[4] = g.kB != 0.0f ? kap / g.kB : 0.0f;
   return true;
 }
 

@@ -542,8 +542,11 @@ def make_adjoint(seed=4, n_events=10, n_tracks=10000, tf_start=1.0e6,
 
 
 def make_tiny(seed=5, n_tracks=20, sectors=(0,), noise_frac=0.0, mode="event",
-              central=False, calib=None, tf_start=0.0, n_coll=1, sigma=0.1, field=None):
-    """Small cases for tests: a few tracks in chosen sectors."""
+              central=False, calib=None, tf_start=0.0, n_coll=1, sigma=0.1, field=None,
+              pt=None):
+    """Small cases for tests: a few tracks in chosen sectors. pt (GeV/c):
+    give every particle this transverse momentum (pt=1000: tracks straight
+    to 5e-3 cm over the rows, for a tracker run without field)."""
     rng = np.random.default_rng(seed)
     geo = geometry()
     parts = []
@@ -559,6 +562,8 @@ def make_tiny(seed=5, n_tracks=20, sectors=(0,), noise_frac=0.0, mode="event",
                                [i for i, s in enumerate(sectors) if s >= 18])
                 pp["eta"] = np.where(flip, -pp["eta"], pp["eta"])
             parts.append(pp)
+        if pt is not None:
+            parts[-1]["pt"] = np.full_like(parts[-1]["pt"], float(pt))
     t_colls = tf_start + 10.0 * (1.0 + np.arange(n_coll)) if mode == "time" else None
     ev = make_event(rng, geo, parts, mode=mode, t_colls=t_colls,
                     noise_frac=noise_frac, calib=calib, tf_start=tf_start,

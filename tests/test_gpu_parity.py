@@ -287,3 +287,61 @@ def test_invalid_input_reports_error(geo):
     with pytest.raises(TpcError) as ei:
         tr2.refit_backward(torch.ones(max(tr2.n_tracks, 1), device=tr2.dev))
     assert ei.value.status == 5
+
+
+@pytest.mark.parametrize("mode", ["event", "time"])
+def test_zero_field(geo, mode):
+    """The degenerate case Bz = 0: straight tracks (1 TeV/c, 5e-3 cm from a
+    line over the rows) through a tracker without field, where the transport
+    and the closest approach take their straight-line branches and q/pT is
+    held at 0. Discrete outputs equal the oracle's FP32 mirror, the refit the
+    FP64 oracle within tolerance, the adjoint the oracle's tape within 1e-3."""
+    import dataclasses
+
+    import torch
+    geo0 = dataclasses.replace(geo, bz=np.float32(0.0))
+    kw = dict(mode="time", n_coll=2, tf_start=1.0e6) if mode == "time" else {}
+    ev = synth.make_tiny(seed=43, n_tracks=480, sectors=(0, 7, 25), noise_frac=0.1, pt=1000.0,
+                         **kw)
+    tr = tracker(geo0)
+    g = gpu_find(tr, ev)
+    o, f = oracle_find(ev, geo0)
+    assert np.array_equal(g["up"], f["up"]) and np.array_equal(g["dn"], f["dn"])
+    sg, lg, tg = canonical_tracks(g["track_start"], g["cluster_idx"], g["start_hit"], g["t_coll"])
+    t = f["tracks"]
+    so, lo, to = canonical_tracks(t["track_start"], t["cluster_idx"], t["start_hit"], t["that"])
+    assert np.array_equal(sg, so) and len(lg) == len(lo) and len(lg) >= 100
+    assert all(np.array_equal(a, b) for a, b in zip(lg, lo))
+    assert np.array_equal(tg, to)
+    r = tr.refit(save_for_backward=True)
+    got = {k: v.cpu().numpy() for k, v in r.items()}
+    ref = o.refit(g["track_start"], g["cluster_idx"], g["t_coll"], prec=64)
+    ok = (got["status"] == 0) & (ref["status"] == 0)
+    assert ok.mean() > 0.95
+    ts = g["track_start"].astype(np.int64)
+    same = np.array([np.array_equal(got["rej"][ts[k]:ts[k + 1]], ref["rej"][ts[k]:ts[k + 1]])
+                     for k in range(ts.size - 1)])
+    sel = ok & same
+    assert sel.sum() > 0.98 * ok.sum()
+    e = rel_err(got["params"][sel].astype(np.float64), ref["params"][sel])
+    assert np.all(e <= RTOL), e.max(0)
+    assert np.all(got["params"][ok, 4] == 0.0) and np.all(ref["params"][ok, 4] == 0.0)
+    nt = tr.n_tracks
+    w = torch.linspace(0.5, 1.5, nt, device=tr.dev)
+    gy, gz, gc = [v.cpu().numpy() for v in tr.refit_backward(w)]
+    ry, rz, rc = o.refit_grad(g["track_start"], g["cluster_idx"], g["t_coll"], ref["seeds"],
+                              got["rej"], w.cpu().numpy().astype(np.float64))
+    m = np.repeat(ok, np.diff(ts))
+    for a, b in ((gy, ry), (gz, rz)):
+        assert np.linalg.norm(a[m] - b[m]) / np.linalg.norm(b[m]) < 1e-3
+    if mode == "time":
+        # the v_drift and t0 gradients are sums over clusters whose terms
+        # cancel for straight tracks (the drift distance is linear along
+        # them, so it lies in the span of the fitted line): each is compared
+        # with the sum of its terms' magnitudes (gz is per drift time)
+        cal = synth.nominal_calib()
+        ci = g["cluster_idx"].astype(np.int64)
+        drift = np.abs(ev.t[ci] - cal.t0 - np.repeat(g["t_coll"], np.diff(ts)))
+        scales = (np.sum(np.abs(rz[m]) * drift[m]) / cal.vdrift, np.sum(np.abs(rz[m])))
+        for k, scale in enumerate(scales):
+            assert abs(gc[k] - rc[k]) <= 1e-3 * scale, (k, gc[k], rc[k], scale)

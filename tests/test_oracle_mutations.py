@@ -72,6 +72,7 @@ MUTANTS = {
  'field_pt_not_updated': ("out[4] = (q * cl) / rho;", "out[4] = q;"),
  'field_difference_sign': ("for (int k = 0; k < 5; ++k) st.p[k] = hx.p[k] + (full[k] - unif[k]);", "for (int k = 0; k < 5; ++k) st.p[k] = hx.p[k] - (full[k] - unif[k]);"),
  'field_not_rotated': ("b0 = B[0] * ca + B[1] * sa;\n      b1 = -(B[0] * sa) + B[1] * ca;", "b0 = B[0];\n      b1 = B[1];"),
+ 'zero_field_seed_unguarded': ("R q = kB_of<R>(c) != R(0) ? kap / kB_of<R>(c) : R(0);", "R q = kap / kB_of<R>(c);"),
  'merge_solve_operand': ("for (int k = 0; k < a; ++k) acc = acc - L[a][k] * w[k];", "for (int k = 0; k < a; ++k) acc = acc - L[a][k] * d[k];"),
 }
 

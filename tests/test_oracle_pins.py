@@ -169,6 +169,26 @@ def test_refit_of_exact_points_is_exact(geo, params):
     assert n >= 10
 
 
+def test_zero_field_refit_of_a_straight_line_is_exact(geo, params):
+    """The degenerate case Bz = 0 (straight tracks, q/pT not observable, held
+    at 0): float64 points on straight lines refit to the line within 1e-9."""
+    import dataclasses
+    geo0 = dataclasses.replace(geo, bz=np.float32(0.0))
+    o = _oracle(synth.make_tiny(seed=14, n_tracks=4, sectors=(0,), sigma=0.0), geo0, params)
+    rng = np.random.default_rng(21)
+    x = geo.row_x.astype(np.float64)
+    for _ in range(10):
+        s, t = rng.uniform(-0.3, 0.3), rng.uniform(-1.0, 1.0)
+        y0, z0 = rng.uniform(-5.0, 5.0), rng.uniform(-100.0, 100.0)
+        c = np.sqrt(1.0 - s * s)
+        y = y0 + (x - x[0]) * (s / c)
+        z = z0 + (x - x[0]) * (t / c)
+        stt, p, chi2, ndf = o.refit_points(x, y, z, 0.01)
+        assert stt == 0
+        assert np.all(np.abs(p - np.array([y0, z0, s, t, 0.0])) < 1e-9), p
+        assert p[4] == 0.0 and chi2 < 1e-12 and ndf == 2 * x.size
+
+
 def _helix_at_planes(p, x0, xs, kB=KB):
     """Independent helix model: circle through (x0, y0) with direction phi,
     curvature kB*q, intersected with planes x = xs; z advances with arc length."""
