@@ -61,3 +61,36 @@ def test_create_rejects_bad_geometry_without_touching_the_device(lib):
     assert not h.value
     assert lib.tpc_last_error(None) == b"null context"
     lib.tpc_destroy(None)
+
+
+def test_every_struct_field_offset_matches_the_compiled_header(tmp_path):
+    """Compile a C program against include/tpc.h that prints sizeof and
+    offsetof of every field the ctypes binding declares, and compare."""
+    import os
+    import subprocess
+    structs = [binding.tpc_geometry, binding.tpc_params, binding.tpc_calib,
+               binding.tpc_clusters, binding.tpc_kernel_stat, binding.tpc_tuning,
+               binding.tpc_tracks]
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "tpc.h"',
+             "int main(void) {"]
+    for st in structs:
+        n = st.__name__
+        lines.append(f'  printf("{n} size %zu\\n", sizeof({n}));')
+        for f, _ in st._fields_:
+            lines.append(f'  printf("{n} {f} %zu\\n", offsetof({n}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "abi.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "abi"
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    subprocess.check_call(["gcc", "-std=c11", "-I", inc, str(src), "-o", str(exe)])
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout
+    got = {}
+    for line in out.splitlines():
+        parts = line.split()
+        got[tuple(parts[:-1])] = int(parts[-1])
+    for st in structs:
+        n = st.__name__
+        assert got[(n, "size")] == C.sizeof(st), n
+        for f, _ in st._fields_:
+            assert got[(n, f)] == getattr(st, f).offset, (n, f)
