@@ -375,7 +375,7 @@ void tpc_destroy(tpc_ctx* ctx) {
   if (!ctx) return;
   cudaStreamSynchronize(ctx->stream);
   void* ptrs[] = {ctx->d_rowx, ctx->d_pads, ctx->d_spline, ctx->d_spl_bound, ctx->d_err, ctx->d_cnt,
-                  ctx->fb.cnt, ctx->fb.row_start, ctx->fb.fill, ctx->fb.zmm, ctx->fb.zr,
+                  ctx->fb.cnt, ctx->fb.row_start, ctx->fb.fill, ctx->fb.row_blk, ctx->fb.zmm, ctx->fb.zr,
                   ctx->fb.zs_in, ctx->fb.perm, ctx->fb.pyz, ctx->fb.gyz,
                   ctx->fb.gorig, ctx->fb.gseg, ctx->fb.bin_start, ctx->fb.big_list, ctx->fb.mid_list, ctx->fb.list_counts,
                   ctx->fb.n_bins, ctx->fb.es_dims, ctx->fb.queue, ctx->fb.up, ctx->fb.dn,
@@ -496,6 +496,7 @@ tpc_status prepare_load(tpc_ctx* ctx, int n_events) {
     CK(alloc(b.cnt, K));
     CK(alloc(b.row_start, (int64_t)K + 1));
     CK(alloc(b.fill, K));
+    CK(alloc(b.row_blk, (int64_t)K / 1024 + 1));
     ctx->cap_K = K;
   }
   if (n_events > ctx->cap_ev) {

@@ -132,23 +132,59 @@ __global__ void __launch_bounds__(256) k_hist(Geo g, Cal c, ClIn cl, uint32_t* c
 // Single block: bucket offsets, the z range of each (event, side) and the bin
 // geometry of each (event, sector): ny x nz bins of about tau clusters each,
 // square in (y, z) on average, shared by the rows of the sector.
+// Many buckets (a batch of events): the bucket offsets in three steps, so
+// that no single block walks all of them: k_rows_local scans each block's
+// counts (row_start holds block-local offsets, blk the block totals),
+// k_scan_rows scans blk into block offsets (and reads row_start through
+// them), k_rows_add adds them.
+constexpr int kRowScanBlock = 1024;
+constexpr int kRowScanSplit = 8 * kRowScanBlock;  // buckets above which the scan is split
+__global__ void __launch_bounds__(kRowScanBlock) k_rows_local(int K, const uint32_t* cnt,
+                                                              uint32_t* row_start, uint32_t* blk) {
+  int i = blockIdx.x * kRowScanBlock + threadIdx.x;
+  uint32_t v = i < K ? cnt[i] : 0u;
+  uint32_t tot;
+  uint32_t ex = block_excl_scan(v, &tot);
+  if (i < K) row_start[i] = ex;
+  if (threadIdx.x == 0) blk[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(kRowScanBlock) k_rows_add(int K, const uint32_t* blk,
+                                                            uint32_t* row_start) {
+  int i = blockIdx.x * kRowScanBlock + threadIdx.x;
+  if (i < K) row_start[i] += blk[blockIdx.x];
+}
+
+// nblk_rows == 0: the bucket offsets are scanned here from cnt; otherwise
+// row_start holds block-local offsets and blk the nblk_rows block totals,
+// which are scanned here in place (k_rows_add then completes row_start).
 __global__ void k_scan_rows(Geo g, int K, int n_events, GridDims gd, const uint32_t* cnt,
-                            uint32_t* row_start, const int32_t* zmm, float* zr, uint2* es_dims,
-                            uint32_t* n_bins) {
+                            uint32_t* row_start, int nblk_rows, uint32_t* blk,
+                            const int32_t* zmm, float* zr, uint2* es_dims, uint32_t* n_bins) {
   __shared__ uint32_t carry;
   if (threadIdx.x == 0) carry = 0u;
   __syncthreads();
-  for (int base = 0; base < K; base += blockDim.x) {
+  const int nscan = nblk_rows > 0 ? nblk_rows : K;
+  uint32_t* dst = nblk_rows > 0 ? blk : row_start;
+  for (int base = 0; base < nscan; base += blockDim.x) {
     int i = base + threadIdx.x;
-    uint32_t v = i < K ? cnt[i] : 0u;
+    uint32_t v = i < nscan ? (nblk_rows > 0 ? blk[i] : cnt[i]) : 0u;
     uint32_t tot;
     uint32_t ex = block_excl_scan(v, &tot);
-    if (i < K) row_start[i] = carry + ex;
+    __syncthreads();
+    if (i < nscan) dst[i] = carry + ex;
     __syncthreads();
     if (threadIdx.x == 0) carry += tot;
     __syncthreads();
   }
-  if (threadIdx.x == 0) row_start[K] = carry;
+  const uint32_t total = carry;
+  if (threadIdx.x == 0) row_start[K] = total;
+  __syncthreads();
+  // final offset of bucket i (i <= K)
+  auto rs = [&](int i) -> uint32_t {
+    if (nblk_rows == 0 || i >= K) return row_start[i];
+    return row_start[i] + blk[i / kRowScanBlock];
+  };
   for (int i = threadIdx.x; i < n_events * 2; i += blockDim.x) {
     float lo = ord2f(zmm[2 * i]), hi = ord2f(zmm[2 * i + 1]);
     if (!(hi >= lo)) {
@@ -173,7 +209,7 @@ __global__ void k_scan_rows(Geo g, int K, int n_events, GridDims gd, const uint3
     uint32_t sz = 0u;
     uint32_t dims = 1u | (1u << 16);
     if (es < nes) {
-      uint32_t tot = row_start[(es + 1) * R] - row_start[es * R];
+      uint32_t tot = rs((es + 1) * R) - rs(es * R);
       int nbt = (int)((float)tot / ((float)R * gd.tau));
       if (nbt < 1) nbt = 1;
       if (nbt > gd.nb_max) nbt = gd.nb_max;
@@ -1410,9 +1446,17 @@ void launch_load(Prof* P, const Geo& g, const Cal& c, const ClIn& cl, const Grid
     TPC_LAUNCH(P, "k_hist", s,
                k_hist<<<min(nblk(cl.n, kB256), 8 * 148), kB256, 0, s>>>(g, c, cl, b.cnt, b.zs_in,
                                                                         b.zmm, err));
+  const int nblk_rows = K > kRowScanSplit ? nblk(K, kRowScanBlock) : 0;
+  if (nblk_rows > 0)
+    TPC_LAUNCH(P, "k_rows_local", s,
+               k_rows_local<<<nblk_rows, kRowScanBlock, 0, s>>>(K, b.cnt, b.row_start,
+                                                                b.row_blk));
   TPC_LAUNCH(P, "k_scan_rows", s,
-             k_scan_rows<<<1, 1024, 0, s>>>(g, K, cl.n_events, gd, b.cnt, b.row_start, b.zmm, b.zr,
-                                            b.es_dims, b.n_bins));
+             k_scan_rows<<<1, 1024, 0, s>>>(g, K, cl.n_events, gd, b.cnt, b.row_start, nblk_rows,
+                                            b.row_blk, b.zmm, b.zr, b.es_dims, b.n_bins));
+  if (nblk_rows > 0)
+    TPC_LAUNCH(P, "k_rows_add", s,
+               k_rows_add<<<nblk_rows, kRowScanBlock, 0, s>>>(K, b.row_blk, b.row_start));
   if (cl.n > 0)
     TPC_LAUNCH(P, "k_scatter", s,
                k_scatter<<<nblk(cl.n, kB256), kB256, 0, s>>>(g, cl, b.row_start, b.zs_in, b.fill,

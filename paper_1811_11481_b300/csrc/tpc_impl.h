@@ -85,6 +85,7 @@ struct FindBuf {
   uint32_t* cnt;        // [K] cluster count per (event, sector, row)
   uint32_t* row_start;  // [K + 1]
   uint32_t* fill;       // [K]
+  uint32_t* row_blk;    // [K / 1024 + 1] block totals, then offsets, of the split bucket scan
   int32_t* zmm;         // [n_events * 2 * 2] ordered-int min/max of seed z per side
   float* zr;            // [n_events * 2 * 2] z0, 1/dz per (event, side)
   float* zs_in;         // [n] seed z in input order
