@@ -46,6 +46,7 @@ struct tpc_ctx {
   bool capturing = false;
   int64_t calib_version = 0;        // incremented by tpc_set_calib
   int64_t refit_calib_version = -1;  // calibration of the saved refit
+  int64_t coords_calib_version = -1;  // calibration of the track set's yc, zc
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
   int64_t graph_kernels = 0;     // kernel launches recorded in the graph
@@ -532,6 +533,7 @@ tpc_status tpc_find_tracks_async(tpc_ctx* ctx) {
   launch_find(&ctx->prof, ctx->geo, ctx->cal, ctx->prm, ctx->cl, ctx->gd, ctx->sh, ctx->K, ctx->fb, ctx->tb,
               ctx->d_cnt, ctx->d_err, ctx->stream);
   CK(cudaGetLastError());
+  ctx->coords_calib_version = ctx->calib_version;
   ctx->tracks_valid = true;
   ctx->saved = false;
   return TPC_OK;
@@ -601,6 +603,7 @@ tpc_status tpc_set_tracks(tpc_ctx* ctx, const tpc_tracks* t) {
   launch_set_tracks(&ctx->prof, ctx->geo, ctx->cal, ctx->cl, t->n_tracks, t->n_assigned, ctx->tb,
                     ctx->d_cnt, ctx->d_err, ctx->stream);
   CK(cudaGetLastError());
+  ctx->coords_calib_version = ctx->calib_version;
   // the pinned words are read by the copy above: keep them stable
   CK(cudaStreamSynchronize(ctx->stream));
   ctx->tracks_valid = true;
@@ -619,9 +622,14 @@ tpc_status tpc_refit(tpc_ctx* ctx, int save_for_backward, float* params, float* 
       ctx->cap_ckpt_alloc = need;
     }
   }
-  // the current calibration applies to the refit inputs (Sec. 4)
-  launch_calib(&ctx->prof, ctx->geo, ctx->cal, ctx->cl, ctx->tb.cap_asg, ctx->tb, ctx->d_cnt,
-               ctx->d_err, ctx->stream);
+  // the current calibration applies to the refit inputs (Sec. 4): the
+  // calibrated coordinates are recomputed when it changed since the track
+  // set's were
+  if (ctx->coords_calib_version != ctx->calib_version) {
+    launch_calib(&ctx->prof, ctx->geo, ctx->cal, ctx->cl, ctx->tb.cap_asg, ctx->tb, ctx->d_cnt,
+                 ctx->d_err, ctx->stream);
+    ctx->coords_calib_version = ctx->calib_version;
+  }
   launch_refit(&ctx->prof, ctx->geo, ctx->prm, ctx->tb.cap_tr, ctx->d_cnt, ctx->tb, ctx->rb,
                save_for_backward != 0, params, cov, x, chi2, ndf, status, rej, ctx->d_err,
                ctx->stream);
@@ -690,6 +698,7 @@ tpc_status tpc_merge_tracks_async(tpc_ctx* ctx, const float* params, const float
   launch_calib(&ctx->prof, ctx->geo, ctx->cal, ctx->cl, t.cap_asg, t, ctx->d_cnt, ctx->d_err,
                ctx->stream);
   CK(cudaGetLastError());
+  ctx->coords_calib_version = ctx->calib_version;
   ctx->saved = false;
   return TPC_OK;
 }
@@ -730,6 +739,7 @@ tpc_status tpc_merge_tracks(tpc_ctx* ctx, const float* params, const float* cov,
     launch_calib(&ctx->prof, ctx->geo, ctx->cal, ctx->cl, t.cap_asg, t, ctx->d_cnt, ctx->d_err,
                  ctx->stream);
     CK(cudaGetLastError());
+    ctx->coords_calib_version = ctx->calib_version;
   }
   st = read_back(ctx);
   if (st != TPC_OK) return st;
@@ -770,6 +780,7 @@ tpc_status tpc_refine_time(tpc_ctx* ctx, const float* params, const float* x,
   launch_calib(&ctx->prof, ctx->geo, ctx->cal, ctx->cl, t.cap_asg, t, ctx->d_cnt, ctx->d_err,
                ctx->stream);
   CK(cudaGetLastError());
+  ctx->coords_calib_version = ctx->calib_version;
   ctx->saved = false;
   return TPC_OK;
 }
