@@ -240,7 +240,10 @@ tpc_status tpc_set_tracks(tpc_ctx* ctx, const tpc_tracks* tracks);
 
 /* Refit the context's track set (Sec. 3) with the current calibration: the
  * calibration transform of the assigned clusters (Sec. 4) is re-applied
- * first, so tpc_set_calib between refits takes effect. Outputs are caller-owned device
+ * first when tpc_set_calib changed the calibration since the track set's
+ * calibrated coordinates were computed (by the find, tpc_set_tracks, a
+ * merge or a time refinement), so tpc_set_calib between refits takes
+ * effect. Outputs are caller-owned device
  * buffers with room for the number of tracks (params [n][5], cov [n][15],
  * x [n], chi2 [n], ndf [n]; rej [n_assigned] receives for each cluster the
  * refit pass that rejected it, 0 = kept; any output may be NULL). status[n]
