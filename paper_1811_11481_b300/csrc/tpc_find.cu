@@ -668,19 +668,36 @@ __global__ void k_scan_blocks(int nblk, const uint32_t* a, uint32_t* off_a, cons
     carry_b = 0u;
   }
   __syncthreads();
-  for (int base = 0; base < nblk; base += blockDim.x) {
-    int i = base + threadIdx.x;
-    uint32_t va = i < nblk ? a[i] : 0u;
-    uint32_t ta;
-    uint32_t ea = block_excl_scan(va, &ta);
-    uint32_t vb = 0u, tb = 0u, eb = 0u;
-    if (b) {
-      vb = i < nblk ? b[i] : 0u;
-      eb = block_excl_scan(vb, &tb);
+  // each thread takes kPer consecutive entries per pass: a serial sum of
+  // its entries, one block scan of the sums, then its entries' offsets
+  constexpr int kPer = 8;
+  const int span = blockDim.x * kPer;
+  for (int base = 0; base < nblk; base += span) {
+    const int i0 = base + threadIdx.x * kPer;
+    uint32_t va[kPer], vb[kPer];
+    uint32_t sa = 0u, sb = 0u;
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+      int i = i0 + q;
+      va[q] = i < nblk ? a[i] : 0u;
+      vb[q] = (b && i < nblk) ? b[i] : 0u;
+      sa += va[q];
+      sb += vb[q];
     }
-    if (i < nblk) {
-      off_a[i] = carry_a + ea;
-      if (b) off_b[i] = carry_b + eb;
+    uint32_t ta;
+    uint32_t ea = block_excl_scan(sa, &ta);
+    uint32_t tb = 0u, eb = 0u;
+    if (b) eb = block_excl_scan(sb, &tb);
+    uint32_t ra = carry_a + ea, rb = carry_b + eb;
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+      int i = i0 + q;
+      if (i < nblk) {
+        off_a[i] = ra;
+        if (b) off_b[i] = rb;
+      }
+      ra += va[q];
+      rb += vb[q];
     }
     __syncthreads();
     if (threadIdx.x == 0) {
