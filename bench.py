@@ -5,8 +5,9 @@ One step = load a batch (bucketing, seeding transform, search grid), find
 tracks (neighbours, link cleaning, start hits, tracklets, selection,
 calibration transform), refit them (3 passes, saved for the adjoint) and run
 the adjoint refit (gradient of the summed chi2 w.r.t. cluster coordinates and
-calibration). Default workload: one central Pb-Pb-like event (36 sectors,
-10,000 primaries, 10 % noise, seed 1), synthetic.
+calibration). Default workload: a 50 kHz continuous-readout time frame of 50
+min-bias Pb-Pb-like collisions (11.1M clusters, float64 drift times, seed 2),
+synthetic; `--workload central` runs one central event instead.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -39,7 +40,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="central",
+    ap.add_argument("--workload", default="timeframe",
                     choices=["central", "timeframe", "batched", "single_sector", "adjoint"])
     ap.add_argument("--collisions", type=int, default=50,
                     help="collisions of the time-frame workload (50: the headline frame)")
@@ -186,11 +187,11 @@ def aggregate(total_ms, units, dist=None, device="cpu"):
     return total_ms, units, units / (total_ms / 1000.0)
 
 
-def ncu_traffic(kernel):
-    """DRAM bytes per launch of 'kernel' from the committed ncu summary, or
+def _ncu_entry(fname, kernel):
+    """The entry of 'kernel' in a committed ncu summary (profiles/fname), or
     None when the kernel's sources changed since that capture."""
     import hashlib
-    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    p = os.path.join(ROOT, "profiles", fname)
     if not os.path.exists(p):
         return None
     e = json.load(open(p))["kernels"].get(kernel)
@@ -201,7 +202,34 @@ def ncu_traffic(kernel):
         fp = os.path.join(src, f)
         if not os.path.exists(fp) or hashlib.sha256(open(fp, "rb").read()).hexdigest()[:16] != h:
             return None
-    return e["bytes_per_launch"]
+    return e
+
+
+def ncu_traffic(kernel, units):
+    """DRAM bytes (read + write) of one launch of 'kernel' that processes
+    'units' (dict of unit counts), from the committed ncu capture scaled by
+    the units the capture processed; None when the sources changed."""
+    e = _ncu_entry("ncu_traffic.json", kernel)
+    if not e or e.get("unit") not in units:
+        return None
+    return e["bytes_per_unit"] * units[e["unit"]]
+
+
+def ncu_flops(kernel, units):
+    """Executed single-precision floating-point operations of one launch of
+    'kernel' (FFMA counted as 2, FADD and FMUL as 1, from ncu's SASS
+    instruction counters), scaled from the capture by the launch's units;
+    None when the sources changed since the capture."""
+    e = _ncu_entry("ncu_alu.json", kernel)
+    if not e or e.get("unit") not in units:
+        return None
+    return e["flops_per_unit"] * units[e["unit"]]
+
+
+def alu_peak_gflops(sms, sm_mhz):
+    """FP32 peak of the GPU at the sampled SM clock: SMs x 128 FP32 lanes x 2
+    operations per fused multiply-add x clock."""
+    return sms * 128 * 2 * sm_mhz * 1e6 / 1e9
 
 
 def load_peaks():
@@ -638,6 +666,33 @@ def run_ours(args):
                    P(out["ndf"]), P(out["status"]), P(out["rej"])), "refit")
     t_bwd = phase_time(lambda: ck(L.tpc_refit_backward(h, P(ones), P(gy), P(gz), P(gc)), "bwd"))
 
+    # ---- find + refit without the adjoint: load, find, refit (no
+    # checkpoints), the quantity the HBM target of the method is stated on
+    def fr_step():
+        tr.load(cl)
+        ck(L.tpc_find_tracks_async(h), "find")
+        ck(L.tpc_refit(h, 0, P(out["params"]), P(out["cov"]), P(out["x"]), P(out["chi2"]),
+                       P(out["ndf"]), P(out["status"]), P(out["rej"])), "refit")
+    for _ in range(3):
+        fr_step()
+    tr.profile(True)
+    barrier()
+    fr_times = []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fr_step()
+        e1.record(stream)
+        fr_times.append((e0, e1))
+    barrier()
+    fr_kstats, _ = tr.profile_read()
+    tr.profile(False)
+    fr_ms, _, fr_value = aggregate(float(np.sum([a.elapsed_time(b) for a, b in fr_times])),
+                                   n * args.steps, dist, dev)
+    fr_ms /= args.steps
+
     # ---- end to end through the C ABI with host buffers
     e2e = None
     if not args.no_e2e:
@@ -694,33 +749,72 @@ def run_ours(args):
                         "stream into one of two device buffers (overlapping the previous "
                         "step), track parameters and chi2 copied back every step")
 
-    # ---- roofline of the dominant kernel
+    # ---- rooflines of the top kernels: HBM (algorithmic bytes) and FP32 ALU
+    # (executed single-precision operations from the ncu capture, scaled by
+    # the launch's units); the dominant kernel's bound is the one it is
+    # closer to
     counts = dict(n=n, mode=1 if ev.mode == "time" else 0, n_tracks=nt, n_assigned=na,
                   n_tracklets=ntl, sum_nh=sum_nh, n_events=ev.n_events)
+    units = dict(cluster=n, tracklet_hit=sum_nh, assigned_cluster=na, track=nt)
     peaks = load_peaks()
+    sm_mhz = clk["sm_mhz"] or peaks["sm_max_mhz"]
+    alu_peak = alu_peak_gflops(torch.cuda.get_device_properties(dev).multi_processor_count,
+                               sm_mhz)
     tot = sum(v[1] for v in kstats_all.values()) or 1.0
+
+    def kernel_roofs(k, per_launch_ms):
+        ab = algorithmic_bytes(k, counts)
+        gbs = ab / (per_launch_ms / 1000.0) / 1e9 if ab else None
+        hbm = dict(bound="hbm", achieved=gbs, peak=peaks["hbm_gbs"], unit="GB/s",
+                   frac=(gbs / peaks["hbm_gbs"]) if gbs else None,
+                   traffic=ncu_traffic(k, units), algorithmic_bytes=ab,
+                   peak_source=peaks["source"] + " (burst copy)")
+        fl = ncu_flops(k, units)
+        gfl = fl / (per_launch_ms / 1000.0) / 1e9 if fl else None
+        alu = dict(bound="alu", achieved=gfl, peak=alu_peak, unit="GFLOP/s",
+                   frac=(gfl / alu_peak) if gfl else None, flops=fl,
+                   traffic=ncu_traffic(k, units),
+                   peak_source=f"148 SMs x 128 FP32 lanes x 2 x sampled SM clock "
+                               f"{sm_mhz:.0f} MHz",
+                   flops_source="executed FP32 operations per unit from the ncu capture "
+                                "(profiles/ncu_alu.json; FFMA = 2), null once the kernel "
+                                "changed")
+        return hbm, alu
+
     roof = None
+    alu_kernels = {}
+    for k in ("k_tracklets", "k_refit", "k_refit_bwd"):
+        if k in kstats_all:
+            nl, kms = kstats_all[k]
+            hb, al = kernel_roofs(k, kms / nl)
+            alu_kernels[k] = dict(ms_per_launch=kms / nl, alu=al, hbm=hb)
     if dom and dom in kstats:
         nl, kms = kstats[dom]
         per_launch_ms = kms / nl
-        ab = algorithmic_bytes(dom, counts)
-        ach = ab / (per_launch_ms / 1000.0) / 1e9 if ab else None
-        roof = dict(kernel=dom, bound="hbm", achieved=ach, peak=peaks["hbm_gbs"], unit="GB/s",
-                    frac=(ach / peaks["hbm_gbs"]) if ach else None, traffic=ncu_traffic(dom),
-                    algorithmic_bytes=ab, ms_per_launch=per_launch_ms,
-                    share=kstats_all[dom][1] / tot, peak_source=peaks["source"] + " (burst copy)",
-                    timing="CUDA events around each of its launches in the timed region")
+        hb, al = kernel_roofs(dom, per_launch_ms)
+        main, other = (al, hb) if (al["frac"] or 0.0) > (hb["frac"] or 0.0) else (hb, al)
+        roof = dict(main, kernel=dom, ms_per_launch=per_launch_ms,
+                    share=kstats_all[dom][1] / tot,
+                    timing="CUDA events around each of its launches in the timed region",
+                    bound_choice="the resource the kernel is closer to: larger fraction of "
+                                 "HBM (algorithmic bytes) and FP32 ALU (executed operations)",
+                    other=other)
     kernels = {k: dict(launches=v[0], ms_per_step=v[1] / n_prof, share=v[1] / tot)
                for k, v in sorted(kstats_all.items(), key=lambda kv: -kv[1][1])}
+
+    def step_bytes_of(ks, nsteps):
+        b = 0
+        for k, v in ks.items():
+            ab = None if k.startswith("k_row_sort") else algorithmic_bytes(k, counts)
+            if ab:
+                b += ab * v[0] / nsteps          # launches per step
+        if any(k.startswith("k_row_sort") for k in ks):
+            b += algorithmic_bytes("k_row_sort", counts)
+        return b
+
     # the whole step against the HBM roofline: the algorithmic bytes of every
     # modelled kernel of a step over the step's time
-    step_bytes = 0
-    for k, v in kstats_all.items():
-        ab = None if k.startswith("k_row_sort") else algorithmic_bytes(k, counts)
-        if ab:
-            step_bytes += ab * v[0] / n_prof          # launches per step
-    if any(k.startswith("k_row_sort") for k in kstats_all):
-        step_bytes += algorithmic_bytes("k_row_sort", counts)
+    step_bytes = step_bytes_of(kstats_all, n_prof)
     step_ms = total_ms / args.steps
     step_gbs = step_bytes / (step_ms / 1000.0) / 1e9
     step_hbm = dict(algorithmic_bytes=step_bytes, achieved=step_gbs, unit="GB/s",
@@ -728,6 +822,20 @@ def run_ours(args):
                     note="algorithmic bytes of all modelled kernels of one step (times "
                          "their launches per step; the row sorts together once) over the "
                          "step time, of measured HBM copy bandwidth")
+    # find + refit: the method's own 180 bytes per cluster (compulsory
+    # reads and writes of the hot path's steps) and this code's kernel model
+    fr_bytes = step_bytes_of(fr_kstats, args.steps)
+    fr_s = fr_ms / 1000.0
+    find_refit = dict(
+        value=fr_value, unit=UNIT, ms_per_step=fr_ms, steps=args.steps,
+        hbm_180=dict(bytes_per_cluster=180, achieved=180 * n / fr_s / 1e9, unit="GB/s",
+                     peak=peaks["hbm_gbs"], frac=180 * n / fr_s / 1e9 / peaks["hbm_gbs"],
+                     frac_of_nominal_8tbs=180 * n / fr_s / 1e9 / 8000.0),
+        hbm_kernels=dict(algorithmic_bytes=fr_bytes, achieved=fr_bytes / fr_s / 1e9,
+                         unit="GB/s", frac=fr_bytes / fr_s / 1e9 / peaks["hbm_gbs"]),
+        note="load, find and refit (no checkpoints, no adjoint) per step, L2 flushed "
+             "before each, CUDA events; hbm_180: 180 algorithmic bytes per cluster for "
+             "the hot path's steps; hbm_kernels: the per-kernel model of this code")
 
     compression = None if args.no_merge else compression_stage(tr, cl, flush, stream)
     merge = None if args.no_merge else merge_stage(tr, cl, ev, flush, stream)
@@ -736,7 +844,7 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(ev, geo, secs=list(range(36)))
+        cpu = cpu_baseline(ev, geo, secs=sample_sectors(ev))
 
     line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps,
                 warmup=args.warmup, ms_per_step=total_ms / args.steps, higher_is_better=True,
@@ -751,7 +859,8 @@ def run_ours(args):
                 refit_fwd_ms=t_fwd, refit_fwd_nosave_ms=t_fwd_nosave, adjoint_ms=t_bwd,
                 adjoint_vs_fwd=(t_bwd / t_fwd_nosave if t_bwd is not None and t_fwd_nosave > 0
                                 else None),
-                roofline=roof, step_hbm=step_hbm, kernels=kernels,
+                roofline=roof, step_hbm=step_hbm, find_refit=find_refit,
+                alu_roofline=alu_kernels, kernels=kernels,
                 kernels_timing=f"separate pass of {n_prof} steps with every launch timed",
                 gpu_launches=launches,
                 graph_replay=graph_replay, track_quality=quality, merge_stage=merge,
@@ -777,9 +886,23 @@ def _subset(ev, secs):
     return s, int(m.sum())
 
 
-def cpu_baseline(ev, geo, secs):
-    """The oracle as it stands, single thread, on the sectors 'secs' of the
-    same event: find (FP32 mirror), refit (FP64) and tape gradient."""
+def sample_sectors(ev, target=300_000):
+    """The first sectors of the workload holding at least `target` clusters
+    (a bounded sample: about 20 s of single-thread oracle work)."""
+    cnt = np.bincount(np.asarray(ev.sector, np.int64), minlength=36)
+    secs, tot = [], 0
+    for k in range(36):
+        secs.append(k)
+        tot += int(cnt[k])
+        if tot >= target:
+            break
+    return secs
+
+
+def oracle_pass(ev, geo, secs):
+    """One pass of the oracle as it stands over sectors 'secs' of the
+    workload: find (FP32 mirror), refit (FP64) and tape gradient. Returns
+    (clusters, seconds)."""
     import oracle
     import synth
     from paper_1811_11481_b300.config import default_params
@@ -792,33 +915,56 @@ def cpu_baseline(ev, geo, secs):
     o.refit_grad(tr["track_start"], tr["cluster_idx"], tr["that"], r["seeds"], r["rej"])
     dt = time.time() - t0
     o.close()
-    return dict(value=n / dt, unit=UNIT, cores=1, kind="oracle",
-                sample=f"sectors {secs[0]}..{secs[-1]} of the same event ({n} clusters): "
-                       f"find (FP32 mirror) + refit (FP64) + tape-AD gradient, {dt:.1f} s")
+    return n, dt
+
+
+def cpu_baseline(ev, geo, secs):
+    """The oracle as it stands on the sectors 'secs' of the same workload,
+    on all host cores (its loops over hits, start hits, tracks and clusters
+    in parallel) and on one."""
+    import oracle
+    ncores = os.cpu_count() or 1
+    oracle.threads(ncores)
+    used = oracle.threads()
+    n, dt = oracle_pass(ev, geo, secs)
+    oracle.threads(1)
+    n1, dt1 = oracle_pass(ev, geo, secs)
+    oracle.threads(ncores)
+    what = (f"sectors {secs[0]}..{secs[-1]} of the same workload ({n} clusters): find (FP32 "
+            f"mirror) + refit (FP64) + tape-AD gradient")
+    return dict(value=n / dt, unit=UNIT, cores=used, kind="oracle", host_cores=ncores,
+                sample=f"{what}, {dt:.1f} s on {used} threads",
+                single_thread=dict(value=n1 / dt1, unit=UNIT, cores=1, seconds=dt1),
+                speedup_all_cores=dt1 / dt)
 
 
 # ------------------------------------------------------- reference arm
 def run_reference(args):
+    """The reference arm: the oracle as it stands on the host cores (all of
+    them), each step one sector of the same workload, rotating over the
+    sectors."""
     rank = int(os.environ.get("RANK", 0))
     if rank != 0:
         return
+    import oracle
     import synth
     geo = synth.geometry()
-    ev, cfg = make_workload(args.workload, 0)
-    per_step = 2  # sectors per step
+    wl = "timeframe" if args.workload == "adjoint" else args.workload
+    ev, cfg = make_workload(wl, 0, args.collisions)
+    ncores = os.cpu_count() or 1
+    oracle.threads(ncores)
+    used = oracle.threads()
     for w in range(args.warmup):
-        cpu_baseline(ev, geo, secs=[(2 * w) % 36, (2 * w + 1) % 36])
+        oracle_pass(ev, geo, [w % 36])
     tot_n, tot_t = 0, 0.0
     for k in range(args.steps):
-        secs = [(per_step * k + j) % 36 for j in range(per_step)]
-        sub, n = _subset(ev, secs)
-        t0 = time.time()
-        cpu_baseline(ev, geo, secs)
-        tot_t += time.time() - t0
+        n, dt = oracle_pass(ev, geo, [k % 36])
+        tot_t += dt
         tot_n += n
     v = tot_n / tot_t
-    cb = dict(value=v, unit=UNIT, cores=1, kind="oracle",
-              sample=f"{per_step} sectors of the event per step, single thread")
+    cb = dict(value=v, unit=UNIT, cores=used, kind="oracle", host_cores=ncores,
+              sample=f"one sector of the workload per step (sector k mod 36 at step k), "
+                     f"find (FP32 mirror) + refit (FP64) + tape-AD gradient, {used} threads")
     line = dict(impl="reference", metric=METRIC, value=v, unit=UNIT,
                 n_gpus=int(os.environ.get("WORLD_SIZE", args.gpus)), steps=args.steps,
                 warmup=args.warmup, ms_per_step=1000.0 * tot_t / args.steps,

@@ -222,6 +222,22 @@ tpc_status tpc_load_clusters(tpc_ctx* ctx, const tpc_clusters* cl);
  * retries with twice the capacity). */
 tpc_status tpc_find_tracks(tpc_ctx* ctx, tpc_tracks* out);
 
+/* Batching (many events of uneven size in one launch sequence): load the
+ * n_parts cluster sets ev[0 .. n_parts-1] (each as for tpc_load_clusters:
+ * device SoA, caller-owned, mode and pads equal across parts, in mode 1
+ * the same tf_start) as one batch and run tpc_find_tracks on it. The parts
+ * are copied (device to device, on the context's stream) into
+ * library-owned buffers, concatenated in order: cluster j of part i gets
+ * the input index (n_0 + ... + n_{i-1}) + j, and its event index is the
+ * part's own (0 when the part has no event array) plus the events of the
+ * parts before it. So the returned tracks, tpc_refit and
+ * tpc_refit_backward then refer to the concatenated numbering; the parts'
+ * arrays may be released once the call returns. At most 4096 events and
+ * 2^31 - 1 clusters in all. Synchronises once (as tpc_find_tracks); may
+ * allocate. Returns TPC_ERR_ARG for inconsistent parts. */
+tpc_status tpc_find_tracks_batched(tpc_ctx* ctx, const tpc_clusters* ev, int32_t n_parts,
+                                   tpc_tracks* out);
+
 /* Same as tpc_find_tracks without the synchronisation: counts stay on the
  * device (readable with tpc_get_counts) and *out is not filled. Makes the
  * whole load-find-refit sequence capturable in a CUDA graph once buffers
@@ -379,8 +395,14 @@ tpc_status tpc_get_grid(tpc_ctx* ctx, uint32_t* order, uint32_t* row_start);
  * not a stream operation), real-time loops that must not take the device-wide
  * synchronisation an allocation can cause, or plug-ins whose host framework's
  * caching allocator owns the device memory.
- * Same three-pass refit as tpc_refit, for tracks given as CSR over assigned
- * clusters with their calibrated coordinates already computed (device):
+ * The three-pass refit of tpc_refit in the uniform field geo->bz, for tracks
+ * given as CSR over assigned clusters with their calibrated coordinates
+ * already computed (device). The inputs carry no sector, so every track is
+ * fitted in one sector frame: each track's clusters must lie in one sector
+ * frame (sectors k and k + 18 share one); refit tracks merged across
+ * sectors with tpc_refit. A geometry with a full field (geo->field not
+ * NULL) returns TPC_ERR_ARG: the full-field transport is tpc_refit's.
+ * Arguments:
  *   track_start [n_tracks + 1], yc, zc [n_assigned] (cm), row, flags
  *   [n_assigned] (flags may be NULL); outputs (device, any may be NULL):
  *   params [n_tracks][5], cov [n_tracks][15], chi2, ndf, status [n_tracks]
@@ -389,7 +411,10 @@ tpc_status tpc_get_grid(tpc_ctx* ctx, uint32_t* order, uint32_t* row_start);
  * every GPU loading the library holds until the process exits; n_assigned
  * above TPC_NOALLOC_MAX_ASSIGNED returns TPC_ERR_CAPACITY. The first call on
  * a device looks up the array's device address (cudaGetSymbolAddress); make
- * that first call before any stream capture on that device. All calls share
+ * that first call before any stream capture on that device. The address is
+ * kept per device ordinal for the life of the process, so the entry point
+ * supports neither a cudaDeviceReset between calls nor contexts other than
+ * the device's primary context. All calls share
  * the array, so calls that can overlap on the GPU (other streams, other
  * threads) race; the array is rewritten by every call before it is read.
  * geo, params: host, as for tpc_create (params NULL = defaults); stream: a

@@ -128,6 +128,8 @@ def lib():
         L.orc_rotate.argtypes = [vp, vp, C.c_double, C.c_double, vp, vp, vp, vp]
         L.orc_dca_z.restype = C.c_double
         L.orc_dca_z.argtypes = [vp, vp, C.c_double]
+        L.orc_threads.restype = C.c_int
+        L.orc_threads.argtypes = [C.c_int]
         L.orc_arc_factor.restype = C.c_double
         L.orc_arc_factor.argtypes = [C.c_int, C.c_double]
         L.orc_arc_deriv.restype = C.c_double
@@ -138,6 +140,12 @@ def lib():
 
 def _p(a):
     return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def threads(n=0):
+    """Set the oracle's thread count (n >= 1; loops over hits, start hits,
+    tracks and clusters run in parallel) and return the count in force."""
+    return lib().orc_threads(int(n))
 
 
 def arc_factor(h, prec=64):

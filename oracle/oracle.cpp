@@ -27,6 +27,7 @@
 #include <cstdint>
 #include <cstring>
 #include <map>
+#include <omp.h>
 #include <type_traits>
 #include <vector>
 
@@ -54,7 +55,8 @@ struct Tape {
     }
   }
 };
-Tape g_tape;
+// one tape per thread: tracks are differentiated independently
+thread_local Tape g_tape;
 
 struct Var {
   double v;
@@ -1415,6 +1417,7 @@ void orc_seed_z(void* ctx, int prec, void* out) {
 void orc_calibrate(void* ctx, int prec, int64_t m, const uint32_t* idx, const double* that,
                    double* yc, double* zc) {
   Ctx& c = *(Ctx*)ctx;
+#pragma omp parallel for schedule(static)
   for (int64_t k = 0; k < m; ++k) {
     if (prec == 32) {
       float a, b;
@@ -1446,6 +1449,7 @@ void orc_neighbours(void* ctx, int prec, const int64_t* hits, int64_t nh, int32_
                     int32_t* dn) {
   Ctx& c = *(Ctx*)ctx;
   int64_t m = hits ? nh : c.cl.n;
+#pragma omp parallel for schedule(dynamic, 256)
   for (int64_t k = 0; k < m; ++k) {
     int64_t h = hits ? hits[k] : k;
     if (prec == 32) neighbours_of<float>(c, h, up[k], dn[k]);
@@ -1475,6 +1479,7 @@ int64_t orc_start_hits(void* ctx, const int32_t* upc, const int32_t* dnc, int64_
 void orc_tracklets(void* ctx, int prec, const int32_t* upc, int64_t m, const int64_t* starts,
                    int32_t* nh, int32_t* hits, double* that, double* state, double* xout) {
   Ctx& c = *(Ctx*)ctx;
+#pragma omp parallel for schedule(dynamic, 16)
   for (int64_t k = 0; k < m; ++k) {
     TrackletOut o = prec == 32 ? tracklet<float>(c, upc, starts[k], hits + k * c.g.n_rows)
                                : tracklet<double>(c, upc, starts[k], hits + k * c.g.n_rows);
@@ -1542,6 +1547,7 @@ void orc_refit(void* ctx, int prec, int64_t nt, const uint32_t* track_start,
                double* seeds_out, int frozen, uint8_t* rej, double* params, double* cov,
                double* xout, double* chi2, int32_t* ndf, int32_t* status) {
   Ctx& c = *(Ctx*)ctx;
+#pragma omp parallel for schedule(dynamic, 16)
   for (int64_t k = 0; k < nt; ++k) {
     size_t a = track_start[k], b = track_start[k + 1], n = b - a;
     uint8_t* rj = rej + a;
@@ -1585,53 +1591,94 @@ void orc_refit_grad(void* ctx, int64_t nt, const uint32_t* track_start,
                     const uint8_t* rej, const double* g, double* grad_y, double* grad_zt,
                     double* grad_calib) {
   Ctx& c = *(Ctx*)ctx;
-  for (int64_t k = 0; k < nt; ++k) {
-    size_t a = track_start[k], b = track_start[k + 1], n = b - a;
-    g_tape.clear();
-    CoefLeaves lv;
-    Var vd = Var::leaf(c.c.vdrift);
-    Var t0 = Var::leaf(c.c.t0);
-    std::vector<Var> ly(n), lz(n), x(n), yc(n), zc(n), var(n);
-    for (size_t q = 0; q < n; ++q) {
-      int64_t i = cluster_idx[a + q];
-      CalIn<Var> in;
-      in.vdrift = vd;
-      in.t0 = t0;
-      ly[q] = Var::leaf(c.cl.y[i]);
-      if (c.cl.mode == 1) {
-        lz[q] = Var::leaf(c.cl.t[i]);
-        in.t = lz[q];
-        in.z = Var(0.0);
-      } else {
-        lz[q] = Var::leaf(c.cl.z[i]);
-        in.z = lz[q];
-        in.t = Var(0.0);
+  // Each track's terms (its own tape, on any thread), then summed in track
+  // order, so the sums do not depend on the number of threads.
+  struct Terms {
+    bool ok = false;
+    std::vector<double> gy, gz;
+    double vd = 0.0, t0 = 0.0;
+    std::vector<std::pair<int, double>> spline;
+  };
+  const int64_t chunk = 4096;
+  std::vector<Terms> terms;
+  for (int64_t k0 = 0; k0 < nt; k0 += chunk) {
+    const int64_t k1 = std::min(nt, k0 + chunk);
+    terms.assign((size_t)(k1 - k0), Terms());
+#pragma omp parallel for schedule(dynamic, 8)
+    for (int64_t k = k0; k < k1; ++k) {
+      Terms& T = terms[(size_t)(k - k0)];
+      size_t a = track_start[k], b = track_start[k + 1], n = b - a;
+      g_tape.clear();
+      CoefLeaves lv;
+      Var vd = Var::leaf(c.c.vdrift);
+      Var t0 = Var::leaf(c.c.t0);
+      std::vector<Var> ly(n), lz(n), x(n), yc(n), zc(n), var(n);
+      for (size_t q = 0; q < n; ++q) {
+        int64_t i = cluster_idx[a + q];
+        CalIn<Var> in;
+        in.vdrift = vd;
+        in.t0 = t0;
+        ly[q] = Var::leaf(c.cl.y[i]);
+        if (c.cl.mode == 1) {
+          lz[q] = Var::leaf(c.cl.t[i]);
+          in.t = lz[q];
+          in.z = Var(0.0);
+        } else {
+          lz[q] = Var::leaf(c.cl.z[i]);
+          in.z = lz[q];
+          in.t = Var(0.0);
+        }
+        in.y = ly[q];
+        x[q] = Var(c.rowx[c.cl.row[i]]);
+        calibrate<Var>(c, i, that[k], in, yc[q], zc[q], &lv);
+        double e = cluster_error<double>(c, c.cl.flags[i]);
+        var[q] = Var(e * e);
       }
-      in.y = ly[q];
-      x[q] = Var(c.rowx[c.cl.row[i]]);
-      calibrate<Var>(c, i, that[k], in, yc[q], zc[q], &lv);
-      double e = cluster_error<double>(c, c.cl.flags[i]);
-      var[q] = Var(e * e);
+      std::vector<uint8_t> rj(rej + a, rej + b);
+      std::vector<double> al = track_alpha(c, cluster_idx + a, n);
+      Var chi2;
+      RefitOut o = refit_core<Var>(c, x, yc, zc, var, seeds + k * 5, rj.data(), true, &chi2,
+                                   al.empty() ? nullptr : &al);
+      if (o.status != 0) {
+        g_tape.clear();
+        continue;
+      }
+      g_tape.backward(chi2.id, g[k]);
+      auto adj = [&](const Var& v) { return v.id >= 0 ? g_tape.adj[v.id] : 0.0; };
+      T.ok = true;
+      T.gy.resize(n);
+      T.gz.resize(n);
+      for (size_t q = 0; q < n; ++q) {
+        // per pad for native input: dy/dpad is the row's pad pitch
+        double dyp = c.cl.pads ? (double)c.padw[c.cl.row[cluster_idx[a + q]]] : 1.0;
+        T.gy[q] = adj(ly[q]) * dyp;
+        T.gz[q] = adj(lz[q]);
+      }
+      T.vd = adj(vd);
+      T.t0 = adj(t0);
+      for (auto& kv : lv.m) T.spline.emplace_back(kv.first, adj(kv.second));
+      g_tape.clear();
     }
-    std::vector<uint8_t> rj(rej + a, rej + b);
-    std::vector<double> al = track_alpha(c, cluster_idx + a, n);
-    Var chi2;
-    RefitOut o = refit_core<Var>(c, x, yc, zc, var, seeds + k * 5, rj.data(), true, &chi2,
-                                 al.empty() ? nullptr : &al);
-    if (o.status != 0) continue;
-    g_tape.backward(chi2.id, g[k]);
-    auto adj = [&](const Var& v) { return v.id >= 0 ? g_tape.adj[v.id] : 0.0; };
-    for (size_t q = 0; q < n; ++q) {
-      // per pad for native input: dy/dpad is the row's pad pitch
-      double dyp = c.cl.pads ? (double)c.padw[c.cl.row[cluster_idx[a + q]]] : 1.0;
-      grad_y[a + q] += adj(ly[q]) * dyp;
-      grad_zt[a + q] += adj(lz[q]);
+    for (int64_t k = k0; k < k1; ++k) {
+      const Terms& T = terms[(size_t)(k - k0)];
+      if (!T.ok) continue;
+      size_t a = track_start[k];
+      for (size_t q = 0; q < T.gy.size(); ++q) {
+        grad_y[a + q] += T.gy[q];
+        grad_zt[a + q] += T.gz[q];
+      }
+      grad_calib[0] += T.vd;
+      grad_calib[1] += T.t0;
+      for (auto& kv : T.spline) grad_calib[2 + kv.first] += kv.second;
     }
-    grad_calib[0] += adj(vd);
-    grad_calib[1] += adj(t0);
-    for (auto& kv : lv.m) grad_calib[2 + kv.first] += adj(kv.second);
   }
-  g_tape.clear();
+}
+
+// Threads used by the parallel loops (over hits, start hits, tracks and
+// clusters); n < 1 leaves the setting unchanged. Returns the count in force.
+int orc_threads(int n) {
+  if (n >= 1) omp_set_num_threads(n);
+  return omp_get_max_threads();
 }
 
 // Segment merging (Sec. 2, second phase), decisions in precision prec.

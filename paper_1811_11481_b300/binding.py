@@ -94,6 +94,8 @@ _PROTOS = {
     "tpc_load_clusters": (C.c_int, [C.c_void_p, C.POINTER(tpc_clusters)]),
     "tpc_find_tracks": (C.c_int, [C.c_void_p, C.POINTER(tpc_tracks)]),
     "tpc_find_tracks_async": (C.c_int, [C.c_void_p]),
+    "tpc_find_tracks_batched": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32,
+                                          C.POINTER(tpc_tracks)]),
     "tpc_set_tracks": (C.c_int, [C.c_void_p, C.POINTER(tpc_tracks)]),
     "tpc_get_tracks": (C.c_int, [C.c_void_p, C.POINTER(tpc_tracks)]),
     "tpc_refit": (C.c_int, [C.c_void_p, C.c_int] + [C.c_void_p] * 7),
@@ -274,6 +276,31 @@ class Tracker:
         torch = self.torch
         t = tpc_tracks()
         self._ck(self.L.tpc_find_tracks(self.h, C.byref(t)), "tpc_find_tracks")
+        self.n_tracks, self.n_assigned = int(t.n_tracks), int(t.n_assigned)
+        view = self._tracks_view(t)
+        self.cluster_idx = view["cluster_idx"]
+        return view
+
+    def find_batched(self, parts):
+        """Load several cluster sets (dicts as returned by upload) as one
+        batch, concatenated in order, and run the finder; returns the track
+        CSR in the concatenated cluster numbering (copies)."""
+        arr = (tpc_clusters * len(parts))()
+        for i, cl in enumerate(parts):
+            arr[i] = tpc_clusters(
+                int(cl["y"].numel()), int(cl["mode"]), int(cl.get("n_events", 1)),
+                float(cl.get("tf_start", 0.0)), cl["y"].data_ptr(),
+                cl["z"].data_ptr() if cl.get("z") is not None else None,
+                cl["t"].data_ptr() if cl.get("t") is not None else None,
+                cl["row"].data_ptr(), cl["sector"].data_ptr(),
+                cl["flags"].data_ptr() if cl.get("flags") is not None else None,
+                cl["event"].data_ptr() if cl.get("event") is not None else None,
+                int(cl.get("pads", 0)))
+        t = tpc_tracks()
+        self._ck(self.L.tpc_find_tracks_batched(self.h, C.cast(arr, C.c_void_p), len(parts),
+                                                C.byref(t)), "tpc_find_tracks_batched")
+        self._keep["clusters"] = None
+        self.n = sum(int(cl["y"].numel()) for cl in parts)
         self.n_tracks, self.n_assigned = int(t.n_tracks), int(t.n_assigned)
         view = self._tracks_view(t)
         self.cluster_idx = view["cluster_idx"]

@@ -35,6 +35,15 @@ struct tpc_ctx {
   TrackBuf tb{};
   RefitBuf rb{};
   MergeBuf mb{};
+  // concatenated inputs of tpc_find_tracks_batched (library-owned)
+  struct {
+    float* y = nullptr;
+    float* z = nullptr;
+    double* t = nullptr;
+    uint8_t *row = nullptr, *sector = nullptr, *flags = nullptr;
+    uint32_t* event = nullptr;
+    int64_t cap = 0;
+  } bb;
   Prof prof;
   // capacities
   int64_t cap_n = 0, cap_K = 0, cap_bins = 0, cap_blk = 0, cap_ev = 0;
@@ -288,10 +297,7 @@ tpc_status tpc_create(const tpc_geometry* geo, const tpc_params* params, void* s
                       tpc_ctx** out) {
   if (!out) return TPC_ERR_ARG;
   *out = nullptr;
-  if (!geo || !geo->row_x || geo->n_rows < 3 || geo->n_rows > TPC_MAX_ROWS) return TPC_ERR_ARG;
-  for (int r = 1; r < geo->n_rows; ++r)
-    if (!(geo->row_x[r] > geo->row_x[r - 1])) return TPC_ERR_ARG;
-  if (!(geo->tan_half > 0.0f) || !(geo->drift_length > 0.0f)) return TPC_ERR_ARG;
+  if (!geometry_valid(geo)) return TPC_ERR_ARG;
   tpc_ctx* ctx = new tpc_ctx();
   if (cudaGetDevice(&ctx->device) != cudaSuccess) {
     delete ctx;
@@ -392,7 +398,9 @@ void tpc_destroy(tpc_ctx* ctx) {
                   ctx->mb.bk_v, ctx->mb.bk_t, ctx->mb.bk_rlo, ctx->mb.bk_cls,
                   ctx->mb.best_in, ctx->mb.best_out, ctx->mb.next, ctx->mb.has_in,
                   ctx->mb.pairs, ctx->mb.n_pairs, ctx->mb.n_seg,
-                  ctx->mb.hpos, ctx->mb.cpos, ctx->mb.blk_h, ctx->mb.blk_c};
+                  ctx->mb.hpos, ctx->mb.cpos, ctx->mb.blk_h, ctx->mb.blk_c,
+                  ctx->bb.y, ctx->bb.z, ctx->bb.t, ctx->bb.row, ctx->bb.sector, ctx->bb.flags,
+                  ctx->bb.event};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
@@ -559,6 +567,91 @@ tpc_status tpc_find_tracks(tpc_ctx* ctx, tpc_tracks* out) {
     out->start_hit = ctx->tb.start_hit;
   }
   return TPC_OK;
+}
+
+namespace {
+// Event index of each cluster of one part of a batched call: the part's own
+// index (0 when it has none) shifted by the events of the parts before it.
+__global__ void k_batch_event(int64_t n, const uint32_t* ev_in, uint32_t offset, uint32_t* out) {
+  int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < n) out[j] = offset + (ev_in ? ev_in[j] : 0u);
+}
+}  // namespace
+
+tpc_status tpc_find_tracks_batched(tpc_ctx* ctx, const tpc_clusters* ev, int32_t n_parts,
+                                   tpc_tracks* out) {
+  if (!ctx || !ev) return fail(ctx, TPC_ERR_ARG, "null argument");
+  if (ctx->capturing) return fail(ctx, TPC_ERR_STATE, "tpc_find_tracks_batched synchronises");
+  if (n_parts < 1) return fail(ctx, TPC_ERR_ARG, "n_parts must be >= 1");
+  int64_t n = 0;
+  int64_t n_events = 0;
+  for (int32_t i = 0; i < n_parts; ++i) {
+    const tpc_clusters& c = ev[i];
+    if (c.n < 0 || c.n_events < 1) return fail(ctx, TPC_ERR_ARG, "part: n or n_events");
+    if (c.mode != ev[0].mode || c.pads != ev[0].pads)
+      return fail(ctx, TPC_ERR_ARG, "parts differ in mode or pads");
+    if (c.mode == 1 && c.tf_start != ev[0].tf_start)
+      return fail(ctx, TPC_ERR_ARG, "parts of a time-frame batch need the same tf_start");
+    if (c.n > 0 && (!c.y || !c.row || !c.sector || (c.mode == 0 && !c.z) ||
+                    (c.mode == 1 && !c.t)))
+      return fail(ctx, TPC_ERR_ARG, "part: missing cluster array");
+    if (c.n_events > 1 && c.n > 0 && !c.event)
+      return fail(ctx, TPC_ERR_ARG, "part: event array required for n_events > 1");
+    n += c.n;
+    n_events += c.n_events;
+  }
+  if (n >= (int64_t)1 << 31) return fail(ctx, TPC_ERR_ARG, "n out of range");
+  if (n_events > 4096) return fail(ctx, TPC_ERR_ARG, "more than 4096 events");
+  const int mode = ev[0].mode;
+  auto& B = ctx->bb;
+  if (n > B.cap || !B.y) {
+    int64_t c = n > 0 ? n : 1;
+    CK(alloc(B.y, c));
+    CK(alloc(B.z, c));
+    CK(alloc(B.t, c));
+    CK(alloc(B.row, c));
+    CK(alloc(B.sector, c));
+    CK(alloc(B.flags, c));
+    CK(alloc(B.event, c));
+    B.cap = c;
+  }
+  cudaStream_t s = ctx->stream;
+  int64_t off = 0;
+  uint32_t ev_off = 0;
+  for (int32_t i = 0; i < n_parts; ++i) {
+    const tpc_clusters& c = ev[i];
+    if (c.n > 0) {
+      size_t m = (size_t)c.n;
+      CK(cudaMemcpyAsync(B.y + off, c.y, 4 * m, cudaMemcpyDeviceToDevice, s));
+      if (mode == 0) CK(cudaMemcpyAsync(B.z + off, c.z, 4 * m, cudaMemcpyDeviceToDevice, s));
+      else CK(cudaMemcpyAsync(B.t + off, c.t, 8 * m, cudaMemcpyDeviceToDevice, s));
+      CK(cudaMemcpyAsync(B.row + off, c.row, m, cudaMemcpyDeviceToDevice, s));
+      CK(cudaMemcpyAsync(B.sector + off, c.sector, m, cudaMemcpyDeviceToDevice, s));
+      if (c.flags) CK(cudaMemcpyAsync(B.flags + off, c.flags, m, cudaMemcpyDeviceToDevice, s));
+      else CK(cudaMemsetAsync(B.flags + off, 0, m, s));
+      k_batch_event<<<(unsigned)((c.n + 255) / 256), 256, 0, s>>>(
+          c.n, c.n_events > 1 ? c.event : nullptr, ev_off, B.event + off);
+      CK(cudaGetLastError());
+    }
+    off += c.n;
+    ev_off += (uint32_t)c.n_events;
+  }
+  tpc_clusters all{};
+  all.n = n;
+  all.mode = mode;
+  all.n_events = (int32_t)n_events;
+  all.tf_start = ev[0].tf_start;
+  all.y = B.y;
+  all.z = mode == 0 ? B.z : nullptr;
+  all.t = mode == 1 ? B.t : nullptr;
+  all.row = B.row;
+  all.sector = B.sector;
+  all.flags = B.flags;
+  all.event = B.event;
+  all.pads = ev[0].pads;
+  tpc_status st = tpc_load_clusters(ctx, &all);
+  if (st != TPC_OK) return st;
+  return tpc_find_tracks(ctx, out);
 }
 
 tpc_status tpc_get_tracks(tpc_ctx* ctx, tpc_tracks* out) {

@@ -302,6 +302,16 @@ void launch_export_tracklets(const FindBuf& b, int n_rows, int64_t n_cap, const 
                              uint32_t* start_hit, int32_t* nh, double* that, int32_t* hits,
                              cudaStream_t s);
 
+// Host-side check of a geometry as every entry point that takes one
+// accepts it: 3 .. TPC_MAX_ROWS pad rows with strictly increasing plane
+// positions, a positive half-opening tangent and a positive drift length.
+inline bool geometry_valid(const tpc_geometry* geo) {
+  if (!geo || !geo->row_x || geo->n_rows < 3 || geo->n_rows > TPC_MAX_ROWS) return false;
+  for (int r = 1; r < geo->n_rows; ++r)
+    if (!(geo->row_x[r] > geo->row_x[r - 1])) return false;
+  return geo->tan_half > 0.0f && geo->drift_length > 0.0f;
+}
+
 // launchers (tpc_refit.cu)
 void launch_refit(Prof* P, const Geo& g, const Params& p, int64_t cap_tr, const uint32_t* cnt,
                   const TrackBuf& tb, RefitBuf& rb, bool save, float* params, float* cov,

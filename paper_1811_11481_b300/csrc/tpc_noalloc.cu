@@ -113,8 +113,10 @@ extern "C" tpc_status tpc_refit_noalloc(const tpc_geometry* geo, const tpc_param
                                         const uint8_t* flags, float* params_out, float* cov_out,
                                         float* chi2_out, int32_t* ndf_out,
                                         int32_t* status_out) {
-  if (!geo || !geo->row_x || geo->n_rows < 3 || geo->n_rows > TPC_MAX_ROWS)
-    return TPC_ERR_ARG;
+  if (!geometry_valid(geo)) return TPC_ERR_ARG;
+  // the uniform-field helix refit only: a full field is refused rather than
+  // ignored (tpc_refit of a context transports in it)
+  if (geo->field) return TPC_ERR_ARG;
   if (n_tracks < 0 || n_assigned < 0) return TPC_ERR_ARG;
   if (n_assigned > kMaxAssigned) return TPC_ERR_CAPACITY;
   if (n_tracks == 0) return TPC_OK;
@@ -124,7 +126,7 @@ extern "C" tpc_status tpc_refit_noalloc(const tpc_geometry* geo, const tpc_param
   tpc_params pc;
   if (params) pc = *params;
   else tpc_default_params(&pc);
-  Geo g;
+  Geo g{};
   RowX rx;
   for (int r = 0; r < TPC_MAX_ROWS; ++r) rx.v[r] = r < geo->n_rows ? geo->row_x[r] : 0.0f;
   g.rx = reinterpret_cast<const float*>(scratch);
@@ -133,7 +135,7 @@ extern "C" tpc_status tpc_refit_noalloc(const tpc_geometry* geo, const tpc_param
   g.L = geo->drift_length;
   g.bz = geo->bz;
   g.kB = (float)2.99792458e-3 * geo->bz;
-  RefitCfg cfg;
+  RefitCfg cfg{};
   cfg.kB = g.kB;
   cfg.s_max = pc.s_max;
   cfg.sigma = pc.sigma;
