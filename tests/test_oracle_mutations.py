@@ -22,7 +22,7 @@ MUTANTS = {
  'jac_ys_index': ("R Jys = dx * dTds;", "R Jys = dx * dTdq;"),
  'cov_transpose': ("acc = acc + Tm[i][l2] * J[j][l2];", "acc = acc + Tm[i][l2] * J[l2][j];"),
  'gain_swap': ("K1[i] = st.C[i][0] * in.W01 + st.C[i][1] * in.W11;", "K1[i] = st.C[i][0] * in.W11 + st.C[i][1] * in.W01;"),
- 'w01_sign': ("in.W01 = -(S01 * idet);", "in.W01 = (S01 * idet);"),
+ 'w01_sign': ("in.W01 = -(S01 / det);", "in.W01 = (S01 / det);"),
  'basis_const': ("b[1] = ((R(3) * f3 - R(6) * f2) + R(4)) / R(6);", "b[1] = ((R(3) * f3 - R(6) * f2) + R(3)) / R(6);"),
  'dca_sign': ("R cy = y - cs / kap;", "R cy = y + cs / kap;"),
  'tape_div': ("return mk(q, a.id, 1.0 / b.v, b.id, -q / b.v);", "return mk(q, a.id, 1.0 / b.v, b.id, q / b.v);"),
@@ -37,7 +37,7 @@ MUTANTS = {
  'nb_pred_sign': ("R py = yh - (yu - yh) * f;", "R py = yh + (yu - yh) * f;"),
  'chi2_drop_term': ("in.chi2 = in.r0 * (in.W00 * in.r0 + in.W01 * in.r1) + in.r1 * (in.W01 * in.r0 + in.W11 * in.r1);", "in.chi2 = in.r0 * (in.W00 * in.r0 + in.W01 * in.r1);"),
  'spline_vw_swap': ("R wb = bw[cc] * bv[bb];", "R wb = bw[bb] * bv[cc];"),
- 'pick_z_weight': ("R d2 = (ry * ry) * ivy + (rz * rz) * ivz;", "R d2 = (ry * ry) * ivy + (rz * rz) * ivy;"),
+ 'pick_z_weight': ("R d2 = (ry * ry) / vy + (rz * rz) / vz;", "R d2 = (ry * ry) / vy + (rz * rz) / vy;"),
  'no_inward_scale': ("st.C[i][j] = st.C[i][j] * R(c.p.inward_cov_scale);", "st.C[i][j] = st.C[i][j];"),
  'clean_one_sided': ("upc[h] = (up[h] >= 0 && dn[up[h]] == h) ? up[h] : -1;", "upc[h] = (up[h] >= 0) ? up[h] : -1;"),
  'start_two_hits': ("if (dnc[h] < 0 && upc[h] >= 0 && upc[upc[h]] >= 0) out[m++] = h;", "if (dnc[h] < 0 && upc[h] >= 0) out[m++] = h;"),

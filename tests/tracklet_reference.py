@@ -70,12 +70,18 @@ def tracklets(o, ev, geo, params, calib, upc, starts):
             continue
         # collision time from the closest approach (time mode)
         that = 0.0
-        shift = 0.0
         if ev.mode == "time":
             sg = 1.0 if sec < 18 else -1.0
             that = ev.tf_start - (sg * o.dca_z(p, x)) / calib.vdrift
-            shift = sg * calib.vdrift * (that - ev.tf_start)
-        cal = lambda j: (float(ev.y[j]), zs[j] + shift)
+
+        def cal(j):
+            """Calibrated position once the collision time is known (Sec. 4):
+            z from the drift time, t = t_coll + t0 + (L - |z|) / v_drift."""
+            if ev.mode != "time":
+                return float(ev.y[j]), zs[j]
+            sg = 1.0 if ev.sector[j] < 18 else -1.0
+            zeta = calib.vdrift * ((float(ev.t[j]) - calib.t0) - that)
+            return float(ev.y[j]), sg * (float(np.float32(geo.drift_length)) - zeta)
         # seed fit in calibrated coordinates
         yz = [cal(h) for h in chain]
         p, C, x = _seed_two_points(xs[0], yz[0][0], yz[0][1], xs[-1], yz[-1][0], yz[-1][1],
@@ -93,13 +99,13 @@ def tracklets(o, ev, geo, params, calib, upc, starts):
             continue
 
         def pick(p, C, r):
-            ivy = 1.0 / (C[0, 0] + sig2)
-            ivz = 1.0 / (C[1, 1] + sig2)
+            vy = C[0, 0] + sig2
+            vz = C[1, 1] + sig2
             best, bd = -1, 0.0
             for j in rows.get((e, sec, r), []):
                 yc, zc = cal(j)
                 ry, rz = yc - p[0], zc - p[1]
-                d2 = (ry * ry) * ivy + (rz * rz) * ivz
+                d2 = (ry * ry) / vy + (rz * rz) / vz
                 if not d2 <= params["chi2_pick"]:
                     continue
                 if best < 0 or d2 < bd:
