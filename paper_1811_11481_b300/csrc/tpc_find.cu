@@ -1,7 +1,10 @@
 // Track finding on the GPU (arXiv:1811.11481 Sec. 2 and Sec. 4).
 //
-// Compiled with -fmad=false: every decision (windows, argmins, pick-up cuts)
-// is taken on single-precision values rounded once per written operation.
+// Compiled with -fmad=false: the neighbour finder's windows and argmins are
+// taken on single-precision values rounded once per written operation; the
+// tracklet constructor's Kalman steps use the explicit Fast arithmetic of
+// tpc_math.cuh (fused multiply-adds, approximate reciprocals), the same bits
+// whatever the launch shape.
 //
 // Data flow of one batch (all on the context's stream, no host round trip):
 //   k_hist      cluster -> (event, sector, row) bucket counts, seed z (Sec. 4
@@ -793,7 +796,7 @@ __device__ int step_measurement(const Geo& g, const Cal& c, const Params& p, con
   int side = ev * 2 + (sec >= 18 ? 1 : 0);
   float sig2 = p.sigma * p.sigma;
   float vy = C[0] + sig2, vz = C[2] + sig2;
-  float ivy = 1.0f / vy, ivz = 1.0f / vz;
+  float ivy = Fast::rcp(vy), ivz = Fast::rcp(vz);
   int iz0 = 0, iz1 = 0, iy0 = 0, iy1 = 0;
   if (!seed) {
     // window half-widths bound the search box only (the cut below decides):
@@ -844,7 +847,7 @@ __device__ int step_measurement(const Geo& g, const Cal& c, const Params& p, con
       }
       float ry = yc - st[0];
       float rz = zc - st[1];
-      float d2 = (ry * ry) * ivy + (rz * rz) * ivz;
+      float d2 = Fast::fma(rz * rz, ivz, (ry * ry) * ivy);
       if (!(d2 <= p.chi2_pick)) continue;
       bool take = best < 0 || d2 < bd;
       if (!take && d2 == bd) take = __ldg(G.gorig + j) < __ldg(G.gorig + best);
@@ -936,7 +939,7 @@ __global__ void __launch_bounds__(BS, kCap ? 512 / BS : 0) k_tracklets(Geo g, Ca
       nh = 0;
       failed = false;
     }
-    bool ok = propagate(g.kB, p.s_max, st, C, x, g.rx[r]);
+    bool ok = propagate<Fast>(g.kB, p.s_max, st, C, x, g.rx[r]);
     bool have = false;
     float my = 0.0f, mz = 0.0f;
     int j = -1;
@@ -944,7 +947,7 @@ __global__ void __launch_bounds__(BS, kCap ? 512 / BS : 0) k_tracklets(Geo g, Ca
       j = step_measurement(g, c, p, gd, BB, G, ev, sec, r, st, C, shift, spl_on, dymax, dzmax,
                            phase, h, my, mz);
       have = j >= 0;
-      if (have) apply_update(st, C, innovation(st, C, my, mz, sig2, sig2));
+      if (have) apply_update<Fast>(st, C, innovation<Fast>(st, C, my, mz, sig2, sig2));
     }
     bool start_in = false;
     if (phase == kSeed1 || phase == kSeed2) {

@@ -1,12 +1,21 @@
 // Device arithmetic of the track model (arXiv:1811.11481 Sec. 2-4).
 //
 // Everything here is __host__ __device__ and single precision except the
-// float64 conversion of absolute drift times (Sec. 4). Operations are written
-// one rounding at a time in a fixed order; translation units that take
-// discrete decisions with these functions are compiled with -fmad=false so no
-// multiply-add is contracted behind the reader's back.
+// float64 conversion of absolute drift times (Sec. 4). The track-model
+// functions take an arithmetic policy:
+//   Exact - the formulas as written, one IEEE rounding per operation
+//           (division and square root correctly rounded); translation units
+//           that use it are compiled with -fmad=false, so that an
+//           implementation of the same formulas elsewhere (the merge and the
+//           compression format are defined by them) gets the same bits;
+//   Fast  - fused multiply-adds and approximate reciprocal and reciprocal
+//           square root (the tracklet constructor, whose discrete decisions
+//           are checked against the float64 method up to near-ties).
+// Both are explicit in the source, so a launch shape or register cap cannot
+// change the rounding.
 #pragma once
 
+#include <cmath>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -37,6 +46,34 @@ struct Geo {
   float field[30];   // (Bx, By, Bz) quadratic polynomials in (X, Y, Z) / 100 cm
 };
 
+// ------------------------------------------------------ arithmetic policies
+struct Exact {
+  static TPC_HD float fma(float a, float b, float c) { return a * b + c; }
+  static TPC_HD float div(float a, float b) { return a / b; }
+  static TPC_HD float rcp(float a) { return 1.0f / a; }
+  static TPC_HD float sqrt(float a) { return sqrtf(a); }
+  static TPC_HD float rsqrt(float a) { return 1.0f / sqrtf(a); }
+};
+struct Fast {
+#ifdef __CUDA_ARCH__
+  static __device__ __forceinline__ float fma(float a, float b, float c) {
+    return __fmaf_rn(a, b, c);
+  }
+  static __device__ __forceinline__ float rcp(float a) { return __fdividef(1.0f, a); }
+  static __device__ __forceinline__ float div(float a, float b) { return __fdividef(a, b); }
+  // a > 0 wherever it is used (1 - sin^2 with |sin| < s_max, 1 + T^2, a
+  // squared chord)
+  static __device__ __forceinline__ float rsqrt(float a) { return rsqrtf(a); }
+  static __device__ __forceinline__ float sqrt(float a) { return a * rsqrtf(a); }
+#else
+  static float fma(float a, float b, float c) { return std::fma(a, b, c); }
+  static float rcp(float a) { return 1.0f / a; }
+  static float div(float a, float b) { return a / b; }
+  static float rsqrt(float a) { return 1.0f / std::sqrt(a); }
+  static float sqrt(float a) { return std::sqrt(a); }
+#endif
+};
+
 struct Cal {
   double vdrift, t0, tf_start;
   const float* spline;    // device [36][2][8][8][8]
@@ -50,37 +87,37 @@ TPC_HD int sidx(int i, int j) { return i >= j ? i * (i + 1) / 2 + j : j * (j + 1
 // --------------------------------------------------------------- arc length
 // A(h) = asin(h)/h from the Maclaurin series after half-angle reductions
 // asin(h) = 2 asin(h / sqrt(2 (1 + sqrt(1 - h^2)))), and B(h) = A'(h).
-TPC_HD float series_asin_over_x(float h2) {
+template <class O = Exact> TPC_HD float series_asin_over_x(float h2) {
   float p = 35.0f / 1152.0f;
-  p = 5.0f / 112.0f + h2 * p;
-  p = 3.0f / 40.0f + h2 * p;
-  p = 1.0f / 6.0f + h2 * p;
-  p = 1.0f + h2 * p;
+  p = O::fma(h2, p, 5.0f / 112.0f);
+  p = O::fma(h2, p, 3.0f / 40.0f);
+  p = O::fma(h2, p, 1.0f / 6.0f);
+  p = O::fma(h2, p, 1.0f);
   return p;
 }
-TPC_HD float arc_factor(float h) {
-  if (fabsf(h) < 0.125f) return series_asin_over_x(h * h);
+template <class O = Exact> TPC_HD float arc_factor(float h) {
+  if (fabsf(h) < 0.125f) return series_asin_over_x<O>(h * h);
   if (!(fabsf(h) <= 1.0f)) return (h - h) / (h - h);  // NaN
   float hh = h, m = 1.0f;
   while (fabsf(hh) >= 0.125f) {
-    float c = sqrtf(1.0f - hh * hh);
-    hh = hh / sqrtf(2.0f * (1.0f + c));
+    float c = O::sqrt(1.0f - hh * hh);
+    hh = O::div(hh, O::sqrt(2.0f * (1.0f + c)));
     m = m * 2.0f;
   }
-  return ((m * hh) * series_asin_over_x(hh * hh)) / h;
+  return O::div((m * hh) * series_asin_over_x<O>(hh * hh), h);
 }
-TPC_HD float arc_factor_deriv(float h) {
+template <class O = Exact> TPC_HD float arc_factor_deriv(float h) {
   if (fabsf(h) < 0.125f) {
     float h2 = h * h;
     float c = 315.0f / 1408.0f;
-    c = 35.0f / 144.0f + h2 * c;
-    c = 15.0f / 56.0f + h2 * c;
-    c = 3.0f / 10.0f + h2 * c;
-    c = 1.0f / 3.0f + h2 * c;
+    c = O::fma(h2, c, 35.0f / 144.0f);
+    c = O::fma(h2, c, 15.0f / 56.0f);
+    c = O::fma(h2, c, 3.0f / 10.0f);
+    c = O::fma(h2, c, 1.0f / 3.0f);
     return h * c;
   }
-  float e = 1.0f / sqrtf(1.0f - h * h);
-  return (e - arc_factor(h)) / h;
+  float e = O::rsqrt(1.0f - h * h);
+  return O::div(e - arc_factor<O>(h), h);
 }
 
 // ----------------------------------------------------------- time to z
@@ -172,66 +209,52 @@ struct Jac {
   float ys, yq, zs, zt, zq, sq;  // non-identity entries
 };
 
-// 1/sqrt(1 - h^2): Maclaurin series for |h| < 1/8, else direct.
-TPC_HD float inv_cos_half(float h) {
-  if (fabsf(h) < 0.125f) {
-    float h2 = h * h;
-    float p = 35.0f / 128.0f;
-    p = 5.0f / 16.0f + h2 * p;
-    p = 3.0f / 8.0f + h2 * p;
-    p = 0.5f + h2 * p;
-    return 1.0f + h2 * p;
-  }
-  return 1.0f / sqrtf(1.0f - h * h);
-}
-
 // Exact helix transport to x2 in a uniform field with its analytic Jacobian.
 // Returns false when |sin(phi)| would reach s_max.
+template <class O = Exact>
 TPC_HD bool transport(float kB, float s_max, float p[5], float& x, float x2, Jac& J) {
   float dx = x2 - x;
   float y = p[0], z = p[1], s = p[2], t = p[3], q = p[4];
   float kap = kB * q;
-  float s2 = s - kap * dx;
+  float s2 = O::fma(-kap, dx, s);
   if (!(fabsf(s2) < s_max)) return false;
-  float c1 = sqrtf(1.0f - s * s);
-  float c2 = sqrtf(1.0f - s2 * s2);
-  float ic1 = 1.0f / c1;
-  float ic2 = 1.0f / c2;
+  float c1 = O::sqrt(O::fma(-s, s, 1.0f));
+  float c2 = O::sqrt(O::fma(-s2, s2, 1.0f));
   float N = s + s2;
   float D = c1 + c2;
-  float iD = 1.0f / D;
-  float T = N * iD;
+  float T = O::div(N, D);
   float dy = dx * T;
-  float opt = 1.0f + T * T;
-  float d = dx * sqrtf(opt);
+  float opt = O::fma(T, T, 1.0f);
+  float d = dx * O::sqrt(opt);
   float h = (kap * d) * 0.5f;
-  float A = arc_factor(h);
+  float A = arc_factor<O>(h);
   float l = d * A;
-  float dDds = -(s * ic1) - (s2 * ic2);
+  float sc1 = O::div(s, c1), sc2 = O::div(s2, c2);
+  float dDds = -sc1 - sc2;
   float kdx = kB * dx;
-  float dDdq = kdx * (s2 * ic2);
-  float dTds = (2.0f - T * dDds) * iD;
-  float dTdq = (-kdx - T * dDdq) * iD;
+  float dDdq = kdx * sc2;
+  float dTds = O::div(O::fma(-T, dDds, 2.0f), D);
+  float dTdq = O::div(O::fma(-T, dDdq, -kdx), D);
   J.ys = dx * dTds;
   J.yq = dx * dTdq;
-  float gg = (d * T) / opt;
+  float gg = O::div(d * T, opt);
   float dds = gg * dTds;
   float ddq = gg * dTdq;
-  float E = inv_cos_half(h);
-  float Bh = arc_factor_deriv(h);
+  float E = O::rsqrt(O::fma(-h, h, 1.0f));
+  float Bh = arc_factor_deriv<O>(h);
   J.zs = t * (E * dds);
-  J.zq = t * (E * ddq + (kB * ((d * d) * Bh)) * 0.5f);
+  J.zq = t * O::fma(E, ddq, (kB * ((d * d) * Bh)) * 0.5f);
   J.zt = l;
   J.sq = -kdx;
   p[0] = y + dy;
-  p[1] = z + t * l;
+  p[1] = O::fma(t, l, z);
   p[2] = s2;
   x = x2;
   return true;
 }
 
 // C' = J C J^T with index-ascending sums over the non-zero entries of J.
-TPC_HD void transport_cov(const Jac& J, float C[15]) {
+template <class O = Exact> TPC_HD void transport_cov(const Jac& J, float C[15]) {
   float Cf[5][5];
 #pragma unroll
   for (int i = 0; i < 5; ++i)
@@ -240,32 +263,37 @@ TPC_HD void transport_cov(const Jac& J, float C[15]) {
   float T[5][5];
 #pragma unroll
   for (int l = 0; l < 5; ++l) {
-    T[0][l] = (Cf[0][l] + J.ys * Cf[2][l]) + J.yq * Cf[4][l];
-    T[1][l] = ((Cf[1][l] + J.zs * Cf[2][l]) + J.zt * Cf[3][l]) + J.zq * Cf[4][l];
-    T[2][l] = Cf[2][l] + J.sq * Cf[4][l];
+    T[0][l] = O::fma(J.yq, Cf[4][l], O::fma(J.ys, Cf[2][l], Cf[0][l]));
+    T[1][l] = O::fma(J.zq, Cf[4][l], O::fma(J.zt, Cf[3][l], O::fma(J.zs, Cf[2][l], Cf[1][l])));
+    T[2][l] = O::fma(J.sq, Cf[4][l], Cf[2][l]);
     T[3][l] = Cf[3][l];
     T[4][l] = Cf[4][l];
   }
 #pragma unroll
   for (int i = 0; i < 5; ++i) {
-    C[sidx(i, 0)] = (T[i][0] + T[i][2] * J.ys) + T[i][4] * J.yq;
-    if (i >= 1) C[sidx(i, 1)] = ((T[i][1] + T[i][2] * J.zs) + T[i][3] * J.zt) + T[i][4] * J.zq;
-    if (i >= 2) C[sidx(i, 2)] = T[i][2] + T[i][4] * J.sq;
+    C[sidx(i, 0)] = O::fma(T[i][4], J.yq, O::fma(T[i][2], J.ys, T[i][0]));
+    if (i >= 1)
+      C[sidx(i, 1)] =
+          O::fma(T[i][4], J.zq, O::fma(T[i][3], J.zt, O::fma(T[i][2], J.zs, T[i][1])));
+    if (i >= 2) C[sidx(i, 2)] = O::fma(T[i][4], J.sq, T[i][2]);
     if (i >= 3) C[sidx(i, 3)] = T[i][3];
     if (i >= 4) C[sidx(i, 4)] = T[i][4];
   }
 }
 
+template <class O = Exact>
 TPC_HD bool propagate(float kB, float s_max, float p[5], float C[15], float& x, float x2) {
   Jac J;
-  if (!transport(kB, s_max, p, x, x2, J)) return false;
-  transport_cov(J, C);
+  if (!transport<O>(kB, s_max, p, x, x2, J)) return false;
+  transport_cov<O>(J, C);
   return true;
 }
 
 struct Innov {
   float r0, r1, W00, W01, W11, chi2;
 };
+// Innovation r = m - H p, its covariance S = H C H^T + V and W = S^-1.
+template <class O = Exact>
 TPC_HD Innov innovation(const float p[5], const float C[15], float my, float mz, float vy,
                         float vz) {
   Innov in;
@@ -274,16 +302,16 @@ TPC_HD Innov innovation(const float p[5], const float C[15], float my, float mz,
   float S00 = C[0] + vy;
   float S01 = C[1];
   float S11 = C[2] + vz;
-  float det = S00 * S11 - S01 * S01;
-  float idet = 1.0f / det;
-  in.W00 = S11 * idet;
-  in.W01 = -(S01 * idet);
-  in.W11 = S00 * idet;
-  in.chi2 = in.r0 * (in.W00 * in.r0 + in.W01 * in.r1) + in.r1 * (in.W01 * in.r0 + in.W11 * in.r1);
+  float det = O::fma(S00, S11, -(S01 * S01));
+  in.W00 = O::div(S11, det);
+  in.W01 = -O::div(S01, det);
+  in.W11 = O::div(S00, det);
+  in.chi2 = O::fma(in.r1, O::fma(in.W11, in.r1, in.W01 * in.r0),
+                   in.r0 * O::fma(in.W01, in.r1, in.W00 * in.r0));
   return in;
 }
 // Kalman gain K = C H^T S^-1; p += K r; C -= K H C (lower triangle).
-TPC_HD void apply_update(float p[5], float C[15], const Innov& in) {
+template <class O = Exact> TPC_HD void apply_update(float p[5], float C[15], const Innov& in) {
   float C0[5], C1[5];
 #pragma unroll
   for (int j = 0; j < 5; ++j) {
@@ -293,15 +321,16 @@ TPC_HD void apply_update(float p[5], float C[15], const Innov& in) {
   float K0[5], K1[5];
 #pragma unroll
   for (int i = 0; i < 5; ++i) {
-    K0[i] = C0[i] * in.W00 + C1[i] * in.W01;
-    K1[i] = C0[i] * in.W01 + C1[i] * in.W11;
+    K0[i] = O::fma(C1[i], in.W01, C0[i] * in.W00);
+    K1[i] = O::fma(C1[i], in.W11, C0[i] * in.W01);
   }
 #pragma unroll
-  for (int i = 0; i < 5; ++i) p[i] = p[i] + (K0[i] * in.r0 + K1[i] * in.r1);
+  for (int i = 0; i < 5; ++i) p[i] = p[i] + O::fma(K1[i], in.r1, K0[i] * in.r0);
 #pragma unroll
   for (int i = 0; i < 5; ++i)
 #pragma unroll
-    for (int j = 0; j <= i; ++j) C[sidx(i, j)] = C[sidx(i, j)] - (K0[i] * C0[j] + K1[i] * C1[j]);
+    for (int j = 0; j <= i; ++j)
+      C[sidx(i, j)] = C[sidx(i, j)] - O::fma(K1[i], C1[j], K0[i] * C0[j]);
 }
 
 TPC_HD void set_diag(float C[15], const float d[5]) {

