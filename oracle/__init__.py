@@ -109,7 +109,9 @@ def lib():
         L.orc_propagate.restype = C.c_int
         L.orc_propagate.argtypes = [vp, vp, C.c_double, C.c_double, vp, vp, vp]
         L.orc_refit_points.restype = C.c_int
-        L.orc_refit_points.argtypes = [vp, C.c_int64, vp, vp, vp, C.c_double, vp, vp, vp]
+        L.orc_refit_points.argtypes = [vp, C.c_int64, vp, vp, vp, C.c_double, vp, vp, vp, vp,
+                                       vp]
+        L.orc_set_joseph.argtypes = [vp, C.c_int]
         L.orc_jacobian.restype = C.c_int
         L.orc_jacobian.argtypes = [vp, vp, C.c_double, C.c_double, vp, vp]
         L.orc_update.argtypes = [vp, vp, C.c_double, C.c_double, C.c_double, C.c_double,
@@ -433,14 +435,32 @@ class Oracle:
         ok = lib().orc_propagate(self.h, _p(s), float(x1), float(x2), _p(cv), _p(so), _p(co))
         return (so, co) if ok else (None, None)
 
-    def refit_points(self, x, y, z, var):
+    def refit_points(self, x, y, z, var, details=False):
+        """FP64 refit of explicit points (three-point seed); with details also
+        the state each pass starts from (x, parameters, 5x5 covariance) and
+        the final covariance (5x5)."""
         x, y, z = (np.ascontiguousarray(a, np.float64) for a in (x, y, z))
         p = np.empty(5)
         ch = np.empty(1)
         nd = np.empty(1, np.int32)
+        pr = np.empty((3, 21))
+        cv = np.empty(15)
         stt = lib().orc_refit_points(self.h, x.size, _p(x), _p(y), _p(z), float(var), _p(p),
-                                     _p(ch), _p(nd))
-        return stt, p, float(ch[0]), int(nd[0])
+                                     _p(ch), _p(nd), _p(pr), _p(cv))
+        if not details:
+            return stt, p, float(ch[0]), int(nd[0])
+
+        def sym(v):
+            m = np.zeros((5, 5))
+            m[np.tril_indices(5)] = v
+            return m + np.tril(m, -1).T
+        priors = [dict(x=pr[k, 0], p=pr[k, 1:6].copy(), C=sym(pr[k, 6:])) for k in range(3)]
+        return stt, p, float(ch[0]), int(nd[0]), priors, sym(cv)
+
+    def set_joseph(self, on=True):
+        """Covariance update of the refit in the Joseph form (on) or the
+        short form (off, the default)."""
+        lib().orc_set_joseph(self.h, int(bool(on)))
 
     def rotate(self, state, x, dalpha, cov=None):
         """The state re-expressed in a frame rotated by dalpha (and its

@@ -272,6 +272,7 @@ struct Ctx {
   std::vector<float> zs32;
   std::vector<double> zs64;
   std::vector<std::vector<int64_t>> rows;  // (event, sector, row) -> clusters
+  bool joseph = false;  // the refit updates its covariance in the Joseph form
   const std::vector<int64_t>& rowlist(int64_t ev, int sec, int r) const {
     return rows[((size_t)ev * kNS + sec) * g.n_rows + r];
   }
@@ -620,6 +621,35 @@ template <class R> Innov<R> innovation(const Trk<R>& st, R my, R mz, R vy, R vz)
   return in;
 }
 // p += K r, C -= K H C (short form), K = C H^T S^-1.
+// Joseph form of the same update (Sec. 3 filter; numerically symmetric and
+// positive): C = (I - K H) C (I - K H)^T + K V K^T with V = diag(vy, vz).
+template <class R> void apply_update_joseph(Trk<R>& st, const Innov<R>& in, R vy, R vz) {
+  R K[5][2];
+  for (int i = 0; i < 5; ++i) {
+    K[i][0] = st.C[i][0] * in.W00 + st.C[i][1] * in.W01;
+    K[i][1] = st.C[i][0] * in.W01 + st.C[i][1] * in.W11;
+  }
+  for (int i = 0; i < 5; ++i) st.p[i] = st.p[i] + (K[i][0] * in.r0 + K[i][1] * in.r1);
+  R A[5][5];  // I - K H
+  for (int i = 0; i < 5; ++i)
+    for (int j = 0; j < 5; ++j) A[i][j] = R(i == j ? 1 : 0) - (j < 2 ? K[i][j] : R(0));
+  R AC[5][5];
+  for (int i = 0; i < 5; ++i)
+    for (int j = 0; j < 5; ++j) {
+      R acc = R(0);
+      for (int l = 0; l < 5; ++l) acc = acc + A[i][l] * st.C[l][j];
+      AC[i][j] = acc;
+    }
+  for (int i = 0; i < 5; ++i)
+    for (int j = 0; j <= i; ++j) {
+      R acc = R(0);
+      for (int l = 0; l < 5; ++l) acc = acc + AC[i][l] * A[j][l];
+      acc = acc + (K[i][0] * vy * K[j][0] + K[i][1] * vz * K[j][1]);
+      st.C[i][j] = acc;
+      st.C[j][i] = acc;
+    }
+}
+
 template <class R> void apply_update(Trk<R>& st, const Innov<R>& in) {
   R K0[5], K1[5];
   for (int i = 0; i < 5; ++i) {
@@ -1080,10 +1110,12 @@ bool seed_three_points(const Ctx& c, const std::vector<R>& x, const std::vector<
 }
 
 template <class R>
+// priors (may be null): the state each pass starts from, per pass its x,
+// the five parameters and the 15 covariance entries (lower triangle).
 RefitOut refit_core(const Ctx& c, const std::vector<R>& x, const std::vector<R>& yc,
                     const std::vector<R>& zc, const std::vector<R>& var, const double seed[5],
                     uint8_t* rej, bool frozen, R* chi2_out,
-                    const std::vector<double>* alpha = nullptr) {
+                    const std::vector<double>* alpha = nullptr, double* priors = nullptr) {
   RefitOut o;
   std::memset(&o, 0, sizeof(o));
   size_t n = x.size();
@@ -1099,6 +1131,14 @@ RefitOut refit_core(const Ctx& c, const std::vector<R>& x, const std::vector<R>&
     if (pass > 1)
       for (int i = 0; i < 5; ++i)
         for (int j = 0; j < 5; ++j) st.C[i][j] = st.C[i][j] * R(c.p.refit_inflate);
+    if (priors) {
+      double* pr = priors + (pass - 1) * 21;
+      pr[0] = val(st.x);
+      for (int i = 0; i < 5; ++i) pr[1 + i] = val(st.p[i]);
+      int q = 6;
+      for (int i = 0; i < 5; ++i)
+        for (int j = 0; j <= i; ++j) pr[q++] = val(st.C[i][j]);
+    }
     chi2 = R(0);
     ndf = 0;
     int nacc = 0;
@@ -1129,7 +1169,8 @@ RefitOut refit_core(const Ctx& c, const std::vector<R>& x, const std::vector<R>&
         if (reject) rej[i] = (uint8_t)pass;
       }
       if (reject) continue;
-      apply_update<R>(st, in);
+      if (c.joseph) apply_update_joseph<R>(st, in, var[i], var[i]);
+      else apply_update<R>(st, in);
       chi2 = chi2 + in.chi2;
       ndf += 2;
       ++nacc;
@@ -1750,6 +1791,9 @@ void orc_refit_grad(void* ctx, int64_t nt, const uint32_t* track_start,
   }
 }
 
+// The refit's covariance update: 1 = Joseph form, 0 = the short form.
+void orc_set_joseph(void* ctx, int on) { ((Ctx*)ctx)->joseph = on != 0; }
+
 // Threads used by the parallel loops (over hits, start hits, tracks and
 // clusters); n < 1 leaves the setting unchanged. Returns the count in force.
 int orc_threads(int n) {
@@ -1852,15 +1896,20 @@ int orc_rotate(void* ctx, const double* state, double x, double dalpha, const do
 }
 
 // Refit of one track given float64 points directly (for closed-form checks).
+// priors (may be NULL): [3][21] the state each pass starts from (x, the
+// parameters, the covariance's lower triangle); cov_out (may be NULL): [15].
 int orc_refit_points(void* ctx, int64_t n, const double* x, const double* y, const double* z,
-                     double var, double* params_out, double* chi2, int32_t* ndf) {
+                     double var, double* params_out, double* chi2, int32_t* ndf,
+                     double* priors, double* cov_out) {
   Ctx& c = *(Ctx*)ctx;
   std::vector<double> X(x, x + n), Y(y, y + n), Z(z, z + n), V(n, var);
   double seed[5];
   if (!seed_three_points<double>(c, X, Y, Z, seed)) return 2;
   std::vector<uint8_t> rj(n, 0);
   double ch;
-  RefitOut o = refit_core<double>(c, X, Y, Z, V, seed, rj.data(), false, &ch);
+  RefitOut o = refit_core<double>(c, X, Y, Z, V, seed, rj.data(), false, &ch, nullptr, priors);
+  if (cov_out)
+    for (int i = 0; i < 15; ++i) cov_out[i] = o.C[i];
   for (int i = 0; i < 5; ++i) params_out[i] = o.p[i];
   *chi2 = o.chi2;
   *ndf = o.ndf;

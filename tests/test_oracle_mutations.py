@@ -74,6 +74,10 @@ MUTANTS = {
  'field_not_rotated': ("b0 = B[0] * ca + B[1] * sa;\n      b1 = -(B[0] * sa) + B[1] * ca;", "b0 = B[0];\n      b1 = B[1];"),
  'zero_field_seed_unguarded': ("R q = kB_of<R>(c) != R(0) ? kap / kB_of<R>(c) : R(0);", "R q = kap / kB_of<R>(c);"),
  'merge_solve_operand': ("for (int k = 0; k < a; ++k) acc = acc - L[a][k] * w[k];", "for (int k = 0; k < a; ++k) acc = acc - L[a][k] * d[k];"),
+ 'joseph_no_kvk': ("      acc = acc + (K[i][0] * vy * K[j][0] + K[i][1] * vz * K[j][1]);\n", ""),
+ 'joseph_transposed': ("for (int l = 0; l < 5; ++l) acc = acc + AC[i][l] * A[j][l];", "for (int l = 0; l < 5; ++l) acc = acc + AC[i][l] * A[l][j];"),
+ 'margin_dcut_gradient': ("mg->take(std::fabs(Dv - (double)val(dmax)) / (2.0 * std::sqrt(Dv * kf) * xr));", "mg->take(std::fabs(Dv - (double)val(dmax)) / (2.0 * std::sqrt(Dv) * xr));"),
+ 'margin_tie_skipped': ("      mg->take(g > 0.0 ? std::fabs(Dp - Db) / (g * xr) : 0.0);", "      mg->take(g > 0.0 && Dp != Db ? std::fabs(Dp - Db) / (g * xr) : INFINITY);"),
 }
 
 
@@ -86,9 +90,9 @@ def _caught(src, name, tmp):
     lib = os.path.join(d, "liborc.so")
     subprocess.check_call(["g++", *oracle.CXXFLAGS, os.path.join(d, "oracle.cpp"), "-o", lib])
     env = dict(os.environ, TPC_ORACLE_LIB=lib)
-    r = subprocess.run([sys.executable, "-m", "pytest", "tests/test_oracle_pins.py", "-q", "-x",
-                        "-p", "no:cacheprovider"], cwd=ROOT, env=env, capture_output=True,
-                       text=True)
+    r = subprocess.run([sys.executable, "-m", "pytest", "tests/test_oracle_pins.py",
+                        "tests/test_parity_checker.py", "-q", "-x", "-p", "no:cacheprovider"],
+                       cwd=ROOT, env=env, capture_output=True, text=True)
     return r.returncode != 0
 
 

@@ -229,24 +229,111 @@ def _ls_fit(geo, e, idx, p_start, sigma=0.1):
 
 
 def test_refit_agrees_with_least_squares(geo, params):
+    """Pass 3 of the refit (Sec. 3) starts from pass 2's state with its
+    covariance inflated; its result is the extended Kalman filter's estimate
+    of the minimum of chi2 over the clusters plus that starting state as a
+    pseudo-measurement. Against Gauss-Newton on the same objective with an
+    independent helix model (scipy), on helices with sigma = 0.1 cm: within
+    1e-3 sigma in the median and 2e-2 sigma at most (the filter linearises at
+    its running estimate once, which leaves ~1e-2 sigma on the most curved of
+    40 tracks; without the pseudo-measurement the two differ by up to ~3 % of
+    sigma, which is the prior's weight, not an error)."""
     ev = synth.make_tiny(seed=15, n_tracks=40, sectors=(0,))
     ts, ci, tc, sids = synth.truth_tracks(ev, 50)
     o = _oracle(ev, geo, params)
-    r = o.refit(ts, ci, np.zeros(ts.size - 1), prec=64)
-    n = 0
+    dev = []
     for k in range(ts.size - 1):
-        if r["status"][k] != 0 or np.any(r["rej"][ts[k]:ts[k + 1]]):
-            continue
         idx = ci[ts[k]:ts[k + 1]]
-        p_ls = _ls_fit(geo, ev, idx, r["params"][k])
-        C = np.zeros((5, 5))
-        C[np.tril_indices(5)] = r["cov"][k]
-        sig = np.sqrt(np.diag(C))
-        # the extended Kalman filter agrees with Gauss-Newton to a small
-        # fraction of the parameter uncertainty
-        assert np.all(np.abs(r["params"][k] - p_ls) < 0.03 * sig), (k, (r["params"][k] - p_ls) / sig)
-        n += 1
-    assert n >= 15
+        xs = geo.row_x[ev.row[idx]].astype(np.float64)
+        ys, zs = ev.y[idx].astype(np.float64), ev.z[idx].astype(np.float64)
+        stt, p, chi2, ndf, pri, C = o.refit_points(xs, ys, zs, 0.01, details=True)
+        if stt != 0 or ndf != 2 * xs.size:
+            continue
+        pr = pri[2]
+        L = np.linalg.cholesky(np.linalg.inv(pr["C"]))
+
+        def res(q):
+            yy, zz = _helix_at_planes(q, xs[0], xs)
+            yn, zn = _helix_at_planes(q, xs[0], np.array([pr["x"]]))
+            sn = q[2] - KB * q[4] * (pr["x"] - xs[0])
+            d = np.array([yn[0], zn[0], sn, q[3], q[4]]) - pr["p"]
+            return np.concatenate([(yy - ys) / 0.1, (zz - zs) / 0.1, L.T @ d])
+        sol = so.least_squares(res, p, xtol=1e-15, ftol=1e-15, gtol=1e-15,
+                               x_scale=np.array([0.1, 0.1, 1e-3, 1e-3, 1e-2]))
+        dev.append(np.abs(p - sol.x) / np.sqrt(np.diag(C)))
+    dev = np.array(dev)
+    assert dev.shape[0] >= 15
+    assert np.all(dev < 2e-2), dev.max(0)
+    assert np.all(np.median(dev, 0) < 1e-3), np.median(dev, 0)
+
+
+def test_zero_field_refit_is_least_squares_with_the_priors(geo, params):
+    """Information-filter identity (Sec. 3 refit, no field): for tracks on
+    the sector's centre line (y = 0, so sin(phi) stays 0 and the transport
+    is linear in (z, tan(lambda)); with sin(phi) != 0 it is not linear even
+    without a field), each pass equals weighted linear least squares of the
+    noisy z measurements with the state the pass starts from (the seed with
+    the prior covariance C0 in pass 1, then the previous pass's state with
+    its inflated covariance) as a pseudo-measurement: state, covariance and
+    chi2 to 1e-12 relative."""
+    import dataclasses
+    geo0 = dataclasses.replace(geo, bz=np.float32(0.0))
+    o = _oracle(synth.make_tiny(seed=14, n_tracks=4, sectors=(0,), sigma=0.0), geo0, params)
+    rng = np.random.default_rng(5)
+    x = geo.row_x.astype(np.float64)
+    sig = 0.1
+    for _ in range(10):
+        t, z0 = rng.uniform(-1, 1), rng.uniform(-100, 100)
+        z = z0 + (x - x[0]) * t + rng.normal(0, sig, x.size)
+        stt, p, chi2, ndf, pri, C = o.refit_points(x, np.zeros_like(x), z, sig * sig,
+                                                   details=True)
+        assert stt == 0 and ndf == 2 * x.size
+        assert p[0] == 0.0 and p[2] == 0.0 and p[4] == 0.0
+        # pass 1 starts from the seed with the prior covariance C0
+        np.testing.assert_array_equal(np.diag(pri[0]["C"]), np.float32(params["c0r"]))
+        for k, xr in enumerate((x[0], x[-1], x[0])):        # plane each pass ends at
+            pr = pri[k]
+            Pi = np.linalg.inv(pr["C"][np.ix_([1, 3], [1, 3])])
+            F = np.array([[1.0, pr["x"] - xr], [0.0, 1.0]])  # (z, t) at xr -> prior plane
+            H = np.stack([np.ones_like(x), x - xr], 1)
+            A = H.T @ H / sig ** 2 + F.T @ Pi @ F
+            sol = np.linalg.solve(A, H.T @ z / sig ** 2 + F.T @ Pi @ pr["p"][[1, 3]])
+            if k < 2:   # the next pass starts from this one's state
+                nxt = pri[k + 1]
+                np.testing.assert_allclose(nxt["p"][[1, 3]], sol, rtol=1e-12, atol=1e-12)
+                cov_next = nxt["C"][np.ix_([1, 3], [1, 3])] / params["refit_inflate"]
+                np.testing.assert_allclose(cov_next, np.linalg.inv(A), rtol=1e-12)
+        np.testing.assert_allclose(p[[1, 3]], sol, rtol=1e-12, atol=1e-12)
+        np.testing.assert_allclose(C[np.ix_([1, 3], [1, 3])], np.linalg.inv(A), rtol=1e-12)
+        r = z - H @ sol
+        d = F @ sol - pr["p"][[1, 3]]
+        assert abs(chi2 - (r @ r / sig ** 2 + d @ Pi @ d)) <= 1e-12 * chi2
+
+
+def test_joseph_form_equals_the_short_form(geo, params):
+    """The Joseph form of the covariance update and the short form used by
+    the refit are the same update in exact arithmetic: in float64 the refit
+    of truth tracks gives the same parameters (1e-10) and covariances
+    (1e-8); in float32 the Joseph form stays at least as close to float64."""
+    ev = synth.make_tiny(seed=16, n_tracks=300, sectors=(0, 5, 19))
+    ts, ci, tc, _ = synth.truth_tracks(ev, 40)
+    o = _oracle(ev, geo, params)
+    short64 = o.refit(ts, ci, tc, prec=64)
+    short32 = o.refit(ts, ci, tc, prec=32, seeds=short64["seeds"])
+    o.set_joseph(True)
+    jos64 = o.refit(ts, ci, tc, prec=64, seeds=short64["seeds"])
+    jos32 = o.refit(ts, ci, tc, prec=32, seeds=short64["seeds"])
+    o.set_joseph(False)
+    ok = (short64["status"] == 0) & (jos64["status"] == 0)
+    assert ok.sum() > 100
+    assert np.array_equal(short64["rej"], jos64["rej"])
+    np.testing.assert_allclose(jos64["params"][ok], short64["params"][ok], rtol=1e-10, atol=1e-12)
+    np.testing.assert_allclose(jos64["cov"][ok], short64["cov"][ok], rtol=1e-8, atol=1e-14)
+    np.testing.assert_allclose(jos64["chi2"][ok], short64["chi2"][ok], rtol=1e-10)
+    ok32 = ok & (short32["status"] == 0) & (jos32["status"] == 0)
+    e_s = np.abs(short32["params"][ok32] - short64["params"][ok32]).max(0)
+    e_j = np.abs(jos32["params"][ok32] - short64["params"][ok32]).max(0)
+    assert np.all(e_j <= 2.0 * e_s + 1e-7), (e_j, e_s)
 
 
 def test_refit_pulls_and_chi2(geo, params):
