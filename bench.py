@@ -60,13 +60,19 @@ def parse():
                     help="launch shapes as JSON (tpc_tuning fields), instead of autotuning")
     ap.add_argument("--graph", action="store_true",
                     help="replay each step as one captured CUDA graph")
+    ap.add_argument("--streams", type=int, default=2,
+                    help="frames in flight: contexts on their own CUDA streams, each with its "
+                         "own frame of the workload (1: one context, serial steps)")
     ap.add_argument("--profile-steps", type=int, default=0,
                     help="only run W+K steps with kernel timing (for ncu launch lists)")
     return ap.parse_args()
 
 
-def make_workload(name, rank, collisions=50, field=None):
+def make_workload(name, rank, collisions=50, field=None, frame=0):
+    """The workload of this rank; frame k > 0 is another frame of the same
+    kind (seed offset by 1000 k) for the k-th context in flight."""
     import synth
+    rank = rank + 1000 * frame
     if name == "central":
         ev = synth.make_central(seed=1 + rank, field=field)
         cfg = dict(workload="central Pb-Pb-like event: 36 sectors x 152 rows, 10000 primaries "
@@ -506,6 +512,18 @@ def run_ours(args):
         tuning, how = tr.autotune(repeats=3), "autotuned"
     else:
         tuning, how = tr.get_tuning(), "default"
+    # the other frames in flight: one context each, on its own stream, with
+    # the same launch shapes
+    others = []
+    for k in range(1, max(1, args.streams)):
+        ev_k, cfg_k = make_workload(args.workload, rank, args.collisions, field, frame=k)
+        st_k = torch.cuda.Stream()
+        tr_k = Tracker(geo, stream=st_k, field=field)
+        tr_k.set_calib()
+        tr_k.set_tuning(**{f: tuning[f] for f in ("grid_tau", "grid_ny_max", "tracklet_block",
+                                                  "tracklet_per_sm", "tracklet_regs")})
+        others.append(dict(ev=ev_k, seed=cfg_k["seed"], stream=st_k, tr=tr_k,
+                           cl=tr_k.upload(ev_k, pads=args.pads)))
     n = ev.n
     cap_tr = n // 10 + 1
     dev = tr.dev
@@ -749,6 +767,15 @@ def run_ours(args):
                         "stream into one of two device buffers (overlapping the previous "
                         "step), track parameters and chi2 copied back every step")
 
+    # ---- frames in flight: every context runs its own frame on its own
+    # stream; a step issues one full pass per context, the step ends when
+    # all have finished (inputs resident, L2 flushed before each step)
+    pipe = None
+    if others:
+        pipe = pipelined(args, torch, dist, dev, flush, stream,
+                         [dict(ev=ev, seed=cfg["seed"], stream=stream, tr=tr, cl=cl)] + others,
+                         barrier)
+
     # ---- rooflines of the top kernels: HBM (algorithmic bytes) and FP32 ALU
     # (executed single-precision operations from the ncu capture, scaled by
     # the launch's units); the dominant kernel's bound is the one it is
@@ -846,14 +873,35 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(ev, geo, secs=sample_sectors(ev))
 
-    line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps,
-                warmup=args.warmup, ms_per_step=total_ms / args.steps, higher_is_better=True,
+    serial = dict(value=value, unit=UNIT, ms_per_step=total_ms / args.steps,
+                  graph_replay=graph_replay, find_refit=dict(value=fr_value, ms_per_step=fr_ms),
+                  e2e=e2e, note="one context, one frame per step (the timed region of the "
+                                "per-kernel events)")
+    step_ms = total_ms / args.steps
+    head_value, head_ms, head_e2e = value, step_ms, e2e
+    head_cfg = dict(cfg)
+    if pipe is not None:
+        head_value, head_ms, head_e2e = pipe["value"], pipe["ms_per_step"], pipe["e2e"]
+        graph_replay = pipe["graph_replay"]
+        head_cfg["workload"] = (f"{len(others) + 1} frames in flight, each on its own context "
+                                f"and CUDA stream: " + cfg["workload"])
+        head_cfg["seed"] = pipe["seeds"]
+        head_cfg["n_clusters"] = pipe["clusters_per_step"]
+        find_refit = dict(find_refit, value=pipe["find_refit"]["value"],
+                          ms_per_step=pipe["find_refit"]["ms_per_step"],
+                          hbm_180=pipe["find_refit"]["hbm_180"],
+                          serial=dict(value=fr_value, ms_per_step=fr_ms,
+                                      hbm_180=find_refit["hbm_180"]))
+    line = dict(metric=METRIC, value=head_value, unit=UNIT, n_gpus=world, steps=args.steps,
+                warmup=args.warmup, ms_per_step=head_ms, higher_is_better=True,
                 scaling="weak", vs_baseline=None, dtype="f32 (f64 timestamps and gradient sums)",
                 data="synthetic",
-                config=dict(cfg, l2="flushed before every timed step (256 MB write)",
+                config=dict(head_cfg, l2="flushed before every timed step (256 MB write)",
                             tuning=dict(tuning, chosen=how),
-                            parallelism=f"replicas x{world}, one independent event per GPU",
+                            parallelism=f"replicas x{world}, independent frames per GPU",
                             launch="one CUDA graph per step" if args.graph else "stream launches"),
+                serial=serial, pipeline=pipe and {k: v for k, v in pipe.items()
+                                                  if k not in ("e2e", "find_refit")},
                 tracks_per_s=aggregate(total_ms, nt * args.steps, dist, dev)[2],
                 n_tracks=nt, n_assigned=na, n_tracklets=ntl,
                 refit_fwd_ms=t_fwd, refit_fwd_nosave_ms=t_fwd_nosave, adjoint_ms=t_bwd,
@@ -865,11 +913,170 @@ def run_ours(args):
                 gpu_launches=launches,
                 graph_replay=graph_replay, track_quality=quality, merge_stage=merge,
                 compression=compression,
-                clocks=clk, e2e=e2e, cpu_baseline=cpu)
+                clocks=clk, e2e=head_e2e, cpu_baseline=cpu)
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
+
+
+# ------------------------------------------------------ frames in flight
+def pipelined(args, torch, dist, dev, flush, stream0, ctxs, barrier):
+    """Throughput with one frame per context in flight on its own stream.
+    ctxs: dicts with ev, seed, stream, tr (a Tracker on that stream), cl
+    (device inputs). Returns the timed step (load, find, refit with
+    checkpoints, adjoint), its graph replay, find + refit, and the end to
+    end through host buffers."""
+    import ctypes as C
+    from paper_1811_11481_b300.binding import TPC_GRAD_CALIB_SIZE
+    P = lambda t: C.c_void_p(t.data_ptr())
+    for c in ctxs:
+        n = c["ev"].n
+        cap = n // 10 + 1
+        f = lambda *sh, **kw: torch.empty(*sh, device=dev, **kw)
+        c["out"] = dict(params=f(cap, 5), cov=f(cap, 15), x=f(cap), chi2=f(cap),
+                        ndf=f(cap, dtype=torch.int32), status=f(cap, dtype=torch.int32),
+                        rej=f(n + 1, dtype=torch.uint8))
+        c["ones"] = torch.ones(cap, device=dev)
+        c["gy"], c["gz"] = f(n + 1), f(n + 1)
+        c["gc"] = f(TPC_GRAD_CALIB_SIZE, dtype=torch.float64)
+
+    def issue(c, save=True, backward=True):
+        tr, o = c["tr"], c["out"]
+        L, h = tr.L, tr.h
+
+        def ck(st, what):
+            if st != 0:
+                raise RuntimeError(f"{what}: status {st}: {L.tpc_last_error(h).decode()}")
+        tr.load(c["cl"])
+        ck(L.tpc_find_tracks_async(h), "find")
+        ck(L.tpc_refit(h, int(save), P(o["params"]), P(o["cov"]), P(o["x"]), P(o["chi2"]),
+                       P(o["ndf"]), P(o["status"]), P(o["rej"])), "refit")
+        if backward:
+            ck(L.tpc_refit_backward(h, P(c["ones"]), P(c["gy"]), P(c["gz"]), P(c["gc"])),
+               "backward")
+
+    def timed(run_one, steps):
+        evs = []
+        for _ in range(steps):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream0)
+            for c in ctxs[1:]:
+                c["stream"].wait_event(e0)
+            for c in ctxs:
+                run_one(c)
+            for c in ctxs[1:]:
+                d = torch.cuda.Event()
+                d.record(c["stream"])
+                stream0.wait_event(d)
+            e1.record(stream0)
+            evs.append((e0, e1))
+        barrier()
+        return float(np.sum([a.elapsed_time(b) for a, b in evs]))
+
+    units = sum(c["ev"].n for c in ctxs)
+    for _ in range(max(3, args.warmup)):
+        for c in ctxs:
+            issue(c)
+    barrier()
+    ms = timed(issue, args.steps)
+    tot, _, value = aggregate(ms, units * args.steps, dist, dev)
+    res = dict(value=value, unit=UNIT, ms_per_step=tot / args.steps, frames=len(ctxs),
+               seeds=[c["seed"] for c in ctxs], clusters_per_step=units,
+               note="one frame per context in flight, each context on its own CUDA stream; "
+                    "a step is one full pass (load, find, refit with checkpoints, adjoint) of "
+                    "every frame; L2 flushed before each step")
+    # the same as one captured graph per context
+    for c in ctxs:
+        c["stream"].synchronize()
+        c["tr"].graph_begin()
+        issue(c)
+        c["tr"].graph_end()
+    barrier()
+    g_ms = timed(lambda c: c["tr"].graph_launch(), args.steps)
+    g_tot, _, g_value = aggregate(g_ms, units * args.steps, dist, dev)
+    res["graph_replay"] = dict(value=g_value, unit=UNIT, ms_per_step=g_tot / args.steps,
+                               steps=args.steps, note="one CUDA graph per context and step")
+    # find + refit (no checkpoints, no adjoint)
+    fr_ms = timed(lambda c: issue(c, save=False, backward=False), args.steps)
+    fr_tot, _, fr_value = aggregate(fr_ms, units * args.steps, dist, dev)
+    fr_s = fr_tot / args.steps / 1000.0
+    peak = load_peaks()["hbm_gbs"]
+    res["find_refit"] = dict(value=fr_value, ms_per_step=fr_tot / args.steps,
+                             hbm_180=dict(bytes_per_cluster=180,
+                                          achieved=180 * units / fr_s / 1e9, unit="GB/s",
+                                          peak=peak, frac=180 * units / fr_s / 1e9 / peak,
+                                          frac_of_nominal_8tbs=180 * units / fr_s / 1e9 / 8000.0))
+    # end to end: each context copies its next frame from pinned host memory
+    # on its own copy stream into one of two device buffers while the
+    # current one runs, and copies the track parameters and chi2 back
+    res["e2e"] = None
+    if not args.no_e2e:
+        h2d = d2h = 0
+        for c in ctxs:
+            c["host"] = {k: v.cpu().pin_memory() for k, v in c["cl"].items()
+                         if hasattr(v, "cpu") and v is not None}
+            cap = c["out"]["chi2"].numel()
+            c["res_h"] = torch.empty(cap * 6, dtype=torch.float32).pin_memory()
+            c["bufs"] = [c["cl"], {k: (torch.empty_like(v) if hasattr(v, "copy_") else v)
+                                   for k, v in c["cl"].items()}]
+            c["cstream"] = torch.cuda.Stream()
+            c["ready"] = [torch.cuda.Event(), torch.cuda.Event()]
+            c["free"] = [torch.cuda.Event(), torch.cuda.Event()]
+            h2d += sum(v.numel() * v.element_size() for v in c["host"].values())
+            d2h += c["res_h"].numel() * 4
+
+        def put(c, i):
+            with torch.cuda.stream(c["cstream"]):
+                c["cstream"].wait_event(c["free"][i % 2])
+                for k, v in c["host"].items():
+                    c["bufs"][i % 2][k].copy_(v, non_blocking=True)
+                c["ready"][i % 2].record(c["cstream"])
+
+        def run(c, i):
+            s = c["stream"]
+            s.wait_event(c["ready"][i % 2])
+            c["cl_saved"] = c["cl"]
+            c["cl"] = c["bufs"][i % 2]
+            issue(c)
+            c["cl"] = c["cl_saved"]
+            c["free"][i % 2].record(s)
+            cap = c["out"]["chi2"].numel()
+            with torch.cuda.stream(s):
+                c["res_h"][:cap * 5].view(cap, 5).copy_(c["out"]["params"], non_blocking=True)
+                c["res_h"][cap * 5:].copy_(c["out"]["chi2"], non_blocking=True)
+
+        barrier()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream0)
+        for c in ctxs:
+            c["stream"].wait_event(a)
+            c["cstream"].wait_event(a)
+            for f in c["free"]:
+                f.record(c["stream"])
+            put(c, 0)
+        for i in range(args.steps):
+            for c in ctxs:
+                if i + 1 < args.steps:
+                    put(c, i + 1)
+                run(c, i)
+        for c in ctxs[1:]:
+            d = torch.cuda.Event()
+            d.record(c["stream"])
+            stream0.wait_event(d)
+        b.record(stream0)
+        barrier()
+        _, _, e_value = aggregate(a.elapsed_time(b), units * args.steps, dist, dev)
+        res["e2e"] = dict(value=e_value, unit=UNIT, h2d_bytes_per_step=int(h2d),
+                          d2h_bytes_per_step=int(d2h),
+                          note="every step each context's frame is copied from pinned host "
+                               "memory on that context's copy stream into one of two device "
+                               "buffers (overlapping its previous step and the other "
+                               "contexts), run, and its track parameters and chi2 copied back")
+    return res
 
 
 # ---------------------------------------------------------- CPU baseline
