@@ -459,13 +459,13 @@ tpc_status tpc_profile_read(tpc_ctx* ctx, tpc_kernel_stat* out, int32_t cap, int
  *   tracklet_per_sm     resident tracklet blocks per SM (0 .. 64); 0 = as many
  *                       as fit
  *   tracklet_regs       register cap of the tracklet kernel: 0 = the compiler's
- *                       choice (~170 per thread), 128 = at most 128 (twice the
- *                       resident threads per SM)
+ *                       choice (128 per thread), 96 = at most 96 (a quarter
+ *                       more resident threads per SM, blocks of 64 or 128)
  * tpc_set_tuning validates (TPC_ERR_ARG) and applies from the next
  * tpc_load_clusters (grid) or tpc_find_tracks (tracklet kernel);
  * TPC_ERR_STATE while capturing. tpc_autotune searches one parameter at a
  * time, in that order, over grid_tau {0.5, 1, 2, 4}, grid_ny_max {8, 16, 32},
- * tracklet_block {64, 128, 256}, tracklet_regs {0, 128}, tracklet_per_sm
+ * tracklet_block {64, 128, 256}, tracklet_regs {0, 96}, tracklet_per_sm
  * {0, 1, 2, 4}, on the loaded
  * batch: each candidate runs load + find (grid parameters) or find (tracklet
  * parameters) `repeats` times (1 .. 50; < 1 means 3) after one untimed run,

@@ -229,6 +229,10 @@ tpc_status ensure_tracklets(tpc_ctx* ctx) {
     CK(alloc(b.starts, cap));
     CK(alloc(b.seed_end, cap));
     CK(alloc(b.range, cap));
+    CK(alloc(b.seed_st, cap * 24));
+    CK(alloc(b.tl_pred, cap));
+    CK(alloc(b.tl_order, cap));
+    if (!b.tl_hist) CK(alloc(b.tl_hist, 512));
     CK(alloc(b.tkey, cap));
     CK(alloc(b.tseg, cap));
     CK(alloc(b.delta_id, cap));
@@ -387,7 +391,7 @@ void tpc_destroy(tpc_ctx* ctx) {
                   ctx->fb.gorig, ctx->fb.gseg, ctx->fb.bin_start, ctx->fb.big_list, ctx->fb.mid_list, ctx->fb.list_counts,
                   ctx->fb.n_bins, ctx->fb.es_dims, ctx->fb.queue, ctx->fb.up, ctx->fb.dn,
                   ctx->fb.upc, ctx->fb.dnc, ctx->fb.blk_a, ctx->fb.blk_b, ctx->fb.off_a,
-                  ctx->fb.off_b, ctx->fb.starts, ctx->fb.seed_end, ctx->fb.range, ctx->fb.tkey, ctx->fb.tseg, ctx->fb.delta_id, ctx->fb.delta_o, ctx->fb.grp_list, ctx->fb.grp_count, ctx->fb.nh, ctx->fb.hits, ctx->fb.that,
+                  ctx->fb.off_b, ctx->fb.starts, ctx->fb.seed_end, ctx->fb.range, ctx->fb.seed_st, ctx->fb.tl_pred, ctx->fb.tl_order, ctx->fb.tl_hist, ctx->fb.tkey, ctx->fb.tseg, ctx->fb.delta_id, ctx->fb.delta_o, ctx->fb.grp_list, ctx->fb.grp_count, ctx->fb.nh, ctx->fb.hits, ctx->fb.that,
                   ctx->fb.weight, ctx->fb.nkeep, ctx->tb.track_start, ctx->tb.cluster_idx,
                   ctx->tb.asg_track, ctx->tb.t_coll, ctx->tb.start_hit, ctx->tb.yc, ctx->tb.zc,
                   ctx->tb.meta, ctx->rb.seed, ctx->rb.order, ctx->rb.slot, ctx->rb.wlen, ctx->rb.wbase, ctx->rb.len_hist,
@@ -1058,7 +1062,7 @@ tpc_status tpc_set_tuning(tpc_ctx* ctx, const tpc_tuning* in) {
   if (ctx->capturing) return fail(ctx, TPC_ERR_STATE, "tuning changes during graph capture");
   if (!(in->grid_tau >= 0.25f && in->grid_tau <= 16.0f) || in->grid_ny_max < 1 ||
       in->grid_ny_max > 64 || !valid_block(in->tracklet_block) || in->tracklet_per_sm < 0 ||
-      in->tracklet_per_sm > 64 || (in->tracklet_regs != 0 && in->tracklet_regs != 128))
+      in->tracklet_per_sm > 64 || (in->tracklet_regs != 0 && in->tracklet_regs != 96))
     return fail(ctx, TPC_ERR_ARG, "tuning out of range");
   ctx->tune = *in;
   apply_tuning(ctx);
@@ -1120,7 +1124,7 @@ tpc_status tpc_autotune(tpc_ctx* ctx, int32_t repeats, tpc_tuning* out) {
   const float taus[] = {0.5f, 1.0f, 2.0f, 4.0f};
   const int nys[] = {8, 16, 32};
   const int blocks[] = {64, 128, 256};
-  const int regs[] = {0, 128};
+  const int regs[] = {0, 96};
   const int pers[] = {0, 1, 2, 4};
   tpc_tuning best = ctx->tune;
   auto trial = [&](tpc_tuning cand, int which, float* ms) -> tpc_status {

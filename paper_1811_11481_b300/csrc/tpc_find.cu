@@ -777,57 +777,41 @@ __device__ __forceinline__ void calibrate_follow(const Geo& g, const Cal& c, boo
   }
 }
 
-enum : int { kSeed1 = 0, kSeed2 = 1, kOut = 2, kIn = 3, kDone = 4 };
+enum : int { kOut = 2, kIn = 3, kDone = 4 };
 
-// The measurement of one tracklet step. In the seed phases it is the chain
-// hit h, taken without a cut (in seeding coordinates in phase kSeed1,
-// calibrated in kSeed2). When following, it is the nearest cluster of row r
+// The measurement of one following step: the nearest cluster of row r
 // (calibrated frame) by the normalised distance inside the pick-up cut, ties
 // to the lowest input index. Returns the grid position or -1, and the
-// calibrated coordinates. Both cases run the same candidate loop, flattened
-// over up to four z rows of bins, so that the lanes of a warp stay together
-// whatever phase their tracklets are in.
+// calibrated coordinates. The candidate loop is flattened over up to four z
+// rows of bins.
 __device__ int step_measurement(const Geo& g, const Cal& c, const Params& p, const GridDims& gd,
                                 const Bins& BB, const Grid& G, int ev, int sec, int r,
                                 const float st[5], const float C[15], float shift, bool spl_on,
-                                float dymax, float dzmax, int phase, int h, float& ycb,
-                                float& zcb) {
-  const bool seed = phase <= kSeed2;
+                                float dymax, float dzmax, float& ycb, float& zcb) {
   int side = ev * 2 + (sec >= 18 ? 1 : 0);
   float sig2 = p.sigma * p.sigma;
   float vy = C[0] + sig2, vz = C[2] + sig2;
   float ivy = Fast::rcp(vy), ivz = Fast::rcp(vz);
-  int iz0 = 0, iz1 = 0, iy0 = 0, iy1 = 0;
-  if (!seed) {
-    // window half-widths bound the search box only (the cut below decides):
-    // a fast square root is enough
-    float qy = p.chi2_pick * vy, qz = p.chi2_pick * vz;
-    float wy = qy * rsqrtf(qy), wz = qz * rsqrtf(qz);
-    float eps = 0.01f + 1.0e-6f * fabsf(shift);
-    float yp = st[0], zp = st[1] - shift;
-    Box B = make_box(g, gd, G.zr, BB, r, side, yp - wy - dymax - eps, yp + wy + dymax + eps,
-                     zp - wz - dzmax - eps, zp + wz + dzmax + eps);
-    iz0 = B.iz0;
-    iz1 = B.iz1;
-    iy0 = B.iy0;
-    iy1 = B.iy1;
-  }
+  // window half-widths bound the search box only (the cut below decides):
+  // a fast square root is enough
+  float qy = p.chi2_pick * vy, qz = p.chi2_pick * vz;
+  float wy = qy * rsqrtf(qy), wz = qz * rsqrtf(qz);
+  float eps = 0.01f + 1.0e-6f * fabsf(shift);
+  float yp = st[0], zp = st[1] - shift;
+  Box B = make_box(g, gd, G.zr, BB, r, side, yp - wy - dymax - eps, yp + wy + dymax + eps,
+                   zp - wz - dzmax - eps, zp + wz + dzmax + eps);
   const uint32_t* __restrict__ bs = G.bin_start + BB.base + (size_t)r * (BB.nb + 1);
   int best = -1;
   float bd = 0.0f;
-  for (int izb = iz0; izb <= iz1; izb += 4) {
+  for (int izb = B.iz0; izb <= B.iz1; izb += 4) {
     // bin offsets of up to four z rows of the box, loaded together
     uint32_t lo[4], hi[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       int iz = izb + q;
-      bool in = !seed && iz <= iz1;
-      lo[q] = in ? __ldg(bs + iz * BB.ny + iy0) : 0u;
-      hi[q] = in ? __ldg(bs + iz * BB.ny + iy1 + 1) : 0u;
-    }
-    if (seed) {
-      lo[0] = (uint32_t)h;
-      hi[0] = (uint32_t)h + 1u;
+      bool in = iz <= B.iz1;
+      lo[q] = in ? __ldg(bs + iz * BB.ny + B.iy0) : 0u;
+      hi[q] = in ? __ldg(bs + iz * BB.ny + B.iy1 + 1) : 0u;
     }
     const uint32_t c0 = hi[0] - lo[0], c1 = c0 + (hi[1] - lo[1]), c2 = c1 + (hi[2] - lo[2]);
     const uint32_t total = c2 + (hi[3] - lo[3]);
@@ -837,14 +821,8 @@ __device__ int step_measurement(const Geo& g, const Cal& c, const Params& p, con
                  : k < c2 ? lo[2] + (k - c1)
                           : lo[3] + (k - c2);
       float2 yz = __ldg(G.gyz + j);
-      float yc = yz.x, zc = yz.y;
-      if (phase != kSeed1) calibrate_follow(g, c, spl_on, sec, r, yz.x, yz.y, shift, yc, zc);
-      if (seed) {
-        best = (int)j;
-        ycb = yc;
-        zcb = zc;
-        continue;
-      }
+      float yc, zc;
+      calibrate_follow(g, c, spl_on, sec, r, yz.x, yz.y, shift, yc, zc);
       float ry = yc - st[0];
       float rz = zc - st[1];
       float d2 = Fast::fma(rz * rz, ivz, (ry * ry) * ivy);
@@ -862,102 +840,41 @@ __device__ int step_measurement(const Geo& g, const Cal& c, const Params& p, con
   return best;
 }
 
-// Persistent tracklet constructor, written as a step machine: every
-// iteration of the loop transports the state to the next row and updates it
-// with either the next seed hit or the picked cluster, so the threads of a
-// warp execute the same instructions whatever phase their tracklet is in;
-// a thread whose tracklet ends takes the next start hit from a queue, so the
-// lanes of a warp stay busy while work is left.
-//   phase 0: seed fit in seeding coordinates (chain hits h0 .. hl)
-//   phase 1: seed fit in calibrated coordinates (after the collision time)
-//   phase 2: outward following from the seed end
-//   phase 3: inward following from the outermost pick down to row 0
-// kCap: the launch bound asks for 512 resident threads per SM, which holds
-// the kernel to 128 registers per thread (no spills): 16 warps per SM instead
-// of 8-12, for the workloads with more tracklets than resident threads.
-// Without it (a minimum of 0 blocks: no occupancy target) the compiler
-// takes ~170 registers, which keeps a single long tracklet a little faster.
-template <int BS, bool kCap>
-__global__ void __launch_bounds__(BS, kCap ? 512 / BS : 0) k_tracklets(Geo g, Cal c, Params p, GridDims gd, Grid G,
-                                                  const uint2* es_dims, int mode,
-                                                  const int32_t* upc,
-                                                  const uint32_t* gseg, const uint32_t* starts,
-                                                  const uint32_t* seed_end, const uint32_t* cnt,
-                                                  int32_t* nh_out, int32_t* hits,
-                                                  uint32_t* range_out, double* that_out,
-                                                  uint32_t* queue) {
+// Tracklet constructor, part 1: the seed of every start hit, one thread
+// each. The chain hits h0 .. hl are fitted in seeding coordinates; in
+// continuous readout the closest approach to the beam line gives the
+// collision time (Sec. 4) and the seed is fitted again in calibrated
+// coordinates (also with a distortion map in event mode). Each hit is one
+// transport and one update in the arithmetic of the following, so a seed
+// gets the same bits as if the following kernel had fitted it. Writes the
+// seed state at the seed's last hit, the collision time, the final outputs of
+// seeds that fail, and the number of rows the seed's helix can still cross
+// inside the sector (outward to its exit, then inward to row 0), counted
+// into the histogram that orders the following longest first.
+constexpr int kSeedStride = 24;   // floats per seed: p[5], C[15], x, ok flag, padding
+constexpr int kLenBuckets = 512;  // predicted steps, capped
+__global__ void k_tl_seed(Geo g, Cal c, Params p, Grid G, int mode, const int32_t* upc,
+                          const uint32_t* gseg, const uint32_t* starts,
+                          const uint32_t* seed_end, const uint32_t* cnt, float* seed_st,
+                          uint32_t* pred, uint32_t* hist, int32_t* nh_out, double* that_out,
+                          uint32_t* range_out) {
   const int ntl = (int)cnt[kCntStart];
   const float sig2 = p.sigma * p.sigma;
   const bool spl_on = c.spl_bound[2] > 0.0f;
-  const float dymax = spl_on ? c.spl_bound[0] : 0.0f;
-  const float dzmax = spl_on ? c.spl_bound[1] : 0.0f;
-  int t = -1;
-  int32_t* H = nullptr;
-  int h0 = 0, r0 = 0, ev = 0, sec = 0, hl = 0, rl = 0;
-  Bins BB{0u, 1, 1, 1};
-  float2 yz0 = make_float2(0.f, 0.f), yzl = yz0;
-  float st[5], C[15], x = 0.0f;
-  double that = 0.0;
-  float shift = 0.0f;
-  float bst[5], bC[15], bx = 0.0f;
-  int phase = kDone, h = 0, r = 0, rlast = 0, miss = 0, nh = 0;
-  bool failed = false;
-  int rlo = 0;
-  while (true) {
-    if (phase == kDone) {
-      if (t >= 0) {
-        // the current tracklet: hit count, collision time and the rows
-        // [rlo, rlast] its inward pass visited (hits[] holds those rows)
-        nh_out[t] = failed ? -1 : nh;
-        that_out[t] = failed ? 0.0 : that;
-        range_out[t] = failed ? 1u : ((uint32_t)rlo | ((uint32_t)rlast << 16));
-      }
-      t = (int)atomicAdd(queue, 1u);
-      if (t >= ntl) break;
-      H = hits + (size_t)t * g.n_rows;
-      h0 = (int)starts[t];
-      hl = (int)seed_end[t];
-      int seg0 = (int)gseg[h0];
-      rl = (int)gseg[hl] % g.n_rows;
-      yz0 = G.gyz[h0];
-      yzl = G.gyz[hl];
-      r0 = seg0 % g.n_rows;
-      int es = seg0 / g.n_rows;
-      ev = es / kNS;
-      sec = es % kNS;
-      BB = es_bins(es_dims, es);
-      seed_two_points(st, C, x, p.c0t, g.rx[r0], yz0.x, yz0.y, g.rx[rl], yzl.x, yzl.y);
-      that = 0.0;
-      shift = 0.0f;
-      bx = x;
-      phase = kSeed1;
-      h = h0;
-      r = r0;
-      rlast = rl;
-      rlo = rl + 1;
-      miss = 0;
-      nh = 0;
-      failed = false;
-    }
-    bool ok = propagate<Fast>(g.kB, p.s_max, st, C, x, g.rx[r]);
-    bool have = false;
-    float my = 0.0f, mz = 0.0f;
-    int j = -1;
-    if (ok) {
-      j = step_measurement(g, c, p, gd, BB, G, ev, sec, r, st, C, shift, spl_on, dymax, dzmax,
-                           phase, h, my, mz);
-      have = j >= 0;
-      if (have) apply_update<Fast>(st, C, innovation<Fast>(st, C, my, mz, sig2, sig2));
-    }
-    bool start_in = false;
-    if (phase == kSeed1 || phase == kSeed2) {
-      if (!ok) {
-        failed = true;
-        phase = kDone;
-      } else if (h != hl) {
-        h = upc[h];
-        ++r;
-      } else if (phase == kSeed1 && (mode == 1 || spl_on)) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ntl; t += gridDim.x * blockDim.x) {
+    const int h0 = (int)starts[t], hl = (int)seed_end[t];
+    const int seg0 = (int)gseg[h0];
+    const int rl = (int)gseg[hl] % g.n_rows, r0 = seg0 % g.n_rows;
+    const int sec = (seg0 / g.n_rows) % kNS;
+    const float2 yz0 = G.gyz[h0], yzl = G.gyz[hl];
+    float st[5], C[15], x;
+    seed_two_points(st, C, x, p.c0t, g.rx[r0], yz0.x, yz0.y, g.rx[rl], yzl.x, yzl.y);
+    double that = 0.0;
+    float shift = 0.0f;
+    bool ok = true;
+    const bool second = mode == 1 || spl_on;
+    for (int pass = 0; ok && pass < (second ? 2 : 1); ++pass) {
+      if (pass == 1) {
         if (mode == 1) {
           float zd = dca_z(g.kB, st, x);
           double sg = sec < 18 ? 1.0 : -1.0;
@@ -968,34 +885,198 @@ __global__ void __launch_bounds__(BS, kCap ? 512 / BS : 0) k_tracklets(Geo g, Ca
         calibrate_follow(g, c, spl_on, sec, r0, yz0.x, yz0.y, shift, y0, z0);
         calibrate_follow(g, c, spl_on, sec, rl, yzl.x, yzl.y, shift, y1, z1);
         seed_two_points(st, C, x, p.c0t, g.rx[r0], y0, z0, g.rx[rl], y1, z1);
-        phase = kSeed2;
-        h = h0;
-        r = r0;
-      } else {
-        // seed fitted (in event mode without a distortion map the calibrated
-        // coordinates equal the seeding ones, so the calibrated refit of the
-        // seed would repeat the first fit operation for operation)
-#pragma unroll
-        for (int i = 0; i < 5; ++i) bst[i] = st[i];
-#pragma unroll
-        for (int i = 0; i < 15; ++i) bC[i] = C[i];
-        bx = x;
-        rlast = rl;
-        miss = 0;
-        phase = kOut;
-        r = rl + 1;
-        if (r >= g.n_rows) start_in = true;
       }
-    } else if (phase == kOut) {
+      int h = h0, r = r0;
+      while (true) {
+        if (!propagate<Fast>(g.kB, p.s_max, st, C, x, g.rx[r])) {
+          ok = false;
+          break;
+        }
+        float2 yz = __ldg(G.gyz + h);
+        float my = yz.x, mz = yz.y;
+        if (pass == 1) calibrate_follow(g, c, spl_on, sec, r, yz.x, yz.y, shift, my, mz);
+        apply_update<Fast>(st, C, innovation<Fast>(st, C, my, mz, sig2, sig2));
+        if (h == hl) break;
+        h = upc[h];
+        ++r;
+      }
+    }
+    uint32_t len = 0;
+    if (!ok) {
+      nh_out[t] = -1;
+      that_out[t] = 0.0;
+      range_out[t] = 1u;
+      seed_st[(size_t)t * kSeedStride + 21] = 0.0f;
+    } else {
+      float* o = seed_st + (size_t)t * kSeedStride;
+#pragma unroll
+      for (int i = 0; i < 5; ++i) o[i] = st[i];
+#pragma unroll
+      for (int i = 0; i < 15; ++i) o[5 + i] = C[i];
+      o[20] = x;
+      o[21] = 1.0f;
+      that_out[t] = that;
+      // rows the seed's helix crosses inside the sector with |sin(phi)| below
+      // its limit: outward from the seed end, then inward from there
+      const float kap = g.kB * st[4];
+      const float c1 = Fast::sqrt(Fast::fma(-st[2], st[2], 1.0f));
+      auto inside = [&](int rr) {
+        float xr = g.rx[rr], dx = xr - x;
+        float s2 = Fast::fma(-kap, dx, st[2]);
+        if (!(fabsf(s2) < p.s_max)) return false;
+        float c2 = Fast::sqrt(Fast::fma(-s2, s2, 1.0f));
+        float yr = Fast::fma(dx, Fast::div(st[2] + s2, c1 + c2), st[0]);
+        return fabsf(yr) <= Fast::fma(xr, g.tan_half, 2.0f);
+      };
+      // (in steps of four rows: an ordering key needs no finer count)
+      int rend = rl;
+      while (rend + 4 < g.n_rows && inside(rend + 4)) rend += 4;
+      int rin = rend;
+      while (rin - 4 >= 0 && inside(rin - 4)) rin -= 4;
+      len = (uint32_t)((rend - rl) + (rend - rin) + 2);
+    }
+    if (len >= (uint32_t)kLenBuckets) len = kLenBuckets - 1;
+    pred[t] = len;
+    atomicAdd(&hist[kLenBuckets - 1 - len], 1u);
+  }
+}
+
+// Following order, longest predicted first: bucket offsets of the histogram
+// (one block), then each tracklet's place (its position inside a bucket is
+// arbitrary; every tracklet's result is independent of the order).
+__global__ void k_tl_order_scan(uint32_t* hist) {
+  __shared__ uint32_t tot;
+  uint32_t v = threadIdx.x < kLenBuckets ? hist[threadIdx.x] : 0u;
+  uint32_t e = block_excl_scan(v, &tot);
+  if (threadIdx.x < kLenBuckets) hist[threadIdx.x] = e;
+}
+__global__ void k_tl_order(const uint32_t* cnt, const uint32_t* pred, uint32_t* cursor,
+                           uint32_t* order) {
+  const int ntl = (int)cnt[kCntStart];
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ntl; t += gridDim.x * blockDim.x)
+    order[atomicAdd(&cursor[kLenBuckets - 1 - pred[t]], 1u)] = (uint32_t)t;
+}
+
+// Tracklet constructor, part 2: the following, as a persistent step machine.
+// Every iteration of the loop transports the state to the next row and
+// updates it with the picked cluster, so the threads of a warp execute the
+// same instructions whatever phase their tracklet is in; a thread whose
+// tracklet ends takes the next one from a queue in the order above, so the
+// lanes of a warp stay busy while work is left and the long tracklets are not
+// the last to start.
+//   phase 2: outward following from the seed end
+//   phase 3: inward following from the outermost pick down to row 0
+// kCap: the launch bound asks for 640 resident threads per SM (blocks of 64
+// or 128), which holds the kernel to 96 registers per thread (no spills, the
+// best state being in shared memory): 20 warps per SM instead of 16, for the
+// workloads with more tracklets than resident threads. Without it (a minimum
+// of 0 blocks: no occupancy target) the compiler takes 128.
+template <int BS, bool kCap>
+__global__ void __launch_bounds__(BS, kCap ? 640 / BS : 0) k_tracklets(Geo g, Cal c, Params p, GridDims gd, Grid G,
+                                                  const uint2* es_dims, int mode,
+                                                  const uint32_t* gseg, const uint32_t* starts,
+                                                  const uint32_t* seed_end, const uint32_t* cnt,
+                                                  const float* seed_st, const uint32_t* order,
+                                                  int32_t* nh_out, int32_t* hits,
+                                                  uint32_t* range_out, const double* that_in,
+                                                  uint32_t* queue) {
+  const int ntl = (int)cnt[kCntStart];
+  const float sig2 = p.sigma * p.sigma;
+  const bool spl_on = c.spl_bound[2] > 0.0f;
+  const float dymax = spl_on ? c.spl_bound[0] : 0.0f;
+  const float dzmax = spl_on ? c.spl_bound[1] : 0.0f;
+  // the state at the outermost pick (the inward pass starts from it), one
+  // column per thread in shared memory: it is written on every outward pick
+  // and read once, and keeping it out of the registers lets more warps stay
+  // resident
+  __shared__ float s_best[21][BS];
+  float* bst = &s_best[0][threadIdx.x];  // element i at bst[i * BS]
+  int t = -1;
+  int32_t* H = nullptr;
+  int ev = 0, sec = 0;
+  Bins BB{0u, 1, 1, 1};
+  float st[5], C[15], x = 0.0f;
+  float shift = 0.0f;
+  int phase = kDone, r = 0, rlast = 0, miss = 0, nh = 0;
+  int rlo = 0;
+  while (true) {
+    if (phase == kDone) {
+      if (t >= 0) {
+        // the current tracklet: hit count and the rows [rlo, rlast] its
+        // inward pass visited (hits[] holds those rows); its collision time
+        // was written with the seed
+        nh_out[t] = nh;
+        range_out[t] = (uint32_t)rlo | ((uint32_t)rlast << 16);
+      }
+      const int q = (int)atomicAdd(queue, 1u);
+      if (q >= ntl) break;
+      t = (int)order[q];
+      const int h0 = (int)starts[t];
+      const int seg0 = (int)gseg[h0];
+      const int rl = (int)gseg[seed_end[t]] % g.n_rows;
+      const float* so = seed_st + (size_t)t * kSeedStride;
+      if (so[21] == 0.0f) {
+        // a failed seed: its outputs are written already
+        t = -1;
+        continue;
+      }
+      const double that = that_in[t];
+      H = hits + (size_t)t * g.n_rows;
+      int es = seg0 / g.n_rows;
+      ev = es / kNS;
+      sec = es % kNS;
+      BB = es_bins(es_dims, es);
+#pragma unroll
+      for (int i = 0; i < 5; ++i) st[i] = so[i];
+#pragma unroll
+      for (int i = 0; i < 15; ++i) C[i] = so[5 + i];
+      x = so[20];
+      shift = 0.0f;
+      if (mode == 1) {
+        double sg = sec < 18 ? 1.0 : -1.0;
+        shift = (float)(sg * c.vdrift * (that - c.tf_start));
+      }
+      rlast = rl;
+      rlo = rl + 1;
+      miss = 0;
+      nh = 0;
+      phase = kOut;
+      r = rl + 1;
+      if (r >= g.n_rows) {
+        // nothing outward: the inward pass starts from the seed
+#pragma unroll
+        for (int i = 0; i < 15; ++i) C[i] = C[i] * p.inward_cov_scale;
+        r = rlast;
+        phase = kIn;
+      } else {
+#pragma unroll
+        for (int i = 0; i < 5; ++i) bst[i * BS] = st[i];
+#pragma unroll
+        for (int i = 0; i < 15; ++i) bst[(5 + i) * BS] = C[i];
+        bst[20 * BS] = x;
+      }
+    }
+    bool ok = propagate<Fast>(g.kB, p.s_max, st, C, x, g.rx[r]);
+    bool have = false;
+    float my = 0.0f, mz = 0.0f;
+    int j = -1;
+    if (ok) {
+      j = step_measurement(g, c, p, gd, BB, G, ev, sec, r, st, C, shift, spl_on, dymax, dzmax,
+                           my, mz);
+      have = j >= 0;
+      if (have) apply_update<Fast>(st, C, innovation<Fast>(st, C, my, mz, sig2, sig2));
+    }
+    bool start_in = false;
+    if (phase == kOut) {
       if (!ok) {
         start_in = true;
       } else {
         if (have) {
 #pragma unroll
-          for (int i = 0; i < 5; ++i) bst[i] = st[i];
+          for (int i = 0; i < 5; ++i) bst[i * BS] = st[i];
 #pragma unroll
-          for (int i = 0; i < 15; ++i) bC[i] = C[i];
-          bx = x;
+          for (int i = 0; i < 15; ++i) bst[(5 + i) * BS] = C[i];
+          bst[20 * BS] = x;
           rlast = r;
           miss = 0;
         } else if (++miss >= p.max_miss) {
@@ -1020,10 +1101,10 @@ __global__ void __launch_bounds__(BS, kCap ? 512 / BS : 0) k_tracklets(Geo g, Ca
     }
     if (start_in) {
 #pragma unroll
-      for (int i = 0; i < 5; ++i) st[i] = bst[i];
+      for (int i = 0; i < 5; ++i) st[i] = bst[i * BS];
 #pragma unroll
-      for (int i = 0; i < 15; ++i) C[i] = bC[i] * p.inward_cov_scale;
-      x = bx;
+      for (int i = 0; i < 15; ++i) C[i] = bst[(5 + i) * BS] * p.inward_cov_scale;
+      x = bst[20 * BS];
       r = rlast;
       rlo = rlast + 1;
       miss = 0;
@@ -1517,7 +1598,7 @@ cudaError_t tracklet_occupancy(int* per, int block) {
 
 int tracklet_blocks_per_sm(int block, int regs) {
   int per = 0;
-  cudaError_t e = regs == 128 ? tracklet_occupancy<true>(&per, block)
+  cudaError_t e = regs == 96 ? tracklet_occupancy<true>(&per, block)
                               : tracklet_occupancy<false>(&per, block);
   return e == cudaSuccess ? per : 0;
 }
@@ -1540,6 +1621,16 @@ void launch_find(Prof* P, const Geo& g, const Cal& c, const Params& p, const ClI
                                         (uint32_t)b.cap_tl, p.seed_max_hits, b.starts, b.seed_end));
   cudaMemsetAsync(b.weight, 0, sizeof(unsigned long long) * (size_t)(n > 0 ? n : 1), s);
   Grid G{b.gyz, b.gorig, b.bin_start, b.zr};
+  // seeds, then the following order (longest predicted first)
+  cudaMemsetAsync(b.tl_hist, 0, sizeof(uint32_t) * kLenBuckets, s);
+  TPC_LAUNCH(P, "k_tl_seed", s,
+             k_tl_seed<<<min(nblk(b.cap_tl, 128), 64 * 148), 128, 0, s>>>(
+                 g, c, p, G, cl.mode, b.upc, b.gseg, b.starts, b.seed_end, cnt, b.seed_st,
+                 b.tl_pred, b.tl_hist, b.nh, b.that, b.range));
+  TPC_LAUNCH(P, "k_tl_order_scan", s, k_tl_order_scan<<<1, kLenBuckets, 0, s>>>(b.tl_hist));
+  TPC_LAUNCH(P, "k_tl_order", s,
+             k_tl_order<<<min(nblk(b.cap_tl, kB256), 16 * 148), kB256, 0, s>>>(
+                 cnt, b.tl_pred, b.tl_hist, b.tl_order));
   // persistent grid: the tuned number of resident blocks, or fewer for a
   // small capacity
   cudaMemsetAsync(b.queue, 0, sizeof(uint32_t), s);
@@ -1549,10 +1640,10 @@ void launch_find(Prof* P, const Geo& g, const Cal& c, const Params& p, const ClI
     if (sh.tl_grid > 0 && nbk > sh.tl_grid) nbk = sh.tl_grid;                              \
     TPC_LAUNCH(P, "k_tracklets", s,                                                        \
                (k_tracklets<BS, CAP><<<nbk, BS, 0, s>>>(                                   \
-                   g, c, p, gd, G, b.es_dims, cl.mode, b.upc, b.gseg, b.starts,             \
-                   b.seed_end, cnt, b.nh, b.hits, b.range, b.that, b.queue)));             \
+                   g, c, p, gd, G, b.es_dims, cl.mode, b.gseg, b.starts, b.seed_end, cnt,   \
+                   b.seed_st, b.tl_order, b.nh, b.hits, b.range, b.that, b.queue)));       \
   }
-  const bool cap = sh.tl_regs == 128;
+  const bool cap = sh.tl_regs == 96;
   if (sh.tl_block == 64) {
     if (cap) TPC_TRACKLETS(64, true) else TPC_TRACKLETS(64, false)
   } else if (sh.tl_block == 256) {

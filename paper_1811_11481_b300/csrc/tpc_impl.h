@@ -121,6 +121,10 @@ struct FindBuf {
   uint32_t* queue;      // [1] next start hit of the persistent tracklet kernel
   uint32_t* seed_end;   // [cap_tl] last hit of each start hit's seed
   uint32_t* range;      // [cap_tl] rows lo | hi << 16 of hits[] the tracklet wrote
+  float* seed_st;       // [cap_tl * 24] seed state (p, C, x) and an ok flag per tracklet
+  uint32_t* tl_pred;    // [cap_tl] predicted following steps of each tracklet
+  uint32_t* tl_order;   // [cap_tl] tracklets in following order (longest predicted first)
+  uint32_t* tl_hist;    // [512] tracklets per predicted length, then bucket offsets
   uint32_t* tkey;       // [cap_tl] input index of the start hit
   uint32_t* tseg;       // [cap_tl] (event, sector, row) segment of the start hit
   int32_t* delta_id;    // [cap_tl] track-order shift inside large groups
@@ -282,7 +286,7 @@ void launch_load(Prof* P, const Geo& g, const Cal& c, const ClIn& cl, const Grid
 struct Shapes {
   int tl_block = 128;    // tracklet kernel threads per block (64, 128, 256)
   int tl_grid = 0;       // persistent tracklet grid (0: one block per 128 tracklets)
-  int tl_regs = 0;       // tracklet kernel register cap (0: compiler's choice, 128)
+  int tl_regs = 0;       // tracklet kernel register cap (0: compiler's choice, 96)
 };
 // Resident blocks per SM of the tracklet kernel at a block size.
 int tracklet_blocks_per_sm(int block, int regs);

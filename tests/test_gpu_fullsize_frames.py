@@ -22,7 +22,7 @@ from pipeline import RTOL, rel_err, tracker
 pytestmark = pytest.mark.gpu
 
 TUNING = dict(grid_tau=0.5, grid_ny_max=8, tracklet_block=128, tracklet_per_sm=0,
-              tracklet_regs=128)
+              tracklet_regs=96)
 
 
 def _make(name):
