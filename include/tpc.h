@@ -269,6 +269,25 @@ tpc_status tpc_set_tracks(tpc_ctx* ctx, const tpc_tracks* tracks);
 tpc_status tpc_refit(tpc_ctx* ctx, int save_for_backward, float* params, float* cov, float* x,
                      float* chi2, int32_t* ndf, int32_t* status, uint8_t* rej);
 
+/* Vertex pseudo-measurements for the refit of the current track set (not
+ * in the paper; a reading of how drift velocity and time offset become
+ * determinable: like a triggered event whose vertex is known). z_vertex:
+ * device [n_tracks], caller-owned and valid until the refits and adjoints
+ * that use it have run; entry k is the vertex z (cm) of track k, NaN for a
+ * track without one. After pass 3 of tpc_refit such a track's state is
+ * transported to the beam line (x = 0 of its frame) and updated with
+ * (y, z) = (0, z_vertex[k]) of variance sigma^2 each: chi2 and ndf include
+ * that term and params, cov and x are those at the vertex. A track whose
+ * transport to x = 0 fails (|sin(phi)| would reach s_max) keeps its state
+ * at the innermost cluster without the term. tpc_refit_backward
+ * differentiates the term too. NULL switches the vertices off; a new track
+ * set (find, tpc_set_tracks, merge) switches them off as well. Returns
+ * TPC_ERR_ARG for sigma <= 0 or a geometry with a full field, TPC_ERR_STATE
+ * without a track set or while capturing; tpc_refit_backward returns
+ * TPC_ERR_STATE when the vertices were set or cleared after the saved
+ * refit. */
+tpc_status tpc_set_vertex(tpc_ctx* ctx, const float* z_vertex, float sigma);
+
 /* Merge the context's track set, taken as sector segments (from
  * tpc_find_tracks, or given by tpc_set_tracks), into tracks across sectors
  * (Sec. 2, second phase: the segments found in the individual sectors are

@@ -104,8 +104,9 @@ def lib():
         L.orc_select.argtypes = [vp, C.c_int64, vp, vp, vp, vp, vp, vp, vp, vp,
                                  C.c_int64, C.c_int64]
         L.orc_refit.argtypes = [vp, C.c_int, C.c_int64, vp, vp, vp, vp, vp, C.c_int, vp,
-                                vp, vp, vp, vp, vp, vp]
-        L.orc_refit_grad.argtypes = [vp, C.c_int64, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+                                vp, vp, vp, vp, vp, vp, vp, C.c_double]
+        L.orc_refit_grad.argtypes = [vp, C.c_int64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp,
+                                     C.c_double]
         L.orc_propagate.restype = C.c_int
         L.orc_propagate.argtypes = [vp, vp, C.c_double, C.c_double, vp, vp, vp]
         L.orc_refit_points.restype = C.c_int
@@ -334,7 +335,10 @@ class Oracle:
         return dict(up=up, dn=dn, upc=upc, dnc=dnc, starts=starts, tracklets=tl, tracks=tr)
 
     # --- a9-a10
-    def refit(self, track_start, cluster_idx, that, prec=64, seeds=None, rej=None):
+    def refit(self, track_start, cluster_idx, that, prec=64, seeds=None, rej=None, zv=None,
+              vsigma=0.01):
+        """Three-pass refit of the tracks (CSR); zv: optional vertex z per
+        track (NaN: none) with error vsigma (cm)."""
         ts = np.ascontiguousarray(track_start, np.uint32)
         ci = np.ascontiguousarray(cluster_idx, np.uint32)
         that = np.ascontiguousarray(that, np.float64)
@@ -346,15 +350,18 @@ class Oracle:
         out = dict(params=np.empty((nt, 5)), cov=np.empty((nt, 15)), x=np.empty(nt),
                    chi2=np.empty(nt), ndf=np.empty(nt, np.int32),
                    status=np.empty(nt, np.int32))
+        zvv = None if zv is None else np.ascontiguousarray(zv, np.float64)
         lib().orc_refit(self.h, prec, nt, _p(ts), _p(ci), _p(that), _p(sd), _p(so),
                         int(frozen), _p(rj), _p(out["params"]), _p(out["cov"]), _p(out["x"]),
-                        _p(out["chi2"]), _p(out["ndf"]), _p(out["status"]))
+                        _p(out["chi2"]), _p(out["ndf"]), _p(out["status"]), _p(zvv),
+                        float(vsigma) ** 2)
         out["rej"] = rj
         out["seeds"] = so
         return out
 
     # --- a11
-    def refit_grad(self, track_start, cluster_idx, that, seeds, rej, g=None):
+    def refit_grad(self, track_start, cluster_idx, that, seeds, rej, g=None, zv=None,
+                   vsigma=0.01):
         ts = np.ascontiguousarray(track_start, np.uint32)
         ci = np.ascontiguousarray(cluster_idx, np.uint32)
         nt = ts.size - 1
@@ -364,7 +371,9 @@ class Oracle:
         gc = np.zeros(2 + N_SPLINE)
         lib().orc_refit_grad(self.h, nt, _p(ts), _p(ci), _p(np.ascontiguousarray(that, np.float64)),
                              _p(np.ascontiguousarray(seeds, np.float64)),
-                             _p(np.ascontiguousarray(rej, np.uint8)), _p(g), _p(gy), _p(gz), _p(gc))
+                             _p(np.ascontiguousarray(rej, np.uint8)), _p(g), _p(gy), _p(gz), _p(gc),
+                             _p(None if zv is None else np.ascontiguousarray(zv, np.float64)),
+                             float(vsigma) ** 2)
         return gy, gz, gc
 
     # --- Sec. 2 second phase: segment merging

@@ -1115,7 +1115,8 @@ template <class R>
 RefitOut refit_core(const Ctx& c, const std::vector<R>& x, const std::vector<R>& yc,
                     const std::vector<R>& zc, const std::vector<R>& var, const double seed[5],
                     uint8_t* rej, bool frozen, R* chi2_out,
-                    const std::vector<double>* alpha = nullptr, double* priors = nullptr) {
+                    const std::vector<double>* alpha = nullptr, double* priors = nullptr,
+                    double zv = NAN, double vvar = 0.0) {
   RefitOut o;
   std::memset(&o, 0, sizeof(o));
   size_t n = x.size();
@@ -1174,6 +1175,22 @@ RefitOut refit_core(const Ctx& c, const std::vector<R>& x, const std::vector<R>&
       chi2 = chi2 + in.chi2;
       ndf += 2;
       ++nacc;
+    }
+  }
+  // Vertex pseudo-measurement (a reading: a known vertex, as in a triggered
+  // event, fixes the absolute z that drift velocity and t0 otherwise share
+  // with every track's z0 and tan(lambda)): the state transported to the
+  // beam line, x = 0, and updated with (y, z) = (0, zv), variance vvar each;
+  // skipped when the transport fails.
+  if (!(zv != zv) && c.field.empty()) {
+    Trk<R> sv = st;
+    if (propagate<R>(c, sv, R(0.0))) {
+      Innov<R> in = innovation<R>(sv, R(0.0), R(zv), R(vvar), R(vvar));
+      if (c.joseph) apply_update_joseph<R>(sv, in, R(vvar), R(vvar));
+      else apply_update<R>(sv, in);
+      chi2 = chi2 + in.chi2;
+      ndf += 2;
+      st = sv;
     }
   }
   for (int i = 0; i < 5; ++i) o.p[i] = val(st.p[i]);
@@ -1659,10 +1676,12 @@ int64_t orc_select(void* ctx, int64_t m, const int64_t* starts, const int32_t* n
 // [nt][5] seed states at the outermost cluster; seeds_out receives the seeds
 // used. rej: [n_assigned] rejection pass per cluster (0 kept); with
 // frozen != 0 it is an input and no new decision is taken.
+// zv (may be NULL): vertex z per track (NaN: none), variance vvar.
 void orc_refit(void* ctx, int prec, int64_t nt, const uint32_t* track_start,
                const uint32_t* cluster_idx, const double* that, const double* seeds,
                double* seeds_out, int frozen, uint8_t* rej, double* params, double* cov,
-               double* xout, double* chi2, int32_t* ndf, int32_t* status) {
+               double* xout, double* chi2, int32_t* ndf, int32_t* status, const double* zv,
+               double vvar) {
   Ctx& c = *(Ctx*)ctx;
 #pragma omp parallel for schedule(dynamic, 16)
   for (int64_t k = 0; k < nt; ++k) {
@@ -1680,13 +1699,21 @@ void orc_refit(void* ctx, int prec, int64_t nt, const uint32_t* track_start,
       track_inputs<float>(c, cluster_idx + a, n, that[k], x, yc, zc, var);
       ok = seeds ? true : seed_track<float>(c, x, yc, zc, al, seed);
       if (seeds) for (int i = 0; i < 5; ++i) seed[i] = seeds[k * 5 + i];
-      if (ok) { float ch; o = refit_core<float>(c, x, yc, zc, var, seed, rj, frozen, &ch, alp); }
+      if (ok) {
+        float ch;
+        o = refit_core<float>(c, x, yc, zc, var, seed, rj, frozen, &ch, alp, nullptr,
+                              zv ? zv[k] : NAN, vvar);
+      }
     } else {
       std::vector<double> x, yc, zc, var;
       track_inputs<double>(c, cluster_idx + a, n, that[k], x, yc, zc, var);
       ok = seeds ? true : seed_track<double>(c, x, yc, zc, al, seed);
       if (seeds) for (int i = 0; i < 5; ++i) seed[i] = seeds[k * 5 + i];
-      if (ok) { double ch; o = refit_core<double>(c, x, yc, zc, var, seed, rj, frozen, &ch, alp); }
+      if (ok) {
+        double ch;
+        o = refit_core<double>(c, x, yc, zc, var, seed, rj, frozen, &ch, alp, nullptr,
+                               zv ? zv[k] : NAN, vvar);
+      }
     }
     if (!ok) o.status = 2;
     if (seeds_out) for (int i = 0; i < 5; ++i) seeds_out[k * 5 + i] = ok ? seed[i] : 0.0;
@@ -1706,7 +1733,7 @@ void orc_refit(void* ctx, int prec, int64_t nt, const uint32_t* track_start,
 void orc_refit_grad(void* ctx, int64_t nt, const uint32_t* track_start,
                     const uint32_t* cluster_idx, const double* that, const double* seeds,
                     const uint8_t* rej, const double* g, double* grad_y, double* grad_zt,
-                    double* grad_calib) {
+                    double* grad_calib, const double* zv, double vvar) {
   Ctx& c = *(Ctx*)ctx;
   // Each track's terms (its own tape, on any thread), then summed in track
   // order, so the sums do not depend on the number of threads.
@@ -1755,7 +1782,7 @@ void orc_refit_grad(void* ctx, int64_t nt, const uint32_t* track_start,
       std::vector<double> al = track_alpha(c, cluster_idx + a, n);
       Var chi2;
       RefitOut o = refit_core<Var>(c, x, yc, zc, var, seeds + k * 5, rj.data(), true, &chi2,
-                                   al.empty() ? nullptr : &al);
+                                   al.empty() ? nullptr : &al, nullptr, zv ? zv[k] : NAN, vvar);
       if (o.status != 0) {
         g_tape.clear();
         continue;

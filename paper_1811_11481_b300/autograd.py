@@ -52,29 +52,69 @@ def calib_vector(vdrift, t0, spline, device):
 
 
 def recover_calibration(tracker, theta0, steps=200, lr_spline=0.02, lr_vdrift=0.0,
-                        lr_t0=0.0, callback=None):
-    """Gradient descent (Adam) on the calibration, minimising the summed chi2
-    over ndf of the tracker's track set; returns the final theta and the loss
-    history. v_drift and t0 only move with a nonzero learning rate: without a
-    vertex constraint they are degenerate with the track z0 and tan(lambda)."""
+                        lr_t0=0.0, tikhonov=0.0, callback=None):
+    """Gradient descent (Adam, cosine-annealed) on the calibration,
+    minimising the summed chi2 over ndf of the tracker's track set plus
+    tikhonov * |spline|^2 (the minimum-norm choice along directions chi2 does
+    not see). Returns the final theta and the loss history. A block moves
+    only with a nonzero learning rate: without vertex pseudo-measurements
+    (Tracker.set_vertex) v_drift and t0 are degenerate with every track's z0
+    and tan(lambda); with them and a free spline, they still share the
+    effect of each sector's constant and z-linear spline modes."""
     cl = tracker._keep["clusters"]
     y = cl["y"]
     zt = cl["t"] if cl.get("t") is not None else cl["z"]
-    head = theta0[:2].clone().requires_grad_(True)
+    vd = theta0[0:1].clone().requires_grad_(True)
+    t0 = theta0[1:2].clone().requires_grad_(True)
     spline = theta0[2:].clone().requires_grad_(True)
-    groups = [{"params": [spline], "lr": lr_spline}]
-    if lr_vdrift > 0 or lr_t0 > 0:
-        groups.append({"params": [head], "lr": max(lr_vdrift, lr_t0)})
+    groups = [{"params": [p], "lr": lr} for p, lr in ((spline, lr_spline), (vd, lr_vdrift),
+                                                       (t0, lr_t0)) if lr > 0]
     opt = torch.optim.Adam(groups)
+    sched = torch.optim.lr_scheduler.CosineAnnealingLR(opt, steps)
     hist = []
     for it in range(steps):
         opt.zero_grad()
-        theta = torch.cat([head, spline])
+        theta = torch.cat([vd, t0, spline])
         chi2 = RefitChi2.apply(theta, y, zt, tracker)
         loss = chi2.sum() / max(1, tracker.ndf_sum)
-        loss.backward()
+        total = loss + tikhonov * (spline * spline).sum() if tikhonov > 0 else loss
+        total.backward()
         opt.step()
+        sched.step()
         hist.append(float(loss.detach()))
         if callback:
             callback(it, hist[-1])
-    return torch.cat([head, spline]).detach(), hist
+    return torch.cat([vd, t0, spline]).detach(), hist
+
+
+def fit_drift_and_t0(tracker, theta0, free=(True, True), iters=60, scale=(0.01, 0.1),
+                     bound=5.0):
+    """Drift velocity and/or t0 (free), the rest held at theta0's: bounded
+    L-BFGS (scipy's L-BFGS-B) in units of `scale` (cm/us, us) within
+    +-bound units of theta0, minimising the summed chi2 over ndf with the
+    adjoint's gradient. The bound keeps the search where the tracks' fits
+    converge: far off, failing tracks would leave the sum and lower the
+    loss. With vertex pseudo-measurements each of the two alone has a clear
+    minimum; together, the change dt0 = dv L / v^2 (which keeps the z of the
+    vertex plane) is held only by the spread of the vertices' z. Returns the
+    final theta."""
+    import numpy as np
+    from scipy.optimize import minimize
+    cl = tracker._keep["clusters"]
+    y = cl["y"]
+    zt = cl["t"] if cl.get("t") is not None else cl["z"]
+    base = theta0.detach().clone()
+    sc = np.asarray(scale, np.float64) * np.asarray(free, np.float64)
+
+    def f(u):
+        du = torch.as_tensor(u * sc, dtype=torch.float64, device=base.device)
+        head = (base[:2] + du).clone().requires_grad_(True)
+        theta = torch.cat([head, base[2:]])
+        chi2 = RefitChi2.apply(theta, y, zt, tracker)
+        loss = chi2.sum() / max(1, tracker.ndf_sum)
+        loss.backward()
+        return float(loss), head.grad.detach().cpu().numpy() * sc
+    res = minimize(f, np.zeros(2), jac=True, method="L-BFGS-B",
+                   bounds=[(-bound, bound)] * 2, options=dict(maxiter=iters))
+    du = torch.as_tensor(res.x * sc, dtype=torch.float64, device=base.device)
+    return torch.cat([base[:2] + du, base[2:]])

@@ -100,6 +100,7 @@ _PROTOS = {
     "tpc_get_tracks": (C.c_int, [C.c_void_p, C.POINTER(tpc_tracks)]),
     "tpc_refit": (C.c_int, [C.c_void_p, C.c_int] + [C.c_void_p] * 7),
     "tpc_refit_backward": (C.c_int, [C.c_void_p] + [C.c_void_p] * 4),
+    "tpc_set_vertex": (C.c_int, [C.c_void_p, C.c_void_p, C.c_float]),
     "tpc_merge_tracks": (C.c_int, [C.c_void_p] + [C.c_void_p] * 6 + [C.POINTER(tpc_tracks)]),
     "tpc_merge_tracks_async": (C.c_int, [C.c_void_p] + [C.c_void_p] * 6),
     "tpc_refine_time": (C.c_int, [C.c_void_p] + [C.c_void_p] * 4),
@@ -373,6 +374,18 @@ class Tracker:
             out[k] = out[k][:nt]
         out["rej"] = out["rej"][:na]
         return out
+
+    def set_vertex(self, z_vertex, sigma=0.01):
+        """Vertex pseudo-measurements (device float32 tensor [n_tracks], NaN =
+        none) for the refits of the current track set; None switches them
+        off. The tensor is kept alive here until the next call."""
+        if z_vertex is None:
+            self._keep["vertex"] = None
+            self._ck(self.L.tpc_set_vertex(self.h, None, 0.0), "tpc_set_vertex")
+            return
+        z = z_vertex.to(self.dev, self.torch.float32).contiguous()
+        self._keep["vertex"] = z
+        self._ck(self.L.tpc_set_vertex(self.h, _ptr(z), float(sigma)), "tpc_set_vertex")
 
     def refit_backward(self, dl_dchi2):
         torch = self.torch

@@ -52,6 +52,7 @@ struct tpc_ctx {
   bool tracks_valid = false;
   bool saved = false;
   bool part_alloc = false;
+  const float* saved_vz = nullptr;  // vertex array of the saved refit
   bool capturing = false;
   int64_t calib_version = 0;        // incremented by tpc_set_calib
   int64_t refit_calib_version = -1;  // calibration of the saved refit
@@ -404,7 +405,7 @@ void tpc_destroy(tpc_ctx* ctx) {
                   ctx->mb.pairs, ctx->mb.n_pairs, ctx->mb.n_seg,
                   ctx->mb.hpos, ctx->mb.cpos, ctx->mb.blk_h, ctx->mb.blk_c,
                   ctx->bb.y, ctx->bb.z, ctx->bb.t, ctx->bb.row, ctx->bb.sector, ctx->bb.flags,
-                  ctx->bb.event};
+                  ctx->bb.event, ctx->rb.vck};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
@@ -474,6 +475,7 @@ tpc_status prepare_load(tpc_ctx* ctx, int n_events) {
   ctx->gd.nb_max = kGridBinsMax;
   ctx->gd.ny_max = ctx->tune.grid_ny_max;
   ctx->gd.y_margin = 2.0f;
+  ctx->gd.pads = ctx->cl.pads;
   ctx->gd.z_margin = 1.0f;
   FindBuf& b = ctx->fb;
   if (n > ctx->cap_n || ctx->cap_n == 0) {
@@ -538,6 +540,7 @@ tpc_status prepare_load(tpc_ctx* ctx, int n_events) {
 }
 
 tpc_status tpc_find_tracks_async(tpc_ctx* ctx) {
+  if (ctx) ctx->rb.vz = nullptr;  // a new track set: no vertices
   if (!ctx) return TPC_ERR_ARG;
   if (!ctx->loaded) return fail(ctx, TPC_ERR_STATE, "no batch loaded");
   tpc_status st = ensure_tracklets(ctx);
@@ -673,6 +676,7 @@ tpc_status tpc_get_tracks(tpc_ctx* ctx, tpc_tracks* out) {
 }
 
 tpc_status tpc_set_tracks(tpc_ctx* ctx, const tpc_tracks* t) {
+  if (ctx) ctx->rb.vz = nullptr;  // a new track set: no vertices
   if (!ctx || !t) return fail(ctx, TPC_ERR_ARG, "null argument");
   if (ctx->capturing) return fail(ctx, TPC_ERR_STATE, "tpc_set_tracks synchronises");
   if (!ctx->loaded) return fail(ctx, TPC_ERR_STATE, "no batch loaded");
@@ -718,6 +722,10 @@ tpc_status tpc_refit(tpc_ctx* ctx, int save_for_backward, float* params, float* 
       CK(alloc(ctx->rb.ckpt, need));
       ctx->cap_ckpt_alloc = need;
     }
+    if (ctx->rb.vz && ctx->tb.cap_tr > ctx->rb.cap_vck) {
+      CK(alloc(ctx->rb.vck, ctx->tb.cap_tr * 24));
+      ctx->rb.cap_vck = ctx->tb.cap_tr;
+    }
   }
   // the current calibration applies to the refit inputs (Sec. 4): the
   // calibrated coordinates are recomputed when it changed since the track
@@ -732,7 +740,24 @@ tpc_status tpc_refit(tpc_ctx* ctx, int save_for_backward, float* params, float* 
                ctx->stream);
   CK(cudaGetLastError());
   ctx->saved = save_for_backward != 0;
+  ctx->saved_vz = ctx->rb.vz;
   ctx->refit_calib_version = ctx->calib_version;
+  return TPC_OK;
+}
+
+tpc_status tpc_set_vertex(tpc_ctx* ctx, const float* z_vertex, float sigma) {
+  if (!ctx) return TPC_ERR_ARG;
+  if (ctx->capturing) return fail(ctx, TPC_ERR_STATE, "tpc_set_vertex while capturing");
+  if (!z_vertex) {
+    ctx->rb.vz = nullptr;
+    return TPC_OK;
+  }
+  if (!(sigma > 0.0f)) return fail(ctx, TPC_ERR_ARG, "vertex sigma must be > 0");
+  if (ctx->geo.field_on)
+    return fail(ctx, TPC_ERR_ARG, "the vertex pseudo-measurement needs the uniform field");
+  if (!ctx->tracks_valid) return fail(ctx, TPC_ERR_STATE, "no track set");
+  ctx->rb.vz = z_vertex;
+  ctx->rb.vvar = sigma * sigma;
   return TPC_OK;
 }
 
@@ -783,6 +808,7 @@ tpc_status ensure_merge_buffers(tpc_ctx* ctx, int64_t n_tr, int64_t n_asg) {
 tpc_status tpc_merge_tracks_async(tpc_ctx* ctx, const float* params, const float* cov,
                                   const float* x, const int32_t* status, int32_t* next,
                                   float* link_chi2) {
+  if (ctx) ctx->rb.vz = nullptr;  // a new track set: no vertices
   if (!ctx) return TPC_ERR_ARG;
   if (!ctx->tracks_valid) return fail(ctx, TPC_ERR_STATE, "no track set");
   if (!params || !cov || !x || !status) return fail(ctx, TPC_ERR_ARG, "null segment state");
@@ -806,6 +832,7 @@ tpc_status tpc_merge_tracks(tpc_ctx* ctx, const float* params, const float* cov,
   if (!ctx) return TPC_ERR_ARG;
   if (ctx->capturing) return fail(ctx, TPC_ERR_STATE, "tpc_merge_tracks synchronises");
   if (!ctx->tracks_valid) return fail(ctx, TPC_ERR_STATE, "no track set");
+  ctx->rb.vz = nullptr;  // a new track set: no vertices
   tpc_status st = read_back(ctx);  // segment and cluster counts
   if (st != TPC_OK) return st;
   int64_t nt = ctx->h_pinned[kCntTracks], na = ctx->h_pinned[kCntAssigned];
@@ -888,6 +915,8 @@ tpc_status tpc_refit_backward(tpc_ctx* ctx, const float* dl_dchi2, float* grad_y
   if (!ctx->saved) return fail(ctx, TPC_ERR_STATE, "refit_backward needs a saved refit");
   if (ctx->refit_calib_version != ctx->calib_version)
     return fail(ctx, TPC_ERR_STATE, "calibration changed since the saved refit");
+  if (ctx->saved_vz != ctx->rb.vz)
+    return fail(ctx, TPC_ERR_STATE, "vertex set or cleared since the saved refit");
   if (!dl_dchi2 || !grad_y || !grad_zt || !grad_calib)
     return fail(ctx, TPC_ERR_ARG, "null output");
   if (!ctx->part_alloc) {

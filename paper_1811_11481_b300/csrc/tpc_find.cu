@@ -238,8 +238,17 @@ __global__ void k_scan_rows(Geo g, int K, int n_events, GridDims gd, const uint3
   if (threadIdx.x == 0) *n_bins = carry;
 }
 
-// Bucket order: the input index and, alongside, (y, seeding z), so that the
-// row sorts read their clusters contiguously.
+// Local y (cm) of a grid coordinate. With native pad input (the next step
+// the paper names after Sec. 4: tracking in native pad, row and time
+// coordinates, transformed to space on the fly) the grid keeps each
+// cluster's pad position, and every kernel that reads one turns it into cm
+// with the row's pad pitch and centre (two roundings, as for the input).
+__device__ __forceinline__ float grid_y(const Geo& g, int pads, int r, float v) {
+  return pads ? (v - g.pc[r]) * g.pw[r] : v;
+}
+
+// Bucket order: the input index and, alongside, (y or pad position, seeding
+// z), so that the row sorts read their clusters contiguously.
 __global__ void k_scatter(Geo g, ClIn cl, const uint32_t* row_start, const float* zs_in,
                           uint32_t* fill, uint32_t* perm, float2* pyz) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -250,7 +259,7 @@ __global__ void k_scatter(Geo g, ClIn cl, const uint32_t* row_start, const float
   int key = (e * kNS + s) * g.n_rows + r;
   uint32_t pos = row_start[key] + atomicAdd(&fill[key], 1u);
   perm[pos] = (uint32_t)i;
-  pyz[pos] = make_float2(cluster_y(g, cl, i), zs_in[i]);
+  pyz[pos] = make_float2(cl.y[i], zs_in[i]);
 }
 
 // Search-grid geometry of one (event, sector): tables of nb + 1 bin offsets
@@ -316,7 +325,7 @@ __device__ void sort_bucket(const Geo& g, const GridDims& gd, const Bins& B, int
     if (j < n) {
       uint32_t i = perm[start + j];
       float2 v = pyz[start + j];
-      int b = bin_z(zr, side, B.nz, v.y) * B.ny + bin_y(g, gd, r, B.ny, v.x);
+      int b = bin_z(zr, side, B.nz, v.y) * B.ny + bin_y(g, gd, r, B.ny, grid_y(g, gd.pads, r, v.x));
       k = sort_key(b, i, j);
     }
     keys[j] = k;
@@ -378,7 +387,7 @@ __device__ bool count_sort_bucket(const Geo& g, const GridDims& gd, const Bins& 
   for (int j = threadIdx.x; j < n; j += blockDim.x) {
     uint32_t i = perm[start + j];
     float2 v = pyz[start + j];
-    int b = bin_z(zr, side, B.nz, v.y) * B.ny + bin_y(g, gd, r, B.ny, v.x);
+    int b = bin_z(zr, side, B.nz, v.y) * B.ny + bin_y(g, gd, r, B.ny, grid_y(g, gd.pads, r, v.x));
     si[j] = i;
     kb[j] = (uint16_t)b;
     atomicAdd(&arr[b], 1u);
@@ -481,7 +490,7 @@ __global__ void k_row_sort_warp(Geo g, GridDims gd, int K, const uint32_t* row_s
     if (j < n) {
       uint32_t i = perm[start + j];
       float2 v = pyz[start + j];
-      int b = bin_z(zr, side, B.nz, v.y) * B.ny + bin_y(g, gd, r, B.ny, v.x);
+      int b = bin_z(zr, side, B.nz, v.y) * B.ny + bin_y(g, gd, r, B.ny, grid_y(g, gd.pads, r, v.x));
       k = sort_key(b, i, j);
     }
     keys[j] = k;
@@ -578,7 +587,7 @@ __global__ void k_neighbours(Geo g, Params p, GridDims gd, const uint2* es_dims,
     int side = e * 2 + (s >= 18 ? 1 : 0);
     float xh = g.rx[r], xu = g.rx[r + 1], xd = g.rx[r - 1];
     float2 hh = gyz[h];
-    float yh = hh.x, zh = hh.y;
+    float yh = grid_y(g, gd.pads, r, hh.x), zh = hh.y;
     float dxu = xu - xh, dxd = xh - xd;
     float wy_u = dxu * p.nb_ty + p.nb_wy;
     float wy_d = dxd * p.nb_ty + p.nb_wy;
@@ -600,7 +609,7 @@ __global__ void k_neighbours(Geo g, Params p, GridDims gd, const uint2* es_dims,
       uint32_t u0 = bsu[iz * BB.ny + BU.iy0], u1 = bsu[iz * BB.ny + BU.iy1 + 1];
       for (uint32_t u = u0; u < u1; ++u) {
         float2 uu = gyz[u];
-        float yu = uu.x, zu = uu.y;
+        float yu = grid_y(g, gd.pads, r + 1, uu.x), zu = uu.y;
         if (!(fabsf(yu - yh) <= wy_u)) continue;
         if (!(fabsf(zu - zh) <= wz_u)) continue;
         float py = yh - (yu - yh) * f;
@@ -610,7 +619,7 @@ __global__ void k_neighbours(Geo g, Params p, GridDims gd, const uint2* es_dims,
           uint32_t d0 = bsd[jz * BB.ny + BD.iy0], d1 = bsd[jz * BB.ny + BD.iy1 + 1];
           for (uint32_t d = d0; d < d1; ++d) {
             float2 dd = gyz[d];
-            float yd = dd.x, zd = dd.y;
+            float yd = grid_y(g, gd.pads, r - 1, dd.x), zd = dd.y;
             if (!(fabsf(yd - yh) <= wy_d)) continue;
             if (!(fabsf(zd - zh) <= wz_d)) continue;
             float ey = yd - py, ez = zd - pz;
@@ -753,10 +762,11 @@ __global__ void k_write_starts(const uint32_t* nvalid, const int32_t* upc, const
 
 // ------------------------------------------------------ a7: tracklets
 struct Grid {
-  const float2* gyz;
+  const float2* gyz;  // (y or pad position, seeding z)
   const uint32_t* gorig;
   const uint32_t* bin_start;
   const float* zr;
+  int32_t pads;       // gyz.x holds pad positions
 };
 
 // Calibrated position of a candidate during following (Sec. 4): the seeding z
@@ -822,7 +832,7 @@ __device__ int step_measurement(const Geo& g, const Cal& c, const Params& p, con
                           : lo[3] + (k - c2);
       float2 yz = __ldg(G.gyz + j);
       float yc, zc;
-      calibrate_follow(g, c, spl_on, sec, r, yz.x, yz.y, shift, yc, zc);
+      calibrate_follow(g, c, spl_on, sec, r, grid_y(g, G.pads, r, yz.x), yz.y, shift, yc, zc);
       float ry = yc - st[0];
       float rz = zc - st[1];
       float d2 = Fast::fma(rz * rz, ivz, (ry * ry) * ivy);
@@ -866,7 +876,9 @@ __global__ void k_tl_seed(Geo g, Cal c, Params p, Grid G, int mode, const int32_
     const int seg0 = (int)gseg[h0];
     const int rl = (int)gseg[hl] % g.n_rows, r0 = seg0 % g.n_rows;
     const int sec = (seg0 / g.n_rows) % kNS;
-    const float2 yz0 = G.gyz[h0], yzl = G.gyz[hl];
+    float2 yz0 = G.gyz[h0], yzl = G.gyz[hl];
+    yz0.x = grid_y(g, G.pads, r0, yz0.x);
+    yzl.x = grid_y(g, G.pads, rl, yzl.x);
     float st[5], C[15], x;
     seed_two_points(st, C, x, p.c0t, g.rx[r0], yz0.x, yz0.y, g.rx[rl], yzl.x, yzl.y);
     double that = 0.0;
@@ -893,6 +905,7 @@ __global__ void k_tl_seed(Geo g, Cal c, Params p, Grid G, int mode, const int32_
           break;
         }
         float2 yz = __ldg(G.gyz + h);
+        yz.x = grid_y(g, G.pads, r, yz.x);
         float my = yz.x, mz = yz.y;
         if (pass == 1) calibrate_follow(g, c, spl_on, sec, r, yz.x, yz.y, shift, my, mz);
         apply_update<Fast>(st, C, innovation<Fast>(st, C, my, mz, sig2, sig2));
@@ -1620,7 +1633,7 @@ void launch_find(Prof* P, const Geo& g, const Cal& c, const Params& p, const ClI
     TPC_LAUNCH(P, "k_write_starts", s, k_write_starts<<<nb, kB256, 0, s>>>(b.row_start + K, b.upc, b.dnc, b.off_a,
                                         (uint32_t)b.cap_tl, p.seed_max_hits, b.starts, b.seed_end));
   cudaMemsetAsync(b.weight, 0, sizeof(unsigned long long) * (size_t)(n > 0 ? n : 1), s);
-  Grid G{b.gyz, b.gorig, b.bin_start, b.zr};
+  Grid G{b.gyz, b.gorig, b.bin_start, b.zr, gd.pads};
   // seeds, then the following order (longest predicted first)
   cudaMemsetAsync(b.tl_hist, 0, sizeof(uint32_t) * kLenBuckets, s);
   TPC_LAUNCH(P, "k_tl_seed", s,

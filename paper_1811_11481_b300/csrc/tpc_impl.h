@@ -54,6 +54,7 @@ struct GridDims {
   int32_t ny_max;         // bins along y at most
   float y_margin;         // cm beyond the sector edge
   float z_margin;         // cm beyond the (event, side) z range
+  int32_t pads;           // the grid keeps native pad positions in place of y
 };
 
 // Cluster input as the kernels see it (device pointers).
@@ -173,6 +174,13 @@ struct RefitBuf {
   uint32_t* gmax;         // [1] largest |coordinate gradient| (float bits)
   double* part_cal;       // [n_part_blocks * 2]
   int64_t cap_ckpt;
+  // vertex pseudo-measurements (tpc_set_vertex): the caller's z per track
+  // (NaN: none) or null, their variance, and the states entering the vertex
+  // step of the saved refit
+  const float* vz;
+  float vvar;
+  float* vck;             // [cap_vck * 24]
+  int64_t cap_vck;
 };
 
 // Segment merging (tpc_merge.cu): a copy of the segments being merged and

@@ -181,6 +181,7 @@ __global__ void __launch_bounds__(kB) k_refit(Geo g, RefitCfg p, const uint32_t*
                                                float* o_params, float* o_cov, float* o_x,
                                                float* o_chi2, int32_t* o_ndf, int32_t* o_status,
                                                uint8_t* o_rej, const uint8_t* multi,
+                                               const float* vz, float vvar, float* vck,
                                                uint32_t* err) {
   int tid = blockIdx.x * blockDim.x + threadIdx.x;
   if (tid >= (int)cnt[kCntTracks]) return;
@@ -195,8 +196,9 @@ __global__ void __launch_bounds__(kB) k_refit(Geo g, RefitCfg p, const uint32_t*
   }
   int n = (int)(b - a);
   Lay ly = warp_layout(wbase, wlen, tid);
+  Vertex vx{vz ? vz[T] : NAN, vvar, (vz && save) ? vck + (size_t)T * kVtxCk : nullptr};
   RefitOut o = refit_track<kField>(g, p, win, ly, n, rej, seed_out + (size_t)T * 5,
-                                   save ? ckpt : nullptr, multi[T] != 0);
+                                   save ? ckpt : nullptr, multi[T] != 0, vx);
   if (o.status == 0 && !(fabsf(o.chi2) < 1.0e30f && fabsf(o.st[4]) < 1.0e30f))
     atomicOr(err, kErrNumeric);
   if (o.status != 0) {
@@ -226,6 +228,7 @@ __global__ void __launch_bounds__(kB) k_refit_bwd(Geo g, RefitCfg p, const uint3
                                                    const uint8_t* rej, const int32_t* status,
                                                    const float* ckpt, const float* dl_dchi2,
                                                    float* gyc, float* gzc, const uint8_t* multi,
+                                                   const float* vz, float vvar, float* vck,
                                                    uint32_t* gmax) {
   int tid = blockIdx.x * blockDim.x + threadIdx.x;
   if (tid >= (int)cnt[kCntTracks]) return;
@@ -240,8 +243,9 @@ __global__ void __launch_bounds__(kB) k_refit_bwd(Geo g, RefitCfg p, const uint3
     }
     return;
   }
+  Vertex vx{vz ? vz[T] : NAN, vvar, vz ? vck + (size_t)T * kVtxCk : nullptr};
   refit_backward_track<kField>(g, p, win, ly, n, rej, ckpt, dl_dchi2[T], gyc, gzc,
-                               multi[T] != 0);
+                               multi[T] != 0, vx);
   // largest |gradient| (as float bits, so that NaN ranks above infinity)
   uint32_t m = 0u;
   for (int k = 0; k < n; ++k) {
@@ -526,13 +530,13 @@ void launch_refit(Prof* P, const Geo& g, const Params& p, int64_t cap_tr, const 
                k_refit<true><<<nblk(cap_tr, kB), kB, 0, s>>>(
                    g, make_cfg(g, p), cnt, rb.order, rb.wbase, rb.wlen, tb.track_start, win,
                    rb.seed, rb.rej, rb.status, rb.ckpt, save ? 1 : 0, params, cov, x, chi2, ndf,
-                   status, rej, rb.multi, err));
+                   status, rej, rb.multi, rb.vz, rb.vvar, rb.vck, err));
   else
     TPC_LAUNCH(P, "k_refit", s,
                k_refit<false><<<nblk(cap_tr, kB), kB, 0, s>>>(
                    g, make_cfg(g, p), cnt, rb.order, rb.wbase, rb.wlen, tb.track_start, win,
                    rb.seed, rb.rej, rb.status, rb.ckpt, save ? 1 : 0, params, cov, x, chi2, ndf,
-                   status, rej, rb.multi, err));
+                   status, rej, rb.multi, rb.vz, rb.vvar, rb.vck, err));
 }
 
 void launch_refit_backward(Prof* P, const Geo& g, const Cal& c, const Params& p, const ClIn& cl,
@@ -547,7 +551,8 @@ void launch_refit_backward(Prof* P, const Geo& g, const Cal& c, const Params& p,
                (g.field_on ? k_refit_bwd<true> : k_refit_bwd<false>)<<<nblk(cap_tr, kB), kB, 0,
                                                                        s>>>(
                    g, make_cfg(g, p), cnt, rb.order, rb.wbase, rb.wlen, tb.track_start, win,
-                   rb.rej, rb.status, rb.ckpt, dl_dchi2, rb.gyc, rb.gzc, rb.multi, rb.gmax));
+                   rb.rej, rb.status, rb.ckpt, dl_dchi2, rb.gyc, rb.gzc, rb.multi, rb.vz,
+                   rb.vvar, rb.vck, rb.gmax));
   TPC_LAUNCH(P, "k_calib_grad", s,
              k_calib_grad<<<kCalibGradBlocks, kCgThreads, 0, s>>>(
                  g, c, cl, cnt, tb.cluster_idx, tb.asg_track, tb.track_start, rb.slot, rb.wbase,

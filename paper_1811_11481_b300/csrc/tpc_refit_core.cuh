@@ -294,6 +294,21 @@ struct RefitOut {
   int32_t status;  // 0 ok, 1 propagation failed, 2 no seed
 };
 
+// Optional vertex pseudo-measurement of a track: after pass 3 the state is
+// transported to the beam line (x = 0 in every sector frame) and updated
+// with (y, z) = (0, zv) of variance var each, like a triggered event with a
+// known vertex; it pins the absolute z scale that drift velocity and time
+// offset otherwise share with every track's z0 and tan(lambda). Skipped
+// when zv is NaN or the transport to x = 0 fails (|sin(phi)| would reach
+// its limit). ck (may be null): 24 floats per track, the state (5) and
+// covariance (15) entering the step and 1 when it was applied.
+struct Vertex {
+  float zv;
+  float var;
+  float* ck;
+};
+constexpr int kVtxCk = 24;
+
 // True when the track's clusters lie in more than one sector frame.
 TPC_HD bool spans_frames(const TrackIn& in, const Lay& ly, int n) {
   if (n <= 0) return false;
@@ -310,7 +325,8 @@ TPC_HD bool spans_frames(const TrackIn& in, const Lay& ly, int n) {
 // kField: transport in the full field (propagate_field) instead of the helix.
 template <bool kRot, bool kField>
 TPC_HD RefitOut refit_track_in(const Geo& g, const RefitCfg& p, const TrackIn& in, const Lay& ly,
-                               int n, uint8_t* rej, float* seed_out, float* ckpt) {
+                               int n, uint8_t* rej, float* seed_out, float* ckpt,
+                               const Vertex vx = Vertex{NAN, 0.0f, nullptr}) {
   RefitOut o;
   for (int k = 0; k < n; ++k) rej[ly.at(k)] = 0;
   o.status = 0;
@@ -391,6 +407,27 @@ TPC_HD RefitOut refit_track_in(const Geo& g, const RefitCfg& p, const TrackIn& i
       mz = mz1;
     }
   }
+  if (!kField && !(vx.zv != vx.zv)) {
+    if (vx.ck) {
+      for (int j = 0; j < 5; ++j) vx.ck[j] = st[j];
+      for (int j = 0; j < 15; ++j) vx.ck[5 + j] = C[j];
+      vx.ck[20] = x;
+      vx.ck[21] = 0.0f;
+    }
+    float sv[5], Cv[15], xv = x;
+    for (int j = 0; j < 5; ++j) sv[j] = st[j];
+    for (int j = 0; j < 15; ++j) Cv[j] = C[j];
+    if (propagate(p.kB, p.s_max, sv, Cv, xv, 0.0f)) {
+      Innov iv = innovation(sv, Cv, 0.0f, vx.zv, vx.var, vx.var);
+      apply_update(sv, Cv, iv);
+      for (int j = 0; j < 5; ++j) st[j] = sv[j];
+      for (int j = 0; j < 15; ++j) C[j] = Cv[j];
+      x = xv;
+      chi2 = chi2 + iv.chi2;
+      ndf += 2;
+      if (vx.ck) vx.ck[21] = 1.0f;
+    }
+  }
   o.x = x;
   o.chi2 = chi2;
   o.ndf = ndf;
@@ -401,9 +438,10 @@ TPC_HD RefitOut refit_track_in(const Geo& g, const RefitCfg& p, const TrackIn& i
 // (spans_frames). kField: transport in the full field.
 template <bool kField = false>
 TPC_HD RefitOut refit_track(const Geo& g, const RefitCfg& p, const TrackIn& in, const Lay& ly,
-                            int n, uint8_t* rej, float* seed_out, float* ckpt, bool multi) {
-  return multi ? refit_track_in<true, kField>(g, p, in, ly, n, rej, seed_out, ckpt)
-               : refit_track_in<false, kField>(g, p, in, ly, n, rej, seed_out, ckpt);
+                            int n, uint8_t* rej, float* seed_out, float* ckpt, bool multi,
+                            const Vertex vx = Vertex{NAN, 0.0f, nullptr}) {
+  return multi ? refit_track_in<true, kField>(g, p, in, ly, n, rej, seed_out, ckpt, vx)
+               : refit_track_in<false, kField>(g, p, in, ly, n, rej, seed_out, ckpt, vx);
 }
 
 // ------------------------------------------------------------ dual numbers
@@ -1051,7 +1089,7 @@ TPC_HD bool step_active(int rj, int pass) { return !(rj != 0 && rj < pass); }
 template <bool kRot, bool kField>
 TPC_HD void refit_backward_in(const Geo& g, const RefitCfg& p, const TrackIn& in, const Lay& ly,
                               int n, const uint8_t* rej, const float* ckpt, float gT, float* gyc,
-                              float* gzc) {
+                              float* gzc, const Vertex vx = Vertex{NAN, 0.0f, nullptr}) {
   for (int k = 0; k < n; ++k) {
     gyc[ly.at(k)] = 0.0f;
     gzc[ly.at(k)] = 0.0f;
@@ -1078,6 +1116,25 @@ TPC_HD void refit_backward_in(const Geo& g, const RefitCfg& p, const TrackIn& in
   float pb[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
   float G[15];
   for (int i = 0; i < 15; ++i) G[i] = 0.0f;
+  // the vertex step, when the forward applied it: its update and transport
+  // reversed, which gives the adjoints of pass 3's final state
+  if (!kField && !(vx.zv != vx.zv) && vx.ck && vx.ck[21] != 0.0f) {
+    float pr[5], Cr[15];
+    for (int j = 0; j < 5; ++j) pr[j] = vx.ck[j];
+    for (int j = 0; j < 15; ++j) Cr[j] = vx.ck[5 + j];
+    float xs = vx.ck[20];
+    float pp[5], xx = xs;
+    for (int j = 0; j < 5; ++j) pp[j] = pr[j];
+    Jac J;
+    transport(p.kB, 2.0f, pp, xx, 0.0f, J);
+    float Cp[15];
+    for (int j = 0; j < 15; ++j) Cp[j] = Cr[j];
+    transport_cov(J, Cp);
+    Innov iv = innovation(pp, Cp, 0.0f, vx.zv, vx.var, vx.var);
+    float mb[2];
+    update_adjoint(Cp, iv, gT, pb, G, mb);
+    transport_adjoint(p.kB, 0.0f - xs, pr, Cr, J, pb, G);
+  }
   for (int pass = 3; pass >= 1; --pass) {
     float cbar = pass == 3 ? gT : 0.0f;
     // previous active step (in processing order) at or before k, or -1
@@ -1247,11 +1304,12 @@ TPC_HD void refit_backward_in(const Geo& g, const RefitCfg& p, const TrackIn& in
 template <bool kField = false>
 TPC_HD void refit_backward_track(const Geo& g, const RefitCfg& p, const TrackIn& in, const Lay& ly,
                                  int n, const uint8_t* rej, const float* ckpt, float gT,
-                                 float* gyc, float* gzc, bool multi) {
+                                 float* gyc, float* gzc, bool multi,
+                                 const Vertex vx = Vertex{NAN, 0.0f, nullptr}) {
   if (multi)
-    refit_backward_in<true, kField>(g, p, in, ly, n, rej, ckpt, gT, gyc, gzc);
+    refit_backward_in<true, kField>(g, p, in, ly, n, rej, ckpt, gT, gyc, gzc, vx);
   else
-    refit_backward_in<false, kField>(g, p, in, ly, n, rej, ckpt, gT, gyc, gzc);
+    refit_backward_in<false, kField>(g, p, in, ly, n, rej, ckpt, gT, gyc, gzc, vx);
 }
 
 }  // namespace tpc

@@ -77,6 +77,8 @@ MUTANTS = {
  'joseph_no_kvk': ("      acc = acc + (K[i][0] * vy * K[j][0] + K[i][1] * vz * K[j][1]);\n", ""),
  'joseph_transposed': ("for (int l = 0; l < 5; ++l) acc = acc + AC[i][l] * A[j][l];", "for (int l = 0; l < 5; ++l) acc = acc + AC[i][l] * A[l][j];"),
  'margin_dcut_gradient': ("mg->take(std::fabs(Dv - (double)val(dmax)) / (2.0 * std::sqrt(Dv * kf) * xr));", "mg->take(std::fabs(Dv - (double)val(dmax)) / (2.0 * std::sqrt(Dv) * xr));"),
+ 'vertex_z_sign': ("Innov<R> in = innovation<R>(sv, R(0.0), R(zv), R(vvar), R(vvar));", "Innov<R> in = innovation<R>(sv, R(0.0), R(-zv), R(vvar), R(vvar));"),
+ 'vertex_no_chi2': ("      chi2 = chi2 + in.chi2;\n      ndf += 2;\n      st = sv;", "      ndf += 2;\n      st = sv;"),
  'margin_tie_skipped': ("      mg->take(g > 0.0 ? std::fabs(Dp - Db) / (g * xr) : 0.0);", "      mg->take(g > 0.0 && Dp != Db ? std::fabs(Dp - Db) / (g * xr) : INFINITY);"),
 }
 

@@ -1349,3 +1349,119 @@ def test_field_refit_removes_the_momentum_bias(geo, params):
     qu = np.abs(ru["params"][ok, 4] - truth[ok, 4]) / np.abs(truth[ok, 4])
     assert np.max(qf) < 1e-4, np.max(qf)
     assert np.median(qu) > 20 * np.median(qf) and np.max(qu) > 3e-3, (np.median(qu), np.max(qu))
+
+
+# ------------------------------------------------ vertex pseudo-measurement
+def _vertex_tracks(ev, min_hits=40):
+    """Truth tracks and their vertex z: only a particle's first outgoing leg
+    passes through its vertex (later legs of a looper reach the beam line on
+    another turn), so the other legs get NaN (no vertex)."""
+    ts, ci, tc, sids = synth.truth_tracks(ev, min_hits)
+    lab = ev.label[ci[ts[:-1].astype(np.int64)]]
+    zv = np.asarray(ev.part["zv"], np.float64)[lab]
+    zv[sids % 4 != 0] = np.nan
+    return ts, ci, tc, zv
+
+
+def test_vertex_refit_of_a_noise_free_primary_is_its_helix_at_the_beam_line(geo, params):
+    """With exact clusters and the true vertex the fit ends at the beam line
+    (x = 0) on the generating helix: y = 0, z = the vertex z, and the
+    direction and curvature the pinned transport gives there; chi2 ~ 0."""
+    ev = synth.make_tiny(seed=27, n_tracks=30, sectors=(3,), sigma=0.0)
+    ts, ci, tc, zv = _vertex_tracks(ev)
+    o = _oracle(ev, geo, params)
+    r = o.refit(ts, ci, tc, prec=64, zv=zv, vsigma=0.01)
+    n = 0
+    for k in range(ts.size - 1):
+        if r["status"][k] != 0 or r["x"][k] != 0.0 or np.isnan(zv[k]):
+            continue
+        i = int(ci[ts[k]])
+        x0 = float(geo.row_x[ev.row[i]])
+        truth = np.array([ev.y_true[i], ev.z_true[i], ev.s_true[i], ev.tl_true[i],
+                          ev.q_true[i]])
+        want, _ = o.propagate(truth, x0, 0.0)
+        assert abs(want[0]) < 1e-9 and abs(want[1] - zv[k]) < 1e-9
+        np.testing.assert_allclose(r["params"][k], want, rtol=0, atol=1e-6)
+        # (cluster coordinates are stored in float32)
+        assert r["chi2"][k] < 1e-6 and r["ndf"][k] == 2 * (ts[k + 1] - ts[k]) + 2
+        n += 1
+    assert n >= 15
+
+
+def test_vertex_breaks_the_drift_velocity_and_t0_degeneracy(geo, params):
+    """Reading of how v_drift and t0 become determinable: a change of t0
+    shifts every cluster of a track along z by the same amount, which the
+    track's z0 absorbs, so without a vertex the summed chi2 of the refit does
+    not change; a change of v_drift by a factor 1 + e moves z by an affine
+    map that z0 and tan(lambda) absorb, except that the measurement noise
+    along z is scaled by 1 + e too, so chi2 changes by at most ~2e of itself.
+    With the vertex z fixed both raise chi2 (a triggered event with a known
+    vertex)."""
+    ev = synth.make_tiny(seed=28, n_tracks=200, central=True, mode="time", tf_start=1.0e6,
+                         n_coll=2)
+    ts, ci, tc, zv = _vertex_tracks(ev)
+    nom = synth.nominal_calib()
+
+    def total(dv, dt0, use_zv):
+        cal = synth.nominal_calib()
+        cal.vdrift = nom.vdrift * (1.0 + dv)
+        cal.t0 = nom.t0 + dt0
+        o = _oracle(ev, geo, params, cal)
+        r = o.refit(ts, ci, tc, prec=64, zv=zv if use_zv else None)
+        o.close()
+        return r["chi2"][r["status"] == 0].sum(), (r["status"] == 0).sum()
+
+    c0, n0 = total(0.0, 0.0, False)
+    v0, m0 = total(0.0, 0.0, True)
+    assert n0 > 100 and m0 == n0
+    for dv, dt0, flat in ((2e-3, 0.0, 2.5 * 2e-3), (0.0, 0.02, 1e-6)):
+        c, n = total(dv, dt0, False)
+        v, m = total(dv, dt0, True)
+        assert n == n0 and m == m0
+        print(f"dv {dv} dt0 {dt0}: without vertex {(c - c0) / c0:.2e}, with {(v - v0) / v0:.2e}")
+        assert abs(c - c0) < flat * c0, (dv, dt0, c, c0)
+        assert (v - v0) - abs(c - c0) > 1e-3 * v0, (dv, dt0, v, v0, c, c0)
+
+
+def test_vertex_gradient_matches_finite_differences(geo, params):
+    """The tape gradient of the refit with vertices (drift velocity, t0, a
+    cluster's drift time) against central differences of the FP64 refit."""
+    ev = synth.make_tiny(seed=29, n_tracks=8, sectors=(4,), mode="time", tf_start=1.0e6)
+    ts, ci, tc, zv = _vertex_tracks(ev)
+    nt = min(3, ts.size - 1)
+    ts, ci, tc, zv = ts[:nt + 1], ci[:ts[nt]], tc[:nt], zv[:nt]
+    cal = synth.nominal_calib()
+    o = _oracle(ev, geo, params, cal)
+    r = o.refit(ts, ci, tc, prec=64, zv=zv)
+    assert np.sum(r["x"] == 0.0) >= 2
+    gy, gz, gc = o.refit_grad(ts, ci, tc, r["seeds"], r["rej"], np.ones(nt), zv=zv)
+
+    def loss(vd, t0, dt=None):
+        c = synth.nominal_calib()
+        c.vdrift, c.t0 = vd, t0
+        e = ev
+        if dt is not None:
+            class E:
+                pass
+            e = E()
+            for k in ("mode", "row", "sector", "flags", "event", "n_events", "tf_start", "z",
+                      "y"):
+                setattr(e, k, getattr(ev, k))
+            e.t = ev.t.copy()
+            e.t[dt[0]] += dt[1]
+        oo = _oracle(e, geo, params, c)
+        rr = oo.refit(ts, ci, tc, prec=64, seeds=r["seeds"], rej=r["rej"], zv=zv)
+        oo.close()
+        return float(rr["chi2"].sum())
+
+    for k, e in ((0, 1e-7), (1, 1e-6)):
+        a = [cal.vdrift, cal.t0]
+        a[k] += e
+        b = [cal.vdrift, cal.t0]
+        b[k] -= e
+        fd = (loss(*a) - loss(*b)) / (2 * e)
+        assert abs(fd - gc[k]) < 1e-4 * max(1.0, abs(fd)), (k, fd, gc[k])
+    q = 2
+    i = int(ci[q])
+    fd = (loss(cal.vdrift, cal.t0, (i, 1e-5)) - loss(cal.vdrift, cal.t0, (i, -1e-5))) / 2e-5
+    assert abs(fd - gz[q]) < 1e-4 * max(1.0, abs(fd)), (fd, gz[q])
