@@ -243,8 +243,17 @@ __global__ void k_scan_rows(Geo g, int K, int n_events, GridDims gd, const uint3
 // coordinates, transformed to space on the fly) the grid keeps each
 // cluster's pad position, and every kernel that reads one turns it into cm
 // with the row's pad pitch and centre (two roundings, as for the input).
+// The conversion of one row, loaded once by its reader: the pad centre and
+// pitch, or 0 and 1 without pads ((v - 0) * 1 is v exactly).
+struct RowPad {
+  float c, w;
+  __device__ __forceinline__ float y(float v) const { return (v - c) * w; }
+};
+__device__ __forceinline__ RowPad row_pad(const Geo& g, int pads, int r) {
+  return pads ? RowPad{g.pc[r], g.pw[r]} : RowPad{0.0f, 1.0f};
+}
 __device__ __forceinline__ float grid_y(const Geo& g, int pads, int r, float v) {
-  return pads ? (v - g.pc[r]) * g.pw[r] : v;
+  return row_pad(g, pads, r).y(v);
 }
 
 // Bucket order: the input index and, alongside, (y or pad position, seeding
@@ -587,6 +596,7 @@ __global__ void k_neighbours(Geo g, Params p, GridDims gd, const uint2* es_dims,
     int side = e * 2 + (s >= 18 ? 1 : 0);
     float xh = g.rx[r], xu = g.rx[r + 1], xd = g.rx[r - 1];
     float2 hh = gyz[h];
+    const RowPad pu = row_pad(g, gd.pads, r + 1), pd = row_pad(g, gd.pads, r - 1);
     float yh = grid_y(g, gd.pads, r, hh.x), zh = hh.y;
     float dxu = xu - xh, dxd = xh - xd;
     float wy_u = dxu * p.nb_ty + p.nb_wy;
@@ -602,37 +612,75 @@ __global__ void k_neighbours(Geo g, Params p, GridDims gd, const uint2* es_dims,
                       zh - wz_d - eps, zh + wz_d + eps);
     const uint32_t* bsu = bin_start + BB.base + (size_t)(r + 1) * (BB.nb + 1);
     const uint32_t* bsd = bin_start + BB.base + (size_t)(r - 1) * (BB.nb + 1);
+    // the down candidates inside their windows, once per hit (the windows
+    // do not depend on the up candidate); beyond kNd of them the down box
+    // is scanned again for each up candidate
+    constexpr int kNd = 6;
+    float cy[kNd], cz[kNd];
+    uint32_t cj[kNd];
+    int nd = 0;
+    for (int jz = BD.iz0; jz <= BD.iz1; ++jz) {
+      uint32_t d0 = bsd[jz * BB.ny + BD.iy0], d1 = bsd[jz * BB.ny + BD.iy1 + 1];
+      for (uint32_t d = d0; d < d1; ++d) {
+        float2 dd = gyz[d];
+        float yd = pd.y(dd.x), zd = dd.y;
+        if (!(fabsf(yd - yh) <= wy_d)) continue;
+        if (!(fabsf(zd - zh) <= wz_d)) continue;
+#pragma unroll
+        for (int q = 0; q < kNd; ++q)
+          if (q == nd) {
+            cy[q] = yd;
+            cz[q] = zd;
+            cj[q] = d;
+          }
+        ++nd;
+      }
+    }
     bool found = false;
     float best = 0.0f;
-    uint32_t bou = 0, bod = 0;
-    for (int iz = BU.iz0; iz <= BU.iz1; ++iz) {
+    // a candidate pair against the best so far: smaller deviation, on an
+    // exact tie the lower (up, down) input-index pair (indices loaded then)
+    auto consider = [&](uint32_t u, uint32_t d, float D) {
+      bool take = !found || D < best;
+      if (!take && D == best) {
+        uint32_t ou = gorig[u], od = gorig[d], bou = gorig[bu], bod = gorig[bd];
+        take = ou < bou || (ou == bou && od < bod);
+      }
+      if (take) {
+        found = true;
+        best = D;
+        bu = (int32_t)u;
+        bd = (int32_t)d;
+      }
+    };
+    for (int iz = BU.iz0; nd > 0 && iz <= BU.iz1; ++iz) {
       uint32_t u0 = bsu[iz * BB.ny + BU.iy0], u1 = bsu[iz * BB.ny + BU.iy1 + 1];
       for (uint32_t u = u0; u < u1; ++u) {
         float2 uu = gyz[u];
-        float yu = grid_y(g, gd.pads, r + 1, uu.x), zu = uu.y;
+        float yu = pu.y(uu.x), zu = uu.y;
         if (!(fabsf(yu - yh) <= wy_u)) continue;
         if (!(fabsf(zu - zh) <= wz_u)) continue;
         float py = yh - (yu - yh) * f;
         float pz = zh - (zu - zh) * f;
-        uint32_t ou = gorig[u];
-        for (int jz = BD.iz0; jz <= BD.iz1; ++jz) {
-          uint32_t d0 = bsd[jz * BB.ny + BD.iy0], d1 = bsd[jz * BB.ny + BD.iy1 + 1];
-          for (uint32_t d = d0; d < d1; ++d) {
-            float2 dd = gyz[d];
-            float yd = grid_y(g, gd.pads, r - 1, dd.x), zd = dd.y;
-            if (!(fabsf(yd - yh) <= wy_d)) continue;
-            if (!(fabsf(zd - zh) <= wz_d)) continue;
-            float ey = yd - py, ez = zd - pz;
+        if (nd <= kNd) {
+#pragma unroll
+          for (int q = 0; q < kNd; ++q) {
+            if (q >= nd) break;
+            float ey = cy[q] - py, ez = cz[q] - pz;
             float D = ey * ey + ez * ez;
-            if (!(D <= p.nb_dmax)) continue;
-            uint32_t od = gorig[d];
-            if (!found || D < best || (D == best && (ou < bou || (ou == bou && od < bod)))) {
-              found = true;
-              best = D;
-              bou = ou;
-              bod = od;
-              bu = (int32_t)u;
-              bd = (int32_t)d;
+            if (D <= p.nb_dmax) consider(u, cj[q], D);
+          }
+        } else {
+          for (int jz = BD.iz0; jz <= BD.iz1; ++jz) {
+            uint32_t d0 = bsd[jz * BB.ny + BD.iy0], d1 = bsd[jz * BB.ny + BD.iy1 + 1];
+            for (uint32_t d = d0; d < d1; ++d) {
+              float2 dd = gyz[d];
+              float yd = pd.y(dd.x), zd = dd.y;
+              if (!(fabsf(yd - yh) <= wy_d)) continue;
+              if (!(fabsf(zd - zh) <= wz_d)) continue;
+              float ey = yd - py, ez = zd - pz;
+              float D = ey * ey + ez * ez;
+              if (D <= p.nb_dmax) consider(u, d, D);
             }
           }
         }
@@ -811,6 +859,7 @@ __device__ int step_measurement(const Geo& g, const Cal& c, const Params& p, con
   Box B = make_box(g, gd, G.zr, BB, r, side, yp - wy - dymax - eps, yp + wy + dymax + eps,
                    zp - wz - dzmax - eps, zp + wz + dzmax + eps);
   const uint32_t* __restrict__ bs = G.bin_start + BB.base + (size_t)r * (BB.nb + 1);
+  const RowPad rp = row_pad(g, G.pads, r);
   int best = -1;
   float bd = 0.0f;
   for (int izb = B.iz0; izb <= B.iz1; izb += 4) {
@@ -832,7 +881,7 @@ __device__ int step_measurement(const Geo& g, const Cal& c, const Params& p, con
                           : lo[3] + (k - c2);
       float2 yz = __ldg(G.gyz + j);
       float yc, zc;
-      calibrate_follow(g, c, spl_on, sec, r, grid_y(g, G.pads, r, yz.x), yz.y, shift, yc, zc);
+      calibrate_follow(g, c, spl_on, sec, r, rp.y(yz.x), yz.y, shift, yc, zc);
       float ry = yc - st[0];
       float rz = zc - st[1];
       float d2 = Fast::fma(rz * rz, ivz, (ry * ry) * ivy);
