@@ -579,7 +579,13 @@ def run_ours(args):
         for _ in range(args.profile_steps):
             step()
         kstats, launches = tr.profile_read()
+        nt_p, na_p, _ = tr.counts()
+        nh_p = int(tr.tracklets()["nh"].clamp(min=0).sum().item())
+        # the units one step of this context processes: ncu figures per
+        # launch divided by these give the per-unit figures of the summaries
         print(json.dumps(dict(profile_steps=args.profile_steps, launches=launches,
+                              units=dict(cluster=int(ev.n), tracklet_hit=nh_p,
+                                         assigned_cluster=int(na_p), track=int(nt_p)),
                               kernels={k: v for k, v in kstats.items()})))
         return
     nt, na, ntl = tr.counts()
