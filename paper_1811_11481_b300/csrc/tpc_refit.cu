@@ -294,19 +294,24 @@ __device__ __forceinline__ long long to_fixed(float v, int kx) {
 // The warp then walks the clusters in order; lane l owns two of the 64
 // coefficients of the current cell (and both components) and sums their
 // contributions in registers while the cell stays the same, which along a
-// track it does for many rows. On a change of cell the sums go to the global
-// 64-bit fixed-point totals. Every sum has a fixed order and integer
-// additions commute, so the gradient is reproducible bit for bit.
+// track it does for many rows. On a change of cell the sums go into the
+// warp's table of the current sector in shared memory (each lane adds to its
+// own entries, no atomics); the table goes to the global 64-bit fixed-point
+// totals when the sector changes and at the end (tracks are grouped by
+// sector, so a warp flushes one or two tables). Every sum has a fixed order
+// and integer additions commute, so the gradient is reproducible bit for
+// bit. Four blocks per SM (64 registers, 48 KB of shared memory each).
 constexpr int kCgThreads = 256;
-__global__ void __launch_bounds__(kCgThreads) k_calib_grad(
+__global__ void __launch_bounds__(kCgThreads, 4) k_calib_grad(
     Geo g, Cal c, ClIn cl, const uint32_t* cnt, const uint32_t* cluster_idx,
     const uint32_t* asg_track, const uint32_t* track_start, const uint32_t* slot,
     const uint32_t* wbase, const double* t_coll, const float* gyc, const float* gzc,
     const uint32_t* gmax, float* grad_y, float* grad_zt, unsigned long long* acc_spline,
     double* part_cal) {
-  __shared__ double red[2][kCgThreads / 32];
-  __shared__ float sw[kCgThreads / 32][32][16];  // per lane: weights, gradient, cell
   constexpr int kComp = kSpl * kSpl * kSpl;
+  __shared__ double red[2][kCgThreads / 32];
+  __shared__ float sw[kCgThreads / 32][32][15];  // per lane: weights, gradient, cell
+  __shared__ float tabs[kCgThreads / 32][2 * kComp];  // per warp: one sector's sums
   int n = (int)cnt[kCntAssigned];
   int kx = 0;
   // a non-finite gradient leaves the spline sums to k_calib_reduce (NaN)
@@ -326,13 +331,36 @@ __global__ void __launch_bounds__(kCgThreads) k_calib_grad(
   const int off2 = off1 + 2 * kSpl * kSpl;
   float a01 = 0.f, a02 = 0.f, a11 = 0.f, a12 = 0.f;  // [component][coefficient]
   int cur = -1;                                        // cell base of the sums
-  unsigned long long* acc = acc_spline;
+  float* tab = tabs[w];
+  int tsec = -1;  // sector of the warp's table
+  for (int e = lane; e < 2 * kComp; e += 32) tab[e] = 0.0f;
+  __syncwarp();
+  // the table into the global totals (all lanes, converged)
+  auto flush_table = [&]() {
+    __syncwarp();
+    unsigned long long* acc = acc_spline + (size_t)tsec * 2 * kComp;
+    for (int e = lane; e < 2 * kComp; e += 32) {
+      const long long q = to_fixed(tab[e], kx);
+      if (q != 0) atomicAdd(&acc[e], (unsigned long long)q);
+      tab[e] = 0.0f;
+    }
+    __syncwarp();
+  };
+  // the cell's sums into the table (all lanes, converged: cur is the same on
+  // every lane); a cell's coefficients lie in its sector's 2 * kComp: base
+  // (iw * kSpl + iv) * kSpl + iu with iu, iv, iw <= kSpl - 4, plus offsets
+  // below 3 * (kSpl^2 + kSpl + 1)
   auto flush = [&]() {
-    long long q;
-    if ((q = to_fixed(a01, kx)) != 0) atomicAdd(&acc[cur + off1], (unsigned long long)q);
-    if ((q = to_fixed(a02, kx)) != 0) atomicAdd(&acc[cur + off2], (unsigned long long)q);
-    if ((q = to_fixed(a11, kx)) != 0) atomicAdd(&acc[cur + kComp + off1], (unsigned long long)q);
-    if ((q = to_fixed(a12, kx)) != 0) atomicAdd(&acc[cur + kComp + off2], (unsigned long long)q);
+    const int sec = cur / (2 * kComp);
+    if (sec != tsec) {
+      if (tsec >= 0) flush_table();
+      tsec = sec;
+    }
+    const int lc = cur - sec * 2 * kComp;
+    tab[lc + off1] += a01;
+    tab[lc + off2] += a02;
+    tab[lc + kComp + off1] += a11;
+    tab[lc + kComp + off2] += a12;
     a01 = a02 = a11 = a12 = 0.f;
   };
   for (int b0 = jb; b0 < je; b0 += 32) {
@@ -453,6 +481,7 @@ __global__ void __launch_bounds__(kCgThreads) k_calib_grad(
     __syncwarp();
   }
   if (cur >= 0) flush();
+  if (tsec >= 0) flush_table();
   // block reduction of the float64 sums, in a fixed order
   for (int o = 16; o > 0; o >>= 1) {
     avd += __shfl_down_sync(0xffffffffu, avd, o);
