@@ -999,7 +999,7 @@ __global__ void k_tl_seed(Geo g, Cal c, Params p, Grid G, int mode, const int32_
     }
     if (len >= (uint32_t)kLenBuckets) len = kLenBuckets - 1;
     pred[t] = len;
-    atomicAdd(&hist[kLenBuckets - 1 - len], 1u);
+    warp_counter_add1(hist, kLenBuckets - 1 - len);
   }
 }
 
@@ -1016,7 +1016,7 @@ __global__ void k_tl_order(const uint32_t* cnt, const uint32_t* pred, uint32_t* 
                            uint32_t* order) {
   const int ntl = (int)cnt[kCntStart];
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ntl; t += gridDim.x * blockDim.x)
-    order[atomicAdd(&cursor[kLenBuckets - 1 - pred[t]], 1u)] = (uint32_t)t;
+    order[warp_counter_add1(cursor, kLenBuckets - 1 - pred[t])] = (uint32_t)t;
 }
 
 // Tracklet constructor, part 2: the following, as a persistent step machine.

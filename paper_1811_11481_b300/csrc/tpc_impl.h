@@ -287,6 +287,23 @@ constexpr int kSortTile = 4096;      // pad-row bucket tile of the common sort
 constexpr int kSortTileBig = 16384;  // tile of the large-bucket sort (128 KB)
 constexpr int kCalibGradBlocks = 4 * 148;
 
+#ifdef __CUDACC__
+// atomicAdd(&ctr[key], 1) for every active lane, one atomic per distinct key
+// of the warp: the lanes with the same key take consecutive values in lane
+// order after the group leader's add. Returns the lane's value. Called by
+// converged lanes (the active mask is the set of callers).
+__device__ __forceinline__ uint32_t warp_counter_add1(uint32_t* ctr, uint32_t key) {
+  const unsigned act = __activemask();
+  const unsigned peers = __match_any_sync(act, key);
+  const int lane = (int)(threadIdx.x & 31);
+  const int leader = __ffs(peers) - 1;
+  uint32_t base = 0u;
+  if (lane == leader) base = atomicAdd(&ctr[key], (uint32_t)__popc(peers));
+  base = __shfl_sync(peers, base, leader);
+  return base + (uint32_t)__popc(peers & ((1u << lane) - 1u));
+}
+#endif
+
 // launchers (tpc_find.cu)
 void launch_load(Prof* P, const Geo& g, const Cal& c, const ClIn& cl, const GridDims& gd, int K,
                  FindBuf& b, uint32_t* err, cudaStream_t s);

@@ -61,7 +61,7 @@ __device__ __forceinline__ int len_bin(const uint32_t* ts, int T) {
 __global__ void k_len_hist(const uint32_t* cnt, const uint32_t* ts, uint32_t* hist) {
   int T = blockIdx.x * blockDim.x + threadIdx.x;
   if (T >= (int)cnt[kCntTracks]) return;
-  atomicAdd(&hist[len_bin(ts, T)], 1u);
+  warp_counter_add1(hist, (uint32_t)len_bin(ts, T));
 }
 __global__ void k_len_scan(uint32_t* hist) {
   __shared__ uint32_t s[kLenBins];
@@ -84,7 +84,7 @@ __global__ void k_len_scatter(const uint32_t* cnt, const uint32_t* ts, uint32_t*
   int T = blockIdx.x * blockDim.x + threadIdx.x;
   if (T >= (int)cnt[kCntTracks]) return;
   int b = len_bin(ts, T);
-  uint32_t pos = hist[b] + atomicAdd(&hist[kLenBins + b], 1u);
+  uint32_t pos = hist[b] + warp_counter_add1(hist + kLenBins, (uint32_t)b);
   order[pos] = (uint32_t)T;
   slot[T] = pos;
   multi[T] = 0;  // set by k_interleave for tracks across sector frames
