@@ -124,17 +124,19 @@ template <class O = Exact> TPC_HD float arc_factor_deriv(float h) {
 // Seeding coordinate (Sec. 4): time scaled linearly to z, reference = tf_start.
 TPC_HD float seed_z(const Geo& g, const Cal& c, int mode, float z, double t, int sector) {
   if (mode == 0) return z;
-  double sg = sector < 18 ? 1.0 : -1.0;
   double zeta = c.vdrift * ((t - c.t0) - c.tf_start);
-  return (float)(sg * ((double)g.L - zeta));
+  // the side's sign after the rounding to float: rounding to nearest is
+  // symmetric, so the bits equal those of (float)(sign * (L - zeta))
+  float a = (float)((double)g.L - zeta);
+  return sector < 18 ? a : -a;
 }
 // Absolute z once the collision time 'that' is known (Sec. 4).
 TPC_HD float abs_z(const Geo& g, const Cal& c, int mode, float z, double t, int sector,
                    double that) {
   if (mode == 0) return z;
-  double sg = sector < 18 ? 1.0 : -1.0;
   double zeta = c.vdrift * ((t - c.t0) - that);
-  return (float)(sg * ((double)g.L - zeta));
+  float a = (float)((double)g.L - zeta);  // sign after rounding, as in seed_z
+  return sector < 18 ? a : -a;
 }
 
 // -------------------------------------------------------- distortion spline

@@ -322,7 +322,12 @@ __global__ void __launch_bounds__(kCgThreads, 4) k_calib_grad(
   const int gw = blockIdx.x * (kCgThreads / 32) + w;
   int per = (n + nwarps - 1) / nwarps;
   int jb = gw * per, je = min(n, jb + per);
-  double avd = 0.0, at0 = 0.0;
+  // (v_drift, t0) partial sums of this lane, in a fixed order; the lanes'
+  // sums are added in float64
+  float avd = 0.0f, at0 = 0.0f;
+  // single precision after the drift time: double precision runs at a small
+  // fraction of the single-precision rate, and the gradient needs no more
+  const float vf = (float)c.vdrift;
   const float kS = (float)(kSpl - 3);
   // this lane's two coefficients of a cell: (w, v, u) offsets (cc, bb, aa)
   // with cc = lane / 16 and cc + 2
@@ -379,8 +384,11 @@ __global__ void __launch_bounds__(kCgThreads, 4) k_calib_grad(
       int r = cl.row[i], s = cl.sector[i];
       float x = g.rx[r];
       float y = cluster_y(g, cl, i);
-      float za = abs_z(g, c, cl.mode, cl.mode == 0 ? cl.z[i] : 0.0f,
-                       cl.mode == 1 ? cl.t[i] : 0.0, s, that);
+      // absolute z (Sec. 4): the drift time in float64 (t and the collision
+      // time are large absolute times), the rest in float32
+      const float sgf = s < 18 ? 1.0f : -1.0f;
+      const float dtf = cl.mode == 1 ? (float)((cl.t[i] - c.t0) - that) : 0.0f;
+      float za = cl.mode == 0 ? cl.z[i] : sgf * (g.L - vf * dtf);
       by = gyc[wpos];
       bz = gzc[wpos];
       float ur = (x - c.spl_x0) / c.spl_dx;
@@ -436,10 +444,9 @@ __global__ void __launch_bounds__(kCgThreads, 4) k_calib_grad(
       float gza = by * dDy_dz + bz * (1.0f + dDz_dz);
       grad_y[j] = cl.pads ? gy * g.pw[r] : gy;  // per pad for native input
       if (cl.mode == 1) {
-        double sg = s < 18 ? 1.0 : -1.0;
-        grad_zt[j] = (float)((double)gza * (-sg * c.vdrift));
-        avd += (double)gza * (-sg * ((cl.t[i] - c.t0) - that));
-        at0 += (double)gza * (sg * c.vdrift);
+        grad_zt[j] = gza * (-sgf * vf);
+        avd += gza * (-sgf * dtf);
+        at0 += gza * (sgf * vf);
       } else {
         grad_zt[j] = gza;
       }
@@ -482,14 +489,15 @@ __global__ void __launch_bounds__(kCgThreads, 4) k_calib_grad(
   }
   if (cur >= 0) flush();
   if (tsec >= 0) flush_table();
-  // block reduction of the float64 sums, in a fixed order
+  // block reduction in float64, in a fixed order
+  double dvd = (double)avd, dt0 = (double)at0;
   for (int o = 16; o > 0; o >>= 1) {
-    avd += __shfl_down_sync(0xffffffffu, avd, o);
-    at0 += __shfl_down_sync(0xffffffffu, at0, o);
+    dvd += __shfl_down_sync(0xffffffffu, dvd, o);
+    dt0 += __shfl_down_sync(0xffffffffu, dt0, o);
   }
   if (lane == 0) {
-    red[0][w] = avd;
-    red[1][w] = at0;
+    red[0][w] = dvd;
+    red[1][w] = dt0;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
