@@ -579,8 +579,9 @@ __device__ __forceinline__ Box make_box(const Geo& g, const GridDims& gd, const 
 // ------------------------------------------------------- a4: neighbour finder
 // For hit h in row r: the pair (u in row r+1, d in row r-1) inside the slope
 // windows whose d lies closest to the straight line through h and u; ties go
-// to the lowest pair of input indices.
-__global__ void k_neighbours(Geo g, Params p, GridDims gd, const uint2* es_dims,
+// to the lowest pair of input indices. Held to 64 registers: four blocks per
+// SM instead of three hide more of the dependent grid loads.
+__global__ void __launch_bounds__(256, 4) k_neighbours(Geo g, Params p, GridDims gd, const uint2* es_dims,
                              const uint32_t* nvalid,
                              const float2* __restrict__ gyz, const uint32_t* __restrict__ gorig,
                              const uint32_t* gseg, const uint32_t* bin_start, const float* zr,
@@ -1485,7 +1486,8 @@ __global__ void k_track_end(const uint32_t* cnt, uint32_t* track_start) {
 }
 
 // ---------------------------------------------------- a9: calibration
-__global__ void k_calib(Geo g, Cal c, ClIn cl, const uint32_t* cnt, const uint32_t* cluster_idx,
+// (held to 32 registers: eight blocks per SM for its gathers)
+__global__ void __launch_bounds__(256, 8) k_calib(Geo g, Cal c, ClIn cl, const uint32_t* cnt, const uint32_t* cluster_idx,
                         const uint32_t* asg_track, const double* t_coll, float* yc, float* zc,
                         uint32_t* meta, uint32_t* err) {
   int j = blockIdx.x * blockDim.x + threadIdx.x;
