@@ -472,7 +472,7 @@ tpc_status tpc_profile_read(tpc_ctx* ctx, tpc_kernel_stat* out, int32_t cap, int
  * search grid breaks ties by input index, not by bin; tracks are emitted in
  * an order that does not depend on the grid; the tracklet kernel is built
  * without contracted multiply-adds, so its block size cannot change rounding).
- *   grid_tau            target clusters per search-grid bin (0.25 .. 16)
+ *   grid_tau            target clusters per search-grid bin (0.125 .. 16)
  *   grid_ny_max         grid bins across a row at most (1 .. 64)
  *   tracklet_block      threads per block of the tracklet kernel (64, 128, 256)
  *   tracklet_per_sm     resident tracklet blocks per SM (0 .. 64); 0 = as many
@@ -483,7 +483,7 @@ tpc_status tpc_profile_read(tpc_ctx* ctx, tpc_kernel_stat* out, int32_t cap, int
  * tpc_set_tuning validates (TPC_ERR_ARG) and applies from the next
  * tpc_load_clusters (grid) or tpc_find_tracks (tracklet kernel);
  * TPC_ERR_STATE while capturing. tpc_autotune searches one parameter at a
- * time, in that order, over grid_tau {0.5, 1, 2, 4}, grid_ny_max {8, 16, 32},
+ * time, in that order, over grid_tau {0.25, 0.5, 1, 2, 4}, grid_ny_max {8, 16, 32},
  * tracklet_block {64, 128, 256}, tracklet_regs {0, 96}, tracklet_per_sm
  * {0, 1, 2, 4}, on the loaded
  * batch: each candidate runs load + find (grid parameters) or find (tracklet

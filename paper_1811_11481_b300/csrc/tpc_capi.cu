@@ -1089,7 +1089,7 @@ tpc_status tpc_get_tuning(const tpc_ctx* ctx, tpc_tuning* out) {
 tpc_status tpc_set_tuning(tpc_ctx* ctx, const tpc_tuning* in) {
   if (!ctx || !in) return fail(ctx, TPC_ERR_ARG, "null argument");
   if (ctx->capturing) return fail(ctx, TPC_ERR_STATE, "tuning changes during graph capture");
-  if (!(in->grid_tau >= 0.25f && in->grid_tau <= 16.0f) || in->grid_ny_max < 1 ||
+  if (!(in->grid_tau >= 0.125f && in->grid_tau <= 16.0f) || in->grid_ny_max < 1 ||
       in->grid_ny_max > 64 || !valid_block(in->tracklet_block) || in->tracklet_per_sm < 0 ||
       in->tracklet_per_sm > 64 || (in->tracklet_regs != 0 && in->tracklet_regs != 96))
     return fail(ctx, TPC_ERR_ARG, "tuning out of range");
@@ -1150,7 +1150,7 @@ tpc_status tpc_autotune(tpc_ctx* ctx, int32_t repeats, tpc_tuning* out) {
   };
   auto find = [&]() -> tpc_status { return tpc_find_tracks_async(ctx); };
   // one parameter at a time, in pipeline order; each keeps the best so far
-  const float taus[] = {0.5f, 1.0f, 2.0f, 4.0f};
+  const float taus[] = {0.25f, 0.5f, 1.0f, 2.0f, 4.0f};
   const int nys[] = {8, 16, 32};
   const int blocks[] = {64, 128, 256};
   const int regs[] = {0, 96};
@@ -1165,7 +1165,7 @@ tpc_status tpc_autotune(tpc_ctx* ctx, int32_t repeats, tpc_tuning* out) {
   for (int knob = 0; knob < 5 && st == TPC_OK; ++knob) {
     float best_ms = 0.0f;
     tpc_tuning keep = best;
-    int nc = knob == 0 ? 4 : knob == 1 ? 3 : knob == 2 ? 3 : knob == 3 ? 2 : 4;
+    int nc = knob == 0 ? 5 : knob == 1 ? 3 : knob == 2 ? 3 : knob == 3 ? 2 : 4;
     for (int k = 0; k < nc && st == TPC_OK; ++k) {
       tpc_tuning cand = best;
       if (knob == 0) cand.grid_tau = taus[k];

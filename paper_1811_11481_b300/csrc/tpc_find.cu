@@ -402,16 +402,31 @@ __device__ bool count_sort_bucket(const Geo& g, const GridDims& gd, const Bins& 
     atomicAdd(&arr[b], 1u);
   }
   __syncthreads();
-  // exclusive scan of the counts, in chunks of the block
-  uint32_t carry = 0u;
-  for (int b0 = 0; b0 < B.nb; b0 += blockDim.x) {
-    int q = b0 + threadIdx.x;
-    uint32_t v = q < B.nb ? arr[q] : 0u;
-    if (v > kCountBinMax) atomicMax(&maxc, v);
-    uint32_t tot;
-    uint32_t ex = block_excl_scan(v, &tot);
-    if (q < B.nb) arr[q] = carry + ex;
-    carry += tot;
+  // exclusive scan of the counts: each thread takes a run of consecutive
+  // bins, one block scan of the runs' sums (an odd run length keeps the
+  // threads' strided reads on distinct shared-memory banks)
+  {
+    const int per = ((B.nb + (int)blockDim.x - 1) / (int)blockDim.x) | 1;
+    const int q0 = (int)threadIdx.x * per;
+    uint32_t sum = 0u, mx = 0u;
+    for (int k = 0; k < per; ++k) {
+      const int q = q0 + k;
+      if (q < B.nb) {
+        const uint32_t v = arr[q];
+        sum += v;
+        mx = v > mx ? v : mx;
+      }
+    }
+    if (mx > kCountBinMax) atomicMax(&maxc, mx);
+    uint32_t run = block_excl_scan(sum, nullptr);
+    for (int k = 0; k < per; ++k) {
+      const int q = q0 + k;
+      if (q < B.nb) {
+        const uint32_t v = arr[q];
+        arr[q] = run;
+        run += v;
+      }
+    }
   }
   __syncthreads();
   if (maxc > (uint32_t)kCountBinMax) return false;

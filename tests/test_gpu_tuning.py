@@ -11,7 +11,8 @@ pytestmark = pytest.mark.gpu
 
 # corners of the tuning space (the autotuner's candidates lie inside)
 TUNINGS = [
-    dict(grid_tau=0.25, grid_ny_max=1, tracklet_block=64, tracklet_per_sm=1, tracklet_regs=0),
+    dict(grid_tau=0.125, grid_ny_max=1, tracklet_block=64, tracklet_per_sm=1, tracklet_regs=0),
+    dict(grid_tau=0.25, grid_ny_max=16, tracklet_block=128, tracklet_per_sm=0, tracklet_regs=96),
     dict(grid_tau=4.0, grid_ny_max=64, tracklet_block=256, tracklet_per_sm=0, tracklet_regs=96),
     dict(grid_tau=16.0, grid_ny_max=8, tracklet_block=128, tracklet_per_sm=2, tracklet_regs=96),
     dict(grid_tau=1.0, grid_ny_max=16, tracklet_block=64, tracklet_per_sm=0, tracklet_regs=96),
@@ -61,7 +62,7 @@ def test_autotune_chooses_a_candidate_and_keeps_results():
     cl = tr.upload(ev)
     ref = _run(tr, cl)
     t = tr.autotune(repeats=2)
-    assert t["grid_tau"] in (0.5, 1.0, 2.0, 4.0)
+    assert t["grid_tau"] in (0.25, 0.5, 1.0, 2.0, 4.0)
     assert t["grid_ny_max"] in (8, 16, 32)
     assert t["tracklet_block"] in (64, 128, 256)
     assert t["tracklet_per_sm"] in (0, 1, 2, 4)
