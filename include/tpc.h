@@ -484,8 +484,8 @@ tpc_status tpc_profile_read(tpc_ctx* ctx, tpc_kernel_stat* out, int32_t cap, int
  * tpc_load_clusters (grid) or tpc_find_tracks (tracklet kernel);
  * TPC_ERR_STATE while capturing. tpc_autotune searches one parameter at a
  * time, in that order, over grid_tau {0.25, 0.5, 1, 2, 4}, grid_ny_max {8, 16, 32},
- * tracklet_block {64, 128, 256}, tracklet_regs {0, 96}, tracklet_per_sm
- * {0, 1, 2, 4}, on the loaded
+ * (tracklet_block, tracklet_regs) together over {(64, 0), (128, 0),
+ * (256, 0), (64, 96), (128, 96)}, and tracklet_per_sm {0, 1, 2, 4}, on the loaded
  * batch: each candidate runs load + find (grid parameters) or find (tracklet
  * parameters) `repeats` times (1 .. 50; < 1 means 3) after one untimed run,
  * timed with CUDA events on the context's stream, and the fastest median is

@@ -1152,8 +1152,11 @@ tpc_status tpc_autotune(tpc_ctx* ctx, int32_t repeats, tpc_tuning* out) {
   // one parameter at a time, in pipeline order; each keeps the best so far
   const float taus[] = {0.25f, 0.5f, 1.0f, 2.0f, 4.0f};
   const int nys[] = {8, 16, 32};
-  const int blocks[] = {64, 128, 256};
-  const int regs[] = {0, 96};
+  // the tracklet kernel's block size and register cap together: which block
+  // size is fastest depends on the cap (the 96-register build holds 640
+  // threads per SM with blocks of 64 or 128 only)
+  const int blocks[] = {64, 128, 256, 64, 128};
+  const int regs[] = {0, 0, 0, 96, 96};
   const int pers[] = {0, 1, 2, 4};
   tpc_tuning best = ctx->tune;
   auto trial = [&](tpc_tuning cand, int which, float* ms) -> tpc_status {
@@ -1162,17 +1165,18 @@ tpc_status tpc_autotune(tpc_ctx* ctx, int32_t repeats, tpc_tuning* out) {
     return which == 0 ? time_median(ctx, repeats, load_find, ms)
                       : time_median(ctx, repeats, find, ms);
   };
-  for (int knob = 0; knob < 5 && st == TPC_OK; ++knob) {
+  for (int knob = 0; knob < 4 && st == TPC_OK; ++knob) {
     float best_ms = 0.0f;
     tpc_tuning keep = best;
-    int nc = knob == 0 ? 5 : knob == 1 ? 3 : knob == 2 ? 3 : knob == 3 ? 2 : 4;
+    int nc = knob == 0 ? 5 : knob == 1 ? 3 : knob == 2 ? 5 : 4;
     for (int k = 0; k < nc && st == TPC_OK; ++k) {
       tpc_tuning cand = best;
       if (knob == 0) cand.grid_tau = taus[k];
       else if (knob == 1) cand.grid_ny_max = nys[k];
-      else if (knob == 2) cand.tracklet_block = blocks[k];
-      else if (knob == 3) cand.tracklet_regs = regs[k];
-      else if (knob == 4) {
+      else if (knob == 2) {
+        cand.tracklet_block = blocks[k];
+        cand.tracklet_regs = regs[k];
+      } else if (knob == 3) {
         int mx = tracklet_blocks_per_sm(cand.tracklet_block, cand.tracklet_regs);
         if (pers[k] > 0 && pers[k] >= mx) continue;  // same as "as many as fit"
         cand.tracklet_per_sm = pers[k];
