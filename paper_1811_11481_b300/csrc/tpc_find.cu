@@ -322,7 +322,7 @@ __device__ __forceinline__ uint32_t key_slot(unsigned long long k) {
 __device__ void sort_bucket(const Geo& g, const GridDims& gd, const Bins& B, int seg,
                             uint32_t start, int n, const uint32_t* perm, const float2* pyz,
                             const float* zr, float2* gyz, uint32_t* gorig, uint32_t* gseg,
-                            uint32_t* bs, unsigned long long* keys) {
+                            uint16_t* bs, unsigned long long* keys) {
   int r = seg % g.n_rows;
   int es = seg / g.n_rows;
   int e = es / kNS, s = es % kNS;
@@ -360,9 +360,9 @@ __device__ void sort_bucket(const Geo& g, const GridDims& gd, const Bins& B, int
     unsigned long long k = keys[j];
     int b = key_bin(k);
     int bprev = j > 0 ? key_bin(keys[j - 1]) : -1;
-    for (int q = bprev + 1; q <= b; ++q) bs[q] = start + j;
+    for (int q = bprev + 1; q <= b; ++q) bs[q] = (uint16_t)j;
     if (j == n - 1)
-      for (int q = b + 1; q <= B.nb; ++q) bs[q] = start + n;
+      for (int q = b + 1; q <= B.nb; ++q) bs[q] = (uint16_t)n;
     gyz[start + j] = pyz[start + key_slot(k)];
     gorig[start + j] = key_index(k);
     gseg[start + j] = (uint32_t)seg;
@@ -379,7 +379,7 @@ constexpr int kCountBinMax = 64;
 __device__ bool count_sort_bucket(const Geo& g, const GridDims& gd, const Bins& B, int seg,
                                   uint32_t start, int n, int tile, const uint32_t* perm,
                                   const float2* pyz, const float* zr, float2* gyz,
-                                  uint32_t* gorig, uint32_t* gseg, uint32_t* bs,
+                                  uint32_t* gorig, uint32_t* gseg, uint16_t* bs,
                                   uint32_t* smem) {
   __shared__ uint32_t maxc;
   uint32_t* arr = smem;                 // [nb] counts, then bin ends
@@ -450,7 +450,7 @@ __device__ bool count_sort_bucket(const Geo& g, const GridDims& gd, const Bins& 
   }
   __syncthreads();
   for (int q = threadIdx.x; q <= B.nb; q += blockDim.x)
-    bs[q] = start + (q > 0 ? arr[q - 1] : 0u);
+    bs[q] = (uint16_t)(q > 0 ? arr[q - 1] : 0u);
   for (int j = threadIdx.x; j < n; j += blockDim.x) {
     uint32_t jj = out[j];
     gyz[start + j] = pyz[start + jj];
@@ -464,8 +464,8 @@ __device__ bool count_sort_bucket(const Geo& g, const GridDims& gd, const Bins& 
 // capacity error is raised).
 __device__ void copy_bucket_unsorted(int nb, int seg, uint32_t start, int n,
                                      const uint32_t* perm, const float2* pyz, float2* gyz,
-                                     uint32_t* gorig, uint32_t* gseg, uint32_t* bs) {
-  for (int b = threadIdx.x; b <= nb; b += blockDim.x) bs[b] = start;
+                                     uint32_t* gorig, uint32_t* gseg, uint16_t* bs) {
+  for (int b = threadIdx.x; b <= nb; b += blockDim.x) bs[b] = 0;
   for (int j = threadIdx.x; j < n; j += blockDim.x) {
     gyz[start + j] = pyz[start + j];
     gorig[start + j] = perm[start + j];
@@ -480,7 +480,7 @@ constexpr int kWarpTile = 256;
 __global__ void k_row_sort_warp(Geo g, GridDims gd, int K, const uint32_t* row_start,
                                 const uint2* es_dims, const uint32_t* perm, const float2* pyz,
                                 const float* zr, float2* gyz, uint32_t* gorig, uint32_t* gseg,
-                                uint32_t* bin_start, uint32_t* mid_list, uint32_t* mid_count,
+                                uint16_t* bin_start, uint32_t* mid_list, uint32_t* mid_count,
                                 uint32_t* big_list, uint32_t* big_count) {
   __shared__ unsigned long long tiles[8][kWarpTile];
   int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -491,9 +491,9 @@ __global__ void k_row_sort_warp(Geo g, GridDims gd, int K, const uint32_t* row_s
   int r = seg % g.n_rows;
   int es = seg / g.n_rows;
   Bins B = es_bins(es_dims, es);
-  uint32_t* bs = bin_start + B.base + (size_t)r * (B.nb + 1);
+  uint16_t* bs = bin_start + B.base + (size_t)r * (B.nb + 1);
   if (n == 0) {
-    for (int q = lane; q <= B.nb; q += 32) bs[q] = start;
+    for (int q = lane; q <= B.nb; q += 32) bs[q] = 0;
     return;
   }
   if (n > kSortTile) {
@@ -540,9 +540,9 @@ __global__ void k_row_sort_warp(Geo g, GridDims gd, int K, const uint32_t* row_s
     unsigned long long k = keys[j];
     int b = key_bin(k);
     int bprev = j > 0 ? key_bin(keys[j - 1]) : -1;
-    for (int q = bprev + 1; q <= b; ++q) bs[q] = start + j;
+    for (int q = bprev + 1; q <= b; ++q) bs[q] = (uint16_t)j;
     if (j == n - 1)
-      for (int q = b + 1; q <= B.nb; ++q) bs[q] = start + n;
+      for (int q = b + 1; q <= B.nb; ++q) bs[q] = (uint16_t)n;
     gyz[start + j] = pyz[start + key_slot(k)];
     gorig[start + j] = key_index(k);
     gseg[start + j] = (uint32_t)seg;
@@ -553,7 +553,7 @@ __global__ void k_row_sort_warp(Geo g, GridDims gd, int K, const uint32_t* row_s
 __global__ void k_row_sort_list(Geo g, GridDims gd, int tile, const uint32_t* row_start,
                                 const uint2* es_dims, const uint32_t* perm, const float2* pyz,
                                 const float* zr, float2* gyz, uint32_t* gorig, uint32_t* gseg,
-                                uint32_t* bin_start, const uint32_t* list, const uint32_t* count,
+                                uint16_t* bin_start, const uint32_t* list, const uint32_t* count,
                                 uint32_t* err) {
   extern __shared__ unsigned long long keys[];
   uint32_t* words = reinterpret_cast<uint32_t*>(keys);
@@ -564,7 +564,7 @@ __global__ void k_row_sort_list(Geo g, GridDims gd, int tile, const uint32_t* ro
     int n = (int)(row_start[seg + 1] - start);
     int r = seg % g.n_rows;
     Bins B = es_bins(es_dims, seg / g.n_rows);
-    uint32_t* bs = bin_start + B.base + (size_t)r * (B.nb + 1);
+    uint16_t* bs = bin_start + B.base + (size_t)r * (B.nb + 1);
     if (n > tile) {
       if (threadIdx.x == 0) atomicOr(err, kErrCapRow);
       copy_bucket_unsorted(B.nb, seg, start, n, perm, pyz, gyz, gorig, gseg, bs);
@@ -599,8 +599,9 @@ __device__ __forceinline__ Box make_box(const Geo& g, const GridDims& gd, const 
 __global__ void __launch_bounds__(256, 4) k_neighbours(Geo g, Params p, GridDims gd, const uint2* es_dims,
                              const uint32_t* nvalid,
                              const float2* __restrict__ gyz, const uint32_t* __restrict__ gorig,
-                             const uint32_t* gseg, const uint32_t* bin_start, const float* zr,
-                             int32_t* up, int32_t* dn) {
+                             const uint32_t* gseg, const uint16_t* bin_start,
+                             const uint32_t* row_start, const float* zr, int32_t* up,
+                             int32_t* dn) {
   int h = blockIdx.x * blockDim.x + threadIdx.x;
   if (h >= (int)*nvalid) return;
   int seg = (int)gseg[h];
@@ -626,8 +627,10 @@ __global__ void __launch_bounds__(256, 4) k_neighbours(Geo g, Params p, GridDims
                       zh - wz_u - eps, zh + wz_u + eps);
     Box BD = make_box(g, gd, zr, BB, r - 1, side, yh - wy_d - eps, yh + wy_d + eps,
                       zh - wz_d - eps, zh + wz_d + eps);
-    const uint32_t* bsu = bin_start + BB.base + (size_t)(r + 1) * (BB.nb + 1);
-    const uint32_t* bsd = bin_start + BB.base + (size_t)(r - 1) * (BB.nb + 1);
+    // bin offsets from the bucket starts of rows r + 1 and r - 1
+    const uint16_t* bsu = bin_start + BB.base + (size_t)(r + 1) * (BB.nb + 1);
+    const uint16_t* bsd = bin_start + BB.base + (size_t)(r - 1) * (BB.nb + 1);
+    const uint32_t ru = row_start[seg + 1], rd = row_start[seg - 1];
     // the down candidates inside their windows, once per hit (the windows
     // do not depend on the up candidate); beyond kNd of them the down box
     // is scanned again for each up candidate
@@ -636,7 +639,7 @@ __global__ void __launch_bounds__(256, 4) k_neighbours(Geo g, Params p, GridDims
     uint32_t cj[kNd];
     int nd = 0;
     for (int jz = BD.iz0; jz <= BD.iz1; ++jz) {
-      uint32_t d0 = bsd[jz * BB.ny + BD.iy0], d1 = bsd[jz * BB.ny + BD.iy1 + 1];
+      uint32_t d0 = rd + bsd[jz * BB.ny + BD.iy0], d1 = rd + bsd[jz * BB.ny + BD.iy1 + 1];
       for (uint32_t d = d0; d < d1; ++d) {
         float2 dd = gyz[d];
         float yd = pd.y(dd.x), zd = dd.y;
@@ -670,7 +673,7 @@ __global__ void __launch_bounds__(256, 4) k_neighbours(Geo g, Params p, GridDims
       }
     };
     for (int iz = BU.iz0; nd > 0 && iz <= BU.iz1; ++iz) {
-      uint32_t u0 = bsu[iz * BB.ny + BU.iy0], u1 = bsu[iz * BB.ny + BU.iy1 + 1];
+      uint32_t u0 = ru + bsu[iz * BB.ny + BU.iy0], u1 = ru + bsu[iz * BB.ny + BU.iy1 + 1];
       for (uint32_t u = u0; u < u1; ++u) {
         float2 uu = gyz[u];
         float yu = pu.y(uu.x), zu = uu.y;
@@ -688,7 +691,7 @@ __global__ void __launch_bounds__(256, 4) k_neighbours(Geo g, Params p, GridDims
           }
         } else {
           for (int jz = BD.iz0; jz <= BD.iz1; ++jz) {
-            uint32_t d0 = bsd[jz * BB.ny + BD.iy0], d1 = bsd[jz * BB.ny + BD.iy1 + 1];
+            uint32_t d0 = rd + bsd[jz * BB.ny + BD.iy0], d1 = rd + bsd[jz * BB.ny + BD.iy1 + 1];
             for (uint32_t d = d0; d < d1; ++d) {
               float2 dd = gyz[d];
               float yd = pd.y(dd.x), zd = dd.y;
@@ -828,7 +831,8 @@ __global__ void k_write_starts(const uint32_t* nvalid, const int32_t* upc, const
 struct Grid {
   const float2* gyz;  // (y or pad position, seeding z)
   const uint32_t* gorig;
-  const uint32_t* bin_start;
+  const uint16_t* bin_start;  // per row, from the row's bucket start
+  const uint32_t* row_start;  // bucket starts
   const float* zr;
   int32_t pads;       // gyz.x holds pad positions
 };
@@ -874,7 +878,8 @@ __device__ int step_measurement(const Geo& g, const Cal& c, const Params& p, con
   float yp = st[0], zp = st[1] - shift;
   Box B = make_box(g, gd, G.zr, BB, r, side, yp - wy - dymax - eps, yp + wy + dymax + eps,
                    zp - wz - dzmax - eps, zp + wz + dzmax + eps);
-  const uint32_t* __restrict__ bs = G.bin_start + BB.base + (size_t)r * (BB.nb + 1);
+  const uint16_t* __restrict__ bs = G.bin_start + BB.base + (size_t)r * (BB.nb + 1);
+  const uint32_t rb0 = __ldg(G.row_start + (size_t)(ev * kNS + sec) * g.n_rows + r);
   const RowPad rp = row_pad(g, G.pads, r);
   int best = -1;
   float bd = 0.0f;
@@ -885,8 +890,8 @@ __device__ int step_measurement(const Geo& g, const Cal& c, const Params& p, con
     for (int q = 0; q < 4; ++q) {
       int iz = izb + q;
       bool in = iz <= B.iz1;
-      lo[q] = in ? __ldg(bs + iz * BB.ny + B.iy0) : 0u;
-      hi[q] = in ? __ldg(bs + iz * BB.ny + B.iy1 + 1) : 0u;
+      lo[q] = in ? rb0 + __ldg(bs + iz * BB.ny + B.iy0) : 0u;
+      hi[q] = in ? rb0 + __ldg(bs + iz * BB.ny + B.iy1 + 1) : 0u;
     }
     const uint32_t c0 = hi[0] - lo[0], c1 = c0 + (hi[1] - lo[1]), c2 = c1 + (hi[2] - lo[2]);
     const uint32_t total = c2 + (hi[3] - lo[3]);
@@ -1690,7 +1695,7 @@ void launch_find(Prof* P, const Geo& g, const Cal& c, const Params& p, const ClI
   if (n > 0) {
     const uint32_t* nv = b.row_start + K;
     TPC_LAUNCH(P, "k_neighbours", s, k_neighbours<<<nb, kB256, 0, s>>>(g, p, gd, b.es_dims, nv, b.gyz, b.gorig, b.gseg, b.bin_start,
-                                      b.zr, b.up, b.dn));
+                                      b.row_start, b.zr, b.up, b.dn));
     TPC_LAUNCH(P, "k_clean", s, k_clean<<<nb, kB256, 0, s>>>(nv, b.up, b.dn, b.upc, b.dnc, b.blk_a));
   }
   TPC_LAUNCH(P, "k_scan_blocks", s, k_scan_blocks<<<1, 1024, 0, s>>>(n > 0 ? nb : 0, b.blk_a, b.off_a, nullptr, nullptr, cnt,
@@ -1699,7 +1704,7 @@ void launch_find(Prof* P, const Geo& g, const Cal& c, const Params& p, const ClI
     TPC_LAUNCH(P, "k_write_starts", s, k_write_starts<<<nb, kB256, 0, s>>>(b.row_start + K, b.upc, b.dnc, b.off_a,
                                         (uint32_t)b.cap_tl, p.seed_max_hits, b.starts, b.seed_end));
   cudaMemsetAsync(b.weight, 0, sizeof(unsigned long long) * (size_t)(n > 0 ? n : 1), s);
-  Grid G{b.gyz, b.gorig, b.bin_start, b.zr, gd.pads};
+  Grid G{b.gyz, b.gorig, b.bin_start, b.row_start, b.zr, gd.pads};
   // seeds, then the following order (longest predicted first)
   cudaMemsetAsync(b.tl_hist, 0, sizeof(uint32_t) * kLenBuckets, s);
   TPC_LAUNCH(P, "k_tl_seed", s,

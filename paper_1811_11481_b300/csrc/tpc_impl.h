@@ -96,7 +96,7 @@ struct FindBuf {
   float2* gyz;          // [n] (y, seed z)
   uint32_t* gorig;      // [n] input index
   uint32_t* gseg;       // [n] bucket (event*36 + sector)*n_rows + row
-  uint32_t* bin_start;  // [cap_bins] per row: nb + 1 bin offsets
+  uint16_t* bin_start;  // [cap_bins] per row: nb + 1 bin offsets from the row's bucket start
   uint2* es_dims;       // [n_events * 36]: table base, ny | nz << 16
   uint32_t* n_bins;     // [1] bin-table entries used
   uint32_t* mid_list;   // [K] buckets for the 4096-entry block sort
